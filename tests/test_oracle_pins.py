@@ -1,0 +1,413 @@
+"""Pins for the FP64 oracle: closed forms, the paper's identities and printed values.
+
+Every check here is independent of the oracle's own formulas: a closed form of
+potential theory or Stokes flow, an identity the paper states (Gauss laws, the
+equivalence lemma), a value the paper prints, or a structural property
+(symmetry, definiteness, invariance, spectral convergence).  The last test
+plants plausible mistakes into the oracle and checks that some pin catches each.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from conftest import read_golden
+from oracle import geometry, laplace, stokes
+
+
+def _geo(curves):
+    return geometry.nodes(synth.assemble(curves))
+
+
+# ---------------------------------------------------------------------------
+# P1: circle identities (Section 3.2 DLP2 / Section 4.1 DLP2Stokes on a circle)
+# ---------------------------------------------------------------------------
+def test_circle_laplace_entries_are_constant():
+    # On a circle of radius R, (r . n_a)/|r|^2 = 1/(2R) for every pair, and the
+    # curvature limit -kappa/(4 pi) equals the same constant -1/(4 pi R).
+    R = 1.7
+    geo = _geo([synth.disc(0.3, -0.2, R, 64)])
+    K = laplace.kernel_matrix(geo)
+    expect = -geo["w"][None, :] / (4 * math.pi * R) * np.ones((64, 1))
+    assert np.max(np.abs(K - expect)) < 1e-15
+    # K 1 = -1/2 (on-curve Gauss identity, eq. DLP2)
+    assert np.max(np.abs(K @ np.ones(64) + 0.5)) < 1e-14
+
+
+def test_circle_stokes_rigid_densities_are_null():
+    # Constant and rotational densities give zero interior traction on a circle:
+    # (1/2 I + K) rho = 0 for rho = e1, e2, (x - c)^perp.
+    geo = _geo([synth.disc(-0.4, 0.9, 1.3, 48)])
+    A = 0.5 * np.eye(96) + stokes.kernel_rows(geo, np.arange(48))
+    px, py = stokes.perp(geo)
+    for rho in (np.tile([1.0, 0.0], 48), np.tile([0.0, 1.0], 48),
+                np.stack([px, py], 1).reshape(-1)):
+        assert np.max(np.abs(A @ rho)) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# P5: Gauss identities on non-circular curves (distinguish K from its adjoint)
+# ---------------------------------------------------------------------------
+def test_laplace_gauss_identity_columns():
+    # int_{Gamma_i} dG(x,y)/dn_x ds_x = -1/2 for y on Gamma_i and 0 for y off
+    # D_i (used in the proof of the equivalence lemma, Section 3.5).
+    geo = _geo([synth.star(0, 0, 1.0, 0.3, 5, 0.2, 256), synth.ellipse(4, 0, 1, 0.4, 0.5, 256)])
+    K = laplace.kernel_matrix(geo)
+    col = geo["w"][:, None] * K / geo["w"][None, :]
+    same = col[:256, :256].sum(0)
+    other = col[256:, :256].sum(0)
+    assert np.max(np.abs(same + 0.5)) < 1e-13
+    assert np.max(np.abs(other)) < 1e-13
+    # the row sums are NOT -1/2 (K is not the double layer K*, Section 3.4 remarks)
+    assert np.max(np.abs(K[:256, :256].sum(1) + 0.5)) > 1e-2
+
+
+def test_stokes_gauss_identities_columns():
+    # Force and torque identities of the stresslet (eqs. DLP2Stokes, DLP2StokesTorque):
+    # sum_a w_a K(a,b) = -I/2 and sum_a w_a p_a^T K(a,b) = -p_b^T / 2 on the same
+    # body, and 0 for a source on another body.
+    geo = _geo([synth.ellipse(0, 0, 1, 0.5, 0.4, 192), synth.star(3.5, 0.5, 0.8, 0.2, 4, 1.0, 192)])
+    M = geo["M"]
+    K = stokes.kernel_rows(geo, np.arange(M))
+    wK = geo["w"].repeat(2)[:, None] * K / geo["w"].repeat(2)[None, :]
+    px, py = stokes.perp(geo)
+    for body, sl in ((0, slice(0, 192)), (1, slice(192, 384))):
+        rows = slice(2 * sl.start, 2 * sl.stop)
+        blk = wK[rows, :]
+        fx = blk[0::2].sum(0)
+        fy = blk[1::2].sum(0)
+        tq = (px[sl, None] * blk[0::2] + py[sl, None] * blk[1::2]).sum(0)
+        cols_same = slice(2 * sl.start, 2 * sl.stop)
+        other = slice(0, 2 * 192) if body == 1 else slice(2 * 192, 4 * 192)
+        # force identity: -1/2 delta
+        assert np.max(np.abs(fx[cols_same][0::2] + 0.5)) < 1e-12
+        assert np.max(np.abs(fx[cols_same][1::2])) < 1e-12
+        assert np.max(np.abs(fy[cols_same][1::2] + 0.5)) < 1e-12
+        assert np.max(np.abs(fx[other])) < 1e-12 and np.max(np.abs(fy[other])) < 1e-12
+        # torque identity: -p_b / 2
+        assert np.max(np.abs(tq[cols_same][0::2] + 0.5 * px[sl])) < 1e-12
+        assert np.max(np.abs(tq[cols_same][1::2] + 0.5 * py[sl])) < 1e-12
+        assert np.max(np.abs(tq[other])) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P2/P3/P4: closed-form elastance solutions
+# ---------------------------------------------------------------------------
+def test_single_disc_elastance():
+    R, q = 1.7, 1.3
+    r = laplace.solve(synth.assemble([synth.disc(0.3, -0.2, R, 64)]), np.array([q]))
+    assert abs(r["phi"][0] + q / (2 * math.pi) * math.log(R)) < 1e-14
+    assert np.max(np.abs(r["mu"])) < 1e-14  # the uniform density already equilibrates
+
+
+@pytest.mark.parametrize("a,b,phi", [(1.0, 0.5, 0.3), (1.3, 0.4, 2.0)])
+def test_single_ellipse_logarithmic_capacity(a, b, phi):
+    # The conductor potential of an ellipse with charge q (u -> -(q/2pi) log|x|)
+    # is -(q/2pi) log((a + b)/2): (a + b)/2 is its logarithmic capacity.
+    g = synth.assemble([synth.ellipse(0.1, 0.2, a, b, phi, 256)])
+    r = laplace.solve(g, np.array([1.0]))
+    assert abs(r["phi"][0] + math.log((a + b) / 2) / (2 * math.pi)) < 1e-13
+
+
+@pytest.mark.parametrize("d,n", [(0.5, 256), (0.05, 1024)])
+def test_two_discs_exact_solution(d, n):
+    # Section 6.1.1: u_ex = -(v1/2pi) log(|x - (alpha,0)|/|x + (alpha,0)|) + v2 with
+    # alpha = sqrt(d + d^2/4) is a pair of point charges -/+ v1 at the inverse points,
+    # so charges (Q, -Q) give phi_1 - phi_2 = (Q/pi) log((alpha + d/2)/(alpha - d/2)).
+    Q = 0.8
+    r = laplace.solve(synth.two_discs(d, n), np.array([Q, -Q]))
+    al = math.sqrt(d + d * d / 4)
+    dphi = Q / math.pi * math.log((al + d / 2) / (al - d / 2))
+    assert abs(r["phi"][0] - r["phi"][1] - dphi) < 1e-12
+    assert abs(r["phi"][0] + r["phi"][1]) < 1e-13  # symmetric: u -> 0 at infinity
+
+
+def test_two_discs_paper_table():
+    # The paper's table: q1 and the prescribed potential difference phi1 - phi2.
+    kv, rows = read_golden("two_disc_elastance.txt")
+    dphi_paper = kv["phi1"][0] - kv["phi2"][0]
+    for d, q1, *_ in rows[:2]:
+        n = 256 if d >= 0.5 else 1024
+        Q = -2 * math.pi * q1
+        r = laplace.solve(synth.two_discs(d, n), np.array([Q, -Q]))
+        # 6 printed digits of q1 -> agreement to ~1e-6 relative
+        assert abs((r["phi"][0] - r["phi"][1]) - dphi_paper) < 2e-6 * abs(dphi_paper) + 1e-7
+
+
+# ---------------------------------------------------------------------------
+# closed-form mobility solutions and the paper's two-disc mobility table
+# ---------------------------------------------------------------------------
+def test_single_disc_mobility():
+    # Uniform force density on a circle: interior velocity F (1/2 - log R)/(4 pi)
+    # (log gauge of the Stokeslet); rotation: omega = T/(4 pi R^2).
+    R = 1.7
+    FT = np.array([[0.7, -0.4, 1.1]])
+    r = stokes.solve(synth.assemble([synth.disc(0.3, -0.2, R, 64)]), FT)
+    v = FT[0, :2] * (0.5 - math.log(R)) / (4 * math.pi)
+    assert np.max(np.abs(r["UW"][0, :2] - v)) < 1e-14
+    assert abs(r["UW"][0, 2] - 1.1 / (4 * math.pi * R * R)) < 1e-14
+    assert np.max(np.abs(r["mu"])) < 1e-14
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 0.5), (1.2, 0.3)])
+def test_rotating_ellipse(a, b):
+    # Torque on an elliptic cylinder rotating in Stokes flow (viscosity 1):
+    # T = 2 pi omega (a^2 + b^2); the circle case gives 4 pi R^2 omega.
+    g = synth.assemble([synth.ellipse(0.2, -0.1, a, b, 0.7, 256)])
+    r = stokes.solve(g, np.array([[0.0, 0.0, 1.0]]))
+    assert abs(r["UW"][0, 2] - 1.0 / (2 * math.pi * (a * a + b * b))) < 1e-13
+    assert np.max(np.abs(r["UW"][0, :2])) < 1e-13
+
+
+def test_two_discs_mobility_paper_table():
+    # Section 6.2.1: the tabulated forces/torques must reproduce the prescribed
+    # motion; u_infinity is unknown, so only velocity differences and omegas.
+    kv, rows = read_golden("two_disc_mobility.txt")
+    d, F11, F21, T1, T2 = rows[0][:5]
+    FT = np.array([[F11, F21, T1], [-F11, -F21, T2]])
+    r = stokes.solve(synth.two_discs(d, 256), FT)
+    U = r["UW"]
+    v_disc1 = np.array([kv["v1"][0], kv["v2"][0]])
+    v_disc2 = np.array([kv["v1"][1], kv["v2"][1]])
+    assert np.max(np.abs((U[0, :2] - U[1, :2]) - (v_disc1 - v_disc2))) < 1e-5
+    assert np.max(np.abs(U[:, 2] - np.array(kv["omega"]))) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# P6/P7: constraints and interior constancy/rigidity at the solution
+# ---------------------------------------------------------------------------
+def _three_bodies():
+    return synth.assemble([synth.star(0, 0, 1.0, 0.25, 3, 0.4, 192),
+                           synth.ellipse(3.0, 0.4, 1.0, 0.45, 1.1, 192),
+                           synth.disc(0.5, 3.0, 0.8, 128)])
+
+
+def test_elastance_constraints_and_interior_constancy():
+    g = _three_bodies()
+    q = np.array([1.0, -0.3, 0.55])
+    r = laplace.solve(g, q)
+    geo = r["geo"]
+    net = np.zeros(3)
+    np.add.at(net, geo["body"], geo["w"] * r["mu"])
+    assert np.max(np.abs(net)) < 1e-13  # int mu_i = 0 (equivalence lemma)
+    # u constant inside each conductor: sample 5 interior points per body
+    pts = geometry.interior_points(geo)
+    for i in range(3):
+        off = 0.6 * pts["delta"][i] * np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0.7, -0.7]])
+        u = laplace.single_layer_at(geo, r["nu"], pts["z0x"][i] + off[:, 0], pts["z0y"][i] + off[:, 1])
+        assert np.max(np.abs(u - r["phi"][i])) < 1e-12
+
+
+def test_mobility_constraints_and_rigidity():
+    g = _three_bodies()
+    FT = np.array([[1.0, -0.5, 0.3], [-0.2, 0.9, -1.1], [-0.8, -0.4, 0.6]])
+    r = stokes.solve(g, FT)
+    geo = r["geo"]
+    px, py = stokes.perp(geo)
+    mu = r["mu"]
+    for i in range(3):
+        sl = geo["body"] == i
+        w = geo["w"][sl]
+        assert abs(np.sum(w * mu[0::2][sl])) < 1e-12
+        assert abs(np.sum(w * mu[1::2][sl])) < 1e-12
+        assert abs(np.sum(w * (px[sl] * mu[0::2][sl] + py[sl] * mu[1::2][sl]))) < 1e-12
+    # interior velocity is the rigid motion v + omega (x - z0)^perp
+    pts = geometry.interior_points(geo)
+    for i in range(3):
+        off = 0.8 * pts["delta"][i] * np.array([[0.5, 0.2], [-0.9, 0.1], [0.3, -0.8]])
+        u = stokes.single_layer_at(geo, r["nu"], pts["z0x"][i] + off[:, 0], pts["z0y"][i] + off[:, 1])
+        v, om = r["UW"][i, :2], r["UW"][i, 2]
+        rig = v[None, :] + om * np.stack([-off[:, 1], off[:, 0]], 1)
+        assert np.max(np.abs(u - rig)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P8: symmetry and definiteness of the elastance and mobility matrices
+# ---------------------------------------------------------------------------
+def test_elastance_matrix_symmetric_positive_on_neutral():
+    P = laplace.elastance_matrix(_three_bodies())
+    assert np.max(np.abs(P - P.T)) < 1e-12 * np.max(np.abs(P))
+    # restrict to sum q = 0
+    Q = np.array([[1, 0], [-1, 1], [0, -1]], dtype=float)
+    ev = np.linalg.eigvalsh(Q.T @ P @ Q)
+    assert ev.min() > 0
+
+
+def test_mobility_matrix_symmetric_positive_on_force_free():
+    Mob = stokes.mobility_matrix(_three_bodies())
+    assert np.max(np.abs(Mob - Mob.T)) < 1e-11 * np.max(np.abs(Mob))
+    # loads with zero net force, torques free
+    C = np.zeros((2, 9))
+    C[0, 0::3] = 1
+    C[1, 1::3] = 1
+    _, _, vt = np.linalg.svd(C)
+    Z = vt[2:].T  # null space of the net-force map
+    ev = np.linalg.eigvalsh(Z.T @ Mob @ Z)
+    assert ev.min() > 0
+
+
+# ---------------------------------------------------------------------------
+# P9/P10: invariance and spectral convergence
+# ---------------------------------------------------------------------------
+def _rigidly_moved(g, angle, shift):
+    c, s = math.cos(angle), math.sin(angle)
+    out = dict(g)
+    for a, b in (("x", "y"), ("dx", "dy"), ("ddx", "ddy")):
+        u, v = g[a], g[b]
+        out[a], out[b] = c * u - s * v, s * u + c * v
+    out["x"] = out["x"] + shift[0]
+    out["y"] = out["y"] + shift[1]
+    return out
+
+
+def test_invariance_under_rigid_motion():
+    g = _three_bodies()
+    h = _rigidly_moved(g, 0.9, (5.0, -3.0))
+    q = np.array([1.0, -0.3, -0.7])
+    assert np.max(np.abs(laplace.solve(g, q)["phi"] - laplace.solve(h, q)["phi"])) < 1e-12
+    FT = np.array([[1.0, -0.5, 0.3], [-0.2, 0.9, -1.1], [-0.8, -0.4, 0.6]])
+    c, s = math.cos(0.9), math.sin(0.9)
+    Rm = np.array([[c, -s], [s, c]])
+    FTr = FT.copy()
+    FTr[:, :2] = FT[:, :2] @ Rm.T
+    U = stokes.solve(g, FT)["UW"]
+    Ur = stokes.solve(h, FTr)["UW"]
+    assert np.max(np.abs(Ur[:, :2] - U[:, :2] @ Rm.T)) < 1e-12
+    assert np.max(np.abs(Ur[:, 2] - U[:, 2])) < 1e-12
+
+
+def test_spectral_convergence():
+    q = np.array([1.0, -1.0])
+    vals = []
+    for n in (32, 64, 128, 256):
+        g = synth.assemble([synth.star(0, 0, 1.0, 0.3, 4, 0.3, n), synth.ellipse(2.6, 0.3, 0.9, 0.5, 0.2, n)])
+        vals.append(laplace.solve(g, q)["phi"])
+    diffs = [np.max(np.abs(vals[i + 1] - vals[i])) for i in range(3)]
+    assert diffs[1] < 1e-2 * diffs[0] and diffs[2] < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# equivalence lemma: the total density nu = mu + sigma solves (1/2 I + K + L) nu = L sigma
+# ---------------------------------------------------------------------------
+def test_total_density_form_is_equivalent():
+    g = _three_bodies()
+    q = np.array([1.0, -0.3, 0.55])
+    r = laplace.solve(g, q)
+    geo = r["geo"]
+    A = laplace.operator_matrix(geo)
+    assert np.max(np.abs(A @ r["nu"] - q[geo["body"]])) < 1e-13
+    FT = np.array([[1.0, -0.5, 0.3], [-0.2, 0.9, -1.1], [-0.8, -0.4, 0.6]])
+    s = stokes.solve(g, FT)
+    geo = s["geo"]
+    px, py = stokes.perp(geo)
+    b = geo["body"]
+    f = np.stack([FT[b, 0] + FT[b, 2] * px, FT[b, 1] + FT[b, 2] * py], 1).reshape(-1)
+    assert np.max(np.abs(stokes.operator_matrix(geo) @ s["nu"] - f)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes: each must be caught by at least one pin above
+# ---------------------------------------------------------------------------
+def _laplace_pins_pass():
+    checks = [test_circle_laplace_entries_are_constant, test_laplace_gauss_identity_columns,
+              test_single_disc_elastance,
+              lambda: test_single_ellipse_logarithmic_capacity(1.0, 0.5, 0.3),
+              lambda: test_two_discs_exact_solution(0.5, 256),
+              test_elastance_constraints_and_interior_constancy]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return False
+    return True
+
+
+def _stokes_pins_pass():
+    checks = [test_circle_stokes_rigid_densities_are_null, test_stokes_gauss_identities_columns,
+              test_single_disc_mobility, lambda: test_rotating_ellipse(1.0, 0.5),
+              test_two_discs_mobility_paper_table, test_mobility_constraints_and_rigidity]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return False
+    return True
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    assert _laplace_pins_pass() and _stokes_pins_pass()
+    good_nodes = geometry.nodes
+
+    def source_normal_rows(geo, rows):  # K* (source normal) instead of K
+        rows = np.asarray(rows)
+        rx = geo["x"][rows, None] - geo["x"][None, :]
+        ry = geo["y"][rows, None] - geo["y"][None, :]
+        r2 = rx * rx + ry * ry
+        self_mask = rows[:, None] == np.arange(geo["M"])[None, :]
+        r2 = np.where(self_mask, 1.0, r2)
+        k = -laplace.INV_2PI * (rx * geo["nx"][None, :] + ry * geo["ny"][None, :]) / r2
+        k[self_mask] = -geo["kappa"][rows] / (4 * math.pi)
+        return k * geo["w"][None, :]
+
+    def no_diag_rows(geo, rows, _f=laplace.kernel_rows):
+        k = _f(geo, rows)
+        k[np.arange(len(rows)), np.asarray(rows)] = 0.0
+        return k
+
+    def flipped_sign_rows(geo, rows, _f=laplace.kernel_rows):
+        return -_f(geo, rows)
+
+    def no_completion(geo, rows):
+        return np.zeros((len(rows), geo["M"]))
+
+    def half_weight_nodes(g):
+        geo = good_nodes(g)
+        geo["w"] = geo["w"] * 0.5
+        return geo
+
+    for name, fn in [("kernel_rows", source_normal_rows), ("kernel_rows", no_diag_rows),
+                     ("kernel_rows", flipped_sign_rows), ("completion_rows", no_completion)]:
+        with monkeypatch.context() as m:
+            m.setattr(laplace, name, fn)
+            assert not _laplace_pins_pass(), f"laplace mistake {fn.__name__} not caught"
+    with monkeypatch.context() as m:
+        m.setattr(geometry, "nodes", half_weight_nodes)
+        assert not _laplace_pins_pass()
+
+    def stokes_no_diag(geo, rows, _f=stokes.kernel_rows):
+        k = _f(geo, rows)
+        rows = np.asarray(rows)
+        for c in range(2):
+            for d in range(2):
+                k[2 * np.arange(len(rows)) + c, 2 * rows + d] = 0.0
+        return k
+
+    def stokes_wrong_perp(geo):
+        b = geo["body"]
+        return geo["y"] - geo["yc"][b], -(geo["x"] - geo["xc"][b])
+
+    def stokes_transposed_normal(geo, rows):
+        rows = np.asarray(rows)
+        rx = geo["x"][rows, None] - geo["x"][None, :]
+        ry = geo["y"][rows, None] - geo["y"][None, :]
+        r2 = rx * rx + ry * ry
+        self_mask = rows[:, None] == np.arange(geo["M"])[None, :]
+        r2 = np.where(self_mask, 1.0, r2)
+        c = -stokes.INV_PI * (rx * geo["nx"][None, :] + ry * geo["ny"][None, :]) / (r2 * r2)
+        kxx, kxy, kyy = c * rx * rx, c * rx * ry, c * ry * ry
+        ia = np.nonzero(self_mask)
+        kap = -geo["kappa"][rows] / (2 * math.pi)
+        kxx[ia] = kap * geo["tx"][rows] ** 2
+        kxy[ia] = kap * geo["tx"][rows] * geo["ty"][rows]
+        kyy[ia] = kap * geo["ty"][rows] ** 2
+        w = geo["w"][None, :]
+        o = np.empty((2 * rows.size, 2 * geo["M"]))
+        o[0::2, 0::2], o[0::2, 1::2], o[1::2, 0::2], o[1::2, 1::2] = kxx * w, kxy * w, kxy * w, kyy * w
+        return o
+
+    for name, fn in [("kernel_rows", stokes_no_diag), ("perp", stokes_wrong_perp),
+                     ("kernel_rows", stokes_transposed_normal)]:
+        with monkeypatch.context() as m:
+            m.setattr(stokes, name, fn)
+            assert not _stokes_pins_pass(), f"stokes mistake {fn.__name__} not caught"
