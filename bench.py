@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the elastance/mobility Nystrom-GMRES hot path on GB300.
+
+One step = one complete elastance solve of 100 star curves x 256 nodes
+(M = 25,600): geometry staging, right-hand side, GMRES with FP32 pair sums
+inside FP64 iterative refinement down to a relative residual of 1e-12, and the
+potentials at interior points.  Inputs are resident in HBM when the timed
+region starts; the L2 is flushed (a 256 MB write) before every step, outside
+the per-step CUDA events.
+
+Printed (rank 0, one JSON line): solves/s (mixed precision, whole job), the
+plain-FP64 solves/s beside it, pair interactions/s of the hot pair-sum kernel,
+per-step latency percentiles, the end-to-end rate through the C ABI with host
+buffers, the roofline of the dominant kernel and the CPU-oracle baseline.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank solves its own replica (independent problems, no
+collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "stars100_M25600"
+METRIC = "elastance solves/s at 1e-12 relative residual (mixed precision: FP32 pair sums, FP64 refinement)"
+# algorithmic flops per pair interaction (FMA = 2): Laplace r (2), |r|^2 (3),
+# q/|r|^2 (1), accumulate q r/|r|^2 (4); Stokes r (2), |r|^2 (3), r.mu (3),
+# r.n (3), (r.mu)(r.n)/|r|^4 (3), accumulate (4)
+FLOPS_PER_PAIR = {"laplace": 10.0, "stokes": 18.0}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(rank: int):
+    return synth.star_grid(seed=1000 + rank)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(full_M: int, n_sample_bodies: int = 16):
+    """Time the FP64 oracle on a subset of the same workload and scale to full size.
+
+    The oracle's cost is dense assembly + output (O(M^2)) plus LU (O(M^3));
+    each part is timed and scaled to the full M separately.
+    """
+    import scipy.linalg as sla
+
+    from oracle import geometry, laplace
+
+    g = synth.star_grid(seed=1000, rows=4, cols=n_sample_bodies // 4)
+    M = g["x"].size
+    t0 = time.perf_counter()
+    geo = geometry.nodes(g)
+    sigma = laplace.incident_density(geo, g["q"])
+    A = laplace.operator_matrix(geo)
+    b = laplace.rhs(geo, sigma)
+    t1 = time.perf_counter()
+    lu = sla.lu_factor(A)
+    mu = sla.lu_solve(lu, b)
+    t2 = time.perf_counter()
+    pts = geometry.interior_points(geo)
+    laplace.single_layer_at(geo, mu + sigma, pts["z0x"], pts["z0y"])
+    t3 = time.perf_counter()
+    s = full_M / M
+    t_full = (t1 - t0 + t3 - t2) * s * s + (t2 - t1) * s**3
+    return dict(seconds_sample=t3 - t0, seconds_full_estimate=t_full, M_sample=M)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=cpu_cores())
+    except Exception:
+        return cpu_cores()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    M = 25600
+    for _ in range(args.warmup):
+        oracle_sample_rate(M, 8)
+    per = []
+    for _ in range(args.steps):
+        per.append(oracle_sample_rate(M, 8))
+    secs = [p["seconds_full_estimate"] for p in per]
+    value = len(secs) / sum(secs)
+    sample = (f"oracle (dense assembly + LU + output, FP64, numpy/scipy) on 8 of the 100 stars "
+              f"(M={per[0]['M_sample']}), O(M^2) parts scaled by (25600/M)^2 and LU by (25600/M)^3")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "M": M, "N": 100, "tol": 1e-12},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    from paper_1507_05925_gb300 import bie, build
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = workload(rank)
+    N, M = g["body_start"].size - 1, g["x"].size
+    gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
+    q = torch.from_numpy(g["q"]).to(dev)
+    phi = torch.empty(N, dtype=torch.float64, device=dev)
+    ctx = bie.Context(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    mixed = bie.make_opts(precision=bie.MIXED)
+    fp64 = bie.make_opts(precision=bie.FP64)
+
+    def solve(opts):
+        rc, info = bie.elastance_solve(ctx, gd, q, phi, opts=opts, stream=stream)
+        if rc != bie.OK:
+            raise RuntimeError(f"solve failed: {rc} {ctx.last_error()} {info}")
+        return info
+
+    for _ in range(args.warmup):
+        info = solve(mixed)
+    torch.cuda.synchronize()
+
+    def timed(opts, steps, profile):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.profile(True)
+        infos = []
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            infos.append(solve(opts))
+            e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile(False) if profile else None
+        if dist is not None:
+            dist.barrier()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return ms, infos, prof
+
+    with ClockSampler(local) as cs:
+        ms, infos, prof = timed(mixed, args.steps, True)
+    clocks = cs.summary()
+    phi_mixed = phi.clone()
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # plain FP64 GPU path on the same workload
+    ms64, infos64, prof64 = timed(fp64, args.fp64_steps, True)
+    fp64_rate = len(ms64) / (sum(ms64) / 1000.0)
+
+    # end to end through the C ABI with host (pinned) buffers: the library copies
+    # the geometry and charges in and the potentials out inside the timed call
+    host = {k: torch.from_numpy(np.ascontiguousarray(g[k])).pin_memory() for k in
+            ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+    qh = torch.from_numpy(g["q"]).pin_memory()
+    phih = torch.empty(N, dtype=torch.float64).pin_memory()
+    h2d = sum(int(t.numel() * t.element_size()) for t in host.values()) + qh.numel() * 8
+    d2h = phih.numel() * 8
+    bie.elastance_solve(ctx, host, qh, phih, opts=mixed, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        rc, _ = bie.elastance_solve(ctx, host, qh, phih, opts=mixed, stream=stream)
+        assert rc == bie.OK
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_rate = world * args.e2e_steps / e2e_s
+    assert np.array_equal(phih.numpy(), phi_mixed.cpu().numpy()), "host and device paths disagree"
+
+    # dominant kernel of the timed mixed-precision solves
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 rate
+    launches = prof.pop("kernel_launches")
+    prof64.pop("kernel_launches")
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    kind = dname.split("_")[0]
+    is32 = dname.endswith("fp32")
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    pairs_per_launch = d["pairs"] / max(d["launches"], 1)
+    achieved = FLOPS_PER_PAIR[kind] * pairs_per_launch / (per_launch_ms / 1e3) / 1e12
+    peak = fp32_peak if is32 else fp64_peak
+    lap32 = prof["laplace_fp32"]
+    pair_rate32 = lap32["pairs"] / (lap32["ms"] / 1e3) if lap32["ms"] > 0 else None
+    lap64 = prof64["laplace_fp64"]
+    pair_rate64 = lap64["pairs"] / (lap64["ms"] / 1e3) if lap64["ms"] > 0 else None
+    kernel_share = {k: round(v["ms"] / total_ms * world, 4) for k, v in prof.items() if v["ms"] > 0}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums / f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M, "N": N, "nodes_per_body": 256, "tol": 1e-12,
+                   "precision": "mixed", "l2": "flushed (256 MB write) before every step, outside the events",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "fp64_solves_per_s": fp64_rate,
+        "mixed_over_fp64": value / world / fp64_rate,
+        "pair_interactions_per_s": {"laplace_fp32": pair_rate32, "laplace_fp64": pair_rate64},
+        "solve_info": {"mixed": infos[-1], "fp64": infos64[-1]},
+        "kernel_share_of_step": kernel_share,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "kernel": f"pair sum {dname}", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_note": (f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of measured peaks)"
+                                   if is32 else "FP64: nominal GB300 1.25 TFLOP/s"),
+                     "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = oracle_sample_rate(M, 16)
+        out["cpu_baseline"] = {"value": 1.0 / smp["seconds_full_estimate"], "unit": "solves/s",
+                               "cores": blas_threads(), "kind": "oracle",
+                               "sample": (f"16 of the 100 stars (M={smp['M_sample']}), dense assembly + LU + "
+                                          f"output in {smp['seconds_sample']:.2f} s; O(M^2) parts scaled by "
+                                          f"(25600/M)^2, LU by (25600/M)^3")}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * bie2d.h -- C ABI of the GB300 (sm_103a) library for the resonance-free
+ * second-kind integral equations of the 2D elastance and mobility problems
+ * (Rachh & Greengard, "Integral equation methods for elastance and mobility
+ * problems in two dimensions", arXiv:1507.05925).
+ *
+ * What is computed
+ * ----------------
+ * Elastance (Section 3): N conductors with boundaries Gamma_i carry prescribed
+ * net charges q_i; the exterior potential u is harmonic, constant (= phi_i) on
+ * each Gamma_i and decays at infinity (eqs. of Section 3.1).  With the uniform
+ * incident density sigma_i = q_i/|Gamma_i| (eq. sigma) and u = S(mu + sigma)
+ * (eq. TotRepresentation), mu solves the second-kind equation (eq. ModRep2)
+ *     (1/2 I + K + L) mu = -(1/2 I + K) sigma,
+ *     (K mu)(x) = int dG(x,y)/dn_x mu(y) ds_y,   G = -(1/2pi) log|x - y|,
+ *     (L mu)(x) = int_{Gamma_i} mu ds   for x on Gamma_i.
+ * Mobility (Section 4, viscosity 1): N rigid bodies with prescribed force F_i
+ * and torque T_i (about the arc-length centroid x^c_i) move with (v_i, omega_i).
+ * With rho_i = F_i/|Gamma_i| + T_i (x - x^c_i)^perp / W_i (eq. rho) and
+ * u = S(mu + rho), mu solves (eq. ModRep2Stokes)
+ *     (1/2 I + K + L) mu = -(1/2 I + K) rho,
+ *     (K mu)_k(x) = n_l(x) int T_kml(x,y) mu_m(y) ds_y,  T_ijk = -(1/pi) r_i r_j r_k/|r|^4,
+ *     (L mu)(x) = int_{Gamma_i} mu ds + (x - x^c_i)^perp int ((y - x^c_i)^perp, mu) ds.
+ *
+ * Discretisation: every boundary is sampled at theta_k = 2 pi k / n_i of a
+ * smooth, counter-clockwise parametrisation; the Nystrom quadrature is the
+ * periodic trapezoidal rule with weight w = |x'(theta)| 2 pi / n_i.  The
+ * diagonal of K is its smooth limit -kappa/(4 pi) (Laplace) and
+ * -(kappa/(2 pi)) tau tau^T (Stokes).  GMRES runs on the L2-rescaled unknowns
+ * sqrt(w) mu (Section 6.1.1, rescaled linear system).
+ *
+ * Memory and ownership
+ * --------------------
+ * Every array argument is a plain pointer to HOST or DEVICE memory of the
+ * context's device; the library tells them apart with cudaPointerGetAttributes.
+ * Host inputs are copied in; when any output is host memory the call returns
+ * only after the result has been written.  All device work is ordered on the
+ * given stream (a cudaStream_t passed as void*, NULL = legacy default stream).
+ * Input arrays are read-only and not retained after return; the caller owns
+ * all input and output buffers.  The context owns its device workspace (the
+ * Krylov basis, staged geometry, partial sums), which grows on demand up to
+ * the cap given at creation.  A context is used by one host thread at a time.
+ *
+ * Errors
+ * ------
+ * Every entry point returns a status: 0 OK; > 0 a warning with a valid result;
+ * < 0 an error, outputs untouched.  bie_last_error() gives a one-line message.
+ */
+#ifndef BIE2D_H
+#define BIE2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIE_OK 0
+#define BIE_WARN_NONNEUTRAL 1    /* sum q != 0 (resp. sum F != 0): no decaying solution
+                                    exists (Sections 3.1, 4.1, conservation conditions);
+                                    the result is the free-space log-gauge field u = S(mu+sigma) */
+#define BIE_WARN_NOT_CONVERGED 2 /* tolerance not reached within max_iter; info has the residual */
+#define BIE_ERR_INVALID (-1)     /* bad argument: NULL pointer, N < 1, n_i < 8, non-monotone body_start */
+#define BIE_ERR_OUTSIDE (-2)     /* an interior evaluation point is not inside its body */
+#define BIE_ERR_CUDA (-3)        /* a CUDA call failed (message in bie_last_error) */
+#define BIE_ERR_NOMEM (-5)       /* workspace needed exceeds the context's cap */
+
+#define BIE_KIND_LAPLACE 0       /* elastance operator, scalar density [M] */
+#define BIE_KIND_STOKES 1        /* mobility operator, node-interleaved density [2M] */
+
+#define BIE_PREC_FP64 0          /* all arithmetic in IEEE double */
+#define BIE_PREC_MIXED 1         /* pair sums in FP32 (FP32 accumulation per source tile);
+                                    epilogue, Arnoldi, residuals and outputs in FP64 */
+
+typedef struct bie_ctx bie_ctx;
+
+/* Create a context bound to CUDA device `device`.  workspace_cap_bytes = 0
+ * means no cap.  Returns BIE_OK and sets *ctx, or an error. */
+int bie_create(bie_ctx** ctx, int device, size_t workspace_cap_bytes);
+
+/* Release the context and its device workspace (NULL is ignored). */
+void bie_destroy(bie_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none); owned by ctx. */
+const char* bie_last_error(const bie_ctx* ctx);
+
+/* Boundary geometry.  N bodies, M = body_start[N] nodes in total; body i owns
+ * nodes [body_start[i], body_start[i+1]) sampled at theta_k = 2 pi k / n_i,
+ * k = 0..n_i-1, n_i >= 8, counter-clockwise (Section 2: positively oriented
+ * smooth closed curves).  All arrays float64 except body_start (int32). */
+typedef struct {
+  int32_t n_bodies;            /* N >= 1 */
+  const int32_t* body_start;   /* [N+1], body_start[0] = 0, strictly increasing */
+  const double* x;             /* [M] node x coordinate */
+  const double* y;             /* [M] node y coordinate */
+  const double* dx;            /* [M] dx/dtheta */
+  const double* dy;            /* [M] dy/dtheta */
+  const double* ddx;           /* [M] d2x/dtheta2 (curvature) */
+  const double* ddy;           /* [M] d2y/dtheta2 */
+  const double* interior_pt;   /* [2N] (x, y) per body, or NULL for the arc-length centroid;
+                                  checked by a discrete winding number (BIE_ERR_OUTSIDE) */
+} bie_geometry;
+
+typedef struct {
+  double tol;            /* stop when ||f - A nu|| <= tol ||f|| in the sqrt(w)-scaled 2-norm
+                            (FP64 operator); default 1e-12 when <= 0 */
+  int32_t max_iter;      /* cap on Krylov iterations over all cycles; default 500 when <= 0 */
+  int32_t restart;       /* GMRES restart length m (1..200); default 50 when <= 0 */
+  int32_t precision;     /* BIE_PREC_FP64 or BIE_PREC_MIXED (FP64 iterative refinement
+                            around FP32-pair-sum GMRES) */
+  int32_t formulation;   /* 0: solve for the total density nu = mu + sigma with the
+                            right-hand side L sigma (= q_i on Gamma_i), an identity of the
+                            equivalence lemma (Section 3.5, 4.4); 1: the paper's form with
+                            right-hand side -(1/2 I + K) sigma */
+  int32_t max_refine;    /* mixed: cap on refinement steps; default 8 when <= 0 */
+  double inner_tol;      /* mixed: relative tolerance of each FP32 inner solve; default 1e-6 */
+} bie_opts;
+
+typedef struct {
+  int32_t iters;               /* Krylov iterations (all cycles, all refinement steps) */
+  int32_t refinements;         /* refinement steps taken (mixed), 0 for FP64 */
+  int32_t matvecs_fp64;        /* FP64 operator applications */
+  int32_t matvecs_fp32;        /* FP32-pair-sum operator applications */
+  double rel_residual;         /* final ||f - A nu|| / ||f|| with the FP64 operator */
+  double constraint_residual;  /* max_i |int_{Gamma_i} mu| (and Stokes moments) / max load */
+  double net_load;             /* |sum_i q_i| or |sum_i F_i| */
+} bie_info;
+
+/* Elastance solve (Section 3): charges q [N] -> conductor potentials phi [N].
+ * density (nullable) receives the total density mu + sigma [M] (unscaled).
+ * opts may be NULL (defaults), info may be NULL. */
+int elastance_solve(bie_ctx* ctx, const bie_geometry* geom, const double* q, double* phi,
+                    double* density, const bie_opts* opts, bie_info* info, void* stream);
+
+/* Mobility solve (Section 4): loads FT [3N] = (Fx, Fy, T) per body ->
+ * rigid motions UW [3N] = (vx, vy, omega) per body, omega about the body's
+ * interior point (default the arc-length centroid x^c_i).  density (nullable)
+ * receives mu + rho, node-interleaved [2M]. */
+int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, double* UW,
+                   double* density, const bie_opts* opts, bie_info* info, void* stream);
+
+/* One application of the discrete second-kind operator (eqs. ModRep2,
+ * ModRep2Stokes): out = (1/2 I + K + L) in, on unscaled densities.
+ * kind = BIE_KIND_LAPLACE ([M] in/out) or BIE_KIND_STOKES ([2M], node-interleaved);
+ * precision = BIE_PREC_FP64 or BIE_PREC_MIXED (FP32 pair sum, FP64 epilogue). */
+int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision,
+                   const double* in, double* out, void* stream);
+
+/* Kernel timing of the pair sums (the O(M^2) hot loop), for measurement.
+ * counters[precision][kind]: launches that did work and their summed device
+ * time, taken with CUDA events recorded on the call's stream around each
+ * pair-sum launch (launches skipped after GMRES convergence are not counted),
+ * and the pair interactions they evaluated, M (M - 1) per launch.  enable = 1
+ * clears the counters and starts timing, 0 stops it; out (nullable) receives
+ * the counters so far.  kernel_launches counts every kernel this library
+ * launched (on any stream) since timing was enabled. */
+typedef struct {
+  int64_t launches[2][2];
+  double ms[2][2];
+  double pairs[2][2];
+  int64_t kernel_launches;
+} bie_profile_counters;
+
+int bie_profile(bie_ctx* ctx, int enable, bie_profile_counters* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIE2D_H */

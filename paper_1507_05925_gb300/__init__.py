@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) library for the second-kind integral equations of the 2D
+elastance and mobility problems (Rachh & Greengard, arXiv:1507.05925).
+
+The compute path is the CUDA library libbie2d (C ABI in include/bie2d.h);
+``bie`` is its thin ctypes binding, ``build`` compiles it in-tree.
+"""
+from .bie import (  # noqa: F401
+    ERR_CUDA, ERR_INVALID, ERR_NOMEM, ERR_OUTSIDE, FP64, LAPLACE, MIXED, OK, STOKES,
+    WARN_NONNEUTRAL, WARN_NOT_CONVERGED, Context, apply_operator, elastance_solve, make_opts,
+    mobility_solve,
+)

@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libbie2d (include/bie2d.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all arithmetic runs
+in the CUDA kernels of the library.  Arrays may be torch tensors (CUDA or CPU)
+or numpy arrays: their data pointers are passed as is, and the library tells
+host from device memory.  The library must have been built
+(``paper_1507_05925_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+OK, WARN_NONNEUTRAL, WARN_NOT_CONVERGED = 0, 1, 2
+ERR_INVALID, ERR_OUTSIDE, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -5
+LAPLACE, STOKES = 0, 1
+FP64, MIXED = 0, 1
+
+
+class BieGeometry(ctypes.Structure):
+    _fields_ = [("n_bodies", ctypes.c_int32), ("body_start", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("dx", ctypes.c_void_p), ("dy", ctypes.c_void_p),
+                ("ddx", ctypes.c_void_p), ("ddy", ctypes.c_void_p),
+                ("interior_pt", ctypes.c_void_p)]
+
+
+class BieOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("formulation", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double)]
+
+
+class BieInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("matvecs_fp64", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("constraint_residual", ctypes.c_double),
+                ("net_load", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BieProfileCounters(ctypes.Structure):
+    _fields_ = [("launches", (ctypes.c_int64 * 2) * 2), ("ms", (ctypes.c_double * 2) * 2),
+                ("pairs", (ctypes.c_double * 2) * 2), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        out = {}
+        for p, pn in ((0, "fp64"), (1, "fp32")):
+            for k, kn in ((0, "laplace"), (1, "stokes")):
+                out[f"{kn}_{pn}"] = dict(launches=int(self.launches[p][k]), ms=float(self.ms[p][k]),
+                                         pairs=float(self.pairs[p][k]))
+        out["kernel_launches"] = int(self.kernel_launches)
+        return out
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libbie2d.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbie2d.so is not built ({path}); call paper_1507_05925_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.bie_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
+    lib.bie_create.restype = i32
+    lib.bie_destroy.argtypes = [vp]
+    lib.bie_destroy.restype = None
+    lib.bie_last_error.argtypes = [vp]
+    lib.bie_last_error.restype = ctypes.c_char_p
+    for name in ("elastance_solve", "mobility_solve"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, ctypes.POINTER(BieGeometry), vp, vp, vp, ctypes.POINTER(BieOpts),
+                      ctypes.POINTER(BieInfo), vp]
+        f.restype = i32
+    lib.apply_operator.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
+    lib.apply_operator.restype = i32
+    lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
+    lib.bie_profile.restype = i32
+    _ = dbl
+    _LIB = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/bie2d.h."""
+    with open(os.path.join(_build.INCLUDE, "bie2d.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(?:int|void|const char\*)\s+\**(\w+)\s*\(", text, flags=re.M)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check_dtypes(geom):
+    for k in ("x", "y", "dx", "dy", "ddx", "ddy"):
+        dt = str(geom[k].dtype)
+        if "float64" not in dt:
+            raise TypeError(f"geometry[{k!r}] must be float64, got {dt}")
+    if "int32" not in str(geom["body_start"].dtype):
+        raise TypeError("geometry['body_start'] must be int32")
+
+
+def make_geometry(geom) -> tuple[BieGeometry, list]:
+    """Build the C geometry struct from a dict of arrays; returns (struct, keepalive)."""
+    _check_dtypes(geom)
+    keep = [geom[k] for k in ("body_start", "x", "y", "dx", "dy", "ddx", "ddy")]
+    ipt = geom.get("interior_pt")
+    if ipt is not None:
+        keep.append(ipt)
+    g = BieGeometry(int(geom["body_start"].shape[0]) - 1, _ptr(geom["body_start"]),
+                    _ptr(geom["x"]), _ptr(geom["y"]), _ptr(geom["dx"]), _ptr(geom["dy"]),
+                    _ptr(geom["ddx"]), _ptr(geom["ddy"]), _ptr(ipt))
+    return g, keep
+
+
+def make_opts(tol=1e-12, max_iter=500, restart=50, precision=FP64, formulation=0,
+              max_refine=8, inner_tol=1e-6) -> BieOpts:
+    return BieOpts(tol, max_iter, restart, precision, formulation, max_refine, inner_tol)
+
+
+class Context:
+    """Owns a bie_ctx (device workspace) on one CUDA device."""
+
+    def __init__(self, device: int = 0, workspace_cap_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.bie_create(ctypes.byref(h), device, workspace_cap_bytes)
+        if rc != OK:
+            raise RuntimeError(f"bie_create failed with status {rc}")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.bie_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self.lib.bie_last_error(self.handle).decode()
+
+    def profile(self, enable: bool) -> dict:
+        """bie_profile: returns the pair-sum timing counters so far, then (re)starts or stops timing."""
+        c = BieProfileCounters()
+        rc = self.lib.bie_profile(self.handle, 1 if enable else 0, ctypes.byref(c))
+        if rc != OK:
+            raise RuntimeError(f"bie_profile failed with status {rc}")
+        return c.as_dict()
+
+
+def elastance_solve(ctx: Context, geom, q, phi, density=None, opts: BieOpts | None = None, stream=None):
+    """elastance_solve of include/bie2d.h; returns (status, info dict)."""
+    g, keep = make_geometry(geom)
+    info = BieInfo()
+    rc = ctx.lib.elastance_solve(ctx.handle, ctypes.byref(g), _ptr(q), _ptr(phi), _ptr(density),
+                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(info),
+                                 _stream_ptr(stream))
+    del keep
+    return rc, info.as_dict()
+
+
+def mobility_solve(ctx: Context, geom, FT, UW, density=None, opts: BieOpts | None = None, stream=None):
+    """mobility_solve of include/bie2d.h; returns (status, info dict)."""
+    g, keep = make_geometry(geom)
+    info = BieInfo()
+    rc = ctx.lib.mobility_solve(ctx.handle, ctypes.byref(g), _ptr(FT), _ptr(UW), _ptr(density),
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(info),
+                                _stream_ptr(stream))
+    del keep
+    return rc, info.as_dict()
+
+
+def apply_operator(ctx: Context, geom, kind: int, precision: int, inp, out, stream=None) -> int:
+    """apply_operator of include/bie2d.h: out = (1/2 I + K + L) inp; returns status."""
+    g, keep = make_geometry(geom)
+    rc = ctx.lib.apply_operator(ctx.handle, ctypes.byref(g), kind, precision, _ptr(inp), _ptr(out),
+                                _stream_ptr(stream))
+    del keep
+    return rc

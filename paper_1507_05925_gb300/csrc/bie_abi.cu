@@ -1,0 +1,667 @@
+// C ABI of libbie2d: context, workspace, argument staging and the solver
+// drivers (restarted GMRES in FP64, and FP64 iterative refinement around
+// GMRES with FP32 pair sums).  Every step of the path runs in the kernels of
+// this library; the host only orders launches and reads the convergence state.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/bie2d.h"
+#include "bie_internal.cuh"
+
+using namespace bie;
+
+namespace bie {
+static std::atomic<long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace bie
+
+struct bie_ctx {
+  int device = 0;
+  size_t cap = 0;
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  KState* h_state = nullptr;  // pinned mirror of the device solver state
+  double* h_small = nullptr;  // pinned scratch for small read-backs
+  std::string err;
+  // pair-sum timing (bie_profile)
+  struct Timing {
+    cudaEvent_t a, b;
+    int prec, kind;
+    double pairs;
+    bool valid;
+  };
+  bool prof = false;
+  long long launch_mark = 0;
+  bie_profile_counters counters{};
+  std::vector<cudaEvent_t> pool;
+  std::vector<Timing> pending;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int fail(bie_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, BIE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Bump allocator over the context workspace: a sizing pass (base == nullptr)
+// and a carving pass.
+struct Arena {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Work {
+  Geo g;
+  int kind = 0, n = 0, m = 50;
+  long long ld = 0;
+  // raw input staging
+  int* body_start = nullptr;
+  double *x = nullptr, *y = nullptr, *dx = nullptr, *dy = nullptr, *ddx = nullptr, *ddy = nullptr;
+  double *ipt = nullptr, *load = nullptr, *io_in = nullptr, *io_out = nullptr;
+  // solver
+  double *V = nullptr, *f = nullptr, *xs = nullptr, *r = nullptr, *d = nullptr, *rin = nullptr, *ytmp = nullptr;
+  double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
+  KState* st = nullptr;
+  PairPlan plan64, plan32;
+  int P = 1, grid = 1;
+};
+
+void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool stage_in, bool stage_ipt,
+           bool stage_load, bool stage_io) {
+  const int comps = kind + 1;
+  const long long n = (long long)M * comps;
+  w.kind = kind;
+  w.n = (int)n;
+  w.m = m;
+  w.ld = (n + 31) & ~31LL;
+  Geo& g = w.g;
+  g.N = N;
+  g.M = M;
+  w.body_start = A.take<int>(N + 1);
+  g.body_of = A.take<int>(M);
+  g.x = A.take<double>(M);
+  g.y = A.take<double>(M);
+  g.nx = A.take<double>(M);
+  g.ny = A.take<double>(M);
+  g.w = A.take<double>(M);
+  g.sw = A.take<double>(M);
+  g.kappa = A.take<double>(M);
+  g.pf = A.take<float4>(M);
+  g.nf = A.take<float2>(M);
+  g.len = A.take<double>(N);
+  g.xc = A.take<double>(N);
+  g.yc = A.take<double>(N);
+  g.W = A.take<double>(N);
+  g.zx = A.take<double>(N);
+  g.zy = A.take<double>(N);
+  g.delta = A.take<double>(N);
+  g.wind = A.take<double>(N);
+  if (stage_in) {
+    w.x = A.take<double>(M);
+    w.y = A.take<double>(M);
+    w.dx = A.take<double>(M);
+    w.dy = A.take<double>(M);
+    w.ddx = A.take<double>(M);
+    w.ddy = A.take<double>(M);
+  }
+  if (stage_ipt) w.ipt = A.take<double>(2 * N);
+  if (stage_load) w.load = A.take<double>(3 * N);
+  if (stage_io) {
+    w.io_in = A.take<double>(n);
+    w.io_out = A.take<double>(n);
+  }
+  w.plan64 = plan_pairs(M, kind, 0);
+  w.plan32 = plan_pairs(M, kind, 1);
+  const int S = std::max(w.plan64.S, w.plan32.S);
+  w.partial = A.take<double>((size_t)S * n);
+  w.grid = vec_grid(n);
+  w.part = A.take<double>((size_t)w.grid * 201 + 64);
+  w.st = A.take<KState>(1);
+  if (solve) {
+    w.V = A.take<double>((size_t)(m + 1) * w.ld);
+    w.f = A.take<double>(n);
+    w.xs = A.take<double>(n);
+    w.r = A.take<double>(n);
+    w.d = A.take<double>(n);
+    w.rin = A.take<double>(n);
+    w.ytmp = A.take<double>(n);
+    w.H = A.take<double>((size_t)(m + 1) * m);
+    w.cs = A.take<double>(m);
+    w.sn = A.take<double>(m);
+    w.gv = A.take<double>(m + 1);
+    w.yv = A.take<double>(m + 1);
+    w.h1 = A.take<double>(201);
+    w.h2 = A.take<double>(201);
+    w.P = output_splits(g, kind);
+    const int targets = kind == 0 ? N : 3 * N;
+    w.outpart = A.take<double>((size_t)w.P * targets * comps + N + 2);
+    w.outv = A.take<double>(3 * N);
+    w.cres = A.take<double>(1);
+  }
+}
+
+int ensure_ws(bie_ctx* ctx, size_t need) {
+  if (need <= ctx->ws_size) return BIE_OK;
+  if (ctx->cap && need > ctx->cap)
+    return fail(ctx, BIE_ERR_NOMEM, "workspace of " + std::to_string(need) + " bytes exceeds the cap of " +
+                                        std::to_string(ctx->cap));
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+  }
+  CK(cudaMalloc(&ctx->ws, need));
+  ctx->ws_size = need;
+  return BIE_OK;
+}
+
+// Copies a host array into staging (or passes a device pointer through).
+template <class T>
+int stage_in(bie_ctx* ctx, const T* src, T* staging, size_t count, const T** out, cudaStream_t s) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return BIE_OK;
+  }
+  CK(cudaMemcpyAsync(staging, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = staging;
+  return BIE_OK;
+}
+
+// Host-side argument checks; fills host copy of body_start.
+int validate(bie_ctx* ctx, const bie_geometry* geom, std::vector<int>& bs) {
+  if (!ctx) return BIE_ERR_INVALID;
+  if (!geom) return fail(ctx, BIE_ERR_INVALID, "geometry is NULL");
+  if (geom->n_bodies < 1) return fail(ctx, BIE_ERR_INVALID, "n_bodies must be >= 1");
+  if (!geom->body_start || !geom->x || !geom->y || !geom->dx || !geom->dy || !geom->ddx || !geom->ddy)
+    return fail(ctx, BIE_ERR_INVALID, "a geometry array is NULL");
+  const int N = geom->n_bodies;
+  bs.resize(N + 1);
+  if (is_device_ptr(geom->body_start)) {
+    CK(cudaMemcpy(bs.data(), geom->body_start, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(bs.data(), geom->body_start, (N + 1) * sizeof(int));
+  }
+  if (bs[0] != 0) return fail(ctx, BIE_ERR_INVALID, "body_start[0] must be 0");
+  for (int i = 0; i < N; ++i)
+    if (bs[i + 1] - bs[i] < 8)
+      return fail(ctx, BIE_ERR_INVALID, "body " + std::to_string(i) + " has fewer than 8 nodes");
+  if ((long long)bs[N] * 2 > 0x7fffffffLL) return fail(ctx, BIE_ERR_INVALID, "too many nodes");
+  return BIE_OK;
+}
+
+// Stage the inputs and the geometry; check that the interior points lie inside.
+int setup(bie_ctx* ctx, const bie_geometry* geom, const std::vector<int>& bs, Work& w, cudaStream_t s) {
+  const int N = geom->n_bodies, M = bs[N];
+  CK(cudaMemcpyAsync(w.body_start, bs.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  w.g.body_start = w.body_start;
+  const double *x, *y, *dx, *dy, *ddx, *ddy, *ipt = nullptr;
+  int rc;
+  if ((rc = stage_in(ctx, geom->x, w.x, M, &x, s)) ||
+      (rc = stage_in(ctx, geom->y, w.y, M, &y, s)) ||
+      (rc = stage_in(ctx, geom->dx, w.dx, M, &dx, s)) ||
+      (rc = stage_in(ctx, geom->dy, w.dy, M, &dy, s)) ||
+      (rc = stage_in(ctx, geom->ddx, w.ddx, M, &ddx, s)) ||
+      (rc = stage_in(ctx, geom->ddy, w.ddy, M, &ddy, s)))
+    return rc;
+  if (geom->interior_pt && (rc = stage_in(ctx, geom->interior_pt, w.ipt, 2 * (size_t)N, &ipt, s)))
+    return rc;
+  CK(stage_geometry(w.g, x, y, dx, dy, ddx, ddy, ipt, s));
+  return BIE_OK;
+}
+
+int check_inside(bie_ctx* ctx, const Work& w, cudaStream_t s) {
+  std::vector<double> wind(w.g.N);
+  CK(cudaMemcpyAsync(wind.data(), w.g.wind, w.g.N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < w.g.N; ++i)
+    if (!(fabs(wind[i] - 1.0) < 0.5))
+      return fail(ctx, BIE_ERR_OUTSIDE,
+                  "interior point of body " + std::to_string(i) + " is not inside it (winding number " +
+                      std::to_string(wind[i]) + "); is the curve counter-clockwise?");
+  return BIE_OK;
+}
+
+cudaEvent_t take_event(bie_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Accumulate finished timings; with wait, block until all have finished.
+void resolve_timings(bie_ctx* ctx, bool wait) {
+  std::vector<bie_ctx::Timing> keep;
+  for (auto& t : ctx->pending) {
+    if (!wait && cudaEventQuery(t.b) != cudaSuccess) {
+      cudaGetLastError();
+      keep.push_back(t);
+      continue;
+    }
+    if (wait) cudaEventSynchronize(t.b);
+    if (t.valid) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+        ctx->counters.launches[t.prec][t.kind] += 1;
+        ctx->counters.ms[t.prec][t.kind] += ms;
+        ctx->counters.pairs[t.prec][t.kind] += t.pairs;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    ctx->pool.push_back(t.a);
+    ctx->pool.push_back(t.b);
+  }
+  ctx->pending.swap(keep);
+}
+
+// Pair sum with optional event timing.  valid = false marks a launch inside a
+// GMRES chunk whose validity is known only after the next state read.
+cudaError_t timed_pair_sum(bie_ctx* ctx, const Geo& g, int kind, int prec, const PairPlan& p, VecRef v,
+                           const double* sscale, double* partial, const int* stop, bool valid,
+                           cudaStream_t s) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ctx->prof) {
+    a = take_event(ctx);
+    b = take_event(ctx);
+    if (a && b) cudaEventRecord(a, s);
+  }
+  cudaError_t e = pair_sum(g, kind, prec, p, v, sscale, partial, stop, s);
+  if (a && b) {
+    cudaEventRecord(b, s);
+    ctx->pending.push_back({a, b, prec, kind, (double)g.M * (double)(g.M - 1), valid});
+  }
+  return e;
+}
+
+// The operator (1/2 I + K + L) on sqrt(w)-scaled vectors, in FP64 or FP32 pair sums.
+struct Op {
+  bie_ctx* ctx;
+  const Work* w;
+  int prec;
+  cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
+    const PairPlan& p = prec == 0 ? w->plan64 : w->plan32;
+    cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
+    if (e != cudaSuccess) return e;
+    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s);
+  }
+};
+
+struct KrylovResult {
+  int iters = 0, matvecs = 0, matvecs64 = 0;
+  double res = 0.0, bnorm = 0.0;
+  bool converged = false;
+};
+
+int read_state(bie_ctx* ctx, const Work& w, cudaStream_t s) {
+  CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+// Restarted GMRES from x = 0 on A x = b until ||b - A x|| <= tol_rel ||b||.
+// Each cycle minimises over x + span(V) with V_0 = r/||r||, so gmres_update
+// adds V y into x and a restart only needs the explicit residual.  With
+// verify, convergence is confirmed by an explicit residual of the FP64 operator.
+int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
+  const long long n = w.n, ld = w.ld;
+  const VecRef vj{w.V, ld, &w.st->j, 0}, vj1{w.V, ld, &w.st->j, 1};
+  int chunk = 4, rc;
+  int iters_before = ctx->h_state->iters;
+  for (;;) {
+    const size_t mark = ctx->pending.size();
+    for (int it = 0; it < chunk; ++it) {
+      CK(op.apply(vj, vj1, &w.st->stop, s, false));
+      CK(cgs_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.grid, s));
+      CK(cgs_update_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.grid, s));
+      CK(cgs_update_norm(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.H, w.cs, w.sn, w.gv, w.grid, s));
+      CK(normalize_next(vj, n, w.st, s));
+    }
+    if ((rc = read_state(ctx, w, s))) return rc;
+    const int done = ctx->h_state->iters - iters_before;
+    for (size_t k = mark; k < ctx->pending.size(); ++k) ctx->pending[k].valid = (int)(k - mark) < done;
+    resolve_timings(ctx, false);
+    iters_before = ctx->h_state->iters;
+    if (ctx->h_state->stop) return BIE_OK;
+    chunk = std::min(chunk * 2, 16);
+  }
+}
+
+int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, double tol_rel, int maxit,
+          bool verify, KrylovResult& out, cudaStream_t s) {
+  const long long n = w.n, ld = w.ld;
+  KState init;
+  memset(&init, 0, sizeof(init));
+  init.scratch[0] = tol_rel;
+  init.pad[0] = 1;  // k_residual sets tol_abs = tol_rel * ||b|| on the first call
+  init.maxit = maxit;
+  init.m = w.m;
+  *ctx->h_state = init;
+  CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
+  CK(fill0(x, n, s));
+  CK(residual_start(b, nullptr, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
+  const Op rop = verify ? Op{ctx, &w, 0} : op;
+  int rc;
+  for (;;) {
+    if ((rc = run_cycle(ctx, w, op, s))) return rc;
+    const KState h = *ctx->h_state;
+    out.bnorm = h.scratch[1];
+    out.iters = h.iters;
+    if (h.j > 0) CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, x, w.grid, s));
+    out.matvecs += h.j;
+    if (h.j == 0) {  // nothing to do: b is (numerically) zero or the cap is reached
+      out.res = h.rnorm;
+      out.converged = h.rnorm <= h.tol_abs;
+      return BIE_OK;
+    }
+    if (!verify && (h.res <= h.tol_abs || h.iters >= h.maxit)) {
+      out.res = h.res;
+      out.converged = h.res <= h.tol_abs;
+      return BIE_OK;
+    }
+    // explicit residual; opens the next cycle unless converged or capped
+    CK(rop.apply(vec(x), vec(w.ytmp), nullptr, s));
+    if (verify) out.matvecs64 += 1; else out.matvecs += 1;
+    CK(residual_start(b, w.ytmp, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
+    if ((rc = read_state(ctx, w, s))) return rc;
+    const KState& h2 = *ctx->h_state;
+    if (h2.rnorm <= h2.tol_abs || h2.iters >= h2.maxit) {
+      out.res = h2.rnorm;
+      out.converged = h2.rnorm <= h2.tol_abs;
+      return BIE_OK;
+    }
+  }
+}
+
+int copy_out(bie_ctx* ctx, double* dst, const double* src, size_t count, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, s));
+  return BIE_OK;
+}
+
+void fill_opts(const bie_opts* o, bie_opts& r) {
+  r.tol = 1e-12;
+  r.max_iter = 500;
+  r.restart = 50;
+  r.precision = BIE_PREC_FP64;
+  r.formulation = 0;
+  r.max_refine = 8;
+  r.inner_tol = 1e-6;
+  if (!o) return;
+  if (o->tol > 0) r.tol = o->tol;
+  if (o->max_iter > 0) r.max_iter = o->max_iter;
+  if (o->restart > 0) r.restart = std::min(o->restart, 200);
+  r.precision = o->precision;
+  r.formulation = o->formulation;
+  if (o->max_refine > 0) r.max_refine = o->max_refine;
+  if (o->inner_tol > 0) r.inner_tol = o->inner_tol;
+}
+
+int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double* load, double* out,
+                 double* density, const bie_opts* opts_in, bie_info* info, cudaStream_t s) {
+  std::vector<int> bs;
+  int rc = validate(ctx, geom, bs);
+  if (rc) return rc;
+  if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
+  bie_opts o;
+  fill_opts(opts_in, o);
+  if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED)
+    return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64 or BIE_PREC_MIXED");
+  if (o.formulation != 0 && o.formulation != 1) return fail(ctx, BIE_ERR_INVALID, "formulation must be 0 or 1");
+  DeviceGuard dg(ctx->device);
+  const int N = geom->n_bodies, M = bs[N];
+  const int nload = kind == 0 ? N : 3 * N;
+  Work w;
+  Arena sz{nullptr};
+  carve(sz, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
+  if ((rc = ensure_ws(ctx, sz.off))) return rc;
+  Arena ar{ctx->ws};
+  carve(ar, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
+  if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  const double* dload;
+  if ((rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
+  if ((rc = check_inside(ctx, w, s))) return rc;
+
+  const long long n = w.n;
+  // right-hand side (scaled by sqrt(w))
+  if (o.formulation == 0) {
+    CK(total_density_rhs(w.g, kind, dload, w.f, s));
+  } else {
+    CK(incident_density_scaled(w.g, kind, dload, w.rin, s));
+    CK(timed_pair_sum(ctx, w.g, kind, 0, w.plan64, vec(w.rin), w.g.sw, w.partial, nullptr, true, s));
+    CK(epilogue(w.g, kind, w.plan64, vec(w.rin), w.partial, 1, 0, -1.0, vec(w.f), nullptr, s));
+  }
+  const Op op64{ctx, &w, 0}, op32{ctx, &w, 1};
+  int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, iters = 0, refs = 0;
+  double relres = 0.0;
+  bool converged = false;
+  if (o.precision == BIE_PREC_FP64) {
+    KrylovResult kr;
+    if ((rc = gmres(ctx, w, op64, w.f, w.xs, o.tol, o.max_iter, true, kr, s))) return rc;
+    m64 += kr.matvecs + kr.matvecs64;
+    iters = kr.iters;
+    relres = kr.bnorm > 0 ? kr.res / kr.bnorm : 0.0;
+    converged = kr.converged;
+  } else {
+    // FP64 iterative refinement: x += A32^{-1}(f - A64 x)
+    CK(fill0(w.xs, n, s));
+    CK(cudaMemcpyAsync(w.r, w.f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // ||f||
+    {
+      KState init;
+      memset(&init, 0, sizeof(init));
+      *ctx->h_state = init;
+      CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
+      CK(residual_start(w.f, nullptr, w.ytmp, w.V, n, w.st, w.part, w.gv, 0, w.grid, s));
+      if ((rc = read_state(ctx, w, s))) return rc;
+    }
+    const double fnorm = ctx->h_state->rnorm;
+    double rnorm = fnorm;
+    int remaining = o.max_iter;
+    converged = fnorm == 0.0;
+    while (!converged && refs < o.max_refine && remaining > 0) {
+      KrylovResult kr;
+      if ((rc = gmres(ctx, w, op32, w.r, w.d, o.inner_tol, remaining, false, kr, s))) return rc;
+      iters += kr.iters;
+      m32 += kr.matvecs;
+      remaining -= kr.iters;
+      refs += 1;
+      CK(axpy(w.xs, w.d, n, s));
+      CK(op64.apply(vec(w.xs), vec(w.ytmp), nullptr, s));
+      m64 += 1;
+      {
+        KState init;
+        memset(&init, 0, sizeof(init));
+        *ctx->h_state = init;
+        CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
+        CK(residual_start(w.f, w.ytmp, w.r, w.V, n, w.st, w.part, w.gv, 0, w.grid, s));
+        if ((rc = read_state(ctx, w, s))) return rc;
+      }
+      rnorm = ctx->h_state->rnorm;
+      converged = rnorm <= o.tol * fnorm;
+      if (kr.iters == 0) break;
+    }
+    relres = fnorm > 0 ? rnorm / fnorm : 0.0;
+  }
+  // total density (scaled): nu = x (total form) or mu + sigma (paper form)
+  double* v = w.xs;
+  if (o.formulation == 1) {
+    CK(incident_density_scaled(w.g, kind, dload, w.rin, s));
+    CK(axpy(w.xs, w.rin, n, s));
+  }
+  CK(evaluate_output(w.g, kind, v, dload, w.outpart, w.P, w.outv, w.cres, s));
+  if (density) {
+    CK(unscale(w.g, kind, v, w.ytmp, s));
+    if ((rc = copy_out(ctx, density, w.ytmp, n, s))) return rc;
+  }
+  if ((rc = copy_out(ctx, out, w.outv, nload, s))) return rc;
+  // constraint residual and net load
+  const int targets = kind == 0 ? N : 3 * N;
+  const double* nl = w.outpart + (size_t)w.P * targets * (kind + 1) + N;
+  CK(cudaMemcpyAsync(ctx->h_small, w.cres, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ctx->h_small + 1, nl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double netload = ctx->h_small[1], maxload = ctx->h_small[2];
+  if (info) {
+    info->iters = iters;
+    info->refinements = refs;
+    info->matvecs_fp64 = m64;
+    info->matvecs_fp32 = m32;
+    info->rel_residual = relres;
+    info->constraint_residual = ctx->h_small[0];
+    info->net_load = netload;
+  }
+  if (!converged) return BIE_WARN_NOT_CONVERGED;
+  if (netload > 1e-12 * std::max(maxload, 1e-300) * std::max(1, N)) return BIE_WARN_NONNEUTRAL;
+  return BIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bie_create(bie_ctx** out, int device, size_t cap) {
+  if (!out) return BIE_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  bie_ctx* c = new bie_ctx();
+  c->device = device;
+  c->cap = cap;
+  DeviceGuard dg(device);
+  if (cudaMallocHost(&c->h_state, sizeof(KState)) != cudaSuccess ||
+      cudaMallocHost(&c->h_small, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->h_state) cudaFreeHost(c->h_state);
+    delete c;
+    return BIE_ERR_CUDA;
+  }
+  *out = c;
+  return BIE_OK;
+}
+
+int bie_profile(bie_ctx* ctx, int enable, bie_profile_counters* out) {
+  if (!ctx) return BIE_ERR_INVALID;
+  DeviceGuard dg(ctx->device);
+  resolve_timings(ctx, true);
+  ctx->counters.kernel_launches = ctx->prof ? launches_so_far() - ctx->launch_mark : 0;
+  if (out) *out = ctx->counters;
+  if (enable) {
+    memset(&ctx->counters, 0, sizeof(ctx->counters));
+    ctx->launch_mark = launches_so_far();
+  }
+  ctx->prof = enable != 0;
+  return BIE_OK;
+}
+
+void bie_destroy(bie_ctx* c) {
+  if (!c) return;
+  DeviceGuard dg(c->device);
+  resolve_timings(c, true);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->ws) cudaFree(c->ws);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  delete c;
+}
+
+const char* bie_last_error(const bie_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int elastance_solve(bie_ctx* ctx, const bie_geometry* geom, const double* q, double* phi, double* density,
+                    const bie_opts* opts, bie_info* info, void* stream) {
+  return solve_common(ctx, geom, 0, q, phi, density, opts, info, (cudaStream_t)stream);
+}
+
+int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, double* UW, double* density,
+                   const bie_opts* opts, bie_info* info, void* stream) {
+  return solve_common(ctx, geom, 1, FT, UW, density, opts, info, (cudaStream_t)stream);
+}
+
+int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, const double* in,
+                   double* out, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> bs;
+  int rc = validate(ctx, geom, bs);
+  if (rc) return rc;
+  if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
+  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED)
+    return fail(ctx, BIE_ERR_INVALID, "bad precision");
+  if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
+  DeviceGuard dg(ctx->device);
+  const int N = geom->n_bodies, M = bs[N];
+  Work w;
+  Arena sz{nullptr};
+  carve(sz, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = ensure_ws(ctx, sz.off))) return rc;
+  Arena ar{ctx->ws};
+  carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  const double* din;
+  if ((rc = stage_in(ctx, in, w.io_in, (size_t)w.n, &din, s))) return rc;
+  const PairPlan& p = precision == 0 ? w.plan64 : w.plan32;
+  const bool dev_out = is_device_ptr(out);
+  double* dout = dev_out ? out : w.io_out;
+  CK(timed_pair_sum(ctx, w.g, kind, precision, p, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr,
+                    true, s));
+  CK(epilogue(w.g, kind, p, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s));
+  if (!dev_out) {
+    CK(cudaMemcpyAsync(out, dout, (size_t)w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return BIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libbie2d.
+//
+// Data layout in device memory (one staged geometry per call):
+//   per node  [M]: x, y, nx, ny, w, sw = sqrt(w), kappa (float64),
+//                  pf = (x_hi, y_hi, x_lo, y_lo) float4 with x = x_hi + x_lo exactly
+//                  to ~2^-48 relative, nf = (nx, ny) float2, body_of (int32)
+//   per body  [N]: len = |Gamma_i|, xc, yc (arc-length centroid), W_i, interior
+//                  point z0 and stencil step delta
+//   densities: scaled by sqrt(w) (the L2 rescaling of Section 6.1.1); Stokes
+//              vectors node-interleaved (2a + c).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bie {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv2Pi = 0.15915494309189533577;  // 1/(2 pi)
+constexpr double kInvPi = 0.31830988618379067154;   // 1/pi
+constexpr double kInv4Pi = 0.07957747154594766788;  // 1/(4 pi)
+
+struct Geo {
+  int N = 0, M = 0;
+  const int* body_start = nullptr;  // [N+1]
+  int* body_of = nullptr;           // [M]
+  double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr;
+  double *w = nullptr, *sw = nullptr, *kappa = nullptr;
+  float4* pf = nullptr;
+  float2* nf = nullptr;
+  double *len = nullptr, *xc = nullptr, *yc = nullptr, *W = nullptr;
+  double *zx = nullptr, *zy = nullptr, *delta = nullptr, *wind = nullptr;
+};
+
+// A vector that lives at base + (idx ? *idx + off : off) * ld, so that a
+// kernel can address the current Krylov vector without a host round trip.
+struct VecRef {
+  double* base;
+  long long ld;
+  const int* idx;
+  int off;
+  __device__ __forceinline__ double* ptr() const {
+    return base + (long long)((idx ? *idx : 0) + off) * ld;
+  }
+};
+
+inline VecRef vec(double* p) { return VecRef{p, 0, nullptr, 0}; }
+
+// Device-side solver state (one per Krylov run).
+struct KState {
+  double tol_abs;  // stop threshold on the residual estimate
+  double beta;     // norm of the cycle's starting residual
+  double res;      // current residual estimate |g_{j+1}|
+  double hnext;    // ||w|| after orthogonalisation (H[j+1][j] before rotation)
+  double rnorm;    // last computed true residual norm
+  double scratch[4];  // [0] relative tolerance, [1] norm of the right-hand side
+  int j;           // iterations done in the current cycle
+  int stop;        // 1 when the cycle has ended (converged, full or breakdown)
+  int iters;       // iterations over all cycles
+  int maxit;       // iteration cap over all cycles
+  int m;           // restart length
+  int counter;     // last-block-done counter for grid reductions
+  int pad[2];         // [0] = 1: set tol_abs from the next starting residual
+};
+
+// Count of kernels launched by this library (all contexts), for bie_profile.
+void note_launches(int k);
+long long launches_so_far();
+
+// ---------------------------------------------------------------- geometry.cu
+// Stage the geometry: weights, normals, curvature, per-body length/centroid/W,
+// interior points, winding numbers, FP32 hi/lo coordinates.
+cudaError_t stage_geometry(const Geo& g, const double* x, const double* y, const double* dx,
+                           const double* dy, const double* ddx, const double* ddy,
+                           const double* interior_pt, cudaStream_t s);
+
+// f (scaled) for the total-density formulation: sw_a * q_i (Laplace) or
+// sw_a * (F_i + T_i p_a) (Stokes).
+cudaError_t total_density_rhs(const Geo& g, int kind, const double* load, double* f, cudaStream_t s);
+// Incident density scaled by sw: sw*sigma (Laplace) or sw*rho (Stokes).
+cudaError_t incident_density_scaled(const Geo& g, int kind, const double* load, double* out,
+                                    cudaStream_t s);
+
+// Output evaluation at interior points from v = sw * nu (scaled total density).
+// Laplace: out[i] = phi_i; Stokes: out[3i..3i+2] = (vx, vy, omega).  Also writes
+// the constraint residual max over bodies into *cres (device) relative to the load.
+cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const double* load,
+                            double* partial, int P, double* out, double* cres, cudaStream_t s);
+int output_splits(const Geo& g, int kind);
+
+// elementwise helpers
+cudaError_t unscale(const Geo& g, int kind, const double* v, double* out, cudaStream_t s);   // v/sw
+cudaError_t scale_by(const Geo& g, int kind, const double* in, const double* fac, double* out,
+                     cudaStream_t s);  // out = fac*in (fac per node)
+cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- pairsum.cu
+// partial[s][a] (scalar for Laplace, 2-vector for Stokes) = sum over sources b
+// of split s, b != a, of the kernel without its constant, with source strength
+// sscale_b * v_b.  FP64 and FP32 variants.
+struct PairPlan {
+  int S;      // source splits
+  int chunk;  // sources per split
+};
+PairPlan plan_pairs(int M, int kind, int precision);
+cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
+                     const double* sscale, double* partial, const int* stop, cudaStream_t s);
+
+// out = sign * [ 1/2 v + oscale * (K v + diag + [L] v) ] with the constants applied.
+// scaled = 1: v is sqrt(w)-scaled, source strength sw, output scaled by sw.
+// scaled = 0: v unscaled, source strength w, output unscaled.
+cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
+                     int scaled, int with_L, double sign, VecRef out, const int* stop,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- krylov.cu
+int vec_grid(long long n);
+// h[i] = <V_i, w> for i <= j (first CGS pass)
+cudaError_t cgs_dots(const double* V, long long ld, VecRef w, long long n, KState* st, double* part,
+                     double* h1, int grid, cudaStream_t s);
+// w -= V h1; h2 = V^T w (second CGS pass)
+cudaError_t cgs_update_dots(const double* V, long long ld, VecRef w, long long n, KState* st,
+                            double* part, const double* h1, double* h2, int grid, cudaStream_t s);
+// w -= V h2; ||w||; Givens; convergence
+cudaError_t cgs_update_norm(const double* V, long long ld, VecRef w, long long n, KState* st,
+                            double* part, const double* h1, const double* h2, double* H,
+                            double* cs, double* sn, double* gv, int grid, cudaStream_t s);
+cudaError_t normalize_next(VecRef w, long long n, KState* st, cudaStream_t s);
+// y = R^{-1} g and x += V y
+cudaError_t gmres_update(const double* V, long long ld, long long n, KState* st, const double* H,
+                         const double* gv, double* y, double* x, int grid, cudaStream_t s);
+// r = f - y, rnorm = ||r||; also optionally starts a cycle: V0 = r/rnorm, g = (rnorm, 0..)
+cudaError_t residual_start(const double* f, const double* y, double* r, double* V0, long long n,
+                           KState* st, double* part, double* gv, int start_cycle, int grid,
+                           cudaStream_t s);
+cudaError_t axpy(double* x, const double* d, long long n, cudaStream_t s);  // x += d
+cudaError_t fill0(double* x, long long n, cudaStream_t s);
+
+}  // namespace bie

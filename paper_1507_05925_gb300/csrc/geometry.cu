@@ -1,0 +1,335 @@
+// Geometry staging (quadrature data), incident densities, right-hand sides and
+// output evaluation at interior points.  All FP64: these are O(M) or O(N M)
+// passes off the per-iteration hot loop.
+#include <math.h>
+
+#include "bie_internal.cuh"
+#include "reduce.cuh"
+
+namespace bie {
+
+namespace {
+
+constexpr int kB = 256;
+
+// One block per body.  Trapezoidal rule on theta_k = 2 pi k / n_i:
+// w = |x'| 2pi/n_i, tau = x'/|x'|, n = (tau_y, -tau_x) (outward for CCW),
+// kappa = (x' y'' - y' x'')/|x'|^3; per body |Gamma_i| = sum w, the arc-length
+// centroid (Section 4, definition of x^c_i) and W_i = sum w |x - x^c|^2 (eq. rho).
+__global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ X,
+                                              const double* __restrict__ Y,
+                                              const double* __restrict__ DX,
+                                              const double* __restrict__ DY,
+                                              const double* __restrict__ DDX,
+                                              const double* __restrict__ DDY,
+                                              const double* __restrict__ ipt) {
+  __shared__ double sh[kB / 32];
+  const int i = blockIdx.x;
+  const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
+  const double hstep = 2.0 * kPi / (double)(a1 - a0);
+  double sl = 0.0, sx = 0.0, sy = 0.0;
+  for (int a = a0 + threadIdx.x; a < a1; a += kB) {
+    const double x = X[a], y = Y[a], dx = DX[a], dy = DY[a];
+    const double sp = sqrt(dx * dx + dy * dy);
+    const double w = sp * hstep;
+    const double tx = dx / sp, ty = dy / sp;
+    const double kap = (dx * DDY[a] - dy * DDX[a]) / (sp * sp * sp);
+    g.x[a] = x;
+    g.y[a] = y;
+    g.nx[a] = ty;
+    g.ny[a] = -tx;
+    g.w[a] = w;
+    g.sw[a] = sqrt(w);
+    g.kappa[a] = kap;
+    const float xh = (float)x, yh = (float)y;
+    g.pf[a] = make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
+    g.nf[a] = make_float2((float)ty, (float)(-tx));
+    g.body_of[a] = i;
+    sl += w;
+    sx += w * x;
+    sy += w * y;
+  }
+  sl = block_sum<kB>(sl, sh);
+  sx = block_sum<kB>(sx, sh);
+  sy = block_sum<kB>(sy, sh);
+  const double xc = sx / sl, yc = sy / sl;
+  const double zx = ipt ? ipt[2 * i] : xc;
+  const double zy = ipt ? ipt[2 * i + 1] : yc;
+  double sW = 0.0, dmin2 = 1e300, wind = 0.0;
+  for (int a = a0 + threadIdx.x; a < a1; a += kB) {
+    const double ux = X[a] - xc, uy = Y[a] - yc;
+    sW += g.w[a] * (ux * ux + uy * uy);
+    const double px = X[a] - zx, py = Y[a] - zy;
+    dmin2 = fmin(dmin2, px * px + py * py);
+    const int b = (a + 1 < a1) ? a + 1 : a0;
+    const double qx = X[b] - zx, qy = Y[b] - zy;
+    wind += atan2(px * qy - py * qx, px * qx + py * qy);
+  }
+  sW = block_sum<kB>(sW, sh);
+  wind = block_sum<kB>(wind, sh);
+  dmin2 = block_min<kB>(dmin2, sh);
+  if (threadIdx.x == 0) {
+    g.len[i] = sl;
+    g.xc[i] = xc;
+    g.yc[i] = yc;
+    g.W[i] = sW;
+    g.zx[i] = zx;
+    g.zy[i] = zy;
+    g.delta[i] = 0.25 * sqrt(dmin2);
+    g.wind[i] = wind / (2.0 * kPi);
+  }
+}
+
+// f = sw * (L sigma): q_i on Gamma_i (Laplace), F_i + T_i (x - x^c_i)^perp (Stokes).
+__global__ void k_total_rhs(Geo g, int kind, const double* __restrict__ load, double* __restrict__ f) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.M; a += gridDim.x * blockDim.x) {
+    const int i = g.body_of[a];
+    const double s = g.sw[a];
+    if (kind == 0) {
+      f[a] = s * load[i];
+    } else {
+      const double px = -(g.y[a] - g.yc[i]), py = g.x[a] - g.xc[i];
+      const double F1 = load[3 * i], F2 = load[3 * i + 1], T = load[3 * i + 2];
+      f[2 * a] = s * (F1 + T * px);
+      f[2 * a + 1] = s * (F2 + T * py);
+    }
+  }
+}
+
+// sw * sigma, sigma_a = q_i/|Gamma_i| (eq. sigma); sw * rho,
+// rho_a = F_i/|Gamma_i| + T_i (x_a - x^c_i)^perp / W_i (eq. rho).
+__global__ void k_incident(Geo g, int kind, const double* __restrict__ load, double* __restrict__ out) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.M; a += gridDim.x * blockDim.x) {
+    const int i = g.body_of[a];
+    const double s = g.sw[a];
+    if (kind == 0) {
+      out[a] = s * (load[i] / g.len[i]);
+    } else {
+      const double px = -(g.y[a] - g.yc[i]), py = g.x[a] - g.xc[i];
+      const double T = load[3 * i + 2];
+      out[2 * a] = s * (load[3 * i] / g.len[i] + T * px / g.W[i]);
+      out[2 * a + 1] = s * (load[3 * i + 1] / g.len[i] + T * py / g.W[i]);
+    }
+  }
+}
+
+__global__ void k_unscale(Geo g, int comps, const double* __restrict__ v, double* __restrict__ out) {
+  const long long n = (long long)g.M * comps;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = v[k] / g.sw[k / comps];
+}
+
+__global__ void k_scale_by(int M, int comps, const double* __restrict__ in, const double* __restrict__ fac,
+                           double* __restrict__ out) {
+  const long long n = (long long)M * comps;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = in[k] * fac[k / comps];
+}
+
+__global__ void k_net_load(int N, int kind, const double* __restrict__ load, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s0 = 0, s1 = 0, mx = 0;
+    for (int i = 0; i < N; ++i) {
+      if (kind == 0) {
+        s0 += load[i];
+        mx = fmax(mx, fabs(load[i]));
+      } else {
+        s0 += load[3 * i];
+        s1 += load[3 * i + 1];
+        mx = fmax(mx, fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
+      }
+    }
+    out[0] = sqrt(s0 * s0 + s1 * s1);
+    out[1] = mx;
+  }
+}
+
+// Laplace single layer at z_i: sum_b w_b nu_b log|z_i - x_b|^2 over split p.
+__global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict__ v,
+                                                double* __restrict__ part, int P) {
+  __shared__ double sh[kB / 32];
+  const int i = blockIdx.x, p = blockIdx.y;
+  const double zx = g.zx[i], zy = g.zy[i];
+  const int chunk = (g.M + P - 1) / P;
+  const int b0 = p * chunk, b1 = min(g.M, b0 + chunk);
+  double acc = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += kB) {
+    const double rx = zx - g.x[b], ry = zy - g.y[b];
+    acc += g.sw[b] * v[b] * log(rx * rx + ry * ry);
+  }
+  acc = block_sum<kB>(acc, sh);
+  if (threadIdx.x == 0) part[(long long)p * g.N + i] = acc;
+}
+
+// Stokes single layer (Stokeslet G_ij = (1/4pi)[-log r d_ij + r_i r_j / r^2]) at
+// the three stencil points of body i: t = 3i + s, s = 0: z0, 1: z0 + delta e1,
+// 2: z0 + delta e2.
+__global__ void __launch_bounds__(kB) k_out_stk(Geo g, const double* __restrict__ v,
+                                                double* __restrict__ part, int P) {
+  __shared__ double sh[kB / 32];
+  const int t = blockIdx.x, p = blockIdx.y;
+  const int i = t / 3, s = t % 3;
+  const double d = g.delta[i];
+  const double zx = g.zx[i] + (s == 1 ? d : 0.0), zy = g.zy[i] + (s == 2 ? d : 0.0);
+  const int chunk = (g.M + P - 1) / P;
+  const int b0 = p * chunk, b1 = min(g.M, b0 + chunk);
+  double u1 = 0.0, u2 = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += kB) {
+    const double rx = zx - g.x[b], ry = zy - g.y[b];
+    const double r2 = rx * rx + ry * ry;
+    const double f1 = g.sw[b] * v[2 * b], f2 = g.sw[b] * v[2 * b + 1];
+    const double lg = -0.5 * log(r2);
+    const double c = (rx * f1 + ry * f2) / r2;
+    u1 += lg * f1 + c * rx;
+    u2 += lg * f2 + c * ry;
+  }
+  u1 = block_sum<kB>(u1, sh);
+  u2 = block_sum<kB>(u2, sh);
+  if (threadIdx.x == 0) {
+    part[((long long)p * 3 * g.N + t) * 2] = u1;
+    part[((long long)p * 3 * g.N + t) * 2 + 1] = u2;
+  }
+}
+
+// One block per body: combine the splits, form the outputs, and measure the
+// constraint residuals int_{Gamma_i} mu = int nu - q_i (Laplace) or the force
+// and torque moments of mu = nu - rho (Stokes).
+__global__ void __launch_bounds__(kB) k_out_final(Geo g, int kind, const double* __restrict__ v,
+                                                  const double* __restrict__ load,
+                                                  const double* __restrict__ part, int P,
+                                                  double* __restrict__ out, double* __restrict__ cbody) {
+  __shared__ double sh[kB / 32];
+  const int i = blockIdx.x;
+  const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for (int a = a0 + threadIdx.x; a < a1; a += kB) {
+    if (kind == 0) {
+      m0 += g.sw[a] * v[a];
+    } else {
+      const double f1 = g.sw[a] * v[2 * a], f2 = g.sw[a] * v[2 * a + 1];
+      const double px = -(g.y[a] - g.yc[i]), py = g.x[a] - g.xc[i];
+      m0 += f1;
+      m1 += f2;
+      m2 += px * f1 + py * f2;
+    }
+  }
+  m0 = block_sum<kB>(m0, sh);
+  if (kind == 1) {
+    m1 = block_sum<kB>(m1, sh);
+    m2 = block_sum<kB>(m2, sh);
+  }
+  if (threadIdx.x == 0) {
+    if (kind == 0) {
+      double acc = 0.0;
+      for (int p = 0; p < P; ++p) acc += part[(long long)p * g.N + i];
+      out[i] = -0.5 * kInv2Pi * acc;
+      cbody[i] = fabs(m0 - load[i]);
+    } else {
+      double u[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+      for (int p = 0; p < P; ++p)
+        for (int s = 0; s < 3; ++s) {
+          u[s][0] += part[((long long)p * 3 * g.N + 3 * i + s) * 2];
+          u[s][1] += part[((long long)p * 3 * g.N + 3 * i + s) * 2 + 1];
+        }
+      for (int s = 0; s < 3; ++s) {
+        u[s][0] *= kInv4Pi;
+        u[s][1] *= kInv4Pi;
+      }
+      const double d = g.delta[i];
+      out[3 * i] = u[0][0];
+      out[3 * i + 1] = u[0][1];
+      out[3 * i + 2] = ((u[1][1] - u[0][1]) - (u[2][0] - u[0][0])) / (2.0 * d);
+      cbody[i] = fmax(fabs(m0 - load[3 * i]), fmax(fabs(m1 - load[3 * i + 1]), fabs(m2 - load[3 * i + 2])));
+    }
+  }
+}
+
+__global__ void k_max_reduce(const double* __restrict__ c, int N, const double* __restrict__ netload,
+                             double* __restrict__ out) {
+  __shared__ double sh[kB / 32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += kB) m = fmax(m, c[i]);
+  m = -block_min<kB>(-m, sh);
+  if (threadIdx.x == 0) out[0] = m / fmax(netload[1], 1e-300);
+}
+
+inline int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+cudaError_t stage_geometry(const Geo& g, const double* x, const double* y, const double* dx,
+                           const double* dy, const double* ddx, const double* ddy,
+                           const double* interior_pt, cudaStream_t s) {
+  k_stage<<<g.N, kB, 0, s>>>(g, x, y, dx, dy, ddx, ddy, interior_pt);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t total_density_rhs(const Geo& g, int kind, const double* load, double* f, cudaStream_t s) {
+  k_total_rhs<<<grid_for(g.M), 256, 0, s>>>(g, kind, load, f);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t incident_density_scaled(const Geo& g, int kind, const double* load, double* out,
+                                    cudaStream_t s) {
+  k_incident<<<grid_for(g.M), 256, 0, s>>>(g, kind, load, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+int output_splits(const Geo& g, int kind) {
+  const int targets = kind == 0 ? g.N : 3 * g.N;
+  int P = (4 * 152 + targets - 1) / targets;
+  const int maxP = (g.M + 255) / 256;
+  if (P > maxP) P = maxP;
+  if (P < 1) P = 1;
+  return P;
+}
+
+cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const double* load,
+                            double* partial, int P, double* out, double* cres, cudaStream_t s) {
+  // partial: [P][targets][comps] followed by N per-body constraint residuals and
+  // two net-load scalars
+  const int targets = kind == 0 ? g.N : 3 * g.N;
+  double* cbody = partial + (long long)P * targets * (kind == 0 ? 1 : 2);
+  double* nl = cbody + g.N;
+  if (kind == 0)
+    k_out_lap<<<dim3(g.N, P), kB, 0, s>>>(g, v, partial, P);
+  else
+    k_out_stk<<<dim3(3 * g.N, P), kB, 0, s>>>(g, v, partial, P);
+  note_launches(1);
+  k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
+  note_launches(1);
+  k_net_load<<<1, 32, 0, s>>>(g.N, kind, load, nl);
+  note_launches(1);
+  k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t unscale(const Geo& g, int kind, const double* v, double* out, cudaStream_t s) {
+  k_unscale<<<grid_for((long long)g.M * (kind + 1)), 256, 0, s>>>(g, kind + 1, v, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_by(const Geo& g, int kind, const double* in, const double* fac, double* out,
+                     cudaStream_t s) {
+  k_scale_by<<<grid_for((long long)g.M * (kind + 1)), 256, 0, s>>>(g.M, kind + 1, in, fac, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s) {
+  k_net_load<<<1, 32, 0, s>>>(N, kind, load, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace bie

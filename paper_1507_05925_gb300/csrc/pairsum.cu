@@ -1,0 +1,348 @@
+// Nystrom pair sums of the paper's second-kind operators and their epilogue.
+//
+// Laplace (Section 3.4, operator K with the TARGET normal):
+//   (K mu)_a = -(1/2pi) sum_{b != a} w_b mu_b (r . n_a) / |r|^2,   r = x_a - x_b
+// Stokes (Section 4.3, operator K built from the stresslet T_ijk = -(1/pi) r_i r_j r_k/|r|^4):
+//   (K mu)_a = -(1/pi) sum_{b != a} w_b r (r . mu_b)(r . n_a) / |r|^4
+//
+// Layout of the work: a block owns B*T targets (T per thread, strided by B so
+// loads coalesce) and one contiguous split of the sources; sources stream
+// through shared memory in tiles.  The splits write partial sums
+// partial[s][a] that the epilogue adds in a fixed order (deterministic), in
+// FP64, together with the diagonal limit, 1/2 I and the completion L.
+//
+// FP32 variant: positions are held as hi/lo float pairs so that
+// dx = (xa_hi - xb_hi) + (xa_lo - xb_lo) is exact to FP32 rounding of dx itself
+// even for neighbouring nodes far from the origin (the near-pair cancellation in
+// r . n_a would otherwise lose digits); the reciprocal is the hardware
+// rcp.approx.f32; each tile's FP32 sums are promoted into FP64 accumulators.
+#include <algorithm>
+
+#include "bie_internal.cuh"
+#include "reduce.cuh"
+
+namespace bie {
+
+namespace {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ------------------------------------------------------------------ FP64 ----
+constexpr int kB64 = 128, kT64 = 2, kTile64 = 128;
+
+template <int KIND>
+__global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double* __restrict__ sscale,
+                                                 int chunk, double* __restrict__ partial,
+                                                 const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ double sx[kTile64], sy[kTile64], sq1[kTile64], sq2[kTile64];
+  const double* __restrict__ v = vr.ptr();
+  const int M = g.M;
+  const int tbase = blockIdx.x * kB64 * kT64;
+  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  double tx[kT64], ty[kT64], tnx[kT64], tny[kT64], ax[kT64], ay[kT64];
+  int ta[kT64];
+#pragma unroll
+  for (int k = 0; k < kT64; ++k) {
+    const int a = tbase + threadIdx.x + k * kB64;
+    ta[k] = a;
+    const bool in = a < M;
+    tx[k] = in ? g.x[a] : 0.0;
+    ty[k] = in ? g.y[a] : 0.0;
+    tnx[k] = in ? g.nx[a] : 0.0;
+    tny[k] = in ? g.ny[a] : 0.0;
+    ax[k] = 0.0;
+    ay[k] = 0.0;
+  }
+  for (int jt = j0; jt < j1; jt += kTile64) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < kTile64; l += kB64) {
+      const int b = jt + l;
+      if (b < j1) {
+        sx[l] = g.x[b];
+        sy[l] = g.y[b];
+        if (KIND == 0) {
+          sq1[l] = sscale[b] * v[b];
+        } else {
+          sq1[l] = sscale[b] * v[2 * b];
+          sq2[l] = sscale[b] * v[2 * b + 1];
+        }
+      }
+    }
+    __syncthreads();
+    const int nt = min(kTile64, j1 - jt);
+    for (int l = 0; l < nt; ++l) {
+      const double px = sx[l], py = sy[l], q1 = sq1[l];
+      const double q2 = KIND == 0 ? 0.0 : sq2[l];
+      const int b = jt + l;
+#pragma unroll
+      for (int k = 0; k < kT64; ++k) {
+        const double dx = tx[k] - px, dy = ty[k] - py;
+        const double r2 = dx * dx + dy * dy;
+        if (KIND == 0) {
+          const double s = (ta[k] == b) ? 0.0 : q1 / r2;
+          ax[k] += dx * s;
+          ay[k] += dy * s;
+        } else {
+          const double rq = dx * q1 + dy * q2;
+          const double rn = dx * tnx[k] + dy * tny[k];
+          const double c = (ta[k] == b) ? 0.0 : (rq * rn) / (r2 * r2);
+          ax[k] += c * dx;
+          ay[k] += c * dy;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kT64; ++k) {
+    const int a = ta[k];
+    if (a < M) {
+      if (KIND == 0)
+        partial[(long long)blockIdx.y * M + a] = tnx[k] * ax[k] + tny[k] * ay[k];
+      else {
+        partial[((long long)blockIdx.y * M + a) * 2] = ax[k];
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = ay[k];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP32 ----
+constexpr int kB32 = 128, kT32 = 4, kTile32 = 256;
+
+template <int KIND, bool DIAG>
+__device__ __forceinline__ void tile32(const float4* __restrict__ sp, const float2* __restrict__ sq,
+                                       int nt, int jt, const int* ta, const float* txh, const float* tyh,
+                                       const float* txl, const float* tyl, const float* tnx,
+                                       const float* tny, float* ax, float* ay) {
+#pragma unroll 2
+  for (int l = 0; l < nt; ++l) {
+    const float4 p = sp[l];
+    const float2 q = sq[l];
+#pragma unroll
+    for (int k = 0; k < kT32; ++k) {
+      const float dx = (txh[k] - p.x) + (txl[k] - p.z);
+      const float dy = (tyh[k] - p.y) + (tyl[k] - p.w);
+      const float r2 = fmaf(dx, dx, dy * dy);
+      const float inv = rcp_approx(r2);
+      if (KIND == 0) {
+        float s = q.x * inv;
+        if (DIAG) s = (ta[k] == jt + l) ? 0.0f : s;
+        ax[k] = fmaf(dx, s, ax[k]);
+        ay[k] = fmaf(dy, s, ay[k]);
+      } else {
+        const float rq = fmaf(dx, q.x, dy * q.y);
+        const float rn = fmaf(dx, tnx[k], dy * tny[k]);
+        float c = (rq * rn) * (inv * inv);
+        if (DIAG) c = (ta[k] == jt + l) ? 0.0f : c;
+        ax[k] = fmaf(c, dx, ax[k]);
+        ay[k] = fmaf(c, dy, ay[k]);
+      }
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kB32) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
+                                                 int chunk, double* __restrict__ partial,
+                                                 const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ float4 sp[kTile32];
+  __shared__ float2 sq[kTile32];
+  const double* __restrict__ v = vr.ptr();
+  const int M = g.M;
+  const int tbase = blockIdx.x * kB32 * kT32;
+  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  float txh[kT32], tyh[kT32], txl[kT32], tyl[kT32], tnx[kT32], tny[kT32];
+  double dax[kT32], day[kT32];
+  int ta[kT32];
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) {
+    const int a = tbase + threadIdx.x + k * kB32;
+    ta[k] = a;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 n = make_float2(0.f, 0.f);
+    if (a < M) {
+      p = g.pf[a];
+      n = g.nf[a];
+    }
+    txh[k] = p.x;
+    tyh[k] = p.y;
+    txl[k] = p.z;
+    tyl[k] = p.w;
+    tnx[k] = n.x;
+    tny[k] = n.y;
+    dax[k] = 0.0;
+    day[k] = 0.0;
+  }
+  for (int jt = j0; jt < j1; jt += kTile32) {
+    __syncthreads();
+    for (int l = threadIdx.x; l < kTile32; l += kB32) {
+      const int b = jt + l;
+      if (b < j1) {
+        sp[l] = g.pf[b];
+        if (KIND == 0)
+          sq[l] = make_float2((float)(sscale[b] * v[b]), 0.f);
+        else
+          sq[l] = make_float2((float)(sscale[b] * v[2 * b]), (float)(sscale[b] * v[2 * b + 1]));
+      } else {
+        // far away, zero strength: contributes exactly 0
+        sp[l] = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);
+        sq[l] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    float ax[kT32], ay[kT32];
+#pragma unroll
+    for (int k = 0; k < kT32; ++k) ax[k] = ay[k] = 0.f;
+    const bool diag = (jt < tbase + kB32 * kT32) && (jt + kTile32 > tbase);
+    if (diag)
+      tile32<KIND, true>(sp, sq, kTile32, jt, ta, txh, tyh, txl, tyl, tnx, tny, ax, ay);
+    else
+      tile32<KIND, false>(sp, sq, kTile32, jt, ta, txh, tyh, txl, tyl, tnx, tny, ax, ay);
+#pragma unroll
+    for (int k = 0; k < kT32; ++k) {
+      dax[k] += (double)ax[k];
+      day[k] += (double)ay[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) {
+    const int a = ta[k];
+    if (a < M) {
+      if (KIND == 0)
+        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax[k] + g.ny[a] * day[k];
+      else {
+        partial[((long long)blockIdx.y * M + a) * 2] = dax[k];
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day[k];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- epilogue ----
+constexpr int kBE = 256;
+
+// One block per body: completion moments, then per node
+//   y = Kv (constant applied) + diagonal limit + [L]; out = sign (1/2 v + oscale y).
+template <int KIND>
+__global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double* __restrict__ partial,
+                                                  int S, int scaled, int with_L, double sign,
+                                                  VecRef outr, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ double sh[kBE / 32];
+  const double* __restrict__ v = vr.ptr();
+  double* __restrict__ out = outr.ptr();
+  const int M = g.M;
+  const int i = blockIdx.x;
+  const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
+  const double xc = g.xc[i], yc = g.yc[i];
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  if (with_L) {
+    for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+      const double s = scaled ? g.sw[a] : g.w[a];
+      if (KIND == 0) {
+        m0 += s * v[a];
+      } else {
+        const double f1 = s * v[2 * a], f2 = s * v[2 * a + 1];
+        m0 += f1;
+        m1 += f2;
+        m2 += -(g.y[a] - yc) * f1 + (g.x[a] - xc) * f2;
+      }
+    }
+    m0 = block_sum<kBE>(m0, sh);
+    if (KIND == 1) {
+      m1 = block_sum<kBE>(m1, sh);
+      m2 = block_sum<kBE>(m2, sh);
+    }
+  }
+  for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+    const double os = scaled ? g.sw[a] : 1.0;
+    const double wk = g.w[a] * g.kappa[a];
+    if (KIND == 0) {
+      double k = 0.0;
+      for (int s = 0; s < S; ++s) k += partial[(long long)s * M + a];
+      const double mu = v[a] / os;
+      const double y = -kInv2Pi * k - kInv4Pi * wk * mu + m0;
+      out[a] = sign * (0.5 * v[a] + os * y);
+    } else {
+      double k1 = 0.0, k2 = 0.0;
+      for (int s = 0; s < S; ++s) {
+        k1 += partial[((long long)s * M + a) * 2];
+        k2 += partial[((long long)s * M + a) * 2 + 1];
+      }
+      const double mu1 = v[2 * a] / os, mu2 = v[2 * a + 1] / os;
+      const double tx = -g.ny[a], ty = g.nx[a];
+      const double dd = -0.5 * kInvPi * wk * (tx * mu1 + ty * mu2);
+      const double px = -(g.y[a] - yc), py = g.x[a] - xc;
+      const double y1 = -kInvPi * k1 + dd * tx + m0 + px * m2;
+      const double y2 = -kInvPi * k2 + dd * ty + m1 + py * m2;
+      out[2 * a] = sign * (0.5 * v[2 * a] + os * y1);
+      out[2 * a + 1] = sign * (0.5 * v[2 * a + 1] + os * y2);
+    }
+  }
+}
+
+}  // namespace
+
+// Choose the source split: the busiest SM's load, ceil(blocks/152) * (chunk + overhead),
+// is minimised over chunks that are multiples of the tile.
+PairPlan plan_pairs(int M, int kind, int precision) {
+  const int per_block = precision == 0 ? kB64 * kT64 : kB32 * kT32;
+  const int tile = precision == 0 ? kTile64 : kTile32;
+  const long long bx = (M + per_block - 1) / per_block;
+  const int nsm = 152;
+  const long long overhead = tile / 2;
+  PairPlan best{1, M};
+  long long best_cost = -1;
+  const int max_c = std::max(1, (M + tile - 1) / tile);
+  for (int c = 1; c <= max_c; ++c) {
+    const long long chunk = (long long)c * tile;
+    const long long S = (M + chunk - 1) / chunk;
+    const long long blocks = bx * S;
+    const long long cost = ((blocks + nsm - 1) / nsm) * (chunk + overhead);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best.S = (int)S;
+      best.chunk = (int)chunk;
+    }
+  }
+  (void)kind;
+  return best;
+}
+
+cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
+                     const double* sscale, double* partial, const int* stop, cudaStream_t s) {
+  if (precision == 0) {
+    dim3 grid((g.M + kB64 * kT64 - 1) / (kB64 * kT64), p.S);
+    if (kind == 0)
+      k_pair64<0><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+    else
+      k_pair64<1><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+  } else {
+    dim3 grid((g.M + kB32 * kT32 - 1) / (kB32 * kT32), p.S);
+    if (kind == 0)
+      k_pair32<0><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+    else
+      k_pair32<1><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
+                     int scaled, int with_L, double sign, VecRef out, const int* stop,
+                     cudaStream_t s) {
+  if (kind == 0)
+    k_epilogue<0><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, sign, out, stop);
+  else
+    k_epilogue<1><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, sign, out, stop);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace bie

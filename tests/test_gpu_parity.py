@@ -1,0 +1,337 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written here, derived in the design notes):
+  FP64 operator           max |gpu - oracle| <= 1e-13 max |oracle|  (rounding order only)
+  FP32-pair-sum operator  max |gpu - oracle| <= TOL32 max |oracle|
+  solves, FP64 and mixed  ||phi - phi_oracle|| / ||phi_oracle|| <= 1e-10 (same for (v, omega))
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import geometry, laplace, stokes  # noqa: E402
+from paper_1507_05925_gb300 import bie  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-13
+TOL32 = {0: 2e-6, 1: 5e-6}
+TOL_SOLVE = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05925_gb300 import build
+    build.build()
+    c = bie.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(g, device="cuda"):
+    out = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(device)
+           for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    out["body_start"] = torch.from_numpy(np.ascontiguousarray(g["body_start"])).to(device)
+    if "interior_pt" in g:
+        out["interior_pt"] = torch.from_numpy(np.ascontiguousarray(g["interior_pt"])).to(device)
+    return out
+
+
+def ragged4():
+    return synth.assemble([synth.star(0, 0, 1.0, 0.25, 5, 0.3, 200), synth.ellipse(3.1, 0.2, 1.0, 0.45, 1.0, 137),
+                           synth.disc(0.4, 3.0, 0.7, 91), synth.star(3.3, 3.2, 0.9, 0.2, 3, 1.3, 300)])
+
+
+def multitile(seed=7, rows=4, cols=4):
+    rng = np.random.default_rng(seed)
+    curves = []
+    for i in range(rows):
+        for j in range(cols):
+            n = int(rng.integers(64, 301))
+            if (i + j) % 2:
+                curves.append(synth.ellipse(3.2 * i, 3.2 * j, 1.0, rng.uniform(0.4, 1.0), rng.uniform(0, 3), n))
+            else:
+                curves.append(synth.star(3.2 * i, 3.2 * j, rng.uniform(0.6, 1.0), rng.uniform(0, 0.3),
+                                         int(rng.integers(3, 7)), rng.uniform(0, 6), n))
+    return synth.assemble(curves)
+
+
+GEOMS = {"four_discs": lambda: synth.four_discs(seed=0), "ragged4": ragged4, "multitile": multitile}
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------
+# operator parity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(GEOMS))
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+def test_apply_operator(ctx, name, kind, prec):
+    g = GEOMS[name]()
+    if kind == bie.STOKES and name == "multitile":
+        g = multitile(rows=3, cols=3)
+    geo = geometry.nodes(g)
+    n = geo["M"] * (kind + 1)
+    v = np.random.default_rng(3).standard_normal(n)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    rc = bie.apply_operator(ctx, to_dev(g), kind, prec, torch.from_numpy(v).cuda(), out)
+    torch.cuda.synchronize()
+    assert rc == bie.OK, ctx.last_error()
+    ref = (laplace if kind == 0 else stokes).apply(geo, v)
+    err = rel_max(out.cpu().numpy(), ref)
+    tol = TOL64 if prec == bie.FP64 else TOL32[kind]
+    print(f"apply {name} kind={kind} prec={prec}: rel max err {err:.2e}")
+    assert err <= tol
+
+
+# ---------------------------------------------------------------------------
+# solve parity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(GEOMS))
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("form", [0, 1])
+def test_elastance_solve(ctx, name, prec, form):
+    g = GEOMS[name]()
+    N = g["body_start"].size - 1
+    q = synth.charges(N, np.random.default_rng(11))
+    ref = laplace.solve(g, q)
+    phi = torch.empty(N, dtype=torch.float64, device="cuda")
+    dens = torch.empty(g["x"].size, dtype=torch.float64, device="cuda")
+    rc, info = bie.elastance_solve(ctx, to_dev(g), torch.from_numpy(q).cuda(), phi, dens,
+                                   opts=bie.make_opts(precision=prec, formulation=form))
+    torch.cuda.synchronize()
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    e_phi = rel2(phi.cpu().numpy(), ref["phi"])
+    w = ref["geo"]["w"]
+    e_den = rel2(np.sqrt(w) * dens.cpu().numpy(), np.sqrt(w) * ref["nu"])
+    print(f"elastance {name} prec={prec} form={form}: phi {e_phi:.2e} density {e_den:.2e} {info}")
+    assert e_phi <= TOL_SOLVE
+    assert e_den <= 1e-9
+    assert info["rel_residual"] <= 1e-12
+    assert info["constraint_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["ragged4", "multitile"])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("form", [0, 1])
+def test_mobility_solve(ctx, name, prec, form):
+    g = GEOMS[name]() if name == "ragged4" else multitile(rows=3, cols=3)
+    N = g["body_start"].size - 1
+    FT = synth.forces_torques(N, np.random.default_rng(12))
+    ref = stokes.solve(g, FT)
+    UW = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    dens = torch.empty(2 * g["x"].size, dtype=torch.float64, device="cuda")
+    rc, info = bie.mobility_solve(ctx, to_dev(g), torch.from_numpy(FT.reshape(-1)).cuda(), UW, dens,
+                                  opts=bie.make_opts(precision=prec, formulation=form))
+    torch.cuda.synchronize()
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    e = rel2(UW.cpu().numpy(), ref["UW"].reshape(-1))
+    w2 = np.repeat(ref["geo"]["w"], 2)
+    e_den = rel2(np.sqrt(w2) * dens.cpu().numpy(), np.sqrt(w2) * ref["nu"])
+    print(f"mobility {name} prec={prec} form={form}: UW {e:.2e} density {e_den:.2e} {info}")
+    assert e <= TOL_SOLVE
+    assert e_den <= 1e-9
+    assert info["rel_residual"] <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# closed forms evaluated by the GPU path
+# ---------------------------------------------------------------------------
+def test_gpu_closed_forms(ctx):
+    # single disc: phi = -(q/2pi) log R; single ellipse: -(q/2pi) log((a+b)/2)
+    for curve, cap in ((synth.disc(0.3, -0.2, 1.7, 64), 1.7), (synth.ellipse(0.1, 0.2, 1.3, 0.4, 2.0, 256), 0.85)):
+        g = synth.assemble([curve])
+        phi = torch.empty(1, dtype=torch.float64, device="cuda")
+        rc, _ = bie.elastance_solve(ctx, to_dev(g), torch.tensor([1.3], dtype=torch.float64, device="cuda"), phi)
+        assert rc == bie.WARN_NONNEUTRAL  # a single charged conductor is not neutral
+        assert abs(phi.item() + 1.3 / (2 * math.pi) * math.log(cap)) < 1e-13
+    # two discs, gap 0.5: phi_1 - phi_2 = (Q/pi) log((alpha + d/2)/(alpha - d/2))
+    d, Q = 0.5, 0.8
+    g = synth.two_discs(d, 256)
+    phi = torch.empty(2, dtype=torch.float64, device="cuda")
+    rc, _ = bie.elastance_solve(ctx, to_dev(g), torch.tensor([Q, -Q], dtype=torch.float64, device="cuda"), phi,
+                                opts=bie.make_opts(precision=bie.MIXED))
+    al = math.sqrt(d + d * d / 4)
+    p = phi.cpu().numpy()
+    assert rc == bie.OK
+    assert abs(p[0] - p[1] - Q / math.pi * math.log((al + d / 2) / (al - d / 2))) < 1e-12
+    # rotating ellipse: omega = T / (2 pi (a^2 + b^2)); single disc translation
+    g = synth.assemble([synth.ellipse(0.2, -0.1, 1.2, 0.3, 0.7, 256)])
+    UW = torch.empty(3, dtype=torch.float64, device="cuda")
+    rc, _ = bie.mobility_solve(ctx, to_dev(g), torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64, device="cuda"), UW)
+    assert rc == bie.OK
+    assert abs(UW[2].item() - 1.0 / (2 * math.pi * (1.44 + 0.09))) < 1e-13
+    g = synth.assemble([synth.disc(0.3, -0.2, 1.7, 64)])
+    rc, _ = bie.mobility_solve(ctx, to_dev(g), torch.tensor([0.7, -0.4, 1.1], dtype=torch.float64, device="cuda"), UW)
+    assert rc == bie.WARN_NONNEUTRAL
+    u = UW.cpu().numpy()
+    assert np.max(np.abs(u[:2] - np.array([0.7, -0.4]) * (0.5 - math.log(1.7)) / (4 * math.pi))) < 1e-14
+    assert abs(u[2] - 1.1 / (4 * math.pi * 1.7**2)) < 1e-14
+
+
+def test_two_disc_mobility_table_gpu(ctx):
+    from conftest import read_golden
+    kv, rows = read_golden("two_disc_mobility.txt")
+    d, F11, F21, T1, T2 = rows[0][:5]
+    FT = np.array([F11, F21, T1, -F11, -F21, T2])
+    UW = torch.empty(6, dtype=torch.float64, device="cuda")
+    rc, info = bie.mobility_solve(ctx, to_dev(synth.two_discs(d, 256)), torch.from_numpy(FT).cuda(), UW,
+                                  opts=bie.make_opts(precision=bie.MIXED))
+    assert rc == bie.OK
+    u = UW.cpu().numpy().reshape(2, 3)
+    assert np.max(np.abs((u[0, :2] - u[1, :2]) - np.array([2.09 - 1.00, -1.034 - 0.254]))) < 1e-5
+    assert np.max(np.abs(u[:, 2] - np.array(kv["omega"]))) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# host pointers, determinism, edge cases
+# ---------------------------------------------------------------------------
+def test_host_and_device_pointers_agree_bitwise(ctx):
+    g = ragged4()
+    q = synth.charges(4, np.random.default_rng(5))
+    phi_d = torch.empty(4, dtype=torch.float64, device="cuda")
+    rc1, _ = bie.elastance_solve(ctx, to_dev(g), torch.from_numpy(q).cuda(), phi_d,
+                                 opts=bie.make_opts(precision=bie.MIXED))
+    phi_h = np.empty(4)
+    host = {k: np.ascontiguousarray(g[k]) for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+    rc2, _ = bie.elastance_solve(ctx, host, q, phi_h, opts=bie.make_opts(precision=bie.MIXED))
+    torch.cuda.synchronize()
+    assert rc1 == rc2 == bie.OK
+    assert np.array_equal(phi_d.cpu().numpy(), phi_h)
+    # repeat: identical bits (fixed-order reductions)
+    phi_h2 = np.empty(4)
+    bie.elastance_solve(ctx, host, q, phi_h2, opts=bie.make_opts(precision=bie.MIXED))
+    assert np.array_equal(phi_h, phi_h2)
+
+
+def test_minimum_size_and_interior_point(ctx):
+    # 8 nodes (the minimum), user interior point off-centre
+    g = synth.assemble([synth.disc(0.0, 0.0, 1.0, 8), synth.disc(3.0, 0.0, 1.0, 8)])
+    g["interior_pt"] = np.array([0.2, 0.1, 3.1, -0.2])
+    q = np.array([1.0, -1.0])
+    phi = np.empty(2)
+    rc, _ = bie.elastance_solve(ctx, g, q, phi)
+    assert rc == bie.OK
+    ref = laplace.solve(g, q)
+    geo = ref["geo"]
+    # the oracle's field at the same interior points
+    u = laplace.single_layer_at(geo, ref["nu"], np.array([0.2, 3.1]), np.array([0.1, -0.2]))
+    assert rel2(phi, u) < 1e-12
+
+
+def test_invalid_arguments(ctx):
+    g = ragged4()
+    host = {k: np.ascontiguousarray(g[k]) for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+    q = np.zeros(4)
+    phi = np.empty(4)
+    bad = dict(host, body_start=np.array([0, 200, 337, 340, 728], dtype=np.int32))  # body of 3 nodes
+    assert bie.elastance_solve(ctx, bad, q, phi)[0] == bie.ERR_INVALID
+    bad = dict(host, body_start=np.array([1, 200, 337, 428, 728], dtype=np.int32))
+    assert bie.elastance_solve(ctx, bad, q, phi)[0] == bie.ERR_INVALID
+    outside = dict(host, interior_pt=np.array([10.0, 10.0, 3.1, 0.2, 0.4, 3.0, 3.3, 3.2]))
+    assert bie.elastance_solve(ctx, outside, q, phi)[0] == bie.ERR_OUTSIDE
+    cw = {k: np.ascontiguousarray(v[::-1]) if k != "body_start" else v for k, v in
+          synth.assemble([synth.disc(0, 0, 1, 32)]).items()}
+    cw["dx"], cw["dy"] = -cw["dx"], -cw["dy"]
+    assert bie.elastance_solve(ctx, cw, np.ones(1), np.empty(1))[0] == bie.ERR_OUTSIDE
+    small = bie.Context(0, workspace_cap_bytes=1024)
+    assert bie.elastance_solve(small, host, q, phi)[0] == bie.ERR_NOMEM
+    small.close()
+    rc, info = bie.elastance_solve(ctx, host, synth.charges(4, np.random.default_rng(1)), phi,
+                                   opts=bie.make_opts(max_iter=2))
+    assert rc == bie.WARN_NOT_CONVERGED and info["iters"] <= 2
+
+
+def test_nonneutral_still_matches_oracle(ctx):
+    g = ragged4()
+    q = np.array([1.0, 0.5, -0.2, 0.3])
+    phi = np.empty(4)
+    rc, info = bie.elastance_solve(ctx, g, q, phi)
+    assert rc == bie.WARN_NONNEUTRAL and abs(info["net_load"] - 1.6) < 1e-12
+    assert rel2(phi, laplace.solve(g, q)["phi"]) <= TOL_SOLVE
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled rows and size-independent properties
+# ---------------------------------------------------------------------------
+def _sampled_rows(geo, kind, v, rows):
+    mod = laplace if kind == 0 else stokes
+    A = mod.kernel_rows(geo, rows) + mod.completion_rows(geo, rows)
+    if kind == 0:
+        return 0.5 * v[rows] + A @ v
+    idx = np.stack([2 * rows, 2 * rows + 1], 1).reshape(-1)
+    return 0.5 * v[idx] + A @ v
+
+
+@pytest.mark.parametrize("wl,kind", [("stars100_M25600", 0), ("ellipses400_M51200", 1)])
+def test_full_size_operator_rows(ctx, wl, kind):
+    g = synth.WORKLOADS[wl]()
+    geo = geometry.nodes(g)
+    n = geo["M"] * (kind + 1)
+    v = np.random.default_rng(4).standard_normal(n)
+    rows = np.sort(np.random.default_rng(5).choice(geo["M"], 48, replace=False))
+    rows = np.unique(np.concatenate([rows, [0, geo["M"] - 1]]))
+    ref = _sampled_rows(geo, kind, v, rows)
+    gd = to_dev(g)
+    for prec, tol in ((bie.FP64, TOL64), (bie.MIXED, TOL32[kind])):
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        assert bie.apply_operator(ctx, gd, kind, prec, torch.from_numpy(v).cuda(), out) == bie.OK
+        o = out.cpu().numpy()
+        got = o[rows] if kind == 0 else o[np.stack([2 * rows, 2 * rows + 1], 1).reshape(-1)]
+        err = rel_max(got, ref)
+        print(f"{wl} rows prec={prec}: {err:.2e}")
+        assert err <= tol
+
+
+@pytest.mark.parametrize("wl,kind", [("stars100_M25600", 0), ("ellipses400_M51200", 1)])
+def test_full_size_solve_properties(ctx, wl, kind):
+    g = synth.WORKLOADS[wl]()
+    geo = geometry.nodes(g)
+    N, M = geo["N"], geo["M"]
+    load = g["q"] if kind == 0 else g["FT"].reshape(-1)
+    gd = to_dev(g)
+    outs = {}
+    for prec in (bie.MIXED, bie.FP64):
+        out = torch.empty(N if kind == 0 else 3 * N, dtype=torch.float64, device="cuda")
+        dens = torch.empty(M * (kind + 1), dtype=torch.float64, device="cuda")
+        fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
+        rc, info = fn(ctx, gd, torch.from_numpy(load).cuda(), out, dens, opts=bie.make_opts(precision=prec))
+        torch.cuda.synchronize()
+        assert rc == bie.OK, (rc, info)
+        print(f"{wl} prec={prec}: {info}")
+        outs[prec] = (out.cpu().numpy(), dens.cpu().numpy(), info)
+    res, nu, info = outs[bie.MIXED]
+    # (1) the density satisfies the oracle's equation at sampled rows: (1/2 I + K + L) nu = L sigma
+    rows = np.sort(np.random.default_rng(6).choice(M, 40, replace=False))
+    lhs = _sampled_rows(geo, kind, nu, rows)
+    if kind == 0:
+        rhs = g["q"][geo["body"][rows]]
+    else:
+        px, py = stokes.perp(geo)
+        b = geo["body"][rows]
+        FT = g["FT"]
+        rhs = np.stack([FT[b, 0] + FT[b, 2] * px[rows], FT[b, 1] + FT[b, 2] * py[rows]], 1).reshape(-1)
+    assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-10
+    # (2) the outputs recomputed by the oracle from the GPU density
+    if kind == 0:
+        ref = laplace.potentials_from_density(g, nu)
+    else:
+        ref = stokes.motion_from_density(g, nu).reshape(-1)
+    assert rel2(res, ref) < 1e-12
+    # (3) mixed precision and FP64 agree
+    assert rel2(res, outs[bie.FP64][0]) < TOL_SOLVE
+    # (4) constraints of the equivalence lemma
+    assert info["constraint_residual"] < 1e-10
