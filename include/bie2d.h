@@ -147,6 +147,32 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision,
                    const double* in, double* out, void* stream);
 
+/* Operator application that allocates nothing (this entry point has no
+ * counterpart in the paper; it serves callers that cannot allocate device
+ * memory: code under a memory budget fixed in advance, inside a framework
+ * that owns every device allocation through its own pool, or in a loop where
+ * cudaMalloc/cudaFree, which may synchronise the device, are not allowed).
+ * Same result as apply_operator (out = (1/2 I + K + L) in, unscaled), but
+ * without a context: its scratch (staged geometry and pair-sum partials, about
+ * 6 MB) is one fixed file-scope device array that every GPU loading this
+ * library holds until the process exits.
+ *   - Limits: M <= BIE_NOALLOC_MAX_NODES nodes and N <= BIE_NOALLOC_MAX_BODIES
+ *     bodies; larger inputs return BIE_ERR_NOMEM and nothing runs.
+ *   - Every array (geometry, in, out) must be device memory of the current
+ *     device (BIE_ERR_INVALID otherwise); body_start is read back with a copy
+ *     that synchronises the stream.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current: make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one scratch array: calls that overlap
+ *     on the GPU (other streams, other host threads) race and corrupt each
+ *     other's results; order them on one stream or serialise them.  Nothing
+ *     in the scratch needs to start at zero: every call writes what it reads. */
+#define BIE_NOALLOC_MAX_NODES 16384
+#define BIE_NOALLOC_MAX_BODIES 2048
+int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, const double* in,
+                           double* out, void* stream);
+
 /* Kernel timing of the pair sums (the O(M^2) hot loop), for measurement.
  * counters[precision][kind]: launches that did work and their summed device
  * time, taken with CUDA events recorded on the call's stream around each

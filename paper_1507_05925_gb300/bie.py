@@ -89,6 +89,8 @@ def load():
         f.restype = i32
     lib.apply_operator.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator.restype = i32
+    lib.apply_operator_noalloc.argtypes = [ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
+    lib.apply_operator_noalloc.restype = i32
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
     _ = dbl
@@ -218,5 +220,14 @@ def apply_operator(ctx: Context, geom, kind: int, precision: int, inp, out, stre
     g, keep = make_geometry(geom)
     rc = ctx.lib.apply_operator(ctx.handle, ctypes.byref(g), kind, precision, _ptr(inp), _ptr(out),
                                 _stream_ptr(stream))
+    del keep
+    return rc
+
+
+def apply_operator_noalloc(geom, kind: int, precision: int, inp, out, stream=None) -> int:
+    """apply_operator_noalloc of include/bie2d.h (no context, no allocation; device arrays only)."""
+    lib = load()
+    g, keep = make_geometry(geom)
+    rc = lib.apply_operator_noalloc(ctypes.byref(g), kind, precision, _ptr(inp), _ptr(out), _stream_ptr(stream))
     del keep
     return rc
