@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None,
+                    choices=["laplace_fp32", "laplace_fp64", "stokes_fp32", "stokes_fp64"],
+                    help="time one operator application (pair sum + epilogue) instead of solves; "
+                         "Laplace on the 100-star workload, Stokes on the 400-ellipse workload")
     return ap.parse_args()
 
 
@@ -204,11 +208,48 @@ def run_reference(args, rank, world):
     }))
 
 
+def run_kernel(args, local):
+    """Operator applications only (for kernel timing and ncu captures)."""
+    import torch
+
+    from paper_1507_05925_gb300 import bie, build
+
+    build.build()
+    kind_name, prec_name = args.kernel.split("_")
+    kind = bie.LAPLACE if kind_name == "laplace" else bie.STOKES
+    prec = bie.MIXED if prec_name == "fp32" else bie.FP64
+    g = synth.star_grid(seed=1000) if kind == bie.LAPLACE else synth.ellipse_suspension(seed=2000)
+    dev = torch.device("cuda", local)
+    gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
+    n = g["x"].size * (kind + 1)
+    v = torch.randn(n, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    ctx = bie.Context(local)
+    for _ in range(args.warmup):
+        assert bie.apply_operator(ctx, gd, kind, prec, v, out) == bie.OK
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for _ in range(args.steps):
+        assert bie.apply_operator(ctx, gd, kind, prec, v, out) == bie.OK
+    torch.cuda.synchronize()
+    prof = ctx.profile(False)[args.kernel]
+    ms = prof["ms"] / max(prof["launches"], 1)
+    flops = FLOPS_PER_PAIR[kind_name] * prof["pairs"] / max(prof["launches"], 1)
+    print(json.dumps({"kernel": args.kernel, "M": g["x"].size, "launches": prof["launches"],
+                      "ms_per_launch": ms, "pairs_per_s": prof["pairs"] / (prof["ms"] / 1e3),
+                      "tflops": flops / (ms / 1e3) / 1e12}))
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.kernel:
+        run_kernel(args, local)
         return
     import torch
 
