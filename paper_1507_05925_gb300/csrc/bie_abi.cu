@@ -141,6 +141,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   g.zy = A.take<double>(N);
   g.delta = A.take<double>(N);
   g.wind = A.take<double>(N);
+  g.bbox = A.take<float4>(N);
   if (stage_in) {
     w.x = A.take<double>(M);
     w.y = A.take<double>(M);

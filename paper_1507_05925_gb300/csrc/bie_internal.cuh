@@ -5,7 +5,7 @@
 //                  pf = (x_hi, y_hi, x_lo, y_lo) float4 with x = x_hi + x_lo exactly
 //                  to ~2^-48 relative, nf = (nx, ny) float2, body_of (int32)
 //   per body  [N]: len = |Gamma_i|, xc, yc (arc-length centroid), W_i, interior
-//                  point z0 and stencil step delta
+//                  point z0 and stencil step delta, FP32 bounding box
 //   densities: scaled by sqrt(w) (the L2 rescaling of Section 6.1.1); Stokes
 //              vectors node-interleaved (2a + c).
 #pragma once
@@ -30,6 +30,7 @@ struct Geo {
   float2* nf = nullptr;
   double *len = nullptr, *xc = nullptr, *yc = nullptr, *W = nullptr;
   double *zx = nullptr, *zy = nullptr, *delta = nullptr, *wind = nullptr;
+  float4* bbox = nullptr;  // [N] (xmin, ymin, xmax, ymax) of the body's nodes, FP32
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a

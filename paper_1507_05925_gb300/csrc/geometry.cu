@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ 
   const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
   const double hstep = 2.0 * kPi / (double)(a1 - a0);
   double sl = 0.0, sx = 0.0, sy = 0.0;
+  double bx0 = 1e300, by0 = 1e300, bx1 = -1e300, by1 = -1e300;
   for (int a = a0 + threadIdx.x; a < a1; a += kB) {
     const double x = X[a], y = Y[a], dx = DX[a], dy = DY[a];
     const double sp = sqrt(dx * dx + dy * dy);
@@ -48,7 +49,15 @@ __global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ 
     sl += w;
     sx += w * x;
     sy += w * y;
+    bx0 = fmin(bx0, x);
+    by0 = fmin(by0, y);
+    bx1 = fmax(bx1, x);
+    by1 = fmax(by1, y);
   }
+  bx0 = block_min<kB>(bx0, sh);
+  by0 = block_min<kB>(by0, sh);
+  bx1 = -block_min<kB>(-bx1, sh);
+  by1 = -block_min<kB>(-by1, sh);
   sl = block_sum<kB>(sl, sh);
   sx = block_sum<kB>(sx, sh);
   sy = block_sum<kB>(sy, sh);
@@ -77,6 +86,9 @@ __global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ 
     g.zy[i] = zy;
     g.delta[i] = 0.25 * sqrt(dmin2);
     g.wind[i] = wind / (2.0 * kPi);
+    // rounded outwards to FP32
+    g.bbox[i] = make_float4(__double2float_rd(bx0), __double2float_rd(by0), __double2float_ru(bx1),
+                            __double2float_ru(by1));
   }
 }
 

@@ -27,13 +27,14 @@ constexpr int kNoallocMaxSplits = 16;
 constexpr int kMaxDevices = 64;
 
 // Bytes for: staged geometry (per node 7 doubles + float4 + float2 + int, per
-// body 8 doubles + body_start) and the partials [splits][2 * nodes] doubles,
+// body 8 doubles + float4 + body_start) and the partials [splits][2 * nodes] doubles,
 // each section padded to 256 bytes.
 constexpr size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kScratchBytes =
     pad256((kNoallocMaxBodies + 1) * sizeof(int)) + pad256(kNoallocMaxNodes * sizeof(int)) +
     7 * pad256(kNoallocMaxNodes * sizeof(double)) + pad256(kNoallocMaxNodes * sizeof(float4)) +
     pad256(kNoallocMaxNodes * sizeof(float2)) + 8 * pad256(kNoallocMaxBodies * sizeof(double)) +
+    pad256(kNoallocMaxBodies * sizeof(float4)) +
     pad256((size_t)kNoallocMaxSplits * 2 * kNoallocMaxNodes * sizeof(double));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -134,6 +135,7 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
   g.zy = c.take<double>(kNoallocMaxBodies);
   g.delta = c.take<double>(kNoallocMaxBodies);
   g.wind = c.take<double>(kNoallocMaxBodies);
+  g.bbox = c.take<float4>(kNoallocMaxBodies);
   double* partial = c.take<double>((size_t)kNoallocMaxSplits * 2 * kNoallocMaxNodes);
   if (c.off > kScratchBytes) return BIE_ERR_NOMEM;  // sizing and carving disagree
 

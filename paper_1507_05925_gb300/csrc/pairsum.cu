@@ -11,11 +11,14 @@
 // partial[s][a] that the epilogue adds in a fixed order (deterministic), in
 // FP64, together with the diagonal limit, 1/2 I and the completion L.
 //
-// FP32 variant: positions are held as hi/lo float pairs so that
-// dx = (xa_hi - xb_hi) + (xa_lo - xb_lo) is exact to FP32 rounding of dx itself
-// even for neighbouring nodes far from the origin (the near-pair cancellation in
-// r . n_a would otherwise lose digits); the reciprocal is the hardware
-// rcp.approx.f32; each tile's FP32 sums are promoted into FP64 accumulators.
+// FP32 variant: positions are held as hi/lo float pairs so that, for a source
+// tile close to the target block, dx = (xa_hi - xb_hi) + (xa_lo - xb_lo) is
+// exact to FP32 rounding of dx itself even for neighbouring nodes far from the
+// origin (the near-pair cancellation in r . n_a would otherwise lose digits).
+// Tiles far from the block (gap at least both boxes' half-diagonals) use plain
+// FP32 coordinates relative to the block centre: 4 fewer instructions a pair.
+// The reciprocal is the hardware rcp.approx.f32; each tile's FP32 sums are
+// promoted into FP64 accumulators.
 #include <algorithm>
 
 #include "bie_internal.cuh"
@@ -114,11 +117,23 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
 // ------------------------------------------------------------------ FP32 ----
 constexpr int kB32 = 128, kT32 = 4, kTile32 = 256;
 
+// Near tiles (sources whose bounding box is close to the target block's):
+// exact differences from the hi/lo coordinates, reloaded here so that they
+// are not live across the far tiles.
 template <int KIND, bool DIAG>
-__device__ __forceinline__ void tile32(const float4* __restrict__ sp, const float2* __restrict__ sq,
-                                       int nt, int jt, const int* ta, const float* txh, const float* tyh,
-                                       const float* txl, const float* tyl, const float* tnx,
-                                       const float* tny, float* ax, float* ay) {
+__device__ __forceinline__ void tile_near(const float4* __restrict__ pf, const float4* __restrict__ sp,
+                                          const float2* __restrict__ sq, int nt, int jt, int a0, int M,
+                                          const float* tnx, const float* tny, float* ax, float* ay) {
+  float txh[kT32], tyh[kT32], txl[kT32], tyl[kT32];
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) {
+    const int a = a0 + k * kB32;
+    const float4 p = a < M ? pf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    txh[k] = p.x;
+    tyh[k] = p.y;
+    txl[k] = p.z;
+    tyl[k] = p.w;
+  }
 #pragma unroll 2
   for (int l = 0; l < nt; ++l) {
     const float4 p = sp[l];
@@ -131,14 +146,14 @@ __device__ __forceinline__ void tile32(const float4* __restrict__ sp, const floa
       const float inv = rcp_approx(r2);
       if (KIND == 0) {
         float s = q.x * inv;
-        if (DIAG) s = (ta[k] == jt + l) ? 0.0f : s;
+        if (DIAG) s = (a0 + k * kB32 == jt + l) ? 0.0f : s;
         ax[k] = fmaf(dx, s, ax[k]);
         ay[k] = fmaf(dy, s, ay[k]);
       } else {
         const float rq = fmaf(dx, q.x, dy * q.y);
         const float rn = fmaf(dx, tnx[k], dy * tny[k]);
         float c = (rq * rn) * (inv * inv);
-        if (DIAG) c = (ta[k] == jt + l) ? 0.0f : c;
+        if (DIAG) c = (a0 + k * kB32 == jt + l) ? 0.0f : c;
         ax[k] = fmaf(c, dx, ax[k]);
         ay[k] = fmaf(c, dy, ay[k]);
       }
@@ -146,8 +161,52 @@ __device__ __forceinline__ void tile32(const float4* __restrict__ sp, const floa
   }
 }
 
+// Far tiles: plain FP32 coordinates relative to the target block's centre.
+// Their rounding (|x'| 2^-24 with |x'| at most ~3 |r| for far pairs) is
+// below 2e-7 of each term.
 template <int KIND>
-__global__ void __launch_bounds__(kB32) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
+__device__ __forceinline__ void tile_far(const float4* __restrict__ sp, int nt, const float* tlx,
+                                         const float* tly, const float* tnx, const float* tny, float* ax,
+                                         float* ay) {
+#pragma unroll 2
+  for (int l = 0; l < nt; ++l) {
+    const float4 p = sp[l];  // (x', y', q1, q2)
+#pragma unroll
+    for (int k = 0; k < kT32; ++k) {
+      const float dx = tlx[k] - p.x;
+      const float dy = tly[k] - p.y;
+      const float r2 = fmaf(dx, dx, dy * dy);
+      const float inv = rcp_approx(r2);
+      if (KIND == 0) {
+        const float s = p.z * inv;
+        ax[k] = fmaf(dx, s, ax[k]);
+        ay[k] = fmaf(dy, s, ay[k]);
+      } else {
+        const float rq = fmaf(dx, p.z, dy * p.w);
+        const float rn = fmaf(dx, tnx[k], dy * tny[k]);
+        const float c = (rq * rn) * (inv * inv);
+        ax[k] = fmaf(c, dx, ax[k]);
+        ay[k] = fmaf(c, dy, ay[k]);
+      }
+    }
+  }
+}
+
+// Union of the bounding boxes of bodies [b0, b1].
+__device__ __forceinline__ float4 body_range_box(const float4* __restrict__ bbox, int b0, int b1) {
+  float4 u = bbox[b0];
+  for (int i = b0 + 1; i <= b1; ++i) {
+    const float4 b = bbox[i];
+    u.x = fminf(u.x, b.x);
+    u.y = fminf(u.y, b.y);
+    u.z = fmaxf(u.z, b.z);
+    u.w = fmaxf(u.w, b.w);
+  }
+  return u;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kB32, KIND == 0 ? 8 : 6) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -156,54 +215,69 @@ __global__ void __launch_bounds__(kB32) k_pair32(Geo g, VecRef vr, const double*
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
+  const int tend = min(M, tbase + kB32 * kT32);
   const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
-  float txh[kT32], tyh[kT32], txl[kT32], tyl[kT32], tnx[kT32], tny[kT32];
+  // the target block's box, centre and half-diagonal
+  const float4 tb = body_range_box(g.bbox, g.body_of[tbase], g.body_of[tend - 1]);
+  const float cx = 0.5f * (tb.x + tb.z), cy = 0.5f * (tb.y + tb.w);
+  const float et = 0.5f * sqrtf((tb.z - tb.x) * (tb.z - tb.x) + (tb.w - tb.y) * (tb.w - tb.y));
+  const int a0 = tbase + threadIdx.x;
+  float tlx[kT32], tly[kT32], tnx[kT32], tny[kT32];
   double dax[kT32], day[kT32];
-  int ta[kT32];
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {
-    const int a = tbase + threadIdx.x + k * kB32;
-    ta[k] = a;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int a = a0 + k * kB32;
+    float4 p = make_float4(cx, cy, 0.f, 0.f);
     float2 n = make_float2(0.f, 0.f);
     if (a < M) {
       p = g.pf[a];
-      n = g.nf[a];
+      if (KIND == 1) n = g.nf[a];
     }
-    txh[k] = p.x;
-    tyh[k] = p.y;
-    txl[k] = p.z;
-    tyl[k] = p.w;
+    tlx[k] = (p.x - cx) + p.z;
+    tly[k] = (p.y - cy) + p.w;
     tnx[k] = n.x;
     tny[k] = n.y;
     dax[k] = 0.0;
     day[k] = 0.0;
   }
   for (int jt = j0; jt < j1; jt += kTile32) {
+    const int nt = min(kTile32, j1 - jt);
+    // far when the boxes are at least both half-diagonals apart (block-uniform)
+    const float4 sb = body_range_box(g.bbox, g.body_of[jt], g.body_of[jt + nt - 1]);
+    const float gx = fmaxf(0.f, fmaxf(sb.x - tb.z, tb.x - sb.z));
+    const float gy = fmaxf(0.f, fmaxf(sb.y - tb.w, tb.y - sb.w));
+    const float es = 0.5f * sqrtf((sb.z - sb.x) * (sb.z - sb.x) + (sb.w - sb.y) * (sb.w - sb.y));
+    const float gap2 = gx * gx + gy * gy;
+    const float need = fmaxf(et, es);
+    const bool far = gap2 > 0.f && gap2 >= need * need;
     __syncthreads();
-    for (int l = threadIdx.x; l < kTile32; l += kB32) {
+    for (int l = threadIdx.x; l < nt; l += kB32) {
       const int b = jt + l;
-      if (b < j1) {
-        sp[l] = g.pf[b];
-        if (KIND == 0)
-          sq[l] = make_float2((float)(sscale[b] * v[b]), 0.f);
-        else
-          sq[l] = make_float2((float)(sscale[b] * v[2 * b]), (float)(sscale[b] * v[2 * b + 1]));
+      const float4 p = g.pf[b];
+      float q1, q2 = 0.f;
+      if (KIND == 0) {
+        q1 = (float)(sscale[b] * v[b]);
       } else {
-        // far away, zero strength: contributes exactly 0
-        sp[l] = make_float4(1.0e15f, 1.0e15f, 0.f, 0.f);
-        sq[l] = make_float2(0.f, 0.f);
+        q1 = (float)(sscale[b] * v[2 * b]);
+        q2 = (float)(sscale[b] * v[2 * b + 1]);
+      }
+      if (far) {
+        sp[l] = make_float4((p.x - cx) + p.z, (p.y - cy) + p.w, q1, q2);
+      } else {
+        sp[l] = p;
+        sq[l] = make_float2(q1, q2);
       }
     }
     __syncthreads();
     float ax[kT32], ay[kT32];
 #pragma unroll
     for (int k = 0; k < kT32; ++k) ax[k] = ay[k] = 0.f;
-    const bool diag = (jt < tbase + kB32 * kT32) && (jt + kTile32 > tbase);
-    if (diag)
-      tile32<KIND, true>(sp, sq, kTile32, jt, ta, txh, tyh, txl, tyl, tnx, tny, ax, ay);
+    if (far)
+      tile_far<KIND>(sp, nt, tlx, tly, tnx, tny, ax, ay);
+    else if ((jt < tend) && (jt + nt > tbase))
+      tile_near<KIND, true>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
     else
-      tile32<KIND, false>(sp, sq, kTile32, jt, ta, txh, tyh, txl, tyl, tnx, tny, ax, ay);
+      tile_near<KIND, false>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
 #pragma unroll
     for (int k = 0; k < kT32; ++k) {
       dax[k] += (double)ax[k];
@@ -212,7 +286,7 @@ __global__ void __launch_bounds__(kB32) k_pair32(Geo g, VecRef vr, const double*
   }
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {
-    const int a = ta[k];
+    const int a = a0 + k * kB32;
     if (a < M) {
       if (KIND == 0)
         partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax[k] + g.ny[a] * day[k];
@@ -287,32 +361,52 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
   }
 }
 
+// Occupancy of each pair kernel (blocks per SM) and the SM count, queried once
+// per device.
+struct DeviceShape {
+  int nsm = 0;
+  int occ[2][2] = {{0, 0}, {0, 0}};  // [precision][kind]
+};
+
+const DeviceShape& device_shape() {
+  static DeviceShape shapes[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  DeviceShape& d = shapes[dev & 63];
+  if (d.nsm == 0) {
+    cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0][0], k_pair64<0>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0][1], k_pair64<1>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][0], k_pair32<0>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][1], k_pair32<1>, kB32, 0);
+    cudaGetLastError();
+    if (d.nsm <= 0) d.nsm = 152;
+    for (auto& row : d.occ)
+      for (int& o : row)
+        if (o <= 0) o = 4;
+  }
+  return d;
+}
+
 }  // namespace
 
-// Choose the source split: the busiest SM's load, ceil(blocks/152) * (chunk + overhead),
-// is minimised over chunks that are multiples of the tile.
+// Choose the source split so that one wave fills every SM with as many
+// blocks as can be resident: blocks = target blocks x splits ~ SMs x occupancy.
+// Splits need not be tile-aligned (the kernels handle a short last tile).
 PairPlan plan_pairs(int M, int kind, int precision) {
+  const DeviceShape& d = device_shape();
   const int per_block = precision == 0 ? kB64 * kT64 : kB32 * kT32;
-  const int tile = precision == 0 ? kTile64 : kTile32;
   const long long bx = (M + per_block - 1) / per_block;
-  const int nsm = 152;
-  const long long overhead = tile / 2;
-  PairPlan best{1, M};
-  long long best_cost = -1;
-  const int max_c = std::max(1, (M + tile - 1) / tile);
-  for (int c = 1; c <= max_c; ++c) {
-    const long long chunk = (long long)c * tile;
-    const long long S = (M + chunk - 1) / chunk;
-    const long long blocks = bx * S;
-    const long long cost = ((blocks + nsm - 1) / nsm) * (chunk + overhead);
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best.S = (int)S;
-      best.chunk = (int)chunk;
-    }
-  }
-  (void)kind;
-  return best;
+  const long long slots = (long long)d.nsm * d.occ[precision == 0 ? 0 : 1][kind];
+  long long S = bx >= slots ? 1 : slots / bx;
+  const long long min_chunk = 64;
+  if (S > (M + min_chunk - 1) / min_chunk) S = (M + min_chunk - 1) / min_chunk;
+  if (S < 1) S = 1;
+  const long long chunk = (M + S - 1) / S;
+  PairPlan p;
+  p.chunk = (int)chunk;
+  p.S = (int)((M + chunk - 1) / chunk);
+  return p;
 }
 
 cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,

@@ -2,9 +2,11 @@
 allocate device memory (a fixed memory budget, a framework that owns every
 allocation, or a loop that must not synchronise through cudaMalloc/cudaFree).
 
-Its output must equal apply_operator's within the FP64 operator tolerance of
-the parity tests, on two calls in a row with different sizes, so that what an
-earlier call left in the shared scratch array cannot leak into a later result.
+Its output must equal apply_operator's within the operator tolerances of the
+parity tests (FP64: 1e-13; FP32 pair sums: the FP32 bound, since a different
+source split regroups the FP32 tile sums), on two calls in a row with
+different sizes, so that what an earlier call left in the shared scratch array
+cannot leak into a later result.
 This file is collected last on purpose.
 """
 import numpy as np
@@ -17,7 +19,7 @@ from paper_1507_05925_gb300 import bie  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-13  # same bound as the FP64 operator parity tests
+TOL = {bie.FP64: {0: 1e-13, 1: 1e-13}, bie.MIXED: {0: 2e-6, 1: 5e-6}}  # as in test_gpu_parity
 
 
 def _dev(g):
@@ -47,7 +49,7 @@ def test_noalloc_matches_apply_operator(kind, prec):
         assert bie.apply_operator_noalloc(gd, kind, prec, v, got) == bie.OK
         torch.cuda.synchronize()
         err = (got - ref).abs().max().item() / ref.abs().max().item()
-        assert err <= TOL, err
+        assert err <= TOL[prec][kind], err
     ctx.close()
 
 
