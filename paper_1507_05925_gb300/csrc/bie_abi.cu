@@ -17,6 +17,11 @@
 
 using namespace bie;
 
+namespace {
+// weight alpha of the per-body completion used inside the FP32 inner solves
+constexpr double kInnerCompletionWeight = 1.0;
+}  // namespace
+
 namespace bie {
 static std::atomic<long long> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -104,6 +109,7 @@ struct Work {
   double *ipt = nullptr, *load = nullptr, *io_in = nullptr, *io_out = nullptr;
   // solver
   double *V = nullptr, *f = nullptr, *xs = nullptr, *r = nullptr, *d = nullptr, *rin = nullptr, *ytmp = nullptr;
+  double* rc = nullptr;
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
   double *h1 = nullptr, *h2 = nullptr, *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
   KState* st = nullptr;
@@ -171,6 +177,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.d = A.take<double>(n);
     w.rin = A.take<double>(n);
     w.ytmp = A.take<double>(n);
+    w.rc = A.take<double>(n);
     w.H = A.take<double>((size_t)(m + 1) * m);
     w.cs = A.take<double>(m);
     w.sn = A.take<double>(m);
@@ -327,15 +334,17 @@ cudaError_t timed_pair_sum(bie_ctx* ctx, const Geo& g, int kind, int prec, const
 }
 
 // The operator (1/2 I + K + L) on sqrt(w)-scaled vectors, in FP64 or FP32 pair sums.
+// alpha = 0: the paper's completion; alpha > 0: weighted per body (inner solves).
 struct Op {
   bie_ctx* ctx;
   const Work* w;
   int prec;
+  double alpha = 0.0;
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
     const PairPlan& p = prec == 0 ? w->plan64 : w->plan32;
     cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
     if (e != cudaSuccess) return e;
-    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s);
+    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
   }
 };
 
@@ -482,7 +491,9 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(timed_pair_sum(ctx, w.g, kind, 0, w.plan64, vec(w.rin), w.g.sw, w.partial, nullptr, true, s));
     CK(epilogue(w.g, kind, w.plan64, vec(w.rin), w.partial, 1, 0, -1.0, vec(w.f), nullptr, s));
   }
-  const Op op64{ctx, &w, 0}, op32{ctx, &w, 1};
+  // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
+  // same solution, no outlier eigenvalue per body in the Krylov spectrum
+  const Op op64{ctx, &w, 0}, op32{ctx, &w, 1, kInnerCompletionWeight};
   int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, iters = 0, refs = 0;
   double relres = 0.0;
   bool converged = false;
@@ -512,7 +523,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     converged = fnorm == 0.0;
     while (!converged && refs < o.max_refine && remaining > 0) {
       KrylovResult kr;
-      if ((rc = gmres(ctx, w, op32, w.r, w.d, o.inner_tol, remaining, false, kr, s))) return rc;
+      CK(consistent_rhs(w.g, kind, kInnerCompletionWeight, w.r, w.rc, s));
+      if ((rc = gmres(ctx, w, op32, w.rc, w.d, o.inner_tol, remaining, false, kr, s))) return rc;
       iters += kr.iters;
       m32 += kr.matvecs;
       remaining -= kr.iters;

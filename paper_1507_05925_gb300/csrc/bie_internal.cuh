@@ -110,9 +110,14 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 // out = sign * [ 1/2 v + oscale * (K v + diag + [L] v) ] with the constants applied.
 // scaled = 1: v is sqrt(w)-scaled, source strength sw, output scaled by sw.
 // scaled = 0: v unscaled, source strength w, output unscaled.
+// alpha = 0: the paper's completion L; alpha > 0: L weighted per body by
+// alpha/|Gamma_i| (force part) and alpha/W_i (torque part).
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s);
+                     cudaStream_t s, double alpha = 0.0);
+// out = in - (I - C) L~(in) for a correction solved with the weighted completion.
+cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* in, double* out,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 int vec_grid(long long n);

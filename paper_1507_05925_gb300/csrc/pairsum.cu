@@ -305,7 +305,7 @@ constexpr int kBE = 256;
 //   y = Kv (constant applied) + diagonal limit + [L]; out = sign (1/2 v + oscale y).
 template <int KIND>
 __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double* __restrict__ partial,
-                                                  int S, int scaled, int with_L, double sign,
+                                                  int S, int scaled, int with_L, double alpha, double sign,
                                                   VecRef outr, const int* __restrict__ stop) {
   if (stop && *stop) return;
   __shared__ double sh[kBE / 32];
@@ -333,6 +333,12 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
       m1 = block_sum<kBE>(m1, sh);
       m2 = block_sum<kBE>(m2, sh);
     }
+    if (alpha > 0.0) {  // completion weighted per body: force part alpha/|Gamma_i|, torque part alpha/W_i
+      const double cf = alpha / g.len[i];
+      m0 *= cf;
+      m1 *= cf;
+      if (KIND == 1) m2 *= alpha / g.W[i];
+    }
   }
   for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
     const double os = scaled ? g.sw[a] : 1.0;
@@ -357,6 +363,50 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
       const double y2 = -kInvPi * k2 + dd * ty + m1 + py * m2;
       out[2 * a] = sign * (0.5 * v[2 * a] + os * y1);
       out[2 * a + 1] = sign * (0.5 * v[2 * a + 1] + os * y2);
+    }
+  }
+}
+
+// Right-hand side for a correction solved with the per-body weighted
+// completion (weights c_i): for A e = g, the discrete Gauss identities (column
+// sums of K equal -1/2 on the own body and 0 elsewhere, Sections 3.2 and 4.1)
+// give the completion moments of e from g alone, L e = L~(g) with
+// L~(g)_i = int_{Gamma_i} g / |Gamma_i| (and the torque moment over W_i), so
+// A_c e = g - (I - C) L~(g).  Scaled vectors; one block per body.
+template <int KIND>
+__global__ void __launch_bounds__(kBE) k_consistent_rhs(Geo g, double alpha, const double* __restrict__ in,
+                                                        double* __restrict__ out) {
+  __shared__ double sh[kBE / 32];
+  const int i = blockIdx.x;
+  const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
+  const double xc = g.xc[i], yc = g.yc[i];
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+    const double s = g.sw[a];
+    if (KIND == 0) {
+      m0 += s * in[a];
+    } else {
+      const double f1 = s * in[2 * a], f2 = s * in[2 * a + 1];
+      m0 += f1;
+      m1 += f2;
+      m2 += -(g.y[a] - yc) * f1 + (g.x[a] - xc) * f2;
+    }
+  }
+  m0 = block_sum<kBE>(m0, sh);
+  if (KIND == 1) {
+    m1 = block_sum<kBE>(m1, sh);
+    m2 = block_sum<kBE>(m2, sh);
+  }
+  const double df = (1.0 - alpha / g.len[i]) / g.len[i];
+  const double dt = KIND == 1 ? (1.0 - alpha / g.W[i]) / g.W[i] : 0.0;
+  for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+    const double s = g.sw[a];
+    if (KIND == 0) {
+      out[a] = in[a] - s * df * m0;
+    } else {
+      const double px = -(g.y[a] - yc), py = g.x[a] - xc;
+      out[2 * a] = in[2 * a] - s * (df * m0 + dt * m2 * px);
+      out[2 * a + 1] = in[2 * a + 1] - s * (df * m1 + dt * m2 * py);
     }
   }
 }
@@ -430,11 +480,21 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s) {
+                     cudaStream_t s, double alpha) {
   if (kind == 0)
-    k_epilogue<0><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, sign, out, stop);
+    k_epilogue<0><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
   else
-    k_epilogue<1><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, sign, out, stop);
+    k_epilogue<1><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* in, double* out,
+                           cudaStream_t s) {
+  if (kind == 0)
+    k_consistent_rhs<0><<<g.N, kBE, 0, s>>>(g, alpha, in, out);
+  else
+    k_consistent_rhs<1><<<g.N, kBE, 0, s>>>(g, alpha, in, out);
   note_launches(1);
   return cudaGetLastError();
 }
