@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "stars100_M25600"
-METRIC = "elastance solves/s at 1e-12 relative residual (mixed precision: FP32 pair sums, FP64 refinement)"
+METRIC = "elastance solves/s at 1e-12 relative residual (mixed precision: FP32 pair sums inside refinement)"
 # algorithmic flops per pair interaction (FMA = 2): Laplace r (2), |r|^2 (3),
 # q/|r|^2 (1), accumulate q r/|r|^2 (4); Stokes r (2), |r|^2 (3), r.mu (3),
 # r.n (3), (r.mu)(r.n)/|r|^4 (3), accumulate (4)
@@ -51,10 +51,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--precision", default="mixed_ff", choices=["mixed", "mixed_ff"],
+                    help="headline path: FP32 pair sums in refinement with an FP64 (mixed) or a "
+                         "float-float (mixed_ff) residual")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None,
-                    choices=["laplace_fp32", "laplace_fp64", "stokes_fp32", "stokes_fp64"],
+                    choices=["laplace_fp32", "laplace_fp64", "laplace_ff", "stokes_fp32", "stokes_fp64",
+                             "stokes_ff"],
                     help="time one operator application (pair sum + epilogue) instead of solves; "
                          "Laplace on the 100-star workload, Stokes on the 400-ellipse workload")
     return ap.parse_args()
@@ -217,7 +221,7 @@ def run_kernel(args, local):
     build.build()
     kind_name, prec_name = args.kernel.split("_")
     kind = bie.LAPLACE if kind_name == "laplace" else bie.STOKES
-    prec = bie.MIXED if prec_name == "fp32" else bie.FP64
+    prec = {"fp32": bie.MIXED, "fp64": bie.FP64, "ff": bie.MIXED_FF}[prec_name]
     g = synth.star_grid(seed=1000) if kind == bie.LAPLACE else synth.ellipse_suspension(seed=2000)
     dev = torch.device("cuda", local)
     gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
@@ -276,7 +280,10 @@ def main():
     ctx = bie.Context(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    mixed = bie.make_opts(precision=bie.MIXED)
+    head_prec = bie.MIXED_FF if args.precision == "mixed_ff" else bie.MIXED
+    other_prec = bie.MIXED if head_prec == bie.MIXED_FF else bie.MIXED_FF
+    mixed = bie.make_opts(precision=head_prec)
+    other = bie.make_opts(precision=other_prec)
     fp64 = bie.make_opts(precision=bie.FP64)
 
     def solve(opts):
@@ -320,11 +327,15 @@ def main():
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1000.0)
 
-    # plain FP64 GPU path on the same workload
+    # the other mixed-precision residual and the plain FP64 GPU path on the same workload
+    for _ in range(2):
+        solve(other)
+    ms_o, infos_o, _ = timed(other, args.steps, False)
+    other_rate = len(ms_o) / (sum(ms_o) / 1000.0)
     ms64, infos64, prof64 = timed(fp64, args.fp64_steps, True)
     fp64_rate = len(ms64) / (sum(ms64) / 1000.0)
 
-    # end to end through the C ABI with host (pinned) buffers: the library copies
+    # end to end through the C ABI with host (pinned) buffers (headline precision): the library copies
     # the geometry and charges in and the potentials out inside the timed call
     host = {k: torch.from_numpy(np.ascontiguousarray(g[k])).pin_memory() for k in
             ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
@@ -360,36 +371,43 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     kind = dname.split("_")[0]
-    is32 = dname.endswith("fp32")
+    is32 = not dname.endswith("fp64")
     per_launch_ms = d["ms"] / max(d["launches"], 1)
     pairs_per_launch = d["pairs"] / max(d["launches"], 1)
     achieved = FLOPS_PER_PAIR[kind] * pairs_per_launch / (per_launch_ms / 1e3) / 1e12
     peak = fp32_peak if is32 else fp64_peak
-    lap32 = prof["laplace_fp32"]
-    pair_rate32 = lap32["pairs"] / (lap32["ms"] / 1e3) if lap32["ms"] > 0 else None
-    lap64 = prof64["laplace_fp64"]
-    pair_rate64 = lap64["pairs"] / (lap64["ms"] / 1e3) if lap64["ms"] > 0 else None
+    def rate(p):
+        return p["pairs"] / (p["ms"] / 1e3) if p["ms"] > 0 else None
+    pair_rate32 = rate(prof["laplace_fp32"])
+    pair_rate64 = rate(prof64["laplace_fp64"])
+    pair_rate_ff = rate(prof["laplace_ff"])
     kernel_share = {k: round(v["ms"] / total_ms * world, 4) for k, v in prof.items() if v["ms"] > 0}
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums / f64 refinement",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("f32 pair sums, float-float residual, f64 Krylov" if head_prec == bie.MIXED_FF
+                  else "f32 pair sums, f64 residual, f64 Krylov"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "M": M, "N": N, "nodes_per_body": 256, "tol": 1e-12,
-                   "precision": "mixed", "l2": "flushed (256 MB write) before every step, outside the events",
+                   "precision": args.precision, "l2": "flushed (256 MB write) before every step, outside the events",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
         "fp64_solves_per_s": fp64_rate,
+        ("mixed_fp64_residual_solves_per_s" if other_prec == bie.MIXED else "mixed_ff_residual_solves_per_s"):
+            other_rate,
         "mixed_over_fp64": value / world / fp64_rate,
-        "pair_interactions_per_s": {"laplace_fp32": pair_rate32, "laplace_fp64": pair_rate64},
-        "solve_info": {"mixed": infos[-1], "fp64": infos64[-1]},
+        "pair_interactions_per_s": {"laplace_fp32": pair_rate32, "laplace_ff": pair_rate_ff,
+                                    "laplace_fp64": pair_rate64},
+        "solve_info": {args.precision: infos[-1], "other_mixed": infos_o[-1], "fp64": infos64[-1]},
         "kernel_share_of_step": kernel_share,
         "gpu_launches": launches,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": f"pair sum {dname}", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_note": (f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of measured peaks)"
+                                   + ("; float-float kernel: algorithmic flops of the FP64 formula" if dname.endswith("ff") else "")
                                    if is32 else "FP64: nominal GB300 1.25 TFLOP/s"),
                      "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms},
         "clocks": clocks,

@@ -72,6 +72,10 @@ extern "C" {
 #define BIE_PREC_FP64 0          /* all arithmetic in IEEE double */
 #define BIE_PREC_MIXED 1         /* pair sums in FP32 (FP32 accumulation per source tile);
                                     epilogue, Arnoldi, residuals and outputs in FP64 */
+#define BIE_PREC_MIXED_FF 2      /* solves: as BIE_PREC_MIXED, but the refinement residual's pair
+                                    sums run in float-float arithmetic on the FP32 pipes (about
+                                    48 significant bits, positions split exactly into three
+                                    floats) instead of FP64; apply_operator: float-float pair sums */
 
 typedef struct bie_ctx bie_ctx;
 
@@ -107,8 +111,9 @@ typedef struct {
                             (FP64 operator); default 1e-12 when <= 0 */
   int32_t max_iter;      /* cap on Krylov iterations over all cycles; default 500 when <= 0 */
   int32_t restart;       /* GMRES restart length m (1..200); default 50 when <= 0 */
-  int32_t precision;     /* BIE_PREC_FP64 or BIE_PREC_MIXED (FP64 iterative refinement
-                            around FP32-pair-sum GMRES) */
+  int32_t precision;     /* BIE_PREC_FP64 (GMRES in FP64), BIE_PREC_MIXED (FP64 iterative
+                            refinement around FP32-pair-sum GMRES) or BIE_PREC_MIXED_FF
+                            (the same refinement with float-float residual pair sums) */
   int32_t formulation;   /* 0: solve for the total density nu = mu + sigma with the
                             right-hand side L sigma (= q_i on Gamma_i), an identity of the
                             equivalence lemma (Section 3.5, 4.4); 1: the paper's form with
@@ -122,6 +127,7 @@ typedef struct {
   int32_t refinements;         /* refinement steps taken (mixed), 0 for FP64 */
   int32_t matvecs_fp64;        /* FP64 operator applications */
   int32_t matvecs_fp32;        /* FP32-pair-sum operator applications */
+  int32_t matvecs_ff;          /* float-float-pair-sum operator applications */
   double rel_residual;         /* final ||f - A nu|| / ||f|| with the FP64 operator */
   double constraint_residual;  /* max_i |int_{Gamma_i} mu| (and Stokes moments) / max load */
   double net_load;             /* |sum_i q_i| or |sum_i F_i| */
@@ -143,7 +149,8 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
 /* One application of the discrete second-kind operator (eqs. ModRep2,
  * ModRep2Stokes): out = (1/2 I + K + L) in, on unscaled densities.
  * kind = BIE_KIND_LAPLACE ([M] in/out) or BIE_KIND_STOKES ([2M], node-interleaved);
- * precision = BIE_PREC_FP64 or BIE_PREC_MIXED (FP32 pair sum, FP64 epilogue). */
+ * precision = BIE_PREC_FP64, BIE_PREC_MIXED (FP32 pair sum, FP64 epilogue) or
+ * BIE_PREC_MIXED_FF (float-float pair sum, FP64 epilogue). */
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision,
                    const double* in, double* out, void* stream);
 
@@ -174,7 +181,7 @@ int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, co
                            double* out, void* stream);
 
 /* Kernel timing of the pair sums (the O(M^2) hot loop), for measurement.
- * counters[precision][kind]: launches that did work and their summed device
+ * counters[precision][kind] (precision 0 FP64, 1 FP32, 2 float-float): launches that did work and their summed device
  * time, taken with CUDA events recorded on the call's stream around each
  * pair-sum launch (launches skipped after GMRES convergence are not counted),
  * and the pair interactions they evaluated, M (M - 1) per launch.  enable = 1
@@ -182,9 +189,9 @@ int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, co
  * the counters so far.  kernel_launches counts every kernel this library
  * launched (on any stream) since timing was enabled. */
 typedef struct {
-  int64_t launches[2][2];
-  double ms[2][2];
-  double pairs[2][2];
+  int64_t launches[3][2];
+  double ms[3][2];
+  double pairs[3][2];
   int64_t kernel_launches;
 } bie_profile_counters;
 

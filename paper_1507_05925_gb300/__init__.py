@@ -5,7 +5,7 @@ The compute path is the CUDA library libbie2d (C ABI in include/bie2d.h);
 ``bie`` is its thin ctypes binding, ``build`` compiles it in-tree.
 """
 from .bie import (  # noqa: F401
-    ERR_CUDA, ERR_INVALID, ERR_NOMEM, ERR_OUTSIDE, FP64, LAPLACE, MIXED, OK, STOKES,
+    ERR_CUDA, ERR_INVALID, ERR_NOMEM, ERR_OUTSIDE, FP64, LAPLACE, MIXED, MIXED_FF, OK, STOKES,
     WARN_NONNEUTRAL, WARN_NOT_CONVERGED, Context, apply_operator, elastance_solve, make_opts,
     mobility_solve,
 )

@@ -17,7 +17,7 @@ from . import build as _build
 OK, WARN_NONNEUTRAL, WARN_NOT_CONVERGED = 0, 1, 2
 ERR_INVALID, ERR_OUTSIDE, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -5
 LAPLACE, STOKES = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FF = 0, 1, 2
 
 
 class BieGeometry(ctypes.Structure):
@@ -38,6 +38,7 @@ class BieOpts(ctypes.Structure):
 class BieInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32),
                 ("matvecs_fp64", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32),
+                ("matvecs_ff", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("constraint_residual", ctypes.c_double),
                 ("net_load", ctypes.c_double)]
 
@@ -46,12 +47,12 @@ class BieInfo(ctypes.Structure):
 
 
 class BieProfileCounters(ctypes.Structure):
-    _fields_ = [("launches", (ctypes.c_int64 * 2) * 2), ("ms", (ctypes.c_double * 2) * 2),
-                ("pairs", (ctypes.c_double * 2) * 2), ("kernel_launches", ctypes.c_int64)]
+    _fields_ = [("launches", (ctypes.c_int64 * 2) * 3), ("ms", (ctypes.c_double * 2) * 3),
+                ("pairs", (ctypes.c_double * 2) * 3), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
-        for p, pn in ((0, "fp64"), (1, "fp32")):
+        for p, pn in ((0, "fp64"), (1, "fp32"), (2, "ff")):
             for k, kn in ((0, "laplace"), (1, "stokes")):
                 out[f"{kn}_{pn}"] = dict(launches=int(self.launches[p][k]), ms=float(self.ms[p][k]),
                                          pairs=float(self.pairs[p][k]))

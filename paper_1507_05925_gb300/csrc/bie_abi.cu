@@ -113,7 +113,7 @@ struct Work {
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
   double *h1 = nullptr, *h2 = nullptr, *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
   KState* st = nullptr;
-  PairPlan plan64, plan32;
+  PairPlan plan64, plan32, planff;
   int P = 1, grid = 1;
 };
 
@@ -148,6 +148,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   g.delta = A.take<double>(N);
   g.wind = A.take<double>(N);
   g.bbox = A.take<float4>(N);
+  g.qscale = A.take<double>(2);
   if (stage_in) {
     w.x = A.take<double>(M);
     w.y = A.take<double>(M);
@@ -164,7 +165,8 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   }
   w.plan64 = plan_pairs(M, kind, 0);
   w.plan32 = plan_pairs(M, kind, 1);
-  const int S = std::max(w.plan64.S, w.plan32.S);
+  w.planff = plan_pairs(M, kind, 2);
+  const int S = std::max(std::max(w.plan64.S, w.plan32.S), w.planff.S);
   w.partial = A.take<double>((size_t)S * n);
   w.grid = vec_grid(n);
   w.part = A.take<double>((size_t)w.grid * 201 + 64);
@@ -341,7 +343,7 @@ struct Op {
   int prec;
   double alpha = 0.0;
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
-    const PairPlan& p = prec == 0 ? w->plan64 : w->plan32;
+    const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
     cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
     if (e != cudaSuccess) return e;
     return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
@@ -465,8 +467,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
   bie_opts o;
   fill_opts(opts_in, o);
-  if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED)
-    return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64 or BIE_PREC_MIXED");
+  if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED && o.precision != BIE_PREC_MIXED_FF)
+    return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64, BIE_PREC_MIXED or BIE_PREC_MIXED_FF");
   if (o.formulation != 0 && o.formulation != 1) return fail(ctx, BIE_ERR_INVALID, "formulation must be 0 or 1");
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
@@ -494,7 +496,9 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
   const Op op64{ctx, &w, 0}, op32{ctx, &w, 1, kInnerCompletionWeight};
-  int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, iters = 0, refs = 0;
+  // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF
+  const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0};
+  int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, mff = 0, iters = 0, refs = 0;
   double relres = 0.0;
   bool converged = false;
   if (o.precision == BIE_PREC_FP64) {
@@ -530,8 +534,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
       remaining -= kr.iters;
       refs += 1;
       CK(axpy(w.xs, w.d, n, s));
-      CK(op64.apply(vec(w.xs), vec(w.ytmp), nullptr, s));
-      m64 += 1;
+      CK(opres.apply(vec(w.xs), vec(w.ytmp), nullptr, s));
+      if (opres.prec == 0) m64 += 1; else mff += 1;
       {
         KState init;
         memset(&init, 0, sizeof(init));
@@ -570,6 +574,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     info->refinements = refs;
     info->matvecs_fp64 = m64;
     info->matvecs_fp32 = m32;
+    info->matvecs_ff = mff;
     info->rel_residual = relres;
     info->constraint_residual = ctx->h_small[0];
     info->net_load = netload;
@@ -650,7 +655,7 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
   int rc = validate(ctx, geom, bs);
   if (rc) return rc;
   if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
-  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED)
+  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED && precision != BIE_PREC_MIXED_FF)
     return fail(ctx, BIE_ERR_INVALID, "bad precision");
   if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
   DeviceGuard dg(ctx->device);
@@ -664,7 +669,7 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;
   const double* din;
   if ((rc = stage_in(ctx, in, w.io_in, (size_t)w.n, &din, s))) return rc;
-  const PairPlan& p = precision == 0 ? w.plan64 : w.plan32;
+  const PairPlan& p = precision == 0 ? w.plan64 : (precision == 1 ? w.plan32 : w.planff);
   const bool dev_out = is_device_ptr(out);
   double* dout = dev_out ? out : w.io_out;
   CK(timed_pair_sum(ctx, w.g, kind, precision, p, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr,

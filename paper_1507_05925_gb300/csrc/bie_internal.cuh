@@ -31,6 +31,7 @@ struct Geo {
   double *len = nullptr, *xc = nullptr, *yc = nullptr, *W = nullptr;
   double *zx = nullptr, *zy = nullptr, *delta = nullptr, *wind = nullptr;
   float4* bbox = nullptr;  // [N] (xmin, ymin, xmax, ymax) of the body's nodes, FP32
+  double* qscale = nullptr;  // [2] 2^Q and 2^(Q+23): quanta of the exact 3-float split of positions
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a

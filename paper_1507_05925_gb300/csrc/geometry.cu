@@ -92,6 +92,26 @@ __global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ 
   }
 }
 
+// Quanta for the exact three-float split of positions used by the
+// float-float pair sums: with |x| < 2^e for every coordinate, Q = 22 - e, so
+// x = h + m + l with h a multiple of 2^-Q (|h| 2^Q < 2^22), m a multiple of
+// 2^-(Q+23) and |l| <= 2^-(Q+24): differences of h's and of m's are exact.
+__global__ void k_geo_scale(Geo g) {
+  __shared__ double sh[kB / 32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < g.N; i += kB) {
+    const float4 b = g.bbox[i];
+    m = fmax(m, fmax(fmax(fabs((double)b.x), fabs((double)b.y)), fmax(fabs((double)b.z), fabs((double)b.w))));
+  }
+  m = -block_min<kB>(-m, sh);
+  if (threadIdx.x == 0) {
+    int e = 0;
+    frexp(fmax(m, 1e-300), &e);  // m < 2^e
+    g.qscale[0] = ldexp(1.0, 22 - e);
+    g.qscale[1] = ldexp(1.0, 45 - e);
+  }
+}
+
 // f = sw * (L sigma): q_i on Gamma_i (Laplace), F_i + T_i (x - x^c_i)^perp (Stokes).
 __global__ void k_total_rhs(Geo g, int kind, const double* __restrict__ load, double* __restrict__ f) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.M; a += gridDim.x * blockDim.x) {
@@ -278,6 +298,8 @@ cudaError_t stage_geometry(const Geo& g, const double* x, const double* y, const
                            const double* dy, const double* ddx, const double* ddy,
                            const double* interior_pt, cudaStream_t s) {
   k_stage<<<g.N, kB, 0, s>>>(g, x, y, dx, dy, ddx, ddy, interior_pt);
+  note_launches(1);
+  k_geo_scale<<<1, kB, 0, s>>>(g);
   note_launches(1);
   return cudaGetLastError();
 }

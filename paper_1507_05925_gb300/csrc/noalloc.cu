@@ -34,7 +34,7 @@ constexpr size_t kScratchBytes =
     pad256((kNoallocMaxBodies + 1) * sizeof(int)) + pad256(kNoallocMaxNodes * sizeof(int)) +
     7 * pad256(kNoallocMaxNodes * sizeof(double)) + pad256(kNoallocMaxNodes * sizeof(float4)) +
     pad256(kNoallocMaxNodes * sizeof(float2)) + 8 * pad256(kNoallocMaxBodies * sizeof(double)) +
-    pad256(kNoallocMaxBodies * sizeof(float4)) +
+    pad256(kNoallocMaxBodies * sizeof(float4)) + pad256(2 * sizeof(double)) +
     pad256((size_t)kNoallocMaxSplits * 2 * kNoallocMaxNodes * sizeof(double));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -74,7 +74,8 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
       !geom->ddx || !geom->ddy)
     return BIE_ERR_INVALID;
   if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return BIE_ERR_INVALID;
-  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED) return BIE_ERR_INVALID;
+  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED && precision != BIE_PREC_MIXED_FF)
+    return BIE_ERR_INVALID;
   const int N = geom->n_bodies;
   if (N < 1) return BIE_ERR_INVALID;
   if (N > kNoallocMaxBodies) return BIE_ERR_NOMEM;
@@ -136,6 +137,7 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
   g.delta = c.take<double>(kNoallocMaxBodies);
   g.wind = c.take<double>(kNoallocMaxBodies);
   g.bbox = c.take<float4>(kNoallocMaxBodies);
+  g.qscale = c.take<double>(2);
   double* partial = c.take<double>((size_t)kNoallocMaxSplits * 2 * kNoallocMaxNodes);
   if (c.off > kScratchBytes) return BIE_ERR_NOMEM;  // sizing and carving disagree
 

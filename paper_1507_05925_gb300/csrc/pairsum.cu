@@ -298,6 +298,187 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 8 : 6) k_pair32(Geo g, VecRe
   }
 }
 
+// ------------------------------------------------------------ float-float ----
+// Pair sums in float-float ("double-single") arithmetic on the FP32 pipes, for
+// residuals that must be accurate far beyond FP32: every quantity is an
+// unevaluated sum h + l of two floats (about 48 significant bits).
+//  - positions: exact split x = h + m + l (quanta from g.qscale), so that
+//    dx = (h_a - h_b) + (m_a - m_b) + (l_a - l_b) has exact leading parts for
+//    every pair, near or far;
+//  - products: error-free a*b = p + fma(a, b, -p);
+//  - reciprocal: MUFU rcp.approx seed y0 refined by one Newton step in
+//    float-float, 1/r2 = y0 + y0 (1 - r2 y0);
+//  - sums: TwoSum (Knuth) for the leading parts, trailing parts added.
+constexpr int kBF = 128, kTF = 2, kTileF = 128;
+
+__device__ __forceinline__ void split3(double x, double s0, double s1, float& h, float& m, float& l) {
+  const double hh = rint(x * s0) / s0;
+  const double r = x - hh;
+  const double mm = rint(r * s1) / s1;
+  h = (float)hh;
+  m = (float)mm;
+  l = (float)(r - mm);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (ah + al)(bh + bl) as an unevaluated pair (p, e), |e| <~ 2^-22 |p|
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = ah * bh;
+  e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+}
+
+// float-float difference of two exactly split coordinates
+__device__ __forceinline__ void ff_diff(float ah, float am, float al, float bh, float bm, float bl, float& dh,
+                                        float& dl) {
+  const float d1 = ah - bh;  // exact: multiples of 2^-Q below 2^23 quanta
+  const float d2 = am - bm;  // exact likewise
+  dh = d1 + d2;              // |d1| >= |d2| unless d1 = 0: fast two-sum
+  dl = (d2 - (dh - d1)) + (al - bl);
+}
+
+template <int KIND, bool DIAG>
+__device__ __forceinline__ void tile_ff(const float4* __restrict__ sp, const float4* __restrict__ sq, int nt,
+                                        int jt, int a0, const float* txh, const float* txm, const float* txl,
+                                        const float* tyh, const float* tym, const float* tyl, const float* tnxh,
+                                        const float* tnxl, const float* tnyh, const float* tnyl, float* axh,
+                                        float* axl, float* ayh, float* ayl) {
+  for (int l = 0; l < nt; ++l) {
+    const float4 pa = sp[2 * l], pb = sp[2 * l + 1];  // (xh, xm, yh, ym), (xl, yl, -, -)
+    const float4 q = sq[l];                            // (q1h, q1l, q2h, q2l)
+#pragma unroll
+    for (int k = 0; k < kTF; ++k) {
+      float dxh, dxl, dyh, dyl;
+      ff_diff(txh[k], txm[k], txl[k], pa.x, pa.y, pb.x, dxh, dxl);
+      ff_diff(tyh[k], tym[k], tyl[k], pa.z, pa.w, pb.y, dyh, dyl);
+      // r2 = dx^2 + dy^2
+      const float p1 = dxh * dxh, p1e = fmaf(dxh, dxh, -p1);
+      const float p2 = dyh * dyh, p2e = fmaf(dyh, dyh, -p2);
+      float s, se;
+      two_sum(p1, p2, s, se);
+      const float lo = se + p1e + p2e + 2.0f * fmaf(dxh, dxl, dyh * dyl);
+      const float r2h = s + lo;
+      const float r2l = lo - (r2h - s);
+      // 1/r2
+      const float y0 = rcp_approx(r2h);
+      const float ee = fmaf(-r2l, y0, fmaf(-r2h, y0, 1.0f));
+      const float il = y0 * ee;
+      float ch, cl;  // the scalar factor multiplying r
+      if (KIND == 0) {
+        ff_mul(q.x, q.y, y0, il, ch, cl);
+      } else {
+        float rqh, rql, rnh, rnl, t1, t1e, t2, t2e, i2h, i2l, uh, ul;
+        // r . q and r . n
+        ff_mul(dxh, dxl, q.x, q.y, t1, t1e);
+        ff_mul(dyh, dyl, q.z, q.w, t2, t2e);
+        two_sum(t1, t2, rqh, rql);
+        rql += t1e + t2e;
+        ff_mul(dxh, dxl, tnxh[k], tnxl[k], t1, t1e);
+        ff_mul(dyh, dyl, tnyh[k], tnyl[k], t2, t2e);
+        two_sum(t1, t2, rnh, rnl);
+        rnl += t1e + t2e;
+        ff_mul(y0, il, y0, il, i2h, i2l);
+        ff_mul(rqh, rql, rnh, rnl, uh, ul);
+        ff_mul(uh, ul, i2h, i2l, ch, cl);
+      }
+      if (DIAG) {
+        const bool self = (a0 + k * kBF == jt + l);
+        ch = self ? 0.0f : ch;
+        cl = self ? 0.0f : cl;
+      }
+      float cxh, cxl, cyh, cyl, t, te;
+      ff_mul(ch, cl, dxh, dxl, cxh, cxl);
+      ff_mul(ch, cl, dyh, dyl, cyh, cyl);
+      two_sum(axh[k], cxh, t, te);
+      axh[k] = t;
+      axl[k] += te + cxl;
+      two_sum(ayh[k], cyh, t, te);
+      ayh[k] = t;
+      ayl[k] += te + cyl;
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double* __restrict__ sscale, int chunk,
+                                                 double* __restrict__ partial, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ float4 sp[2 * kTileF];
+  __shared__ float4 sq[kTileF];
+  const double* __restrict__ v = vr.ptr();
+  const int M = g.M;
+  const double s0 = g.qscale[0], s1 = g.qscale[1];
+  const int tbase = blockIdx.x * kBF * kTF;
+  const int tend = min(M, tbase + kBF * kTF);
+  const int a0 = tbase + threadIdx.x;
+  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  float txh[kTF], txm[kTF], txl[kTF], tyh[kTF], tym[kTF], tyl[kTF];
+  float tnxh[kTF], tnxl[kTF], tnyh[kTF], tnyl[kTF];
+  double dax[kTF], day[kTF];
+#pragma unroll
+  for (int k = 0; k < kTF; ++k) {
+    const int a = a0 + k * kBF;
+    const double x = a < M ? g.x[a] : 0.0, y = a < M ? g.y[a] : 0.0;
+    split3(x, s0, s1, txh[k], txm[k], txl[k]);
+    split3(y, s0, s1, tyh[k], tym[k], tyl[k]);
+    const double nx = a < M ? g.nx[a] : 0.0, ny = a < M ? g.ny[a] : 0.0;
+    tnxh[k] = (float)nx;
+    tnxl[k] = (float)(nx - (double)tnxh[k]);
+    tnyh[k] = (float)ny;
+    tnyl[k] = (float)(ny - (double)tnyh[k]);
+    dax[k] = 0.0;
+    day[k] = 0.0;
+  }
+  for (int jt = j0; jt < j1; jt += kTileF) {
+    const int nt = min(kTileF, j1 - jt);
+    __syncthreads();
+    for (int l = threadIdx.x; l < nt; l += kBF) {
+      const int b = jt + l;
+      float xh, xm, xl, yh, ym, yl;
+      split3(g.x[b], s0, s1, xh, xm, xl);
+      split3(g.y[b], s0, s1, yh, ym, yl);
+      sp[2 * l] = make_float4(xh, xm, yh, ym);
+      sp[2 * l + 1] = make_float4(xl, yl, 0.f, 0.f);
+      const double q1 = KIND == 0 ? sscale[b] * v[b] : sscale[b] * v[2 * b];
+      const double q2 = KIND == 0 ? 0.0 : sscale[b] * v[2 * b + 1];
+      const float q1h = (float)q1, q2h = (float)q2;
+      sq[l] = make_float4(q1h, (float)(q1 - (double)q1h), q2h, (float)(q2 - (double)q2h));
+    }
+    __syncthreads();
+    float axh[kTF], axl[kTF], ayh[kTF], ayl[kTF];
+#pragma unroll
+    for (int k = 0; k < kTF; ++k) axh[k] = axl[k] = ayh[k] = ayl[k] = 0.f;
+    if ((jt < tend) && (jt + nt > tbase))
+      tile_ff<KIND, true>(sp, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tnxh, tnxl, tnyh, tnyl, axh, axl, ayh,
+                          ayl);
+    else
+      tile_ff<KIND, false>(sp, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tnxh, tnxl, tnyh, tnyl, axh, axl, ayh,
+                           ayl);
+#pragma unroll
+    for (int k = 0; k < kTF; ++k) {
+      dax[k] += (double)axh[k] + (double)axl[k];
+      day[k] += (double)ayh[k] + (double)ayl[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTF; ++k) {
+    const int a = a0 + k * kBF;
+    if (a < M) {
+      if (KIND == 0)
+        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax[k] + g.ny[a] * day[k];
+      else {
+        partial[((long long)blockIdx.y * M + a) * 2] = dax[k];
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day[k];
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------- epilogue ----
 constexpr int kBE = 256;
 
@@ -415,7 +596,7 @@ __global__ void __launch_bounds__(kBE) k_consistent_rhs(Geo g, double alpha, con
 // per device.
 struct DeviceShape {
   int nsm = 0;
-  int occ[2][2] = {{0, 0}, {0, 0}};  // [precision][kind]
+  int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // [precision][kind]
 };
 
 const DeviceShape& device_shape() {
@@ -429,6 +610,8 @@ const DeviceShape& device_shape() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0][1], k_pair64<1>, kB64, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][0], k_pair32<0>, kB32, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][1], k_pair32<1>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[2][0], k_pair_ff<0>, kBF, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[2][1], k_pair_ff<1>, kBF, 0);
     cudaGetLastError();
     if (d.nsm <= 0) d.nsm = 152;
     for (auto& row : d.occ)
@@ -445,9 +628,9 @@ const DeviceShape& device_shape() {
 // Splits need not be tile-aligned (the kernels handle a short last tile).
 PairPlan plan_pairs(int M, int kind, int precision) {
   const DeviceShape& d = device_shape();
-  const int per_block = precision == 0 ? kB64 * kT64 : kB32 * kT32;
+  const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
   const long long bx = (M + per_block - 1) / per_block;
-  const long long slots = (long long)d.nsm * d.occ[precision == 0 ? 0 : 1][kind];
+  const long long slots = (long long)d.nsm * d.occ[precision][kind];
   long long S = bx >= slots ? 1 : slots / bx;
   const long long min_chunk = 64;
   if (S > (M + min_chunk - 1) / min_chunk) S = (M + min_chunk - 1) / min_chunk;
@@ -467,12 +650,18 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
       k_pair64<0><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
     else
       k_pair64<1><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
-  } else {
+  } else if (precision == 1) {
     dim3 grid((g.M + kB32 * kT32 - 1) / (kB32 * kT32), p.S);
     if (kind == 0)
       k_pair32<0><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
     else
       k_pair32<1><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+  } else {
+    dim3 grid((g.M + kBF * kTF - 1) / (kBF * kTF), p.S);
+    if (kind == 0)
+      k_pair_ff<0><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+    else
+      k_pair_ff<1><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
   }
   note_launches(1);
   return cudaGetLastError();

@@ -3,7 +3,8 @@
 Tolerances (written here, derived in the design notes):
   FP64 operator           max |gpu - oracle| <= 1e-13 max |oracle|  (rounding order only)
   FP32-pair-sum operator  max |gpu - oracle| <= TOL32 max |oracle|
-  solves, FP64 and mixed  ||phi - phi_oracle|| / ||phi_oracle|| <= 1e-10 (same for (v, omega))
+  float-float operator    max |gpu - oracle| <= TOLFF max |oracle|
+  solves, all precisions  ||phi - phi_oracle|| / ||phi_oracle|| <= 1e-10 (same for (v, omega))
 """
 import math
 
@@ -20,6 +21,8 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-13
 TOL32 = {0: 2e-6, 1: 5e-6}
+TOLFF = 1e-12
+TOL_OP = {bie.FP64: {0: TOL64, 1: TOL64}, bie.MIXED: TOL32, bie.MIXED_FF: {0: TOLFF, 1: TOLFF}}
 TOL_SOLVE = 1e-10
 
 
@@ -78,7 +81,7 @@ def rel2(a, b):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("name", list(GEOMS))
 @pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
-@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
 def test_apply_operator(ctx, name, kind, prec):
     g = GEOMS[name]()
     if kind == bie.STOKES and name == "multitile":
@@ -92,7 +95,7 @@ def test_apply_operator(ctx, name, kind, prec):
     assert rc == bie.OK, ctx.last_error()
     ref = (laplace if kind == 0 else stokes).apply(geo, v)
     err = rel_max(out.cpu().numpy(), ref)
-    tol = TOL64 if prec == bie.FP64 else TOL32[kind]
+    tol = TOL_OP[prec][kind]
     print(f"apply {name} kind={kind} prec={prec}: rel max err {err:.2e}")
     assert err <= tol
 
@@ -101,7 +104,7 @@ def test_apply_operator(ctx, name, kind, prec):
 # solve parity
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("name", list(GEOMS))
-@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
 @pytest.mark.parametrize("form", [0, 1])
 def test_elastance_solve(ctx, name, prec, form):
     g = GEOMS[name]()
@@ -125,7 +128,7 @@ def test_elastance_solve(ctx, name, prec, form):
 
 
 @pytest.mark.parametrize("name", ["ragged4", "multitile"])
-@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
 @pytest.mark.parametrize("form", [0, 1])
 def test_mobility_solve(ctx, name, prec, form):
     g = GEOMS[name]() if name == "ragged4" else multitile(rows=3, cols=3)
@@ -286,7 +289,7 @@ def test_full_size_operator_rows(ctx, wl, kind):
     rows = np.unique(np.concatenate([rows, [0, geo["M"] - 1]]))
     ref = _sampled_rows(geo, kind, v, rows)
     gd = to_dev(g)
-    for prec, tol in ((bie.FP64, TOL64), (bie.MIXED, TOL32[kind])):
+    for prec, tol in ((bie.FP64, TOL64), (bie.MIXED, TOL32[kind]), (bie.MIXED_FF, TOLFF)):
         out = torch.empty(n, dtype=torch.float64, device="cuda")
         assert bie.apply_operator(ctx, gd, kind, prec, torch.from_numpy(v).cuda(), out) == bie.OK
         o = out.cpu().numpy()
@@ -304,7 +307,7 @@ def test_full_size_solve_properties(ctx, wl, kind):
     load = g["q"] if kind == 0 else g["FT"].reshape(-1)
     gd = to_dev(g)
     outs = {}
-    for prec in (bie.MIXED, bie.FP64):
+    for prec in (bie.MIXED_FF, bie.MIXED, bie.FP64):
         out = torch.empty(N if kind == 0 else 3 * N, dtype=torch.float64, device="cuda")
         dens = torch.empty(M * (kind + 1), dtype=torch.float64, device="cuda")
         fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
@@ -313,7 +316,13 @@ def test_full_size_solve_properties(ctx, wl, kind):
         assert rc == bie.OK, (rc, info)
         print(f"{wl} prec={prec}: {info}")
         outs[prec] = (out.cpu().numpy(), dens.cpu().numpy(), info)
-    res, nu, info = outs[bie.MIXED]
+    for prec in (bie.MIXED, bie.MIXED_FF):
+        res, nu, info = outs[prec]
+        _check_full_size(g, geo, kind, res, nu, info, outs[bie.FP64][0])
+
+
+def _check_full_size(g, geo, kind, res, nu, info, res64):
+    M = geo["M"]
     # (1) the density satisfies the oracle's equation at sampled rows: (1/2 I + K + L) nu = L sigma
     rows = np.sort(np.random.default_rng(6).choice(M, 40, replace=False))
     lhs = _sampled_rows(geo, kind, nu, rows)
@@ -332,6 +341,6 @@ def test_full_size_solve_properties(ctx, wl, kind):
         ref = stokes.motion_from_density(g, nu).reshape(-1)
     assert rel2(res, ref) < 1e-12
     # (3) mixed precision and FP64 agree
-    assert rel2(res, outs[bie.FP64][0]) < TOL_SOLVE
+    assert rel2(res, res64) < TOL_SOLVE
     # (4) constraints of the equivalence lemma
     assert info["constraint_residual"] < 1e-10
