@@ -71,16 +71,3 @@ def interior_points(geo: dict) -> dict:
     dmin = np.full(N, np.inf)
     np.minimum.at(dmin, body, d)
     return dict(z0x=geo["xc"].copy(), z0y=geo["yc"].copy(), delta=0.25 * dmin)
-
-
-def winding_number(geo: dict, px: np.ndarray, py: np.ndarray) -> np.ndarray:
-    """Discrete winding number of body i around point (px[i], py[i]) (sum of turning angles)."""
-    out = np.zeros(geo["N"])
-    bs = geo["body_start"]
-    for i in range(geo["N"]):
-        sl = slice(bs[i], bs[i + 1])
-        ang = np.arctan2(geo["y"][sl] - py[i], geo["x"][sl] - px[i])
-        dang = np.diff(np.concatenate([ang, ang[:1]]))
-        dang = (dang + math.pi) % (2 * math.pi) - math.pi
-        out[i] = dang.sum() / (2 * math.pi)
-    return out
