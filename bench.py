@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -56,6 +56,9 @@ def parse():
                          "float-float (mixed_ff) residual")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="served stream: mixed elastance/mobility requests (0 = skip)")
+    ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--kernel", default=None,
                     choices=["laplace_fp32", "laplace_fp64", "laplace_ff", "stokes_fp32", "stokes_fp64",
                              "stokes_ff"],
@@ -139,7 +142,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -210,6 +213,91 @@ def run_reference(args, rank, world):
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def run_serving(args, rank, local):
+    """Served stream: Poisson arrivals of mixed elastance/mobility requests
+    (1..64 bodies of 64/128/256 nodes, ellipses or stars) through bie_server.
+    Phase 1 queues every request at once (saturated solves/s); phase 2 submits
+    at 80% of that rate with exponential gaps and reports latency percentiles
+    (submit to completion, host clock)."""
+    import threading
+
+    import torch
+
+    from paper_1507_05925_gb300 import bie
+
+    rng = np.random.default_rng(3000 + rank)
+    reqs = [synth.random_request(rng) for _ in range(args.serve_requests)]
+    host = []
+    for g in reqs:
+        geom = {k: np.ascontiguousarray(g[k]) for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+        load = np.ascontiguousarray(g["q"] if g["kind"] == 0 else g["FT"].reshape(-1))
+        n = g["body_start"].size - 1
+        host.append((g["kind"], geom, load, np.empty(n if g["kind"] == 0 else 3 * n)))
+    cap = 8 << 30
+    srv = bie.Server(local, workers=args.serve_workers, hbm_cap_bytes=cap)
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+
+    def submit(i):
+        kind, geom, load, out = host[i]
+        t = srv.submit(kind, geom, load, out, opts=opts)
+        if t <= 0:
+            raise RuntimeError(f"request {i} rejected: {t}")
+        return t
+
+    for i in range(min(32, len(host))):  # warm-up
+        srv.wait(submit(i))
+    t0 = time.perf_counter()
+    tickets = [submit(i) for i in range(len(host))]
+    lat_sat = []
+    for t in tickets:
+        rc, _, sec = srv.wait(t)
+        if rc < 0:
+            raise RuntimeError(f"served solve failed: {rc}")
+        lat_sat.append(sec)
+    sat_s = time.perf_counter() - t0
+    sat_rate = len(host) / sat_s
+    rate = 0.8 * sat_rate
+    gaps = np.random.default_rng(4000 + rank).exponential(1.0 / rate, len(host))
+    tickets = [None] * len(host)
+
+    def producer():
+        t_next = time.perf_counter()
+        for i in range(len(host)):
+            t_next += gaps[i]
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = submit(i)
+
+    th = threading.Thread(target=producer)
+    t0 = time.perf_counter()
+    th.start()
+    lat = []
+    for i in range(len(host)):
+        while tickets[i] is None:
+            time.sleep(0.0002)
+        rc, _, sec = srv.wait(tickets[i])
+        lat.append(sec)
+    th.join()
+    poisson_s = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    M = [g["x"].size for g in reqs]
+    return {
+        "requests": len(host), "workers": args.serve_workers, "hbm_cap_bytes": cap,
+        "precision": "mixed_ff", "elastance": int(sum(1 for g in reqs if g["kind"] == 0)),
+        "mobility": int(sum(1 for g in reqs if g["kind"] == 1)), "mean_nodes": float(np.mean(M)),
+        "max_nodes": int(max(M)),
+        "saturated": {"solves_per_s": sat_rate, "seconds": sat_s,
+                      "p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
+                      "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},
+        "poisson_80pct": {"arrival_rate_per_s": rate, "solves_per_s": len(host) / poisson_s,
+                          "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                          "p99_ms": 1e3 * float(np.percentile(lat, 99))},
+        "peak_inflight_bytes": st["peak_inflight_bytes"],
+    }
 
 
 def run_kernel(args, local):
@@ -292,6 +380,9 @@ def main():
             raise RuntimeError(f"solve failed: {rc} {ctx.last_error()} {info}")
         return info
 
+    # clocks are sampled from the warm-up through the timed region (a short
+    # region alone would give nvidia-smi too few samples)
+    cs = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         info = solve(mixed)
     torch.cuda.synchronize()
@@ -316,8 +407,8 @@ def main():
         ms = [e0.elapsed_time(e1) for e0, e1 in evs]
         return ms, infos, prof
 
-    with ClockSampler(local) as cs:
-        ms, infos, prof = timed(mixed, args.steps, True)
+    ms, infos, prof = timed(mixed, args.steps, True)
+    cs.__exit__(None, None, None)
     clocks = cs.summary()
     phi_mixed = phi.clone()
     total_ms = sum(ms)
@@ -412,6 +503,8 @@ def main():
                      "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms},
         "clocks": clocks,
     }
+    if args.serve_requests > 0:
+        out["serving"] = run_serving(args, rank, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample_rate(M, 16)
         out["cpu_baseline"] = {"value": 1.0 / smp["seconds_full_estimate"], "unit": "solves/s",

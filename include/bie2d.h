@@ -180,6 +180,45 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
 int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, const double* in,
                            double* out, void* stream);
 
+/* Device workspace (bytes) that elastance_solve (kind 0) or mobility_solve
+ * (kind 1) needs for N bodies, M nodes and GMRES restart length `restart`
+ * (0 = default): the Krylov basis, the staged geometry, the partial sums and
+ * the staging of host inputs.  Requires a current CUDA device. */
+size_t bie_workspace_bytes(int kind, int n_bodies, int n_nodes, int restart);
+
+/* ---- Serving: continuous batching of solve requests ----
+ * A server owns `workers` host threads, each with its own context and its own
+ * non-blocking CUDA stream, so that the solves of concurrent requests overlap
+ * on the device.  Requests wait in a queue and are admitted when a worker is
+ * free and their workspace (bie_workspace_bytes) fits under hbm_cap_bytes
+ * together with the requests in flight (0 = no cap); a request may pass an
+ * earlier one that does not fit yet, but not more than 64 times.  Results do
+ * not depend on what else is in flight: every kernel reduces in a fixed order. */
+typedef struct bie_server bie_server;
+
+typedef struct {
+  int32_t kind;          /* BIE_KIND_LAPLACE -> elastance_solve, BIE_KIND_STOKES -> mobility_solve */
+  bie_geometry geom;     /* arrays (host or device) must stay valid until the request completes */
+  const double* load;    /* q [N] or FT [3N] */
+  double* out;           /* phi [N] or UW [3N] */
+  double* density;       /* nullable */
+  bie_opts opts;         /* all zero = defaults */
+} bie_request;
+
+int bie_server_create(bie_server** srv, int device, int workers, size_t hbm_cap_bytes);
+/* Queue a request (copied; its arrays are not).  Returns BIE_ERR_NOMEM at once
+ * if the request alone exceeds the cap, BIE_ERR_INVALID for a malformed one. */
+int bie_server_submit(bie_server* srv, const bie_request* req, int64_t* ticket);
+/* Block until the request completes; returns its solve status and fills info
+ * (nullable) and seconds (nullable) = time from submit to completion.  Each
+ * ticket can be waited for once. */
+int bie_server_wait(bie_server* srv, int64_t ticket, bie_info* info, double* seconds);
+/* Completed requests, workspace bytes of the requests now in flight, and the
+ * largest such sum seen. */
+int bie_server_stats(bie_server* srv, int64_t* completed, size_t* inflight_bytes, size_t* peak_inflight_bytes);
+/* Finish the queued requests, stop the workers and free everything. */
+void bie_server_destroy(bie_server* srv);
+
 /* Kernel timing of the pair sums (the O(M^2) hot loop), for measurement.
  * counters[precision][kind] (precision 0 FP64, 1 FP32, 2 float-float): launches that did work and their summed device
  * time, taken with CUDA events recorded on the call's stream around each

@@ -46,6 +46,11 @@ class BieInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BieRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("geom", BieGeometry), ("load", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("density", ctypes.c_void_p), ("opts", BieOpts)]
+
+
 class BieProfileCounters(ctypes.Structure):
     _fields_ = [("launches", (ctypes.c_int64 * 2) * 3), ("ms", (ctypes.c_double * 2) * 3),
                 ("pairs", (ctypes.c_double * 2) * 3), ("kernel_launches", ctypes.c_int64)]
@@ -92,6 +97,19 @@ def load():
     lib.apply_operator.restype = i32
     lib.apply_operator_noalloc.argtypes = [ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator_noalloc.restype = i32
+    lib.bie_workspace_bytes.argtypes = [i32, i32, i32, i32]
+    lib.bie_workspace_bytes.restype = ctypes.c_size_t
+    lib.bie_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_size_t]
+    lib.bie_server_create.restype = i32
+    lib.bie_server_submit.argtypes = [vp, ctypes.POINTER(BieRequest), ctypes.POINTER(ctypes.c_int64)]
+    lib.bie_server_submit.restype = i32
+    lib.bie_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(BieInfo), ctypes.POINTER(ctypes.c_double)]
+    lib.bie_server_wait.restype = i32
+    lib.bie_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]
+    lib.bie_server_stats.restype = i32
+    lib.bie_server_destroy.argtypes = [vp]
+    lib.bie_server_destroy.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
     _ = dbl
@@ -104,7 +122,7 @@ def declared_symbols() -> list[str]:
     with open(os.path.join(_build.INCLUDE, "bie2d.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return re.findall(r"^\s*(?:int|void|const char\*)\s+\**(\w+)\s*\(", text, flags=re.M)
+    return re.findall(r"^\s*(?:int|void|size_t|const char\*)\s+\**(\w+)\s*\(", text, flags=re.M)
 
 
 def _ptr(a):
@@ -232,3 +250,57 @@ def apply_operator_noalloc(geom, kind: int, precision: int, inp, out, stream=Non
     rc = lib.apply_operator_noalloc(ctypes.byref(g), kind, precision, _ptr(inp), _ptr(out), _stream_ptr(stream))
     del keep
     return rc
+
+
+def workspace_bytes(kind: int, n_bodies: int, n_nodes: int, restart: int = 0) -> int:
+    """bie_workspace_bytes of include/bie2d.h."""
+    return int(load().bie_workspace_bytes(kind, n_bodies, n_nodes, restart))
+
+
+class Server:
+    """bie_server: continuous batching of solve requests on one GPU."""
+
+    def __init__(self, device: int = 0, workers: int = 4, hbm_cap_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.bie_server_create(ctypes.byref(h), device, workers, hbm_cap_bytes)
+        if rc != OK:
+            raise RuntimeError(f"bie_server_create failed with status {rc}")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, kind: int, geom, load, out, density=None, opts: BieOpts | None = None) -> int:
+        """Queue a request; returns its ticket (raises on a rejected request)."""
+        g, keep = make_geometry(geom)
+        req = BieRequest(kind, g, _ptr(load), _ptr(out), _ptr(density), opts if opts is not None else BieOpts())
+        t = ctypes.c_int64()
+        rc = self.lib.bie_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if rc != OK:
+            return rc if rc < 0 else OK
+        self._keep[t.value] = (keep, load, out, density)
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        """Block until the request completes; returns (status, info dict, seconds)."""
+        info = BieInfo()
+        sec = ctypes.c_double()
+        rc = self.lib.bie_server_wait(self.handle, ticket, ctypes.byref(info), ctypes.byref(sec))
+        self._keep.pop(ticket, None)
+        return rc, info.as_dict(), sec.value
+
+    def stats(self) -> dict:
+        c, i, p = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t()
+        self.lib.bie_server_stats(self.handle, ctypes.byref(c), ctypes.byref(i), ctypes.byref(p))
+        return dict(completed=c.value, inflight_bytes=i.value, peak_inflight_bytes=p.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.bie_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

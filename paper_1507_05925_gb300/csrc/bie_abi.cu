@@ -195,17 +195,19 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   }
 }
 
-int ensure_ws(bie_ctx* ctx, size_t need) {
+// Stream-ordered (cudaMallocAsync) so that growing one context's workspace
+// never synchronises the device under other contexts' work.
+int ensure_ws(bie_ctx* ctx, size_t need, cudaStream_t s) {
   if (need <= ctx->ws_size) return BIE_OK;
   if (ctx->cap && need > ctx->cap)
     return fail(ctx, BIE_ERR_NOMEM, "workspace of " + std::to_string(need) + " bytes exceeds the cap of " +
                                         std::to_string(ctx->cap));
   if (ctx->ws) {
-    cudaFree(ctx->ws);
+    cudaFreeAsync(ctx->ws, s);
     ctx->ws = nullptr;
     ctx->ws_size = 0;
   }
-  CK(cudaMalloc(&ctx->ws, need));
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&ctx->ws), need, s));
   ctx->ws_size = need;
   return BIE_OK;
 }
@@ -476,7 +478,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   Work w;
   Arena sz{nullptr};
   carve(sz, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
-  if ((rc = ensure_ws(ctx, sz.off))) return rc;
+  if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
   Arena ar{ctx->ws};
   carve(ar, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;
@@ -611,6 +613,29 @@ int bie_create(bie_ctx** out, int device, size_t cap) {
   return BIE_OK;
 }
 
+}  // extern "C"
+
+namespace bie {
+void release_workspace(bie_ctx* ctx, cudaStream_t s) {
+  if (ctx && ctx->ws) {
+    cudaFreeAsync(ctx->ws, s);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+  }
+}
+}  // namespace bie
+
+extern "C" {
+
+size_t bie_workspace_bytes(int kind, int n_bodies, int n_nodes, int restart) {
+  if (n_bodies < 1 || n_nodes < 1 || (kind != 0 && kind != 1)) return 0;
+  Work w;
+  Arena sz{nullptr};
+  const int m = restart > 0 ? std::min(restart, 200) : 50;
+  carve(sz, w, n_bodies, n_nodes, kind, m, true, true, true, true, false);
+  return sz.off;
+}
+
 int bie_profile(bie_ctx* ctx, int enable, bie_profile_counters* out) {
   if (!ctx) return BIE_ERR_INVALID;
   DeviceGuard dg(ctx->device);
@@ -630,7 +655,10 @@ void bie_destroy(bie_ctx* c) {
   DeviceGuard dg(c->device);
   resolve_timings(c, true);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
-  if (c->ws) cudaFree(c->ws);
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+  }
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;
@@ -663,7 +691,7 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
   Work w;
   Arena sz{nullptr};
   carve(sz, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
-  if ((rc = ensure_ws(ctx, sz.off))) return rc;
+  if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
   Arena ar{ctx->ws};
   carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;

@@ -65,6 +65,13 @@ struct KState {
   int pad[2];         // [0] = 1: set tol_abs from the next starting residual
 };
 
+}  // namespace bie
+struct bie_ctx;
+namespace bie {
+// Return a context's workspace to the stream-ordered pool (used by the server
+// between requests, so that memory follows the requests in flight).
+void release_workspace(bie_ctx* ctx, cudaStream_t s);
+
 // Count of kernels launched by this library (all contexts), for bie_profile.
 void note_launches(int k);
 long long launches_so_far();

@@ -28,7 +28,36 @@ __device__ bool block_dots(const double* __restrict__ V, long long ld, const dou
   __shared__ int is_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * kBV;
-  for (int i = 0; i < jc; ++i) {
+  // four basis vectors per round: four independent load streams per thread
+  int i = 0;
+  for (; i + 4 <= jc; i += 4) {
+    const double* __restrict__ V0 = V + (long long)i * ld;
+    const double* __restrict__ V1 = V0 + ld;
+    const double* __restrict__ V2 = V1 + ld;
+    const double* __restrict__ V3 = V2 + ld;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+      const double wk = w[k];
+      a0 += V0[k] * wk;
+      a1 += V1[k] * wk;
+      a2 += V2[k] * wk;
+      a3 += V3[k] * wk;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o);
+      a2 += __shfl_down_sync(0xffffffffu, a2, o);
+      a3 += __shfl_down_sync(0xffffffffu, a3, o);
+    }
+    if (lane == 0) {
+      sh[wid][i] = a0;
+      sh[wid][i + 1] = a1;
+      sh[wid][i + 2] = a2;
+      sh[wid][i + 3] = a3;
+    }
+  }
+  for (; i < jc; ++i) {
     const double* __restrict__ Vi = V + (long long)i * ld;
     double acc = 0.0;
     for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) acc += Vi[k] * w[k];
@@ -58,6 +87,21 @@ __device__ bool block_dots(const double* __restrict__ V, long long ld, const dou
   return true;
 }
 
+// sum_i c[i] V_i[k] for i < jc, four independent partial sums
+__device__ __forceinline__ double combine(const double* __restrict__ V, long long ld, long long k,
+                                          const double* c, int jc) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = 0;
+  for (; i + 4 <= jc; i += 4) {
+    s0 += c[i] * V[(long long)i * ld + k];
+    s1 += c[i + 1] * V[(long long)(i + 1) * ld + k];
+    s2 += c[i + 2] * V[(long long)(i + 2) * ld + k];
+    s3 += c[i + 3] * V[(long long)(i + 3) * ld + k];
+  }
+  for (; i < jc; ++i) s0 += c[i] * V[(long long)i * ld + k];
+  return (s0 + s1) + (s2 + s3);
+}
+
 __global__ void __launch_bounds__(kBV) k_cgs_dots(const double* __restrict__ V, long long ld, VecRef wr,
                                                   long long n, KState* st, double* part, double* h1) {
   if (st->stop) return;
@@ -75,9 +119,7 @@ __global__ void __launch_bounds__(kBV) k_cgs_update_dots(const double* __restric
   double* __restrict__ w = wr.ptr();
   const long long stride = (long long)gridDim.x * kBV;
   for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-    double acc = w[k];
-    for (int i = 0; i < jc; ++i) acc -= hs[i] * V[(long long)i * ld + k];
-    w[k] = acc;
+    w[k] = w[k] - combine(V, ld, k, hs, jc);
   }
   block_dots(V, ld, w, n, jc, part, h2, &st->counter);
 }
@@ -101,8 +143,7 @@ __global__ void __launch_bounds__(kBV) k_cgs_update_norm(const double* __restric
   const long long stride = (long long)gridDim.x * kBV;
   double nrm = 0.0;
   for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-    double acc = w[k];
-    for (int i = 0; i < jc; ++i) acc -= hs[i] * V[(long long)i * ld + k];
+    const double acc = w[k] - combine(V, ld, k, hs, jc);
     w[k] = acc;
     nrm += acc * acc;
   }
@@ -173,9 +214,7 @@ __global__ void k_update_x(const double* __restrict__ V, long long ld, long long
   __syncthreads();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    double acc = x[k];
-    for (int i = 0; i < j; ++i) acc += ys[i] * V[(long long)i * ld + k];
-    x[k] = acc;
+    x[k] += combine(V, ld, k, ys, j);
   }
 }
 

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
 }
 
 // ------------------------------------------------------------------ FP32 ----
-constexpr int kB32 = 128, kT32 = 4, kTile32 = 256;
+constexpr int kB32 = 64, kT32 = 4, kTile32 = 256;
 
 // Near tiles (sources whose bounding box is close to the target block's):
 // exact differences from the hi/lo coordinates, reloaded here so that they
@@ -206,7 +206,7 @@ __device__ __forceinline__ float4 body_range_box(const float4* __restrict__ bbox
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kB32, KIND == 0 ? 8 : 6) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
+__global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -240,13 +240,15 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 8 : 6) k_pair32(Geo g, VecRe
     dax[k] = 0.0;
     day[k] = 0.0;
   }
-  for (int jt = j0; jt < j1; jt += kTile32) {
-    const int nt = min(kTile32, j1 - jt);
+  // source tiles never cross a body boundary, so a tile's box is its body's
+  for (int jt = j0; jt < j1;) {
+    const int sb = g.body_of[jt];
+    const int nt = min(kTile32, min(j1, g.body_start[sb + 1]) - jt);
     // far when the boxes are at least both half-diagonals apart (block-uniform)
-    const float4 sb = body_range_box(g.bbox, g.body_of[jt], g.body_of[jt + nt - 1]);
-    const float gx = fmaxf(0.f, fmaxf(sb.x - tb.z, tb.x - sb.z));
-    const float gy = fmaxf(0.f, fmaxf(sb.y - tb.w, tb.y - sb.w));
-    const float es = 0.5f * sqrtf((sb.z - sb.x) * (sb.z - sb.x) + (sb.w - sb.y) * (sb.w - sb.y));
+    const float4 sbx = g.bbox[sb];
+    const float gx = fmaxf(0.f, fmaxf(sbx.x - tb.z, tb.x - sbx.z));
+    const float gy = fmaxf(0.f, fmaxf(sbx.y - tb.w, tb.y - sbx.w));
+    const float es = 0.5f * sqrtf((sbx.z - sbx.x) * (sbx.z - sbx.x) + (sbx.w - sbx.y) * (sbx.w - sbx.y));
     const float gap2 = gx * gx + gy * gy;
     const float need = fmaxf(et, es);
     const bool far = gap2 > 0.f && gap2 >= need * need;
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 8 : 6) k_pair32(Geo g, VecRe
       dax[k] += (double)ax[k];
       day[k] += (double)ay[k];
     }
+    jt += nt;
   }
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {

@@ -1,0 +1,226 @@
+// Continuous-batching server for elastance and mobility solves.
+//
+// Worker threads each own a context and a non-blocking CUDA stream; a request
+// runs on one worker from start to finish, so the solves of different requests
+// overlap on the device.  Admission is by device-memory footprint: a request
+// starts only when a worker is free and its workspace fits under the cap
+// together with the requests in flight.  The queue is first-in first-out,
+// except that a request that fits may pass the head of the queue when the
+// head does not fit yet, at most kMaxPass times per head request.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bie2d.h"
+#include "bie_internal.cuh"
+
+namespace {
+
+constexpr int kMaxPass = 64;
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  bie_request req;
+  int64_t ticket = 0;
+  size_t need = 0;
+  Clock::time_point t_submit;
+  double seconds = 0.0;
+  int status = BIE_OK;
+  bie_info info{};
+  bool done = false;
+};
+
+}  // namespace
+
+struct bie_server {
+  int device = 0;
+  size_t cap = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> queue;
+  std::unordered_map<int64_t, Job*> jobs;
+  size_t inflight = 0, peak = 0;
+  int64_t next_ticket = 1, completed = 0;
+  int head_passed = 0;
+  bool stopping = false;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Pick the next job a free worker may run (mu held); nullptr if none fits.
+Job* pick(bie_server* s) {
+  if (s->queue.empty()) return nullptr;
+  auto fits = [&](const Job* j) { return s->cap == 0 || s->inflight == 0 || s->inflight + j->need <= s->cap; };
+  if (fits(s->queue.front())) {
+    Job* j = s->queue.front();
+    s->queue.pop_front();
+    s->head_passed = 0;
+    return j;
+  }
+  if (s->head_passed >= kMaxPass) return nullptr;  // the head waits for memory; nobody passes it now
+  for (auto it = s->queue.begin() + 1; it != s->queue.end(); ++it) {
+    if (fits(*it)) {
+      Job* j = *it;
+      s->queue.erase(it);
+      s->head_passed += 1;
+      return j;
+    }
+  }
+  return nullptr;
+}
+
+void worker_main(bie_server* s) {
+  cudaSetDevice(s->device);
+  bie_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  const bool ok = bie_create(&ctx, s->device, 0) == BIE_OK &&
+                  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (;;) {
+    Job* j = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return (s->stopping && s->queue.empty()) || (j = pick(s)) != nullptr; });
+      if (!j) break;
+      s->inflight += j->need;
+      if (s->inflight > s->peak) s->peak = s->inflight;
+    }
+    int status = BIE_ERR_CUDA;
+    bie_info info{};
+    if (ok) {
+      const bie_opts* opts = &j->req.opts;
+      if (j->req.kind == BIE_KIND_LAPLACE)
+        status = elastance_solve(ctx, &j->req.geom, j->req.load, j->req.out, j->req.density, opts, &info, stream);
+      else
+        status = mobility_solve(ctx, &j->req.geom, j->req.load, j->req.out, j->req.density, opts, &info, stream);
+      // memory follows the requests in flight: hand the workspace back to the pool
+      bie::release_workspace(ctx, stream);
+      cudaStreamSynchronize(stream);
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->inflight -= j->need;
+      j->status = status;
+      j->info = info;
+      j->seconds = std::chrono::duration<double>(Clock::now() - j->t_submit).count();
+      j->done = true;
+      s->completed += 1;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+  if (stream) cudaStreamDestroy(stream);
+  if (ctx) bie_destroy(ctx);
+}
+
+bool is_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bie_server_create(bie_server** out, int device, int workers, size_t hbm_cap_bytes) {
+  if (!out || workers < 1 || workers > 256) return BIE_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  bie_server* s = new bie_server();
+  s->device = device;
+  s->cap = hbm_cap_bytes;
+  for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s);
+  *out = s;
+  return BIE_OK;
+}
+
+int bie_server_submit(bie_server* s, const bie_request* req, int64_t* ticket) {
+  if (!s || !req || !ticket) return BIE_ERR_INVALID;
+  const bie_geometry& g = req->geom;
+  if ((req->kind != BIE_KIND_LAPLACE && req->kind != BIE_KIND_STOKES) || g.n_bodies < 1 || !g.body_start ||
+      !req->load || !req->out)
+    return BIE_ERR_INVALID;
+  // total node count from body_start (host or device)
+  int M = 0;
+  const int32_t* last = g.body_start + g.n_bodies;
+  if (is_device(g.body_start)) {
+    cudaSetDevice(s->device);
+    if (cudaMemcpy(&M, last, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BIE_ERR_CUDA;
+  } else {
+    M = *last;
+  }
+  if (M < 8) return BIE_ERR_INVALID;
+  cudaSetDevice(s->device);
+  const size_t need = bie_workspace_bytes(req->kind, g.n_bodies, M, req->opts.restart);
+  if (s->cap && need > s->cap) return BIE_ERR_NOMEM;
+  Job* j = new Job();
+  j->req = *req;
+  j->need = need;
+  j->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) {
+      delete j;
+      return BIE_ERR_INVALID;
+    }
+    j->ticket = s->next_ticket++;
+    s->jobs[j->ticket] = j;
+    s->queue.push_back(j);
+    *ticket = j->ticket;
+  }
+  s->cv_work.notify_one();
+  return BIE_OK;
+}
+
+int bie_server_wait(bie_server* s, int64_t ticket, bie_info* info, double* seconds) {
+  if (!s) return BIE_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return BIE_ERR_INVALID;
+  Job* j = it->second;
+  s->cv_done.wait(lk, [&] { return j->done; });
+  const int status = j->status;
+  if (info) *info = j->info;
+  if (seconds) *seconds = j->seconds;
+  s->jobs.erase(it);
+  delete j;
+  return status;
+}
+
+int bie_server_stats(bie_server* s, int64_t* completed, size_t* inflight, size_t* peak) {
+  if (!s) return BIE_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (completed) *completed = s->completed;
+  if (inflight) *inflight = s->inflight;
+  if (peak) *peak = s->peak;
+  return BIE_OK;
+}
+
+void bie_server_destroy(bie_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& kv : s->jobs) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

@@ -19,7 +19,8 @@ def lib():
 def test_exports_every_declared_symbol(lib):
     names = bie.declared_symbols()
     assert set(names) >= {"bie_create", "bie_destroy", "bie_last_error", "elastance_solve",
-                          "mobility_solve", "apply_operator", "bie_profile"}
+                          "mobility_solve", "apply_operator", "bie_profile", "bie_server_create",
+                          "bie_server_submit", "bie_server_wait", "bie_server_destroy", "bie_workspace_bytes"}
     for n in names:
         assert hasattr(lib, n), n
 
@@ -42,7 +43,7 @@ def test_struct_layout_matches_c_compiler(tmp_path):
     # sizes and field offsets as the C compiler lays them out from the header
     checks = []
     structs = (("bie_geometry", bie.BieGeometry), ("bie_opts", bie.BieOpts), ("bie_info", bie.BieInfo),
-               ("bie_profile_counters", bie.BieProfileCounters))
+               ("bie_profile_counters", bie.BieProfileCounters), ("bie_request", bie.BieRequest))
     for cname, cls in structs:
         checks.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
