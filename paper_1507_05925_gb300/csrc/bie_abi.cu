@@ -4,6 +4,7 @@
 // this library; the host only orders launches and reads the convergence state.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -48,6 +49,13 @@ struct bie_ctx {
   bie_profile_counters counters{};
   std::vector<cudaEvent_t> pool;
   std::vector<Timing> pending;
+  // CUDA graphs of one GMRES iteration, keyed by everything their kernels read
+  struct IterGraph {
+    long long key[10];
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<IterGraph> graphs;
 };
 
 namespace {
@@ -207,6 +215,8 @@ int ensure_ws(bie_ctx* ctx, size_t need, cudaStream_t s) {
     ctx->ws = nullptr;
     ctx->ws_size = 0;
   }
+  for (auto& gi : ctx->graphs) cudaGraphExecDestroy(gi.exec);  // their pointers are stale
+  ctx->graphs.clear();
   CK(cudaMallocAsync(reinterpret_cast<void**>(&ctx->ws), need, s));
   ctx->ws_size = need;
   return BIE_OK;
@@ -368,19 +378,78 @@ int read_state(bie_ctx* ctx, const Work& w, cudaStream_t s) {
 // Each cycle minimises over x + span(V) with V_0 = r/||r||, so gmres_update
 // adds V y into x and a restart only needs the explicit residual.  With
 // verify, convergence is confirmed by an explicit residual of the FP64 operator.
-int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
+// One Arnoldi iteration: w = A v_j, CGS2 against V_0..V_j, Givens, v_{j+1}.
+// Every kernel reads j from the device state, so the same launches (or the
+// same captured graph) serve every iteration.
+int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   const long long n = w.n, ld = w.ld;
   const VecRef vj{w.V, ld, &w.st->j, 0}, vj1{w.V, ld, &w.st->j, 1};
+  CK(op.apply(vj, vj1, &w.st->stop, s, false));
+  CK(cgs_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.grid, s));
+  CK(cgs_update_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.grid, s));
+  CK(cgs_update_norm(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.H, w.cs, w.sn, w.gv, w.grid, s));
+  CK(normalize_next(vj, n, w.st, s));
+  return BIE_OK;
+}
+
+bool capturable(cudaStream_t s) {
+  return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
+// The iteration as a CUDA graph (built once per workspace layout and operator;
+// not while pair-sum timing is on, whose events are per launch).  nullptr if
+// the stream cannot be captured.
+bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
+  if (ctx->prof || !capturable(s)) return nullptr;
+  const PairPlan& p = op.prec == 0 ? w.plan64 : (op.prec == 1 ? w.plan32 : w.planff);
+  long long alpha_bits;
+  memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
+  const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
+                             w.kind, w.m, op.prec, alpha_bits, p.S * 1000003LL + p.chunk, w.grid};
+  for (auto& gi : ctx->graphs)
+    if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
+  const long long before = launches_so_far();
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const int rc = launch_iteration(ctx, w, op, s);
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  const long long kernels = launches_so_far() - before;
+  note_launches((int)-kernels);  // captured, not launched
+  cudaGraphExec_t exec = nullptr;
+  if (rc != BIE_OK || e != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return nullptr;
+  }
+  cudaGraphDestroy(graph);
+  if (ctx->graphs.size() >= 4) {
+    cudaGraphExecDestroy(ctx->graphs.front().exec);
+    ctx->graphs.erase(ctx->graphs.begin());
+  }
+  bie_ctx::IterGraph gi;
+  memcpy(gi.key, key, sizeof(key));
+  gi.exec = exec;
+  gi.kernels = kernels;
+  ctx->graphs.push_back(gi);
+  return &ctx->graphs.back();
+}
+
+int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   int chunk = 4, rc;
   int iters_before = ctx->h_state->iters;
+  bie_ctx::IterGraph* graph = iteration_graph(ctx, w, op, s);
   for (;;) {
     const size_t mark = ctx->pending.size();
     for (int it = 0; it < chunk; ++it) {
-      CK(op.apply(vj, vj1, &w.st->stop, s, false));
-      CK(cgs_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.grid, s));
-      CK(cgs_update_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.grid, s));
-      CK(cgs_update_norm(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.H, w.cs, w.sn, w.gv, w.grid, s));
-      CK(normalize_next(vj, n, w.st, s));
+      if (graph) {
+        CK(cudaGraphLaunch(graph->exec, s));
+        note_launches((int)graph->kernels);
+      } else if ((rc = launch_iteration(ctx, w, op, s))) {
+        return rc;
+      }
     }
     if ((rc = read_state(ctx, w, s))) return rc;
     const int done = ctx->h_state->iters - iters_before;
@@ -621,6 +690,8 @@ void release_workspace(bie_ctx* ctx, cudaStream_t s) {
     cudaFreeAsync(ctx->ws, s);
     ctx->ws = nullptr;
     ctx->ws_size = 0;
+    for (auto& gi : ctx->graphs) cudaGraphExecDestroy(gi.exec);
+    ctx->graphs.clear();
   }
 }
 }  // namespace bie
@@ -655,6 +726,7 @@ void bie_destroy(bie_ctx* c) {
   DeviceGuard dg(c->device);
   resolve_timings(c, true);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  for (auto& gi : c->graphs) cudaGraphExecDestroy(gi.exec);
   if (c->ws) {
     cudaDeviceSynchronize();
     cudaFree(c->ws);
