@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--fmm-order", type=int, default=36)
     ap.add_argument("--kernel", default=None,
-                    choices=["laplace_fp32", "laplace_fp64", "laplace_ff", "stokes_fp32", "stokes_fp64",
-                             "stokes_ff"],
+                    choices=["laplace_fp32", "laplace_fp64", "laplace_ff", "laplace_fmm", "stokes_fp32",
+                             "stokes_fp64", "stokes_ff", "stokes_fmm", "stokes_fmm_large", "stokes_fp32_large"],
                     help="time one operator application (pair sum + epilogue) instead of solves; "
                          "Laplace on the 100-star workload, Stokes on the 400-ellipse workload")
     return ap.parse_args()
@@ -307,10 +308,15 @@ def run_kernel(args, local):
     from paper_1507_05925_gb300 import bie, build
 
     build.build()
-    kind_name, prec_name = args.kernel.split("_")
+    parts = args.kernel.split("_")
+    kind_name, prec_name = parts[0], parts[1]
     kind = bie.LAPLACE if kind_name == "laplace" else bie.STOKES
-    prec = {"fp32": bie.MIXED, "fp64": bie.FP64, "ff": bie.MIXED_FF}[prec_name]
-    g = synth.star_grid(seed=1000) if kind == bie.LAPLACE else synth.ellipse_suspension(seed=2000)
+    fmm = prec_name == "fmm"
+    prec = {"fp32": bie.MIXED, "fp64": bie.FP64, "ff": bie.MIXED_FF, "fmm": bie.FP64}[prec_name]
+    if parts[-1] == "large":
+        g = synth.ellipse_lattice(seed=5000)
+    else:
+        g = synth.star_grid(seed=1000) if kind == bie.LAPLACE else synth.ellipse_suspension(seed=2000)
     dev = torch.device("cuda", local)
     gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
     gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
@@ -318,14 +324,36 @@ def run_kernel(args, local):
     v = torch.randn(n, dtype=torch.float64, device=dev)
     out = torch.empty_like(v)
     ctx = bie.Context(local)
+
+    def apply():
+        if fmm:
+            rc = bie.apply_operator_fmm(ctx, gd, kind, args.fmm_order, v, out)
+        else:
+            rc = bie.apply_operator(ctx, gd, kind, prec, v, out)
+        assert rc == bie.OK, ctx.last_error()
+
     for _ in range(args.warmup):
-        assert bie.apply_operator(ctx, gd, kind, prec, v, out) == bie.OK
+        apply()
     torch.cuda.synchronize()
+    if fmm:  # whole operator application (tree build included), CUDA events
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            apply()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        M = g["x"].size
+        print(json.dumps({"kernel": args.kernel, "order": args.fmm_order, "M": M, "ms_per_apply": ms,
+                          "equivalent_pairs_per_s": M * (M - 1) / (ms / 1e3)}))
+        ctx.close()
+        return
     ctx.profile(True)
     for _ in range(args.steps):
-        assert bie.apply_operator(ctx, gd, kind, prec, v, out) == bie.OK
+        apply()
     torch.cuda.synchronize()
-    prof = ctx.profile(False)[args.kernel]
+    key = kind_name + "_" + prec_name
+    prof = ctx.profile(False)[key]
     ms = prof["ms"] / max(prof["launches"], 1)
     flops = FLOPS_PER_PAIR[kind_name] * prof["pairs"] / max(prof["launches"], 1)
     print(json.dumps({"kernel": args.kernel, "M": g["x"].size, "launches": prof["launches"],

@@ -120,6 +120,10 @@ typedef struct {
                             right-hand side -(1/2 I + K) sigma */
   int32_t max_refine;    /* mixed: cap on refinement steps; default 8 when <= 0 */
   double inner_tol;      /* mixed: relative tolerance of each FP32 inner solve; default 1e-6 */
+  int32_t fmm_order;     /* 0: direct pair sums; p in 2..64: the pair sums are evaluated by the
+                            quadtree FMM (FP64 expansions) with order p for residuals and FP64
+                            GMRES, and order ceil(p/2) for the inner solves of the refinement */
+  int32_t reserved;
 } bie_opts;
 
 typedef struct {
@@ -179,6 +183,14 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
 #define BIE_NOALLOC_MAX_BODIES 2048
 int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, const double* in,
                            double* out, void* stream);
+
+/* apply_operator with the pair sums evaluated by the quadtree fast multipole
+ * method in complex variables (Laplace: Re(nu F) with F the Cauchy sum of
+ * q = w mu; Stokes: four Cauchy sums of q, conj(q) and q conj(z)), expansion
+ * order p = order (2..64), FP64 expansions, direct near field.  Relative error
+ * roughly 0.35^order of the operator's size. */
+int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, const double* in,
+                       double* out, void* stream);
 
 /* Device workspace (bytes) that elastance_solve (kind 0) or mobility_solve
  * (kind 1) needs for N bodies, M nodes and GMRES restart length `restart`

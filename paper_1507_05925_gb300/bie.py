@@ -32,7 +32,7 @@ class BieOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("formulation", ctypes.c_int32), ("max_refine", ctypes.c_int32),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("fmm_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BieInfo(ctypes.Structure):
@@ -95,6 +95,8 @@ def load():
         f.restype = i32
     lib.apply_operator.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator.restype = i32
+    lib.apply_operator_fmm.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
+    lib.apply_operator_fmm.restype = i32
     lib.apply_operator_noalloc.argtypes = [ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator_noalloc.restype = i32
     lib.bie_workspace_bytes.argtypes = [i32, i32, i32, i32]
@@ -174,8 +176,8 @@ def make_geometry(geom) -> tuple[BieGeometry, list]:
 
 
 def make_opts(tol=1e-12, max_iter=500, restart=50, precision=FP64, formulation=0,
-              max_refine=8, inner_tol=1e-6) -> BieOpts:
-    return BieOpts(tol, max_iter, restart, precision, formulation, max_refine, inner_tol)
+              max_refine=8, inner_tol=1e-6, fmm_order=0) -> BieOpts:
+    return BieOpts(tol, max_iter, restart, precision, formulation, max_refine, inner_tol, fmm_order, 0)
 
 
 class Context:
@@ -304,3 +306,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def apply_operator_fmm(ctx: Context, geom, kind: int, order: int, inp, out, stream=None) -> int:
+    """apply_operator_fmm of include/bie2d.h: the operator with FMM pair sums of the given order."""
+    g, keep = make_geometry(geom)
+    rc = ctx.lib.apply_operator_fmm(ctx.handle, ctypes.byref(g), kind, order, _ptr(inp), _ptr(out),
+                                    _stream_ptr(stream))
+    del keep
+    return rc

@@ -56,6 +56,7 @@ struct bie_ctx {
     long long kernels;
   };
   std::vector<IterGraph> graphs;
+  bie::FmmState* fmm = nullptr;  // quadtree of the last FMM call
 };
 
 namespace {
@@ -349,12 +350,20 @@ cudaError_t timed_pair_sum(bie_ctx* ctx, const Geo& g, int kind, int prec, const
 
 // The operator (1/2 I + K + L) on sqrt(w)-scaled vectors, in FP64 or FP32 pair sums.
 // alpha = 0: the paper's completion; alpha > 0: weighted per body (inner solves).
+// fmm_p > 0: the pair sums by the FMM of that order instead of direct sums.
 struct Op {
   bie_ctx* ctx;
   const Work* w;
   int prec;
   double alpha = 0.0;
+  int fmm_p = 0;
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
+    if (fmm_p > 0) {
+      const PairPlan one{1, w->g.M};
+      cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s);
+      if (e != cudaSuccess) return e;
+      return epilogue(w->g, w->kind, one, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
+    }
     const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
     cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
     if (e != cudaSuccess) return e;
@@ -405,7 +414,8 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   long long alpha_bits;
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
   const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
-                             w.kind, w.m, op.prec, alpha_bits, p.S * 1000003LL + p.chunk, w.grid};
+                             w.kind, w.m, op.prec * 1000 + op.fmm_p, alpha_bits, p.S * 1000003LL + p.chunk,
+                             w.grid};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
   const long long before = launches_so_far();
@@ -520,6 +530,8 @@ void fill_opts(const bie_opts* o, bie_opts& r) {
   r.formulation = 0;
   r.max_refine = 8;
   r.inner_tol = 1e-6;
+  r.fmm_order = 0;
+  r.reserved = 0;
   if (!o) return;
   if (o->tol > 0) r.tol = o->tol;
   if (o->max_iter > 0) r.max_iter = o->max_iter;
@@ -528,6 +540,7 @@ void fill_opts(const bie_opts* o, bie_opts& r) {
   r.formulation = o->formulation;
   if (o->max_refine > 0) r.max_refine = o->max_refine;
   if (o->inner_tol > 0) r.inner_tol = o->inner_tol;
+  r.fmm_order = o->fmm_order;
 }
 
 int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double* load, double* out,
@@ -541,6 +554,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED && o.precision != BIE_PREC_MIXED_FF)
     return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64, BIE_PREC_MIXED or BIE_PREC_MIXED_FF");
   if (o.formulation != 0 && o.formulation != 1) return fail(ctx, BIE_ERR_INVALID, "formulation must be 0 or 1");
+  if (o.fmm_order != 0 && (o.fmm_order < 2 || o.fmm_order > 64))
+    return fail(ctx, BIE_ERR_INVALID, "fmm_order must be 0 or in 2..64");
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
   const int nload = kind == 0 ? N : 3 * N;
@@ -554,6 +569,11 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const double* dload;
   if ((rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
   if ((rc = check_inside(ctx, w, s))) return rc;
+  const int p_res = o.fmm_order, p_in = (o.fmm_order + 1) / 2;
+  if (o.fmm_order > 0) {
+    const int orders[2] = {p_res, std::max(2, p_in)};
+    if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err))) return rc;
+  }
 
   const long long n = w.n;
   // right-hand side (scaled by sqrt(w))
@@ -566,9 +586,11 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   }
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
-  const Op op64{ctx, &w, 0}, op32{ctx, &w, 1, kInnerCompletionWeight};
-  // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF
-  const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0};
+  const int fres = o.fmm_order > 0 ? p_res : 0, fin = o.fmm_order > 0 ? std::max(2, p_in) : 0;
+  const Op op64{ctx, &w, 0, 0.0, fres}, op32{ctx, &w, 1, kInnerCompletionWeight, fin};
+  // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF (direct sums),
+  // or the FMM of the full order
+  const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0, 0.0, fres};
   int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, mff = 0, iters = 0, refs = 0;
   double relres = 0.0;
   bool converged = false;
@@ -606,7 +628,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
       refs += 1;
       CK(axpy(w.xs, w.d, n, s));
       CK(opres.apply(vec(w.xs), vec(w.ytmp), nullptr, s));
-      if (opres.prec == 0) m64 += 1; else mff += 1;
+      if (opres.prec == 0 || opres.fmm_p > 0) m64 += 1; else mff += 1;
       {
         KState init;
         memset(&init, 0, sizeof(init));
@@ -698,6 +720,39 @@ void release_workspace(bie_ctx* ctx, cudaStream_t s) {
 
 extern "C" {
 
+int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, const double* in, double* out,
+                       void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> bs;
+  int rc = validate(ctx, geom, bs);
+  if (rc) return rc;
+  if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
+  if (order < 2 || order > 64) return fail(ctx, BIE_ERR_INVALID, "order must be in 2..64");
+  if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
+  DeviceGuard dg(ctx->device);
+  const int N = geom->n_bodies, M = bs[N];
+  Work w;
+  Arena sz{nullptr};
+  carve(sz, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
+  Arena ar{ctx->ws};
+  carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  if ((rc = fmm_setup(ctx->fmm, w.g, kind, &order, 1, s, ctx->err))) return rc;
+  const double* din;
+  if ((rc = stage_in(ctx, in, w.io_in, (size_t)w.n, &din, s))) return rc;
+  const bool dev_out = is_device_ptr(out);
+  double* dout = dev_out ? out : w.io_out;
+  const PairPlan one{1, M};
+  CK(fmm_pair_sum(ctx->fmm, w.g, kind, order, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr, s));
+  CK(epilogue(w.g, kind, one, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s));
+  if (!dev_out) {
+    CK(cudaMemcpyAsync(out, dout, (size_t)w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return BIE_OK;
+}
+
 size_t bie_workspace_bytes(int kind, int n_bodies, int n_nodes, int restart) {
   if (n_bodies < 1 || n_nodes < 1 || (kind != 0 && kind != 1)) return 0;
   Work w;
@@ -727,6 +782,7 @@ void bie_destroy(bie_ctx* c) {
   resolve_timings(c, true);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (auto& gi : c->graphs) cudaGraphExecDestroy(gi.exec);
+  if (c->fmm) bie::fmm_free(c->fmm, nullptr);
   if (c->ws) {
     cudaDeviceSynchronize();
     cudaFree(c->ws);

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace bie {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -126,6 +128,17 @@ cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const 
 // out = in - (I - C) L~(in) for a correction solved with the weighted completion.
 cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* in, double* out,
                            cudaStream_t s);
+
+// ---------------------------------------------------------------- fmm.cu
+struct FmmState;
+// Build the quadtree for the staged geometry and the translation operators of
+// every order in `orders` (at most 64).  One host round trip.
+int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norders, cudaStream_t s,
+              std::string& err);
+// Pair sums by the FMM of order p into partial (layout of a single source split).
+cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
+                         double* partial, const int* stop, cudaStream_t s);
+void fmm_free(FmmState* f, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 int vec_grid(long long n);

@@ -1,0 +1,571 @@
+// Quadtree fast multipole method for the pair sums, in complex variables.
+//
+// With z = x1 + i x2, both kernels reduce to Cauchy sums
+//   F_q(z_a) = sum_{b != a} q_b / (z_a - z_b),   F'_q its z-derivative.
+// Laplace (Section 3.4): with q = w mu (real) and nu = n1 + i n2 at the target,
+//   sum_b q_b (r . n_a)/|r|^2 = Re(nu_a F_q(z_a)).
+// Stokes traction (Section 4.3): with q = w (mu1 + i mu2) complex, and
+//   S1 = F_q, S2 = -F'_q, S3 = -F'_{q conj(z - c0)}, S6 = F_{conj q} (any fixed c0),
+//   sum_b r (r . q_b)(r . n_a)/|r|^4 =
+//     (1/4) [ conj(nu) conj(conj(z_a - c0) S2 - S3) + nu conj(S1) + conj(nu) conj(S6) + nu S1 ],
+// an identity of complex algebra (r . m = Re(r conj(m)) for complex r, m).
+//
+// Uniform quadtree on the bounding square, leaf level L chosen so that a
+// non-empty leaf holds about 24-50 nodes.  Expansions in scaled form (powers of
+// (z - c)/s), so the translation operators do not depend on the level: 4
+// multipole-to-multipole, 4 local-to-local and 49 multipole-to-local
+// (offsets -3..3 in each direction) p x p complex matrices, built on the host
+// in double precision.  Multipole:  F(z) = sum_k a_k s^k / (z - c)^(k+1),
+// a_k = sum_j q_j ((z_j - c)/s)^k; local: F(z) = sum_l b_l ((z - c)/s)^l.
+// Translations (d = target centre - source centre):
+//   M2M  a'_k = sum_{m<=k} C(k,m) 2^-m w^(k-m) a_m,        w = (c_child - c_parent)/S
+//   M2L  b_l  = (1/s) sum_k (-1)^l C(k+l,l) D^-(k+l+1) a_k,  D = d/s (integer offset)
+//   L2L  b'_m = sum_{l>=m} C(l,m) 2^-m w^(l-m) b_l
+// The near field (the 3 x 3 leaves around a target's leaf) is summed directly.
+// Nodes are grouped by leaf with a counting sort whose order inside a leaf is
+// the node order, so every sum runs in a fixed order (deterministic results).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/bie2d.h"
+#include "bie_internal.cuh"
+
+namespace bie {
+
+namespace {
+
+constexpr int kMaxP = 64;
+constexpr int kB = 64;       // threads per box block (>= p)
+constexpr int kChunk = 32;   // points per P2M chunk
+constexpr int kNops = 57;    // 4 M2M + 4 L2L + 49 M2L
+
+__host__ __device__ inline long long lev_off(int l) { return ((1LL << (2 * l)) - 1) / 3; }
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+
+struct FmmDev {
+  int L, nb, p, nd, M;
+  double x0, y0, D;
+  const int* leaf;
+  const int* perm;
+  const int* start;
+  const int* count;
+  double2* Q;
+  double2* mp;
+  double2* lc;
+  const double2* ops;
+};
+
+__device__ __forceinline__ double2 box_center(const FmmDev& f, int l, int bx, int by, double& s) {
+  s = f.D / (double)(1 << l);
+  return make_double2(f.x0 + (bx + 0.5) * s, f.y0 + (by + 0.5) * s);
+}
+
+// ------------------------------------------------------------------ setup ----
+// Bounding square of the body boxes and the total arc length.
+__global__ void k_fmm_box(Geo g, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300, len = 0.0;
+  for (int i = 0; i < g.N; ++i) {
+    const float4 b = g.bbox[i];
+    x0 = fmin(x0, (double)b.x);
+    y0 = fmin(y0, (double)b.y);
+    x1 = fmax(x1, (double)b.z);
+    y1 = fmax(y1, (double)b.w);
+    len += g.len[i];
+  }
+  const double D = fmax(x1 - x0, y1 - y0) * (1.0 + 1e-6) + 1e-12;
+  out[0] = x0 - 1e-7 * D;
+  out[1] = y0 - 1e-7 * D;
+  out[2] = D * (1.0 + 2e-7);
+  out[3] = len;
+}
+
+__global__ void k_fmm_leaf(Geo g, int L, double x0, double y0, double D, int* leaf, int* cnt) {
+  const int nb = 1 << L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.M; i += gridDim.x * blockDim.x) {
+    int ix = (int)((g.x[i] - x0) / D * nb), iy = (int)((g.y[i] - y0) / D * nb);
+    ix = min(max(ix, 0), nb - 1);
+    iy = min(max(iy, 0), nb - 1);
+    const int b = iy * nb + ix;
+    leaf[i] = b;
+    atomicAdd(&cnt[b], 1);
+  }
+}
+
+// Exclusive scan of n counts into start[0..n] (one block of 1024 threads).
+__global__ void k_fmm_scan(const int* cnt, int n, int* start) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (n + 1023) / 1024;
+  const int b0 = t * per, b1 = min(n, b0 + per);
+  int s = 0;
+  for (int i = b0; i < b1; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const int v = part[k];
+      part[k] = acc;
+      acc += v;
+    }
+    start[n] = acc;
+  }
+  __syncthreads();
+  int acc = part[t];
+  for (int i = b0; i < b1; ++i) {
+    start[i] = acc;
+    acc += cnt[i];
+  }
+}
+
+__global__ void k_fmm_scatter(int M, const int* leaf, const int* start, int* cursor, int* tmp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int b = leaf[i];
+    tmp[start[b] + atomicAdd(&cursor[b], 1)] = i;
+  }
+}
+
+// Within each leaf, put the nodes in increasing node order (rank by counting).
+__global__ void k_fmm_order(const int* start, const int* tmp, int* perm) {
+  const int b = blockIdx.x;
+  const int s0 = start[b], n = start[b + 1] - s0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int v = tmp[s0 + j];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += tmp[s0 + k] < v;
+    perm[s0 + rank] = v;
+  }
+}
+
+// Points per box on every level: leaves from start, parents from children.
+__global__ void k_fmm_leaf_counts(const int* start, int nleaf, int* count_leaf) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nleaf; b += gridDim.x * blockDim.x)
+    count_leaf[b] = start[b + 1] - start[b];
+}
+__global__ void k_fmm_parent_counts(int l, int* count) {
+  const int n = 1 << l;
+  const long long off = lev_off(l), offc = lev_off(l + 1);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n * n; b += gridDim.x * blockDim.x) {
+    const int bx = b % n, by = b / n;
+    const int nc = 2 * n;
+    int s = 0;
+    for (int c = 0; c < 4; ++c) s += count[offc + (2 * by + (c >> 1)) * nc + 2 * bx + (c & 1)];
+    count[off + b] = s;
+  }
+}
+
+// ------------------------------------------------------------------ apply ----
+// Densities: Laplace q = sw v (real); Stokes q = sw (v1 + i v2), conj(q),
+// q conj(z - c0) with c0 the centre of the bounding square (the Stokes
+// combination cancels conj(z_a) S2 against S3, so smaller |z - c0| keeps the
+// expansion error of S3 small).
+__global__ void k_fmm_density(Geo g, int nd, double cx0, double cy0, VecRef vr, const double* __restrict__ sscale,
+                              double2* Q, const int* stop) {
+  if (stop && *stop) return;
+  const double* v = vr.ptr();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.M; i += gridDim.x * blockDim.x) {
+    if (nd == 1) {
+      Q[i] = make_double2(sscale[i] * v[i], 0.0);
+    } else {
+      const double2 q = make_double2(sscale[i] * v[2 * i], sscale[i] * v[2 * i + 1]);
+      Q[3 * i] = q;
+      Q[3 * i + 1] = cconj(q);
+      Q[3 * i + 2] = cmul(q, make_double2(g.x[i] - cx0, -(g.y[i] - cy0)));
+    }
+  }
+}
+
+// P2M on the leaves: a_k = sum_j q_j u_j^k, u = (z - c)/s.
+__global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDev f, Geo g, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ double2 sm[];
+  double2* pw = sm;                       // [p][kChunk + 1]
+  double2* qs = sm + f.p * (kChunk + 1);  // [kChunk][nd]
+  const int b = blockIdx.x;
+  const long long box = lev_off(f.L) + b;
+  const int s0 = f.start[b], n = f.start[b + 1] - s0;
+  if (n == 0) return;
+  double s;
+  const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
+  const int t = threadIdx.x;
+  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int ch = 0; ch < n; ch += kChunk) {
+    const int m = min(kChunk, n - ch);
+    if (t < kChunk) {
+      if (t < m) {
+        const int i = f.perm[s0 + ch + t];
+        const double2 u = make_double2((g.x[i] - c.x) / s, (g.y[i] - c.y) / s);
+        double2 w = make_double2(1.0, 0.0);
+        for (int k = 0; k < f.p; ++k) {
+          pw[k * (kChunk + 1) + t] = w;
+          w = cmul(w, u);
+        }
+        for (int d = 0; d < f.nd; ++d) qs[t * f.nd + d] = f.Q[(long long)i * f.nd + d];
+      }
+    }
+    __syncthreads();
+    if (t < f.p)
+      for (int j = 0; j < m; ++j)
+        for (int d = 0; d < f.nd; ++d) cfma(acc[d], pw[t * (kChunk + 1) + j], qs[j * f.nd + d]);
+    __syncthreads();
+  }
+  if (t < f.p)
+    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
+}
+
+// M2M into level l (parents) from level l + 1.
+__global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ double2 sm[];  // [nd][p]
+  const int n = 1 << l;
+  const int b = blockIdx.x, bx = b % n, by = b / n;
+  const long long box = lev_off(l) + b;
+  if (f.count[box] == 0) return;
+  const int t = threadIdx.x;
+  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int c = 0; c < 4; ++c) {
+    const long long child = lev_off(l + 1) + (2 * by + (c >> 1)) * (2 * n) + 2 * bx + (c & 1);
+    if (f.count[child] == 0) continue;  // uniform over the block
+    __syncthreads();
+    for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[child * f.nd * f.p + e];
+    __syncthreads();
+    if (t < f.p) {
+      const double2* op = f.ops + (long long)c * f.p * f.p;  // [in][out]
+      for (int m = 0; m <= t; ++m) {
+        const double2 o = op[m * f.p + t];
+        for (int d = 0; d < f.nd; ++d) cfma(acc[d], o, sm[d * f.p + m]);
+      }
+    }
+  }
+  if (t < f.p)
+    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
+}
+
+// M2L for the target boxes of all levels 2..L (one block per box).
+__global__ void __launch_bounds__(kB) k_fmm_m2l(FmmDev f, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ double2 sm[];  // [nd][p]
+  long long gb = blockIdx.x + lev_off(2);
+  int l = 2;
+  while (l < f.L && gb >= lev_off(l + 1)) ++l;
+  if (f.count[gb] == 0) return;
+  const int n = 1 << l;
+  const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
+  const int px = bx >> 1, py = by >> 1;
+  const double s = f.D / (double)n;
+  const int t = threadIdx.x;
+  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int sy = max(0, 2 * py - 2); sy <= min(n - 1, 2 * py + 3); ++sy) {
+    for (int sx = max(0, 2 * px - 2); sx <= min(n - 1, 2 * px + 3); ++sx) {
+      if (abs(sx - bx) <= 1 && abs(sy - by) <= 1) continue;
+      const long long src = lev_off(l) + sy * n + sx;
+      if (f.count[src] == 0) continue;
+      __syncthreads();
+      for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[src * f.nd * f.p + e];
+      __syncthreads();
+      if (t < f.p) {
+        const int oi = 8 + (bx - sx + 3) + 7 * (by - sy + 3);
+        const double2* op = f.ops + (long long)oi * f.p * f.p;
+        for (int k = 0; k < f.p; ++k) {
+          const double2 o = op[k * f.p + t];
+          for (int d = 0; d < f.nd; ++d) cfma(acc[d], o, sm[d * f.p + k]);
+        }
+      }
+    }
+  }
+  if (t < f.p)
+    for (int d = 0; d < f.nd; ++d)
+      f.lc[(gb * f.nd + d) * f.p + t] = make_double2(acc[d].x / s, acc[d].y / s);
+}
+
+// L2L from level l to the children at level l + 1 (added to their M2L part).
+__global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ double2 sm[];  // [nd][p]
+  const int nc = 2 << l;
+  const int b = blockIdx.x, cx = b % nc, cy = b / nc;
+  const long long child = lev_off(l + 1) + b;
+  if (f.count[child] == 0) return;
+  const long long parent = lev_off(l) + (cy >> 1) * (nc >> 1) + (cx >> 1);
+  const int c = (cx & 1) + 2 * (cy & 1);
+  const int t = threadIdx.x;
+  for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.lc[parent * f.nd * f.p + e];
+  __syncthreads();
+  if (t < f.p) {
+    const double2* op = f.ops + (long long)(4 + c) * f.p * f.p;
+    for (int d = 0; d < f.nd; ++d) {
+      double2 acc = f.lc[(child * f.nd + d) * f.p + t];
+      for (int m = t; m < f.p; ++m) cfma(acc, op[m * f.p + t], sm[d * f.p + m]);
+      f.lc[(child * f.nd + d) * f.p + t] = acc;
+    }
+  }
+}
+
+// Local expansion and near field at every node of a leaf, then the kernel's
+// combination into the pair-sum partial (Laplace scalar / Stokes 2-vector).
+__global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __restrict__ partial, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ double2 sm[];  // [nd][p]
+  const int b = blockIdx.x, bx = b % f.nb, by = b / f.nb;
+  const int s0 = f.start[b], n = f.start[b + 1] - s0;
+  if (n == 0) return;
+  const long long box = lev_off(f.L) + b;
+  for (int e = threadIdx.x; e < f.nd * f.p; e += kB) sm[e] = f.lc[box * f.nd * f.p + e];
+  __syncthreads();
+  double s;
+  const double2 c = box_center(f, f.L, bx, by, s);
+  for (int j = threadIdx.x; j < n; j += kB) {
+    const int i = f.perm[s0 + j];
+    const double2 zi = make_double2(g.x[i], g.y[i]);
+    const double2 u = make_double2((zi.x - c.x) / s, (zi.y - c.y) / s);
+    double2 F[3], dF[3];
+    for (int d = 0; d < f.nd; ++d) {
+      // Horner for F and F' in u
+      double2 h = sm[d * f.p + f.p - 1], dh = make_double2(0.0, 0.0);
+      for (int l = f.p - 2; l >= 0; --l) {
+        dh = cadd(cmul(dh, u), h);
+        h = cadd(cmul(h, u), sm[d * f.p + l]);
+      }
+      F[d] = h;
+      dF[d] = make_double2(dh.x / s, dh.y / s);
+    }
+    // near field: 3 x 3 leaves
+    for (int ny = max(0, by - 1); ny <= min(f.nb - 1, by + 1); ++ny) {
+      for (int nx = max(0, bx - 1); nx <= min(f.nb - 1, bx + 1); ++nx) {
+        const int nl = ny * f.nb + nx;
+        for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+          const int i2 = f.perm[k];
+          if (i2 == i) continue;
+          const double rx = zi.x - g.x[i2], ry = zi.y - g.y[i2];
+          const double inv = 1.0 / (rx * rx + ry * ry);
+          const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
+          const double2 r2 = cmul(r1, r1);
+          for (int d = 0; d < f.nd; ++d) {
+            const double2 q = f.Q[(long long)i2 * f.nd + d];
+            cfma(F[d], q, r1);
+            cfma(dF[d], make_double2(-q.x, -q.y), r2);
+          }
+        }
+      }
+    }
+    const double nx1 = g.nx[i], ny1 = g.ny[i];
+    if (f.nd == 1) {
+      partial[i] = nx1 * F[0].x - ny1 * F[0].y;
+    } else {
+      const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
+      const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-dF[2].x, -dF[2].y);
+      const double2 S6 = F[1];
+      const double2 zb = make_double2(zi.x - (f.x0 + 0.5 * f.D), -(zi.y - (f.y0 + 0.5 * f.D)));
+      double2 w = cmul(zb, S2);
+      w = make_double2(w.x - S3.x, w.y - S3.y);
+      double2 tt = cmul(nub, cconj(w));
+      tt = cadd(tt, cmul(nu, cconj(S1)));
+      tt = cadd(tt, cmul(nub, cconj(S6)));
+      tt = cadd(tt, cmul(nu, S1));
+      partial[2 * i] = 0.25 * tt.x;
+      partial[2 * i + 1] = 0.25 * tt.y;
+    }
+  }
+}
+
+inline int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+// Translation operators for order p, stored [op][in][out].
+std::vector<std::complex<double>> build_ops(int p) {
+  using C = std::complex<double>;
+  std::vector<double> bin((2 * p + 1) * (2 * p + 1), 0.0);
+  auto B = [&](int a, int b) -> double& { return bin[a * (2 * p + 1) + b]; };
+  for (int a = 0; a <= 2 * p; ++a) {
+    B(a, 0) = 1.0;
+    for (int b = 1; b <= a; ++b) B(a, b) = B(a - 1, b - 1) + (b <= a - 1 ? B(a - 1, b) : 0.0);
+  }
+  std::vector<C> ops((size_t)kNops * p * p, C(0, 0));
+  auto at = [&](int o, int in, int out) -> C& { return ops[((size_t)o * p + in) * p + out]; };
+  for (int c = 0; c < 4; ++c) {
+    const C w(((c & 1) - 0.5) / 2.0, ((c >> 1) - 0.5) / 2.0);
+    for (int k = 0; k < p; ++k)
+      for (int m = 0; m <= k; ++m) at(c, m, k) = B(k, m) * std::pow(0.5, m) * std::pow(w, k - m);  // M2M
+    for (int m = 0; m < p; ++m)
+      for (int l = m; l < p; ++l) at(4 + c, l, m) = B(l, m) * std::pow(0.5, m) * std::pow(w, l - m);  // L2L
+  }
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx) {
+      if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+      const int o = 8 + (dx + 3) + 7 * (dy + 3);
+      const C Dinv = 1.0 / C(dx, dy);
+      for (int l = 0; l < p; ++l)
+        for (int k = 0; k < p; ++k)
+          at(o, k, l) = ((l & 1) ? -1.0 : 1.0) * B(k + l, l) * std::pow(Dinv, k + l + 1);  // M2L
+    }
+  return ops;
+}
+
+}  // namespace
+
+struct FmmState {
+  int L = 0, nb = 0, nleaf = 0, kind = 0, M = 0, N = 0;
+  double x0 = 0, y0 = 0, D = 0;
+  long long nbox = 0;
+  // device buffers (stream-ordered), grown on demand
+  char* buf = nullptr;
+  size_t buf_size = 0;
+  int *leaf = nullptr, *perm = nullptr, *tmp = nullptr, *start = nullptr, *cursor = nullptr, *count = nullptr;
+  double2 *Q = nullptr, *mp = nullptr, *lc = nullptr;
+  double* scal = nullptr;
+  int pmax = 0;
+  // operators per order
+  std::vector<std::pair<int, double2*>> ops;
+};
+
+void fmm_free(FmmState* f, cudaStream_t s) {
+  if (!f) return;
+  if (f->buf) cudaFreeAsync(f->buf, s);
+  for (auto& o : f->ops) cudaFreeAsync(o.second, s);
+  delete f;
+}
+
+// Build the tree for the staged geometry (one host round trip for the box).
+int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norders, cudaStream_t s,
+              std::string& err) {
+  int pmax = 0;
+  for (int k = 0; k < norders; ++k) {
+    if (orders[k] < 2 || orders[k] > kMaxP) {
+      err = "FMM order must be in 2.." + std::to_string(kMaxP);
+      return BIE_ERR_INVALID;
+    }
+    pmax = std::max(pmax, orders[k]);
+  }
+  if (!f) f = new FmmState();
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess) err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaSuccess;
+  };
+  // bounding square and total length
+  double* scal = nullptr;
+  if (!f->scal) {
+    if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&f->scal), 4 * sizeof(double), s), "fmm scal")) return BIE_ERR_CUDA;
+  }
+  scal = f->scal;
+  k_fmm_box<<<1, 32, 0, s>>>(g, scal);
+  note_launches(1);
+  double h[4];
+  if (!ck(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s), "fmm box") ||
+      !ck(cudaStreamSynchronize(s), "fmm box sync"))
+    return BIE_ERR_CUDA;
+  f->x0 = h[0];
+  f->y0 = h[1];
+  f->D = h[2];
+  // leaf level: the finest level whose non-empty leaves hold at least ~24 nodes;
+  // nodes on curves of total length P occupy about min(4^L, 1.3 P 2^L / D) leaves
+  int L = 2;
+  for (int l = 2; l <= 10; ++l) {
+    const double boxes = fmin((double)(1LL << (2 * l)), 1.3 * h[3] * (double)(1 << l) / f->D);
+    if ((double)g.M / fmax(boxes, 1.0) >= 24.0) L = l;
+  }
+  f->L = L;
+  f->nb = 1 << L;
+  f->nleaf = f->nb * f->nb;
+  f->nbox = lev_off(L + 1);
+  f->kind = kind;
+  f->M = g.M;
+  f->N = g.N;
+  const int nd = kind == 0 ? 1 : 3;
+  f->pmax = pmax;
+  // buffers
+  auto pad = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t need = 3 * pad((size_t)g.M * 4) + 2 * pad(((size_t)f->nleaf + 1) * 4) + pad((size_t)f->nbox * 4) +
+                      pad((size_t)g.M * nd * 16) + 2 * pad((size_t)f->nbox * nd * pmax * 16);
+  if (need > f->buf_size) {
+    if (f->buf) cudaFreeAsync(f->buf, s);
+    f->buf = nullptr;
+    f->buf_size = 0;
+    if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&f->buf), need, s), "fmm buffers")) return BIE_ERR_CUDA;
+    f->buf_size = need;
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = f->buf + off;
+    off += pad(bytes);
+    return p;
+  };
+  f->leaf = (int*)take((size_t)g.M * 4);
+  f->perm = (int*)take((size_t)g.M * 4);
+  f->tmp = (int*)take((size_t)g.M * 4);
+  f->start = (int*)take(((size_t)f->nleaf + 1) * 4);
+  f->cursor = (int*)take(((size_t)f->nleaf + 1) * 4);
+  f->count = (int*)take((size_t)f->nbox * 4);
+  f->Q = (double2*)take((size_t)g.M * nd * 16);
+  f->mp = (double2*)take((size_t)f->nbox * nd * pmax * 16);
+  f->lc = (double2*)take((size_t)f->nbox * nd * pmax * 16);
+  // counting sort of the nodes by leaf, node order inside a leaf
+  if (!ck(cudaMemsetAsync(f->cursor, 0, ((size_t)f->nleaf + 1) * 4, s), "fmm memset")) return BIE_ERR_CUDA;
+  k_fmm_leaf<<<grid_for(g.M), 256, 0, s>>>(g, L, f->x0, f->y0, f->D, f->leaf, f->cursor);
+  k_fmm_scan<<<1, 1024, 0, s>>>(f->cursor, f->nleaf, f->start);
+  cudaMemsetAsync(f->cursor, 0, ((size_t)f->nleaf + 1) * 4, s);
+  k_fmm_scatter<<<grid_for(g.M), 256, 0, s>>>(g.M, f->leaf, f->start, f->cursor, f->tmp);
+  k_fmm_order<<<f->nleaf, 128, 0, s>>>(f->start, f->tmp, f->perm);
+  k_fmm_leaf_counts<<<grid_for(f->nleaf), 256, 0, s>>>(f->start, f->nleaf, f->count + lev_off(L));
+  for (int l = L - 1; l >= 0; --l) k_fmm_parent_counts<<<grid_for(1LL << (2 * l)), 256, 0, s>>>(l, f->count);
+  note_launches(6 + L);
+  if (!ck(cudaGetLastError(), "fmm setup")) return BIE_ERR_CUDA;
+  // translation operators, built before any capture of the apply
+  for (int k = 0; k < norders; ++k) {
+    const int p = orders[k];
+    bool have = false;
+    for (auto& o : f->ops) have |= o.first == p;
+    if (have) continue;
+    const auto host = build_ops(p);
+    double2* ops = nullptr;
+    if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&ops), host.size() * sizeof(double2), s), "fmm ops") ||
+        !ck(cudaMemcpyAsync(ops, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice, s), "fmm ops") ||
+        !ck(cudaStreamSynchronize(s), "fmm ops"))
+      return BIE_ERR_CUDA;
+    f->ops.push_back({p, ops});
+  }
+  return BIE_OK;
+}
+
+cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
+                         double* partial, const int* stop, cudaStream_t s) {
+  if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;
+  double2* ops = nullptr;
+  for (auto& o : f->ops)
+    if (o.first == p) ops = o.second;
+  if (!ops) return cudaErrorInvalidValue;  // fmm_setup prepares every order
+  const int nd = kind == 0 ? 1 : 3;
+  FmmDev d{f->L, f->nb, p, nd, g.M, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count,
+           f->Q, f->mp, f->lc, ops};
+  const size_t sm_exp = (size_t)nd * p * sizeof(double2);
+  const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
+  k_fmm_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, f->x0 + 0.5 * f->D, f->y0 + 0.5 * f->D, v, sscale, f->Q,
+                                               stop);
+  k_fmm_p2m<<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
+  k_fmm_m2l<<<(int)(lev_off(f->L + 1) - lev_off(2)), kB, sm_exp, s>>>(d, stop);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
+  k_fmm_eval<<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+  note_launches(4 + 2 * std::max(0, f->L - 2));
+  return cudaGetLastError();
+}
+
+}  // namespace bie

@@ -269,6 +269,34 @@ def ellipse_suspension(seed: int = 2000, n_bodies: int = 400, n: int = 128,
     return g
 
 
+def ellipse_lattice(seed: int = 5000, rows: int = 100, cols: int = 100, n: int = 64,
+                    aspect: tuple[float, float] = (1.0, 3.0), gap_factor: float = 5.0) -> dict:
+    """Ellipses (major semi-axis 1, aspect ratio U[aspect], random orientation) on
+    a hexagonal lattice whose spacing 2 + gap_factor * (2 pi / n) keeps every
+    node gap >= gap_factor node spacings for any orientations.  The default
+    (100 x 100, 64 nodes: M = 640,000) has area fraction about 0.32; random
+    sequential addition jams before 0.3 at this gap.  Forces N(0,1)^2 with the
+    mean removed, torques N(0,1).
+    """
+    rng = np.random.default_rng(seed)
+    h = TWO_PI / n  # largest node spacing of a major-semi-axis-1 ellipse
+    d = 2.0 + gap_factor * h
+    curves = []
+    area = 0.0
+    for i in range(rows):
+        for j in range(cols):
+            cx = j * d + (0.5 * d if i % 2 else 0.0)
+            cy = i * d * math.sqrt(3.0) / 2.0
+            b = 1.0 / rng.uniform(aspect[0], aspect[1])
+            curves.append(ellipse(cx, cy, 1.0, b, rng.uniform(0.0, math.pi), n))
+            area += math.pi * b
+    g = assemble(curves)
+    g["FT"] = forces_torques(rows * cols, rng)
+    g["area_fraction"] = area / (cols * d * rows * d * math.sqrt(3.0) / 2.0)
+    g["name"] = f"{rows * cols} ellipses on a hexagonal lattice, n={n} (M={rows * cols * n})"
+    return g
+
+
 def two_discs(d: float, n: int) -> dict:
     """Two unit discs centred at (-1 - d/2, 0) and (1 + d/2, 0) (Section 6.1.1 layout)."""
     return assemble([disc(-1.0 - d / 2, 0.0, 1.0, n), disc(1.0 + d / 2, 0.0, 1.0, n)])
@@ -318,4 +346,5 @@ WORKLOADS = {
     "four_discs_M512": lambda: four_discs(seed=0),
     "stars100_M25600": lambda: star_grid(seed=1000),
     "ellipses400_M51200": lambda: ellipse_suspension(seed=2000),
+    "ellipses10000_M640000": lambda: ellipse_lattice(seed=5000),
 }

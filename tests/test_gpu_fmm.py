@@ -1,0 +1,94 @@
+"""Quadtree FMM pair sums: operator parity with the direct FP64 sums and the
+oracle, determinism, and solves with FMM pair sums against the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import geometry, laplace, stokes  # noqa: E402
+from paper_1507_05925_gb300 import bie  # noqa: E402
+from test_gpu_parity import _sampled_rows, multitile, rel2, rel_max, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# FMM order -> operator tolerance (relative max-norm): the truncation decays
+# about like 0.35^p for the 3 x 3-neighbour separation of this quadtree
+TOL_FMM = {16: 1e-6, 36: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05925_gb300 import build
+    build.build()
+    c = bie.Context(0)
+    yield c
+    c.close()
+
+
+def _apply(ctx, g, kind, v, order=None, prec=bie.FP64):
+    out = torch.empty(v.size, dtype=torch.float64, device="cuda")
+    vin = torch.from_numpy(v).cuda()
+    if order is None:
+        rc = bie.apply_operator(ctx, to_dev(g), kind, prec, vin, out)
+    else:
+        rc = bie.apply_operator_fmm(ctx, to_dev(g), kind, order, vin, out)
+    torch.cuda.synchronize()
+    assert rc == bie.OK, ctx.last_error()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+@pytest.mark.parametrize("order", [16, 36])
+def test_fmm_operator_matches_direct(ctx, kind, order):
+    g = multitile(rows=5, cols=5)
+    v = np.random.default_rng(3).standard_normal(g["x"].size * (kind + 1))
+    ref = _apply(ctx, g, kind, v)
+    got = _apply(ctx, g, kind, v, order=order)
+    err = rel_max(got, ref)
+    print(f"fmm kind={kind} order={order}: {err:.2e}")
+    assert err <= TOL_FMM[order]
+    assert np.array_equal(got, _apply(ctx, g, kind, v, order=order))  # deterministic
+
+
+@pytest.mark.parametrize("wl,kind,nrows", [("stars100_M25600", 0, 48), ("ellipses400_M51200", 1, 24),
+                                           ("ellipses10000_M640000", 1, 8)])
+def test_fmm_full_size_rows(ctx, wl, kind, nrows):
+    g = synth.WORKLOADS[wl]()
+    geo = geometry.nodes(g)
+    v = np.random.default_rng(4).standard_normal(geo["M"] * (kind + 1))
+    rows = np.sort(np.random.default_rng(5).choice(geo["M"], nrows, replace=False))
+    ref = _sampled_rows(geo, kind, v, rows)
+    got = _apply(ctx, g, kind, v, order=36)
+    got = got[rows] if kind == 0 else got[np.stack([2 * rows, 2 * rows + 1], 1).reshape(-1)]
+    err = rel_max(got, ref)
+    print(f"fmm {wl} rows: {err:.2e}")
+    assert err <= TOL_FMM[36]
+
+
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED_FF])
+def test_solve_with_fmm(ctx, kind, prec):
+    g = multitile(rows=4, cols=4) if kind == 0 else multitile(rows=3, cols=3)
+    N = g["body_start"].size - 1
+    if kind == 0:
+        load = synth.charges(N, np.random.default_rng(11))
+        ref = laplace.solve(g, load)["phi"]
+        out = torch.empty(N, dtype=torch.float64, device="cuda")
+        fn = bie.elastance_solve
+    else:
+        FT = synth.forces_torques(N, np.random.default_rng(12))
+        load = FT.reshape(-1)
+        ref = stokes.solve(g, FT)["UW"].reshape(-1)
+        out = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        fn = bie.mobility_solve
+    rc, info = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out,
+                  opts=bie.make_opts(precision=prec, fmm_order=36))
+    torch.cuda.synchronize()
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    err = rel2(out.cpu().numpy(), ref)
+    print(f"fmm solve kind={kind} prec={prec}: {err:.2e} {info}")
+    assert err <= 1e-10
+    assert info["rel_residual"] <= 1e-12
