@@ -60,6 +60,8 @@ def parse():
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--fmm-order", type=int, default=36)
+    ap.add_argument("--large-steps", type=int, default=1,
+                    help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
                     choices=["laplace_fp32", "laplace_fp64", "laplace_ff", "laplace_fmm", "stokes_fp32",
                              "stokes_fp64", "stokes_ff", "stokes_fmm", "stokes_fmm_large", "stokes_fp32_large"],
@@ -301,6 +303,41 @@ def run_serving(args, rank, local):
     }
 
 
+def run_large(args, rank, local):
+    """Mobility of 10,000 ellipses (M = 640,000): refinement with FMM pair sums
+    (order fmm_order for residuals, half for the inner solves)."""
+    import torch
+
+    from paper_1507_05925_gb300 import bie
+
+    g = synth.ellipse_lattice(seed=5000 + rank)
+    dev = torch.device("cuda", local)
+    gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
+    N = g["body_start"].size - 1
+    FT = torch.from_numpy(g["FT"].reshape(-1)).to(dev)
+    UW = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    ctx = bie.Context(local)
+    opts = bie.make_opts(precision=bie.MIXED_FF, fmm_order=args.fmm_order)
+    rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
+    assert rc == bie.OK, (rc, ctx.last_error())
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.large_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        assert rc == bie.OK
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    return {"workload": "ellipses10000_M640000 (hexagonal lattice, area fraction %.2f)" % g["area_fraction"],
+            "M": int(g["x"].size), "fmm_order": args.fmm_order, "precision": "mixed_ff",
+            "seconds_per_solve": float(np.mean(ms)) / 1e3, "solves_per_s": 1e3 / float(np.mean(ms)),
+            "info": info}
+
+
 def run_kernel(args, local):
     """Operator applications only (for kernel timing and ncu captures)."""
     import torch
@@ -533,6 +570,8 @@ def main():
     }
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, rank, local)
+    if args.large_steps > 0:
+        out["large_mobility"] = run_large(args, rank, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample_rate(M, 16)
         out["cpu_baseline"] = {"value": 1.0 / smp["seconds_full_estimate"], "unit": "solves/s",
