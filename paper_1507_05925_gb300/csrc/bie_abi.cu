@@ -649,7 +649,12 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(incident_density_scaled(w.g, kind, dload, w.rin, s));
     CK(axpy(w.xs, w.rin, n, s));
   }
-  CK(evaluate_output(w.g, kind, v, dload, w.outpart, w.P, w.outv, w.cres, s));
+  if (o.fmm_order > 0) {
+    CK(fmm_output(ctx->fmm, w.g, kind, p_res, v, w.outpart, s));
+    CK(finalize_output(w.g, kind, v, dload, w.outpart, 1, w.outv, w.cres, s));
+  } else {
+    CK(evaluate_output(w.g, kind, v, dload, w.outpart, w.P, w.outv, w.cres, s));
+  }
   if (density) {
     CK(unscale(w.g, kind, v, w.ytmp, s));
     if ((rc = copy_out(ctx, density, w.ytmp, n, s))) return rc;
@@ -657,7 +662,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   if ((rc = copy_out(ctx, out, w.outv, nload, s))) return rc;
   // constraint residual and net load
   const int targets = kind == 0 ? N : 3 * N;
-  const double* nl = w.outpart + (size_t)w.P * targets * (kind + 1) + N;
+  const int P_used = o.fmm_order > 0 ? 1 : w.P;  // splits of the output sums
+  const double* nl = w.outpart + (size_t)P_used * targets * (kind + 1) + N;
   CK(cudaMemcpyAsync(ctx->h_small, w.cres, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_small + 1, nl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

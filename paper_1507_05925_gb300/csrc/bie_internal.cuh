@@ -98,6 +98,9 @@ cudaError_t incident_density_scaled(const Geo& g, int kind, const double* load, 
 cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const double* load,
                             double* partial, int P, double* out, double* cres, cudaStream_t s);
 int output_splits(const Geo& g, int kind);
+// the second half of evaluate_output, on sums already in partial (P splits)
+cudaError_t finalize_output(const Geo& g, int kind, const double* v, const double* load, double* partial, int P,
+                            double* out, double* cres, cudaStream_t s);
 
 // elementwise helpers
 cudaError_t unscale(const Geo& g, int kind, const double* v, double* out, cudaStream_t s);   // v/sw
@@ -139,6 +142,9 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
                          double* partial, const int* stop, cudaStream_t s);
 void fmm_free(FmmState* f, cudaStream_t s);
+// Output single layers at the interior targets by the FMM (one split, the
+// layout of evaluate_output's direct sums).
+cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
 int vec_grid(long long n);

@@ -43,7 +43,8 @@ namespace {
 constexpr int kMaxP = 64;
 constexpr int kB = 64;       // threads per box block (>= p)
 constexpr int kChunk = 32;   // points per P2M chunk
-constexpr int kNops = 57;    // 4 M2M + 4 L2L + 49 M2L
+constexpr int kNops = 106;   // 4 M2M + 4 L2L + 49 Cauchy M2L + 49 logarithm M2L
+constexpr int kMaxNd = 4;    // channels per box
 
 __host__ __device__ inline long long lev_off(int l) { return ((1LL << (2 * l)) - 1) / 3; }
 
@@ -60,11 +61,13 @@ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
 
 struct FmmDev {
   int L, nb, p, nd, M;
+  int nlog;           // the first nlog channels carry the logarithm kernel, the rest Cauchy sums
   double x0, y0, D;
   const int* leaf;
   const int* perm;
   const int* start;
-  const int* count;
+  const int* count;   // sources per box (all levels)
+  const int* tcount;  // targets per box: boxes that need local expansions
   double2* Q;
   double2* mp;
   double2* lc;
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDev f, Geo g, const int* stop
   double s;
   const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
   const int t = threadIdx.x;
-  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int ch = 0; ch < n; ch += kChunk) {
     const int m = min(kChunk, n - ch);
     if (t < kChunk) {
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop
   const long long box = lev_off(l) + b;
   if (f.count[box] == 0) return;
   const int t = threadIdx.x;
-  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int c = 0; c < 4; ++c) {
     const long long child = lev_off(l + 1) + (2 * by + (c >> 1)) * (2 * n) + 2 * bx + (c & 1);
     if (f.count[child] == 0) continue;  // uniform over the block
@@ -258,20 +261,23 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop
     for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
 }
 
-// M2L for the target boxes of all levels 2..L (one block per box).
+// M2L for the target boxes of all levels 2..L (one block per box).  Cauchy
+// channels: b = (1/s) T_D a; logarithm channels: b = T^log_D a, plus
+// a_0 log(s) on b_0 (the level's share of log d = log D + log s).
 __global__ void __launch_bounds__(kB) k_fmm_m2l(FmmDev f, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ double2 sm[];  // [nd][p]
   long long gb = blockIdx.x + lev_off(2);
   int l = 2;
   while (l < f.L && gb >= lev_off(l + 1)) ++l;
-  if (f.count[gb] == 0) return;
+  if (f.tcount[gb] == 0) return;
   const int n = 1 << l;
   const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
   const int px = bx >> 1, py = by >> 1;
   const double s = f.D / (double)n;
+  const double logs = log(s);
   const int t = threadIdx.x;
-  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int sy = max(0, 2 * py - 2); sy <= min(n - 1, 2 * py + 3); ++sy) {
     for (int sx = max(0, 2 * px - 2); sx <= min(n - 1, 2 * px + 3); ++sx) {
       if (abs(sx - bx) <= 1 && abs(sy - by) <= 1) continue;
@@ -281,18 +287,30 @@ __global__ void __launch_bounds__(kB) k_fmm_m2l(FmmDev f, const int* stop) {
       for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[src * f.nd * f.p + e];
       __syncthreads();
       if (t < f.p) {
-        const int oi = 8 + (bx - sx + 3) + 7 * (by - sy + 3);
-        const double2* op = f.ops + (long long)oi * f.p * f.p;
+        const int oi = (bx - sx + 3) + 7 * (by - sy + 3);
+        const double2* opc = f.ops + (long long)(8 + oi) * f.p * f.p;
+        const double2* opl = f.ops + (long long)(57 + oi) * f.p * f.p;
         for (int k = 0; k < f.p; ++k) {
-          const double2 o = op[k * f.p + t];
-          for (int d = 0; d < f.nd; ++d) cfma(acc[d], o, sm[d * f.p + k]);
+          const double2 oc = opc[k * f.p + t];
+          for (int d = f.nlog; d < f.nd; ++d) cfma(acc[d], oc, sm[d * f.p + k]);
+          if (f.nlog) {
+            const double2 ol = opl[k * f.p + t];
+            for (int d = 0; d < f.nlog; ++d) cfma(acc[d], ol, sm[d * f.p + k]);
+          }
         }
+        if (t == 0)
+          for (int d = 0; d < f.nlog; ++d) {
+            acc[d].x += logs * sm[d * f.p].x;
+            acc[d].y += logs * sm[d * f.p].y;
+          }
       }
     }
   }
   if (t < f.p)
-    for (int d = 0; d < f.nd; ++d)
-      f.lc[(gb * f.nd + d) * f.p + t] = make_double2(acc[d].x / s, acc[d].y / s);
+    for (int d = 0; d < f.nd; ++d) {
+      const double sc = d < f.nlog ? 1.0 : 1.0 / s;
+      f.lc[(gb * f.nd + d) * f.p + t] = make_double2(acc[d].x * sc, acc[d].y * sc);
+    }
 }
 
 // L2L from level l to the children at level l + 1 (added to their M2L part).
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop
   const int nc = 2 << l;
   const int b = blockIdx.x, cx = b % nc, cy = b / nc;
   const long long child = lev_off(l + 1) + b;
-  if (f.count[child] == 0) return;
+  if (f.tcount[child] == 0) return;
   const long long parent = lev_off(l) + (cy >> 1) * (nc >> 1) + (cx >> 1);
   const int c = (cx & 1) + 2 * (cy & 1);
   const int t = threadIdx.x;
@@ -335,7 +353,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __rest
     const int i = f.perm[s0 + j];
     const double2 zi = make_double2(g.x[i], g.y[i]);
     const double2 u = make_double2((zi.x - c.x) / s, (zi.y - c.y) / s);
-    double2 F[3], dF[3];
+    double2 F[kMaxNd], dF[kMaxNd];
     for (int d = 0; d < f.nd; ++d) {
       // Horner for F and F' in u
       double2 h = sm[d * f.p + f.p - 1], dh = make_double2(0.0, 0.0);
@@ -385,6 +403,91 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __rest
   }
 }
 
+// Output densities at the boundary nodes (v = sqrt(w)-scaled total density):
+// Laplace channel 0 = q = w nu (logarithm); Stokes f = w (nu1 + i nu2):
+// channels f1, f2 (logarithm), f and f conj(z - c0) (Cauchy).
+__global__ void k_fmm_out_density(Geo g, int nd, double cx0, double cy0, const double* __restrict__ v, double2* Q) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.M; i += gridDim.x * blockDim.x) {
+    if (nd == 1) {
+      Q[i] = make_double2(g.sw[i] * v[i], 0.0);
+    } else {
+      const double2 fq = make_double2(g.sw[i] * v[2 * i], g.sw[i] * v[2 * i + 1]);
+      Q[4 * i] = make_double2(fq.x, 0.0);
+      Q[4 * i + 1] = make_double2(fq.y, 0.0);
+      Q[4 * i + 2] = fq;
+      Q[4 * i + 3] = cmul(fq, make_double2(g.x[i] - cx0, -(g.y[i] - cy0)));
+    }
+  }
+}
+
+// Output targets: z0 per body (Laplace) or z0, z0 + delta e1, z0 + delta e2
+// (Stokes); their leaves and the target counts of the leaves.
+__global__ void k_fmm_targets(Geo g, int per, int L, double x0, double y0, double D, double* tx, double* ty,
+                              int* tleaf, int* tcount_leaf) {
+  const int T = g.N * per, nb = 1 << L;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    const int i = t / per, k = t % per;
+    const double d = g.delta[i];
+    const double x = g.zx[i] + (k == 1 ? d : 0.0), y = g.zy[i] + (k == 2 ? d : 0.0);
+    tx[t] = x;
+    ty[t] = y;
+    int ix = (int)((x - x0) / D * nb), iy = (int)((y - y0) / D * nb);
+    ix = min(max(ix, 0), nb - 1);
+    iy = min(max(iy, 0), nb - 1);
+    tleaf[t] = iy * nb + ix;
+    atomicAdd(&tcount_leaf[iy * nb + ix], 1);
+  }
+}
+
+// Single layers at the output targets: local expansion plus the 3 x 3 near
+// leaves, in the layout of the direct output sums (Laplace: sum w nu log r^2;
+// Stokes: sum [-log|r| f + r (r . f)/|r|^2] as a 2-vector).
+__global__ void k_fmm_eval_targets(FmmDev f, Geo g, int kind, int T, const double* __restrict__ tx,
+                                   const double* __restrict__ ty, const int* __restrict__ tleaf, double c0x,
+                                   double c0y, double* __restrict__ part) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int b = tleaf[t], bx = b % f.nb, by = b / f.nb;
+  const long long box = lev_off(f.L) + b;
+  double s;
+  const double2 c = box_center(f, f.L, bx, by, s);
+  const double x = tx[t], y = ty[t];
+  const double2 u = make_double2((x - c.x) / s, (y - c.y) / s);
+  double2 val[kMaxNd];
+  for (int d = 0; d < f.nd; ++d) {
+    const double2* lc = f.lc + (box * f.nd + d) * f.p;
+    double2 h = lc[f.p - 1];
+    for (int l = f.p - 2; l >= 0; --l) h = cadd(cmul(h, u), lc[l]);
+    val[d] = h;
+  }
+  for (int ny = max(0, by - 1); ny <= min(f.nb - 1, by + 1); ++ny)
+    for (int nx = max(0, bx - 1); nx <= min(f.nb - 1, bx + 1); ++nx) {
+      const int nl = ny * f.nb + nx;
+      for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+        const int j = f.perm[k];
+        const double rx = x - g.x[j], ry = y - g.y[j];
+        const double r2 = rx * rx + ry * ry;
+        const double lg = 0.5 * log(r2);
+        for (int d = 0; d < f.nlog; ++d) val[d].x += f.Q[(long long)j * f.nd + d].x * lg;
+        const double2 inv = make_double2(rx / r2, -ry / r2);
+        for (int d = f.nlog; d < f.nd; ++d) cfma(val[d], f.Q[(long long)j * f.nd + d], inv);
+      }
+    }
+  if (kind == 0) {
+    part[t] = 2.0 * val[0].x;
+  } else {
+    double2 ftot = make_double2(0.0, 0.0);  // sum of f over all nodes: the level-2 moments a_0
+    for (int q = 0; q < 16; ++q) {
+      const long long b2 = lev_off(2) + q;
+      if (f.count[b2] > 0) ftot = cadd(ftot, f.mp[(b2 * f.nd + 2) * f.p]);
+    }
+    double2 w = cmul(make_double2(x - c0x, -(y - c0y)), val[2]);
+    w = make_double2(w.x - val[3].x, -(w.y - val[3].y));  // conj(conj(t - c0) F_f - F_{f conj(z - c0)})
+    part[2 * t] = -val[0].x + 0.5 * ftot.x + 0.5 * w.x;
+    part[2 * t + 1] = -val[1].x + 0.5 * ftot.y + 0.5 * w.y;
+  }
+}
+
 inline int grid_for(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
@@ -416,6 +519,17 @@ std::vector<std::complex<double>> build_ops(int p) {
       for (int l = 0; l < p; ++l)
         for (int k = 0; k < p; ++k)
           at(o, k, l) = ((l & 1) ? -1.0 : 1.0) * B(k + l, l) * std::pow(Dinv, k + l + 1);  // M2L
+      // logarithm kernel: log(d + u) = log d + sum_l (-1)^(l+1) (u/d)^l / l and
+      // (d + u)^-k = sum_l C(k+l-1, l) (-1)^l u^l d^-(k+l); the log s part of log d
+      // is added by the kernel
+      const int ol = o + 49;
+      at(ol, 0, 0) = std::log(C(dx, dy));
+      for (int l = 1; l < p; ++l) at(ol, 0, l) = ((l & 1) ? 1.0 : -1.0) * std::pow(Dinv, l) / (double)l;
+      for (int k = 1; k < p; ++k) {
+        at(ol, k, 0) = -std::pow(Dinv, k) / (double)k;
+        for (int l = 1; l < p; ++l)
+          at(ol, k, l) = -((l & 1) ? -1.0 : 1.0) * B(k + l - 1, l) * std::pow(Dinv, k + l) / (double)k;
+      }
     }
   return ops;
 }
@@ -430,6 +544,8 @@ struct FmmState {
   char* buf = nullptr;
   size_t buf_size = 0;
   int *leaf = nullptr, *perm = nullptr, *tmp = nullptr, *start = nullptr, *cursor = nullptr, *count = nullptr;
+  int *tcount = nullptr, *tleaf = nullptr;
+  double *tx = nullptr, *ty = nullptr;
   double2 *Q = nullptr, *mp = nullptr, *lc = nullptr;
   double* scal = nullptr;
   int pmax = 0;
@@ -489,12 +605,13 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   f->kind = kind;
   f->M = g.M;
   f->N = g.N;
-  const int nd = kind == 0 ? 1 : 3;
+  const int nd = kMaxNd;  // room for the output channels
   f->pmax = pmax;
   // buffers
   auto pad = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t need = 3 * pad((size_t)g.M * 4) + 2 * pad(((size_t)f->nleaf + 1) * 4) + pad((size_t)f->nbox * 4) +
-                      pad((size_t)g.M * nd * 16) + 2 * pad((size_t)f->nbox * nd * pmax * 16);
+  const size_t need = 3 * pad((size_t)g.M * 4) + 2 * pad(((size_t)f->nleaf + 1) * 4) + 2 * pad((size_t)f->nbox * 4) +
+                      pad((size_t)g.M * nd * 16) + 2 * pad((size_t)f->nbox * nd * pmax * 16) +
+                      pad((size_t)3 * g.N * 4) + 2 * pad((size_t)3 * g.N * 8);
   if (need > f->buf_size) {
     if (f->buf) cudaFreeAsync(f->buf, s);
     f->buf = nullptr;
@@ -514,6 +631,10 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   f->start = (int*)take(((size_t)f->nleaf + 1) * 4);
   f->cursor = (int*)take(((size_t)f->nleaf + 1) * 4);
   f->count = (int*)take((size_t)f->nbox * 4);
+  f->tcount = (int*)take((size_t)f->nbox * 4);
+  f->tleaf = (int*)take((size_t)3 * g.N * 4);
+  f->tx = (double*)take((size_t)3 * g.N * 8);
+  f->ty = (double*)take((size_t)3 * g.N * 8);
   f->Q = (double2*)take((size_t)g.M * nd * 16);
   f->mp = (double2*)take((size_t)f->nbox * nd * pmax * 16);
   f->lc = (double2*)take((size_t)f->nbox * nd * pmax * 16);
@@ -553,7 +674,7 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
     if (o.first == p) ops = o.second;
   if (!ops) return cudaErrorInvalidValue;  // fmm_setup prepares every order
   const int nd = kind == 0 ? 1 : 3;
-  FmmDev d{f->L, f->nb, p, nd, g.M, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count,
+  FmmDev d{f->L, f->nb, p, nd, g.M, 0, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->count,
            f->Q, f->mp, f->lc, ops};
   const size_t sm_exp = (size_t)nd * p * sizeof(double2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
@@ -565,6 +686,40 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
   k_fmm_eval<<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
   note_launches(4 + 2 * std::max(0, f->L - 2));
+  return cudaGetLastError();
+}
+
+}  // namespace bie
+
+namespace bie {
+
+// The output single layers at the interior targets by the FMM of order p
+// (logarithm and Cauchy channels on the source tree of fmm_setup).
+cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s) {
+  if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;
+  double2* ops = nullptr;
+  for (auto& o : f->ops)
+    if (o.first == p) ops = o.second;
+  if (!ops) return cudaErrorInvalidValue;
+  const int nd = kind == 0 ? 1 : 4, nlog = kind == 0 ? 1 : 2, per = kind == 0 ? 1 : 3;
+  const int T = g.N * per;
+  const double c0x = f->x0 + 0.5 * f->D, c0y = f->y0 + 0.5 * f->D;
+  cudaError_t e = cudaMemsetAsync(f->tcount, 0, (size_t)f->nbox * 4, s);
+  if (e != cudaSuccess) return e;
+  k_fmm_targets<<<grid_for(T), 256, 0, s>>>(g, per, f->L, f->x0, f->y0, f->D, f->tx, f->ty, f->tleaf,
+                                          f->tcount + lev_off(f->L));
+  for (int l = f->L - 1; l >= 0; --l) k_fmm_parent_counts<<<grid_for(1LL << (2 * l)), 256, 0, s>>>(l, f->tcount);
+  k_fmm_out_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, c0x, c0y, v, f->Q);
+  FmmDev d{f->L, f->nb, p, nd, g.M, nlog, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
+           f->Q, f->mp, f->lc, ops};
+  const size_t sm_exp = (size_t)nd * p * sizeof(double2);
+  const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
+  k_fmm_p2m<<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
+  k_fmm_m2l<<<(int)(lev_off(f->L + 1) - lev_off(2)), kB, sm_exp, s>>>(d, nullptr);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
+  k_fmm_eval_targets<<<grid_for(T), 256, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y, part);
+  note_launches(7 + f->L + 2 * std::max(0, f->L - 2));
   return cudaGetLastError();
 }
 

@@ -326,18 +326,11 @@ int output_splits(const Geo& g, int kind) {
   return P;
 }
 
-cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const double* load,
-                            double* partial, int P, double* out, double* cres, cudaStream_t s) {
-  // partial: [P][targets][comps] followed by N per-body constraint residuals and
-  // two net-load scalars
+cudaError_t finalize_output(const Geo& g, int kind, const double* v, const double* load, double* partial, int P,
+                            double* out, double* cres, cudaStream_t s) {
   const int targets = kind == 0 ? g.N : 3 * g.N;
   double* cbody = partial + (long long)P * targets * (kind == 0 ? 1 : 2);
   double* nl = cbody + g.N;
-  if (kind == 0)
-    k_out_lap<<<dim3(g.N, P), kB, 0, s>>>(g, v, partial, P);
-  else
-    k_out_stk<<<dim3(3 * g.N, P), kB, 0, s>>>(g, v, partial, P);
-  note_launches(1);
   k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
   note_launches(1);
   k_net_load<<<1, 32, 0, s>>>(g.N, kind, load, nl);
@@ -345,6 +338,18 @@ cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const doubl
   k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t evaluate_output(const Geo& g, int kind, const double* v, const double* load,
+                            double* partial, int P, double* out, double* cres, cudaStream_t s) {
+  // partial: [P][targets][comps] followed by N per-body constraint residuals and
+  // two net-load scalars
+  if (kind == 0)
+    k_out_lap<<<dim3(g.N, P), kB, 0, s>>>(g, v, partial, P);
+  else
+    k_out_stk<<<dim3(3 * g.N, P), kB, 0, s>>>(g, v, partial, P);
+  note_launches(1);
+  return finalize_output(g, kind, v, load, partial, P, out, cres, s);
 }
 
 cudaError_t unscale(const Geo& g, int kind, const double* v, double* out, cudaStream_t s) {

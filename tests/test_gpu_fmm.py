@@ -92,3 +92,38 @@ def test_solve_with_fmm(ctx, kind, prec):
     print(f"fmm solve kind={kind} prec={prec}: {err:.2e} {info}")
     assert err <= 1e-10
     assert info["rel_residual"] <= 1e-12
+
+
+def test_large_mobility_solve_with_fmm(ctx):
+    # 10,000 ellipses x 64 nodes: FMM pair sums and FMM output evaluation
+    g = synth.WORKLOADS["ellipses10000_M640000"]()
+    geo = geometry.nodes(g)
+    N, M = geo["N"], geo["M"]
+    UW = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    dens = torch.empty(2 * M, dtype=torch.float64, device="cuda")
+    rc, info = bie.mobility_solve(ctx, to_dev(g), torch.from_numpy(g["FT"].reshape(-1)).cuda(), UW, dens,
+                                  opts=bie.make_opts(precision=bie.MIXED_FF, fmm_order=36))
+    torch.cuda.synchronize()
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    print(f"large mobility: {info}")
+    nu = dens.cpu().numpy()
+    res = UW.cpu().numpy().reshape(N, 3)
+    # (1) outputs at 20 sampled bodies recomputed by the oracle from the density
+    pts = geometry.interior_points(geo)
+    idx = np.sort(np.random.default_rng(8).choice(N, 20, replace=False))
+    z0x, z0y, d = pts["z0x"][idx], pts["z0y"][idx], pts["delta"][idx]
+    u0 = stokes.single_layer_at(geo, nu, z0x, z0y)
+    u1 = stokes.single_layer_at(geo, nu, z0x + d, z0y)
+    u2 = stokes.single_layer_at(geo, nu, z0x, z0y + d)
+    om = ((u1[:, 1] - u0[:, 1]) - (u2[:, 0] - u0[:, 0])) / (2 * d)
+    ref = np.stack([u0[:, 0], u0[:, 1], om], 1)
+    assert rel2(res[idx], ref) < 1e-11
+    # (2) the density satisfies the oracle's equation at sampled rows
+    rows = np.sort(np.random.default_rng(9).choice(M, 8, replace=False))
+    lhs = _sampled_rows(geo, 1, nu, rows)
+    px, py = stokes.perp(geo)
+    b = geo["body"][rows]
+    FT = g["FT"]
+    rhs = np.stack([FT[b, 0] + FT[b, 2] * px[rows], FT[b, 1] + FT[b, 2] * py[rows]], 1).reshape(-1)
+    assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-10
+    assert info["rel_residual"] <= 1e-12
