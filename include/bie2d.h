@@ -123,7 +123,10 @@ typedef struct {
   int32_t fmm_order;     /* 0: direct pair sums; p in 2..64: the pair sums are evaluated by the
                             quadtree FMM (FP64 expansions) with order p for residuals and FP64
                             GMRES, and order ceil(p/2) for the inner solves of the refinement */
-  int32_t reserved;
+  int32_t precond;       /* mixed: right preconditioner of the inner solves; 0: block Jacobi
+                            (one block per body, the body's own diagonal block of the inner
+                            operator inverted in FP32; bodies over 640 unknowns keep the
+                            identity), 1: none */
 } bie_opts;
 
 typedef struct {

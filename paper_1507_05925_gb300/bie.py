@@ -18,6 +18,7 @@ OK, WARN_NONNEUTRAL, WARN_NOT_CONVERGED = 0, 1, 2
 ERR_INVALID, ERR_OUTSIDE, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -5
 LAPLACE, STOKES = 0, 1
 FP64, MIXED, MIXED_FF = 0, 1, 2
+PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1
 
 
 class BieGeometry(ctypes.Structure):
@@ -32,7 +33,7 @@ class BieOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("formulation", ctypes.c_int32), ("max_refine", ctypes.c_int32),
-                ("inner_tol", ctypes.c_double), ("fmm_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double), ("fmm_order", ctypes.c_int32), ("precond", ctypes.c_int32)]
 
 
 class BieInfo(ctypes.Structure):
@@ -176,8 +177,8 @@ def make_geometry(geom) -> tuple[BieGeometry, list]:
 
 
 def make_opts(tol=1e-12, max_iter=500, restart=50, precision=FP64, formulation=0,
-              max_refine=8, inner_tol=1e-6, fmm_order=0) -> BieOpts:
-    return BieOpts(tol, max_iter, restart, precision, formulation, max_refine, inner_tol, fmm_order, 0)
+              max_refine=8, inner_tol=1e-6, fmm_order=0, precond=0) -> BieOpts:
+    return BieOpts(tol, max_iter, restart, precision, formulation, max_refine, inner_tol, fmm_order, precond)
 
 
 class Context:

@@ -119,6 +119,12 @@ struct Work {
   // solver
   double *V = nullptr, *f = nullptr, *xs = nullptr, *r = nullptr, *d = nullptr, *rin = nullptr, *ytmp = nullptr;
   double* rc = nullptr;
+  // block-Jacobi preconditioner of the inner solves
+  long long* bj_off = nullptr;
+  int* bj_pairs = nullptr;
+  float* bj_blocks = nullptr;
+  double* zbuf = nullptr;
+  int bj_max_nb = 0;
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
   double *h1 = nullptr, *h2 = nullptr, *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
   KState* st = nullptr;
@@ -127,7 +133,7 @@ struct Work {
 };
 
 void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool stage_in, bool stage_ipt,
-           bool stage_load, bool stage_io) {
+           bool stage_load, bool stage_io, long long bj_floats = 0) {
   const int comps = kind + 1;
   const long long n = (long long)M * comps;
   w.kind = kind;
@@ -201,6 +207,12 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.outpart = A.take<double>((size_t)w.P * targets * comps + N + 2);
     w.outv = A.take<double>(3 * N);
     w.cres = A.take<double>(1);
+    if (bj_floats > 0) {
+      w.bj_off = A.take<long long>(N + 1);
+      w.bj_pairs = A.take<int>(N);
+      w.bj_blocks = A.take<float>((size_t)bj_floats);
+      w.zbuf = A.take<double>(n);
+    }
   }
 }
 
@@ -357,7 +369,15 @@ struct Op {
   int prec;
   double alpha = 0.0;
   int fmm_p = 0;
+  bool precond = false;  // right block-Jacobi: out = A P in
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
+    if (precond) {
+      cudaError_t e = bj_apply(w->g, w->kind, w->bj_off, w->bj_blocks, in, w->zbuf, stop, w->bj_max_nb, s);
+      if (e != cudaSuccess) return e;
+      Op plain = *this;
+      plain.precond = false;
+      return plain.apply(vec(w->zbuf), out, stop, s, valid);
+    }
     if (fmm_p > 0) {
       const PairPlan one{1, w->g.M};
       cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s);
@@ -414,7 +434,7 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   long long alpha_bits;
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
   const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
-                             w.kind, w.m, op.prec * 1000 + op.fmm_p, alpha_bits, p.S * 1000003LL + p.chunk,
+                             w.kind, w.m, op.prec * 1000 + op.fmm_p + (op.precond ? 500 : 0), alpha_bits, p.S * 1000003LL + p.chunk,
                              w.grid};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
@@ -484,14 +504,24 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
   CK(fill0(x, n, s));
   CK(residual_start(b, nullptr, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
-  const Op rop = verify ? Op{ctx, &w, 0} : op;
+  Op rop = verify ? Op{ctx, &w, 0} : op;
+  rop.precond = false;  // residuals of x itself (x = P y is kept in original variables)
   int rc;
   for (;;) {
     if ((rc = run_cycle(ctx, w, op, s))) return rc;
     const KState h = *ctx->h_state;
     out.bnorm = h.scratch[1];
     out.iters = h.iters;
-    if (h.j > 0) CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, x, w.grid, s));
+    if (h.j > 0) {
+      if (op.precond) {  // x += P (V y)
+        CK(fill0(w.ytmp, n, s));
+        CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, w.ytmp, w.grid, s));
+        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s));
+        CK(axpy(x, w.zbuf, n, s));
+      } else {
+        CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, x, w.grid, s));
+      }
+    }
     out.matvecs += h.j;
     if (h.j == 0) {  // nothing to do: b is (numerically) zero or the cap is reached
       out.res = h.rnorm;
@@ -531,13 +561,14 @@ void fill_opts(const bie_opts* o, bie_opts& r) {
   r.max_refine = 8;
   r.inner_tol = 1e-6;
   r.fmm_order = 0;
-  r.reserved = 0;
+  r.precond = 0;
   if (!o) return;
   if (o->tol > 0) r.tol = o->tol;
   if (o->max_iter > 0) r.max_iter = o->max_iter;
   if (o->restart > 0) r.restart = std::min(o->restart, 200);
   r.precision = o->precision;
   r.formulation = o->formulation;
+  r.precond = o->precond;
   if (o->max_refine > 0) r.max_refine = o->max_refine;
   if (o->inner_tol > 0) r.inner_tol = o->inner_tol;
   r.fmm_order = o->fmm_order;
@@ -554,18 +585,24 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED && o.precision != BIE_PREC_MIXED_FF)
     return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64, BIE_PREC_MIXED or BIE_PREC_MIXED_FF");
   if (o.formulation != 0 && o.formulation != 1) return fail(ctx, BIE_ERR_INVALID, "formulation must be 0 or 1");
+  if (o.precond != 0 && o.precond != 1) return fail(ctx, BIE_ERR_INVALID, "precond must be 0 or 1");
   if (o.fmm_order != 0 && (o.fmm_order < 2 || o.fmm_order > 64))
     return fail(ctx, BIE_ERR_INVALID, "fmm_order must be 0 or in 2..64");
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
   const int nload = kind == 0 ? N : 3 * N;
   Work w;
+  const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
+  const long long bjf = use_bj ? bj_block_floats(bs.data(), N, kind) : 0;
   Arena sz{nullptr};
-  carve(sz, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
+  carve(sz, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false, bjf);
   if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
   Arena ar{ctx->ws};
-  carve(ar, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false);
+  carve(ar, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false, bjf);
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  if (bjf > 0) {
+    for (int i = 0; i < N; ++i) w.bj_max_nb = std::max(w.bj_max_nb, (bs[i + 1] - bs[i]) * (kind + 1));
+  }
   const double* dload;
   if ((rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
   if ((rc = check_inside(ctx, w, s))) return rc;
@@ -574,6 +611,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     const int orders[2] = {p_res, std::max(2, p_in)};
     if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err))) return rc;
   }
+  if (bjf > 0) CK(bj_setup(w.g, kind, kInnerCompletionWeight, bs.data(), w.bj_off, w.bj_pairs, w.bj_blocks, s));
 
   const long long n = w.n;
   // right-hand side (scaled by sqrt(w))
@@ -587,7 +625,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
   const int fres = o.fmm_order > 0 ? p_res : 0, fin = o.fmm_order > 0 ? std::max(2, p_in) : 0;
-  const Op op64{ctx, &w, 0, 0.0, fres}, op32{ctx, &w, 1, kInnerCompletionWeight, fin};
+  const Op op64{ctx, &w, 0, 0.0, fres}, op32{ctx, &w, 1, kInnerCompletionWeight, fin, bjf > 0};
   // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF (direct sums),
   // or the FMM of the full order
   const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0, 0.0, fres};
@@ -724,6 +762,18 @@ void release_workspace(bie_ctx* ctx, cudaStream_t s) {
 }
 }  // namespace bie
 
+namespace bie {
+size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart) {
+  const int n_nodes = body_start_host[n_bodies];
+  Work w;
+  Arena sz{nullptr};
+  const int m = restart > 0 ? std::min(restart, 200) : 50;
+  carve(sz, w, n_bodies, n_nodes, kind, m, true, true, true, true, false,
+        bj_block_floats(body_start_host, n_bodies, kind));
+  return sz.off;
+}
+}  // namespace bie
+
 extern "C" {
 
 int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, const double* in, double* out,
@@ -759,13 +809,13 @@ int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int ord
   return BIE_OK;
 }
 
+
 size_t bie_workspace_bytes(int kind, int n_bodies, int n_nodes, int restart) {
   if (n_bodies < 1 || n_nodes < 1 || (kind != 0 && kind != 1)) return 0;
-  Work w;
-  Arena sz{nullptr};
-  const int m = restart > 0 ? std::min(restart, 200) : 50;
-  carve(sz, w, n_bodies, n_nodes, kind, m, true, true, true, true, false);
-  return sz.off;
+  // preconditioner blocks sized for bodies of equal size
+  std::vector<int> bs(n_bodies + 1);
+  for (int i = 0; i <= n_bodies; ++i) bs[i] = (int)((long long)n_nodes * i / n_bodies);
+  return bie::workspace_bytes_for(kind, bs.data(), n_bodies, restart);
 }
 
 int bie_profile(bie_ctx* ctx, int enable, bie_profile_counters* out) {

@@ -146,6 +146,18 @@ void fmm_free(FmmState* f, cudaStream_t s);
 // layout of evaluate_output's direct sums).
 cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s);
 
+// workspace of a solve with the given host body_start (bie_workspace_bytes assumes equal bodies)
+size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart);
+
+// ---------------------------------------------------------------- precond.cu
+// Block-Jacobi (per body) preconditioner of the weighted-completion operator.
+long long bj_block_floats(const int* body_start_host, int N, int kind);
+cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
+                     int* pair_dev, float* blocks, cudaStream_t s);
+// z = P v (v scaled, z scaled)
+cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
+                     const int* stop, int max_nb, cudaStream_t s);
+
 // ---------------------------------------------------------------- krylov.cu
 int vec_grid(long long n);
 // h[i] = <V_i, w> for i <= j (first CGS pass)

@@ -1,0 +1,355 @@
+// Block-Jacobi preconditioner for the FP32 inner solves of the refinement.
+//
+// The inner operator is the second-kind operator with the per-body weighted
+// completion (sqrt(w)-scaled).  Its diagonal block for body i,
+//   B_i = 1/2 I + D (K_ii + C_i L_ii) D^{-1}     (Laplace: n_i x n_i; Stokes: 2n_i x 2n_i)
+// is assembled in FP32 (from FP64 coordinate differences) directly in shared
+// memory and inverted in place by blocked Gauss-Jordan elimination without
+// pivoting: the blocks are 1/2 I + compact, their pivots stay near 1/2 and
+// their condition numbers are small, so no pivoting is needed (an FP32 inverse
+// accurate to ~1e-6 is far more than a preconditioner needs).  A block of
+// nb <= 128 unknowns is inverted by one CTA; nb <= 448 by a cluster of four
+// CTAs and nb <= 640 by one of eight, each CTA holding a slice of the columns
+// and reading the pivot panels of the others through distributed shared
+// memory; larger blocks are left as the identity.  The inverses are stored
+// column-major in FP32.  Preconditioning is applied from the right, z = P v,
+// so the GMRES residual stays the true residual.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/bie2d.h"
+#include "bie_internal.cuh"
+#include "reduce.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace bie {
+
+namespace {
+
+constexpr int kMaxSingle = 128;  // one CTA
+constexpr int kMaxBlock4 = 448;  // cluster of four CTAs
+constexpr int kMaxBlock = 640;   // cluster of eight CTAs; larger bodies keep the identity
+constexpr int kPB = 16;          // panel width of the blocked elimination
+constexpr int kMaxThreads = 640; // one thread per row
+constexpr int kBA = 256;         // threads of an application CTA
+constexpr int kApplyRows = 64, kApplyGroups = kBA / kApplyRows;
+
+// Shared-memory leading dimension of a column: odd, so that reading a row
+// (stride ld across threads) is free of bank conflicts.
+__host__ __device__ __forceinline__ int gj_ld(int nb) { return nb | 1; }
+// Columns per CTA of a cluster of cs CTAs: a multiple of the panel width, so
+// that each panel lies in one CTA.
+__host__ __device__ __forceinline__ int gj_cols(int nb, int cs) {
+  return ((nb + cs - 1) / cs + kPB - 1) / kPB * kPB;
+}
+__host__ __device__ __forceinline__ size_t gj_smem_floats(int nb, int cs) {
+  const int h = gj_cols(nb, cs);
+  return (size_t)gj_ld(nb) * h + (size_t)h * kPB + 2 * kPB;
+}
+
+// Entry (row r, column c) of the inner operator's diagonal block of body i
+// (sqrt(w)-scaled, weighted completion), in FP32 from FP64 coordinate
+// differences.
+struct BlockRow {
+  int kind, a0;
+  float cf, ct;
+  double xc, yc;
+  // row data
+  double xa, ya;
+  float nxa, nya, swa, ka, pa0, pa1;
+  int al, a;
+  __device__ BlockRow(const Geo& g, int kind_, int i, int r, double alpha) : kind(kind_) {
+    a0 = g.body_start[i];
+    cf = (float)(alpha / g.len[i]);
+    ct = kind == 1 ? (float)(alpha / g.W[i]) : 0.f;
+    xc = g.xc[i];
+    yc = g.yc[i];
+    a = a0 + (kind == 1 ? r >> 1 : r);
+    al = kind == 1 ? r & 1 : 0;
+    xa = g.x[a];
+    ya = g.y[a];
+    nxa = (float)g.nx[a];
+    nya = (float)g.ny[a];
+    swa = (float)g.sw[a];
+    ka = (float)g.kappa[a];
+    pa0 = (float)(-(ya - yc));
+    pa1 = (float)(xa - xc);
+  }
+  __device__ float entry(const Geo& g, int r, int c) const {
+    const int b = a0 + (kind == 1 ? c >> 1 : c);
+    const float swb = (float)g.sw[b];
+    float k;
+    if (kind == 0) {
+      if (a == b) {
+        k = -ka * (float)kInv4Pi;
+      } else {
+        const float rx = (float)(xa - g.x[b]), ry = (float)(ya - g.y[b]);
+        k = -(float)kInv2Pi * (rx * nxa + ry * nya) / (rx * rx + ry * ry);
+      }
+      return (r == c ? 0.5f : 0.f) + swa * swb * (k + cf);
+    }
+    const int be = c & 1;
+    if (a == b) {
+      const float t[2] = {-nya, nxa};
+      k = -0.5f * (float)kInvPi * ka * t[al] * t[be];
+    } else {
+      const float rv[2] = {(float)(xa - g.x[b]), (float)(ya - g.y[b])};
+      const float r2 = rv[0] * rv[0] + rv[1] * rv[1];
+      const float rn = rv[0] * nxa + rv[1] * nya;
+      k = -(float)kInvPi * rv[al] * rv[be] * rn / (r2 * r2);
+    }
+    const float pb = be == 0 ? (float)(-(g.y[b] - yc)) : (float)(g.x[b] - xc);
+    const float pa = al == 0 ? pa0 : pa1;
+    return (r == c ? 0.5f : 0.f) + swa * swb * (k + (al == be ? cf : 0.f) + ct * pa * pb);
+  }
+};
+
+// A_:j += F G_j for the local columns [j0, j1) of row r (F = this row of the
+// panel minus E_K, G_j = rows K of column j).
+__device__ __forceinline__ void rank_update(float* __restrict__ A, const float* __restrict__ G, int ld, int r,
+                                            const float (&fr)[kPB], int j0, int j1) {
+  for (int j = j0; j < j1; ++j) {
+    const float4* gj = reinterpret_cast<const float4*>(G + j * kPB);
+    float acc = A[j * ld + r];
+#pragma unroll
+    for (int q = 0; q < kPB / 4; ++q) {
+      const float4 v = gj[q];
+      acc = fmaf(fr[4 * q], v.x, acc);
+      acc = fmaf(fr[4 * q + 1], v.y, acc);
+      acc = fmaf(fr[4 * q + 2], v.z, acc);
+      acc = fmaf(fr[4 * q + 3], v.w, acc);
+    }
+    A[j * ld + r] = acc;
+  }
+}
+
+// Assembly and in-place inversion of one diagonal block by a cluster of CS CTAs
+// (CS = 1: one CTA).  CTA q holds the columns [q h, min(nb, (q+1) h)) and all
+// rows, one thread per row.  Blocked Gauss-Jordan without pivoting: for each
+// panel K of kPB pivots, the owning CTA eliminates the panel's own columns in
+// registers, after which its columns hold [inv(A_KK); -A_RK inv(A_KK)]; every
+// CTA then applies the rank-kPB update A_:j += (panel - E_K) A_Kj to its other
+// columns, reading the panel from the owner's shared memory.  The panel stays
+// unchanged until the owner's next update, which follows the next panel's
+// cluster barrier, which no CTA reaches before it is done reading.
+template <int CS>
+__global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, double alpha,
+                                                           const int* __restrict__ list,
+                                                           const long long* __restrict__ off,
+                                                           float* __restrict__ blocks) {
+  extern __shared__ float sm[];
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int i = list[blockIdx.x / CS];
+  const int nb = (g.body_start[i + 1] - g.body_start[i]) * (kind + 1);
+  const int ld = gj_ld(nb), h = gj_cols(nb, CS);
+  const int c0 = min(nb, rank * h), nc = min(nb, c0 + h) - c0;
+  float* A = sm;                 // ld x h, column-major
+  float* G = A + (size_t)ld * h; // h x kPB: rows K of the local columns
+  float* rowbuf = G + (size_t)h * kPB;  // [2][kPB] pivot rows of the panel steps
+  const int r = threadIdx.x;
+  const bool live = r < nb;
+  if (live) {
+    const BlockRow br(g, kind, i, r, alpha);
+    for (int j = 0; j < nc; ++j) A[j * ld + r] = br.entry(g, r, c0 + j);
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < nb; k0 += kPB) {
+    const int bsz = min(kPB, nb - k0);
+    const int owner = k0 / h;
+    if (rank == owner) {
+      // panel elimination in registers: thread r holds row r of the panel
+      const int lj = k0 - c0;
+      float pr[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) pr[t] = (live && t < bsz) ? A[(lj + t) * ld + r] : 0.f;
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        if (t < bsz) {
+          float* rb = rowbuf + (t & 1) * kPB;
+          if (r == k0 + t) {
+#pragma unroll
+            for (int u = 0; u < kPB; ++u) rb[u] = pr[u];
+          }
+          __syncthreads();
+          const float ip = 1.0f / rb[t];
+          if (r == k0 + t) {
+#pragma unroll
+            for (int u = 0; u < kPB; ++u) pr[u] = (u == t) ? ip : pr[u] * ip;
+          } else {
+            const float fr = pr[t] * ip;
+#pragma unroll
+            for (int u = 0; u < kPB; ++u) pr[u] = (u == t) ? -fr : fmaf(-fr, rb[u], pr[u]);
+          }
+        }
+      }
+      if (live) {
+#pragma unroll
+        for (int t = 0; t < kPB; ++t)
+          if (t < bsz) A[(lj + t) * ld + r] = pr[t];
+      }
+    }
+    // rows K of the local columns, before any of them changes
+    for (int e = threadIdx.x; e < nc * bsz; e += blockDim.x) {
+      const int j = e / bsz, t = e % bsz;
+      G[j * kPB + t] = A[j * ld + k0 + t];
+    }
+    if constexpr (CS > 1) {
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+    }
+    if (live) {
+      const float* P = A + (k0 - owner * h) * ld;  // the panel in the owner's shared memory
+      if constexpr (CS > 1) P = cg::this_cluster().map_shared_rank(P, owner);
+      float fr[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) fr[t] = t < bsz ? P[t * ld + r] - (r == k0 + t ? 1.f : 0.f) : 0.f;
+      // all local columns but the panel's own (owner: [k0 - c0, k0 - c0 + bsz))
+      const int s0 = rank == owner ? k0 - c0 : nc, s1 = rank == owner ? k0 - c0 + bsz : nc;
+      rank_update(A, G, ld, r, fr, 0, s0);
+      rank_update(A, G, ld, r, fr, s1, nc);
+    }
+    __syncthreads();
+  }
+  if constexpr (CS > 1) cg::this_cluster().sync();  // no CTA leaves while the last panel is read
+  float* B = blocks + off[i];
+  if (live)
+    for (int j = 0; j < nc; ++j) B[(long long)(c0 + j) * nb + r] = A[j * ld + r];
+}
+
+// z = P v: z_i = B_i^{-1} v_i per body (identity for bodies left out).  CTA
+// (i, y) computes rows [64 y, 64 y + 64) of body i with four column groups of
+// 64 threads, reduced in shared memory; each warp reads 32 consecutive rows of
+// one column (coalesced).
+__global__ void __launch_bounds__(kBA) k_bj_apply(Geo g, int kind, const long long* __restrict__ off,
+                                                  const float* __restrict__ blocks, VecRef vr, double* __restrict__ z,
+                                                  const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ float vs[];
+  __shared__ float part[kBA];
+  const double* v = vr.ptr();
+  const int i = blockIdx.x;
+  const int c = kind + 1;
+  const int a0 = g.body_start[i] * c, nb = (g.body_start[i + 1] - g.body_start[i]) * c;
+  const int r0 = blockIdx.y * kApplyRows;
+  if (r0 >= nb) return;
+  const int lr = threadIdx.x % kApplyRows, grp = threadIdx.x / kApplyRows;
+  const int r = r0 + lr;
+  if (nb > kMaxBlock) {
+    if (grp == 0 && r < nb) z[a0 + r] = v[a0 + r];
+    return;
+  }
+  for (int e = threadIdx.x; e < nb; e += kBA) vs[e] = (float)v[a0 + e];
+  __syncthreads();
+  const float* B = blocks + off[i];
+  float acc = 0.f;
+  if (r < nb) {
+    const int per = (nb + kApplyGroups - 1) / kApplyGroups;
+    const int cb = grp * per, ce = min(nb, cb + per);
+#pragma unroll 4
+    for (int col = cb; col < ce; ++col) acc = fmaf(B[(long long)col * nb + r], vs[col], acc);
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (grp == 0 && r < nb) {
+    float t = part[lr];
+#pragma unroll
+    for (int q = 1; q < kApplyGroups; ++q) t += part[q * kApplyRows + lr];
+    z[a0 + r] = (double)t;
+  }
+}
+
+}  // namespace
+
+long long bj_block_floats(const int* body_start_host, int N, int kind) {
+  long long s = 0;
+  for (int i = 0; i < N; ++i) {
+    const long long nb = (long long)(body_start_host[i + 1] - body_start_host[i]) * (kind + 1);
+    if (nb <= kMaxBlock) s += nb * nb;
+  }
+  return s;
+}
+
+namespace {
+
+// Launch of k_bj_factor<CS> over count bodies of list, one thread per row.
+template <int CS>
+cudaError_t launch_factor(const Geo& g, int kind, double alpha, const int* list, int count, int threads, size_t smem,
+                          const long long* off, float* blocks, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_bj_factor<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS * count);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CS > 1 ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, k_bj_factor<CS>, g, kind, alpha, list, off, blocks);
+  note_launches(1);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
+                     int* list_dev, float* blocks, cudaStream_t s) {
+  // bodies by kernel: one CTA (nb <= 128), clusters of four (<= 448) and eight (<= 640) CTAs
+  constexpr int kCs[3] = {1, 4, 8};
+  std::vector<long long> off(g.N + 1, 0);
+  std::vector<int> lists[3];
+  int max_nb[3] = {0, 0, 0};
+  size_t smem[3] = {0, 0, 0};
+  for (int i = 0; i < g.N; ++i) {
+    const int nb = (body_start_host[i + 1] - body_start_host[i]) * (kind + 1);
+    off[i + 1] = off[i] + (nb <= kMaxBlock ? (long long)nb * nb : 0);
+    const int c = nb <= kMaxSingle ? 0 : nb <= kMaxBlock4 ? 1 : nb <= kMaxBlock ? 2 : -1;
+    if (c < 0) continue;
+    lists[c].push_back(i);
+    max_nb[c] = std::max(max_nb[c], nb);
+    smem[c] = std::max(smem[c], gj_smem_floats(nb, kCs[c]) * sizeof(float));
+  }
+  std::vector<int> all;
+  for (const auto& l : lists) all.insert(all.end(), l.begin(), l.end());
+  cudaError_t e = cudaMemcpyAsync(off_dev, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if (!all.empty()) {
+    e = cudaMemcpyAsync(list_dev, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  size_t at = 0;
+  for (int c = 0; c < 3; ++c) {
+    const int count = (int)lists[c].size();
+    if (count == 0) continue;
+    const int threads = (max_nb[c] + 31) / 32 * 32;
+    const int* l = list_dev + at;
+    e = c == 0   ? launch_factor<1>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s)
+        : c == 1 ? launch_factor<4>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s)
+                 : launch_factor<8>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s);
+    if (e != cudaSuccess) return e;
+    at += count;
+  }
+  // the host vectors must outlive the asynchronous copies
+  return cudaStreamSynchronize(s);
+}
+
+cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
+                     const int* stop, int max_nb, cudaStream_t s) {
+  const dim3 grid(g.N, (max_nb + kApplyRows - 1) / kApplyRows);
+  k_bj_apply<<<grid, kBA, (size_t)std::min(max_nb, kMaxBlock) * sizeof(float), s>>>(g, kind, off_dev, blocks, v, z,
+                                                                                     stop);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace bie

@@ -155,18 +155,20 @@ int bie_server_submit(bie_server* s, const bie_request* req, int64_t* ticket) {
   if ((req->kind != BIE_KIND_LAPLACE && req->kind != BIE_KIND_STOKES) || g.n_bodies < 1 || !g.body_start ||
       !req->load || !req->out)
     return BIE_ERR_INVALID;
-  // total node count from body_start (host or device)
-  int M = 0;
-  const int32_t* last = g.body_start + g.n_bodies;
+  // body_start (host or device) sizes the workspace
+  std::vector<int> bs(g.n_bodies + 1);
   if (is_device(g.body_start)) {
     cudaSetDevice(s->device);
-    if (cudaMemcpy(&M, last, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BIE_ERR_CUDA;
+    if (cudaMemcpy(bs.data(), g.body_start, bs.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return BIE_ERR_CUDA;
   } else {
-    M = *last;
+    std::copy(g.body_start, g.body_start + g.n_bodies + 1, bs.begin());
   }
-  if (M < 8) return BIE_ERR_INVALID;
+  if (bs[g.n_bodies] < 8) return BIE_ERR_INVALID;
+  for (int i = 0; i < g.n_bodies; ++i)
+    if (bs[i + 1] < bs[i]) return BIE_ERR_INVALID;
   cudaSetDevice(s->device);
-  const size_t need = bie_workspace_bytes(req->kind, g.n_bodies, M, req->opts.restart);
+  const size_t need = bie::workspace_bytes_for(req->kind, bs.data(), g.n_bodies, req->opts.restart);
   if (s->cap && need > s->cap) return BIE_ERR_NOMEM;
   Job* j = new Job();
   j->req = *req;

@@ -151,6 +151,83 @@ def test_mobility_solve(ctx, name, prec, form):
 
 
 # ---------------------------------------------------------------------------
+# block-Jacobi preconditioner of the inner solves: every inversion path
+# (one CTA, clusters of four and eight CTAs, identity for large bodies)
+# ---------------------------------------------------------------------------
+def _precond_paths(kind):
+    # unknowns per body: one CTA (<= 128), four-CTA cluster (<= 448),
+    # eight-CTA cluster (<= 640), identity (> 640)
+    n = (64, 200, 500, 700) if kind == 0 else (48, 150, 260, 330)
+    curves = [synth.ellipse(0.0, 0.0, 1.0, 0.6, 0.3, n[0]), synth.star(3.0, 0.2, 1.0, 0.2, 5, 0.1, n[1]),
+              synth.ellipse(0.3, 3.1, 1.2, 0.5, -0.4, n[2]), synth.star(3.4, 3.2, 1.1, 0.15, 3, 0.7, n[3])]
+    return synth.assemble(curves)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("prec", [bie.MIXED, bie.MIXED_FF])
+def test_block_jacobi_paths(ctx, kind, prec):
+    g = _precond_paths(kind)
+    N = g["body_start"].size - 1
+    if kind == 0:
+        load = synth.charges(N, np.random.default_rng(21))
+        ref = laplace.solve(g, load)["phi"]
+        fn, nout = bie.elastance_solve, N
+    else:
+        FT = synth.forces_torques(N, np.random.default_rng(22))
+        load = FT.reshape(-1)
+        ref = stokes.solve(g, FT)["UW"].reshape(-1)
+        fn, nout = bie.mobility_solve, 3 * N
+    infos = []
+    for pc in (bie.PRECOND_BLOCK_JACOBI, bie.PRECOND_NONE):
+        out = torch.empty(nout, dtype=torch.float64, device="cuda")
+        rc, info = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out,
+                      opts=bie.make_opts(precision=prec, precond=pc))
+        torch.cuda.synchronize()
+        assert rc == bie.OK, (rc, ctx.last_error(), info)
+        e = rel2(out.cpu().numpy(), ref)
+        print(f"precond={pc} kind={kind} prec={prec}: {e:.2e} {info}")
+        assert e <= TOL_SOLVE
+        assert info["rel_residual"] <= 1e-12
+        infos.append(info)
+    # widely separated bodies: the blocks are well conditioned already, and the
+    # preconditioner must not cost iterations
+    assert infos[0]["matvecs_fp32"] <= infos[1]["matvecs_fp32"]
+
+
+@pytest.mark.parametrize("wl,kind", [("stars100_M25600", 0), ("stars100_M25600", 1)])
+def test_block_jacobi_cuts_inner_iterations(ctx, wl, kind):
+    # 100 five- and three-armed stars: the self-interaction of each body is what
+    # the unpreconditioned inner GMRES spends its iterations on
+    g = synth.WORKLOADS[wl]()
+    N = g["body_start"].size - 1
+    if kind == 0:
+        load, fn, nout = synth.charges(N, np.random.default_rng(23)), bie.elastance_solve, N
+    else:
+        load, fn, nout = synth.forces_torques(N, np.random.default_rng(24)).reshape(-1), bie.mobility_solve, 3 * N
+    res, infos = [], []
+    for pc in (bie.PRECOND_BLOCK_JACOBI, bie.PRECOND_NONE):
+        out = torch.empty(nout, dtype=torch.float64, device="cuda")
+        rc, info = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out,
+                      opts=bie.make_opts(precision=bie.MIXED_FF, precond=pc))
+        torch.cuda.synchronize()
+        assert rc == bie.OK, (rc, ctx.last_error(), info)
+        print(f"{wl} kind={kind} precond={pc}: {info}")
+        res.append(out.cpu().numpy())
+        infos.append(info)
+    assert rel2(res[0], res[1]) <= TOL_SOLVE
+    assert infos[0]["matvecs_fp32"] < 0.75 * infos[1]["matvecs_fp32"]
+
+
+def test_precond_option_validated(ctx):
+    g = ragged4()
+    N = g["body_start"].size - 1
+    out = torch.empty(N, dtype=torch.float64, device="cuda")
+    rc, _ = bie.elastance_solve(ctx, to_dev(g), torch.zeros(N, dtype=torch.float64, device="cuda"), out,
+                                opts=bie.make_opts(precision=bie.MIXED, precond=2))
+    assert rc == bie.ERR_INVALID
+
+
+# ---------------------------------------------------------------------------
 # closed forms evaluated by the GPU path
 # ---------------------------------------------------------------------------
 def test_gpu_closed_forms(ctx):
