@@ -163,33 +163,57 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ pf, const f
 
 // Far tiles: plain FP32 coordinates relative to the target block's centre.
 // Their rounding (|x'| 2^-24 with |x'| at most ~3 |r| for far pairs) is
-// below 2e-7 of each term.
+// below 2e-7 of each term.  The two lanes of the packed FP32x2 instructions
+// hold two sources for the same target, read as one 16-byte pair
+// (-x'_l, -x'_l+1, -y'_l, -y'_l+1), so that D = T + (-P) = r.  On GB300 the
+// FMA pipe retires 128 FP32 lanes a clock per SM whether packed or not, so
+// packing halves the issue slots, not the pipe cycles; the loop costs 7 FP32
+// lane operations and one MUFU reciprocal a pair.  (Sharing one MUFU operation
+// between two reciprocals, 1/a = b rcp(ab), costs 1.5 more FP32 operations a
+// pair and measured slower.)
 template <int KIND>
-__device__ __forceinline__ void tile_far(const float4* __restrict__ sp, int nt, const float* tlx,
-                                         const float* tly, const float* tnx, const float* tny, float* ax,
-                                         float* ay) {
+__device__ __forceinline__ void tile_far2(const float4* __restrict__ sp2, const float4* __restrict__ sq2, int np,
+                                          const float2* TX, const float2* TY, const float2* NX, const float2* NY,
+                                          float2* AX, float2* AY) {
 #pragma unroll 2
-  for (int l = 0; l < nt; ++l) {
-    const float4 p = sp[l];  // (x', y', q1, q2)
+  for (int l = 0; l < np; ++l) {
+    const float4 p = sp2[l];
+    const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);
+    float2 q1, q2;
+    if (KIND == 0) {
+      q1 = reinterpret_cast<const float2*>(sq2)[l];
+    } else {
+      const float4 q = sq2[l];
+      q1 = make_float2(q.x, q.y);
+      q2 = make_float2(q.z, q.w);
+    }
 #pragma unroll
     for (int k = 0; k < kT32; ++k) {
-      const float dx = tlx[k] - p.x;
-      const float dy = tly[k] - p.y;
-      const float r2 = fmaf(dx, dx, dy * dy);
-      const float inv = rcp_approx(r2);
+      const float2 dx = __fadd2_rn(TX[k], px);
+      const float2 dy = __fadd2_rn(TY[k], py);
+      const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+      const float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
       if (KIND == 0) {
-        const float s = p.z * inv;
-        ax[k] = fmaf(dx, s, ax[k]);
-        ay[k] = fmaf(dy, s, ay[k]);
+        const float2 sc = __fmul2_rn(q1, inv);
+        AX[k] = __ffma2_rn(dx, sc, AX[k]);
+        AY[k] = __ffma2_rn(dy, sc, AY[k]);
       } else {
-        const float rq = fmaf(dx, p.z, dy * p.w);
-        const float rn = fmaf(dx, tnx[k], dy * tny[k]);
-        const float c = (rq * rn) * (inv * inv);
-        ax[k] = fmaf(c, dx, ax[k]);
-        ay[k] = fmaf(c, dy, ay[k]);
+        const float2 rq = __ffma2_rn(dx, q1, __fmul2_rn(dy, q2));
+        const float2 rn = __ffma2_rn(dx, NX[k], __fmul2_rn(dy, NY[k]));
+        const float2 c = __fmul2_rn(__fmul2_rn(rq, rn), __fmul2_rn(inv, inv));
+        AX[k] = __ffma2_rn(c, dx, AX[k]);
+        AY[k] = __ffma2_rn(c, dy, AY[k]);
       }
     }
   }
+}
+
+// s + e += t with the rounding error of the leading sum kept (TwoSum)
+__device__ __forceinline__ void comp_add(float& s, float& e, float t) {
+  const float u = s + t;
+  const float bb = u - s;
+  e += (s - (u - bb)) + (t - bb);
+  s = u;
 }
 
 // Union of the bounding boxes of bodies [b0, b1].
@@ -206,12 +230,14 @@ __device__ __forceinline__ float4 body_range_box(const float4* __restrict__ bbox
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
+__global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
-  __shared__ float4 sp[kTile32];
+  __shared__ float4 sp[kTile32];  // near: (xh, yh, xl, yl)
   __shared__ float2 sq[kTile32];
+  __shared__ float4 sp2[kTile32 / 2];  // far: source pairs (-x', -x', -y', -y')
+  __shared__ float4 sq2[kTile32 / 2];  // far: (q1, q1', q2, q2'); Laplace packs (q, q') pairs
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
@@ -222,8 +248,10 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, Vec
   const float cx = 0.5f * (tb.x + tb.z), cy = 0.5f * (tb.y + tb.w);
   const float et = 0.5f * sqrtf((tb.z - tb.x) * (tb.z - tb.x) + (tb.w - tb.y) * (tb.w - tb.y));
   const int a0 = tbase + threadIdx.x;
-  float tlx[kT32], tly[kT32], tnx[kT32], tny[kT32];
-  double dax[kT32], day[kT32];
+  float tnx[kT32], tny[kT32];
+  float2 TX[kT32], TY[kT32], NX[kT32], NY[kT32];
+  // compensated FP32 sums over the tiles: value sx + ex
+  float sx[kT32], ex[kT32], sy[kT32], ey[kT32];
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {
     const int a = a0 + k * kB32;
@@ -233,12 +261,14 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, Vec
       p = g.pf[a];
       if (KIND == 1) n = g.nf[a];
     }
-    tlx[k] = (p.x - cx) + p.z;
-    tly[k] = (p.y - cy) + p.w;
+    const float tlx = (p.x - cx) + p.z, tly = (p.y - cy) + p.w;
     tnx[k] = n.x;
     tny[k] = n.y;
-    dax[k] = 0.0;
-    day[k] = 0.0;
+    TX[k] = make_float2(tlx, tlx);
+    TY[k] = make_float2(tly, tly);
+    NX[k] = make_float2(n.x, n.x);
+    NY[k] = make_float2(n.y, n.y);
+    sx[k] = ex[k] = sy[k] = ey[k] = 0.f;
   }
   // source tiles never cross a body boundary, so a tile's box is its body's
   for (int jt = j0; jt < j1;) {
@@ -252,19 +282,32 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, Vec
     const float gap2 = gx * gx + gy * gy;
     const float need = fmaxf(et, es);
     const bool far = gap2 > 0.f && gap2 >= need * need;
+    // far tiles are padded to an even count with a zero-strength copy of the last source
+    const int ntl = far ? (nt + 1) & ~1 : nt;
     __syncthreads();
-    for (int l = threadIdx.x; l < nt; l += kB32) {
-      const int b = jt + l;
+    for (int l = threadIdx.x; l < ntl; l += kB32) {
+      const int b = jt + min(l, nt - 1);
       const float4 p = g.pf[b];
-      float q1, q2 = 0.f;
-      if (KIND == 0) {
-        q1 = (float)(sscale[b] * v[b]);
-      } else {
-        q1 = (float)(sscale[b] * v[2 * b]);
-        q2 = (float)(sscale[b] * v[2 * b + 1]);
+      float q1 = 0.f, q2 = 0.f;
+      if (l < nt) {
+        if (KIND == 0) {
+          q1 = (float)(sscale[b] * v[b]);
+        } else {
+          q1 = (float)(sscale[b] * v[2 * b]);
+          q2 = (float)(sscale[b] * v[2 * b + 1]);
+        }
       }
       if (far) {
-        sp[l] = make_float4((p.x - cx) + p.z, (p.y - cy) + p.w, q1, q2);
+        float* pp = reinterpret_cast<float*>(&sp2[l >> 1]);
+        pp[l & 1] = -((p.x - cx) + p.z);
+        pp[2 + (l & 1)] = -((p.y - cy) + p.w);
+        if (KIND == 0) {
+          reinterpret_cast<float*>(sq2)[l] = q1;
+        } else {
+          float* qq = reinterpret_cast<float*>(&sq2[l >> 1]);
+          qq[l & 1] = q1;
+          qq[2 + (l & 1)] = q2;
+        }
       } else {
         sp[l] = p;
         sq[l] = make_float2(q1, q2);
@@ -272,30 +315,41 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 16 : 12) k_pair32(Geo g, Vec
     }
     __syncthreads();
     float ax[kT32], ay[kT32];
+    if (far) {
+      float2 AX[kT32], AY[kT32];
 #pragma unroll
-    for (int k = 0; k < kT32; ++k) ax[k] = ay[k] = 0.f;
-    if (far)
-      tile_far<KIND>(sp, nt, tlx, tly, tnx, tny, ax, ay);
-    else if ((jt < tend) && (jt + nt > tbase))
-      tile_near<KIND, true>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
-    else
-      tile_near<KIND, false>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
+      for (int k = 0; k < kT32; ++k) AX[k] = AY[k] = make_float2(0.f, 0.f);
+      tile_far2<KIND>(sp2, sq2, ntl >> 1, TX, TY, NX, NY, AX, AY);
+#pragma unroll
+      for (int k = 0; k < kT32; ++k) {
+        ax[k] = AX[k].x + AX[k].y;
+        ay[k] = AY[k].x + AY[k].y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kT32; ++k) ax[k] = ay[k] = 0.f;
+      if ((jt < tend) && (jt + nt > tbase))
+        tile_near<KIND, true>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
+      else
+        tile_near<KIND, false>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
+    }
 #pragma unroll
     for (int k = 0; k < kT32; ++k) {
-      dax[k] += (double)ax[k];
-      day[k] += (double)ay[k];
+      comp_add(sx[k], ex[k], ax[k]);
+      comp_add(sy[k], ey[k], ay[k]);
     }
     jt += nt;
   }
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {
     const int a = a0 + k * kB32;
+    const double dax_k = (double)sx[k] + (double)ex[k], day_k = (double)sy[k] + (double)ey[k];
     if (a < M) {
       if (KIND == 0)
-        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax[k] + g.ny[a] * day[k];
+        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax_k + g.ny[a] * day_k;
       else {
-        partial[((long long)blockIdx.y * M + a) * 2] = dax[k];
-        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day[k];
+        partial[((long long)blockIdx.y * M + a) * 2] = dax_k;
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day_k;
       }
     }
   }
