@@ -154,6 +154,9 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   g.kappa = A.take<double>(M);
   g.pf = A.take<float4>(M);
   g.nf = A.take<float2>(M);
+  g.xff = A.take<float4>(M);
+  g.xfl = A.take<float2>(M);
+  g.nff = A.take<float4>(M);
   g.len = A.take<double>(N);
   g.xc = A.take<double>(N);
   g.yc = A.take<double>(N);

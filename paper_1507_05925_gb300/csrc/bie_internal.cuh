@@ -34,6 +34,11 @@ struct Geo {
   double *zx = nullptr, *zy = nullptr, *delta = nullptr, *wind = nullptr;
   float4* bbox = nullptr;  // [N] (xmin, ymin, xmax, ymax) of the body's nodes, FP32
   double* qscale = nullptr;  // [2] 2^Q and 2^(Q+23): quanta of the exact 3-float split of positions
+  // exact 3-float split x = h + m + l of the positions (quanta from qscale) and
+  // 2-float split of the normals, for the float-float pair sums
+  float4* xff = nullptr;  // [M] (xh, xm, yh, ym)
+  float2* xfl = nullptr;  // [M] (xl, yl)
+  float4* nff = nullptr;  // [M] (nx_h, nx_l, ny_h, ny_l)
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a

@@ -112,6 +112,32 @@ __global__ void k_geo_scale(Geo g) {
   }
 }
 
+// Per-node splits for the float-float pair sums: positions x = h + m + l on
+// the quanta of qscale (multiplying by the inverse quantum, a power of two,
+// is exact), normals n = h + l.
+__global__ void k_geo_split(Geo g) {
+  const double s0 = g.qscale[0], s1 = g.qscale[1];
+  const double i0 = 1.0 / s0, i1 = 1.0 / s1;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.M; a += gridDim.x * blockDim.x) {
+    float h[2], m[2], l[2];
+    const double c[2] = {g.x[a], g.y[a]};
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const double hh = rint(c[d] * s0) * i0;
+      const double r = c[d] - hh;
+      const double mm = rint(r * s1) * i1;
+      h[d] = (float)hh;
+      m[d] = (float)mm;
+      l[d] = (float)(r - mm);
+    }
+    g.xff[a] = make_float4(h[0], m[0], h[1], m[1]);
+    g.xfl[a] = make_float2(l[0], l[1]);
+    const double nx = g.nx[a], ny = g.ny[a];
+    const float nxh = (float)nx, nyh = (float)ny;
+    g.nff[a] = make_float4(nxh, (float)(nx - (double)nxh), nyh, (float)(ny - (double)nyh));
+  }
+}
+
 // f = sw * (L sigma): q_i on Gamma_i (Laplace), F_i + T_i (x - x^c_i)^perp (Stokes).
 __global__ void k_total_rhs(Geo g, int kind, const double* __restrict__ load, double* __restrict__ f) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.M; a += gridDim.x * blockDim.x) {
@@ -300,6 +326,8 @@ cudaError_t stage_geometry(const Geo& g, const double* x, const double* y, const
   k_stage<<<g.N, kB, 0, s>>>(g, x, y, dx, dy, ddx, ddy, interior_pt);
   note_launches(1);
   k_geo_scale<<<1, kB, 0, s>>>(g);
+  note_launches(1);
+  k_geo_split<<<grid_for(g.M), 256, 0, s>>>(g);
   note_launches(1);
   return cudaGetLastError();
 }

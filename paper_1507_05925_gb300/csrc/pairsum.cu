@@ -359,23 +359,15 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
 // Pair sums in float-float ("double-single") arithmetic on the FP32 pipes, for
 // residuals that must be accurate far beyond FP32: every quantity is an
 // unevaluated sum h + l of two floats (about 48 significant bits).
-//  - positions: exact split x = h + m + l (quanta from g.qscale), so that
-//    dx = (h_a - h_b) + (m_a - m_b) + (l_a - l_b) has exact leading parts for
-//    every pair, near or far;
+//  - positions: exact split x = h + m + l (quanta from g.qscale, computed
+//    once per geometry), so that dx = (h_a - h_b) + (m_a - m_b) + (l_a - l_b)
+//    has exact leading parts for every pair, near or far;
 //  - products: error-free a*b = p + fma(a, b, -p);
 //  - reciprocal: MUFU rcp.approx seed y0 refined by one Newton step in
 //    float-float, 1/r2 = y0 + y0 (1 - r2 y0);
-//  - sums: TwoSum (Knuth) for the leading parts, trailing parts added.
-constexpr int kBF = 128, kTF = 2, kTileF = 128;
-
-__device__ __forceinline__ void split3(double x, double s0, double s1, float& h, float& m, float& l) {
-  const double hh = rint(x * s0) / s0;
-  const double r = x - hh;
-  const double mm = rint(r * s1) / s1;
-  h = (float)hh;
-  m = (float)mm;
-  l = (float)(r - mm);
-}
+//  - sums: TwoSum (Knuth) for the leading parts, trailing parts added, within
+//    a tile and across tiles (no FP64 in the loop: GB300's FP64 pipe is slow).
+constexpr int kBF = 64, kTF = 4, kTileF = 256;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -399,26 +391,36 @@ __device__ __forceinline__ void ff_diff(float ah, float am, float al, float bh, 
   dl = (d2 - (dh - d1)) + (al - bl);
 }
 
+// (sh, sl) += (th, tl)
+__device__ __forceinline__ void ff_acc(float& sh, float& sl, float th, float tl) {
+  float u, e;
+  two_sum(sh, th, u, e);
+  sh = u;
+  sl += e + tl;
+}
+
 template <int KIND, bool DIAG>
-__device__ __forceinline__ void tile_ff(const float4* __restrict__ sp, const float4* __restrict__ sq, int nt,
-                                        int jt, int a0, const float* txh, const float* txm, const float* txl,
-                                        const float* tyh, const float* tym, const float* tyl, const float* tnxh,
-                                        const float* tnxl, const float* tnyh, const float* tnyl, float* axh,
-                                        float* axl, float* ayh, float* ayl) {
+__device__ __forceinline__ void tile_ff(const float4* __restrict__ sa, const float2* __restrict__ sb,
+                                        const float4* __restrict__ sq, int nt, int jt, int a0, const float* txh,
+                                        const float* txm, const float* txl, const float* tyh, const float* tym,
+                                        const float* tyl, const float4* tn, float* axh, float* axl, float* ayh,
+                                        float* ayl) {
   for (int l = 0; l < nt; ++l) {
-    const float4 pa = sp[2 * l], pb = sp[2 * l + 1];  // (xh, xm, yh, ym), (xl, yl, -, -)
-    const float4 q = sq[l];                            // (q1h, q1l, q2h, q2l)
+    const float4 pa = sa[l];  // (xh, xm, yh, ym)
+    const float2 pb = sb[l];  // (xl, yl)
+    const float4 q = sq[l];   // (q1h, q1l, q2h, q2l)
 #pragma unroll
     for (int k = 0; k < kTF; ++k) {
       float dxh, dxl, dyh, dyl;
       ff_diff(txh[k], txm[k], txl[k], pa.x, pa.y, pb.x, dxh, dxl);
       ff_diff(tyh[k], tym[k], tyl[k], pa.z, pa.w, pb.y, dyh, dyl);
-      // r2 = dx^2 + dy^2
+      // r2 = dx^2 + dy^2: error-free squares, Fast2Sum of the two (both >= 0,
+      // ordered by max/min), then the cross terms and renormalisation
       const float p1 = dxh * dxh, p1e = fmaf(dxh, dxh, -p1);
       const float p2 = dyh * dyh, p2e = fmaf(dyh, dyh, -p2);
-      float s, se;
-      two_sum(p1, p2, s, se);
-      const float lo = se + p1e + p2e + 2.0f * fmaf(dxh, dxl, dyh * dyl);
+      const float s = p1 + p2;
+      const float se = fminf(p1, p2) - (s - fmaxf(p1, p2));
+      const float lo = fmaf(2.0f, fmaf(dxh, dxl, dyh * dyl), (se + p1e) + p2e);
       const float r2h = s + lo;
       const float r2l = lo - (r2h - s);
       // 1/r2
@@ -435,8 +437,8 @@ __device__ __forceinline__ void tile_ff(const float4* __restrict__ sp, const flo
         ff_mul(dyh, dyl, q.z, q.w, t2, t2e);
         two_sum(t1, t2, rqh, rql);
         rql += t1e + t2e;
-        ff_mul(dxh, dxl, tnxh[k], tnxl[k], t1, t1e);
-        ff_mul(dyh, dyl, tnyh[k], tnyl[k], t2, t2e);
+        ff_mul(dxh, dxl, tn[k].x, tn[k].y, t1, t1e);
+        ff_mul(dyh, dyl, tn[k].z, tn[k].w, t2, t2e);
         two_sum(t1, t2, rnh, rnl);
         rnl += t1e + t2e;
         ff_mul(y0, il, y0, il, i2h, i2l);
@@ -448,15 +450,11 @@ __device__ __forceinline__ void tile_ff(const float4* __restrict__ sp, const flo
         ch = self ? 0.0f : ch;
         cl = self ? 0.0f : cl;
       }
-      float cxh, cxl, cyh, cyl, t, te;
+      float cxh, cxl, cyh, cyl;
       ff_mul(ch, cl, dxh, dxl, cxh, cxl);
       ff_mul(ch, cl, dyh, dyl, cyh, cyl);
-      two_sum(axh[k], cxh, t, te);
-      axh[k] = t;
-      axl[k] += te + cxl;
-      two_sum(ayh[k], cyh, t, te);
-      ayh[k] = t;
-      ayl[k] += te + cyl;
+      ff_acc(axh[k], axl[k], cxh, cxl);
+      ff_acc(ayh[k], ayl[k], cyh, cyl);
     }
   }
 }
@@ -465,42 +463,40 @@ template <int KIND>
 __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double* __restrict__ sscale, int chunk,
                                                  double* __restrict__ partial, const int* __restrict__ stop) {
   if (stop && *stop) return;
-  __shared__ float4 sp[2 * kTileF];
+  __shared__ float4 sa[kTileF];
+  __shared__ float2 sb[kTileF];
   __shared__ float4 sq[kTileF];
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
-  const double s0 = g.qscale[0], s1 = g.qscale[1];
   const int tbase = blockIdx.x * kBF * kTF;
   const int tend = min(M, tbase + kBF * kTF);
   const int a0 = tbase + threadIdx.x;
   const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
   float txh[kTF], txm[kTF], txl[kTF], tyh[kTF], tym[kTF], tyl[kTF];
-  float tnxh[kTF], tnxl[kTF], tnyh[kTF], tnyl[kTF];
-  double dax[kTF], day[kTF];
+  float4 tn[kTF];
+  // float-float sums over the tiles
+  float sxh[kTF], sxl[kTF], syh[kTF], syl[kTF];
 #pragma unroll
   for (int k = 0; k < kTF; ++k) {
     const int a = a0 + k * kBF;
-    const double x = a < M ? g.x[a] : 0.0, y = a < M ? g.y[a] : 0.0;
-    split3(x, s0, s1, txh[k], txm[k], txl[k]);
-    split3(y, s0, s1, tyh[k], tym[k], tyl[k]);
-    const double nx = a < M ? g.nx[a] : 0.0, ny = a < M ? g.ny[a] : 0.0;
-    tnxh[k] = (float)nx;
-    tnxl[k] = (float)(nx - (double)tnxh[k]);
-    tnyh[k] = (float)ny;
-    tnyl[k] = (float)(ny - (double)tnyh[k]);
-    dax[k] = 0.0;
-    day[k] = 0.0;
+    const float4 p = a < M ? g.xff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 pl = a < M ? g.xfl[a] : make_float2(0.f, 0.f);
+    txh[k] = p.x;
+    txm[k] = p.y;
+    tyh[k] = p.z;
+    tym[k] = p.w;
+    txl[k] = pl.x;
+    tyl[k] = pl.y;
+    tn[k] = (KIND == 1 && a < M) ? g.nff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sxh[k] = sxl[k] = syh[k] = syl[k] = 0.f;
   }
   for (int jt = j0; jt < j1; jt += kTileF) {
     const int nt = min(kTileF, j1 - jt);
     __syncthreads();
     for (int l = threadIdx.x; l < nt; l += kBF) {
       const int b = jt + l;
-      float xh, xm, xl, yh, ym, yl;
-      split3(g.x[b], s0, s1, xh, xm, xl);
-      split3(g.y[b], s0, s1, yh, ym, yl);
-      sp[2 * l] = make_float4(xh, xm, yh, ym);
-      sp[2 * l + 1] = make_float4(xl, yl, 0.f, 0.f);
+      sa[l] = g.xff[b];
+      sb[l] = g.xfl[b];
       const double q1 = KIND == 0 ? sscale[b] * v[b] : sscale[b] * v[2 * b];
       const double q2 = KIND == 0 ? 0.0 : sscale[b] * v[2 * b + 1];
       const float q1h = (float)q1, q2h = (float)q2;
@@ -511,26 +507,25 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
 #pragma unroll
     for (int k = 0; k < kTF; ++k) axh[k] = axl[k] = ayh[k] = ayl[k] = 0.f;
     if ((jt < tend) && (jt + nt > tbase))
-      tile_ff<KIND, true>(sp, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tnxh, tnxl, tnyh, tnyl, axh, axl, ayh,
-                          ayl);
+      tile_ff<KIND, true>(sa, sb, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tn, axh, axl, ayh, ayl);
     else
-      tile_ff<KIND, false>(sp, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tnxh, tnxl, tnyh, tnyl, axh, axl, ayh,
-                           ayl);
+      tile_ff<KIND, false>(sa, sb, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tn, axh, axl, ayh, ayl);
 #pragma unroll
     for (int k = 0; k < kTF; ++k) {
-      dax[k] += (double)axh[k] + (double)axl[k];
-      day[k] += (double)ayh[k] + (double)ayl[k];
+      ff_acc(sxh[k], sxl[k], axh[k], axl[k]);
+      ff_acc(syh[k], syl[k], ayh[k], ayl[k]);
     }
   }
 #pragma unroll
   for (int k = 0; k < kTF; ++k) {
     const int a = a0 + k * kBF;
+    const double dax = (double)sxh[k] + (double)sxl[k], day = (double)syh[k] + (double)syl[k];
     if (a < M) {
       if (KIND == 0)
-        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax[k] + g.ny[a] * day[k];
+        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax + g.ny[a] * day;
       else {
-        partial[((long long)blockIdx.y * M + a) * 2] = dax[k];
-        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day[k];
+        partial[((long long)blockIdx.y * M + a) * 2] = dax;
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day;
       }
     }
   }
