@@ -124,9 +124,10 @@ struct Work {
   int* bj_pairs = nullptr;
   float* bj_blocks = nullptr;
   double* zbuf = nullptr;
+  double* arn = nullptr;  // per-CTA partials of the fused Arnoldi step
   int bj_max_nb = 0;
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
-  double *h1 = nullptr, *h2 = nullptr, *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
+  double *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
   KState* st = nullptr;
   PairPlan plan64, plan32, planff;
   int P = 1, grid = 1;
@@ -188,6 +189,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   w.partial = A.take<double>((size_t)S * n);
   w.grid = vec_grid(n);
   w.part = A.take<double>((size_t)w.grid * 201 + 64);
+  w.arn = A.take<double>((size_t)3 * w.grid * 201 + 64);
   w.st = A.take<KState>(1);
   if (solve) {
     w.V = A.take<double>((size_t)(m + 1) * w.ld);
@@ -203,8 +205,6 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.sn = A.take<double>(m);
     w.gv = A.take<double>(m + 1);
     w.yv = A.take<double>(m + 1);
-    w.h1 = A.take<double>(201);
-    w.h2 = A.take<double>(201);
     w.P = output_splits(g, kind);
     const int targets = kind == 0 ? N : 3 * N;
     w.outpart = A.take<double>((size_t)w.P * targets * comps + N + 2);
@@ -372,15 +372,9 @@ struct Op {
   int prec;
   double alpha = 0.0;
   int fmm_p = 0;
-  bool precond = false;  // right block-Jacobi: out = A P in
+  bool precond = false;  // GMRES on A P with the right block-Jacobi preconditioner P
+  // out = A in (the preconditioner is applied by the GMRES driver)
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
-    if (precond) {
-      cudaError_t e = bj_apply(w->g, w->kind, w->bj_off, w->bj_blocks, in, w->zbuf, stop, w->bj_max_nb, s);
-      if (e != cudaSuccess) return e;
-      Op plain = *this;
-      plain.precond = false;
-      return plain.apply(vec(w->zbuf), out, stop, s, valid);
-    }
     if (fmm_p > 0) {
       const PairPlan one{1, w->g.M};
       cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s);
@@ -416,11 +410,11 @@ int read_state(bie_ctx* ctx, const Work& w, cudaStream_t s) {
 int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   const long long n = w.n, ld = w.ld;
   const VecRef vj{w.V, ld, &w.st->j, 0}, vj1{w.V, ld, &w.st->j, 1};
-  CK(op.apply(vj, vj1, &w.st->stop, s, false));
-  CK(cgs_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.grid, s));
-  CK(cgs_update_dots(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.grid, s));
-  CK(cgs_update_norm(w.V, ld, vj1, n, w.st, w.part, w.h1, w.h2, w.H, w.cs, w.sn, w.gv, w.grid, s));
-  CK(normalize_next(vj, n, w.st, s));
+  // w = A v_j, or A z_j with z_j = P v_j left in zbuf by the previous step
+  CK(op.apply(op.precond ? vec(w.zbuf) : vj, vj1, &w.st->stop, s, false));
+  const ArnoldiArgs a{w.V,        ld,       n,      w.st,      w.arn, w.H, w.cs, w.sn, w.gv, w.g,
+                      w.kind,     w.bj_off, op.precond ? w.bj_blocks : nullptr, w.zbuf};
+  CK(arnoldi(a, arnoldi_grid(n), s));
   return BIE_OK;
 }
 
@@ -485,6 +479,7 @@ int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
       }
     }
     if ((rc = read_state(ctx, w, s))) return rc;
+    if (ctx->h_state->error) return fail(ctx, BIE_ERR_CUDA, "a grid barrier of the Arnoldi step timed out");
     const int done = ctx->h_state->iters - iters_before;
     for (size_t k = mark; k < ctx->pending.size(); ++k) ctx->pending[k].valid = (int)(k - mark) < done;
     resolve_timings(ctx, false);
@@ -507,6 +502,7 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
   CK(fill0(x, n, s));
   CK(residual_start(b, nullptr, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
+  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
   Op rop = verify ? Op{ctx, &w, 0} : op;
   rop.precond = false;  // residuals of x itself (x = P y is kept in original variables)
   int rc;
@@ -540,6 +536,7 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
     CK(rop.apply(vec(x), vec(w.ytmp), nullptr, s));
     if (verify) out.matvecs64 += 1; else out.matvecs += 1;
     CK(residual_start(b, w.ytmp, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
+    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
     if ((rc = read_state(ctx, w, s))) return rc;
     const KState& h2 = *ctx->h_state;
     if (h2.rnorm <= h2.tol_abs || h2.iters >= h2.maxit) {

@@ -70,6 +70,9 @@ struct KState {
   int m;           // restart length
   int counter;     // last-block-done counter for grid reductions
   int pad[2];         // [0] = 1: set tol_abs from the next starting residual
+  unsigned bar_count, bar_gen;  // grid barrier of the fused Arnoldi step
+  int error;          // 1: a grid barrier gave up waiting (results invalid)
+  int pad2;
 };
 
 }  // namespace bie
@@ -155,6 +158,9 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
 size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart);
 
 // ---------------------------------------------------------------- precond.cu
+// Largest per-body block (unknowns) that the block-Jacobi preconditioner inverts.
+constexpr int kBjMaxBlock = 640;
+
 // Block-Jacobi (per body) preconditioner of the weighted-completion operator.
 long long bj_block_floats(const int* body_start_host, int N, int kind);
 cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
@@ -165,17 +171,25 @@ cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const flo
 
 // ---------------------------------------------------------------- krylov.cu
 int vec_grid(long long n);
+
+// One fused Arnoldi step (CGS2, norm, Givens, normalisation and optionally
+// z = P v_{j+1}); part holds [3][grid][201] doubles.
+struct ArnoldiArgs {
+  double* V;
+  long long ld, n;
+  KState* st;
+  double *part, *H, *cs, *sn, *gv;
+  // block-Jacobi preconditioner: blocks == nullptr for none
+  Geo g;
+  int kind;
+  const long long* off;
+  const float* blocks;
+  double* z;
+};
+int arnoldi_grid(long long n);  // co-resident CTAs for the cooperative launch
+cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s);
 // h[i] = <V_i, w> for i <= j (first CGS pass)
-cudaError_t cgs_dots(const double* V, long long ld, VecRef w, long long n, KState* st, double* part,
-                     double* h1, int grid, cudaStream_t s);
-// w -= V h1; h2 = V^T w (second CGS pass)
-cudaError_t cgs_update_dots(const double* V, long long ld, VecRef w, long long n, KState* st,
-                            double* part, const double* h1, double* h2, int grid, cudaStream_t s);
-// w -= V h2; ||w||; Givens; convergence
-cudaError_t cgs_update_norm(const double* V, long long ld, VecRef w, long long n, KState* st,
-                            double* part, const double* h1, const double* h2, double* H,
-                            double* cs, double* sn, double* gv, int grid, cudaStream_t s);
-cudaError_t normalize_next(VecRef w, long long n, KState* st, cudaStream_t s);
+
 // y = R^{-1} g and x += V y
 cudaError_t gmres_update(const double* V, long long ld, long long n, KState* st, const double* H,
                          const double* gv, double* y, double* x, int grid, cudaStream_t s);

@@ -4,12 +4,16 @@
 // returns at once when the flag is set, so the host may enqueue iterations
 // ahead of the check.
 //
-// Grid reductions write per-block partials and the last block to finish (an
-// atomic ticket) adds them in block order: results are deterministic.
+// Grid reductions write per-block partials that are added in block order
+// (by the last block to finish, through an atomic ticket, or by every block
+// after a grid barrier): results are deterministic.
 #include <math.h>
 
 #include "bie_internal.cuh"
 #include "reduce.cuh"
+
+#include <algorithm>
+#include <atomic>
 
 namespace bie {
 
@@ -17,75 +21,6 @@ namespace {
 
 constexpr int kBV = 256;
 constexpr int kMaxBasis = 201;  // restart length <= 200
-
-// Partial dot products of the thread's elements of w with V_0..V_{jc-1}; the
-// per-block results land in part[blockIdx.x][i]; the last block reduces them
-// into h[i] and returns true.
-__device__ bool block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
-                           long long n, int jc, double* __restrict__ part, double* __restrict__ h,
-                           int* counter) {
-  __shared__ double sh[kBV / 32][kMaxBasis];
-  __shared__ int is_last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long stride = (long long)gridDim.x * kBV;
-  // four basis vectors per round: four independent load streams per thread
-  int i = 0;
-  for (; i + 4 <= jc; i += 4) {
-    const double* __restrict__ V0 = V + (long long)i * ld;
-    const double* __restrict__ V1 = V0 + ld;
-    const double* __restrict__ V2 = V1 + ld;
-    const double* __restrict__ V3 = V2 + ld;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-      const double wk = w[k];
-      a0 += V0[k] * wk;
-      a1 += V1[k] * wk;
-      a2 += V2[k] * wk;
-      a3 += V3[k] * wk;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_down_sync(0xffffffffu, a0, o);
-      a1 += __shfl_down_sync(0xffffffffu, a1, o);
-      a2 += __shfl_down_sync(0xffffffffu, a2, o);
-      a3 += __shfl_down_sync(0xffffffffu, a3, o);
-    }
-    if (lane == 0) {
-      sh[wid][i] = a0;
-      sh[wid][i + 1] = a1;
-      sh[wid][i + 2] = a2;
-      sh[wid][i + 3] = a3;
-    }
-  }
-  for (; i < jc; ++i) {
-    const double* __restrict__ Vi = V + (long long)i * ld;
-    double acc = 0.0;
-    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) acc += Vi[k] * w[k];
-    acc = warp_sum(acc);
-    if (lane == 0) sh[wid][i] = acc;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < jc; i += kBV) {
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < kBV / 32; ++q) s += sh[q][i];
-    part[(long long)blockIdx.x * kMaxBasis + i] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  for (int i = threadIdx.x; i < jc; i += kBV) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)part)[(long long)b * kMaxBasis + i];
-    h[i] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *counter = 0;
-  return true;
-}
 
 // sum_i c[i] V_i[k] for i < jc, four independent partial sums
 __device__ __forceinline__ double combine(const double* __restrict__ V, long long ld, long long k,
@@ -102,96 +37,285 @@ __device__ __forceinline__ double combine(const double* __restrict__ V, long lon
   return (s0 + s1) + (s2 + s3);
 }
 
-__global__ void __launch_bounds__(kBV) k_cgs_dots(const double* __restrict__ V, long long ld, VecRef wr,
-                                                  long long n, KState* st, double* part, double* h1) {
-  if (st->stop) return;
-  block_dots(V, ld, wr.ptr(), n, st->j + 1, part, h1, &st->counter);
-}
+// ------------------------------------------------------------ fused Arnoldi
+// One Arnoldi step after w = A z_j (w = V_{j+1}) in a single cooperative
+// cooperative launch with three grid barriers: CGS2 (h1 = V^T w; w -= V h1; h2 = V^T w;
+// w -= V h2), ||w||, the Hessenberg column with its Givens rotations and the
+// residual estimate, v_{j+1} = w / ||w|| and, with the block-Jacobi
+// preconditioner, z_{j+1} = P v_{j+1}.  After each barrier every CTA adds the
+// per-CTA partials itself, in CTA order (deterministic; no atomics), so
+// nothing else synchronises the grid.  In the last phase a CTA that owns a
+// body reads that body's w, writes z and normalises v in place: every element
+// is written only by its owner, after the owner has read it.
 
-__global__ void __launch_bounds__(kBV) k_cgs_update_dots(const double* __restrict__ V, long long ld,
-                                                         VecRef wr, long long n, KState* st, double* part,
-                                                         const double* __restrict__ h1, double* h2) {
-  if (st->stop) return;
-  __shared__ double hs[kMaxBasis];
-  const int jc = st->j + 1;
-  for (int i = threadIdx.x; i < jc; i += kBV) hs[i] = h1[i];
-  __syncthreads();
-  double* __restrict__ w = wr.ptr();
+// Partial dot products of this CTA's elements of w with V_0..V_{jc-1} into
+// out[0..jc).
+__device__ void arn_block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
+                               long long n, int jc, double* __restrict__ out, double (*sh)[kMaxBasis]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * kBV;
-  for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-    w[k] = w[k] - combine(V, ld, k, hs, jc);
+  int i = 0;
+  for (; i + 4 <= jc; i += 4) {
+    const double* __restrict__ V0 = V + (long long)i * ld;
+    const double* __restrict__ V1 = V0 + ld;
+    const double* __restrict__ V2 = V1 + ld;
+    const double* __restrict__ V3 = V2 + ld;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+      const double wk = w[k];
+      a0 = fma(V0[k], wk, a0);
+      a1 = fma(V1[k], wk, a1);
+      a2 = fma(V2[k], wk, a2);
+      a3 = fma(V3[k], wk, a3);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) {
+      sh[wid][i] = a0;
+      sh[wid][i + 1] = a1;
+      sh[wid][i + 2] = a2;
+      sh[wid][i + 3] = a3;
+    }
   }
-  block_dots(V, ld, w, n, jc, part, h2, &st->counter);
+  for (; i < jc; ++i) {
+    const double* __restrict__ Vi = V + (long long)i * ld;
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) acc = fma(Vi[k], w[k], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) sh[wid][i] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < jc; q += kBV) {
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < kBV / 32; ++u) t += sh[u][q];
+    out[q] = t;
+  }
 }
 
-// w -= V h2, ||w||, then (last block, one thread) the Hessenberg column j,
-// the previous rotations, a new rotation and the residual estimate |g_{j+1}|.
-__global__ void __launch_bounds__(kBV) k_cgs_update_norm(const double* __restrict__ V, long long ld,
-                                                         VecRef wr, long long n, KState* st, double* part,
-                                                         const double* __restrict__ h1,
-                                                         const double* __restrict__ h2, double* H,
-                                                         double* cs, double* sn, double* gv) {
-  if (st->stop) return;
-  __shared__ double hs[kMaxBasis];
-  __shared__ double sh[kBV / 32];
-  __shared__ int is_last;
-  const int j = st->j;
-  const int jc = j + 1;
-  for (int i = threadIdx.x; i < jc; i += kBV) hs[i] = h2[i];
+// Sum over CTAs b < gridDim.x of part[b * stride] (written by other CTAs
+// before a barrier or ticket; read through L2), by one warp: lanes take
+// b = lane, lane + 32, ... with independent loads, then a fixed-order warp
+// reduction (deterministic).  The total is valid in lane 0.
+__device__ __forceinline__ double warp_gather(const double* part, long long stride) {
+  const int lane = threadIdx.x & 31;
+  double t0 = 0.0, t1 = 0.0;
+  int b = lane;
+  for (; b + 32 < (int)gridDim.x; b += 64) {
+    t0 += __ldcg(part + (long long)b * stride);
+    t1 += __ldcg(part + (long long)(b + 32) * stride);
+  }
+  if (b < (int)gridDim.x) t0 += __ldcg(part + (long long)b * stride);
+  return warp_sum(t0 + t1);
+}
+
+// hs[i] = sum over CTAs b of part[b][i], one warp per i.
+__device__ void arn_grid_sum(const double* part, int jc, double* hs) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < jc; i += kBV / 32) {
+    const double t = warp_gather(part + i, kMaxBasis);
+    if (lane == 0) hs[i] = t;
+  }
   __syncthreads();
-  double* __restrict__ w = wr.ptr();
+}
+
+// Grid barrier for a cooperative launch (all CTAs co-resident): arrival
+// counter plus generation number in the solver state.  The wait is bounded:
+// after about a second it records st->error and returns, so a fault can never
+// hang the GPU (the results of that step are then invalid and the host
+// reports an error).
+constexpr long long kBarrierSpins = 1LL << 24;
+
+__device__ void grid_barrier(KState* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &st->bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      st->bar_count = 0;
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g0) {
+        if (++it > kBarrierSpins) {
+          atomicExch(&st->error, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
+  KState* st = a.st;
+  if (st->stop) return;  // read by every CTA before the first barrier: uniform
+  __shared__ double sh[kBV / 32][kMaxBasis];
+  __shared__ double hs1[kMaxBasis], hs2[kMaxBasis];
+  __shared__ double red[kBV / 32];
+  __shared__ float ws[kBjMaxBlock];
+  const int j = st->j, jc = j + 1;
+  const long long n = a.n, ld = a.ld;
+  double* __restrict__ w = a.V + (long long)(j + 1) * ld;
   const long long stride = (long long)gridDim.x * kBV;
+  const long long G = gridDim.x;
+  double* part1 = a.part;
+  double* part2 = part1 + G * kMaxBasis;
+  double* part3 = part2 + G * kMaxBasis;
+  // h1 = V^T w
+  arn_block_dots(a.V, ld, w, n, jc, part1 + blockIdx.x * kMaxBasis, sh);
+  grid_barrier(st);
+  arn_grid_sum(part1, jc, hs1);
+  // w -= V h1; h2 = V^T w
+  for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride)
+    w[k] = w[k] - combine(a.V, ld, k, hs1, jc);
+  __syncthreads();
+  arn_block_dots(a.V, ld, w, n, jc, part2 + blockIdx.x * kMaxBasis, sh);
+  grid_barrier(st);
+  arn_grid_sum(part2, jc, hs2);
+  // w -= V h2; ||w||^2
   double nrm = 0.0;
   for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-    const double acc = w[k] - combine(V, ld, k, hs, jc);
-    w[k] = acc;
-    nrm += acc * acc;
+    const double t = w[k] - combine(a.V, ld, k, hs2, jc);
+    w[k] = t;
+    nrm = fma(t, t, nrm);
   }
-  nrm = block_sum<kBV>(nrm, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = nrm;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
-  __threadfence();
-  double s = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)part)[b];
-  st->counter = 0;
-  const int m = st->m;
-  double* Hc = H + (long long)j * (m + 1);
-  for (int i = 0; i <= j; ++i) Hc[i] = h1[i] + h2[i];
-  const double hn = sqrt(s);
-  Hc[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * Hc[i] + sn[i] * Hc[i + 1];
-    Hc[i + 1] = -sn[i] * Hc[i] + cs[i] * Hc[i + 1];
-    Hc[i] = t;
+  nrm = block_sum<kBV>(nrm, red);
+  if (threadIdx.x == 0) part3[blockIdx.x * kMaxBasis] = nrm;
+  grid_barrier(st);
+  __shared__ double hn_s;
+  if (threadIdx.x < 32) {
+    const double t = warp_gather(part3, kMaxBasis);
+    if (threadIdx.x == 0) hn_s = sqrt(t);
   }
-  const double a = Hc[j], b = Hc[j + 1];
-  const double r = hypot(a, b);
-  const double c = r > 0.0 ? a / r : 1.0, sg = r > 0.0 ? b / r : 0.0;
-  cs[j] = c;
-  sn[j] = sg;
-  Hc[j] = r;
-  Hc[j + 1] = 0.0;
-  gv[j + 1] = -sg * gv[j];
-  gv[j] = c * gv[j];
-  st->res = fabs(gv[j + 1]);
-  st->hnext = hn;
-  st->j = j + 1;
-  st->iters += 1;
-  if (st->res <= st->tol_abs || !(hn > 1e-300 * st->beta) || st->j >= m || st->iters >= st->maxit)
-    st->stop = 1;
-}
-
-__global__ void k_normalize(VecRef wr, long long n, const KState* st) {
-  if (st->stop) return;
-  double* w = wr.ptr();
-  const double inv = 1.0 / st->hnext;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    w[k] *= inv;
+  __syncthreads();
+  const double hn = hn_s;
+  if (blockIdx.x == 0) {
+    // Hessenberg column j and the previous rotations in shared memory (one
+    // thread applies the rotations; no global round trips in the chain)
+    __shared__ double hcol[kMaxBasis + 1], css[kMaxBasis], sns[kMaxBasis];
+    const int m = st->m;
+    double* Hc = a.H + (long long)j * (m + 1);
+    for (int i = threadIdx.x; i <= j; i += kBV) hcol[i] = hs1[i] + hs2[i];
+    for (int i = threadIdx.x; i < j; i += kBV) {
+      css[i] = a.cs[i];
+      sns[i] = a.sn[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      hcol[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = css[i] * hcol[i] + sns[i] * hcol[i + 1];
+        hcol[i + 1] = -sns[i] * hcol[i] + css[i] * hcol[i + 1];
+        hcol[i] = t;
+      }
+      const double x = hcol[j], y = hcol[j + 1];
+      const double r = hypot(x, y);
+      const double c = r > 0.0 ? x / r : 1.0, sg = r > 0.0 ? y / r : 0.0;
+      a.cs[j] = c;
+      a.sn[j] = sg;
+      hcol[j] = r;
+      hcol[j + 1] = 0.0;
+      const double g = a.gv[j];
+      a.gv[j + 1] = -sg * g;
+      a.gv[j] = c * g;
+      st->res = fabs(sg * g);
+      st->hnext = hn;
+      st->j = j + 1;
+      st->iters += 1;
+      if (st->res <= st->tol_abs || !(hn > 1e-300 * st->beta) || st->j >= m || st->iters >= st->maxit)
+        st->stop = 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += kBV) Hc[i] = hcol[i];
+  }
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (!a.blocks) {
+    // v_{j+1} = w / ||w|| over this CTA's own elements
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) w[k] *= inv;
+    return;
+  }
+  // per body: v = w inv (w read through L2: other CTAs wrote it), z = P v
+  __shared__ float4 red4[kBV];
+  const int c = a.kind + 1;
+  for (int i = blockIdx.x; i < a.g.N; i += (int)G) {
+    const long long a0 = (long long)a.g.body_start[i] * c;
+    const int nb = (a.g.body_start[i + 1] - a.g.body_start[i]) * c;
+    if (nb > kBjMaxBlock) {
+      for (int r = threadIdx.x; r < nb; r += kBV) {
+        const double v = __ldcg(w + a0 + r) * inv;
+        w[a0 + r] = v;
+        a.z[a0 + r] = v;
+      }
+      continue;
+    }
+    for (int r = threadIdx.x; r < nb; r += kBV) {
+      const double v = __ldcg(w + a0 + r) * inv;
+      w[a0 + r] = v;
+      ws[r] = (float)v;
+    }
+    __syncthreads();
+    const float* __restrict__ B = a.blocks + a.off[i];
+    if ((nb & 3) == 0 && (a.off[i] & 3) == 0) {
+      // 16-byte loads of four consecutive rows: 64 row quads x 4 column groups
+      const int nq = nb >> 2, qd = threadIdx.x & 63, grp = threadIdx.x >> 6;
+      const int per = (nb + 3) >> 2, cb = grp * per, ce = min(nb, cb + per);
+      for (int q0 = 0; q0 < nq; q0 += 64) {
+        const int q = q0 + qd;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < nq) {
+          const float4* __restrict__ Bq = reinterpret_cast<const float4*>(B) + q;
+#pragma unroll 8
+          for (int col = cb; col < ce; ++col) {
+            const float4 b = Bq[(long long)col * nq];
+            const float x = ws[col];
+            acc.x = fmaf(b.x, x, acc.x);
+            acc.y = fmaf(b.y, x, acc.y);
+            acc.z = fmaf(b.z, x, acc.z);
+            acc.w = fmaf(b.w, x, acc.w);
+          }
+        }
+        red4[threadIdx.x] = acc;
+        __syncthreads();
+        if (grp == 0 && q < nq) {
+          float4 t = red4[qd];
+#pragma unroll
+          for (int u = 1; u < 4; ++u) {
+            const float4 o = red4[u * 64 + qd];
+            t.x += o.x;
+            t.y += o.y;
+            t.z += o.z;
+            t.w += o.w;
+          }
+          double* zr = a.z + a0 + 4 * q;
+          zr[0] = t.x;
+          zr[1] = t.y;
+          zr[2] = t.z;
+          zr[3] = t.w;
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int r = threadIdx.x; r < nb; r += kBV) {
+        float s0 = 0.f, s1 = 0.f;
+        int col = 0;
+#pragma unroll 4
+        for (; col + 2 <= nb; col += 2) {
+          s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
+          s1 = fmaf(B[(long long)(col + 1) * nb + r], ws[col + 1], s1);
+        }
+        if (col < nb) s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
+        a.z[a0 + r] = (double)(s0 + s1);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Back substitution R y = g on the j x j triangle (single thread; j <= 200).
@@ -239,10 +363,10 @@ __global__ void __launch_bounds__(kBV) k_residual(const double* __restrict__ f, 
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1) == (int)gridDim.x - 1);
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last || threadIdx.x >= 32) return;
   __threadfence();
-  double s = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)part)[b];
+  const double s = warp_gather(part, 1);
+  if (threadIdx.x != 0) return;
   st->counter = 0;
   const double rn = sqrt(s);
   st->rnorm = rn;
@@ -294,32 +418,29 @@ int vec_grid(long long n) {
   return (int)b;
 }
 
-cudaError_t cgs_dots(const double* V, long long ld, VecRef w, long long n, KState* st, double* part,
-                     double* h1, int grid, cudaStream_t s) {
-  k_cgs_dots<<<grid, kBV, 0, s>>>(V, ld, w, n, st, part, h1);
-  note_launches(1);
-  return cudaGetLastError();
+int arnoldi_grid(long long n) {
+  static std::atomic<int> coresident[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (coresident[dev].load() == 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, kBV, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm * sms < 1) {
+      cudaGetLastError();
+      return 1;  // not cached: a launch of one CTA is always co-resident
+    }
+    coresident[dev].store(per_sm * sms);
+  }
+  return std::min(vec_grid(n), coresident[dev].load());
 }
 
-cudaError_t cgs_update_dots(const double* V, long long ld, VecRef w, long long n, KState* st,
-                            double* part, const double* h1, double* h2, int grid, cudaStream_t s) {
-  k_cgs_update_dots<<<grid, kBV, 0, s>>>(V, ld, w, n, st, part, h1, h2);
+cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s) {
+  ArnoldiArgs args = a;
+  void* params[] = {&args};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(grid), dim3(kBV), params, 0, s);
   note_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t cgs_update_norm(const double* V, long long ld, VecRef w, long long n, KState* st,
-                            double* part, const double* h1, const double* h2, double* H, double* cs,
-                            double* sn, double* gv, int grid, cudaStream_t s) {
-  k_cgs_update_norm<<<grid, kBV, 0, s>>>(V, ld, w, n, st, part, h1, h2, H, cs, sn, gv);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t normalize_next(VecRef w, long long n, KState* st, cudaStream_t s) {
-  k_normalize<<<elt_grid(n), 256, 0, s>>>(w, n, st);
-  note_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t gmres_update(const double* V, long long ld, long long n, KState* st, const double* H,

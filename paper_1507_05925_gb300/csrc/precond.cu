@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kMaxSingle = 128;  // one CTA
 constexpr int kMaxBlock4 = 448;  // cluster of four CTAs
-constexpr int kMaxBlock = 640;   // cluster of eight CTAs; larger bodies keep the identity
+constexpr int kMaxBlock = kBjMaxBlock;  // cluster of eight CTAs (640); larger bodies keep the identity
 constexpr int kPB = 16;          // panel width of the blocked elimination
 constexpr int kMaxThreads = 640; // one thread per row
 constexpr int kBA = 256;         // threads of an application CTA
