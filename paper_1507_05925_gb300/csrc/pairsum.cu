@@ -175,7 +175,7 @@ template <int KIND>
 __device__ __forceinline__ void tile_far2(const float4* __restrict__ sp2, const float4* __restrict__ sq2, int np,
                                           const float2* TX, const float2* TY, const float2* NX, const float2* NY,
                                           float2* AX, float2* AY) {
-#pragma unroll 2
+#pragma unroll(KIND == 0 ? 4 : 2)
   for (int l = 0; l < np; ++l) {
     const float4 p = sp2[l];
     const float2 px = make_float2(p.x, p.y), py = make_float2(p.z, p.w);

@@ -398,6 +398,43 @@ def test_full_size_solve_properties(ctx, wl, kind):
         _check_full_size(g, geo, kind, res, nu, info, outs[bie.FP64][0])
 
 
+@pytest.mark.parametrize("wl,kind", [("stars100_M25600", 0), ("stars100_M25600", 1), ("ellipses400_M51200", 1)])
+def test_refinement_residual_is_certified(ctx, wl, kind):
+    # the float-float refinement updates its residual with FP32 pair sums after
+    # the first true residual; the reported relative residual (update plus its
+    # error bound) must bound the true one, recomputed here with the FP64
+    # operator from the returned density
+    g = synth.WORKLOADS[wl]()
+    geo = geometry.nodes(g)
+    N, M = geo["N"], geo["M"]
+    if kind == 0:
+        load = g["q"]
+    else:
+        FT = g["FT"] if "FT" in g else synth.forces_torques(N, np.random.default_rng(25))
+        load = FT.reshape(-1)
+    gd = to_dev(g)
+    out = torch.empty(N if kind == 0 else 3 * N, dtype=torch.float64, device="cuda")
+    dens = torch.empty(M * (kind + 1), dtype=torch.float64, device="cuda")
+    fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
+    rc, info = fn(ctx, gd, torch.from_numpy(load).cuda(), out, dens, opts=bie.make_opts(precision=bie.MIXED_FF))
+    assert rc == bie.OK, (rc, info)
+    Anu = torch.empty_like(dens)
+    assert bie.apply_operator(ctx, gd, kind, bie.FP64, dens, Anu) == bie.OK
+    torch.cuda.synchronize()
+    if kind == 0:
+        rhs = g["q"][geo["body"]]
+        sw = np.sqrt(geo["w"])
+    else:
+        px, py = stokes.perp(geo)
+        b = geo["body"]
+        rhs = np.stack([FT[b, 0] + FT[b, 2] * px, FT[b, 1] + FT[b, 2] * py], 1).reshape(-1)
+        sw = np.repeat(np.sqrt(geo["w"]), 2)
+    true_rel = np.linalg.norm(sw * (Anu.cpu().numpy() - rhs)) / np.linalg.norm(sw * rhs)
+    print(f"{wl} kind={kind}: reported {info['rel_residual']:.2e} true {true_rel:.2e} {info}")
+    assert info["rel_residual"] <= 1e-12
+    assert true_rel <= 1.5 * info["rel_residual"] + 1e-14
+
+
 def _check_full_size(g, geo, kind, res, nu, info, res64):
     M = geo["M"]
     # (1) the density satisfies the oracle's equation at sampled rows: (1/2 I + K + L) nu = L sigma
