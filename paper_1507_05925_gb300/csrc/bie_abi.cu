@@ -377,7 +377,7 @@ struct Op {
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
     if (fmm_p > 0) {
       const PairPlan one{1, w->g.M};
-      cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s);
+      cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s, prec);
       if (e != cudaSuccess) return e;
       return epilogue(w->g, w->kind, one, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
     }

@@ -146,9 +146,10 @@ struct FmmState;
 // every order in `orders` (at most 64).  One host round trip.
 int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norders, cudaStream_t s,
               std::string& err);
-// Pair sums by the FMM of order p into partial (layout of a single source split).
+// Pair sums by the FMM of order p into partial (layout of a single source
+// split); the near field in FP64 (near_prec 0), FP32 (1) or float-float (2).
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
-                         double* partial, const int* stop, cudaStream_t s);
+                         double* partial, const int* stop, cudaStream_t s, int near_prec = 0);
 void fmm_free(FmmState* f, cudaStream_t s);
 // Output single layers at the interior targets by the FMM (one split, the
 // layout of evaluate_output's direct sums).

@@ -35,6 +35,7 @@
 
 #include "../../include/bie2d.h"
 #include "bie_internal.cuh"
+#include "pair_math.cuh"
 
 namespace bie {
 
@@ -338,6 +339,13 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop
 
 // Local expansion and near field at every node of a leaf, then the kernel's
 // combination into the pair-sum partial (Laplace scalar / Stokes 2-vector).
+// NEARP = 0: the near field enters the FP64 Cauchy sums.  NEARP = 1 (FP32)
+// and 2 (float-float): the far part is combined into the kernel value in
+// FP64 and the near field is summed as the real kernel with the pair
+// arithmetic of the direct sums (exact leading coordinate differences), so
+// the accuracy follows the operator that uses it: FP32 for the inner solves,
+// float-float for residuals.
+template <int NEARP>
 __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __restrict__ partial, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ double2 sm[];  // [nd][p]
@@ -364,28 +372,34 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __rest
       F[d] = h;
       dF[d] = make_double2(dh.x / s, dh.y / s);
     }
-    // near field: 3 x 3 leaves
-    for (int ny = max(0, by - 1); ny <= min(f.nb - 1, by + 1); ++ny) {
-      for (int nx = max(0, bx - 1); nx <= min(f.nb - 1, bx + 1); ++nx) {
-        const int nl = ny * f.nb + nx;
-        for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
-          const int i2 = f.perm[k];
-          if (i2 == i) continue;
-          const double rx = zi.x - g.x[i2], ry = zi.y - g.y[i2];
-          const double inv = 1.0 / (rx * rx + ry * ry);
-          const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
-          const double2 r2 = cmul(r1, r1);
-          for (int d = 0; d < f.nd; ++d) {
-            const double2 q = f.Q[(long long)i2 * f.nd + d];
-            cfma(F[d], q, r1);
-            cfma(dF[d], make_double2(-q.x, -q.y), r2);
+    const int y0 = max(0, by - 1), y1 = min(f.nb - 1, by + 1);
+    const int x0 = max(0, bx - 1), x1 = min(f.nb - 1, bx + 1);
+    if (NEARP == 0) {
+      // near field: 3 x 3 leaves, as Cauchy terms
+      for (int ny = y0; ny <= y1; ++ny) {
+        for (int nx = x0; nx <= x1; ++nx) {
+          const int nl = ny * f.nb + nx;
+          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+            const int i2 = f.perm[k];
+            if (i2 == i) continue;
+            const double rx = zi.x - g.x[i2], ry = zi.y - g.y[i2];
+            const double inv = 1.0 / (rx * rx + ry * ry);
+            const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
+            const double2 r2 = cmul(r1, r1);
+            for (int d = 0; d < f.nd; ++d) {
+              const double2 q = f.Q[(long long)i2 * f.nd + d];
+              cfma(F[d], q, r1);
+              cfma(dF[d], make_double2(-q.x, -q.y), r2);
+            }
           }
         }
       }
     }
+    // the kernel's combination of the Cauchy sums
     const double nx1 = g.nx[i], ny1 = g.ny[i];
+    double ox, oy = 0.0;
     if (f.nd == 1) {
-      partial[i] = nx1 * F[0].x - ny1 * F[0].y;
+      ox = nx1 * F[0].x - ny1 * F[0].y;
     } else {
       const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
       const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-dF[2].x, -dF[2].y);
@@ -397,8 +411,80 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __rest
       tt = cadd(tt, cmul(nu, cconj(S1)));
       tt = cadd(tt, cmul(nub, cconj(S6)));
       tt = cadd(tt, cmul(nu, S1));
-      partial[2 * i] = 0.25 * tt.x;
-      partial[2 * i + 1] = 0.25 * tt.y;
+      ox = 0.25 * tt.x;
+      oy = 0.25 * tt.y;
+    }
+    if (NEARP == 1) {
+      const float4 tp = g.pf[i];
+      const float2 tn = g.nf[i];
+      float ax = 0.f, ay = 0.f;
+      for (int ny = y0; ny <= y1; ++ny) {
+        for (int nx = x0; nx <= x1; ++nx) {
+          const int nl = ny * f.nb + nx;
+          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+            const int i2 = f.perm[k];
+            if (i2 == i) continue;
+            const double2 q = f.Q[(long long)i2 * f.nd];
+            float cx, cy;
+            if (f.nd == 1)
+              f32_pair<0>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, g.pf[i2], (float)q.x, 0.f, cx, cy);
+            else
+              f32_pair<1>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, g.pf[i2], (float)q.x, (float)q.y, cx, cy);
+            ax += cx;
+            ay += cy;
+          }
+        }
+      }
+      if (f.nd == 1)
+        ox += nx1 * (double)ax + ny1 * (double)ay;
+      else {
+        ox += (double)ax;
+        oy += (double)ay;
+      }
+    } else if (NEARP == 2) {
+      FFTarget t;
+      const float4 p = g.xff[i];
+      const float2 pl = g.xfl[i];
+      t.xh = p.x;
+      t.xm = p.y;
+      t.yh = p.z;
+      t.ym = p.w;
+      t.xl = pl.x;
+      t.yl = pl.y;
+      t.n = g.nff[i];
+      float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
+      for (int ny = y0; ny <= y1; ++ny) {
+        for (int nx = x0; nx <= x1; ++nx) {
+          const int nl = ny * f.nb + nx;
+          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+            const int i2 = f.perm[k];
+            if (i2 == i) continue;
+            const double2 q = f.Q[(long long)i2 * f.nd];
+            const float q1h = (float)q.x, q2h = (float)q.y;
+            const float4 qq = make_float4(q1h, (float)(q.x - (double)q1h), q2h, (float)(q.y - (double)q2h));
+            float cxh, cxl, cyh, cyl;
+            if (f.nd == 1)
+              ff_pair<0>(t, g.xff[i2], g.xfl[i2], qq, cxh, cxl, cyh, cyl);
+            else
+              ff_pair<1>(t, g.xff[i2], g.xfl[i2], qq, cxh, cxl, cyh, cyl);
+            ff_acc(axh, axl, cxh, cxl);
+            ff_acc(ayh, ayl, cyh, cyl);
+          }
+        }
+      }
+      const double ax = (double)axh + (double)axl, ay = (double)ayh + (double)ayl;
+      if (f.nd == 1)
+        ox += nx1 * ax + ny1 * ay;
+      else {
+        ox += ax;
+        oy += ay;
+      }
+    }
+    if (f.nd == 1) {
+      partial[i] = ox;
+    } else {
+      partial[2 * i] = ox;
+      partial[2 * i + 1] = oy;
     }
   }
 }
@@ -667,7 +753,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
 }
 
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
-                         double* partial, const int* stop, cudaStream_t s) {
+                         double* partial, const int* stop, cudaStream_t s, int near_prec) {
   if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;
   double2* ops = nullptr;
   for (auto& o : f->ops)
@@ -684,7 +770,12 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
   k_fmm_m2l<<<(int)(lev_off(f->L + 1) - lev_off(2)), kB, sm_exp, s>>>(d, stop);
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
-  k_fmm_eval<<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+  if (near_prec == 1)
+    k_fmm_eval<1><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+  else if (near_prec == 2)
+    k_fmm_eval<2><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+  else
+    k_fmm_eval<0><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
   note_launches(4 + 2 * std::max(0, f->L - 2));
   return cudaGetLastError();
 }

@@ -17,22 +17,18 @@
 // origin (the near-pair cancellation in r . n_a would otherwise lose digits).
 // Tiles far from the block (gap at least both boxes' half-diagonals) use plain
 // FP32 coordinates relative to the block centre: 4 fewer instructions a pair.
-// The reciprocal is the hardware rcp.approx.f32; each tile's FP32 sums are
-// promoted into FP64 accumulators.
+// The reciprocal is the hardware rcp.approx.f32; tile sums enter
+// TwoSum-compensated FP32 accumulators.  The per-pair arithmetic (FP32 near
+// pairs and float-float pairs) is shared with the FMM near field.
 #include <algorithm>
 
 #include "bie_internal.cuh"
+#include "pair_math.cuh"
 #include "reduce.cuh"
 
 namespace bie {
 
 namespace {
-
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
 
 // ------------------------------------------------------------------ FP64 ----
 constexpr int kB64 = 128, kT64 = 2, kTile64 = 128;
@@ -140,23 +136,11 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ pf, const f
     const float2 q = sq[l];
 #pragma unroll
     for (int k = 0; k < kT32; ++k) {
-      const float dx = (txh[k] - p.x) + (txl[k] - p.z);
-      const float dy = (tyh[k] - p.y) + (tyl[k] - p.w);
-      const float r2 = fmaf(dx, dx, dy * dy);
-      const float inv = rcp_approx(r2);
-      if (KIND == 0) {
-        float s = q.x * inv;
-        if (DIAG) s = (a0 + k * kB32 == jt + l) ? 0.0f : s;
-        ax[k] = fmaf(dx, s, ax[k]);
-        ay[k] = fmaf(dy, s, ay[k]);
-      } else {
-        const float rq = fmaf(dx, q.x, dy * q.y);
-        const float rn = fmaf(dx, tnx[k], dy * tny[k]);
-        float c = (rq * rn) * (inv * inv);
-        if (DIAG) c = (a0 + k * kB32 == jt + l) ? 0.0f : c;
-        ax[k] = fmaf(c, dx, ax[k]);
-        ay[k] = fmaf(c, dy, ay[k]);
-      }
+      float cx, cy;
+      f32_pair<KIND>(txh[k], tyh[k], txl[k], tyl[k], tnx[k], tny[k], p, q.x, q.y, cx, cy);
+      if (DIAG && a0 + k * kB32 == jt + l) cx = cy = 0.0f;  // the self pair (r = 0)
+      ax[k] += cx;
+      ay[k] += cy;
     }
   }
 }
@@ -369,90 +353,19 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
 //    a tile and across tiles (no FP64 in the loop: GB300's FP64 pipe is slow).
 constexpr int kBF = 64, kTF = 4, kTileF = 256;
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (ah + al)(bh + bl) as an unevaluated pair (p, e), |e| <~ 2^-22 |p|
-__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& p, float& e) {
-  p = ah * bh;
-  e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, fmaf(al, bh, e));
-}
-
-// float-float difference of two exactly split coordinates
-__device__ __forceinline__ void ff_diff(float ah, float am, float al, float bh, float bm, float bl, float& dh,
-                                        float& dl) {
-  const float d1 = ah - bh;  // exact: multiples of 2^-Q below 2^23 quanta
-  const float d2 = am - bm;  // exact likewise
-  dh = d1 + d2;              // |d1| >= |d2| unless d1 = 0: fast two-sum
-  dl = (d2 - (dh - d1)) + (al - bl);
-}
-
-// (sh, sl) += (th, tl)
-__device__ __forceinline__ void ff_acc(float& sh, float& sl, float th, float tl) {
-  float u, e;
-  two_sum(sh, th, u, e);
-  sh = u;
-  sl += e + tl;
-}
-
 template <int KIND, bool DIAG>
 __device__ __forceinline__ void tile_ff(const float4* __restrict__ sa, const float2* __restrict__ sb,
-                                        const float4* __restrict__ sq, int nt, int jt, int a0, const float* txh,
-                                        const float* txm, const float* txl, const float* tyh, const float* tym,
-                                        const float* tyl, const float4* tn, float* axh, float* axl, float* ayh,
-                                        float* ayl) {
+                                        const float4* __restrict__ sq, int nt, int jt, int a0, const FFTarget* t,
+                                        float* axh, float* axl, float* ayh, float* ayl) {
   for (int l = 0; l < nt; ++l) {
     const float4 pa = sa[l];  // (xh, xm, yh, ym)
     const float2 pb = sb[l];  // (xl, yl)
     const float4 q = sq[l];   // (q1h, q1l, q2h, q2l)
 #pragma unroll
     for (int k = 0; k < kTF; ++k) {
-      float dxh, dxl, dyh, dyl;
-      ff_diff(txh[k], txm[k], txl[k], pa.x, pa.y, pb.x, dxh, dxl);
-      ff_diff(tyh[k], tym[k], tyl[k], pa.z, pa.w, pb.y, dyh, dyl);
-      // r2 = dx^2 + dy^2: error-free squares, Fast2Sum of the two (both >= 0,
-      // ordered by max/min), then the cross terms and renormalisation
-      const float p1 = dxh * dxh, p1e = fmaf(dxh, dxh, -p1);
-      const float p2 = dyh * dyh, p2e = fmaf(dyh, dyh, -p2);
-      const float s = p1 + p2;
-      const float se = fminf(p1, p2) - (s - fmaxf(p1, p2));
-      const float lo = fmaf(2.0f, fmaf(dxh, dxl, dyh * dyl), (se + p1e) + p2e);
-      const float r2h = s + lo;
-      const float r2l = lo - (r2h - s);
-      // 1/r2
-      const float y0 = rcp_approx(r2h);
-      const float ee = fmaf(-r2l, y0, fmaf(-r2h, y0, 1.0f));
-      const float il = y0 * ee;
-      float ch, cl;  // the scalar factor multiplying r
-      if (KIND == 0) {
-        ff_mul(q.x, q.y, y0, il, ch, cl);
-      } else {
-        float rqh, rql, rnh, rnl, t1, t1e, t2, t2e, i2h, i2l, uh, ul;
-        // r . q and r . n
-        ff_mul(dxh, dxl, q.x, q.y, t1, t1e);
-        ff_mul(dyh, dyl, q.z, q.w, t2, t2e);
-        two_sum(t1, t2, rqh, rql);
-        rql += t1e + t2e;
-        ff_mul(dxh, dxl, tn[k].x, tn[k].y, t1, t1e);
-        ff_mul(dyh, dyl, tn[k].z, tn[k].w, t2, t2e);
-        two_sum(t1, t2, rnh, rnl);
-        rnl += t1e + t2e;
-        ff_mul(y0, il, y0, il, i2h, i2l);
-        ff_mul(rqh, rql, rnh, rnl, uh, ul);
-        ff_mul(uh, ul, i2h, i2l, ch, cl);
-      }
-      if (DIAG) {
-        const bool self = (a0 + k * kBF == jt + l);
-        ch = self ? 0.0f : ch;
-        cl = self ? 0.0f : cl;
-      }
       float cxh, cxl, cyh, cyl;
-      ff_mul(ch, cl, dxh, dxl, cxh, cxl);
-      ff_mul(ch, cl, dyh, dyl, cyh, cyl);
+      ff_pair<KIND>(t[k], pa, pb, q, cxh, cxl, cyh, cyl);
+      if (DIAG && a0 + k * kBF == jt + l) cxh = cxl = cyh = cyl = 0.0f;  // the self pair
       ff_acc(axh[k], axl[k], cxh, cxl);
       ff_acc(ayh[k], ayl[k], cyh, cyl);
     }
@@ -472,8 +385,7 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
   const int tend = min(M, tbase + kBF * kTF);
   const int a0 = tbase + threadIdx.x;
   const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
-  float txh[kTF], txm[kTF], txl[kTF], tyh[kTF], tym[kTF], tyl[kTF];
-  float4 tn[kTF];
+  FFTarget t[kTF];
   // float-float sums over the tiles
   float sxh[kTF], sxl[kTF], syh[kTF], syl[kTF];
 #pragma unroll
@@ -481,13 +393,13 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
     const int a = a0 + k * kBF;
     const float4 p = a < M ? g.xff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 pl = a < M ? g.xfl[a] : make_float2(0.f, 0.f);
-    txh[k] = p.x;
-    txm[k] = p.y;
-    tyh[k] = p.z;
-    tym[k] = p.w;
-    txl[k] = pl.x;
-    tyl[k] = pl.y;
-    tn[k] = (KIND == 1 && a < M) ? g.nff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+    t[k].xh = p.x;
+    t[k].xm = p.y;
+    t[k].yh = p.z;
+    t[k].ym = p.w;
+    t[k].xl = pl.x;
+    t[k].yl = pl.y;
+    t[k].n = (KIND == 1 && a < M) ? g.nff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
     sxh[k] = sxl[k] = syh[k] = syl[k] = 0.f;
   }
   for (int jt = j0; jt < j1; jt += kTileF) {
@@ -507,9 +419,9 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
 #pragma unroll
     for (int k = 0; k < kTF; ++k) axh[k] = axl[k] = ayh[k] = ayl[k] = 0.f;
     if ((jt < tend) && (jt + nt > tbase))
-      tile_ff<KIND, true>(sa, sb, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tn, axh, axl, ayh, ayl);
+      tile_ff<KIND, true>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
     else
-      tile_ff<KIND, false>(sa, sb, sq, nt, jt, a0, txh, txm, txl, tyh, tym, tyl, tn, axh, axl, ayh, ayl);
+      tile_ff<KIND, false>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
 #pragma unroll
     for (int k = 0; k < kTF; ++k) {
       ff_acc(sxh[k], sxl[k], axh[k], axl[k]);

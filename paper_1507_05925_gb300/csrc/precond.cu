@@ -49,63 +49,60 @@ __host__ __device__ __forceinline__ int gj_cols(int nb, int cs) {
 }
 __host__ __device__ __forceinline__ size_t gj_smem_floats(int nb, int cs) {
   const int h = gj_cols(nb, cs);
-  return (size_t)gj_ld(nb) * h + (size_t)h * kPB + 2 * kPB;
+  return (size_t)gj_ld(nb) * h + (size_t)h * kPB + 2 * kPB + 8 * (size_t)h;
 }
 
 // Entry (row r, column c) of the inner operator's diagonal block of body i
-// (sqrt(w)-scaled, weighted completion), in FP32 from FP64 coordinate
-// differences.
+// (sqrt(w)-scaled, weighted completion), in FP32: coordinate differences from
+// the hi/lo split (x = x_hi + x_lo, exact leading differences as in the near
+// tiles of the pair sum), the column's node data staged in shared memory.
 struct BlockRow {
-  int kind, a0;
+  int kind, a;
   float cf, ct;
-  double xc, yc;
-  // row data
-  double xa, ya;
+  float4 pa;  // (x_hi, y_hi, x_lo, y_lo) of the row's node
   float nxa, nya, swa, ka, pa0, pa1;
-  int al, a;
+  int al;
   __device__ BlockRow(const Geo& g, int kind_, int i, int r, double alpha) : kind(kind_) {
-    a0 = g.body_start[i];
+    const int a0 = g.body_start[i];
     cf = (float)(alpha / g.len[i]);
     ct = kind == 1 ? (float)(alpha / g.W[i]) : 0.f;
-    xc = g.xc[i];
-    yc = g.yc[i];
     a = a0 + (kind == 1 ? r >> 1 : r);
     al = kind == 1 ? r & 1 : 0;
-    xa = g.x[a];
-    ya = g.y[a];
-    nxa = (float)g.nx[a];
-    nya = (float)g.ny[a];
+    pa = g.pf[a];
+    const float2 n = g.nf[a];
+    nxa = n.x;
+    nya = n.y;
     swa = (float)g.sw[a];
     ka = (float)g.kappa[a];
-    pa0 = (float)(-(ya - yc));
-    pa1 = (float)(xa - xc);
+    pa0 = (float)(-(g.y[a] - g.yc[i]));
+    pa1 = (float)(g.x[a] - g.xc[i]);
   }
-  __device__ float entry(const Geo& g, int r, int c) const {
-    const int b = a0 + (kind == 1 ? c >> 1 : c);
-    const float swb = (float)g.sw[b];
+  // column data: cp = (x_hi, y_hi, x_lo, y_lo), cw = (sqrt(w), p_1, p_2, node index)
+  __device__ float entry(int r, int c, float4 cp, float4 cw) const {
+    const int b = __float_as_int(cw.w);
+    const float swb = cw.x;
+    const float rx = (pa.x - cp.x) + (pa.z - cp.z), ry = (pa.y - cp.y) + (pa.w - cp.w);
     float k;
     if (kind == 0) {
       if (a == b) {
         k = -ka * (float)kInv4Pi;
       } else {
-        const float rx = (float)(xa - g.x[b]), ry = (float)(ya - g.y[b]);
         k = -(float)kInv2Pi * (rx * nxa + ry * nya) / (rx * rx + ry * ry);
       }
       return (r == c ? 0.5f : 0.f) + swa * swb * (k + cf);
     }
     const int be = c & 1;
     if (a == b) {
-      const float t[2] = {-nya, nxa};
-      k = -0.5f * (float)kInvPi * ka * t[al] * t[be];
+      const float t = al == 0 ? -nya : nxa, u = be == 0 ? -nya : nxa;
+      k = -0.5f * (float)kInvPi * ka * t * u;
     } else {
-      const float rv[2] = {(float)(xa - g.x[b]), (float)(ya - g.y[b])};
-      const float r2 = rv[0] * rv[0] + rv[1] * rv[1];
-      const float rn = rv[0] * nxa + rv[1] * nya;
-      k = -(float)kInvPi * rv[al] * rv[be] * rn / (r2 * r2);
+      const float r2 = rx * rx + ry * ry;
+      const float rn = rx * nxa + ry * nya;
+      k = -(float)kInvPi * (al == 0 ? rx : ry) * (be == 0 ? rx : ry) * rn / (r2 * r2);
     }
-    const float pb = be == 0 ? (float)(-(g.y[b] - yc)) : (float)(g.x[b] - xc);
-    const float pa = al == 0 ? pa0 : pa1;
-    return (r == c ? 0.5f : 0.f) + swa * swb * (k + (al == be ? cf : 0.f) + ct * pa * pb);
+    const float pb = be == 0 ? cw.y : cw.z;
+    const float pa_ = al == 0 ? pa0 : pa1;
+    return (r == c ? 0.5f : 0.f) + swa * swb * (k + (al == be ? cf : 0.f) + ct * pa_ * pb);
   }
 };
 
@@ -151,11 +148,24 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
   float* A = sm;                 // ld x h, column-major
   float* G = A + (size_t)ld * h; // h x kPB: rows K of the local columns
   float* rowbuf = G + (size_t)h * kPB;  // [2][kPB] pivot rows of the panel steps
+  float4* colp = reinterpret_cast<float4*>(rowbuf + 2 * kPB);  // [h] column node positions
+  float4* colw = colp + h;                                       // [h] column node data
   const int r = threadIdx.x;
   const bool live = r < nb;
+  {
+    const int a0 = g.body_start[i];
+    const double xc = g.xc[i], yc = g.yc[i];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      const int c = c0 + j;
+      const int b = a0 + (kind == 1 ? c >> 1 : c);
+      colp[j] = g.pf[b];
+      colw[j] = make_float4((float)g.sw[b], (float)(-(g.y[b] - yc)), (float)(g.x[b] - xc), __int_as_float(b));
+    }
+  }
+  __syncthreads();
   if (live) {
     const BlockRow br(g, kind, i, r, alpha);
-    for (int j = 0; j < nc; ++j) A[j * ld + r] = br.entry(g, r, c0 + j);
+    for (int j = 0; j < nc; ++j) A[j * ld + r] = br.entry(r, c0 + j, colp[j], colw[j]);
   }
   __syncthreads();
   for (int k0 = 0; k0 < nb; k0 += kPB) {
