@@ -60,7 +60,28 @@ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
   acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
 }
 
-struct FmmDev {
+// The same in FP32 (expansions of the inner solves' operator).
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+template <class T2>
+__device__ __forceinline__ T2 cx(double x, double y);
+template <>
+__device__ __forceinline__ double2 cx<double2>(double x, double y) { return make_double2(x, y); }
+template <>
+__device__ __forceinline__ float2 cx<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+
+// Tree and expansion buffers of one apply; T2 = double2 (FP64 expansions) or
+// float2 (FP32 expansions).  Densities Q stay FP64.
+template <class T2>
+struct FmmDevT {
   int L, nb, p, nd, M;
   int nlog;           // the first nlog channels carry the logarithm kernel, the rest Cauchy sums
   double x0, y0, D;
@@ -70,12 +91,14 @@ struct FmmDev {
   const int* count;   // sources per box (all levels)
   const int* tcount;  // targets per box: boxes that need local expansions
   double2* Q;
-  double2* mp;
-  double2* lc;
-  const double2* ops;
+  T2* mp;
+  T2* lc;
+  const T2* ops;
 };
+using FmmDev = FmmDevT<double2>;
 
-__device__ __forceinline__ double2 box_center(const FmmDev& f, int l, int bx, int by, double& s) {
+template <class T2>
+__device__ __forceinline__ double2 box_center(const FmmDevT<T2>& f, int l, int bx, int by, double& s) {
   s = f.D / (double)(1 << l);
   return make_double2(f.x0 + (bx + 0.5) * s, f.y0 + (by + 0.5) * s);
 }
@@ -197,11 +220,13 @@ __global__ void k_fmm_density(Geo g, int nd, double cx0, double cy0, VecRef vr, 
 }
 
 // P2M on the leaves: a_k = sum_j q_j u_j^k, u = (z - c)/s.
-__global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDev f, Geo g, const int* stop) {
+template <class T2>
+__global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ double2 sm[];
-  double2* pw = sm;                       // [p][kChunk + 1]
-  double2* qs = sm + f.p * (kChunk + 1);  // [kChunk][nd]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  T2* pw = sm;                       // [p][kChunk + 1]
+  T2* qs = sm + f.p * (kChunk + 1);  // [kChunk][nd]
   const int b = blockIdx.x;
   const long long box = lev_off(f.L) + b;
   const int s0 = f.start[b], n = f.start[b + 1] - s0;
@@ -209,19 +234,23 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDev f, Geo g, const int* stop
   double s;
   const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
   const int t = threadIdx.x;
-  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  T2 acc[kMaxNd];
+  for (int d = 0; d < kMaxNd; ++d) acc[d] = cx<T2>(0.0, 0.0);
   for (int ch = 0; ch < n; ch += kChunk) {
     const int m = min(kChunk, n - ch);
     if (t < kChunk) {
       if (t < m) {
         const int i = f.perm[s0 + ch + t];
-        const double2 u = make_double2((g.x[i] - c.x) / s, (g.y[i] - c.y) / s);
-        double2 w = make_double2(1.0, 0.0);
+        const T2 u = cx<T2>((g.x[i] - c.x) / s, (g.y[i] - c.y) / s);
+        T2 w = cx<T2>(1.0, 0.0);
         for (int k = 0; k < f.p; ++k) {
           pw[k * (kChunk + 1) + t] = w;
           w = cmul(w, u);
         }
-        for (int d = 0; d < f.nd; ++d) qs[t * f.nd + d] = f.Q[(long long)i * f.nd + d];
+        for (int d = 0; d < f.nd; ++d) {
+          const double2 q = f.Q[(long long)i * f.nd + d];
+          qs[t * f.nd + d] = cx<T2>(q.x, q.y);
+        }
       }
     }
     __syncthreads();
@@ -235,15 +264,18 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDev f, Geo g, const int* stop
 }
 
 // M2M into level l (parents) from level l + 1.
-__global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop) {
+template <class T2>
+__global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ double2 sm[];  // [nd][p]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
   const int n = 1 << l;
   const int b = blockIdx.x, bx = b % n, by = b / n;
   const long long box = lev_off(l) + b;
   if (f.count[box] == 0) return;
   const int t = threadIdx.x;
-  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  T2 acc[kMaxNd];
+  for (int d = 0; d < kMaxNd; ++d) acc[d] = cx<T2>(0.0, 0.0);
   for (int c = 0; c < 4; ++c) {
     const long long child = lev_off(l + 1) + (2 * by + (c >> 1)) * (2 * n) + 2 * bx + (c & 1);
     if (f.count[child] == 0) continue;  // uniform over the block
@@ -251,9 +283,9 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop
     for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[child * f.nd * f.p + e];
     __syncthreads();
     if (t < f.p) {
-      const double2* op = f.ops + (long long)c * f.p * f.p;  // [in][out]
+      const T2* op = f.ops + (long long)c * f.p * f.p;  // [in][out]
       for (int m = 0; m <= t; ++m) {
-        const double2 o = op[m * f.p + t];
+        const T2 o = op[m * f.p + t];
         for (int d = 0; d < f.nd; ++d) cfma(acc[d], o, sm[d * f.p + m]);
       }
     }
@@ -264,10 +296,20 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDev f, int l, const int* stop
 
 // M2L for the target boxes of all levels 2..L (one block per box).  Cauchy
 // channels: b = (1/s) T_D a; logarithm channels: b = T^log_D a, plus
-// a_0 log(s) on b_0 (the level's share of log d = log D + log s).
-__global__ void __launch_bounds__(kB) k_fmm_m2l(FmmDev f, const int* stop) {
+// a_0 log(s) on b_0 (the level's share of log d = log D + log s).  The
+// multipoles of the whole interaction list (at most 27 boxes) are staged in
+// shared memory behind one barrier; thread e < p nd computes coefficient
+// e % p of channel e / p.
+constexpr int kBM = 128;
+constexpr int kMaxList = 27;
+
+template <class T2>
+__global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ double2 sm[];  // [nd][p]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);  // [kMaxList][nd][p]
+  __shared__ int soi[kMaxList];
+  __shared__ int ns;
   long long gb = blockIdx.x + lev_off(2);
   int l = 2;
   while (l < f.L && gb >= lev_off(l + 1)) ++l;
@@ -276,48 +318,52 @@ __global__ void __launch_bounds__(kB) k_fmm_m2l(FmmDev f, const int* stop) {
   const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
   const int px = bx >> 1, py = by >> 1;
   const double s = f.D / (double)n;
+  const int np = f.nd * f.p;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int sy = max(0, 2 * py - 2); sy <= min(n - 1, 2 * py + 3); ++sy)
+      for (int sx = max(0, 2 * px - 2); sx <= min(n - 1, 2 * px + 3); ++sx) {
+        if (abs(sx - bx) <= 1 && abs(sy - by) <= 1) continue;
+        const long long src = lev_off(l) + sy * n + sx;
+        if (f.count[src] == 0) continue;
+        soi[c++] = (int)(src - lev_off(l)) * 64 + (bx - sx + 3) + 7 * (by - sy + 3);
+      }
+    ns = c;
+  }
+  __syncthreads();
+  const int cnt = ns;
+  for (int e = threadIdx.x; e < cnt * np; e += kBM) {
+    const int q = e / np, r = e % np;
+    const long long src = lev_off(l) + soi[q] / 64;
+    sm[e] = f.mp[src * np + r];
+  }
+  __syncthreads();
   const double logs = log(s);
-  const int t = threadIdx.x;
-  double2 acc[kMaxNd] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-  for (int sy = max(0, 2 * py - 2); sy <= min(n - 1, 2 * py + 3); ++sy) {
-    for (int sx = max(0, 2 * px - 2); sx <= min(n - 1, 2 * px + 3); ++sx) {
-      if (abs(sx - bx) <= 1 && abs(sy - by) <= 1) continue;
-      const long long src = lev_off(l) + sy * n + sx;
-      if (f.count[src] == 0) continue;
-      __syncthreads();
-      for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[src * f.nd * f.p + e];
-      __syncthreads();
-      if (t < f.p) {
-        const int oi = (bx - sx + 3) + 7 * (by - sy + 3);
-        const double2* opc = f.ops + (long long)(8 + oi) * f.p * f.p;
-        const double2* opl = f.ops + (long long)(57 + oi) * f.p * f.p;
-        for (int k = 0; k < f.p; ++k) {
-          const double2 oc = opc[k * f.p + t];
-          for (int d = f.nlog; d < f.nd; ++d) cfma(acc[d], oc, sm[d * f.p + k]);
-          if (f.nlog) {
-            const double2 ol = opl[k * f.p + t];
-            for (int d = 0; d < f.nlog; ++d) cfma(acc[d], ol, sm[d * f.p + k]);
-          }
-        }
-        if (t == 0)
-          for (int d = 0; d < f.nlog; ++d) {
-            acc[d].x += logs * sm[d * f.p].x;
-            acc[d].y += logs * sm[d * f.p].y;
-          }
+  for (int e = threadIdx.x; e < np; e += kBM) {
+    const int d = e / f.p, t = e % f.p;
+    const bool lg = d < f.nlog;
+    T2 acc = cx<T2>(0.0, 0.0);
+    for (int q = 0; q < cnt; ++q) {
+      const int oi = soi[q] % 64;
+      const T2* op = f.ops + (long long)((lg ? 57 : 8) + oi) * f.p * f.p + t;
+      const T2* a = sm + (long long)q * np + d * f.p;
+      for (int k = 0; k < f.p; ++k) cfma(acc, op[(long long)k * f.p], a[k]);
+      if (lg && t == 0) {
+        acc.x += logs * a[0].x;
+        acc.y += logs * a[0].y;
       }
     }
+    const double sc = lg ? 1.0 : 1.0 / s;
+    f.lc[(gb * f.nd + d) * f.p + t] = cx<T2>(acc.x * sc, acc.y * sc);
   }
-  if (t < f.p)
-    for (int d = 0; d < f.nd; ++d) {
-      const double sc = d < f.nlog ? 1.0 : 1.0 / s;
-      f.lc[(gb * f.nd + d) * f.p + t] = make_double2(acc[d].x * sc, acc[d].y * sc);
-    }
 }
 
 // L2L from level l to the children at level l + 1 (added to their M2L part).
-__global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop) {
+template <class T2>
+__global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDevT<T2> f, int l, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ double2 sm[];  // [nd][p]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
   const int nc = 2 << l;
   const int b = blockIdx.x, cx = b % nc, cy = b / nc;
   const long long child = lev_off(l + 1) + b;
@@ -328,9 +374,9 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop
   for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.lc[parent * f.nd * f.p + e];
   __syncthreads();
   if (t < f.p) {
-    const double2* op = f.ops + (long long)(4 + c) * f.p * f.p;
+    const T2* op = f.ops + (long long)(4 + c) * f.p * f.p;
     for (int d = 0; d < f.nd; ++d) {
-      double2 acc = f.lc[(child * f.nd + d) * f.p + t];
+      T2 acc = f.lc[(child * f.nd + d) * f.p + t];
       for (int m = t; m < f.p; ++m) cfma(acc, op[m * f.p + t], sm[d * f.p + m]);
       f.lc[(child * f.nd + d) * f.p + t] = acc;
     }
@@ -345,146 +391,192 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDev f, int l, const int* stop
 // arithmetic of the direct sums (exact leading coordinate differences), so
 // the accuracy follows the operator that uses it: FP32 for the inner solves,
 // float-float for residuals.
-template <int NEARP>
-__global__ void __launch_bounds__(kB) k_fmm_eval(FmmDev f, Geo g, double* __restrict__ partial, const int* stop) {
+constexpr int kNearChunk = 256;  // near-field sources staged per round
+
+template <class T2, int NEARP>
+__global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* __restrict__ partial, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ double2 sm[];  // [nd][p]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
+  // near-field sources of the 3 x 3 leaves, staged in rounds
+  __shared__ float4 spa[kNearChunk];  // FP32: (x_hi, y_hi, x_lo, y_lo); float-float: (xh, xm, yh, ym)
+  __shared__ float2 spb[NEARP == 2 ? kNearChunk : 1];  // float-float: (xl, yl)
+  __shared__ float4 sq[kNearChunk];   // FP32: (q1, q2, -, -); float-float: (q1h, q1l, q2h, q2l)
+  __shared__ int sid[kNearChunk];
+  __shared__ int lst[10], lbeg[9];
   const int b = blockIdx.x, bx = b % f.nb, by = b / f.nb;
   const int s0 = f.start[b], n = f.start[b + 1] - s0;
   if (n == 0) return;
   const long long box = lev_off(f.L) + b;
   for (int e = threadIdx.x; e < f.nd * f.p; e += kB) sm[e] = f.lc[box * f.nd * f.p + e];
+  const int y0 = max(0, by - 1), y1 = min(f.nb - 1, by + 1);
+  const int x0 = max(0, bx - 1), x1 = min(f.nb - 1, bx + 1);
+  if (threadIdx.x == 0) {
+    int c = 0, tot = 0;
+    for (int ny = y0; ny <= y1; ++ny)
+      for (int nx = x0; nx <= x1; ++nx) {
+        const int nl = ny * f.nb + nx;
+        lbeg[c] = f.start[nl];
+        lst[c] = tot;
+        tot += f.start[nl + 1] - f.start[nl];
+        ++c;
+      }
+    for (int k = c; k < 10; ++k) lst[k] = tot;
+  }
   __syncthreads();
+  const int total = lst[9];
   double s;
   const double2 c = box_center(f, f.L, bx, by, s);
-  for (int j = threadIdx.x; j < n; j += kB) {
-    const int i = f.perm[s0 + j];
-    const double2 zi = make_double2(g.x[i], g.y[i]);
-    const double2 u = make_double2((zi.x - c.x) / s, (zi.y - c.y) / s);
-    double2 F[kMaxNd], dF[kMaxNd];
-    for (int d = 0; d < f.nd; ++d) {
-      // Horner for F and F' in u
-      double2 h = sm[d * f.p + f.p - 1], dh = make_double2(0.0, 0.0);
-      for (int l = f.p - 2; l >= 0; --l) {
-        dh = cadd(cmul(dh, u), h);
-        h = cadd(cmul(h, u), sm[d * f.p + l]);
+  for (int j0 = 0; j0 < n; j0 += kB) {
+    const int j = j0 + threadIdx.x;
+    const bool act = j < n;
+    const int i = act ? f.perm[s0 + j] : 0;
+    double ox = 0.0, oy = 0.0;
+    const double nx1 = act ? g.nx[i] : 0.0, ny1 = act ? g.ny[i] : 0.0;
+    if (act) {
+      const double2 zi = make_double2(g.x[i], g.y[i]);
+      const T2 u = cx<T2>((zi.x - c.x) / s, (zi.y - c.y) / s);
+      double2 F[kMaxNd], dF[kMaxNd];
+      for (int d = 0; d < f.nd; ++d) {
+        // Horner for F and F' in u
+        T2 h = sm[d * f.p + f.p - 1], dh = cx<T2>(0.0, 0.0);
+        for (int l = f.p - 2; l >= 0; --l) {
+          dh = cadd(cmul(dh, u), h);
+          h = cadd(cmul(h, u), sm[d * f.p + l]);
+        }
+        F[d] = to_d2(h);
+        dF[d] = make_double2((double)dh.x / s, (double)dh.y / s);
       }
-      F[d] = h;
-      dF[d] = make_double2(dh.x / s, dh.y / s);
-    }
-    const int y0 = max(0, by - 1), y1 = min(f.nb - 1, by + 1);
-    const int x0 = max(0, bx - 1), x1 = min(f.nb - 1, bx + 1);
-    if (NEARP == 0) {
-      // near field: 3 x 3 leaves, as Cauchy terms
-      for (int ny = y0; ny <= y1; ++ny) {
-        for (int nx = x0; nx <= x1; ++nx) {
-          const int nl = ny * f.nb + nx;
-          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
-            const int i2 = f.perm[k];
-            if (i2 == i) continue;
-            const double rx = zi.x - g.x[i2], ry = zi.y - g.y[i2];
-            const double inv = 1.0 / (rx * rx + ry * ry);
-            const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
-            const double2 r2 = cmul(r1, r1);
-            for (int d = 0; d < f.nd; ++d) {
-              const double2 q = f.Q[(long long)i2 * f.nd + d];
-              cfma(F[d], q, r1);
-              cfma(dF[d], make_double2(-q.x, -q.y), r2);
+      if constexpr (NEARP == 0) {
+        // near field: 3 x 3 leaves, as Cauchy terms
+        for (int ny = y0; ny <= y1; ++ny) {
+          for (int nx = x0; nx <= x1; ++nx) {
+            const int nl = ny * f.nb + nx;
+            for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
+              const int i2 = f.perm[k];
+              if (i2 == i) continue;
+              const double rx = zi.x - g.x[i2], ry = zi.y - g.y[i2];
+              const double inv = 1.0 / (rx * rx + ry * ry);
+              const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
+              const double2 r2 = cmul(r1, r1);
+              for (int d = 0; d < f.nd; ++d) {
+                const double2 q = f.Q[(long long)i2 * f.nd + d];
+                cfma(F[d], q, r1);
+                cfma(dF[d], make_double2(-q.x, -q.y), r2);
+              }
             }
           }
         }
       }
-    }
-    // the kernel's combination of the Cauchy sums
-    const double nx1 = g.nx[i], ny1 = g.ny[i];
-    double ox, oy = 0.0;
-    if (f.nd == 1) {
-      ox = nx1 * F[0].x - ny1 * F[0].y;
-    } else {
-      const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
-      const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-dF[2].x, -dF[2].y);
-      const double2 S6 = F[1];
-      const double2 zb = make_double2(zi.x - (f.x0 + 0.5 * f.D), -(zi.y - (f.y0 + 0.5 * f.D)));
-      double2 w = cmul(zb, S2);
-      w = make_double2(w.x - S3.x, w.y - S3.y);
-      double2 tt = cmul(nub, cconj(w));
-      tt = cadd(tt, cmul(nu, cconj(S1)));
-      tt = cadd(tt, cmul(nub, cconj(S6)));
-      tt = cadd(tt, cmul(nu, S1));
-      ox = 0.25 * tt.x;
-      oy = 0.25 * tt.y;
-    }
-    if (NEARP == 1) {
-      const float4 tp = g.pf[i];
-      const float2 tn = g.nf[i];
-      float ax = 0.f, ay = 0.f;
-      for (int ny = y0; ny <= y1; ++ny) {
-        for (int nx = x0; nx <= x1; ++nx) {
-          const int nl = ny * f.nb + nx;
-          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
-            const int i2 = f.perm[k];
-            if (i2 == i) continue;
-            const double2 q = f.Q[(long long)i2 * f.nd];
-            float cx, cy;
-            if (f.nd == 1)
-              f32_pair<0>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, g.pf[i2], (float)q.x, 0.f, cx, cy);
-            else
-              f32_pair<1>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, g.pf[i2], (float)q.x, (float)q.y, cx, cy);
-            ax += cx;
-            ay += cy;
-          }
-        }
+      // the kernel's combination of the Cauchy sums
+      if (f.nd == 1) {
+        ox = nx1 * F[0].x - ny1 * F[0].y;
+      } else {
+        const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
+        const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-dF[2].x, -dF[2].y);
+        const double2 S6 = F[1];
+        const double2 zb = make_double2(zi.x - (f.x0 + 0.5 * f.D), -(zi.y - (f.y0 + 0.5 * f.D)));
+        double2 w = cmul(zb, S2);
+        w = make_double2(w.x - S3.x, w.y - S3.y);
+        double2 tt = cmul(nub, cconj(w));
+        tt = cadd(tt, cmul(nu, cconj(S1)));
+        tt = cadd(tt, cmul(nub, cconj(S6)));
+        tt = cadd(tt, cmul(nu, S1));
+        ox = 0.25 * tt.x;
+        oy = 0.25 * tt.y;
       }
-      if (f.nd == 1)
-        ox += nx1 * (double)ax + ny1 * (double)ay;
-      else {
-        ox += (double)ax;
-        oy += (double)ay;
-      }
-    } else if (NEARP == 2) {
+    }
+    if constexpr (NEARP != 0) {
+      // near field as the real kernel, sources staged through shared memory
+      float4 tp = make_float4(0.f, 0.f, 0.f, 0.f);
+      float2 tn = make_float2(0.f, 0.f);
       FFTarget t;
-      const float4 p = g.xff[i];
-      const float2 pl = g.xfl[i];
-      t.xh = p.x;
-      t.xm = p.y;
-      t.yh = p.z;
-      t.ym = p.w;
-      t.xl = pl.x;
-      t.yl = pl.y;
-      t.n = g.nff[i];
-      float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
-      for (int ny = y0; ny <= y1; ++ny) {
-        for (int nx = x0; nx <= x1; ++nx) {
-          const int nl = ny * f.nb + nx;
-          for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
-            const int i2 = f.perm[k];
-            if (i2 == i) continue;
-            const double2 q = f.Q[(long long)i2 * f.nd];
+      if (act) {
+        if (NEARP == 1) {
+          tp = g.pf[i];
+          tn = g.nf[i];
+        } else {
+          const float4 pp = g.xff[i];
+          const float2 pl = g.xfl[i];
+          t.xh = pp.x;
+          t.xm = pp.y;
+          t.yh = pp.z;
+          t.ym = pp.w;
+          t.xl = pl.x;
+          t.yl = pl.y;
+          t.n = g.nff[i];
+        }
+      }
+      float ax = 0.f, ay = 0.f, axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
+      for (int v0 = 0; v0 < total; v0 += kNearChunk) {
+        const int m = min(kNearChunk, total - v0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < m; e += kB) {
+          const int vv = v0 + e;
+          int lf = 0;
+          while (vv >= lst[lf + 1]) ++lf;
+          const int i2 = f.perm[lbeg[lf] + (vv - lst[lf])];
+          sid[e] = i2;
+          const double2 q = f.Q[(long long)i2 * f.nd];
+          if (NEARP == 1) {
+            spa[e] = g.pf[i2];
+            sq[e] = make_float4((float)q.x, (float)q.y, 0.f, 0.f);
+          } else {
+            spa[e] = g.xff[i2];
+            spb[e] = g.xfl[i2];
             const float q1h = (float)q.x, q2h = (float)q.y;
-            const float4 qq = make_float4(q1h, (float)(q.x - (double)q1h), q2h, (float)(q.y - (double)q2h));
-            float cxh, cxl, cyh, cyl;
-            if (f.nd == 1)
-              ff_pair<0>(t, g.xff[i2], g.xfl[i2], qq, cxh, cxl, cyh, cyl);
-            else
-              ff_pair<1>(t, g.xff[i2], g.xfl[i2], qq, cxh, cxl, cyh, cyl);
-            ff_acc(axh, axl, cxh, cxl);
-            ff_acc(ayh, ayl, cyh, cyl);
+            sq[e] = make_float4(q1h, (float)(q.x - (double)q1h), q2h, (float)(q.y - (double)q2h));
+          }
+        }
+        __syncthreads();
+        if (act) {
+          for (int e = 0; e < m; ++e) {
+            if (sid[e] == i) continue;
+            if (NEARP == 1) {
+              float cxv, cyv;
+              if (f.nd == 1)
+                f32_pair<0>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, spa[e], sq[e].x, 0.f, cxv, cyv);
+              else
+                f32_pair<1>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, spa[e], sq[e].x, sq[e].y, cxv, cyv);
+              ax += cxv;
+              ay += cyv;
+            } else {
+              float cxh, cxl, cyh, cyl;
+              if (f.nd == 1)
+                ff_pair<0>(t, spa[e], spb[e], sq[e], cxh, cxl, cyh, cyl);
+              else
+                ff_pair<1>(t, spa[e], spb[e], sq[e], cxh, cxl, cyh, cyl);
+              ff_acc(axh, axl, cxh, cxl);
+              ff_acc(ayh, ayl, cyh, cyl);
+            }
           }
         }
       }
-      const double ax = (double)axh + (double)axl, ay = (double)ayh + (double)ayl;
-      if (f.nd == 1)
-        ox += nx1 * ax + ny1 * ay;
-      else {
-        ox += ax;
-        oy += ay;
+      if (NEARP == 2) {
+        ax = 0.f;  // unused
+        const double dax = (double)axh + (double)axl, day = (double)ayh + (double)ayl;
+        if (f.nd == 1)
+          ox += nx1 * dax + ny1 * day;
+        else {
+          ox += dax;
+          oy += day;
+        }
+      } else {
+        if (f.nd == 1)
+          ox += nx1 * (double)ax + ny1 * (double)ay;
+        else {
+          ox += (double)ax;
+          oy += (double)ay;
+        }
       }
     }
-    if (f.nd == 1) {
-      partial[i] = ox;
-    } else {
-      partial[2 * i] = ox;
-      partial[2 * i + 1] = oy;
+    if (act) {
+      if (f.nd == 1) {
+        partial[i] = ox;
+      } else {
+        partial[2 * i] = ox;
+        partial[2 * i + 1] = oy;
+      }
     }
   }
 }
@@ -635,14 +727,16 @@ struct FmmState {
   double2 *Q = nullptr, *mp = nullptr, *lc = nullptr;
   double* scal = nullptr;
   int pmax = 0;
-  // operators per order
+  // operators per order (FP64, and their FP32 copies)
   std::vector<std::pair<int, double2*>> ops;
+  std::vector<std::pair<int, float2*>> ops32;
 };
 
 void fmm_free(FmmState* f, cudaStream_t s) {
   if (!f) return;
   if (f->buf) cudaFreeAsync(f->buf, s);
   for (auto& o : f->ops) cudaFreeAsync(o.second, s);
+  for (auto& o : f->ops32) cudaFreeAsync(o.second, s);
   delete f;
 }
 
@@ -742,40 +836,71 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
     for (auto& o : f->ops) have |= o.first == p;
     if (have) continue;
     const auto host = build_ops(p);
+    std::vector<float2> host32(host.size());
+    for (size_t e = 0; e < host.size(); ++e)
+      host32[e] = make_float2((float)host[e].real(), (float)host[e].imag());
     double2* ops = nullptr;
+    float2* ops32 = nullptr;
     if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&ops), host.size() * sizeof(double2), s), "fmm ops") ||
+        !ck(cudaMallocAsync(reinterpret_cast<void**>(&ops32), host32.size() * sizeof(float2), s), "fmm ops") ||
         !ck(cudaMemcpyAsync(ops, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice, s), "fmm ops") ||
+        !ck(cudaMemcpyAsync(ops32, host32.data(), host32.size() * sizeof(float2), cudaMemcpyHostToDevice, s),
+            "fmm ops") ||
         !ck(cudaStreamSynchronize(s), "fmm ops"))
       return BIE_ERR_CUDA;
     f->ops.push_back({p, ops});
+    f->ops32.push_back({p, ops32});
   }
   return BIE_OK;
 }
+
+namespace {
+
+// The upward pass, M2L, downward pass and evaluation with expansions of type T2.
+template <class T2, int NEARP>
+void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial, const int* stop, cudaStream_t s) {
+  const int p = d.p, nd = d.nd;
+  const size_t sm_exp = (size_t)nd * p * sizeof(T2);
+  const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(T2);
+  k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<T2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
+  const size_t sm_m2l = (size_t)kMaxList * nd * p * sizeof(T2);
+  cudaFuncSetAttribute(k_fmm_m2l<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2l);
+  k_fmm_m2l<T2><<<(int)(lev_off(f->L + 1) - lev_off(2)), kBM, sm_m2l, s>>>(d, stop);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<T2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
+  k_fmm_eval<T2, NEARP><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+}
+
+}  // namespace
 
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
                          double* partial, const int* stop, cudaStream_t s, int near_prec) {
   if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;
   double2* ops = nullptr;
+  float2* ops32 = nullptr;
   for (auto& o : f->ops)
     if (o.first == p) ops = o.second;
-  if (!ops) return cudaErrorInvalidValue;  // fmm_setup prepares every order
+  for (auto& o : f->ops32)
+    if (o.first == p) ops32 = o.second;
+  if (!ops || !ops32) return cudaErrorInvalidValue;  // fmm_setup prepares every order
   const int nd = kind == 0 ? 1 : 3;
-  FmmDev d{f->L, f->nb, p, nd, g.M, 0, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->count,
-           f->Q, f->mp, f->lc, ops};
-  const size_t sm_exp = (size_t)nd * p * sizeof(double2);
-  const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
   k_fmm_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, f->x0 + 0.5 * f->D, f->y0 + 0.5 * f->D, v, sscale, f->Q,
                                                stop);
-  k_fmm_p2m<<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
-  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
-  k_fmm_m2l<<<(int)(lev_off(f->L + 1) - lev_off(2)), kB, sm_exp, s>>>(d, stop);
-  for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
-  if (near_prec == 1)
-    k_fmm_eval<1><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
-  else if (near_prec == 2)
-    k_fmm_eval<2><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
-  else
-    k_fmm_eval<0><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
+  if (near_prec == 1) {
+    // the inner solves' operator: FP32 expansions (in the FP64 buffers) and FP32 near field
+    const FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,
+                            f->x0,    f->y0,     f->D,     f->leaf,  f->perm, f->start,
+                            f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
+                            reinterpret_cast<float2*>(f->lc), ops32};
+    fmm_passes<float2, 1>(d, f, g, partial, stop, s);
+  } else {
+    const FmmDev d{f->L, f->nb, p, nd, g.M, 0, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->count,
+                   f->Q, f->mp, f->lc, ops};
+    if (near_prec == 2)
+      fmm_passes<double2, 2>(d, f, g, partial, stop, s);
+    else
+      fmm_passes<double2, 0>(d, f, g, partial, stop, s);
+  }
   note_launches(4 + 2 * std::max(0, f->L - 2));
   return cudaGetLastError();
 }
@@ -805,10 +930,12 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
            f->Q, f->mp, f->lc, ops};
   const size_t sm_exp = (size_t)nd * p * sizeof(double2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
-  k_fmm_p2m<<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
-  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
-  k_fmm_m2l<<<(int)(lev_off(f->L + 1) - lev_off(2)), kB, sm_exp, s>>>(d, nullptr);
-  for (int l = 2; l < f->L; ++l) k_fmm_l2l<<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
+  k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
+  const size_t sm_m2l = (size_t)kMaxList * nd * p * sizeof(double2);
+  cudaFuncSetAttribute(k_fmm_m2l<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2l);
+  k_fmm_m2l<double2><<<(int)(lev_off(f->L + 1) - lev_off(2)), kBM, sm_m2l, s>>>(d, nullptr);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
   k_fmm_eval_targets<<<grid_for(T), 256, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y, part);
   note_launches(7 + f->L + 2 * std::max(0, f->L - 2));
   return cudaGetLastError();
