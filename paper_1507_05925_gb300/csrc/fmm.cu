@@ -5,7 +5,7 @@
 // Laplace (Section 3.4): with q = w mu (real) and nu = n1 + i n2 at the target,
 //   sum_b q_b (r . n_a)/|r|^2 = Re(nu_a F_q(z_a)).
 // Stokes traction (Section 4.3): with q = w (mu1 + i mu2) complex, and
-//   S1 = F_q, S2 = -F'_q, S3 = -F'_{q conj(z - c0)}, S6 = F_{conj q} (any fixed c0),
+//   S1 = F_q, S2 = -F'_q, S3 = -F'_{q conj(z - c0)}, S6 = F_{conj q} (any c0 fixed for the target),
 //   sum_b r (r . q_b)(r . n_a)/|r|^4 =
 //     (1/4) [ conj(nu) conj(conj(z_a - c0) S2 - S3) + nu conj(S1) + conj(nu) conj(S6) + nu S1 ],
 // an identity of complex algebra (r . m = Re(r conj(m)) for complex r, m).
@@ -22,6 +22,13 @@
 //   M2L  b_l  = (1/s) sum_k (-1)^l C(k+l,l) D^-(k+l+1) a_k,  D = d/s (integer offset)
 //   L2L  b'_m = sum_{l>=m} C(l,m) 2^-m w^(l-m) b_l
 // The near field (the 3 x 3 leaves around a target's leaf) is summed directly.
+// For the pair sums the S3 channel carries, in every box B, the box-relative
+// density q conj(z - c_B)/s_B, so that the combination conj(z_a - c) S2 - S3
+// is formed about the target's own leaf centre c: about one global c0 its two
+// terms grow with |z_a - c0| and cancel, which costs FP32 expansions their
+// accuracy.  The translations add the exact shift terms: M2M takes
+// 1/2 a_B + gamma a_0 (gamma = conj(c_child - c_parent)/(2 s_child)), M2L
+// a_S - conj(D) a_0, L2L 2 b_P + delta b_0 (delta = conj(c_P - c_C)/s_C).
 // Nodes are grouped by leaf with a counting sort whose order inside a leaf is
 // the node order, so every sum runs in a fixed order (deterministic results).
 #include <cuda_runtime.h>
@@ -84,6 +91,7 @@ template <class T2>
 struct FmmDevT {
   int L, nb, p, nd, M;
   int nlog;           // the first nlog channels carry the logarithm kernel, the rest Cauchy sums
+  int cm;             // channel with the box-relative moment density q conj(z - c_B)/s_B (-1: none)
   double x0, y0, D;
   const int* leaf;
   const int* perm;
@@ -248,8 +256,11 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int*
           w = cmul(w, u);
         }
         for (int d = 0; d < f.nd; ++d) {
-          const double2 q = f.Q[(long long)i * f.nd + d];
-          qs[t * f.nd + d] = cx<T2>(q.x, q.y);
+          const double2 q = f.Q[(long long)i * f.nd + (d == f.cm ? 0 : d)];
+          // channel cm: q conj(u), the leaf-relative moment density
+          qs[t * f.nd + d] = d == f.cm ? cx<T2>(q.x * (double)u.x + q.y * (double)u.y,
+                                                q.y * (double)u.x - q.x * (double)u.y)
+                                       : cx<T2>(q.x, q.y);
         }
       }
     }
@@ -282,6 +293,18 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int*
     __syncthreads();
     for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[child * f.nd * f.p + e];
     __syncthreads();
+    if (f.cm >= 0) {
+      // child moment density relative to the parent centre: 1/2 rho_C + gamma rho_0,
+      // gamma = conj(c_C - c_P)/(2 s_C)
+      __syncthreads();
+      const T2 gam = cx<T2>(0.5 * ((c & 1) - 0.5), -0.5 * ((c >> 1) - 0.5));
+      for (int m = t; m < f.p; m += kB) {
+        T2 v = cx<T2>(0.5 * (double)sm[f.cm * f.p + m].x, 0.5 * (double)sm[f.cm * f.p + m].y);
+        cfma(v, gam, sm[m]);
+        sm[f.cm * f.p + m] = v;
+      }
+      __syncthreads();
+    }
     if (t < f.p) {
       const T2* op = f.ops + (long long)c * f.p * f.p;  // [in][out]
       for (int m = 0; m <= t; ++m) {
@@ -338,6 +361,20 @@ __global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
     sm[e] = f.mp[src * np + r];
   }
   __syncthreads();
+  if (f.cm >= 0) {
+    // source moment density relative to the target centre: rho_S - conj(D) rho_0,
+    // D = (c_T - c_S)/s the integer offset
+    for (int e = threadIdx.x; e < cnt * f.p; e += kBM) {
+      const int q = e / f.p, k = e % f.p;
+      const int oi = soi[q] % 64;
+      const double Dx = oi % 7 - 3, Dy = oi / 7 - 3;
+      T2* a = sm + (long long)q * np;
+      T2 v = a[f.cm * f.p + k];
+      cfma(v, cx<T2>(-Dx, Dy), a[k]);
+      a[f.cm * f.p + k] = v;
+    }
+    __syncthreads();
+  }
   const double logs = log(s);
   for (int e = threadIdx.x; e < np; e += kBM) {
     const int d = e / f.p, t = e % f.p;
@@ -365,14 +402,25 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDevT<T2> f, int l, const int*
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
   const int nc = 2 << l;
-  const int b = blockIdx.x, cx = b % nc, cy = b / nc;
+  const int b = blockIdx.x, bx = b % nc, by = b / nc;
   const long long child = lev_off(l + 1) + b;
   if (f.tcount[child] == 0) return;
-  const long long parent = lev_off(l) + (cy >> 1) * (nc >> 1) + (cx >> 1);
-  const int c = (cx & 1) + 2 * (cy & 1);
+  const long long parent = lev_off(l) + (by >> 1) * (nc >> 1) + (bx >> 1);
+  const int c = (bx & 1) + 2 * (by & 1);
   const int t = threadIdx.x;
   for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.lc[parent * f.nd * f.p + e];
   __syncthreads();
+  if (f.cm >= 0) {
+    // moment density relative to the child centre: 2 rho_P + delta rho_0,
+    // delta = conj(c_P - c_C)/s_C
+    const T2 del = cx<T2>(-((c & 1) - 0.5), (c >> 1) - 0.5);
+    for (int m = t; m < f.p; m += kB) {
+      T2 v = cx<T2>(2.0 * (double)sm[f.cm * f.p + m].x, 2.0 * (double)sm[f.cm * f.p + m].y);
+      cfma(v, del, sm[m]);
+      sm[f.cm * f.p + m] = v;
+    }
+    __syncthreads();
+  }
   if (t < f.p) {
     const T2* op = f.ops + (long long)(4 + c) * f.p * f.p;
     for (int d = 0; d < f.nd; ++d) {
@@ -460,7 +508,9 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
               const double2 r1 = make_double2(rx * inv, -ry * inv);  // 1/(z_i - z_j)
               const double2 r2 = cmul(r1, r1);
               for (int d = 0; d < f.nd; ++d) {
-                const double2 q = f.Q[(long long)i2 * f.nd + d];
+                double2 q = f.Q[(long long)i2 * f.nd + (d == f.cm ? 0 : d)];
+                if (d == f.cm)  // leaf-relative moment density q conj(z_j - c)/s
+                  q = cmul(q, make_double2((g.x[i2] - c.x) / s, -(g.y[i2] - c.y) / s));
                 cfma(F[d], q, r1);
                 cfma(dF[d], make_double2(-q.x, -q.y), r2);
               }
@@ -473,9 +523,10 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
         ox = nx1 * F[0].x - ny1 * F[0].y;
       } else {
         const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
-        const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-dF[2].x, -dF[2].y);
+        // S3 = -F'_{q conj(z_j - c)} with c the leaf centre (channel cm holds that density / s)
+        const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-s * dF[2].x, -s * dF[2].y);
         const double2 S6 = F[1];
-        const double2 zb = make_double2(zi.x - (f.x0 + 0.5 * f.D), -(zi.y - (f.y0 + 0.5 * f.D)));
+        const double2 zb = make_double2(zi.x - c.x, -(zi.y - c.y));
         double2 w = cmul(zb, S2);
         w = make_double2(w.x - S3.x, w.y - S3.y);
         double2 tt = cmul(nub, cconj(w));
@@ -888,14 +939,14 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
                                                stop);
   if (near_prec == 1) {
     // the inner solves' operator: FP32 expansions (in the FP64 buffers) and FP32 near field
-    const FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,
+    const FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,       kind == 1 ? 2 : -1,
                             f->x0,    f->y0,     f->D,     f->leaf,  f->perm, f->start,
                             f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
                             reinterpret_cast<float2*>(f->lc), ops32};
     fmm_passes<float2, 1>(d, f, g, partial, stop, s);
   } else {
-    const FmmDev d{f->L, f->nb, p, nd, g.M, 0, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->count,
-                   f->Q, f->mp, f->lc, ops};
+    const FmmDev d{f->L,    f->nb,    p,     nd,    g.M,   0,   kind == 1 ? 2 : -1, f->x0, f->y0, f->D, f->leaf,
+                   f->perm, f->start, f->count, f->count, f->Q, f->mp, f->lc,  ops};
     if (near_prec == 2)
       fmm_passes<double2, 2>(d, f, g, partial, stop, s);
     else
@@ -926,7 +977,7 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
                                           f->tcount + lev_off(f->L));
   for (int l = f->L - 1; l >= 0; --l) k_fmm_parent_counts<<<grid_for(1LL << (2 * l)), 256, 0, s>>>(l, f->tcount);
   k_fmm_out_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, c0x, c0y, v, f->Q);
-  FmmDev d{f->L, f->nb, p, nd, g.M, nlog, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
+  FmmDev d{f->L, f->nb, p, nd, g.M, nlog, -1, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
            f->Q, f->mp, f->lc, ops};
   const size_t sm_exp = (size_t)nd * p * sizeof(double2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
