@@ -76,7 +76,23 @@ def dist_env():
 
 
 def workload(rank: int):
+    """Each rank solves its own replica: the 100-star workload with a rank seed."""
     return synth.star_grid(seed=1000 + rank)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's (a no-op without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank did `steps` units in at most `seconds`."""
+    return world * steps / seconds
 
 
 # ---------------------------------------------------------------------------
@@ -476,12 +492,8 @@ def main():
     cs.__exit__(None, None, None)
     clocks = cs.summary()
     phi_mixed = phi.clone()
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(ms), dist, dev)
+    value = job_rate(world, args.steps, total_ms / 1000.0)
 
     # the other mixed-precision residual and the plain FP64 GPU path on the same workload
     for _ in range(2):
@@ -509,12 +521,8 @@ def main():
         rc, _ = bie.elastance_solve(ctx, host, qh, phih, opts=mixed, stream=stream)
         assert rc == bie.OK
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_rate = world * args.e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_rate = job_rate(world, args.e2e_steps, e2e_s)
     assert np.array_equal(phih.numpy(), phi_mixed.cpu().numpy()), "host and device paths disagree"
 
     # dominant kernel of the timed mixed-precision solves
