@@ -135,9 +135,15 @@ typedef struct {
   int32_t matvecs_fp64;        /* FP64 operator applications */
   int32_t matvecs_fp32;        /* FP32-pair-sum operator applications */
   int32_t matvecs_ff;          /* float-float-pair-sum operator applications */
-  double rel_residual;         /* final ||f - A nu|| / ||f|| with the FP64 operator */
+  double rel_residual;         /* final ||f - A nu|| / ||f|| in the sqrt(w)-scaled norm: with the
+                                  FP64 operator, or (MIXED_FF without FMM) the residual updated
+                                  with FP32 pair sums after the first true one plus the bound
+                                  3 fp32_error sum ||A32 d|| of that update */
   double constraint_residual;  /* max_i |int_{Gamma_i} mu| (and Stokes moments) / max load */
   double net_load;             /* |sum_i q_i| or |sum_i F_i| */
+  double fp32_error;           /* mixed: ||A32 x - A x|| / ||A x|| at the first refinement step,
+                                  A32 the FP32-pair-sum operator of the inner solves and A the
+                                  residual operator (FP64 or float-float); 0 for FP64 solves */
 } bie_info;
 
 /* Elastance solve (Section 3): charges q [N] -> conductor potentials phi [N].

@@ -41,7 +41,7 @@ class BieInfo(ctypes.Structure):
                 ("matvecs_fp64", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32),
                 ("matvecs_ff", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("constraint_residual", ctypes.c_double),
-                ("net_load", ctypes.c_double)]
+                ("net_load", ctypes.c_double), ("fp32_error", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -630,7 +630,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   // or the FMM of the full order
   const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0, 0.0, fres};
   int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, mff = 0, iters = 0, refs = 0;
-  double relres = 0.0;
+  double relres = 0.0, eps32_report = 0.0;
   bool converged = false;
   if (o.precision == BIE_PREC_FP64) {
     KrylovResult kr;
@@ -670,7 +670,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     // geometry (A32 x against A_ff x at the first step) and the accumulated
     // bound 3 eps32 sum ||A32 d|| added to ||r|| before comparing with tol.
     const bool recursive = o.precision == BIE_PREC_MIXED_FF && o.fmm_order == 0;
-    const Op op32p{ctx, &w, 1, 0.0, 0};  // FP32 pair sums, the paper's completion
+    const Op op32p{ctx, &w, 1, 0.0, fin};  // FP32 pair sums (or FP32 FMM), the paper's completion
     double eps32 = -1.0, bound = 0.0;
     bool true_residual = true;
     while (!converged && refs < o.max_refine && remaining > 0) {
@@ -697,8 +697,9 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
         if ((rc = norm_of(w.f, w.ytmp, w.r))) return rc;
         rnorm = ctx->h_state->rnorm;
         bound = 0.0;
-        if (recursive && eps32 < 0.0) {
-          // eps32 = ||A_ff x - A32 x|| / ||A_ff x||
+        if (eps32 < 0.0) {
+          // eps32 = ||A x - A32 x|| / ||A x||, A the residual operator (reported; the
+          // float-float refinement's residual update bound uses it)
           CK(op32p.apply(vec(w.xs), vec(w.rin), nullptr, s));
           m32 += 1;
           if ((rc = norm_of(w.ytmp, w.rin, w.rc))) return rc;
@@ -713,6 +714,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
       if (kr.iters == 0) break;
     }
     relres = fnorm > 0 ? rnorm / fnorm : 0.0;
+    eps32_report = eps32 > 0.0 ? eps32 : 0.0;
   }
   // total density (scaled): nu = x (total form) or mu + sigma (paper form)
   double* v = w.xs;
@@ -748,6 +750,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     info->rel_residual = relres;
     info->constraint_residual = ctx->h_small[0];
     info->net_load = netload;
+    info->fp32_error = eps32_report;
   }
   if (!converged) return BIE_WARN_NOT_CONVERGED;
   if (netload > 1e-12 * std::max(maxload, 1e-300) * std::max(1, N)) return BIE_WARN_NONNEUTRAL;

@@ -125,6 +125,11 @@ def test_elastance_solve(ctx, name, prec, form):
     assert e_den <= 1e-9
     assert info["rel_residual"] <= 1e-12
     assert info["constraint_residual"] <= 1e-10
+    # the FP32 operator's measured error is reported by mixed solves only
+    if prec == bie.FP64:
+        assert info["fp32_error"] == 0.0
+    else:
+        assert 0.0 < info["fp32_error"] < TOL32[0]
 
 
 @pytest.mark.parametrize("name", ["ragged4", "multitile"])
@@ -433,6 +438,7 @@ def test_refinement_residual_is_certified(ctx, wl, kind):
     print(f"{wl} kind={kind}: reported {info['rel_residual']:.2e} true {true_rel:.2e} {info}")
     assert info["rel_residual"] <= 1e-12
     assert true_rel <= 1.5 * info["rel_residual"] + 1e-14
+    assert 0.0 < info["fp32_error"] < TOL32[kind]
 
 
 def _check_full_size(g, geo, kind, res, nu, info, res64):
