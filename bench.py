@@ -60,6 +60,8 @@ def parse():
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--fmm-order", type=int, default=36)
+    ap.add_argument("--only-large", action="store_true",
+                    help="run only the large mobility section (FMM), e.g. for ncu captures")
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
@@ -423,6 +425,11 @@ def main():
         return
     if args.kernel:
         run_kernel(args, local)
+        return
+    if args.only_large:  # the large mobility section alone (profiling)
+        from paper_1507_05925_gb300 import build
+        build.build()
+        print(json.dumps({"large_mobility": run_large(args, rank, local)}))
         return
     import torch
 

@@ -72,6 +72,7 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
   acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
@@ -82,8 +83,6 @@ template <>
 __device__ __forceinline__ double2 cx<double2>(double x, double y) { return make_double2(x, y); }
 template <>
 __device__ __forceinline__ float2 cx<float2>(double x, double y) { return make_float2((float)x, (float)y); }
-__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
-__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
 
 // Tree and expansion buffers of one apply; T2 = double2 (FP64 expansions) or
 // float2 (FP32 expansions).  Densities Q stay FP64.
@@ -92,7 +91,7 @@ struct FmmDevT {
   int L, nb, p, nd, M;
   int nlog;           // the first nlog channels carry the logarithm kernel, the rest Cauchy sums
   int cm;             // channel with the box-relative moment density q conj(z - c_B)/s_B (-1: none)
-  double x0, y0, D;
+  double x0, y0, D, Dinv;  // bounding square: corner, side, 1/side
   const int* leaf;
   const int* perm;
   const int* start;
@@ -107,7 +106,7 @@ using FmmDev = FmmDevT<double2>;
 
 template <class T2>
 __device__ __forceinline__ double2 box_center(const FmmDevT<T2>& f, int l, int bx, int by, double& s) {
-  s = f.D / (double)(1 << l);
+  s = ldexp(f.D, -l);  // exact: no division on the (slow) FP64 pipe
   return make_double2(f.x0 + (bx + 0.5) * s, f.y0 + (by + 0.5) * s);
 }
 
@@ -249,7 +248,8 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int*
     if (t < kChunk) {
       if (t < m) {
         const int i = f.perm[s0 + ch + t];
-        const T2 u = cx<T2>((g.x[i] - c.x) / s, (g.y[i] - c.y) / s);
+        const double is = ldexp(f.Dinv, f.L);
+        const T2 u = cx<T2>((g.x[i] - c.x) * is, (g.y[i] - c.y) * is);
         T2 w = cx<T2>(1.0, 0.0);
         for (int k = 0; k < f.p; ++k) {
           pw[k * (kChunk + 1) + t] = w;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
   const int n = 1 << l;
   const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
   const int px = bx >> 1, py = by >> 1;
-  const double s = f.D / (double)n;
+  const double s = ldexp(f.D, -l), inv_s = ldexp(f.Dinv, l);
   const int np = f.nd * f.p;
   if (threadIdx.x == 0) {
     int c = 0;
@@ -367,15 +367,15 @@ __global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
     for (int e = threadIdx.x; e < cnt * f.p; e += kBM) {
       const int q = e / f.p, k = e % f.p;
       const int oi = soi[q] % 64;
-      const double Dx = oi % 7 - 3, Dy = oi / 7 - 3;
+      const int Dx = oi % 7 - 3, Dy = oi / 7 - 3;
       T2* a = sm + (long long)q * np;
       T2 v = a[f.cm * f.p + k];
-      cfma(v, cx<T2>(-Dx, Dy), a[k]);
+      cfma(v, cx<T2>((double)-Dx, (double)Dy), a[k]);
       a[f.cm * f.p + k] = v;
     }
     __syncthreads();
   }
-  const double logs = log(s);
+  const double logs = f.nlog ? log(s) : 0.0;  // only the output's logarithm channels use it
   for (int e = threadIdx.x; e < np; e += kBM) {
     const int d = e / f.p, t = e % f.p;
     const bool lg = d < f.nlog;
@@ -390,8 +390,11 @@ __global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
         acc.y += logs * a[0].y;
       }
     }
-    const double sc = lg ? 1.0 : 1.0 / s;
-    f.lc[(gb * f.nd + d) * f.p + t] = cx<T2>(acc.x * sc, acc.y * sc);
+    // Cauchy channels carry 1/s; in the precision of the expansions
+    const decltype(acc.x) sc = lg ? 1.0 : inv_s;
+    acc.x *= sc;
+    acc.y *= sc;
+    f.lc[(gb * f.nd + d) * f.p + t] = acc;
   }
 }
 
@@ -475,6 +478,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
   const int total = lst[9];
   double s;
   const double2 c = box_center(f, f.L, bx, by, s);
+  const double inv_s = ldexp(f.Dinv, f.L);
   for (int j0 = 0; j0 < n; j0 += kB) {
     const int j = j0 + threadIdx.x;
     const bool act = j < n;
@@ -483,8 +487,10 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
     const double nx1 = act ? g.nx[i] : 0.0, ny1 = act ? g.ny[i] : 0.0;
     if (act) {
       const double2 zi = make_double2(g.x[i], g.y[i]);
-      const T2 u = cx<T2>((zi.x - c.x) / s, (zi.y - c.y) / s);
-      double2 F[kMaxNd], dF[kMaxNd];
+      const T2 u = cx<T2>((zi.x - c.x) * inv_s, (zi.y - c.y) * inv_s);
+      using R = decltype(u.x);
+      const R is = (R)inv_s;
+      T2 F[kMaxNd], dF[kMaxNd];
       for (int d = 0; d < f.nd; ++d) {
         // Horner for F and F' in u
         T2 h = sm[d * f.p + f.p - 1], dh = cx<T2>(0.0, 0.0);
@@ -492,8 +498,10 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
           dh = cadd(cmul(dh, u), h);
           h = cadd(cmul(h, u), sm[d * f.p + l]);
         }
-        F[d] = to_d2(h);
-        dF[d] = make_double2((double)dh.x / s, (double)dh.y / s);
+        F[d] = h;
+        dF[d] = h;
+        dF[d].x = dh.x * is;
+        dF[d].y = dh.y * is;
       }
       if constexpr (NEARP == 0) {
         // near field: 3 x 3 leaves, as Cauchy terms
@@ -510,7 +518,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
               for (int d = 0; d < f.nd; ++d) {
                 double2 q = f.Q[(long long)i2 * f.nd + (d == f.cm ? 0 : d)];
                 if (d == f.cm)  // leaf-relative moment density q conj(z_j - c)/s
-                  q = cmul(q, make_double2((g.x[i2] - c.x) / s, -(g.y[i2] - c.y) / s));
+                  q = cmul(q, make_double2((g.x[i2] - c.x) * inv_s, -(g.y[i2] - c.y) * inv_s));
                 cfma(F[d], q, r1);
                 cfma(dF[d], make_double2(-q.x, -q.y), r2);
               }
@@ -518,23 +526,30 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
           }
         }
       }
-      // the kernel's combination of the Cauchy sums
+      // the kernel's combination of the Cauchy sums, in the expansions' precision
+      // (about the leaf centre its terms do not cancel)
       if (f.nd == 1) {
-        ox = nx1 * F[0].x - ny1 * F[0].y;
+        ox = (double)((R)nx1 * F[0].x - (R)ny1 * F[0].y);
       } else {
-        const double2 nu = make_double2(nx1, ny1), nub = make_double2(nx1, -ny1);
+        const T2 nu = cx<T2>(nx1, ny1), nub = cx<T2>(nx1, -ny1);
+        const R sl = (R)s;
         // S3 = -F'_{q conj(z_j - c)} with c the leaf centre (channel cm holds that density / s)
-        const double2 S1 = F[0], S2 = make_double2(-dF[0].x, -dF[0].y), S3 = make_double2(-s * dF[2].x, -s * dF[2].y);
-        const double2 S6 = F[1];
-        const double2 zb = make_double2(zi.x - c.x, -(zi.y - c.y));
-        double2 w = cmul(zb, S2);
-        w = make_double2(w.x - S3.x, w.y - S3.y);
-        double2 tt = cmul(nub, cconj(w));
+        T2 S2 = dF[0], S3 = dF[2];
+        S2.x = -S2.x;
+        S2.y = -S2.y;
+        S3.x = -sl * S3.x;
+        S3.y = -sl * S3.y;
+        const T2 S1 = F[0], S6 = F[1];
+        const T2 zb = cx<T2>(zi.x - c.x, -(zi.y - c.y));
+        T2 w = cmul(zb, S2);
+        w.x -= S3.x;
+        w.y -= S3.y;
+        T2 tt = cmul(nub, cconj(w));
         tt = cadd(tt, cmul(nu, cconj(S1)));
         tt = cadd(tt, cmul(nub, cconj(S6)));
         tt = cadd(tt, cmul(nu, S1));
-        ox = 0.25 * tt.x;
-        oy = 0.25 * tt.y;
+        ox = 0.25 * (double)tt.x;
+        oy = 0.25 * (double)tt.y;
       }
     }
     if constexpr (NEARP != 0) {
@@ -940,12 +955,12 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
   if (near_prec == 1) {
     // the inner solves' operator: FP32 expansions (in the FP64 buffers) and FP32 near field
     const FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,       kind == 1 ? 2 : -1,
-                            f->x0,    f->y0,     f->D,     f->leaf,  f->perm, f->start,
+                            f->x0,    f->y0,     f->D,     1.0 / f->D, f->leaf,  f->perm, f->start,
                             f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
                             reinterpret_cast<float2*>(f->lc), ops32};
     fmm_passes<float2, 1>(d, f, g, partial, stop, s);
   } else {
-    const FmmDev d{f->L,    f->nb,    p,     nd,    g.M,   0,   kind == 1 ? 2 : -1, f->x0, f->y0, f->D, f->leaf,
+    const FmmDev d{f->L,    f->nb,    p,     nd,    g.M,   0,   kind == 1 ? 2 : -1, f->x0, f->y0, f->D, 1.0 / f->D, f->leaf,
                    f->perm, f->start, f->count, f->count, f->Q, f->mp, f->lc,  ops};
     if (near_prec == 2)
       fmm_passes<double2, 2>(d, f, g, partial, stop, s);
@@ -977,7 +992,7 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
                                           f->tcount + lev_off(f->L));
   for (int l = f->L - 1; l >= 0; --l) k_fmm_parent_counts<<<grid_for(1LL << (2 * l)), 256, 0, s>>>(l, f->tcount);
   k_fmm_out_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, c0x, c0y, v, f->Q);
-  FmmDev d{f->L, f->nb, p, nd, g.M, nlog, -1, f->x0, f->y0, f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
+  FmmDev d{f->L, f->nb, p, nd, g.M, nlog, -1, f->x0, f->y0, f->D, 1.0 / f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
            f->Q, f->mp, f->lc, ops};
   const size_t sm_exp = (size_t)nd * p * sizeof(double2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
