@@ -43,6 +43,7 @@
 #include "../../include/bie2d.h"
 #include "bie_internal.cuh"
 #include "pair_math.cuh"
+#include "reduce.cuh"
 
 namespace bie {
 
@@ -112,22 +113,29 @@ __device__ __forceinline__ double2 box_center(const FmmDevT<T2>& f, int l, int b
 
 // ------------------------------------------------------------------ setup ----
 // Bounding square of the body boxes and the total arc length.
-__global__ void k_fmm_box(Geo g, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300, len = 0.0;
-  for (int i = 0; i < g.N; ++i) {
+constexpr int kBoxT = 256;
+__global__ void __launch_bounds__(kBoxT) k_fmm_box(Geo g, double* out) {
+  __shared__ double sh[kBoxT / 32];
+  double x0 = 1e300, y0 = 1e300, nx1 = 1e300, ny1 = 1e300, len = 0.0;  // nx1, ny1: -max
+  for (int i = threadIdx.x; i < g.N; i += kBoxT) {
     const float4 b = g.bbox[i];
     x0 = fmin(x0, (double)b.x);
     y0 = fmin(y0, (double)b.y);
-    x1 = fmax(x1, (double)b.z);
-    y1 = fmax(y1, (double)b.w);
+    nx1 = fmin(nx1, -(double)b.z);
+    ny1 = fmin(ny1, -(double)b.w);
     len += g.len[i];
   }
-  const double D = fmax(x1 - x0, y1 - y0) * (1.0 + 1e-6) + 1e-12;
-  out[0] = x0 - 1e-7 * D;
-  out[1] = y0 - 1e-7 * D;
-  out[2] = D * (1.0 + 2e-7);
-  out[3] = len;
+  x0 = block_min<kBoxT>(x0, sh);
+  y0 = block_min<kBoxT>(y0, sh);
+  const double x1 = -block_min<kBoxT>(nx1, sh), y1 = -block_min<kBoxT>(ny1, sh);
+  len = block_sum<kBoxT>(len, sh);
+  if (threadIdx.x == 0) {
+    const double D = fmax(x1 - x0, y1 - y0) * (1.0 + 1e-6) + 1e-12;
+    out[0] = x0 - 1e-7 * D;
+    out[1] = y0 - 1e-7 * D;
+    out[2] = D * (1.0 + 2e-7);
+    out[3] = len;
+  }
 }
 
 __global__ void k_fmm_leaf(Geo g, int L, double x0, double y0, double D, int* leaf, int* cnt) {
@@ -828,7 +836,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
     if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&f->scal), 4 * sizeof(double), s), "fmm scal")) return BIE_ERR_CUDA;
   }
   scal = f->scal;
-  k_fmm_box<<<1, 32, 0, s>>>(g, scal);
+  k_fmm_box<<<1, kBoxT, 0, s>>>(g, scal);
   note_launches(1);
   double h[4];
   if (!ck(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s), "fmm box") ||

@@ -186,21 +186,26 @@ __global__ void k_scale_by(int M, int comps, const double* __restrict__ in, cons
     out[k] = in[k] * fac[k / comps];
 }
 
-__global__ void k_net_load(int N, int kind, const double* __restrict__ load, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s0 = 0, s1 = 0, mx = 0;
-    for (int i = 0; i < N; ++i) {
-      if (kind == 0) {
-        s0 += load[i];
-        mx = fmax(mx, fabs(load[i]));
-      } else {
-        s0 += load[3 * i];
-        s1 += load[3 * i + 1];
-        mx = fmax(mx, fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
-      }
+__global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* __restrict__ load,
+                                                  double* __restrict__ out) {
+  __shared__ double sh[kB / 32];
+  double s0 = 0, s1 = 0, nmx = 0;  // nmx: -max |load|
+  for (int i = threadIdx.x; i < N; i += kB) {
+    if (kind == 0) {
+      s0 += load[i];
+      nmx = fmin(nmx, -fabs(load[i]));
+    } else {
+      s0 += load[3 * i];
+      s1 += load[3 * i + 1];
+      nmx = fmin(nmx, -fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
     }
+  }
+  s0 = block_sum<kB>(s0, sh);
+  s1 = block_sum<kB>(s1, sh);
+  nmx = block_min<kB>(nmx, sh);
+  if (threadIdx.x == 0) {
     out[0] = sqrt(s0 * s0 + s1 * s1);
-    out[1] = mx;
+    out[1] = -nmx;
   }
 }
 
@@ -361,7 +366,7 @@ cudaError_t finalize_output(const Geo& g, int kind, const double* v, const doubl
   double* nl = cbody + g.N;
   k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
   note_launches(1);
-  k_net_load<<<1, 32, 0, s>>>(g.N, kind, load, nl);
+  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, nl);
   note_launches(1);
   k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
   note_launches(1);
@@ -394,7 +399,7 @@ cudaError_t scale_by(const Geo& g, int kind, const double* in, const double* fac
 }
 
 cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s) {
-  k_net_load<<<1, 32, 0, s>>>(N, kind, load, out);
+  k_net_load<<<1, kB, 0, s>>>(N, kind, load, out);
   note_launches(1);
   return cudaGetLastError();
 }

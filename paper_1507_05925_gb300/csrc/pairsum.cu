@@ -448,12 +448,12 @@ constexpr int kBE = 256;
 
 // One block per body: completion moments, then per node
 //   y = Kv (constant applied) + diagonal limit + [L]; out = sign (1/2 v + oscale y).
-template <int KIND>
-__global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double* __restrict__ partial,
+template <int KIND, int B>
+__global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* __restrict__ partial,
                                                   int S, int scaled, int with_L, double alpha, double sign,
                                                   VecRef outr, const int* __restrict__ stop) {
   if (stop && *stop) return;
-  __shared__ double sh[kBE / 32];
+  __shared__ double sh[B / 32];
   const double* __restrict__ v = vr.ptr();
   double* __restrict__ out = outr.ptr();
   const int M = g.M;
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
   const double xc = g.xc[i], yc = g.yc[i];
   double m0 = 0.0, m1 = 0.0, m2 = 0.0;
   if (with_L) {
-    for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+    for (int a = a0 + threadIdx.x; a < a1; a += B) {
       const double s = scaled ? g.sw[a] : g.w[a];
       if (KIND == 0) {
         m0 += s * v[a];
@@ -473,10 +473,10 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
         m2 += -(g.y[a] - yc) * f1 + (g.x[a] - xc) * f2;
       }
     }
-    m0 = block_sum<kBE>(m0, sh);
+    m0 = block_sum<B>(m0, sh);
     if (KIND == 1) {
-      m1 = block_sum<kBE>(m1, sh);
-      m2 = block_sum<kBE>(m2, sh);
+      m1 = block_sum<B>(m1, sh);
+      m2 = block_sum<B>(m2, sh);
     }
     if (alpha > 0.0) {  // completion weighted per body: force part alpha/|Gamma_i|, torque part alpha/W_i
       const double cf = alpha / g.len[i];
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kBE) k_epilogue(Geo g, VecRef vr, const double
       if (KIND == 1) m2 *= alpha / g.W[i];
     }
   }
-  for (int a = a0 + threadIdx.x; a < a1; a += kBE) {
+  for (int a = a0 + threadIdx.x; a < a1; a += B) {
     const double os = scaled ? g.sw[a] : 1.0;
     const double wk = g.w[a] * g.kappa[a];
     if (KIND == 0) {
@@ -634,10 +634,19 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
                      cudaStream_t s, double alpha) {
-  if (kind == 0)
-    k_epilogue<0><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
-  else
-    k_epilogue<1><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+  // one block per body, sized to the bodies (many small bodies: small blocks)
+  const int avg = g.M / std::max(1, g.N);
+  if (avg <= 64) {
+    if (kind == 0)
+      k_epilogue<0, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+    else
+      k_epilogue<1, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+  } else {
+    if (kind == 0)
+      k_epilogue<0, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+    else
+      k_epilogue<1, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
