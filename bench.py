@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--fmm-order", type=int, default=36)
     ap.add_argument("--only-large", action="store_true",
                     help="run only the large mobility section (FMM), e.g. for ncu captures")
+    ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
@@ -426,10 +427,13 @@ def main():
     if args.kernel:
         run_kernel(args, local)
         return
-    if args.only_large:  # the large mobility section alone (profiling)
+    if args.only_large or args.only_serving:  # one section alone (profiling, tuning)
         from paper_1507_05925_gb300 import build
         build.build()
-        print(json.dumps({"large_mobility": run_large(args, rank, local)}))
+        if args.only_large:
+            print(json.dumps({"large_mobility": run_large(args, rank, local)}))
+        else:
+            print(json.dumps({"serving": run_serving(args, rank, local)}))
         return
     import torch
 

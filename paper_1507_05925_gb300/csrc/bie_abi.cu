@@ -25,8 +25,15 @@ constexpr double kInnerCompletionWeight = 1.0;
 
 namespace bie {
 static std::atomic<long long> g_launches{0};
-void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// launches noted by this thread (a capture counts its own kernels while other
+// server threads launch)
+static thread_local long long t_launches = 0;
+void note_launches(int k) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  t_launches += k;
+}
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launches() { return t_launches; }
 }  // namespace bie
 
 struct bie_ctx {
@@ -435,7 +442,7 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
                              w.grid};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
-  const long long before = launches_so_far();
+  const long long before = thread_launches();
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -443,7 +450,7 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   }
   const int rc = launch_iteration(ctx, w, op, s);
   const cudaError_t e = cudaStreamEndCapture(s, &graph);
-  const long long kernels = launches_so_far() - before;
+  const long long kernels = thread_launches() - before;
   note_launches((int)-kernels);  // captured, not launched
   cudaGraphExec_t exec = nullptr;
   if (rc != BIE_OK || e != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {

@@ -21,6 +21,7 @@
 // TwoSum-compensated FP32 accumulators.  The per-pair arithmetic (FP32 near
 // pairs and float-float pairs) is shared with the FMM near field.
 #include <algorithm>
+#include <mutex>
 
 #include "bie_internal.cuh"
 #include "pair_math.cuh"
@@ -563,24 +564,31 @@ struct DeviceShape {
   int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // [precision][kind]
 };
 
+// Per device, filled once under a lock: concurrent server threads must never
+// see a half-filled entry (a different split count changes the summation
+// order of the results).
 const DeviceShape& device_shape() {
   static DeviceShape shapes[64];
+  static std::mutex mu;
   int dev = 0;
   cudaGetDevice(&dev);
   DeviceShape& d = shapes[dev & 63];
+  std::lock_guard<std::mutex> lk(mu);
   if (d.nsm == 0) {
-    cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0][0], k_pair64<0>, kB64, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0][1], k_pair64<1>, kB64, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][0], k_pair32<0>, kB32, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1][1], k_pair32<1>, kB32, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[2][0], k_pair_ff<0>, kBF, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[2][1], k_pair_ff<1>, kBF, 0);
+    DeviceShape t;
+    cudaDeviceGetAttribute(&t.nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][0], k_pair64<0>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][1], k_pair64<1>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][0], k_pair32<0>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][1], k_pair32<1>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][0], k_pair_ff<0>, kBF, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][1], k_pair_ff<1>, kBF, 0);
     cudaGetLastError();
-    if (d.nsm <= 0) d.nsm = 152;
-    for (auto& row : d.occ)
+    if (t.nsm <= 0) t.nsm = 152;
+    for (auto& row : t.occ)
       for (int& o : row)
         if (o <= 0) o = 4;
+    d = t;
   }
   return d;
 }
