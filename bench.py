@@ -41,6 +41,11 @@ METRIC = "elastance solves/s at 1e-12 relative residual (mixed precision: FP32 p
 # q/|r|^2 (1), accumulate q r/|r|^2 (4); Stokes r (2), |r|^2 (3), r.mu (3),
 # r.n (3), (r.mu)(r.n)/|r|^4 (3), accumulate (4)
 FLOPS_PER_PAIR = {"laplace": 10.0, "stokes": 18.0}
+# DRAM bytes (read + write) per launch of the 100-star pair sums, from one ncu
+# capture of the current kernels (profiles/k_pair32_laplace_stars100_M25600.md,
+# profiles/k_pair_ff_laplace_stars100_M25600.md); a kernel changed since its
+# capture must be taken out of this table
+DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 1.289e6, "laplace_ff": 1.467e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -580,7 +585,8 @@ def main():
         "gpu_launches": launches,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": f"pair sum {dname}", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(dname),
+                     "traffic_note": "DRAM bytes per launch from ncu (inputs L2-resident)",
                      "peak_note": (f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of measured peaks)"
                                    + ("; float-float kernel: algorithmic flops of the FP64 formula" if dname.endswith("ff") else "")
                                    if is32 else "FP64: nominal GB300 1.25 TFLOP/s"),
