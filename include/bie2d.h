@@ -159,6 +159,23 @@ int elastance_solve(bie_ctx* ctx, const bie_geometry* geom, const double* q, dou
 int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, double* UW,
                    double* density, const bie_opts* opts, bie_info* info, void* stream);
 
+/* Batched solves (no counterpart in the paper: a throughput path for many small
+ * problems).  count independent problems of one kind -- geoms[p] with loads[p]
+ * (q [N_p] or FT [3 N_p]) into outs[p] (phi [N_p] or UW [3 N_p]), host or device
+ * arrays -- are solved together as one block-diagonal system: one set of
+ * launches per GMRES iteration for all of them, every pair and output sum kept
+ * inside its own problem.  Each problem's right-hand side is scaled to unit
+ * norm and the combined residual is driven below opts->tol, so every problem's
+ * own relative residual is at most tol; info is for the batch (rel_residual:
+ * that combined bound; net load: the largest of any problem).  The iteration
+ * count is that of the slowest problem.  Direct pair sums only (fmm_order 0),
+ * no density output; interior points for all problems or for none.  Errors:
+ * BIE_ERR_INVALID for a bad argument in any problem (message names it). */
+int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
+                          double* const* phi, const bie_opts* opts, bie_info* info, void* stream);
+int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,
+                         double* const* UW, const bie_opts* opts, bie_info* info, void* stream);
+
 /* One application of the discrete second-kind operator (eqs. ModRep2,
  * ModRep2Stokes): out = (1/2 I + K + L) in, on unscaled densities.
  * kind = BIE_KIND_LAPLACE ([M] in/out) or BIE_KIND_STOKES ([2M], node-interleaved);

@@ -94,6 +94,11 @@ def load():
         f.argtypes = [vp, ctypes.POINTER(BieGeometry), vp, vp, vp, ctypes.POINTER(BieOpts),
                       ctypes.POINTER(BieInfo), vp]
         f.restype = i32
+    for name in ("elastance_solve_batch", "mobility_solve_batch"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, i32, ctypes.POINTER(BieGeometry), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                      ctypes.POINTER(BieOpts), ctypes.POINTER(BieInfo), vp]
+        f.restype = i32
     lib.apply_operator.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator.restype = i32
     lib.apply_operator_fmm.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
@@ -235,6 +240,31 @@ def mobility_solve(ctx: Context, geom, FT, UW, density=None, opts: BieOpts | Non
                                 _stream_ptr(stream))
     del keep
     return rc, info.as_dict()
+
+
+def _solve_batch(fn, ctx: Context, geoms, loads, outs, opts, stream):
+    if not (len(geoms) == len(loads) == len(outs)) or len(geoms) == 0:
+        raise ValueError("geoms, loads and outs must be non-empty lists of one length")
+    built = [make_geometry(g) for g in geoms]
+    arr = (BieGeometry * len(geoms))(*[b[0] for b in built])
+    pl = (ctypes.c_void_p * len(loads))(*[_ptr(x) for x in loads])
+    po = (ctypes.c_void_p * len(outs))(*[_ptr(x) for x in outs])
+    info = BieInfo()
+    rc = fn(ctx.handle, len(geoms), arr, pl, po, ctypes.byref(opts) if opts is not None else None,
+            ctypes.byref(info), _stream_ptr(stream))
+    del built
+    return rc, info.as_dict()
+
+
+def elastance_solve_batch(ctx: Context, geoms, qs, phis, opts: BieOpts | None = None, stream=None):
+    """elastance_solve_batch of include/bie2d.h: lists of geometries, charges and
+    potential outputs, solved together; returns (status, info dict for the batch)."""
+    return _solve_batch(ctx.lib.elastance_solve_batch, ctx, geoms, qs, phis, opts, stream)
+
+
+def mobility_solve_batch(ctx: Context, geoms, FTs, UWs, opts: BieOpts | None = None, stream=None):
+    """mobility_solve_batch of include/bie2d.h; returns (status, info dict for the batch)."""
+    return _solve_batch(ctx.lib.mobility_solve_batch, ctx, geoms, FTs, UWs, opts, stream)
 
 
 def apply_operator(ctx: Context, geom, kind: int, precision: int, inp, out, stream=None) -> int:

@@ -88,8 +88,10 @@ int fail(bie_ctx* c, int code, const std::string& msg) {
 #define CK(call)                                                                         \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
+    if (e_ != cudaSuccess) {                                                             \
+      cudaGetLastError(); /* a non-sticky error must not fail the next call */           \
       return fail(ctx, BIE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                    \
   } while (0)
 
 bool is_device_ptr(const void* p) {
@@ -132,6 +134,12 @@ struct Work {
   float* bj_blocks = nullptr;
   double* zbuf = nullptr;
   double* arn = nullptr;  // per-CTA partials of the fused Arnoldi step
+  // batched solves: per-body problem node range, first body and first entry of
+  // each problem, and the problems' right-hand-side scales
+  int2* prange = nullptr;
+  int* pbody = nullptr;
+  long long* pnode = nullptr;
+  double* pscale = nullptr;
   int bj_max_nb = 0;
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
   double *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
@@ -141,7 +149,7 @@ struct Work {
 };
 
 void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool stage_in, bool stage_ipt,
-           bool stage_load, bool stage_io, long long bj_floats = 0) {
+           bool stage_load, bool stage_io, long long bj_floats = 0, int nprob = 0, int src_max = 0) {
   const int comps = kind + 1;
   const long long n = (long long)M * comps;
   w.kind = kind;
@@ -189,9 +197,15 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.io_in = A.take<double>(n);
     w.io_out = A.take<double>(n);
   }
-  w.plan64 = plan_pairs(M, kind, 0);
-  w.plan32 = plan_pairs(M, kind, 1);
-  w.planff = plan_pairs(M, kind, 2);
+  w.plan64 = plan_pairs(M, kind, 0, src_max);
+  w.plan32 = plan_pairs(M, kind, 1, src_max);
+  w.planff = plan_pairs(M, kind, 2, src_max);
+  if (nprob > 0) {  // a batch (of one or more problems)
+    if (nprob > 1) w.prange = A.take<int2>(N);
+    w.pbody = A.take<int>(nprob + 1);
+    w.pnode = A.take<long long>(nprob + 1);
+    w.pscale = A.take<double>(nprob);
+  }
   const int S = std::max(std::max(w.plan64.S, w.plan32.S), w.planff.S);
   w.partial = A.take<double>((size_t)S * n);
   w.grid = vec_grid(n);
@@ -296,6 +310,55 @@ int setup(bie_ctx* ctx, const bie_geometry* geom, const std::vector<int>& bs, Wo
   if (geom->interior_pt && (rc = stage_in(ctx, geom->interior_pt, w.ipt, 2 * (size_t)N, &ipt, s)))
     return rc;
   CK(stage_geometry(w.g, x, y, dx, dy, ddx, ddy, ipt, s));
+  return BIE_OK;
+}
+
+// Batched solves: P independent problems of one kind, solved as one
+// block-diagonal system.
+struct BatchIn {
+  int P;
+  const bie_geometry* geoms;   // [P]
+  const double* const* loads;  // [P]
+  double* const* outs;         // [P]
+};
+
+// Stage the problems one after another (host or device inputs) and the tables
+// that keep every pair and output sum inside its own problem.
+int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, const std::vector<int>& pb,
+                bool ipt, Work& w, cudaStream_t s) {
+  const int N = (int)bs.size() - 1, P = b.P, c = w.kind + 1;
+  CK(cudaMemcpyAsync(w.body_start, bs.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  w.g.body_start = w.body_start;
+  for (int p = 0; p < P; ++p) {
+    const bie_geometry& g = b.geoms[p];
+    const size_t off = bs[pb[p]], Mp = bs[pb[p + 1]] - bs[pb[p]], Np = pb[p + 1] - pb[p];
+    const double* src[6] = {g.x, g.y, g.dx, g.dy, g.ddx, g.ddy};
+    double* dst[6] = {w.x, w.y, w.dx, w.dy, w.ddx, w.ddy};
+    for (int k = 0; k < 6; ++k) CK(cudaMemcpyAsync(dst[k] + off, src[k], Mp * sizeof(double), cudaMemcpyDefault, s));
+    if (ipt) CK(cudaMemcpyAsync(w.ipt + 2 * pb[p], g.interior_pt, 2 * Np * sizeof(double), cudaMemcpyDefault, s));
+  }
+  std::vector<int2> pr(N);
+  std::vector<long long> pn(P + 1);
+  for (int p = 0; p < P; ++p) {
+    for (int i = pb[p]; i < pb[p + 1]; ++i) pr[i] = make_int2(bs[pb[p]], bs[pb[p + 1]]);
+    pn[p] = (long long)bs[pb[p]] * c;
+  }
+  pn[P] = (long long)bs[N] * c;
+  // one problem needs no masking: its pair sums run as a single solve's
+  if (P > 1) CK(cudaMemcpyAsync(w.prange, pr.data(), N * sizeof(int2), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.pbody, pb.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.pnode, pn.data(), (P + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  w.g.prange = P > 1 ? w.prange : nullptr;
+  w.g.pbody = w.pbody;
+  w.g.nprob = P;
+  CK(stage_geometry(w.g, w.x, w.y, w.dx, w.dy, w.ddx, w.ddy, ipt ? w.ipt : nullptr, s));
+  // loads, one after another
+  for (int p = 0, off = 0; p < P; ++p) {
+    const int nl = (pb[p + 1] - pb[p]) * (w.kind == 0 ? 1 : 3);
+    CK(cudaMemcpyAsync(w.load + off, b.loads[p], nl * sizeof(double), cudaMemcpyDefault, s));
+    off += nl;
+  }
+  CK(cudaStreamSynchronize(s));  // the host tables above must outlive their copies
   return BIE_OK;
 }
 
@@ -582,11 +645,36 @@ void fill_opts(const bie_opts* o, bie_opts& r) {
 }
 
 int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double* load, double* out,
-                 double* density, const bie_opts* opts_in, bie_info* info, cudaStream_t s) {
-  std::vector<int> bs;
-  int rc = validate(ctx, geom, bs);
-  if (rc) return rc;
-  if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
+                 double* density, const bie_opts* opts_in, bie_info* info, cudaStream_t s,
+                 const BatchIn* batch = nullptr) {
+  std::vector<int> bs, pb;
+  bool has_ipt = false;
+  int src_max = 0, rc;
+  if (batch) {
+    if (!ctx) return BIE_ERR_INVALID;
+    if (batch->P < 1 || !batch->geoms || !batch->loads || !batch->outs)
+      return fail(ctx, BIE_ERR_INVALID, "batch: count < 1 or a NULL array");
+    if (density) return fail(ctx, BIE_ERR_INVALID, "batch: no density output");
+    bs.push_back(0);
+    pb.push_back(0);
+    for (int p = 0; p < batch->P; ++p) {
+      std::vector<int> b;
+      if ((rc = validate(ctx, &batch->geoms[p], b))) return rc;
+      if (!batch->loads[p] || !batch->outs[p]) return fail(ctx, BIE_ERR_INVALID, "batch: a load or output is NULL");
+      if (p > 0 && (batch->geoms[p].interior_pt != nullptr) != has_ipt)
+        return fail(ctx, BIE_ERR_INVALID, "batch: interior points for all problems or for none");
+      has_ipt = batch->geoms[p].interior_pt != nullptr;
+      const int off = bs.back(), Np = batch->geoms[p].n_bodies;
+      if ((long long)off + b[Np] > 0x3fffffffLL) return fail(ctx, BIE_ERR_INVALID, "batch: too many nodes");
+      for (int i = 1; i <= Np; ++i) bs.push_back(off + b[i]);
+      pb.push_back(pb.back() + Np);
+      src_max = std::max(src_max, b[Np]);
+    }
+  } else {
+    if ((rc = validate(ctx, geom, bs))) return rc;
+    if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
+    has_ipt = geom->interior_pt != nullptr;
+  }
   bie_opts o;
   fill_opts(opts_in, o);
   if (o.precision != BIE_PREC_FP64 && o.precision != BIE_PREC_MIXED && o.precision != BIE_PREC_MIXED_FF)
@@ -595,23 +683,29 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   if (o.precond != 0 && o.precond != 1) return fail(ctx, BIE_ERR_INVALID, "precond must be 0 or 1");
   if (o.fmm_order != 0 && (o.fmm_order < 2 || o.fmm_order > 64))
     return fail(ctx, BIE_ERR_INVALID, "fmm_order must be 0 or in 2..64");
+  if (batch && o.fmm_order != 0) return fail(ctx, BIE_ERR_INVALID, "batch: direct pair sums only (fmm_order 0)");
   DeviceGuard dg(ctx->device);
-  const int N = geom->n_bodies, M = bs[N];
+  const int N = (int)bs.size() - 1, M = bs[N];
+  const int P = batch ? batch->P : 1;
   const int nload = kind == 0 ? N : 3 * N;
   Work w;
   const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
   const long long bjf = use_bj ? bj_block_floats(bs.data(), N, kind) : 0;
   Arena sz{nullptr};
-  carve(sz, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false, bjf);
+  carve(sz, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, src_max);
   if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
   Arena ar{ctx->ws};
-  carve(ar, w, N, M, kind, o.restart, true, true, geom->interior_pt != nullptr, true, false, bjf);
-  if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  carve(ar, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, src_max);
+  if (batch) {
+    if ((rc = batch_setup(ctx, *batch, bs, pb, has_ipt, w, s))) return rc;
+  } else if ((rc = setup(ctx, geom, bs, w, s))) {
+    return rc;
+  }
   if (bjf > 0) {
     for (int i = 0; i < N; ++i) w.bj_max_nb = std::max(w.bj_max_nb, (bs[i + 1] - bs[i]) * (kind + 1));
   }
-  const double* dload;
-  if ((rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
+  const double* dload = w.load;
+  if (!batch && (rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
   if ((rc = check_inside(ctx, w, s))) return rc;
   const int p_res = o.fmm_order, p_in = (o.fmm_order + 1) / 2;
   if (o.fmm_order > 0) {
@@ -628,6 +722,21 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(incident_density_scaled(w.g, kind, dload, w.rin, s));
     CK(timed_pair_sum(ctx, w.g, kind, 0, w.plan64, vec(w.rin), w.g.sw, w.partial, nullptr, true, s));
     CK(epilogue(w.g, kind, w.plan64, vec(w.rin), w.partial, 1, 0, -1.0, vec(w.f), nullptr, s));
+  }
+  // a batch: every problem's right-hand side scaled to unit norm and the
+  // tolerance made absolute, so that each problem's own relative residual is
+  // at most the combined residual (the solution is scaled back below)
+  double fnorm_batch = 1.0;
+  if (batch) {
+    CK(batch_normalize(P, w.pnode, w.f, w.pscale, s));
+    KState init;
+    memset(&init, 0, sizeof(init));
+    *ctx->h_state = init;
+    CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
+    CK(residual_start(w.f, nullptr, w.ytmp, w.V, n, w.st, w.part, w.gv, 0, w.grid, s));
+    if ((rc = read_state(ctx, w, s))) return rc;
+    fnorm_batch = ctx->h_state->rnorm;
+    if (fnorm_batch > 0.0) o.tol /= fnorm_batch;
   }
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
@@ -723,6 +832,10 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     relres = fnorm > 0 ? rnorm / fnorm : 0.0;
     eps32_report = eps32 > 0.0 ? eps32 : 0.0;
   }
+  if (batch) {
+    CK(batch_unscale(P, w.pnode, w.pscale, w.xs, s));
+    relres *= fnorm_batch;  // the combined residual bounds every problem's relative residual
+  }
   // total density (scaled): nu = x (total form) or mu + sigma (paper form)
   double* v = w.xs;
   if (o.formulation == 1) {
@@ -739,7 +852,15 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(unscale(w.g, kind, v, w.ytmp, s));
     if ((rc = copy_out(ctx, density, w.ytmp, n, s))) return rc;
   }
-  if ((rc = copy_out(ctx, out, w.outv, nload, s))) return rc;
+  if (batch) {
+    for (int p = 0, off = 0; p < P; ++p) {
+      const int nl = (pb[p + 1] - pb[p]) * (kind == 0 ? 1 : 3);
+      if ((rc = copy_out(ctx, batch->outs[p], w.outv + off, nl, s))) return rc;
+      off += nl;
+    }
+  } else if ((rc = copy_out(ctx, out, w.outv, nload, s))) {
+    return rc;
+  }
   // constraint residual and net load
   const int targets = kind == 0 ? N : 3 * N;
   const int P_used = o.fmm_order > 0 ? 1 : w.P;  // splits of the output sums
@@ -901,6 +1022,18 @@ int elastance_solve(bie_ctx* ctx, const bie_geometry* geom, const double* q, dou
 int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, double* UW, double* density,
                    const bie_opts* opts, bie_info* info, void* stream) {
   return solve_common(ctx, geom, 1, FT, UW, density, opts, info, (cudaStream_t)stream);
+}
+
+int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
+                          double* const* phi, const bie_opts* opts, bie_info* info, void* stream) {
+  const BatchIn b{count, geoms, q, phi};
+  return solve_common(ctx, nullptr, 0, nullptr, nullptr, nullptr, opts, info, (cudaStream_t)stream, &b);
+}
+
+int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,
+                         double* const* UW, const bie_opts* opts, bie_info* info, void* stream) {
+  const BatchIn b{count, geoms, FT, UW};
+  return solve_common(ctx, nullptr, 1, nullptr, nullptr, nullptr, opts, info, (cudaStream_t)stream, &b);
 }
 
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, const double* in,

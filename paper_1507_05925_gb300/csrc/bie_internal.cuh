@@ -39,6 +39,11 @@ struct Geo {
   float4* xff = nullptr;  // [M] (xh, xm, yh, ym)
   float2* xfl = nullptr;  // [M] (xl, yl)
   float4* nff = nullptr;  // [M] (nx_h, nx_l, ny_h, ny_l)
+  // batched solves: [N] node range [x, y) of the problem each body belongs to
+  // (pair and output sums stay inside a problem); nullptr: one problem [0, M)
+  const int2* prange = nullptr;
+  const int* pbody = nullptr;  // [nprob+1] first body of each problem (batched solves)
+  int nprob = 1;
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a
@@ -124,7 +129,8 @@ struct PairPlan {
   int S;      // source splits
   int chunk;  // sources per split
 };
-PairPlan plan_pairs(int M, int kind, int precision);
+// src_max > 0: no block sums over more than src_max sources (batched solves)
+PairPlan plan_pairs(int M, int kind, int precision, int src_max = 0);
 cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
                      const double* sscale, double* partial, const int* stop, cudaStream_t s);
 
@@ -157,6 +163,11 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
 
 // workspace of a solve with the given host body_start (bie_workspace_bytes assumes equal bodies)
 size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart);
+
+// Batched solves: per-problem unit-norm scaling of f (pnode = entry offsets
+// of the problems) and the inverse scaling of the solution.
+cudaError_t batch_normalize(int nprob, const long long* pnode, double* f, double* scale, cudaStream_t s);
+cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale, double* x, cudaStream_t s);
 
 // ---------------------------------------------------------------- precond.cu
 // Largest per-body block (unknowns) that the block-Jacobi preconditioner inverts.

@@ -186,27 +186,58 @@ __global__ void k_scale_by(int M, int comps, const double* __restrict__ in, cons
     out[k] = in[k] * fac[k / comps];
 }
 
+// Net load |sum_i q_i| (or |sum_i F_i|) and max |load|; in a batch (pbody =
+// body offsets of the P problems) the largest net load of any problem.
 __global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* __restrict__ load,
-                                                  double* __restrict__ out) {
+                                                  const int* __restrict__ pbody, int P, double* __restrict__ out) {
   __shared__ double sh[kB / 32];
-  double s0 = 0, s1 = 0, nmx = 0;  // nmx: -max |load|
-  for (int i = threadIdx.x; i < N; i += kB) {
-    if (kind == 0) {
-      s0 += load[i];
-      nmx = fmin(nmx, -fabs(load[i]));
-    } else {
-      s0 += load[3 * i];
-      s1 += load[3 * i + 1];
-      nmx = fmin(nmx, -fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
+  double nmx = 0, worst = 0;  // nmx: -max |load|
+  for (int p = 0; p < P; ++p) {
+    const int i0 = pbody ? pbody[p] : 0, i1 = pbody ? pbody[p + 1] : N;
+    double s0 = 0, s1 = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kB) {
+      if (kind == 0) {
+        s0 += load[i];
+        nmx = fmin(nmx, -fabs(load[i]));
+      } else {
+        s0 += load[3 * i];
+        s1 += load[3 * i + 1];
+        nmx = fmin(nmx, -fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
+      }
     }
+    s0 = block_sum<kB>(s0, sh);
+    s1 = block_sum<kB>(s1, sh);
+    worst = fmax(worst, sqrt(s0 * s0 + s1 * s1));
   }
-  s0 = block_sum<kB>(s0, sh);
-  s1 = block_sum<kB>(s1, sh);
   nmx = block_min<kB>(nmx, sh);
   if (threadIdx.x == 0) {
-    out[0] = sqrt(s0 * s0 + s1 * s1);
+    out[0] = worst;
     out[1] = -nmx;
   }
+}
+
+// Batched solves: scale each problem's entries [pnode[p], pnode[p+1]) of f to
+// unit 2-norm (scale[p] = the norm, 1 for a zero segment), or multiply them
+// back by scale[p].
+__global__ void __launch_bounds__(kB) k_batch_normalize(double* __restrict__ f, const long long* __restrict__ pnode,
+                                                        double* __restrict__ scale) {
+  __shared__ double sh[kB / 32];
+  const int p = blockIdx.x;
+  const long long e0 = pnode[p], e1 = pnode[p + 1];
+  double s = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += kB) s += f[e] * f[e];
+  s = sqrt(block_sum<kB>(s, sh));
+  const double sc = s > 0.0 ? s : 1.0;
+  const double inv = 1.0 / sc;
+  for (long long e = e0 + threadIdx.x; e < e1; e += kB) f[e] *= inv;
+  if (threadIdx.x == 0) scale[p] = sc;
+}
+
+__global__ void __launch_bounds__(kB) k_batch_unscale(double* __restrict__ x, const long long* __restrict__ pnode,
+                                                      const double* __restrict__ scale) {
+  const int p = blockIdx.x;
+  const double sc = scale[p];
+  for (long long e = pnode[p] + threadIdx.x; e < pnode[p + 1]; e += kB) x[e] *= sc;
 }
 
 // Laplace single layer at z_i: sum_b w_b nu_b log|z_i - x_b|^2 over split p.
@@ -215,8 +246,10 @@ __global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict_
   __shared__ double sh[kB / 32];
   const int i = blockIdx.x, p = blockIdx.y;
   const double zx = g.zx[i], zy = g.zy[i];
-  const int chunk = (g.M + P - 1) / P;
-  const int b0 = p * chunk, b1 = min(g.M, b0 + chunk);
+  // sources: all nodes, or the nodes of body i's problem (batched solves)
+  const int s0 = g.prange ? g.prange[i].x : 0, s1 = g.prange ? g.prange[i].y : g.M;
+  const int chunk = (s1 - s0 + P - 1) / P;
+  const int b0 = s0 + p * chunk, b1 = min(s1, b0 + chunk);
   double acc = 0.0;
   for (int b = b0 + threadIdx.x; b < b1; b += kB) {
     const double rx = zx - g.x[b], ry = zy - g.y[b];
@@ -236,8 +269,9 @@ __global__ void __launch_bounds__(kB) k_out_stk(Geo g, const double* __restrict_
   const int i = t / 3, s = t % 3;
   const double d = g.delta[i];
   const double zx = g.zx[i] + (s == 1 ? d : 0.0), zy = g.zy[i] + (s == 2 ? d : 0.0);
-  const int chunk = (g.M + P - 1) / P;
-  const int b0 = p * chunk, b1 = min(g.M, b0 + chunk);
+  const int s0 = g.prange ? g.prange[i].x : 0, s1 = g.prange ? g.prange[i].y : g.M;
+  const int chunk = (s1 - s0 + P - 1) / P;
+  const int b0 = s0 + p * chunk, b1 = min(s1, b0 + chunk);
   double u1 = 0.0, u2 = 0.0;
   for (int b = b0 + threadIdx.x; b < b1; b += kB) {
     const double rx = zx - g.x[b], ry = zy - g.y[b];
@@ -366,7 +400,7 @@ cudaError_t finalize_output(const Geo& g, int kind, const double* v, const doubl
   double* nl = cbody + g.N;
   k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
   note_launches(1);
-  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, nl);
+  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, g.pbody, g.pbody ? g.nprob : 1, nl);
   note_launches(1);
   k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
   note_launches(1);
@@ -398,8 +432,20 @@ cudaError_t scale_by(const Geo& g, int kind, const double* in, const double* fac
   return cudaGetLastError();
 }
 
+cudaError_t batch_normalize(int nprob, const long long* pnode, double* f, double* scale, cudaStream_t s) {
+  k_batch_normalize<<<nprob, kB, 0, s>>>(f, pnode, scale);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale, double* x, cudaStream_t s) {
+  k_batch_unscale<<<nprob, kB, 0, s>>>(x, pnode, scale);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s) {
-  k_net_load<<<1, kB, 0, s>>>(N, kind, load, out);
+  k_net_load<<<1, kB, 0, s>>>(N, kind, load, nullptr, 1, out);
   note_launches(1);
   return cudaGetLastError();
 }

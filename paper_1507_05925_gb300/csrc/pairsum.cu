@@ -31,6 +31,44 @@ namespace bie {
 
 namespace {
 
+// Source range of a target block [tbase, tend): all nodes, or in a batch the
+// nodes of the problems its targets belong to (straddle: more than one); the
+// block's split blockIdx.y of it (single problem: the planned chunk).
+struct SrcRange {
+  int j0, j1;
+  bool straddle;
+};
+
+__device__ __forceinline__ SrcRange src_range(const Geo& g, int tbase, int tend, int chunk) {
+  SrcRange r;
+  if (!g.prange) {
+    r.j0 = blockIdx.y * chunk;
+    r.j1 = min(g.M, r.j0 + chunk);
+    r.straddle = false;
+    return r;
+  }
+  const int2 p0 = g.prange[g.body_of[tbase]], p1 = g.prange[g.body_of[tend - 1]];
+  const int ch = (p1.y - p0.x + (int)gridDim.y - 1) / (int)gridDim.y;
+  r.j0 = p0.x + blockIdx.y * ch;
+  r.j1 = min(p1.y, r.j0 + ch);
+  r.straddle = p0.x != p1.x;
+  return r;
+}
+
+// Does source node b belong to target a's problem (batched solves)?
+__device__ __forceinline__ bool same_problem(const Geo& g, int a, int b) {
+  if (!g.prange || a >= g.M) return true;
+  const int2 r = g.prange[g.body_of[a]];
+  return b >= r.x && b < r.y;
+}
+
+// End of the tile starting at source jt: at most `want`, cut at the end of
+// jt's problem (a tile must not mix problems).
+__device__ __forceinline__ int tile_len(const Geo& g, int jt, int want) {
+  if (!g.prange) return want;
+  return min(want, g.prange[g.body_of[jt]].y - jt);
+}
+
 // ------------------------------------------------------------------ FP64 ----
 constexpr int kB64 = 128, kT64 = 2, kTile64 = 128;
 
@@ -43,7 +81,8 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB64 * kT64;
-  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  const SrcRange sr = src_range(g, tbase, min(M, tbase + kB64 * kT64), chunk);
+  const int j0 = sr.j0, j1 = sr.j1;
   double tx[kT64], ty[kT64], tnx[kT64], tny[kT64], ax[kT64], ay[kT64];
   int ta[kT64];
 #pragma unroll
@@ -83,14 +122,15 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
       for (int k = 0; k < kT64; ++k) {
         const double dx = tx[k] - px, dy = ty[k] - py;
         const double r2 = dx * dx + dy * dy;
+        const bool skip = ta[k] == b || (sr.straddle && !same_problem(g, ta[k], b));
         if (KIND == 0) {
-          const double s = (ta[k] == b) ? 0.0 : q1 / r2;
+          const double s = skip ? 0.0 : q1 / r2;
           ax[k] += dx * s;
           ay[k] += dy * s;
         } else {
           const double rq = dx * q1 + dy * q2;
           const double rn = dx * tnx[k] + dy * tny[k];
-          const double c = (ta[k] == b) ? 0.0 : (rq * rn) / (r2 * r2);
+          const double c = skip ? 0.0 : (rq * rn) / (r2 * r2);
           ax[k] += c * dx;
           ay[k] += c * dy;
         }
@@ -227,7 +267,8 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
   const int tend = min(M, tbase + kB32 * kT32);
-  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  const SrcRange sr = src_range(g, tbase, tend, chunk);
+  const int j0 = sr.j0, j1 = sr.j1;
   // the target block's box, centre and half-diagonal
   const float4 tb = body_range_box(g.bbox, g.body_of[tbase], g.body_of[tend - 1]);
   const float cx = 0.5f * (tb.x + tb.z), cy = 0.5f * (tb.y + tb.w);
@@ -318,6 +359,13 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
       else
         tile_near<KIND, false>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
     }
+    if (g.prange) {
+      // batched solves: a tile counts only for its own problem's targets (a block
+      // may straddle two problems)
+#pragma unroll
+      for (int k = 0; k < kT32; ++k)
+        if (!same_problem(g, a0 + k * kB32, jt)) ax[k] = ay[k] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < kT32; ++k) {
       comp_add(sx[k], ex[k], ax[k]);
@@ -385,7 +433,8 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
   const int tbase = blockIdx.x * kBF * kTF;
   const int tend = min(M, tbase + kBF * kTF);
   const int a0 = tbase + threadIdx.x;
-  const int j0 = blockIdx.y * chunk, j1 = min(M, j0 + chunk);
+  const SrcRange sr = src_range(g, tbase, tend, chunk);
+  const int j0 = sr.j0, j1 = sr.j1;
   FFTarget t[kTF];
   // float-float sums over the tiles
   float sxh[kTF], sxl[kTF], syh[kTF], syl[kTF];
@@ -403,8 +452,8 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
     t[k].n = (KIND == 1 && a < M) ? g.nff[a] : make_float4(0.f, 0.f, 0.f, 0.f);
     sxh[k] = sxl[k] = syh[k] = syl[k] = 0.f;
   }
-  for (int jt = j0; jt < j1; jt += kTileF) {
-    const int nt = min(kTileF, j1 - jt);
+  for (int jt = j0; jt < j1;) {
+    const int nt = tile_len(g, jt, min(kTileF, j1 - jt));
     __syncthreads();
     for (int l = threadIdx.x; l < nt; l += kBF) {
       const int b = jt + l;
@@ -423,11 +472,17 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
       tile_ff<KIND, true>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
     else
       tile_ff<KIND, false>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
+    if (g.prange) {
+#pragma unroll
+      for (int k = 0; k < kTF; ++k)
+        if (!same_problem(g, a0 + k * kBF, jt)) axh[k] = axl[k] = ayh[k] = ayl[k] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < kTF; ++k) {
       ff_acc(sxh[k], sxl[k], axh[k], axl[k]);
       ff_acc(syh[k], syl[k], ayh[k], ayl[k]);
     }
+    jt += nt;
   }
 #pragma unroll
   for (int k = 0; k < kTF; ++k) {
@@ -598,14 +653,16 @@ const DeviceShape& device_shape() {
 // Choose the source split so that one wave fills every SM with as many
 // blocks as can be resident: blocks = target blocks x splits ~ SMs x occupancy.
 // Splits need not be tile-aligned (the kernels handle a short last tile).
-PairPlan plan_pairs(int M, int kind, int precision) {
+PairPlan plan_pairs(int M, int kind, int precision, int src_max) {
   const DeviceShape& d = device_shape();
   const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
   const long long bx = (M + per_block - 1) / per_block;
   const long long slots = (long long)d.nsm * d.occ[precision][kind];
   long long S = bx >= slots ? 1 : slots / bx;
   const long long min_chunk = 64;
-  if (S > (M + min_chunk - 1) / min_chunk) S = (M + min_chunk - 1) / min_chunk;
+  // a block's sources: all M nodes, or (batched solves) at most src_max
+  const long long src = src_max > 0 ? src_max : M;
+  if (S > (src + min_chunk - 1) / min_chunk) S = (src + min_chunk - 1) / min_chunk;
   if (S < 1) S = 1;
   const long long chunk = (M + S - 1) / S;
   PairPlan p;

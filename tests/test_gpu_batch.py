@@ -1,0 +1,126 @@
+"""Batched solves: many independent problems solved as one block-diagonal
+system must give each problem its own solution (oracle and solo solves), with
+no pair or output sum crossing between problems."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import laplace, stokes  # noqa: E402
+from paper_1507_05925_gb300 import bie  # noqa: E402
+from test_gpu_parity import TOL_SOLVE, rel2  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05925_gb300 import build
+    build.build()
+    c = bie.Context(0)
+    yield c
+    c.close()
+
+
+def _host(g):
+    return {k: np.ascontiguousarray(g[k]) for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+
+
+def _problems(kind, seed, count):
+    # ragged: 1-8 bodies of 40-200 nodes, so target blocks straddle problems
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        g = synth.random_request(rng, max_bodies=8, nodes=(40, 64, 137, 200))
+        N = g["body_start"].size - 1
+        if kind == 0:
+            load = synth.charges(N, rng)
+        else:
+            load = synth.forces_torques(N, rng).reshape(-1)
+        out.append((g, np.ascontiguousarray(load)))
+    return out
+
+
+def _oracle(kind, g, load):
+    if kind == 0:
+        return laplace.solve(g, load)["phi"]
+    return stokes.solve(g, load.reshape(-1, 3))["UW"].reshape(-1)
+
+
+def _solve_batch(ctx, kind, probs, opts, device=False):
+    geoms = [_host(g) for g, _ in probs]
+    loads = [ld for _, ld in probs]
+    outs = [np.full(ld.size, np.nan) for ld in loads]
+    if device:
+        geoms = [{k: torch.from_numpy(v).cuda() for k, v in gm.items()} for gm in geoms]
+        loads = [torch.from_numpy(ld).cuda() for ld in loads]
+        outs = [torch.full((ld.shape[0],), float("nan"), dtype=torch.float64, device="cuda") for ld in loads]
+    fn = bie.elastance_solve_batch if kind == 0 else bie.mobility_solve_batch
+    rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+    torch.cuda.synchronize()
+    return rc, info, [o.cpu().numpy() if device else o for o in outs]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
+def test_batch_matches_oracle_and_solo(ctx, kind, prec):
+    probs = _problems(kind, 50 + kind, 7)
+    opts = bie.make_opts(precision=prec)
+    rc, info, outs = _solve_batch(ctx, kind, probs, opts, device=(prec == bie.MIXED))
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    assert info["rel_residual"] <= 1e-12
+    fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
+    for (g, load), out in zip(probs, outs):
+        ref = _oracle(kind, g, load)
+        assert rel2(out, ref) <= TOL_SOLVE
+        solo = np.empty_like(out)
+        rc1, _ = fn(ctx, _host(g), load, solo, opts=opts)
+        assert rc1 == bie.OK
+        assert rel2(out, solo) <= TOL_SOLVE
+    print(f"batch kind={kind} prec={prec}: {info}")
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_overlapping_problems_do_not_interact(ctx, kind):
+    # the same geometry 9 times at the same place with different loads: any
+    # pair crossing problems would couple them
+    g = synth.four_discs(seed=3, n=128)
+    rng = np.random.default_rng(60)
+    probs = []
+    for _ in range(9):
+        load = synth.charges(4, rng) if kind == 0 else synth.forces_torques(4, rng).reshape(-1)
+        probs.append((g, np.ascontiguousarray(load)))
+    rc, info, outs = _solve_batch(ctx, kind, probs, bie.make_opts(precision=bie.MIXED_FF))
+    assert rc == bie.OK, (rc, ctx.last_error())
+    for (gg, load), out in zip(probs, outs):
+        assert rel2(out, _oracle(kind, gg, load)) <= TOL_SOLVE
+
+
+def test_batch_of_one_equals_solo(ctx):
+    (g, load), = _problems(0, 70, 1)
+    rc, _, outs = _solve_batch(ctx, 0, [(g, load)], bie.make_opts(precision=bie.MIXED_FF))
+    assert rc == bie.OK, ctx.last_error()
+    solo = np.empty(load.size)
+    assert bie.elastance_solve(ctx, _host(g), load, solo, opts=bie.make_opts(precision=bie.MIXED_FF))[0] == bie.OK
+    assert rc == bie.OK and rel2(outs[0], solo) <= TOL_SOLVE
+
+
+def test_batch_nonneutral_and_errors(ctx):
+    probs = _problems(0, 80, 3)
+    g, load = probs[1]
+    probs[1] = (g, load + 1.0)  # one charged problem among neutral ones
+    rc, _, outs = _solve_batch(ctx, 0, probs, bie.make_opts(precision=bie.MIXED_FF))
+    assert rc == bie.WARN_NONNEUTRAL
+    assert rel2(outs[1], _oracle(0, g, load + 1.0)) <= TOL_SOLVE
+    geoms = [_host(gg) for gg, _ in probs]
+    loads = [ld for _, ld in probs]
+    outs = [np.empty(ld.size) for ld in loads]
+    assert bie.elastance_solve_batch(ctx, geoms, loads, outs, opts=bie.make_opts(fmm_order=16))[0] == bie.ERR_INVALID
+    bad = dict(geoms[2])
+    bad["body_start"] = bad["body_start"].copy()
+    bad["body_start"][1] = 3  # a body of 3 nodes
+    assert bie.elastance_solve_batch(ctx, [geoms[0], bad], loads[:2], outs[:2])[0] == bie.ERR_INVALID
+    assert "fewer than 8" in ctx.last_error()
