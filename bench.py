@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--only-large", action="store_true",
                     help="run only the large mobility section (FMM), e.g. for ncu captures")
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched-solves section")
+    ap.add_argument("--batch-requests", type=int, default=1000,
+                    help="batched solves: served-mix requests solved in batches of one kind (0 = skip the section)")
+    ap.add_argument("--batch-size", type=int, default=16)
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
@@ -327,6 +331,82 @@ def run_serving(args, rank, local):
     }
 
 
+def run_batched(args, rank, local):
+    """Batched solves (elastance_solve_batch / mobility_solve_batch): independent
+    problems solved as one block-diagonal system.  (1) Four-disc problems (4
+    discs x 128 nodes, M = 512), inputs resident on the device, batches of
+    1..128; (2) the served request mix (1..64 bodies of 64/128/256 nodes),
+    grouped by kind into batches of args.batch_size, inputs and outputs in host
+    memory (copies inside the timed region, as for the server).  Host clock
+    around synchronised calls: every batch call ends with a device-to-host read
+    of its status."""
+    import torch
+
+    from paper_1507_05925_gb300 import bie
+
+    dev = torch.device("cuda", local)
+    ctx = bie.Context(local)
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    out = {"precision": "mixed_ff", "four_discs_M512": {}}
+    rng = np.random.default_rng(5000 + rank)
+    for kind, name in ((0, "elastance"), (1, "mobility")):
+        fn = bie.elastance_solve_batch if kind == 0 else bie.mobility_solve_batch
+        per = {}
+        for P in (1, 8, 32, 128):
+            geoms, loads, outs = [], [], []
+            for i in range(P):
+                g = synth.four_discs(seed=i)
+                geoms.append({k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev)
+                              for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")})
+                ld = synth.charges(4, rng) if kind == 0 else synth.forces_torques(4, rng).reshape(-1)
+                loads.append(torch.from_numpy(np.ascontiguousarray(ld)).to(dev))
+                outs.append(torch.empty_like(loads[-1]))
+            for _ in range(3):
+                rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+            reps = max(3, 512 // P)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+                if rc < 0:
+                    raise RuntimeError(f"batched solve failed: {rc} {ctx.last_error()}")
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            per[str(P)] = {"solves_per_s": P / dt, "ms_per_batch": 1e3 * dt, "iters": info["iters"],
+                           "refinements": info["refinements"]}
+        out["four_discs_M512"][name] = per
+    # the served request mix, in batches of one kind
+    rng = np.random.default_rng(3000 + rank)
+    reqs = [synth.random_request(rng) for _ in range(args.batch_requests)]
+    t_all, n_all, iters = 0.0, 0, []
+    for kind in (0, 1):
+        fn = bie.elastance_solve_batch if kind == 0 else bie.mobility_solve_batch
+        mine = [g for g in reqs if g["kind"] == kind]
+        groups = [mine[i:i + args.batch_size] for i in range(0, len(mine), args.batch_size)]
+        host = []
+        for grp in groups:
+            geoms = [{k: np.ascontiguousarray(g[k]) for k in ("x", "y", "dx", "dy", "ddx", "ddy", "body_start")}
+                     for g in grp]
+            loads = [np.ascontiguousarray(g["q"] if kind == 0 else g["FT"].reshape(-1)) for g in grp]
+            host.append((geoms, loads, [np.empty(ld.size) for ld in loads]))
+        fn(ctx, *host[0], opts=opts)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for geoms, loads, outs in host:
+            rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+            if rc < 0:
+                raise RuntimeError(f"batched solve failed: {rc} {ctx.last_error()}")
+            iters.append(info["iters"])
+        torch.cuda.synchronize()
+        t_all += time.perf_counter() - t0
+        n_all += len(mine)
+    out["served_mix"] = {"requests": n_all, "batch_size": args.batch_size, "solves_per_s": n_all / t_all,
+                         "seconds": t_all, "median_iters": float(np.median(iters)),
+                         "note": "same request generator and seed as the serving section; host inputs"}
+    ctx.close()
+    return out
+
+
 def run_large(args, rank, local):
     """Mobility of 10,000 ellipses (M = 640,000): refinement with FMM pair sums
     (order fmm_order for residuals, half for the inner solves)."""
@@ -432,11 +512,13 @@ def main():
     if args.kernel:
         run_kernel(args, local)
         return
-    if args.only_large or args.only_serving:  # one section alone (profiling, tuning)
+    if args.only_large or args.only_serving or args.only_batched:  # one section alone (profiling, tuning)
         from paper_1507_05925_gb300 import build
         build.build()
         if args.only_large:
             print(json.dumps({"large_mobility": run_large(args, rank, local)}))
+        elif args.only_batched:
+            print(json.dumps({"batched": run_batched(args, rank, local)}))
         else:
             print(json.dumps({"serving": run_serving(args, rank, local)}))
         return
@@ -595,6 +677,8 @@ def main():
     }
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, rank, local)
+    if args.batch_requests > 0:
+        out["batched"] = run_batched(args, rank, local)
     if args.large_steps > 0:
         out["large_mobility"] = run_large(args, rank, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

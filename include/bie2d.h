@@ -164,13 +164,17 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
  * (q [N_p] or FT [3 N_p]) into outs[p] (phi [N_p] or UW [3 N_p]), host or device
  * arrays -- are solved together as one block-diagonal system: one set of
  * launches per GMRES iteration for all of them, every pair and output sum kept
- * inside its own problem.  Each problem's right-hand side is scaled to unit
- * norm and the combined residual is driven below opts->tol, so every problem's
- * own relative residual is at most tol; info is for the batch (rel_residual:
- * that combined bound; net load: the largest of any problem).  The iteration
- * count is that of the slowest problem.  Direct pair sums only (fmm_order 0),
- * no density output; interior points for all problems or for none.  Errors:
- * BIE_ERR_INVALID for a bad argument in any problem (message names it). */
+ * inside its own problem.  Each problem has its own Krylov space (Hessenberg
+ * matrix, rotations and stopping test); the problems advance in lockstep and a
+ * problem that has converged stops taking part.  Each problem's right-hand side
+ * is scaled to unit norm; every problem's own relative residual ends at most
+ * opts->tol.  info is for the batch: iters counts lockstep iterations (those of
+ * the slowest problem); rel_residual is the largest relative residual of any
+ * problem (mixed with float-float residual updates: plus their rounding
+ * bound); net load is the largest of any problem.  Direct pair sums
+ * only (fmm_order 0), no density output; interior points for all problems or
+ * for none; 1 <= count <= 65535.  Errors: BIE_ERR_INVALID for a bad argument in
+ * any problem (message names it). */
 int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
                           double* const* phi, const bie_opts* opts, bie_info* info, void* stream);
 int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,

@@ -140,6 +140,15 @@ struct Work {
   int* pbody = nullptr;
   long long* pnode = nullptr;
   double* pscale = nullptr;
+  double* pnorm = nullptr;  // per-problem residual norms of the refinement
+  // batched GMRES (one Krylov space per problem): element ranges of the fused
+  // Arnoldi step and per-problem state; seg.P == 0 for a single system
+  SegArgs seg;
+  PState* ps = nullptr;
+  long long* ibeg = nullptr;
+  int *iprob = nullptr, *pitem = nullptr, *bprob = nullptr;
+  int seg_grid = 1;
+  long long max_plen = 0;
   int bj_max_nb = 0;
   double *partial = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *yv = nullptr;
   double *part = nullptr, *outpart = nullptr, *outv = nullptr, *cres = nullptr;
@@ -200,17 +209,31 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   w.plan64 = plan_pairs(M, kind, 0, src_max);
   w.plan32 = plan_pairs(M, kind, 1, src_max);
   w.planff = plan_pairs(M, kind, 2, src_max);
+  // problems solved as one system share every Krylov array; nseg copies of the
+  // Hessenberg and rotation arrays with one Krylov space per problem
+  const int nseg = nprob > 1 ? nprob : 1;
+  long long arn_units = 0;
   if (nprob > 0) {  // a batch (of one or more problems)
-    if (nprob > 1) w.prange = A.take<int2>(N);
     w.pbody = A.take<int>(nprob + 1);
     w.pnode = A.take<long long>(nprob + 1);
     w.pscale = A.take<double>(nprob);
+    w.pnorm = A.take<double>(nprob);
+  }
+  if (nprob > 1) {
+    w.prange = A.take<int2>(N);
+    const int items = kMaxVecGrid + nprob;  // ranges: at most grid + one per problem
+    w.ps = A.take<PState>(nprob);
+    w.ibeg = A.take<long long>(items + 1);
+    w.iprob = A.take<int>(items);
+    w.pitem = A.take<int>(nprob + 1);
+    w.bprob = A.take<int>(N);
+    arn_units = items;
   }
   const int S = std::max(std::max(w.plan64.S, w.plan32.S), w.planff.S);
   w.partial = A.take<double>((size_t)S * n);
   w.grid = vec_grid(n);
   w.part = A.take<double>((size_t)w.grid * 201 + 64);
-  w.arn = A.take<double>((size_t)3 * w.grid * 201 + 64);
+  w.arn = A.take<double>((size_t)3 * std::max<long long>(w.grid, arn_units) * 201 + 64);
   w.st = A.take<KState>(1);
   if (solve) {
     w.V = A.take<double>((size_t)(m + 1) * w.ld);
@@ -221,11 +244,11 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.rin = A.take<double>(n);
     w.ytmp = A.take<double>(n);
     w.rc = A.take<double>(n);
-    w.H = A.take<double>((size_t)(m + 1) * m);
-    w.cs = A.take<double>(m);
-    w.sn = A.take<double>(m);
-    w.gv = A.take<double>(m + 1);
-    w.yv = A.take<double>(m + 1);
+    w.H = A.take<double>((size_t)nseg * (m + 1) * m);
+    w.cs = A.take<double>((size_t)nseg * m);
+    w.sn = A.take<double>((size_t)nseg * m);
+    w.gv = A.take<double>((size_t)nseg * (m + 1));
+    w.yv = A.take<double>((size_t)nseg * (m + 1));
     w.P = output_splits(g, kind);
     const int targets = kind == 0 ? N : 3 * N;
     w.outpart = A.take<double>((size_t)w.P * targets * comps + N + 2);
@@ -351,6 +374,42 @@ int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, cons
   w.g.prange = P > 1 ? w.prange : nullptr;
   w.g.pbody = w.pbody;
   w.g.nprob = P;
+  std::vector<long long> ib;
+  std::vector<int> ip, pi, bp;
+  if (P > 1) {
+    // element ranges of the batched Arnoldi step: about n / grid entries each
+    // (at least 512), none crossing a problem
+    w.seg_grid = arnoldi_seg_grid(pn[P]);
+    const long long L = std::max<long long>(512, (pn[P] + w.seg_grid - 1) / w.seg_grid);
+    pi.resize(P + 1);
+    bp.resize(N);
+    for (int p = 0; p < P; ++p) {
+      pi[p] = (int)ip.size();
+      const long long len = pn[p + 1] - pn[p];
+      const long long k = std::max<long long>(1, (len + L - 1) / L);
+      for (long long t = 0; t < k; ++t) {
+        ib.push_back(pn[p] + len * t / k);
+        ip.push_back(p);
+      }
+      for (int i = pb[p]; i < pb[p + 1]; ++i) bp[i] = p;
+      w.max_plen = std::max(w.max_plen, len);
+    }
+    pi[P] = (int)ip.size();
+    ib.push_back(pn[P]);
+    if ((int)ip.size() > kMaxVecGrid + P) return fail(ctx, BIE_ERR_INVALID, "batch: internal range count");
+    CK(cudaMemcpyAsync(w.ibeg, ib.data(), ib.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.iprob, ip.data(), ip.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.pitem, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.bprob, bp.data(), bp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    w.seg.P = P;
+    w.seg.nitem = (int)ip.size();
+    w.seg.pnode = w.pnode;
+    w.seg.ibeg = w.ibeg;
+    w.seg.iprob = w.iprob;
+    w.seg.pitem = w.pitem;
+    w.seg.bprob = w.bprob;
+    w.seg.ps = w.ps;
+  }
   CK(stage_geometry(w.g, w.x, w.y, w.dx, w.dy, w.ddx, w.ddy, ipt ? w.ipt : nullptr, s));
   // loads, one after another
   for (int p = 0, off = 0; p < P; ++p) {
@@ -484,7 +543,11 @@ int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   CK(op.apply(op.precond ? vec(w.zbuf) : vj, vj1, &w.st->stop, s, false));
   const ArnoldiArgs a{w.V,        ld,       n,      w.st,      w.arn, w.H, w.cs, w.sn, w.gv, w.g,
                       w.kind,     w.bj_off, op.precond ? w.bj_blocks : nullptr, w.zbuf};
-  CK(arnoldi(a, arnoldi_grid(n), s));
+  if (w.seg.P > 1) {
+    CK(arnoldi_seg(a, w.seg, w.seg_grid, s));
+  } else {
+    CK(arnoldi(a, arnoldi_grid(n), s));
+  }
   return BIE_OK;
 }
 
@@ -501,8 +564,8 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   long long alpha_bits;
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
   const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
-                             w.kind, w.m, op.prec * 1000 + op.fmm_p + (op.precond ? 500 : 0), alpha_bits, p.S * 1000003LL + p.chunk,
-                             w.grid};
+                             w.kind + 4LL * w.seg.P, w.m, op.prec * 1000 + op.fmm_p + (op.precond ? 500 : 0), alpha_bits,
+                             p.S * 1000003LL + p.chunk, w.grid + 1000003LL * w.seg.nitem};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
   const long long before = thread_launches();
@@ -617,6 +680,72 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
   }
 }
 
+// Batched restarted GMRES: the same iteration with one Krylov space per
+// problem (the problems advance in lockstep; each stops at its own
+// tolerance, tol_rel ||b_p||).  out.res and out.bnorm are those of the problem
+// with the largest relative residual (true residuals with verify).
+int gmres_seg(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, double tol_rel, int maxit,
+              bool verify, KrylovResult& out, cudaStream_t s) {
+  const long long n = w.n, ld = w.ld;
+  KState init;
+  memset(&init, 0, sizeof(init));
+  init.scratch[0] = tol_rel;
+  init.pad[0] = 1;  // k_residual_seg sets every problem's tolerance on the first call
+  init.maxit = maxit;
+  init.m = w.m;
+  *ctx->h_state = init;
+  CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
+  CK(fill0(x, n, s));
+  CK(residual_start_seg(b, nullptr, w.rin, w.V, w.st, w.seg, w.gv, w.m, s));
+  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+  Op rop = verify ? Op{ctx, &w, 0} : op;
+  rop.precond = false;
+  auto worst = [&](bool converged) -> int {
+    std::vector<PState> ps(w.seg.P);
+    CK(cudaMemcpyAsync(ps.data(), w.ps, ps.size() * sizeof(PState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rel = -1.0;
+    for (const PState& q : ps) {
+      const double r = verify ? q.rnorm : q.res;
+      const double e = q.bnorm > 0.0 ? r / q.bnorm : 0.0;
+      if (e > rel) {
+        rel = e;
+        out.res = r;
+        out.bnorm = q.bnorm;
+      }
+    }
+    out.converged = converged;
+    return BIE_OK;
+  };
+  int rc;
+  for (;;) {
+    if ((rc = run_cycle(ctx, w, op, s))) return rc;
+    const KState h = *ctx->h_state;
+    out.iters = h.iters;
+    if (h.j > 0) {
+      if (op.precond) {  // x += P (V y)
+        CK(fill0(w.ytmp, n, s));
+        CK(gmres_update_seg(w.V, ld, w.st, w.seg, w.H, w.gv, w.yv, w.ytmp, w.m, w.max_plen, s));
+        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s));
+        CK(axpy(x, w.zbuf, n, s));
+      } else {
+        CK(gmres_update_seg(w.V, ld, w.st, w.seg, w.H, w.gv, w.yv, x, w.m, w.max_plen, s));
+      }
+    }
+    out.matvecs += h.j;
+    if (h.j == 0) return worst(h.nactive == 0);
+    if (!verify && (h.nactive == 0 || h.iters >= h.maxit)) return worst(h.nactive == 0);
+    // explicit residual; opens the next cycle for the problems above tolerance
+    CK(rop.apply(vec(x), vec(w.ytmp), nullptr, s));
+    if (verify) out.matvecs64 += 1; else out.matvecs += 1;
+    CK(residual_start_seg(b, w.ytmp, w.rin, w.V, w.st, w.seg, w.gv, w.m, s));
+    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+    if ((rc = read_state(ctx, w, s))) return rc;
+    const KState& h2 = *ctx->h_state;
+    if (h2.nactive == 0 || h2.iters >= h2.maxit) return worst(h2.nactive == 0);
+  }
+}
+
 int copy_out(bie_ctx* ctx, double* dst, const double* src, size_t count, cudaStream_t s) {
   CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, s));
   return BIE_OK;
@@ -652,8 +781,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   int src_max = 0, rc;
   if (batch) {
     if (!ctx) return BIE_ERR_INVALID;
-    if (batch->P < 1 || !batch->geoms || !batch->loads || !batch->outs)
-      return fail(ctx, BIE_ERR_INVALID, "batch: count < 1 or a NULL array");
+    if (batch->P < 1 || batch->P > 65535 || !batch->geoms || !batch->loads || !batch->outs)
+      return fail(ctx, BIE_ERR_INVALID, "batch: count outside 1..65535 or a NULL array");
     if (density) return fail(ctx, BIE_ERR_INVALID, "batch: no density output");
     bs.push_back(0);
     pb.push_back(0);
@@ -727,6 +856,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   // tolerance made absolute, so that each problem's own relative residual is
   // at most the combined residual (the solution is scaled back below)
   double fnorm_batch = 1.0;
+  const double tol_user = o.tol;
   if (batch) {
     CK(batch_normalize(P, w.pnode, w.f, w.pscale, s));
     KState init;
@@ -747,13 +877,21 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0, 0.0, fres};
   int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, mff = 0, iters = 0, refs = 0;
   double relres = 0.0, eps32_report = 0.0;
-  bool converged = false;
+  bool converged = false, relres_per_problem = false;
+  // GMRES on one system, or (several problems) one Krylov space per problem
+  auto krylov = [&](const Op& op, const double* b, double* x, double tol_rel, int maxit, bool verify,
+                    KrylovResult& kr) -> int {
+    return w.seg.P > 1 ? gmres_seg(ctx, w, op, b, x, tol_rel, maxit, verify, kr, s)
+                       : gmres(ctx, w, op, b, x, tol_rel, maxit, verify, kr, s);
+  };
   if (o.precision == BIE_PREC_FP64) {
     KrylovResult kr;
-    if ((rc = gmres(ctx, w, op64, w.f, w.xs, o.tol, o.max_iter, true, kr, s))) return rc;
+    // batched: every problem to the relative tolerance on its own right-hand side
+    if ((rc = krylov(op64, w.f, w.xs, w.seg.P > 1 ? tol_user : o.tol, o.max_iter, true, kr))) return rc;
     m64 += kr.matvecs + kr.matvecs64;
     iters = kr.iters;
     relres = kr.bnorm > 0 ? kr.res / kr.bnorm : 0.0;
+    relres_per_problem = w.seg.P > 1;
     converged = kr.converged;
   } else {
     // FP64 iterative refinement: x += A32^{-1}(f - A64 x)
@@ -789,10 +927,27 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     const Op op32p{ctx, &w, 1, 0.0, fin};  // FP32 pair sums (or FP32 FMM), the paper's completion
     double eps32 = -1.0, bound = 0.0;
     bool true_residual = true;
+    // batched (one Krylov space per problem): every problem's own residual
+    // (right-hand sides of unit norm) against the tolerance, and a problem
+    // already below it sits out the next inner solve
+    const bool per_problem = w.seg.P > 1;
+    double worst = 0.0;
+    std::vector<double> pn_host(per_problem ? w.seg.P : 0);
+    auto problem_norms = [&]() -> int {
+      CK(seg_norms(w.seg.P, w.pnode, w.r, w.pnorm, s));
+      CK(cudaMemcpyAsync(pn_host.data(), w.pnorm, pn_host.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      worst = 0.0;
+      for (double v : pn_host) worst = std::max(worst, v);
+      return BIE_OK;
+    };
+    if (per_problem && (rc = problem_norms())) return rc;
     while (!converged && refs < o.max_refine && remaining > 0) {
       KrylovResult kr;
       CK(consistent_rhs(w.g, kind, kInnerCompletionWeight, w.r, w.rc, s));
-      if ((rc = gmres(ctx, w, op32, w.rc, w.d, o.inner_tol, remaining, false, kr, s))) return rc;
+      if (per_problem && tol_user - bound > 0.0)
+        CK(seg_zero_below(w.seg.P, w.pnode, w.pnorm, tol_user - bound, w.rc, s));
+      if ((rc = krylov(op32, w.rc, w.d, o.inner_tol, remaining, false, kr))) return rc;
       iters += kr.iters;
       m32 += kr.matvecs;
       remaining -= kr.iters;
@@ -826,15 +981,26 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
         }
         true_residual = !recursive;
       }
-      converged = rnorm <= o.tol * fnorm;
+      if (per_problem) {
+        if ((rc = problem_norms())) return rc;
+        converged = worst + bound <= tol_user;
+      } else {
+        converged = rnorm <= o.tol * fnorm;
+      }
       if (kr.iters == 0) break;
     }
     relres = fnorm > 0 ? rnorm / fnorm : 0.0;
+    if (per_problem) {
+      relres = worst + bound;  // the largest relative residual of any problem (unit right-hand sides)
+      relres_per_problem = true;
+    }
     eps32_report = eps32 > 0.0 ? eps32 : 0.0;
   }
   if (batch) {
     CK(batch_unscale(P, w.pnode, w.pscale, w.xs, s));
-    relres *= fnorm_batch;  // the combined residual bounds every problem's relative residual
+    // the combined residual of the unit right-hand sides bounds every problem's
+    // relative residual
+    if (!relres_per_problem) relres *= fnorm_batch;
   }
   // total density (scaled): nu = x (total form) or mu + sigma (paper form)
   double* v = w.xs;

@@ -77,7 +77,31 @@ struct KState {
   int pad[2];         // [0] = 1: set tol_abs from the next starting residual
   unsigned bar_count, bar_gen;  // grid barrier of the fused Arnoldi step
   int error;          // 1: a grid barrier gave up waiting (results invalid)
-  int pad2;
+  int nactive;        // batched GMRES: problems still iterating in this cycle
+};
+
+// Batched GMRES (many independent problems in one block-diagonal system): each
+// problem has its own Krylov space, Hessenberg matrix, rotations and stopping
+// test; the problems advance in lockstep and a problem that has converged
+// stops taking part.
+struct PState {
+  double tol_abs;  // stop threshold on this problem's residual estimate
+  double beta;     // norm of the problem's starting residual in this cycle
+  double res;      // residual estimate |g_{j+1}|
+  double rnorm;    // last computed true residual norm
+  double bnorm;    // norm of the problem's right-hand side
+  int stop_j;      // steps of this cycle it took part in (INT_MAX: still active)
+  int pad;
+};
+struct SegArgs {
+  int P = 0;                      // problems (0: one system, not segmented)
+  int nitem = 0;                  // element ranges of the fused Arnoldi step
+  const long long* pnode = nullptr;  // [P+1] first vector entry of each problem
+  const long long* ibeg = nullptr;   // [nitem+1] ranges, none crossing a problem
+  const int* iprob = nullptr;        // [nitem] problem of each range
+  const int* pitem = nullptr;        // [P+1] first range of each problem
+  const int* bprob = nullptr;        // [N] problem of each body
+  PState* ps = nullptr;              // [P]
 };
 
 }  // namespace bie
@@ -168,6 +192,10 @@ size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, i
 // of the problems) and the inverse scaling of the solution.
 cudaError_t batch_normalize(int nprob, const long long* pnode, double* f, double* scale, cudaStream_t s);
 cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale, double* x, cudaStream_t s);
+// norms[p] = ||x_p|| per problem; x_p = 0 where norms[p] <= thr
+cudaError_t seg_norms(int nprob, const long long* pnode, const double* x, double* norms, cudaStream_t s);
+cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norms, double thr, double* x,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------- precond.cu
 // Largest per-body block (unknowns) that the block-Jacobi preconditioner inverts.
@@ -182,6 +210,7 @@ cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const flo
                      const int* stop, int max_nb, cudaStream_t s);
 
 // ---------------------------------------------------------------- krylov.cu
+constexpr int kMaxVecGrid = 608;  // largest grid of the vector kernels and the Arnoldi step
 int vec_grid(long long n);
 
 // One fused Arnoldi step (CGS2, norm, Givens, normalisation and optionally
@@ -201,6 +230,19 @@ struct ArnoldiArgs {
 int arnoldi_grid(long long n);  // co-resident CTAs for the cooperative launch
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s);
 // h[i] = <V_i, w> for i <= j (first CGS pass)
+
+// Batched GMRES: the same Arnoldi step per problem (H, cs, sn, gv hold P
+// consecutive copies: [P][m][m+1], [P][m], [P][m], [P][m+1]); part holds
+// [3][nitem][201] doubles.
+int arnoldi_seg_grid(long long n);
+cudaError_t arnoldi_seg(const ArnoldiArgs& a, const SegArgs& sg, int grid, cudaStream_t s);
+// per problem p: r = f - y over its entries, rnorm_p; opens a cycle: V0 = r/rnorm_p
+// (zero for a problem already below its tolerance), g_p = (rnorm_p, 0, ..)
+cudaError_t residual_start_seg(const double* f, const double* y, double* r, double* V0, KState* st,
+                               const SegArgs& sg, double* gv, int m, cudaStream_t s);
+// per problem: y_p = R_p^{-1} g_p over the steps it took part in, x += V y_p
+cudaError_t gmres_update_seg(const double* V, long long ld, KState* st, const SegArgs& sg, const double* H,
+                             const double* gv, double* y, double* x, int m, long long max_len, cudaStream_t s);
 
 // y = R^{-1} g and x += V y
 cudaError_t gmres_update(const double* V, long long ld, long long n, KState* st, const double* H,

@@ -240,6 +240,25 @@ __global__ void __launch_bounds__(kB) k_batch_unscale(double* __restrict__ x, co
   for (long long e = pnode[p] + threadIdx.x; e < pnode[p + 1]; e += kB) x[e] *= sc;
 }
 
+// Batched solves: ||x_p|| of every problem's entries into norms[p].
+__global__ void __launch_bounds__(kB) k_seg_norms(const double* __restrict__ x, const long long* __restrict__ pnode,
+                                                  double* __restrict__ norms) {
+  __shared__ double sh[kB / 32];
+  const int p = blockIdx.x;
+  double s = 0.0;
+  for (long long e = pnode[p] + threadIdx.x; e < pnode[p + 1]; e += kB) s += x[e] * x[e];
+  s = block_sum<kB>(s, sh);
+  if (threadIdx.x == 0) norms[p] = sqrt(s);
+}
+
+// Batched solves: x_p = 0 for every problem with norms[p] <= thr.
+__global__ void __launch_bounds__(kB) k_seg_zero_below(double* __restrict__ x, const long long* __restrict__ pnode,
+                                                       const double* __restrict__ norms, double thr) {
+  const int p = blockIdx.x;
+  if (!(norms[p] <= thr)) return;
+  for (long long e = pnode[p] + threadIdx.x; e < pnode[p + 1]; e += kB) x[e] = 0.0;
+}
+
 // Laplace single layer at z_i: sum_b w_b nu_b log|z_i - x_b|^2 over split p.
 __global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict__ v,
                                                 double* __restrict__ part, int P) {
@@ -440,6 +459,19 @@ cudaError_t batch_normalize(int nprob, const long long* pnode, double* f, double
 
 cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale, double* x, cudaStream_t s) {
   k_batch_unscale<<<nprob, kB, 0, s>>>(x, pnode, scale);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t seg_norms(int nprob, const long long* pnode, const double* x, double* norms, cudaStream_t s) {
+  k_seg_norms<<<nprob, kB, 0, s>>>(x, pnode, norms);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norms, double thr, double* x,
+                           cudaStream_t s) {
+  k_seg_zero_below<<<nprob, kB, 0, s>>>(x, pnode, norms, thr);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -153,6 +153,64 @@ __device__ void grid_barrier(KState* st) {
   __syncthreads();
 }
 
+// z = B v for one body's block-Jacobi block B (column-major nb x nb, FP32;
+// off = its offset in the block array) and v = ws in shared memory.
+__device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long long off, int nb, const float* ws,
+                              double* __restrict__ z, float4* red4) {
+  if ((nb & 3) == 0 && (off & 3) == 0) {
+    // 16-byte loads of four consecutive rows: 64 row quads x 4 column groups
+    const int nq = nb >> 2, qd = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int per = (nb + 3) >> 2, cb = grp * per, ce = min(nb, cb + per);
+    for (int q0 = 0; q0 < nq; q0 += 64) {
+      const int q = q0 + qd;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < nq) {
+        const float4* __restrict__ Bq = reinterpret_cast<const float4*>(B) + q;
+#pragma unroll 8
+        for (int col = cb; col < ce; ++col) {
+          const float4 b = Bq[(long long)col * nq];
+          const float x = ws[col];
+          acc.x = fmaf(b.x, x, acc.x);
+          acc.y = fmaf(b.y, x, acc.y);
+          acc.z = fmaf(b.z, x, acc.z);
+          acc.w = fmaf(b.w, x, acc.w);
+        }
+      }
+      red4[threadIdx.x] = acc;
+      __syncthreads();
+      if (grp == 0 && q < nq) {
+        float4 t = red4[qd];
+#pragma unroll
+        for (int u = 1; u < 4; ++u) {
+          const float4 o = red4[u * 64 + qd];
+          t.x += o.x;
+          t.y += o.y;
+          t.z += o.z;
+          t.w += o.w;
+        }
+        double* zr = z + 4 * q;
+        zr[0] = t.x;
+        zr[1] = t.y;
+        zr[2] = t.z;
+        zr[3] = t.w;
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int r = threadIdx.x; r < nb; r += kBV) {
+      float s0 = 0.f, s1 = 0.f;
+      int col = 0;
+#pragma unroll 4
+      for (; col + 2 <= nb; col += 2) {
+        s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
+        s1 = fmaf(B[(long long)(col + 1) * nb + r], ws[col + 1], s1);
+      }
+      if (col < nb) s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
+      z[r] = (double)(s0 + s1);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
   KState* st = a.st;
   if (st->stop) return;  // read by every CTA before the first barrier: uniform
@@ -261,60 +319,225 @@ __global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
       ws[r] = (float)v;
     }
     __syncthreads();
-    const float* __restrict__ B = a.blocks + a.off[i];
-    if ((nb & 3) == 0 && (a.off[i] & 3) == 0) {
-      // 16-byte loads of four consecutive rows: 64 row quads x 4 column groups
-      const int nq = nb >> 2, qd = threadIdx.x & 63, grp = threadIdx.x >> 6;
-      const int per = (nb + 3) >> 2, cb = grp * per, ce = min(nb, cb + per);
-      for (int q0 = 0; q0 < nq; q0 += 64) {
-        const int q = q0 + qd;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < nq) {
-          const float4* __restrict__ Bq = reinterpret_cast<const float4*>(B) + q;
-#pragma unroll 8
-          for (int col = cb; col < ce; ++col) {
-            const float4 b = Bq[(long long)col * nq];
-            const float x = ws[col];
-            acc.x = fmaf(b.x, x, acc.x);
-            acc.y = fmaf(b.y, x, acc.y);
-            acc.z = fmaf(b.z, x, acc.z);
-            acc.w = fmaf(b.w, x, acc.w);
-          }
-        }
-        red4[threadIdx.x] = acc;
-        __syncthreads();
-        if (grp == 0 && q < nq) {
-          float4 t = red4[qd];
+    bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ batched Arnoldi
+// The fused Arnoldi step of many independent problems (one block-diagonal
+// system, each problem its own Krylov space).  The vector is cut into element
+// ranges that never cross a problem; CTA b takes ranges b, b + G, ...  The
+// inner products of a problem add the per-range partials of that problem's
+// ranges in range order (deterministic).  Problem p takes part in step j while
+// stop_j > j; its Givens rotations run on CTA p mod G.  A problem that stopped
+// earlier is skipped and its next basis vector set to zero, so that the
+// operator applied to it gives zero.
+
+// Partial dot products of w[e0, e1) with V_0..V_{jc-1} into out[0..jc).
+__device__ __forceinline__ void seg_block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
+                               long long e0, long long e1, int jc, double* __restrict__ out,
+                               double (*sh)[kMaxBasis]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int i = 0;
+  for (; i + 4 <= jc; i += 4) {
+    const double* __restrict__ V0 = V + (long long)i * ld;
+    const double* __restrict__ V1 = V0 + ld;
+    const double* __restrict__ V2 = V1 + ld;
+    const double* __restrict__ V3 = V2 + ld;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) {
+      const double wk = w[k];
+      a0 = fma(V0[k], wk, a0);
+      a1 = fma(V1[k], wk, a1);
+      a2 = fma(V2[k], wk, a2);
+      a3 = fma(V3[k], wk, a3);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane == 0) {
+      sh[wid][i] = a0;
+      sh[wid][i + 1] = a1;
+      sh[wid][i + 2] = a2;
+      sh[wid][i + 3] = a3;
+    }
+  }
+  for (; i < jc; ++i) {
+    const double* __restrict__ Vi = V + (long long)i * ld;
+    double acc = 0.0;
+    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) acc = fma(Vi[k], w[k], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) sh[wid][i] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < jc; q += kBV) {
+    double t = 0.0;
 #pragma unroll
-          for (int u = 1; u < 4; ++u) {
-            const float4 o = red4[u * 64 + qd];
-            t.x += o.x;
-            t.y += o.y;
-            t.z += o.z;
-            t.w += o.w;
-          }
-          double* zr = a.z + a0 + 4 * q;
-          zr[0] = t.x;
-          zr[1] = t.y;
-          zr[2] = t.z;
-          zr[3] = t.w;
-        }
-        __syncthreads();
-      }
-    } else {
-      for (int r = threadIdx.x; r < nb; r += kBV) {
-        float s0 = 0.f, s1 = 0.f;
-        int col = 0;
+    for (int u = 0; u < kBV / 32; ++u) t += sh[u][q];
+    out[q] = t;
+  }
+  __syncthreads();  // sh is reused by the next range
+}
+
+// hs[i] = sum over the ranges [it0, it1) of part[it][i] (written by other CTAs
+// before a grid barrier; read through L2), i < jc.
+__device__ __forceinline__ void seg_sum(const double* part, int it0, int it1, int jc, double* hs) {
+  __syncthreads();  // hs may still be read from the previous range
+  for (int i = threadIdx.x; i < jc; i += kBV) {
+    double t = 0.0;
 #pragma unroll 4
-        for (; col + 2 <= nb; col += 2) {
-          s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
-          s1 = fmaf(B[(long long)(col + 1) * nb + r], ws[col + 1], s1);
-        }
-        if (col < nb) s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
-        a.z[a0 + r] = (double)(s0 + s1);
+    for (int it = it0; it < it1; ++it) t += __ldcg(part + (long long)it * kMaxBasis + i);
+    hs[i] = t;
+  }
+  __syncthreads();
+}
+
+// ||w_p|| after orthogonalisation: the sum of the range partials, broadcast.
+__device__ __forceinline__ double seg_hn(const double* part3, int it0, int it1, double* cell) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int it = it0; it < it1; ++it) t += __ldcg(part3 + (long long)it * kMaxBasis);
+    *cell = sqrt(t);
+  }
+  __syncthreads();
+  return *cell;
+}
+
+__global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) {
+  KState* st = a.st;
+  if (st->stop) return;  // read by every CTA before the first barrier: uniform
+  __shared__ double sh[kBV / 32][kMaxBasis];
+  __shared__ double hs[kMaxBasis], hcol[kMaxBasis + 1];
+  __shared__ double red[kBV / 32];
+  __shared__ double cell;
+  __shared__ float ws[kBjMaxBlock];
+  __shared__ float4 red4[kBV];
+  const int j = st->j, jc = j + 1;
+  const long long ld = a.ld;
+  double* __restrict__ w = a.V + (long long)(j + 1) * ld;
+  const int G = gridDim.x;
+  double* part1 = a.part;
+  double* part2 = part1 + (long long)sg.nitem * kMaxBasis;
+  double* part3 = part2 + (long long)sg.nitem * kMaxBasis;
+  // h1 = V^T w per range
+  for (int it = blockIdx.x; it < sg.nitem; it += G) {
+    const int p = sg.iprob[it];
+    if (sg.ps[p].stop_j <= j) continue;
+    seg_block_dots(a.V, ld, w, sg.ibeg[it], sg.ibeg[it + 1], jc, part1 + (long long)it * kMaxBasis, sh);
+  }
+  grid_barrier(st);
+  // w -= V h1; h2 = V^T w
+  for (int it = blockIdx.x; it < sg.nitem; it += G) {
+    const int p = sg.iprob[it];
+    if (sg.ps[p].stop_j <= j) continue;
+    seg_sum(part1, sg.pitem[p], sg.pitem[p + 1], jc, hs);
+    const long long e0 = sg.ibeg[it], e1 = sg.ibeg[it + 1];
+    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) w[k] = w[k] - combine(a.V, ld, k, hs, jc);
+    __syncthreads();
+    seg_block_dots(a.V, ld, w, e0, e1, jc, part2 + (long long)it * kMaxBasis, sh);
+  }
+  grid_barrier(st);
+  // w -= V h2; ||w||^2 per range
+  for (int it = blockIdx.x; it < sg.nitem; it += G) {
+    const int p = sg.iprob[it];
+    if (sg.ps[p].stop_j <= j) continue;
+    seg_sum(part2, sg.pitem[p], sg.pitem[p + 1], jc, hs);
+    const long long e0 = sg.ibeg[it], e1 = sg.ibeg[it + 1];
+    double nrm = 0.0;
+    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) {
+      const double t = w[k] - combine(a.V, ld, k, hs, jc);
+      w[k] = t;
+      nrm = fma(t, t, nrm);
+    }
+    nrm = block_sum<kBV>(nrm, red);
+    if (threadIdx.x == 0) part3[(long long)it * kMaxBasis] = nrm;
+  }
+  grid_barrier(st);
+  // Hessenberg column, rotations and stopping test of each problem
+  const int m = st->m;
+  for (int p = blockIdx.x; p < sg.P; p += G) {
+    PState* q = sg.ps + p;
+    if (q->stop_j <= j) continue;
+    const int it0 = sg.pitem[p], it1 = sg.pitem[p + 1];
+    seg_sum(part1, it0, it1, jc, hs);
+    for (int i = threadIdx.x; i < jc; i += kBV) hcol[i] = hs[i];
+    seg_sum(part2, it0, it1, jc, hs);
+    for (int i = threadIdx.x; i < jc; i += kBV) hcol[i] += hs[i];
+    const double hn = seg_hn(part3, it0, it1, &cell);
+    double* Hc = a.H + (long long)p * (m + 1) * m + (long long)j * (m + 1);
+    double* cs = a.cs + (long long)p * m;
+    double* sn = a.sn + (long long)p * m;
+    double* gv = a.gv + (long long)p * (m + 1);
+    if (threadIdx.x == 0) {
+      hcol[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = t;
+      }
+      const double x = hcol[j], y = hcol[j + 1];
+      const double r = hypot(x, y);
+      const double c = r > 0.0 ? x / r : 1.0, sgn = r > 0.0 ? y / r : 0.0;
+      cs[j] = c;
+      sn[j] = sgn;
+      hcol[j] = r;
+      hcol[j + 1] = 0.0;
+      const double g = gv[j];
+      gv[j + 1] = -sgn * g;
+      gv[j] = c * g;
+      q->res = fabs(sgn * g);
+      if (q->res <= q->tol_abs || !(hn > 1e-300 * q->beta)) {
+        q->stop_j = j + 1;
+        if (atomicSub(&st->nactive, 1) == 1) st->stop = 1;
       }
     }
     __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += kBV) Hc[i] = hcol[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->j = j + 1;
+    st->iters += 1;
+    if (j + 1 >= m || st->iters >= st->maxit) st->stop = 1;
+  }
+  // v_{j+1} = w / ||w|| per problem (zero for a problem that stopped before
+  // this step); with the preconditioner also z = P v, per body
+  if (!a.blocks) {
+    for (int it = blockIdx.x; it < sg.nitem; it += G) {
+      const int p = sg.iprob[it];
+      const bool active = sg.ps[p].stop_j > j;  // stop_j is j + 1 or above if set in this step
+      const double hn = active ? seg_hn(part3, sg.pitem[p], sg.pitem[p + 1], &cell) : 0.0;
+      const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+      for (long long k = sg.ibeg[it] + threadIdx.x; k < sg.ibeg[it + 1]; k += kBV) w[k] = active ? w[k] * inv : 0.0;
+    }
+    return;
+  }
+  const int c = a.kind + 1;
+  for (int i = blockIdx.x; i < a.g.N; i += G) {
+    const int p = sg.bprob[i];
+    const long long a0 = (long long)a.g.body_start[i] * c;
+    const int nb = (a.g.body_start[i + 1] - a.g.body_start[i]) * c;
+    const bool active = sg.ps[p].stop_j > j;
+    const double hn = active ? seg_hn(part3, sg.pitem[p], sg.pitem[p + 1], &cell) : 0.0;
+    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (!active || nb > kBjMaxBlock) {
+      for (int r = threadIdx.x; r < nb; r += kBV) {
+        const double v = active ? __ldcg(w + a0 + r) * inv : 0.0;
+        w[a0 + r] = v;
+        a.z[a0 + r] = v;
+      }
+      continue;
+    }
+    __syncthreads();  // ws may still be read for the previous body
+    for (int r = threadIdx.x; r < nb; r += kBV) {
+      const double v = __ldcg(w + a0 + r) * inv;
+      w[a0 + r] = v;
+      ws[r] = (float)v;
+    }
+    __syncthreads();
+    bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
   }
 }
 
@@ -404,6 +627,105 @@ __global__ void k_fill0(double* __restrict__ x, long long n) {
     x[k] = 0.0;
 }
 
+// Batched GMRES, one CTA per problem: r = f - y over the problem's entries,
+// its norm, and the opening of a cycle (g_p = (||r_p||, 0, ..); the problem
+// takes part unless already below its tolerance).  On the first call of a
+// solve (st->pad[0]) the tolerance is set relative to ||r_p|| = ||b_p||.  The
+// last CTA counts the active problems and stops the cycle if there are none.
+__global__ void __launch_bounds__(kBV) k_residual_seg(const double* __restrict__ f, const double* __restrict__ y,
+                                                      double* __restrict__ r, KState* st, SegArgs sg,
+                                                      double* gv, int m) {
+  __shared__ double sh[kBV / 32];
+  __shared__ int is_last;
+  const int p = blockIdx.x;
+  const long long k0 = sg.pnode[p], k1 = sg.pnode[p + 1];
+  double nrm = 0.0;
+  for (long long k = k0 + threadIdx.x; k < k1; k += kBV) {
+    const double v = y ? f[k] - y[k] : f[k];
+    r[k] = v;
+    nrm += v * v;
+  }
+  nrm = block_sum<kBV>(nrm, sh);
+  if (threadIdx.x == 0) {
+    PState* q = sg.ps + p;
+    const double rn = sqrt(nrm);
+    if (st->pad[0]) {
+      q->tol_abs = st->scratch[0] * rn;
+      q->bnorm = rn;
+    }
+    q->rnorm = rn;
+    q->beta = rn;
+    q->res = rn;
+    gv[(long long)p * (m + 1)] = rn;
+    q->stop_j = (rn <= q->tol_abs || !(rn > 0.0)) ? 0 : 0x7fffffff;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!is_last || threadIdx.x >= 32) return;
+  __threadfence();
+  int cnt = 0;
+  double s2 = 0.0;
+  for (int q = threadIdx.x; q < sg.P; q += 32) {
+    const double rn = __ldcg(&sg.ps[q].rnorm);
+    s2 += rn * rn;
+    cnt += __ldcg(&sg.ps[q].stop_j) > 0 ? 1 : 0;
+  }
+  s2 = warp_sum(s2);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (threadIdx.x != 0) return;
+  st->counter = 0;
+  st->pad[0] = 0;
+  st->rnorm = sqrt(s2);
+  st->nactive = cnt;
+  st->j = 0;
+  st->stop = (cnt == 0 || st->iters >= st->maxit) ? 1 : 0;
+}
+
+// V_0 = r / beta_p per problem (blockIdx.y = p; zero if the problem does not
+// take part in the cycle).
+__global__ void k_start_v0_seg(const double* __restrict__ r, double* __restrict__ V0, const KState* st,
+                               SegArgs sg) {
+  if (st->stop) return;
+  const int p = blockIdx.y;
+  const PState& q = sg.ps[p];
+  const double inv = q.stop_j > 0 ? 1.0 / q.beta : 0.0;
+  for (long long k = sg.pnode[p] + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < sg.pnode[p + 1];
+       k += (long long)gridDim.x * blockDim.x)
+    V0[k] = r[k] * inv;
+}
+
+// y_p = R_p^{-1} g_p over the steps problem p took part in (one thread each).
+__global__ void k_triangular_seg(const KState* st, SegArgs sg, const double* __restrict__ H,
+                                 const double* __restrict__ gv, double* y, int m) {
+  const int p = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const int jp = min(sg.ps[p].stop_j, st->j);
+  const double* Hp = H + (long long)p * (m + 1) * m;
+  const double* gp = gv + (long long)p * (m + 1);
+  double* yp = y + (long long)p * (m + 1);
+  for (int i = jp - 1; i >= 0; --i) {
+    double s = gp[i];
+    for (int k = i + 1; k < jp; ++k) s -= Hp[(long long)k * (m + 1) + i] * yp[k];
+    yp[i] = s / Hp[(long long)i * (m + 1) + i];
+  }
+}
+
+// x += V y_p over problem p's entries (blockIdx.y = p).
+__global__ void k_update_x_seg(const double* __restrict__ V, long long ld, const KState* st, SegArgs sg,
+                               const double* __restrict__ y, double* __restrict__ x, int m) {
+  __shared__ double ys[kMaxBasis];
+  const int p = blockIdx.y;
+  const int jp = min(sg.ps[p].stop_j, st->j);
+  if (jp <= 0) return;
+  for (int i = threadIdx.x; i < jp; i += blockDim.x) ys[i] = y[(long long)p * (m + 1) + i];
+  __syncthreads();
+  for (long long k = sg.pnode[p] + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < sg.pnode[p + 1];
+       k += (long long)gridDim.x * blockDim.x)
+    x[k] += combine(V, ld, k, ys, jp);
+}
+
 inline int elt_grid(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
@@ -413,7 +735,7 @@ inline int elt_grid(long long n) {
 
 int vec_grid(long long n) {
   long long b = (n + kBV - 1) / kBV;
-  if (b > 608) b = 608;
+  if (b > kMaxVecGrid) b = kMaxVecGrid;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -473,6 +795,51 @@ cudaError_t axpy(double* x, const double* d, long long n, cudaStream_t s) {
 
 cudaError_t fill0(double* x, long long n, cudaStream_t s) {
   k_fill0<<<elt_grid(n), 256, 0, s>>>(x, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+int arnoldi_seg_grid(long long n) {
+  static std::atomic<int> coresident[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (coresident[dev].load() == 0) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_seg, kBV, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm * sms < 1) {
+      cudaGetLastError();
+      return 1;
+    }
+    coresident[dev].store(per_sm * sms);
+  }
+  return std::min(vec_grid(n), coresident[dev].load());
+}
+
+cudaError_t arnoldi_seg(const ArnoldiArgs& a, const SegArgs& sg, int grid, cudaStream_t s) {
+  ArnoldiArgs args = a;
+  SegArgs sargs = sg;
+  void* params[] = {&args, &sargs};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi_seg, dim3(grid), dim3(kBV), params, 0, s);
+  note_launches(1);
+  return e;
+}
+
+cudaError_t residual_start_seg(const double* f, const double* y, double* r, double* V0, KState* st,
+                               const SegArgs& sg, double* gv, int m, cudaStream_t s) {
+  k_residual_seg<<<sg.P, kBV, 0, s>>>(f, y, r, st, sg, gv, m);
+  note_launches(1);
+  k_start_v0_seg<<<dim3(8, sg.P), 256, 0, s>>>(r, V0, st, sg);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_update_seg(const double* V, long long ld, KState* st, const SegArgs& sg, const double* H,
+                             const double* gv, double* y, double* x, int m, long long max_len, cudaStream_t s) {
+  k_triangular_seg<<<sg.P, 32, 0, s>>>(st, sg, H, gv, y, m);
+  note_launches(1);
+  const long long bx = std::min<long long>(64, std::max<long long>(1, (max_len + 255) / 256));
+  k_update_x_seg<<<dim3((unsigned)bx, sg.P), 256, 0, s>>>(V, ld, st, sg, y, x, m);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -124,3 +124,43 @@ def test_batch_nonneutral_and_errors(ctx):
     bad["body_start"][1] = 3  # a body of 3 nodes
     assert bie.elastance_solve_batch(ctx, [geoms[0], bad], loads[:2], outs[:2])[0] == bie.ERR_INVALID
     assert "fewer than 8" in ctx.last_error()
+
+
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED_FF])
+def test_zero_load_problem_in_batch(ctx, prec):
+    probs = _problems(1, 90, 4)
+    g, load = probs[2]
+    probs[2] = (g, np.zeros_like(load))
+    rc, _, outs = _solve_batch(ctx, 1, probs, bie.make_opts(precision=prec))
+    assert rc == bie.OK, ctx.last_error()
+    assert np.all(outs[2] == 0.0)
+    for i in (0, 1, 3):
+        assert rel2(outs[i], _oracle(1, *probs[i])) <= TOL_SOLVE
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_iterations_follow_the_slowest_problem(ctx, kind):
+    # one Krylov space per problem: the lockstep count is about the slowest
+    # problem's own count, not more because the problems are many
+    rng = np.random.default_rng(95)
+    probs = []
+    for i in range(32):
+        g = synth.four_discs(seed=i)
+        load = synth.charges(4, rng) if kind == 0 else synth.forces_torques(4, rng).reshape(-1)
+        probs.append((g, np.ascontiguousarray(load)))
+    for prec in (bie.FP64, bie.MIXED_FF):
+        opts = bie.make_opts(precision=prec)
+        rc, info, outs = _solve_batch(ctx, kind, probs, opts)
+        assert rc == bie.OK
+        fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
+        solo_iters = []
+        for (g, load), out in zip(probs, outs):
+            solo = np.empty_like(out)
+            rc1, inf1 = fn(ctx, _host(g), load, solo, opts=opts)
+            assert rc1 == bie.OK
+            solo_iters.append(inf1["iters"])
+            assert rel2(out, solo) <= TOL_SOLVE
+        print(f"kind={kind} prec={prec} batch iters {info['iters']} solo max {max(solo_iters)} "
+              f"rel_residual {info['rel_residual']:.2e}")
+        assert info["iters"] <= max(solo_iters) + 6
+        assert info["rel_residual"] <= 1e-12
