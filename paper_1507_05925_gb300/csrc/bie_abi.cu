@@ -158,7 +158,8 @@ struct Work {
 };
 
 void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool stage_in, bool stage_ipt,
-           bool stage_load, bool stage_io, long long bj_floats = 0, int nprob = 0, int src_max = 0) {
+           bool stage_load, bool stage_io, long long bj_floats = 0, int nprob = 0, const int* bs = nullptr,
+           const int* pb = nullptr) {
   const int comps = kind + 1;
   const long long n = (long long)M * comps;
   w.kind = kind;
@@ -206,9 +207,15 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.io_in = A.take<double>(n);
     w.io_out = A.take<double>(n);
   }
-  w.plan64 = plan_pairs(M, kind, 0, src_max);
-  w.plan32 = plan_pairs(M, kind, 1, src_max);
-  w.planff = plan_pairs(M, kind, 2, src_max);
+  if (nprob > 1) {
+    w.plan64 = plan_pairs_batch(bs, N, pb, nprob, kind, 0);
+    w.plan32 = plan_pairs_batch(bs, N, pb, nprob, kind, 1);
+    w.planff = plan_pairs_batch(bs, N, pb, nprob, kind, 2);
+  } else {
+    w.plan64 = plan_pairs(M, kind, 0);
+    w.plan32 = plan_pairs(M, kind, 1);
+    w.planff = plan_pairs(M, kind, 2);
+  }
   // problems solved as one system share every Krylov array; nseg copies of the
   // Hessenberg and rotation arrays with one Krylov space per problem
   const int nseg = nprob > 1 ? nprob : 1;
@@ -374,6 +381,11 @@ int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, cons
   w.g.prange = P > 1 ? w.prange : nullptr;
   w.g.pbody = w.pbody;
   w.g.nprob = P;
+  w.g.pairs = 0.0;
+  for (int p = 0; p < P; ++p) {
+    const double mp = bs[pb[p + 1]] - bs[pb[p]];
+    w.g.pairs += mp * (mp - 1.0);
+  }
   std::vector<long long> ib;
   std::vector<int> ip, pi, bp;
   if (P > 1) {
@@ -487,7 +499,7 @@ cudaError_t timed_pair_sum(bie_ctx* ctx, const Geo& g, int kind, int prec, const
   cudaError_t e = pair_sum(g, kind, prec, p, v, sscale, partial, stop, s);
   if (a && b) {
     cudaEventRecord(b, s);
-    ctx->pending.push_back({a, b, prec, kind, (double)g.M * (double)(g.M - 1), valid});
+    ctx->pending.push_back({a, b, prec, kind, g.pairs > 0.0 ? g.pairs : (double)g.M * (double)(g.M - 1), valid});
   }
   return e;
 }
@@ -502,8 +514,19 @@ struct Op {
   double alpha = 0.0;
   int fmm_p = 0;
   bool precond = false;  // GMRES on A P with the right block-Jacobi preconditioner P
+  bool skip_stopped = false;  // batched GMRES iteration: no pair sums for stopped problems
   // out = A in (the preconditioner is applied by the GMRES driver)
   cudaError_t apply(VecRef in, VecRef out, const int* stop, cudaStream_t s, bool valid = true) const {
+    if (skip_stopped && w->seg.P > 1 && fmm_p == 0) {
+      Geo g = w->g;
+      g.ps = w->ps;
+      g.bprob = w->bprob;
+      g.jstep = &w->st->j;
+      const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
+      cudaError_t e = timed_pair_sum(ctx, g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
+      if (e != cudaSuccess) return e;
+      return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
+    }
     if (fmm_p > 0) {
       const PairPlan one{1, w->g.M};
       cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s, prec);
@@ -540,7 +563,9 @@ int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   const long long n = w.n, ld = w.ld;
   const VecRef vj{w.V, ld, &w.st->j, 0}, vj1{w.V, ld, &w.st->j, 1};
   // w = A v_j, or A z_j with z_j = P v_j left in zbuf by the previous step
-  CK(op.apply(op.precond ? vec(w.zbuf) : vj, vj1, &w.st->stop, s, false));
+  Op it = op;
+  it.skip_stopped = true;
+  CK(it.apply(op.precond ? vec(w.zbuf) : vj, vj1, &w.st->stop, s, false));
   const ArnoldiArgs a{w.V,        ld,       n,      w.st,      w.arn, w.H, w.cs, w.sn, w.gv, w.g,
                       w.kind,     w.bj_off, op.precond ? w.bj_blocks : nullptr, w.zbuf};
   if (w.seg.P > 1) {
@@ -778,7 +803,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
                  const BatchIn* batch = nullptr) {
   std::vector<int> bs, pb;
   bool has_ipt = false;
-  int src_max = 0, rc;
+  int rc;
   if (batch) {
     if (!ctx) return BIE_ERR_INVALID;
     if (batch->P < 1 || batch->P > 65535 || !batch->geoms || !batch->loads || !batch->outs)
@@ -797,7 +822,6 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
       if ((long long)off + b[Np] > 0x3fffffffLL) return fail(ctx, BIE_ERR_INVALID, "batch: too many nodes");
       for (int i = 1; i <= Np; ++i) bs.push_back(off + b[i]);
       pb.push_back(pb.back() + Np);
-      src_max = std::max(src_max, b[Np]);
     }
   } else {
     if ((rc = validate(ctx, geom, bs))) return rc;
@@ -821,10 +845,10 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
   const long long bjf = use_bj ? bj_block_floats(bs.data(), N, kind) : 0;
   Arena sz{nullptr};
-  carve(sz, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, src_max);
+  carve(sz, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, bs.data(), pb.data());
   if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
   Arena ar{ctx->ws};
-  carve(ar, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, src_max);
+  carve(ar, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, bs.data(), pb.data());
   if (batch) {
     if ((rc = batch_setup(ctx, *batch, bs, pb, has_ipt, w, s))) return rc;
   } else if ((rc = setup(ctx, geom, bs, w, s))) {

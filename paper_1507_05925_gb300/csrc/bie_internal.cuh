@@ -22,6 +22,19 @@ constexpr double kInv2Pi = 0.15915494309189533577;  // 1/(2 pi)
 constexpr double kInvPi = 0.31830988618379067154;   // 1/pi
 constexpr double kInv4Pi = 0.07957747154594766788;  // 1/(4 pi)
 
+// Batched GMRES (many independent problems in one block-diagonal system): each
+// problem has its own Krylov space, Hessenberg matrix, rotations and stopping
+// test; the problems advance in lockstep and a problem that has converged
+// stops taking part.
+struct PState {
+  double tol_abs;  // stop threshold on this problem's residual estimate
+  double beta;     // norm of the problem's starting residual in this cycle
+  double res;      // residual estimate |g_{j+1}|
+  double rnorm;    // last computed true residual norm
+  double bnorm;    // norm of the problem's right-hand side
+  int stop_j;      // steps of this cycle it took part in (INT_MAX: still active)
+  int pad;
+};
 struct Geo {
   int N = 0, M = 0;
   const int* body_start = nullptr;  // [N+1]
@@ -44,6 +57,12 @@ struct Geo {
   const int2* prange = nullptr;
   const int* pbody = nullptr;  // [nprob+1] first body of each problem (batched solves)
   int nprob = 1;
+  // batched GMRES iterations only: a target block whose problems have all
+  // stopped (stop_j <= *jstep) skips its pair sums and writes zero partials
+  const PState* ps = nullptr;
+  const int* bprob = nullptr;  // [N] problem of each body
+  const int* jstep = nullptr;
+  double pairs = 0.0;  // pair interactions of one operator application (0: M (M - 1))
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a
@@ -80,19 +99,6 @@ struct KState {
   int nactive;        // batched GMRES: problems still iterating in this cycle
 };
 
-// Batched GMRES (many independent problems in one block-diagonal system): each
-// problem has its own Krylov space, Hessenberg matrix, rotations and stopping
-// test; the problems advance in lockstep and a problem that has converged
-// stops taking part.
-struct PState {
-  double tol_abs;  // stop threshold on this problem's residual estimate
-  double beta;     // norm of the problem's starting residual in this cycle
-  double res;      // residual estimate |g_{j+1}|
-  double rnorm;    // last computed true residual norm
-  double bnorm;    // norm of the problem's right-hand side
-  int stop_j;      // steps of this cycle it took part in (INT_MAX: still active)
-  int pad;
-};
 struct SegArgs {
   int P = 0;                      // problems (0: one system, not segmented)
   int nitem = 0;                  // element ranges of the fused Arnoldi step
@@ -153,8 +159,9 @@ struct PairPlan {
   int S;      // source splits
   int chunk;  // sources per split
 };
-// src_max > 0: no block sums over more than src_max sources (batched solves)
-PairPlan plan_pairs(int M, int kind, int precision, int src_max = 0);
+PairPlan plan_pairs(int M, int kind, int precision);
+// batched solves (host arrays: body_start [N+1], first body of each problem [P+1])
+PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P, int kind, int precision);
 cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
                      const double* sscale, double* partial, const int* stop, cudaStream_t s);
 

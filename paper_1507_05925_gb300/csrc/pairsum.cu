@@ -22,6 +22,7 @@
 // pairs and float-float pairs) is shared with the FMM near field.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "bie_internal.cuh"
 #include "pair_math.cuh"
@@ -33,7 +34,11 @@ namespace {
 
 // Source range of a target block [tbase, tend): all nodes, or in a batch the
 // nodes of the problems its targets belong to (straddle: more than one); the
-// block's split blockIdx.y of it (single problem: the planned chunk).
+// block's split blockIdx.y of it, `chunk` sources long.  In a batch the range
+// is cut into chunks of the planned length, so a block of a small problem has
+// fewer busy splits than one of a large problem (the others are empty and
+// write zero partials); a range longer than all splits together (a block
+// straddling problems) is cut into gridDim.y equal parts.
 struct SrcRange {
   int j0, j1;
   bool straddle;
@@ -48,11 +53,36 @@ __device__ __forceinline__ SrcRange src_range(const Geo& g, int tbase, int tend,
     return r;
   }
   const int2 p0 = g.prange[g.body_of[tbase]], p1 = g.prange[g.body_of[tend - 1]];
-  const int ch = (p1.y - p0.x + (int)gridDim.y - 1) / (int)gridDim.y;
-  r.j0 = p0.x + blockIdx.y * ch;
+  const int len = p1.y - p0.x;
+  const int ch = max(chunk, (len + (int)gridDim.y - 1) / (int)gridDim.y);
+  r.j0 = min(p1.y, p0.x + (int)blockIdx.y * ch);
   r.j1 = min(p1.y, r.j0 + ch);
   r.straddle = p0.x != p1.x;
   return r;
+}
+
+// Batched GMRES: have all problems of the target block [tbase, tend) stopped?
+// (block-uniform)  Such a block writes zero partials: its problems' next
+// Krylov vectors are not used.
+__device__ __forceinline__ bool block_stopped(const Geo& g, int tbase, int tend) {
+  if (!g.ps) return false;
+  const int j = *g.jstep;
+  const int p0 = g.bprob[g.body_of[tbase]], p1 = g.bprob[g.body_of[tend - 1]];
+  for (int p = p0; p <= p1; ++p)
+    if (g.ps[p].stop_j > j) return false;
+  return true;
+}
+
+template <int KIND>
+__device__ __forceinline__ void zero_partials(int tbase, int tend, int M, double* __restrict__ partial) {
+  for (int a = tbase + threadIdx.x; a < tend; a += blockDim.x) {
+    if (KIND == 0) {
+      partial[(long long)blockIdx.y * M + a] = 0.0;
+    } else {
+      partial[((long long)blockIdx.y * M + a) * 2] = 0.0;
+      partial[((long long)blockIdx.y * M + a) * 2 + 1] = 0.0;
+    }
+  }
 }
 
 // Does source node b belong to target a's problem (batched solves)?
@@ -81,6 +111,10 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB64 * kT64;
+  if (block_stopped(g, tbase, min(M, tbase + kB64 * kT64))) {
+    zero_partials<KIND>(tbase, min(M, tbase + kB64 * kT64), M, partial);
+    return;
+  }
   const SrcRange sr = src_range(g, tbase, min(M, tbase + kB64 * kT64), chunk);
   const int j0 = sr.j0, j1 = sr.j1;
   double tx[kT64], ty[kT64], tnx[kT64], tny[kT64], ax[kT64], ay[kT64];
@@ -267,6 +301,10 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
   const int tend = min(M, tbase + kB32 * kT32);
+  if (block_stopped(g, tbase, tend)) {
+    zero_partials<KIND>(tbase, tend, M, partial);
+    return;
+  }
   const SrcRange sr = src_range(g, tbase, tend, chunk);
   const int j0 = sr.j0, j1 = sr.j1;
   // the target block's box, centre and half-diagonal
@@ -432,6 +470,10 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
   const int M = g.M;
   const int tbase = blockIdx.x * kBF * kTF;
   const int tend = min(M, tbase + kBF * kTF);
+  if (block_stopped(g, tbase, tend)) {
+    zero_partials<KIND>(tbase, tend, M, partial);
+    return;
+  }
   const int a0 = tbase + threadIdx.x;
   const SrcRange sr = src_range(g, tbase, tend, chunk);
   const int j0 = sr.j0, j1 = sr.j1;
@@ -653,21 +695,58 @@ const DeviceShape& device_shape() {
 // Choose the source split so that one wave fills every SM with as many
 // blocks as can be resident: blocks = target blocks x splits ~ SMs x occupancy.
 // Splits need not be tile-aligned (the kernels handle a short last tile).
-PairPlan plan_pairs(int M, int kind, int precision, int src_max) {
+PairPlan plan_pairs(int M, int kind, int precision) {
   const DeviceShape& d = device_shape();
   const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
   const long long bx = (M + per_block - 1) / per_block;
   const long long slots = (long long)d.nsm * d.occ[precision][kind];
   long long S = bx >= slots ? 1 : slots / bx;
   const long long min_chunk = 64;
-  // a block's sources: all M nodes, or (batched solves) at most src_max
-  const long long src = src_max > 0 ? src_max : M;
-  if (S > (src + min_chunk - 1) / min_chunk) S = (src + min_chunk - 1) / min_chunk;
+  if (S > (M + min_chunk - 1) / min_chunk) S = (M + min_chunk - 1) / min_chunk;
   if (S < 1) S = 1;
   const long long chunk = (M + S - 1) / S;
   PairPlan p;
   p.chunk = (int)chunk;
   p.S = (int)((M + chunk - 1) / chunk);
+  return p;
+}
+
+// Batched solves: target block x sums over the len_x nodes of its problems.
+// With S splits of chunk = ceil(src_max / S) sources, block x has
+// ceil(len_x / chunk) busy splits, each with about the same work whatever the
+// problem's size.  S is the smallest count whose busy blocks fill every
+// resident slot once (chunks of at least 64 sources).
+PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P, int kind, int precision) {
+  const DeviceShape& d = device_shape();
+  const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
+  const int M = body_start[N];
+  std::vector<int> pstart(P + 1);
+  int src_max = 1;
+  for (int p = 0; p <= P; ++p) pstart[p] = p < P ? body_start[pbody[p]] : M;
+  for (int p = 0; p < P; ++p) src_max = std::max(src_max, pstart[p + 1] - pstart[p]);
+  const int bx = (M + per_block - 1) / per_block;
+  std::vector<int> len(bx);
+  for (int x = 0; x < bx; ++x) {
+    const int tb = x * per_block, te = std::min(M, tb + per_block);
+    const int p0 = (int)(std::upper_bound(pstart.begin(), pstart.end(), tb) - pstart.begin()) - 1;
+    const int p1 = (int)(std::upper_bound(pstart.begin(), pstart.end(), te - 1) - pstart.begin()) - 1;
+    len[x] = pstart[p1 + 1] - pstart[p0];
+  }
+  const long long slots = (long long)d.nsm * d.occ[precision][kind];
+  const int s_cap = std::max(1, (src_max + 63) / 64);
+  int S = 1;
+  for (; S < s_cap; ++S) {
+    const long long chunk = ((long long)src_max + S - 1) / S;
+    long long busy = 0;
+    for (int x = 0; x < bx; ++x) {
+      const long long ch = std::max(chunk, ((long long)len[x] + S - 1) / S);
+      busy += (len[x] + ch - 1) / ch;
+    }
+    if (busy >= slots) break;
+  }
+  PairPlan p;
+  p.S = S;
+  p.chunk = (src_max + S - 1) / S;
   return p;
 }
 
