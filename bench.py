@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--serve-batch", type=int, default=8,
+                    help="served stream again with up to this many queued requests solved together (<= 1: skip)")
     ap.add_argument("--fmm-order", type=int, default=36)
     ap.add_argument("--only-large", action="store_true",
                     help="run only the large mobility section (FMM), e.g. for ncu captures")
@@ -315,6 +317,27 @@ def run_serving(args, rank, local):
     poisson_s = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+    batched = None
+    if args.serve_batch > 1:
+        # the same saturated stream with queued requests solved in batches
+        srv = bie.Server(local, workers=args.serve_workers, hbm_cap_bytes=cap)
+        srv.batching(args.serve_batch)
+        for i in range(min(32, len(host))):  # warm-up
+            srv.wait(submit(i))
+        nb0 = srv.batching()
+        t0 = time.perf_counter()
+        tickets = [submit(i) for i in range(len(host))]
+        lat_b = []
+        for t in tickets:
+            rc, _, sec = srv.wait(t)
+            if rc < 0:
+                raise RuntimeError(f"served solve failed: {rc}")
+            lat_b.append(sec)
+        bat_s = time.perf_counter() - t0
+        batched = {"max_batch": args.serve_batch, "solves_per_s": len(host) / bat_s, "seconds": bat_s,
+                   "batched_solves": srv.batching() - nb0, "p50_ms": 1e3 * float(np.percentile(lat_b, 50)),
+                   "p99_ms": 1e3 * float(np.percentile(lat_b, 99)), "peak_inflight_bytes": srv.stats()["peak_inflight_bytes"]}
+        srv.close()
     M = [g["x"].size for g in reqs]
     return {
         "requests": len(host), "workers": args.serve_workers, "hbm_cap_bytes": cap,
@@ -328,6 +351,7 @@ def run_serving(args, rank, local):
                           "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                           "p99_ms": 1e3 * float(np.percentile(lat, 99))},
         "peak_inflight_bytes": st["peak_inflight_bytes"],
+        "saturated_batched": batched,
     }
 
 
@@ -362,12 +386,14 @@ def run_batched(args, rank, local):
                 loads.append(torch.from_numpy(np.ascontiguousarray(ld)).to(dev))
                 outs.append(torch.empty_like(loads[-1]))
             for _ in range(3):
-                rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+                rc, infos, _ = fn(ctx, geoms, loads, outs, opts=opts)
+                info = infos[0]
             reps = max(3, 512 // P)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
-                rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+                rc, infos, _ = fn(ctx, geoms, loads, outs, opts=opts)
+                info = infos[0]
                 if rc < 0:
                     raise RuntimeError(f"batched solve failed: {rc} {ctx.last_error()}")
             torch.cuda.synchronize()
@@ -393,7 +419,8 @@ def run_batched(args, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for geoms, loads, outs in host:
-            rc, info = fn(ctx, geoms, loads, outs, opts=opts)
+            rc, infos, _ = fn(ctx, geoms, loads, outs, opts=opts)
+            info = infos[0]
             if rc < 0:
                 raise RuntimeError(f"batched solve failed: {rc} {ctx.last_error()}")
             iters.append(info["iters"])

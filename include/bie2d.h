@@ -168,17 +168,20 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
  * matrix, rotations and stopping test); the problems advance in lockstep and a
  * problem that has converged stops taking part.  Each problem's right-hand side
  * is scaled to unit norm; every problem's own relative residual ends at most
- * opts->tol.  info is for the batch: iters counts lockstep iterations (those of
- * the slowest problem); rel_residual is the largest relative residual of any
- * problem (mixed with float-float residual updates: plus their rounding
- * bound); net load is the largest of any problem.  Direct pair sums
- * only (fmm_order 0), no density output; interior points for all problems or
- * for none; 1 <= count <= 65535.  Errors: BIE_ERR_INVALID for a bad argument in
- * any problem (message names it). */
+ * opts->tol.  info (nullable) receives one bie_info per problem [count]: iters,
+ * refinements and matvec counts are the batch's (lockstep iterations, those of
+ * the slowest problem); rel_residual, constraint_residual and net_load are the
+ * problem's own (mixed with float-float residual updates, rel_residual
+ * includes their rounding bound).  status (nullable) receives each problem's
+ * status [count] (BIE_OK, BIE_WARN_NONNEUTRAL, BIE_WARN_NOT_CONVERGED); the
+ * return value is the worst of them, or an error for the whole batch.  Direct
+ * pair sums only (fmm_order 0), no density output; interior points for all
+ * problems or for none; 1 <= count <= 65535.  Errors: BIE_ERR_INVALID for a bad
+ * argument in any problem (message names it). */
 int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
-                          double* const* phi, const bie_opts* opts, bie_info* info, void* stream);
+                          double* const* phi, const bie_opts* opts, bie_info* info, int* status, void* stream);
 int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,
-                         double* const* UW, const bie_opts* opts, bie_info* info, void* stream);
+                         double* const* UW, const bie_opts* opts, bie_info* info, int* status, void* stream);
 
 /* One application of the discrete second-kind operator (eqs. ModRep2,
  * ModRep2Stokes): out = (1/2 I + K + L) in, on unscaled densities.
@@ -235,7 +238,8 @@ size_t bie_workspace_bytes(int kind, int n_bodies, int n_nodes, int restart);
  * free and their workspace (bie_workspace_bytes) fits under hbm_cap_bytes
  * together with the requests in flight (0 = no cap); a request may pass an
  * earlier one that does not fit yet, but not more than 64 times.  Results do
- * not depend on what else is in flight: every kernel reduces in a fixed order. */
+ * not depend on what else is in flight: every kernel reduces in a fixed order
+ * (unless batching is turned on, bie_server_batching). */
 typedef struct bie_server bie_server;
 
 typedef struct {
@@ -255,6 +259,17 @@ int bie_server_submit(bie_server* srv, const bie_request* req, int64_t* ticket);
  * (nullable) and seconds (nullable) = time from submit to completion.  Each
  * ticket can be waited for once. */
 int bie_server_wait(bie_server* srv, int64_t ticket, bie_info* info, double* seconds);
+/* Batching of queued requests (off by default: max_batch 1).  A worker that
+ * takes a request also takes up to max_batch - 1 queued requests of the same
+ * kind, the same bie_opts and the same use of interior points (each of at most
+ * max_request_nodes nodes, default 16,384; no density output, fmm_order 0;
+ * 262,144 nodes a batch) and solves them together (elastance_solve_batch /
+ * mobility_solve_batch); admission reserves the batch's workspace.  A batched
+ * request's result agrees with its solo result to the solve tolerance, not
+ * bitwise; with max_batch 1 results do not depend on what else is in flight.
+ * 0 leaves a limit unchanged.  batches (nullable) receives the number of
+ * batched solves (two or more requests) run so far. */
+int bie_server_batching(bie_server* srv, int max_batch, int max_request_nodes, int64_t* batches);
 /* Completed requests, workspace bytes of the requests now in flight, and the
  * largest such sum seen. */
 int bie_server_stats(bie_server* srv, int64_t* completed, size_t* inflight_bytes, size_t* peak_inflight_bytes);

@@ -97,7 +97,7 @@ def load():
     for name in ("elastance_solve_batch", "mobility_solve_batch"):
         f = getattr(lib, name)
         f.argtypes = [vp, i32, ctypes.POINTER(BieGeometry), ctypes.POINTER(vp), ctypes.POINTER(vp),
-                      ctypes.POINTER(BieOpts), ctypes.POINTER(BieInfo), vp]
+                      ctypes.POINTER(BieOpts), ctypes.POINTER(BieInfo), ctypes.POINTER(i32), vp]
         f.restype = i32
     lib.apply_operator.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator.restype = i32
@@ -116,6 +116,8 @@ def load():
     lib.bie_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
     lib.bie_server_stats.restype = i32
+    lib.bie_server_batching.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.bie_server_batching.restype = i32
     lib.bie_server_destroy.argtypes = [vp]
     lib.bie_server_destroy.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
@@ -245,25 +247,29 @@ def mobility_solve(ctx: Context, geom, FT, UW, density=None, opts: BieOpts | Non
 def _solve_batch(fn, ctx: Context, geoms, loads, outs, opts, stream):
     if not (len(geoms) == len(loads) == len(outs)) or len(geoms) == 0:
         raise ValueError("geoms, loads and outs must be non-empty lists of one length")
+    P = len(geoms)
     built = [make_geometry(g) for g in geoms]
-    arr = (BieGeometry * len(geoms))(*[b[0] for b in built])
-    pl = (ctypes.c_void_p * len(loads))(*[_ptr(x) for x in loads])
-    po = (ctypes.c_void_p * len(outs))(*[_ptr(x) for x in outs])
-    info = BieInfo()
-    rc = fn(ctx.handle, len(geoms), arr, pl, po, ctypes.byref(opts) if opts is not None else None,
-            ctypes.byref(info), _stream_ptr(stream))
+    arr = (BieGeometry * P)(*[b[0] for b in built])
+    pl = (ctypes.c_void_p * P)(*[_ptr(x) for x in loads])
+    po = (ctypes.c_void_p * P)(*[_ptr(x) for x in outs])
+    infos = (BieInfo * P)()
+    status = (ctypes.c_int32 * P)()
+    rc = fn(ctx.handle, P, arr, pl, po, ctypes.byref(opts) if opts is not None else None,
+            infos, status, _stream_ptr(stream))
     del built
-    return rc, info.as_dict()
+    return rc, [i.as_dict() for i in infos], list(status)
 
 
 def elastance_solve_batch(ctx: Context, geoms, qs, phis, opts: BieOpts | None = None, stream=None):
     """elastance_solve_batch of include/bie2d.h: lists of geometries, charges and
-    potential outputs, solved together; returns (status, info dict for the batch)."""
+    potential outputs, solved together; returns (status of the batch, per-problem
+    info dicts, per-problem statuses)."""
     return _solve_batch(ctx.lib.elastance_solve_batch, ctx, geoms, qs, phis, opts, stream)
 
 
 def mobility_solve_batch(ctx: Context, geoms, FTs, UWs, opts: BieOpts | None = None, stream=None):
-    """mobility_solve_batch of include/bie2d.h; returns (status, info dict for the batch)."""
+    """mobility_solve_batch of include/bie2d.h; returns (status of the batch,
+    per-problem info dicts, per-problem statuses)."""
     return _solve_batch(ctx.lib.mobility_solve_batch, ctx, geoms, FTs, UWs, opts, stream)
 
 
@@ -320,6 +326,15 @@ class Server:
         rc = self.lib.bie_server_wait(self.handle, ticket, ctypes.byref(info), ctypes.byref(sec))
         self._keep.pop(ticket, None)
         return rc, info.as_dict(), sec.value
+
+    def batching(self, max_batch: int = 0, max_request_nodes: int = 0) -> int:
+        """bie_server_batching: set the batch limits (0 = unchanged); returns the
+        number of batched solves run so far."""
+        b = ctypes.c_int64()
+        rc = self.lib.bie_server_batching(self.handle, max_batch, max_request_nodes, ctypes.byref(b))
+        if rc != OK:
+            raise ValueError(f"bie_server_batching failed with status {rc}")
+        return int(b.value)
 
     def stats(self) -> dict:
         c, i, p = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t()

@@ -141,6 +141,7 @@ struct Work {
   long long* pnode = nullptr;
   double* pscale = nullptr;
   double* pnorm = nullptr;  // per-problem residual norms of the refinement
+  double* pnet = nullptr;   // per-problem net load and largest |load|
   // batched GMRES (one Krylov space per problem): element ranges of the fused
   // Arnoldi step and per-problem state; seg.P == 0 for a single system
   SegArgs seg;
@@ -225,6 +226,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.pnode = A.take<long long>(nprob + 1);
     w.pscale = A.take<double>(nprob);
     w.pnorm = A.take<double>(nprob);
+    w.pnet = A.take<double>(2 * nprob);
   }
   if (nprob > 1) {
     w.prange = A.take<int2>(N);
@@ -350,6 +352,8 @@ struct BatchIn {
   const bie_geometry* geoms;   // [P]
   const double* const* loads;  // [P]
   double* const* outs;         // [P]
+  bie_info* infos;             // [P] or nullptr
+  int* status;                 // [P] or nullptr
 };
 
 // Stage the problems one after another (host or device inputs) and the tables
@@ -381,6 +385,7 @@ int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, cons
   w.g.prange = P > 1 ? w.prange : nullptr;
   w.g.pbody = w.pbody;
   w.g.nprob = P;
+  w.g.pnet = w.pnet;
   w.g.pairs = 0.0;
   for (int p = 0; p < P; ++p) {
     const double mp = bs[pb[p + 1]] - bs[pb[p]];
@@ -544,6 +549,7 @@ struct KrylovResult {
   int iters = 0, matvecs = 0, matvecs64 = 0;
   double res = 0.0, bnorm = 0.0;
   bool converged = false;
+  std::vector<double> prel;  // batched GMRES: every problem's relative residual
 };
 
 int read_state(bie_ctx* ctx, const Work& w, cudaStream_t s) {
@@ -730,9 +736,11 @@ int gmres_seg(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, d
     CK(cudaMemcpyAsync(ps.data(), w.ps, ps.size() * sizeof(PState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double rel = -1.0;
+    out.prel.clear();
     for (const PState& q : ps) {
       const double r = verify ? q.rnorm : q.res;
       const double e = q.bnorm > 0.0 ? r / q.bnorm : 0.0;
+      out.prel.push_back(e);
       if (e > rel) {
         rel = e;
         out.res = r;
@@ -902,6 +910,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   int m64 = o.formulation == 1 ? 1 : 0, m32 = 0, mff = 0, iters = 0, refs = 0;
   double relres = 0.0, eps32_report = 0.0;
   bool converged = false, relres_per_problem = false;
+  std::vector<double> prob_rel;  // batched: every problem's relative residual
   // GMRES on one system, or (several problems) one Krylov space per problem
   auto krylov = [&](const Op& op, const double* b, double* x, double tol_rel, int maxit, bool verify,
                     KrylovResult& kr) -> int {
@@ -917,6 +926,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     relres = kr.bnorm > 0 ? kr.res / kr.bnorm : 0.0;
     relres_per_problem = w.seg.P > 1;
     converged = kr.converged;
+    prob_rel = kr.prel;
   } else {
     // FP64 iterative refinement: x += A32^{-1}(f - A64 x)
     CK(fill0(w.xs, n, s));
@@ -1017,6 +1027,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     if (per_problem) {
       relres = worst + bound;  // the largest relative residual of any problem (unit right-hand sides)
       relres_per_problem = true;
+      for (double v : pn_host) prob_rel.push_back(v + bound);
     }
     eps32_report = eps32 > 0.0 ? eps32 : 0.0;
   }
@@ -1057,6 +1068,40 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const double* nl = w.outpart + (size_t)P_used * targets * (kind + 1) + N;
   CK(cudaMemcpyAsync(ctx->h_small, w.cres, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_small + 1, nl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (batch) {
+    // every problem's own info and status: per-body constraint values and
+    // per-problem net loads from the output kernels
+    std::vector<double> cbody(N), pnet(2 * P);
+    CK(cudaMemcpyAsync(cbody.data(), nl - N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pnet.data(), w.pnet, 2 * P * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (prob_rel.size() != (size_t)P) prob_rel.assign(P, relres);  // a batch of one
+    int worst_status = BIE_OK;
+    for (int p = 0; p < P; ++p) {
+      double cmax = 0.0;
+      for (int i = pb[p]; i < pb[p + 1]; ++i) cmax = std::max(cmax, cbody[i]);
+      const double net = pnet[2 * p], mx = pnet[2 * p + 1];
+      const int Np = pb[p + 1] - pb[p];
+      int st = BIE_OK;
+      if (!(prob_rel[p] <= tol_user) && !(converged && P == 1)) st = BIE_WARN_NOT_CONVERGED;
+      else if (net > 1e-12 * std::max(mx, 1e-300) * std::max(1, Np)) st = BIE_WARN_NONNEUTRAL;
+      if (batch->status) batch->status[p] = st;
+      if (batch->infos) {
+        bie_info& q = batch->infos[p];
+        q.iters = iters;
+        q.refinements = refs;
+        q.matvecs_fp64 = m64;
+        q.matvecs_fp32 = m32;
+        q.matvecs_ff = mff;
+        q.rel_residual = prob_rel[p];
+        q.constraint_residual = cmax / std::max(mx, 1e-300);
+        q.net_load = net;
+        q.fp32_error = eps32_report;
+      }
+      if (st == BIE_WARN_NOT_CONVERGED || (st == BIE_WARN_NONNEUTRAL && worst_status == BIE_OK)) worst_status = st;
+    }
+    return worst_status;
+  }
   CK(cudaStreamSynchronize(s));
   const double netload = ctx->h_small[1], maxload = ctx->h_small[2];
   if (info) {
@@ -1117,6 +1162,17 @@ void release_workspace(bie_ctx* ctx, cudaStream_t s) {
 }  // namespace bie
 
 namespace bie {
+size_t workspace_bytes_batch(int kind, const int* bs, int n_bodies, const int* pb, int nprob, const bie_opts* opts) {
+  bie_opts o;
+  fill_opts(opts, o);
+  Work w;
+  Arena sz{nullptr};
+  const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
+  carve(sz, w, n_bodies, bs[n_bodies], kind, o.restart, true, true, true, true, false,
+        use_bj ? bj_block_floats(bs, n_bodies, kind) : 0, nprob, bs, pb);
+  return sz.off;
+}
+
 size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart) {
   const int n_nodes = body_start_host[n_bodies];
   Work w;
@@ -1215,15 +1271,15 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
 }
 
 int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
-                          double* const* phi, const bie_opts* opts, bie_info* info, void* stream) {
-  const BatchIn b{count, geoms, q, phi};
-  return solve_common(ctx, nullptr, 0, nullptr, nullptr, nullptr, opts, info, (cudaStream_t)stream, &b);
+                          double* const* phi, const bie_opts* opts, bie_info* info, int* status, void* stream) {
+  const BatchIn b{count, geoms, q, phi, info, status};
+  return solve_common(ctx, nullptr, 0, nullptr, nullptr, nullptr, opts, nullptr, (cudaStream_t)stream, &b);
 }
 
 int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,
-                         double* const* UW, const bie_opts* opts, bie_info* info, void* stream) {
-  const BatchIn b{count, geoms, FT, UW};
-  return solve_common(ctx, nullptr, 1, nullptr, nullptr, nullptr, opts, info, (cudaStream_t)stream, &b);
+                         double* const* UW, const bie_opts* opts, bie_info* info, int* status, void* stream) {
+  const BatchIn b{count, geoms, FT, UW, info, status};
+  return solve_common(ctx, nullptr, 1, nullptr, nullptr, nullptr, opts, nullptr, (cudaStream_t)stream, &b);
 }
 
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, const double* in,

@@ -15,6 +15,8 @@
 
 #include <string>
 
+#include "../../include/bie2d.h"
+
 namespace bie {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -63,6 +65,7 @@ struct Geo {
   const int* bprob = nullptr;  // [N] problem of each body
   const int* jstep = nullptr;
   double pairs = 0.0;  // pair interactions of one operator application (0: M (M - 1))
+  double* pnet = nullptr;  // [2 nprob] batched solves: each problem's net load and largest |load|
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a
@@ -194,6 +197,9 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
 
 // workspace of a solve with the given host body_start (bie_workspace_bytes assumes equal bodies)
 size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart);
+// workspace of a batched solve (host arrays: concatenated body_start [N+1],
+// first body of each problem [nprob+1])
+size_t workspace_bytes_batch(int kind, const int* bs, int n_bodies, const int* pb, int nprob, const bie_opts* opts);
 
 // Batched solves: per-problem unit-norm scaling of f (pnode = entry offsets
 // of the problems) and the inverse scaling of the solution.

@@ -187,14 +187,16 @@ __global__ void k_scale_by(int M, int comps, const double* __restrict__ in, cons
 }
 
 // Net load |sum_i q_i| (or |sum_i F_i|) and max |load|; in a batch (pbody =
-// body offsets of the P problems) the largest net load of any problem.
+// body offsets of the P problems) the largest net load of any problem, and
+// (per != nullptr) each problem's net load and largest |load| in per[2p], per[2p+1].
 __global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* __restrict__ load,
-                                                  const int* __restrict__ pbody, int P, double* __restrict__ out) {
+                                                  const int* __restrict__ pbody, int P, double* __restrict__ out,
+                                                  double* __restrict__ per) {
   __shared__ double sh[kB / 32];
-  double nmx = 0, worst = 0;  // nmx: -max |load|
+  double gmax = 0, worst = 0;
   for (int p = 0; p < P; ++p) {
     const int i0 = pbody ? pbody[p] : 0, i1 = pbody ? pbody[p + 1] : N;
-    double s0 = 0, s1 = 0;
+    double s0 = 0, s1 = 0, nmx = 0;  // nmx: -max |load| over the problem
     for (int i = i0 + threadIdx.x; i < i1; i += kB) {
       if (kind == 0) {
         s0 += load[i];
@@ -207,12 +209,18 @@ __global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* 
     }
     s0 = block_sum<kB>(s0, sh);
     s1 = block_sum<kB>(s1, sh);
-    worst = fmax(worst, sqrt(s0 * s0 + s1 * s1));
+    nmx = block_min<kB>(nmx, sh);
+    const double net = sqrt(s0 * s0 + s1 * s1);
+    worst = fmax(worst, net);
+    gmax = fmax(gmax, -nmx);
+    if (per && threadIdx.x == 0) {
+      per[2 * p] = net;
+      per[2 * p + 1] = -nmx;
+    }
   }
-  nmx = block_min<kB>(nmx, sh);
   if (threadIdx.x == 0) {
     out[0] = worst;
-    out[1] = -nmx;
+    out[1] = gmax;
   }
 }
 
@@ -419,7 +427,7 @@ cudaError_t finalize_output(const Geo& g, int kind, const double* v, const doubl
   double* nl = cbody + g.N;
   k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
   note_launches(1);
-  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, g.pbody, g.pbody ? g.nprob : 1, nl);
+  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, g.pbody, g.pbody ? g.nprob : 1, nl, g.pnet);
   note_launches(1);
   k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
   note_launches(1);
@@ -477,7 +485,7 @@ cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norm
 }
 
 cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s) {
-  k_net_load<<<1, kB, 0, s>>>(N, kind, load, nullptr, 1, out);
+  k_net_load<<<1, kB, 0, s>>>(N, kind, load, nullptr, 1, out, nullptr);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -6,7 +6,10 @@
 // starts only when a worker is free and its workspace fits under the cap
 // together with the requests in flight.  The queue is first-in first-out,
 // except that a request that fits may pass the head of the queue when the
-// head does not fit yet, at most kMaxPass times per head request.
+// head does not fit yet, at most kMaxPass times per head request.  With
+// batching on (bie_server_batching), a worker that takes a request also takes
+// queued requests of the same kind and options (up to the batch limits) and
+// solves them together as one block-diagonal system (the batched solves).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -30,6 +33,7 @@ struct Job {
   bie_request req;
   int64_t ticket = 0;
   size_t need = 0;
+  std::vector<int> bs;  // body_start (host copy)
   Clock::time_point t_submit;
   double seconds = 0.0;
   int status = BIE_OK;
@@ -50,6 +54,10 @@ struct bie_server {
   int64_t next_ticket = 1, completed = 0;
   int head_passed = 0;
   bool stopping = false;
+  int max_batch = 1;                  // requests a worker may solve together
+  int max_request_nodes = 16384;      // larger requests are solved alone
+  int max_batch_nodes = 262144;       // nodes of one batch
+  int64_t batches = 0;                // batched solves run (two or more requests)
   std::vector<std::thread> workers;
 };
 
@@ -77,41 +85,120 @@ Job* pick(bie_server* s) {
   return nullptr;
 }
 
+bool batchable(const bie_server* s, const Job* j) {
+  return j->req.density == nullptr && j->req.opts.fmm_order == 0 && j->bs.back() <= s->max_request_nodes;
+}
+
+bool same_batch(const Job* a, const Job* b) {
+  return a->req.kind == b->req.kind && memcmp(&a->req.opts, &b->req.opts, sizeof(bie_opts)) == 0 &&
+         (a->req.geom.interior_pt != nullptr) == (b->req.geom.interior_pt != nullptr);
+}
+
+// After pick: more queued requests to solve together with `first` (mu held),
+// in queue order, while the batch's workspace fits under the cap.  Returns
+// the bytes to reserve for the whole batch.
+size_t grow_batch(bie_server* s, Job* first, std::vector<Job*>& batch) {
+  batch.assign(1, first);
+  size_t need = first->need;
+  if (s->max_batch <= 1 || !batchable(s, first)) return need;
+  std::vector<int> bs(first->bs), pb{0, (int)first->bs.size() - 1};
+  int nodes = first->bs.back();
+  for (auto it = s->queue.begin(); it != s->queue.end() && (int)batch.size() < s->max_batch;) {
+    Job* c = *it;
+    if (!batchable(s, c) || !same_batch(first, c) || nodes + c->bs.back() > s->max_batch_nodes) {
+      ++it;
+      continue;
+    }
+    std::vector<int> bs2(bs), pb2(pb);
+    const int off = bs2.back();
+    for (size_t i = 1; i < c->bs.size(); ++i) bs2.push_back(off + c->bs[i]);
+    pb2.push_back(pb2.back() + (int)c->bs.size() - 1);
+    const int N = (int)bs2.size() - 1, P = (int)pb2.size() - 1;
+    const size_t need2 = bie::workspace_bytes_batch(first->req.kind, bs2.data(), N, pb2.data(), P, &first->req.opts);
+    if (s->cap && s->inflight + need2 > s->cap) break;  // the batch would not fit
+    batch.push_back(c);
+    bs.swap(bs2);
+    pb.swap(pb2);
+    nodes += c->bs.back();
+    need = need2;
+    it = s->queue.erase(it);
+  }
+  return need;
+}
+
+void finish(bie_server* s, Job* j, int status, const bie_info& info) {
+  j->status = status;
+  j->info = info;
+  j->seconds = std::chrono::duration<double>(Clock::now() - j->t_submit).count();
+  j->done = true;
+  s->completed += 1;
+}
+
 void worker_main(bie_server* s) {
   cudaSetDevice(s->device);
   bie_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   const bool ok = bie_create(&ctx, s->device, 0) == BIE_OK &&
                   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  std::vector<Job*> batch;
+  std::vector<bie_geometry> geoms;
+  std::vector<const double*> loads;
+  std::vector<double*> outs;
+  std::vector<bie_info> infos;
+  std::vector<int> status;
+  auto solo = [&](Job* b, bie_info* info) -> int {
+    const bie_request& r = b->req;
+    if (r.kind == BIE_KIND_LAPLACE)
+      return elastance_solve(ctx, &r.geom, r.load, r.out, r.density, &r.opts, info, stream);
+    return mobility_solve(ctx, &r.geom, r.load, r.out, r.density, &r.opts, info, stream);
+  };
   for (;;) {
     Job* j = nullptr;
+    size_t reserved = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return (s->stopping && s->queue.empty()) || (j = pick(s)) != nullptr; });
       if (!j) break;
-      s->inflight += j->need;
+      reserved = grow_batch(s, j, batch);
+      s->inflight += reserved;
       if (s->inflight > s->peak) s->peak = s->inflight;
+      if (batch.size() > 1) s->batches += 1;
     }
-    int status = BIE_ERR_CUDA;
-    bie_info info{};
+    const int P = (int)batch.size();
+    infos.assign(P, bie_info{});
+    status.assign(P, BIE_ERR_CUDA);
     if (ok) {
       const bie_opts* opts = &j->req.opts;
-      if (j->req.kind == BIE_KIND_LAPLACE)
-        status = elastance_solve(ctx, &j->req.geom, j->req.load, j->req.out, j->req.density, opts, &info, stream);
-      else
-        status = mobility_solve(ctx, &j->req.geom, j->req.load, j->req.out, j->req.density, opts, &info, stream);
+      if (P == 1) {
+        status[0] = solo(j, &infos[0]);
+      } else {
+        geoms.clear();
+        loads.clear();
+        outs.clear();
+        for (Job* b : batch) {
+          geoms.push_back(b->req.geom);
+          loads.push_back(b->req.load);
+          outs.push_back(b->req.out);
+        }
+        const int rc = j->req.kind == BIE_KIND_LAPLACE
+                           ? elastance_solve_batch(ctx, P, geoms.data(), loads.data(), outs.data(), opts,
+                                                   infos.data(), status.data(), stream)
+                           : mobility_solve_batch(ctx, P, geoms.data(), loads.data(), outs.data(), opts,
+                                                  infos.data(), status.data(), stream);
+        if (rc < 0) {
+          // one bad request must fail alone: solve the batch's requests one by one
+          cudaStreamSynchronize(stream);
+          for (int p = 0; p < P; ++p) status[p] = solo(batch[p], &infos[p]);
+        }
+      }
       // memory follows the requests in flight: hand the workspace back to the pool
       bie::release_workspace(ctx, stream);
       cudaStreamSynchronize(stream);
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->inflight -= j->need;
-      j->status = status;
-      j->info = info;
-      j->seconds = std::chrono::duration<double>(Clock::now() - j->t_submit).count();
-      j->done = true;
-      s->completed += 1;
+      s->inflight -= reserved;
+      for (int p = 0; p < P; ++p) finish(s, batch[p], status[p], infos[p]);
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -173,6 +260,7 @@ int bie_server_submit(bie_server* s, const bie_request* req, int64_t* ticket) {
   Job* j = new Job();
   j->req = *req;
   j->need = need;
+  j->bs.swap(bs);
   j->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -202,6 +290,15 @@ int bie_server_wait(bie_server* s, int64_t ticket, bie_info* info, double* secon
   s->jobs.erase(it);
   delete j;
   return status;
+}
+
+int bie_server_batching(bie_server* s, int max_batch, int max_request_nodes, int64_t* batches) {
+  if (!s || max_batch < 0 || max_batch > 65535 || max_request_nodes < 0) return BIE_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (max_batch > 0) s->max_batch = max_batch;
+  if (max_request_nodes > 0) s->max_request_nodes = max_request_nodes;
+  if (batches) *batches = s->batches;
+  return BIE_OK;
 }
 
 int bie_server_stats(bie_server* s, int64_t* completed, size_t* inflight, size_t* peak) {

@@ -119,3 +119,67 @@ def test_bad_requests_fail_alone(requests_, alone):
     assert srv.wait(tb)[0] == bie.ERR_INVALID
     assert srv.wait(tb)[0] == bie.ERR_INVALID  # a ticket can be waited for once
     srv.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("cap_factor", [0, 3])
+def test_batching_matches_results_alone(requests_, alone, cap_factor):
+    # queued requests of one kind and options are solved together: the results
+    # agree with the solo ones to the solve tolerance, memory admission holds
+    needs = [bie.workspace_bytes(g["kind"], g["body_start"].size - 1, g["x"].size) for g in requests_]
+    cap = int(cap_factor * max(needs))
+    srv = bie.Server(0, workers=2, hbm_cap_bytes=cap)
+    assert srv.batching(8) == 0
+    outs, tickets = [], []
+    for i, g in enumerate(requests_):
+        out = np.full(_nout(g), np.nan)
+        geom = _host(g) if i % 2 == 0 else {k: torch.from_numpy(v).cuda() for k, v in _host(g).items()}
+        tickets.append(srv.submit(g["kind"], geom, _load(g), out, opts=bie.make_opts(precision=bie.MIXED_FF)))
+        outs.append(out)
+    for t, out, ref in zip(tickets, outs, alone):
+        rc, info, _ = srv.wait(t)
+        assert rc == bie.OK
+        assert info["rel_residual"] <= 1e-12
+        assert _rel(out, ref) <= 1e-10
+    batches = srv.batching()
+    st = srv.stats()
+    assert st["completed"] == len(requests_) and st["inflight_bytes"] == 0
+    if cap:
+        assert st["peak_inflight_bytes"] <= cap
+    srv.close()
+    print(f"cap {cap}: {batches} batched solves for {len(requests_)} requests")
+    assert batches >= 1
+
+
+def test_batching_bad_request_fails_alone(requests_, alone):
+    srv = bie.Server(0, workers=1)
+    srv.batching(16)
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    idx = [i for i, g in enumerate(requests_) if g["kind"] == 0][:5]
+    g0 = requests_[idx[0]]
+    bad = dict(_host(g0))
+    bs = bad["body_start"].copy()
+    bs = np.array([0, 3, bs[-1]], dtype=np.int32)  # a body of 3 nodes: invalid, found by the solve
+    bad["body_start"] = bs
+    # a long first request keeps the single worker busy while the rest queue
+    first = synth.star_grid(seed=5, n=128, rows=4, cols=4)
+    t_first = srv.submit(0, _host(first), synth.charges(16, np.random.default_rng(1)), np.empty(16), opts=opts)
+    outs, tickets = [], []
+    for k, i in enumerate(idx):
+        g = requests_[i]
+        out = np.empty(_nout(g))
+        tickets.append(srv.submit(0, _host(g), _load(g), out, opts=opts))
+        outs.append(out)
+        if k == 1:
+            tb = srv.submit(0, bad, np.zeros(2), np.empty(2), opts=opts)
+            assert tb > 0
+    assert srv.wait(t_first)[0] == bie.OK
+    for t, out, i in zip(tickets, outs, idx):
+        rc, _, _ = srv.wait(t)
+        assert rc == bie.OK and _rel(out, alone[i]) <= 1e-10
+    assert srv.wait(tb)[0] == bie.ERR_INVALID
+    assert srv.batching() >= 1  # the requests behind the first one were taken together
+    srv.close()
