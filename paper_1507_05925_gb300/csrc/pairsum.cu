@@ -44,9 +44,10 @@ struct SrcRange {
   bool straddle;
 };
 
+template <bool BATCH>
 __device__ __forceinline__ SrcRange src_range(const Geo& g, int tbase, int tend, int chunk) {
   SrcRange r;
-  if (!g.prange) {
+  if (!BATCH) {
     r.j0 = blockIdx.y * chunk;
     r.j1 = min(g.M, r.j0 + chunk);
     r.straddle = false;
@@ -87,22 +88,23 @@ __device__ __forceinline__ void zero_partials(int tbase, int tend, int M, double
 
 // Does source node b belong to target a's problem (batched solves)?
 __device__ __forceinline__ bool same_problem(const Geo& g, int a, int b) {
-  if (!g.prange || a >= g.M) return true;
+  if (a >= g.M) return true;
   const int2 r = g.prange[g.body_of[a]];
   return b >= r.x && b < r.y;
 }
 
 // End of the tile starting at source jt: at most `want`, cut at the end of
 // jt's problem (a tile must not mix problems).
+template <bool BATCH>
 __device__ __forceinline__ int tile_len(const Geo& g, int jt, int want) {
-  if (!g.prange) return want;
+  if (!BATCH) return want;
   return min(want, g.prange[g.body_of[jt]].y - jt);
 }
 
 // ------------------------------------------------------------------ FP64 ----
 constexpr int kB64 = 128, kT64 = 2, kTile64 = 128;
 
-template <int KIND>
+template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
@@ -111,11 +113,11 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
   const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB64 * kT64;
-  if (block_stopped(g, tbase, min(M, tbase + kB64 * kT64))) {
+  if (BATCH && block_stopped(g, tbase, min(M, tbase + kB64 * kT64))) {
     zero_partials<KIND>(tbase, min(M, tbase + kB64 * kT64), M, partial);
     return;
   }
-  const SrcRange sr = src_range(g, tbase, min(M, tbase + kB64 * kT64), chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, min(M, tbase + kB64 * kT64), chunk);
   const int j0 = sr.j0, j1 = sr.j1;
   double tx[kT64], ty[kT64], tnx[kT64], tny[kT64], ax[kT64], ay[kT64];
   int ta[kT64];
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
       for (int k = 0; k < kT64; ++k) {
         const double dx = tx[k] - px, dy = ty[k] - py;
         const double r2 = dx * dx + dy * dy;
-        const bool skip = ta[k] == b || (sr.straddle && !same_problem(g, ta[k], b));
+        const bool skip = ta[k] == b || (BATCH && sr.straddle && !same_problem(g, ta[k], b));
         if (KIND == 0) {
           const double s = skip ? 0.0 : q1 / r2;
           ax[k] += dx * s;
@@ -288,7 +290,7 @@ __device__ __forceinline__ float4 body_range_box(const float4* __restrict__ bbox
   return u;
 }
 
-template <int KIND>
+template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
@@ -301,11 +303,11 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
   const int tend = min(M, tbase + kB32 * kT32);
-  if (block_stopped(g, tbase, tend)) {
+  if (BATCH && block_stopped(g, tbase, tend)) {
     zero_partials<KIND>(tbase, tend, M, partial);
     return;
   }
-  const SrcRange sr = src_range(g, tbase, tend, chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, tend, chunk);
   const int j0 = sr.j0, j1 = sr.j1;
   // the target block's box, centre and half-diagonal
   const float4 tb = body_range_box(g.bbox, g.body_of[tbase], g.body_of[tend - 1]);
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
       else
         tile_near<KIND, false>(g.pf, sp, sq, nt, jt, a0, M, tnx, tny, ax, ay);
     }
-    if (g.prange) {
+    if (BATCH) {
       // batched solves: a tile counts only for its own problem's targets (a block
       // may straddle two problems)
 #pragma unroll
@@ -459,7 +461,7 @@ __device__ __forceinline__ void tile_ff(const float4* __restrict__ sa, const flo
   }
 }
 
-template <int KIND>
+template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double* __restrict__ sscale, int chunk,
                                                  double* __restrict__ partial, const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -470,12 +472,12 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
   const int M = g.M;
   const int tbase = blockIdx.x * kBF * kTF;
   const int tend = min(M, tbase + kBF * kTF);
-  if (block_stopped(g, tbase, tend)) {
+  if (BATCH && block_stopped(g, tbase, tend)) {
     zero_partials<KIND>(tbase, tend, M, partial);
     return;
   }
   const int a0 = tbase + threadIdx.x;
-  const SrcRange sr = src_range(g, tbase, tend, chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, tend, chunk);
   const int j0 = sr.j0, j1 = sr.j1;
   FFTarget t[kTF];
   // float-float sums over the tiles
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
     sxh[k] = sxl[k] = syh[k] = syl[k] = 0.f;
   }
   for (int jt = j0; jt < j1;) {
-    const int nt = tile_len(g, jt, min(kTileF, j1 - jt));
+    const int nt = tile_len<BATCH>(g, jt, min(kTileF, j1 - jt));
     __syncthreads();
     for (int l = threadIdx.x; l < nt; l += kBF) {
       const int b = jt + l;
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
       tile_ff<KIND, true>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
     else
       tile_ff<KIND, false>(sa, sb, sq, nt, jt, a0, t, axh, axl, ayh, ayl);
-    if (g.prange) {
+    if (BATCH) {
 #pragma unroll
       for (int k = 0; k < kTF; ++k)
         if (!same_problem(g, a0 + k * kBF, jt)) axh[k] = axl[k] = ayh[k] = ayl[k] = 0.f;
@@ -674,12 +676,12 @@ const DeviceShape& device_shape() {
   if (d.nsm == 0) {
     DeviceShape t;
     cudaDeviceGetAttribute(&t.nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][0], k_pair64<0>, kB64, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][1], k_pair64<1>, kB64, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][0], k_pair32<0>, kB32, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][1], k_pair32<1>, kB32, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][0], k_pair_ff<0>, kBF, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][1], k_pair_ff<1>, kBF, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][0], k_pair64<0, false>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[0][1], k_pair64<1, false>, kB64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][0], k_pair32<0, false>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[1][1], k_pair32<1, false>, kB32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][0], k_pair_ff<0, false>, kBF, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][1], k_pair_ff<1, false>, kBF, 0);
     cudaGetLastError();
     if (t.nsm <= 0) t.nsm = 152;
     for (auto& row : t.occ)
@@ -750,27 +752,42 @@ PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P,
   return p;
 }
 
-cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
-                     const double* sscale, double* partial, const int* stop, cudaStream_t s) {
+namespace {
+
+template <bool BATCH>
+void launch_pairs(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v, const double* sscale,
+                  double* partial, const int* stop, cudaStream_t s) {
   if (precision == 0) {
     dim3 grid((g.M + kB64 * kT64 - 1) / (kB64 * kT64), p.S);
     if (kind == 0)
-      k_pair64<0><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair64<0, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
     else
-      k_pair64<1><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair64<1, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
   } else if (precision == 1) {
     dim3 grid((g.M + kB32 * kT32 - 1) / (kB32 * kT32), p.S);
     if (kind == 0)
-      k_pair32<0><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair32<0, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
     else
-      k_pair32<1><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair32<1, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
   } else {
     dim3 grid((g.M + kBF * kTF - 1) / (kBF * kTF), p.S);
     if (kind == 0)
-      k_pair_ff<0><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair_ff<0, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
     else
-      k_pair_ff<1><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair_ff<1, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
   }
+}
+
+}  // namespace
+
+// Batched solves (g.prange set) run instances with the problem masks; a single
+// problem runs instances without any of that code.
+cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,
+                     const double* sscale, double* partial, const int* stop, cudaStream_t s) {
+  if (g.prange)
+    launch_pairs<true>(g, kind, precision, p, v, sscale, partial, stop, s);
+  else
+    launch_pairs<false>(g, kind, precision, p, v, sscale, partial, stop, s);
   note_launches(1);
   return cudaGetLastError();
 }
