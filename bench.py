@@ -60,6 +60,8 @@ def parse():
                     help="headline path: FP32 pair sums in refinement with an FP64 (mixed) or a "
                          "float-float (mixed_ff) residual")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the occupancy rule's pair-sum split counts (no bie_tune before the warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
@@ -586,6 +588,16 @@ def main():
             raise RuntimeError(f"solve failed: {rc} {ctx.last_error()} {info}")
         return info
 
+    # split counts of the headline shape tuned by timing (bie_tune), before the
+    # warm-up: the FP32 inner pair sums and the float-float residual
+    tuning = None
+    if not args.no_tune:
+        tuning = {}
+        for name, prec in (("laplace_fp32", bie.MIXED), ("laplace_ff", bie.MIXED_FF)):
+            rc, S, tms = bie.tune(ctx, gd, bie.LAPLACE, prec, stream=stream)
+            if rc != bie.OK:
+                raise RuntimeError(f"bie_tune failed: {rc} {ctx.last_error()}")
+            tuning[name] = {"splits": S, "ms_per_application": tms}
     # clocks are sampled from the warm-up through the timed region (a short
     # region alone would give nvidia-smi too few samples)
     cs = ClockSampler(local).__enter__()
@@ -691,6 +703,7 @@ def main():
                                     "laplace_fp64": pair_rate64},
         "solve_info": {args.precision: infos[-1], "other_mixed": infos_o[-1], "fp64": infos64[-1]},
         "kernel_share_of_step": kernel_share,
+        "pair_sum_tuning": tuning,
         "gpu_launches": launches,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "kernel": f"pair sum {dname}", "achieved": achieved, "peak": peak,

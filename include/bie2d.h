@@ -159,6 +159,21 @@ int elastance_solve(bie_ctx* ctx, const bie_geometry* geom, const double* q, dou
 int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, double* UW,
                    double* density, const bie_opts* opts, bie_info* info, void* stream);
 
+/* Autotuning of the pair-sum grid (no counterpart in the paper).  Times one
+ * application of the operator (pair sum + epilogue, CUDA events on the stream,
+ * the fastest of five after two warm-ups) on this geometry for source-split
+ * counts around the occupancy rule's, and keeps the fastest for this device
+ * and shape (M, kind, precision): later solves and operator applications of
+ * that shape, in any context of the process, use it (the occupancy rule is
+ * kept unless another count is faster by 2%).  A different split count changes
+ * the summation order, so results of that shape may change in rounding.
+ * splits and ms (nullable) receive the chosen count and its time.  Errors as
+ * for apply_operator. */
+int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
+             void* stream);
+/* Forget every tuned split count (back to the occupancy rule). */
+void bie_tune_clear(void);
+
 /* Batched solves (no counterpart in the paper: a throughput path for many small
  * problems).  count independent problems of one kind -- geoms[p] with loads[p]
  * (q [N_p] or FT [3 N_p]) into outs[p] (phi [N_p] or UW [3 N_p]), host or device

@@ -120,6 +120,11 @@ def load():
     lib.bie_server_batching.restype = i32
     lib.bie_server_destroy.argtypes = [vp]
     lib.bie_server_destroy.restype = None
+    lib.bie_tune.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, ctypes.POINTER(i32),
+                             ctypes.POINTER(ctypes.c_double), vp]
+    lib.bie_tune.restype = i32
+    lib.bie_tune_clear.argtypes = []
+    lib.bie_tune_clear.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
     _ = dbl
@@ -271,6 +276,23 @@ def mobility_solve_batch(ctx: Context, geoms, FTs, UWs, opts: BieOpts | None = N
     """mobility_solve_batch of include/bie2d.h; returns (status of the batch,
     per-problem info dicts, per-problem statuses)."""
     return _solve_batch(ctx.lib.mobility_solve_batch, ctx, geoms, FTs, UWs, opts, stream)
+
+
+def tune(ctx: Context, geom, kind: int, precision: int, stream=None):
+    """bie_tune of include/bie2d.h: time the pair-sum grid on this geometry and keep
+    the fastest split count for its shape; returns (status, splits, ms)."""
+    g, keep = make_geometry(geom)
+    S = ctypes.c_int32()
+    ms = ctypes.c_double()
+    rc = ctx.lib.bie_tune(ctx.handle, ctypes.byref(g), kind, precision, ctypes.byref(S), ctypes.byref(ms),
+                          _stream_ptr(stream))
+    del keep
+    return rc, int(S.value), float(ms.value)
+
+
+def tune_clear() -> None:
+    """bie_tune_clear: forget every tuned split count."""
+    load().bie_tune_clear()
 
 
 def apply_operator(ctx: Context, geom, kind: int, precision: int, inp, out, stream=None) -> int:

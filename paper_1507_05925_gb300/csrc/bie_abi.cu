@@ -1282,6 +1282,83 @@ int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, con
   return solve_common(ctx, nullptr, 1, nullptr, nullptr, nullptr, opts, nullptr, (cudaStream_t)stream, &b);
 }
 
+int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
+             void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> bs;
+  int rc = validate(ctx, geom, bs);
+  if (rc) return rc;
+  if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
+  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED && precision != BIE_PREC_MIXED_FF)
+    return fail(ctx, BIE_ERR_INVALID, "bad precision");
+  DeviceGuard dg(ctx->device);
+  const int N = geom->n_bodies, M = bs[N];
+  Work w;
+  Arena sz{nullptr};
+  carve(sz, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = ensure_ws(ctx, sz.off, s))) return rc;
+  Arena ar{ctx->ws};
+  carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
+  if ((rc = setup(ctx, geom, bs, w, s))) return rc;
+  // candidates around the occupancy rule's split count
+  const int S0 = occupancy_plan(M, kind, precision).S;
+  std::vector<int> cand;
+  for (int c : {S0, S0 / 2, (2 * S0) / 3, (3 * S0) / 2, 2 * S0, 3 * S0, 4 * S0, 6 * S0, 1}) {
+    const int S = plan_with_splits(M, std::max(1, c)).S;
+    if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
+  }
+  int smax = 1;
+  for (int S : cand) smax = std::max(smax, S);
+  double* partial = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&partial), (size_t)smax * w.n * sizeof(double), s));
+  CK(fill0(w.io_in, w.n, s));  // the cost of a pair sum does not depend on the values
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = S0;
+  double best_ms = 0.0, s0_ms = 0.0;
+  for (int S : cand) {
+    const PairPlan p = plan_with_splits(M, S);
+    auto apply = [&]() -> cudaError_t {
+      cudaError_t e = pair_sum(w.g, kind, precision, p, vec(w.io_in), w.g.w, partial, nullptr, s);
+      if (e != cudaSuccess) return e;
+      return epilogue(w.g, kind, p, vec(w.io_in), partial, 0, 1, 1.0, vec(w.io_out), nullptr, s);
+    };
+    for (int it = 0; it < 2; ++it) CK(apply());
+    // the fastest of five single applications
+    double t_min = 1e300;
+    for (int it = 0; it < 5; ++it) {
+      CK(cudaEventRecord(e0, s));
+      CK(apply());
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      t_min = std::min(t_min, (double)t);
+    }
+    if (S == S0) s0_ms = t_min;
+    if (best_ms == 0.0 || t_min < best_ms) {
+      best_ms = t_min;
+      best = S;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaFreeAsync(partial, s));
+  CK(cudaStreamSynchronize(s));
+  // keep the occupancy rule unless another count is clearly faster (2%)
+  if (best != S0 && best_ms > 0.98 * s0_ms) {
+    best = S0;
+    best_ms = s0_ms;
+  }
+  set_tuned_splits(M, kind, precision, best);
+  if (splits) *splits = best;
+  if (ms) *ms = best_ms;
+  return BIE_OK;
+}
+
+void bie_tune_clear(void) { clear_tuned_splits(); }
+
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, const double* in,
                    double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -162,7 +162,13 @@ struct PairPlan {
   int S;      // source splits
   int chunk;  // sources per split
 };
+// the tuned split count of this shape (bie_tune) if any, else occupancy_plan:
+// one wave of blocks (target blocks x splits) over every SM
 PairPlan plan_pairs(int M, int kind, int precision);
+PairPlan occupancy_plan(int M, int kind, int precision);
+PairPlan plan_with_splits(int M, int S);
+void set_tuned_splits(int M, int kind, int precision, int S);  // S <= 0: forget
+void clear_tuned_splits();
 // batched solves (host arrays: body_start [N+1], first body of each problem [P+1])
 PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P, int kind, int precision);
 cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, VecRef v,

@@ -21,6 +21,8 @@
 // TwoSum-compensated FP32 accumulators.  The per-pair arithmetic (FP32 near
 // pairs and float-float pairs) is shared with the FMM near field.
 #include <algorithm>
+#include <array>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -697,7 +699,54 @@ const DeviceShape& device_shape() {
 // Choose the source split so that one wave fills every SM with as many
 // blocks as can be resident: blocks = target blocks x splits ~ SMs x occupancy.
 // Splits need not be tile-aligned (the kernels handle a short last tile).
+namespace {
+
+// Split counts chosen by timing (bie_tune), per device and shape (M, kind,
+// precision); plan_pairs takes them before the occupancy rule.
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, int> g_tuned;
+
+std::array<int, 4> tune_key(int M, int kind, int precision) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return {dev, M, kind, precision};
+}
+
+}  // namespace
+
+void set_tuned_splits(int M, int kind, int precision, int S) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (S > 0)
+    g_tuned[tune_key(M, kind, precision)] = S;
+  else
+    g_tuned.erase(tune_key(M, kind, precision));
+}
+
+void clear_tuned_splits() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
+}
+
+PairPlan plan_with_splits(int M, int S) {
+  const long long cap = std::max(1, (M + 63) / 64);  // chunks of at least 64 sources
+  long long s = std::min<long long>(std::max(S, 1), cap);
+  const long long chunk = (M + s - 1) / s;
+  PairPlan p;
+  p.chunk = (int)chunk;
+  p.S = (int)((M + chunk - 1) / chunk);
+  return p;
+}
+
 PairPlan plan_pairs(int M, int kind, int precision) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(M, kind, precision));
+    if (it != g_tuned.end()) return plan_with_splits(M, it->second);
+  }
+  return occupancy_plan(M, kind, precision);
+}
+
+PairPlan occupancy_plan(int M, int kind, int precision) {
   const DeviceShape& d = device_shape();
   const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
   const long long bx = (M + per_block - 1) / per_block;
