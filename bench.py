@@ -45,7 +45,7 @@ FLOPS_PER_PAIR = {"laplace": 10.0, "stokes": 18.0}
 # capture of the current kernels (profiles/k_pair32_laplace_stars100_M25600.md,
 # profiles/k_pair_ff_laplace_stars100_M25600.md); a kernel changed since its
 # capture must be taken out of this table
-DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 1.288e6, "laplace_ff": 1.462e6}
+DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 1.291e6, "laplace_ff": 1.462e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -60,6 +60,8 @@ def parse():
                     help="headline path: FP32 pair sums in refinement with an FP64 (mixed) or a "
                          "float-float (mixed_ff) residual")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--splits", type=int, default=0,
+                    help="--kernel: install this pair-sum split count instead of searching (0 = search)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the occupancy rule's pair-sum split counts (no bie_tune before the warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -494,6 +496,12 @@ def run_kernel(args, local):
     v = torch.randn(n, dtype=torch.float64, device=dev)
     out = torch.empty_like(v)
     ctx = bie.Context(local)
+    splits = None
+    if not fmm and not args.no_tune:
+        # the split count the solves use after tuning (--splits S: install S
+        # untimed, so that no tuning launches come before the timed ones)
+        rc, splits, _ = bie.tune(ctx, gd, kind, prec, splits=args.splits)
+        assert rc == bie.OK, ctx.last_error()
 
     def apply():
         if fmm:
@@ -526,7 +534,7 @@ def run_kernel(args, local):
     prof = ctx.profile(False)[key]
     ms = prof["ms"] / max(prof["launches"], 1)
     flops = FLOPS_PER_PAIR[kind_name] * prof["pairs"] / max(prof["launches"], 1)
-    print(json.dumps({"kernel": args.kernel, "M": g["x"].size, "launches": prof["launches"],
+    print(json.dumps({"kernel": args.kernel, "M": g["x"].size, "launches": prof["launches"], "splits": splits,
                       "ms_per_launch": ms, "pairs_per_s": prof["pairs"] / (prof["ms"] / 1e3),
                       "tflops": flops / (ms / 1e3) / 1e12}))
     ctx.close()

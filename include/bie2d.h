@@ -167,8 +167,10 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
  * that shape, in any context of the process, use it (the occupancy rule is
  * kept unless another count is faster by 2%).  A different split count changes
  * the summation order, so results of that shape may change in rounding.
- * splits and ms (nullable) receive the chosen count and its time.  Errors as
- * for apply_operator. */
+ * splits (nullable): on input 0 to search, or a count to install without
+ * timing (rounded to the counts the source chunking allows); on output the
+ * count kept.  ms (nullable) receives its time (0 when installed untimed).
+ * Errors as for apply_operator. */
 int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
              void* stream);
 /* Forget every tuned split count (back to the occupancy rule). */

@@ -278,11 +278,12 @@ def mobility_solve_batch(ctx: Context, geoms, FTs, UWs, opts: BieOpts | None = N
     return _solve_batch(ctx.lib.mobility_solve_batch, ctx, geoms, FTs, UWs, opts, stream)
 
 
-def tune(ctx: Context, geom, kind: int, precision: int, stream=None):
+def tune(ctx: Context, geom, kind: int, precision: int, splits: int = 0, stream=None):
     """bie_tune of include/bie2d.h: time the pair-sum grid on this geometry and keep
-    the fastest split count for its shape; returns (status, splits, ms)."""
+    the fastest split count for its shape (splits > 0: install that count
+    untimed); returns (status, splits, ms)."""
     g, keep = make_geometry(geom)
-    S = ctypes.c_int32()
+    S = ctypes.c_int32(splits)
     ms = ctypes.c_double()
     rc = ctx.lib.bie_tune(ctx.handle, ctypes.byref(g), kind, precision, ctypes.byref(S), ctypes.byref(ms),
                           _stream_ptr(stream))

@@ -1293,6 +1293,13 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
     return fail(ctx, BIE_ERR_INVALID, "bad precision");
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
+  if (splits && *splits > 0) {  // install the given count, no timing
+    const int S = plan_with_splits(M, *splits).S;
+    set_tuned_splits(M, kind, precision, S);
+    *splits = S;
+    if (ms) *ms = 0.0;
+    return BIE_OK;
+  }
   Work w;
   Arena sz{nullptr};
   carve(sz, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);

@@ -59,6 +59,17 @@ def test_tuned_solve_matches_oracle(ctx):
     bie.tune_clear()
 
 
+def test_install_given_split_count(ctx):
+    g = ragged4()
+    v = np.random.default_rng(13).standard_normal(g["x"].size)
+    rc, S, ms = bie.tune(ctx, g, 0, bie.MIXED, splits=5)
+    assert rc == bie.OK and S == 5 and ms == 0.0
+    out = np.empty_like(v)
+    assert bie.apply_operator(ctx, g, 0, bie.MIXED, v, out) == bie.OK
+    assert rel_max(out, laplace.apply(geometry.nodes(g), v)) <= TOL32[0]
+    bie.tune_clear()
+
+
 def test_tune_rejects_bad_arguments(ctx):
     g = ragged4()
     assert bie.tune(ctx, g, 2, bie.MIXED)[0] == bie.ERR_INVALID
