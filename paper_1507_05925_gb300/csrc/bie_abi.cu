@@ -361,16 +361,44 @@ struct BatchIn {
 int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, const std::vector<int>& pb,
                 bool ipt, Work& w, cudaStream_t s) {
   const int N = (int)bs.size() - 1, P = b.P, c = w.kind + 1;
+  const long long M = bs[N];
+  const int per = w.kind == 0 ? 1 : 3;  // load entries per body
   CK(cudaMemcpyAsync(w.body_start, bs.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   w.g.body_start = w.body_start;
+  // geometry arrays, interior points and loads: device sources gathered by one
+  // kernel, host sources packed and copied once per array (before the gather,
+  // which then overwrites the device-sourced parts)
+  double* dst[6] = {w.x, w.y, w.dx, w.dy, w.ddx, w.ddy};
+  const long long ipt_off = 6 * M, load_off = 6 * M + 2LL * N;
+  std::vector<double> pack;
+  bool from_host[8] = {false, false, false, false, false, false, false, false};
+  std::vector<CopySeg> segs;
+  auto take = [&](int slot, const double* src, double* to, long long count, long long pack_at) {
+    if (count <= 0) return;
+    if (is_device_ptr(src)) {
+      segs.push_back(CopySeg{src, to, 2 * count});
+    } else {
+      if (pack.empty()) pack.resize(load_off + (size_t)per * N);
+      memcpy(pack.data() + pack_at, src, count * sizeof(double));
+      from_host[slot] = true;
+    }
+  };
   for (int p = 0; p < P; ++p) {
     const bie_geometry& g = b.geoms[p];
-    const size_t off = bs[pb[p]], Mp = bs[pb[p + 1]] - bs[pb[p]], Np = pb[p + 1] - pb[p];
+    const long long off = bs[pb[p]], Mp = bs[pb[p + 1]] - bs[pb[p]], Np = pb[p + 1] - pb[p];
     const double* src[6] = {g.x, g.y, g.dx, g.dy, g.ddx, g.ddy};
-    double* dst[6] = {w.x, w.y, w.dx, w.dy, w.ddx, w.ddy};
-    for (int k = 0; k < 6; ++k) CK(cudaMemcpyAsync(dst[k] + off, src[k], Mp * sizeof(double), cudaMemcpyDefault, s));
-    if (ipt) CK(cudaMemcpyAsync(w.ipt + 2 * pb[p], g.interior_pt, 2 * Np * sizeof(double), cudaMemcpyDefault, s));
+    for (int k = 0; k < 6; ++k) take(k, src[k], dst[k] + off, Mp, k * M + off);
+    if (ipt) take(6, g.interior_pt, w.ipt + 2 * pb[p], 2 * Np, ipt_off + 2 * pb[p]);
+    take(7, b.loads[p], w.load + (long long)per * pb[p], per * Np, load_off + (long long)per * pb[p]);
   }
+  for (int k = 0; k < 6; ++k)
+    if (from_host[k]) CK(cudaMemcpyAsync(dst[k], pack.data() + k * M, M * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (from_host[6])
+    CK(cudaMemcpyAsync(w.ipt, pack.data() + ipt_off, 2 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (from_host[7])
+    CK(cudaMemcpyAsync(w.load, pack.data() + load_off, (size_t)per * N * sizeof(double), cudaMemcpyHostToDevice,
+                       s));
+  CK(gather_segments(segs, s));
   std::vector<int2> pr(N);
   std::vector<long long> pn(P + 1);
   for (int p = 0; p < P; ++p) {
@@ -428,13 +456,69 @@ int batch_setup(bie_ctx* ctx, const BatchIn& b, const std::vector<int>& bs, cons
     w.seg.ps = w.ps;
   }
   CK(stage_geometry(w.g, w.x, w.y, w.dx, w.dy, w.ddx, w.ddy, ipt ? w.ipt : nullptr, s));
-  // loads, one after another
-  for (int p = 0, off = 0; p < P; ++p) {
-    const int nl = (pb[p + 1] - pb[p]) * (w.kind == 0 ? 1 : 3);
-    CK(cudaMemcpyAsync(w.load + off, b.loads[p], nl * sizeof(double), cudaMemcpyDefault, s));
-    off += nl;
-  }
   CK(cudaStreamSynchronize(s));  // the host tables above must outlive their copies
+  return BIE_OK;
+}
+
+// Batched solves: every problem's argument checks, and the concatenated
+// body_start (body offsets) and first body of each problem.  Device body_start
+// arrays are gathered by one kernel and read back once.
+int validate_batch(bie_ctx* ctx, const BatchIn& b, std::vector<int>& bs, std::vector<int>& pb, bool& has_ipt,
+                   cudaStream_t s) {
+  const int P = b.P;
+  std::vector<long long> roff(P + 1, 0);
+  for (int p = 0; p < P; ++p) {
+    const bie_geometry& g = b.geoms[p];
+    const std::string who = "problem " + std::to_string(p) + ": ";
+    if (g.n_bodies < 1) return fail(ctx, BIE_ERR_INVALID, who + "n_bodies must be >= 1");
+    if (!g.body_start || !g.x || !g.y || !g.dx || !g.dy || !g.ddx || !g.ddy)
+      return fail(ctx, BIE_ERR_INVALID, who + "a geometry array is NULL");
+    if (!b.loads[p] || !b.outs[p]) return fail(ctx, BIE_ERR_INVALID, who + "a load or output is NULL");
+    if (p > 0 && (g.interior_pt != nullptr) != has_ipt)
+      return fail(ctx, BIE_ERR_INVALID, "batch: interior points for all problems or for none");
+    has_ipt = g.interior_pt != nullptr;
+    roff[p + 1] = roff[p] + g.n_bodies + 1;
+    if (roff[p + 1] > 0x3fffffffLL) return fail(ctx, BIE_ERR_INVALID, "batch: too many bodies");
+  }
+  std::vector<int> raw(roff[P]);
+  std::vector<CopySeg> segs;
+  std::vector<int> on_device;
+  for (int p = 0; p < P; ++p) {
+    const bie_geometry& g = b.geoms[p];
+    if (is_device_ptr(g.body_start)) {
+      segs.push_back(CopySeg{g.body_start, nullptr, g.n_bodies + 1});
+      on_device.push_back(p);
+    } else {
+      memcpy(raw.data() + roff[p], g.body_start, (g.n_bodies + 1) * sizeof(int));
+    }
+  }
+  if (!segs.empty()) {
+    DeviceGuard dg(ctx->device);
+    int* d = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d), roff[P] * sizeof(int), s));
+    for (size_t i = 0; i < segs.size(); ++i) segs[i].dst = d + roff[on_device[i]];
+    CK(gather_segments(segs, s));
+    std::vector<int> tmp(roff[P]);
+    CK(cudaMemcpyAsync(tmp.data(), d, roff[P] * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(d, s));
+    CK(cudaStreamSynchronize(s));
+    for (int p : on_device) std::copy(tmp.begin() + roff[p], tmp.begin() + roff[p + 1], raw.begin() + roff[p]);
+  }
+  bs.assign(1, 0);
+  pb.assign(1, 0);
+  for (int p = 0; p < P; ++p) {
+    const int* q = raw.data() + roff[p];
+    const int Np = b.geoms[p].n_bodies;
+    const std::string who = "problem " + std::to_string(p) + ": ";
+    if (q[0] != 0) return fail(ctx, BIE_ERR_INVALID, who + "body_start[0] must be 0");
+    for (int i = 0; i < Np; ++i)
+      if (q[i + 1] - q[i] < 8)
+        return fail(ctx, BIE_ERR_INVALID, who + "body " + std::to_string(i) + " has fewer than 8 nodes");
+    const int off = bs.back();
+    if ((long long)off + q[Np] > 0x3fffffffLL) return fail(ctx, BIE_ERR_INVALID, "batch: too many nodes");
+    for (int i = 1; i <= Np; ++i) bs.push_back(off + q[i]);
+    pb.push_back(pb.back() + Np);
+  }
   return BIE_OK;
 }
 
@@ -817,20 +901,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     if (batch->P < 1 || batch->P > 65535 || !batch->geoms || !batch->loads || !batch->outs)
       return fail(ctx, BIE_ERR_INVALID, "batch: count outside 1..65535 or a NULL array");
     if (density) return fail(ctx, BIE_ERR_INVALID, "batch: no density output");
-    bs.push_back(0);
-    pb.push_back(0);
-    for (int p = 0; p < batch->P; ++p) {
-      std::vector<int> b;
-      if ((rc = validate(ctx, &batch->geoms[p], b))) return rc;
-      if (!batch->loads[p] || !batch->outs[p]) return fail(ctx, BIE_ERR_INVALID, "batch: a load or output is NULL");
-      if (p > 0 && (batch->geoms[p].interior_pt != nullptr) != has_ipt)
-        return fail(ctx, BIE_ERR_INVALID, "batch: interior points for all problems or for none");
-      has_ipt = batch->geoms[p].interior_pt != nullptr;
-      const int off = bs.back(), Np = batch->geoms[p].n_bodies;
-      if ((long long)off + b[Np] > 0x3fffffffLL) return fail(ctx, BIE_ERR_INVALID, "batch: too many nodes");
-      for (int i = 1; i <= Np; ++i) bs.push_back(off + b[i]);
-      pb.push_back(pb.back() + Np);
-    }
+    if ((rc = validate_batch(ctx, *batch, bs, pb, has_ipt, s))) return rc;
   } else {
     if ((rc = validate(ctx, geom, bs))) return rc;
     if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
@@ -1054,10 +1125,24 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     if ((rc = copy_out(ctx, density, w.ytmp, n, s))) return rc;
   }
   if (batch) {
-    for (int p = 0, off = 0; p < P; ++p) {
-      const int nl = (pb[p + 1] - pb[p]) * (kind == 0 ? 1 : 3);
-      if ((rc = copy_out(ctx, batch->outs[p], w.outv + off, nl, s))) return rc;
-      off += nl;
+    // device outputs scattered by one kernel, host outputs from one read-back
+    std::vector<CopySeg> segs;
+    std::vector<int> on_host;
+    const int per = kind == 0 ? 1 : 3;
+    for (int p = 0; p < P; ++p) {
+      const long long nl = (long long)(pb[p + 1] - pb[p]) * per;
+      if (is_device_ptr(batch->outs[p]))
+        segs.push_back(CopySeg{w.outv + (long long)pb[p] * per, batch->outs[p], 2 * nl});
+      else
+        on_host.push_back(p);
+    }
+    CK(gather_segments(segs, s));
+    if (!on_host.empty()) {
+      std::vector<double> h(nload);
+      CK(cudaMemcpyAsync(h.data(), w.outv, nload * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int p : on_host)
+        memcpy(batch->outs[p], h.data() + (long long)pb[p] * per, (size_t)(pb[p + 1] - pb[p]) * per * sizeof(double));
     }
   } else if ((rc = copy_out(ctx, out, w.outv, nload, s))) {
     return rc;

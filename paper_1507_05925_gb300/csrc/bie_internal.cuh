@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bie2d.h"
 
@@ -211,6 +212,15 @@ size_t workspace_bytes_batch(int kind, const int* bs, int n_bodies, const int* p
 // of the problems) and the inverse scaling of the solution.
 cudaError_t batch_normalize(int nprob, const long long* pnode, double* f, double* scale, cudaStream_t s);
 cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale, double* x, cudaStream_t s);
+// Many small device-to-device copies in one launch (batched solves): segment
+// i copies words 4-byte words from src to dst; the table is uploaded to a
+// stream-ordered temporary buffer.
+struct CopySeg {
+  const void* src;
+  void* dst;
+  long long words;
+};
+cudaError_t gather_segments(const std::vector<CopySeg>& segs, cudaStream_t s);
 // norms[p] = ||x_p|| per problem; x_p = 0 where norms[p] <= thr
 cudaError_t seg_norms(int nprob, const long long* pnode, const double* x, double* norms, cudaStream_t s);
 cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norms, double thr, double* x,

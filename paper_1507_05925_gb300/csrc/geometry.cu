@@ -248,6 +248,15 @@ __global__ void __launch_bounds__(kB) k_batch_unscale(double* __restrict__ x, co
   for (long long e = pnode[p] + threadIdx.x; e < pnode[p + 1]; e += kB) x[e] *= sc;
 }
 
+__global__ void __launch_bounds__(kB) k_gather(const CopySeg* __restrict__ segs, int nseg) {
+  for (int i = blockIdx.x; i < nseg; i += gridDim.x) {
+    const CopySeg sg = segs[i];
+    const unsigned* __restrict__ src = static_cast<const unsigned*>(sg.src);
+    unsigned* __restrict__ dst = static_cast<unsigned*>(sg.dst);
+    for (long long k = threadIdx.x; k < sg.words; k += kB) dst[k] = src[k];
+  }
+}
+
 // Batched solves: ||x_p|| of every problem's entries into norms[p].
 __global__ void __launch_bounds__(kB) k_seg_norms(const double* __restrict__ x, const long long* __restrict__ pnode,
                                                   double* __restrict__ norms) {
@@ -469,6 +478,23 @@ cudaError_t batch_unscale(int nprob, const long long* pnode, const double* scale
   k_batch_unscale<<<nprob, kB, 0, s>>>(x, pnode, scale);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t gather_segments(const std::vector<CopySeg>& segs, cudaStream_t s) {
+  if (segs.empty()) return cudaSuccess;
+  CopySeg* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), segs.size() * sizeof(CopySeg), s);
+  if (e != cudaSuccess) return e;
+  // a pageable source: the call returns once the table is staged
+  e = cudaMemcpyAsync(d, segs.data(), segs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    const int n = (int)segs.size();
+    k_gather<<<n < 1024 ? n : 1024, kB, 0, s>>>(d, n);
+    note_launches(1);
+    e = cudaGetLastError();
+  }
+  const cudaError_t f = cudaFreeAsync(d, s);
+  return e != cudaSuccess ? e : f;
 }
 
 cudaError_t seg_norms(int nprob, const long long* pnode, const double* x, double* norms, cudaStream_t s) {

@@ -177,3 +177,31 @@ def test_batch_iterations_follow_the_slowest_problem(ctx, kind):
               f"rel_residual {max(i['rel_residual'] for i in infos):.2e}")
         assert info["iters"] <= max(solo_iters) + 2
         assert max(i["rel_residual"] for i in infos) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_mixed_host_and_device_arrays(ctx, kind):
+    # staging gathers device arrays in one launch and packs host arrays: any mix
+    # of the two, also within one problem, gives the same results
+    probs = _problems(kind, 120 + kind, 6)
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    ref = _solve_batch(ctx, kind, probs, opts)[3]
+    geoms, loads, outs = [], [], []
+    for i, (g, load) in enumerate(probs):
+        h = _host(g)
+        if i % 3 == 0:
+            gm = h
+        elif i % 3 == 1:
+            gm = {k: torch.from_numpy(v).cuda() for k, v in h.items()}
+        else:  # body_start and positions on the device, derivatives on the host
+            gm = {k: (torch.from_numpy(v).cuda() if k in ("body_start", "x", "y") else v) for k, v in h.items()}
+        geoms.append(gm)
+        loads.append(load if i % 2 == 0 else torch.from_numpy(load).cuda())
+        outs.append(np.empty(load.size) if i % 2 == 1 else torch.empty(load.size, dtype=torch.float64, device="cuda"))
+    fn = bie.elastance_solve_batch if kind == 0 else bie.mobility_solve_batch
+    rc, _, status = fn(ctx, geoms, loads, outs, opts=opts)
+    torch.cuda.synchronize()
+    assert rc == bie.OK and status == [bie.OK] * len(probs)
+    for out, r in zip(outs, ref):
+        o = out.cpu().numpy() if isinstance(out, torch.Tensor) else out
+        assert np.array_equal(o, r)  # staging does not change the arithmetic
