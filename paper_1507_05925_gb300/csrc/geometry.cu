@@ -186,41 +186,64 @@ __global__ void k_scale_by(int M, int comps, const double* __restrict__ in, cons
     out[k] = in[k] * fac[k / comps];
 }
 
-// Net load |sum_i q_i| (or |sum_i F_i|) and max |load|; in a batch (pbody =
-// body offsets of the P problems) the largest net load of any problem, and
-// (per != nullptr) each problem's net load and largest |load| in per[2p], per[2p+1].
-__global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* __restrict__ load,
-                                                  const int* __restrict__ pbody, int P, double* __restrict__ out,
-                                                  double* __restrict__ per) {
-  __shared__ double sh[kB / 32];
-  double gmax = 0, worst = 0;
-  for (int p = 0; p < P; ++p) {
-    const int i0 = pbody ? pbody[p] : 0, i1 = pbody ? pbody[p + 1] : N;
-    double s0 = 0, s1 = 0, nmx = 0;  // nmx: -max |load| over the problem
-    for (int i = i0 + threadIdx.x; i < i1; i += kB) {
-      if (kind == 0) {
-        s0 += load[i];
-        nmx = fmin(nmx, -fabs(load[i]));
-      } else {
-        s0 += load[3 * i];
-        s1 += load[3 * i + 1];
-        nmx = fmin(nmx, -fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
-      }
-    }
-    s0 = block_sum<kB>(s0, sh);
-    s1 = block_sum<kB>(s1, sh);
-    nmx = block_min<kB>(nmx, sh);
-    const double net = sqrt(s0 * s0 + s1 * s1);
-    worst = fmax(worst, net);
-    gmax = fmax(gmax, -nmx);
-    if (per && threadIdx.x == 0) {
-      per[2 * p] = net;
-      per[2 * p + 1] = -nmx;
+// Net load |sum_i q_i| (or |sum_i F_i|) and max |load| over bodies [i0, i1)
+// (block-wide; valid in every thread).
+__device__ __forceinline__ double2 net_and_max(int kind, const double* __restrict__ load, int i0, int i1,
+                                               double* sh) {
+  double s0 = 0, s1 = 0, nmx = 0;  // nmx: -max |load|
+  for (int i = i0 + threadIdx.x; i < i1; i += kB) {
+    if (kind == 0) {
+      s0 += load[i];
+      nmx = fmin(nmx, -fabs(load[i]));
+    } else {
+      s0 += load[3 * i];
+      s1 += load[3 * i + 1];
+      nmx = fmin(nmx, -fmax(fabs(load[3 * i]), fmax(fabs(load[3 * i + 1]), fabs(load[3 * i + 2]))));
     }
   }
+  s0 = block_sum<kB>(s0, sh);
+  s1 = block_sum<kB>(s1, sh);
+  nmx = block_min<kB>(nmx, sh);
+  return make_double2(sqrt(s0 * s0 + s1 * s1), -nmx);
+}
+
+// One problem: out = (net load, max |load|).
+__global__ void __launch_bounds__(kB) k_net_load(int N, int kind, const double* __restrict__ load,
+                                                  double* __restrict__ out) {
+  __shared__ double sh[kB / 32];
+  const double2 r = net_and_max(kind, load, 0, N, sh);
   if (threadIdx.x == 0) {
-    out[0] = worst;
-    out[1] = gmax;
+    out[0] = r.x;
+    out[1] = r.y;
+  }
+}
+
+// Batched solves, one block per problem p (bodies pbody[p]..pbody[p+1]):
+// per[2p] = its net load, per[2p+1] = its max |load|.
+__global__ void __launch_bounds__(kB) k_net_load_batch(int kind, const double* __restrict__ load,
+                                                        const int* __restrict__ pbody, double* __restrict__ per) {
+  __shared__ double sh[kB / 32];
+  const int p = blockIdx.x;
+  const double2 r = net_and_max(kind, load, pbody[p], pbody[p + 1], sh);
+  if (threadIdx.x == 0) {
+    per[2 * p] = r.x;
+    per[2 * p + 1] = r.y;
+  }
+}
+
+// out = (largest net load, largest |load|) over the P problems.
+__global__ void __launch_bounds__(kB) k_net_load_max(const double* __restrict__ per, int P, double* __restrict__ out) {
+  __shared__ double sh[kB / 32];
+  double a = 0.0, b = 0.0;
+  for (int p = threadIdx.x; p < P; p += kB) {
+    a = fmax(a, per[2 * p]);
+    b = fmax(b, per[2 * p + 1]);
+  }
+  a = -block_min<kB>(-a, sh);
+  b = -block_min<kB>(-b, sh);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
   }
 }
 
@@ -436,8 +459,14 @@ cudaError_t finalize_output(const Geo& g, int kind, const double* v, const doubl
   double* nl = cbody + g.N;
   k_out_final<<<g.N, kB, 0, s>>>(g, kind, v, load, partial, P, out, cbody);
   note_launches(1);
-  k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, g.pbody, g.pbody ? g.nprob : 1, nl, g.pnet);
-  note_launches(1);
+  if (g.pbody && g.pnet) {
+    k_net_load_batch<<<g.nprob, kB, 0, s>>>(kind, load, g.pbody, g.pnet);
+    k_net_load_max<<<1, kB, 0, s>>>(g.pnet, g.nprob, nl);
+    note_launches(2);
+  } else {
+    k_net_load<<<1, kB, 0, s>>>(g.N, kind, load, nl);
+    note_launches(1);
+  }
   k_max_reduce<<<1, kB, 0, s>>>(cbody, g.N, nl, cres);
   note_launches(1);
   return cudaGetLastError();
@@ -511,7 +540,7 @@ cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norm
 }
 
 cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s) {
-  k_net_load<<<1, kB, 0, s>>>(N, kind, load, nullptr, 1, out, nullptr);
+  k_net_load<<<1, kB, 0, s>>>(N, kind, load, out);
   note_launches(1);
   return cudaGetLastError();
 }
