@@ -74,3 +74,34 @@ def test_tune_rejects_bad_arguments(ctx):
     g = ragged4()
     assert bie.tune(ctx, g, 2, bie.MIXED)[0] == bie.ERR_INVALID
     assert bie.tune(ctx, g, 0, 7)[0] == bie.ERR_INVALID
+
+
+def test_full_size_in_the_tuned_launch_configuration(ctx):
+    # bench.py tunes the 100-star workload before timing it: the operator rows
+    # and the solve in that launch configuration, against the oracle
+    from test_gpu_parity import TOLFF, _check_full_size, _sampled_rows, to_dev
+    g = synth.WORKLOADS["stars100_M25600"]()
+    geo = geometry.nodes(g)
+    gd = to_dev(g)
+    splits = {prec: bie.tune(ctx, gd, 0, prec)[1] for prec in (bie.MIXED, bie.MIXED_FF)}
+    print(f"tuned splits {splits}")
+    M, N = geo["M"], geo["N"]
+    v = np.random.default_rng(14).standard_normal(M)
+    rows = np.unique(np.concatenate([np.random.default_rng(15).choice(M, 48, replace=False), [0, M - 1]]))
+    ref = _sampled_rows(geo, 0, v, rows)
+    for prec, tol in ((bie.MIXED, TOL32[0]), (bie.MIXED_FF, TOLFF)):
+        out = torch.empty(M, dtype=torch.float64, device="cuda")
+        assert bie.apply_operator(ctx, gd, 0, prec, torch.from_numpy(v).cuda(), out) == bie.OK
+        assert rel_max(out.cpu().numpy()[rows], ref) <= tol
+    q = torch.from_numpy(g["q"]).cuda()
+    res = {}
+    for prec in (bie.MIXED_FF, bie.MIXED, bie.FP64):
+        phi = torch.empty(N, dtype=torch.float64, device="cuda")
+        dens = torch.empty(M, dtype=torch.float64, device="cuda")
+        rc, info = bie.elastance_solve(ctx, gd, q, phi, dens, opts=bie.make_opts(precision=prec))
+        assert rc == bie.OK, info
+        res[prec] = (phi.cpu().numpy(), dens.cpu().numpy(), info)
+    for prec in (bie.MIXED_FF, bie.MIXED):
+        phi, nu, info = res[prec]
+        _check_full_size(g, geo, 0, phi, nu, info, res[bie.FP64][0])
+    bie.tune_clear()
