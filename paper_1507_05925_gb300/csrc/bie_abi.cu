@@ -184,6 +184,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   g.xff = A.take<float4>(M);
   g.xfl = A.take<float2>(M);
   g.nff = A.take<float4>(M);
+  g.qf = A.take<float>(2 * (size_t)M);
   g.len = A.take<double>(N);
   g.xc = A.take<double>(N);
   g.yc = A.take<double>(N);

@@ -67,6 +67,7 @@ struct Geo {
   const int* jstep = nullptr;
   double pairs = 0.0;  // pair interactions of one operator application (0: M (M - 1))
   double* pnet = nullptr;  // [2 nprob] batched solves: each problem's net load and largest |load|
+  float* qf = nullptr;     // [2M] scratch: FP32 source strengths of the FP32 pair sum
 };
 
 // A vector that lives at base + (idx ? *idx + off : off) * ld, so that a

@@ -292,6 +292,21 @@ __device__ __forceinline__ float4 body_range_box(const float4* __restrict__ bbox
   return u;
 }
 
+// FP32 source strengths q_b = sscale_b v_b (two per node for Stokes), once per
+// operator application: every target block of k_pair32 reads them.
+template <int KIND>
+__global__ void k_src32(Geo g, VecRef vr, const double* __restrict__ sscale, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const double* __restrict__ v = vr.ptr();
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < g.M; b += gridDim.x * blockDim.x) {
+    if (KIND == 0)
+      g.qf[b] = (float)(sscale[b] * v[b]);
+    else
+      reinterpret_cast<float2*>(g.qf)[b] =
+          make_float2((float)(sscale[b] * v[2 * b]), (float)(sscale[b] * v[2 * b + 1]));
+  }
+}
+
 template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
                                                  int chunk, double* __restrict__ partial,
@@ -301,7 +316,6 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
   __shared__ float2 sq[kTile32];
   __shared__ float4 sp2[kTile32 / 2];  // far: source pairs (-x', -x', -y', -y')
   __shared__ float4 sq2[kTile32 / 2];  // far: (q1, q1', q2, q2'); Laplace packs (q, q') pairs
-  const double* __restrict__ v = vr.ptr();
   const int M = g.M;
   const int tbase = blockIdx.x * kB32 * kT32;
   const int tend = min(M, tbase + kB32 * kT32);
@@ -359,10 +373,11 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
       float q1 = 0.f, q2 = 0.f;
       if (l < nt) {
         if (KIND == 0) {
-          q1 = (float)(sscale[b] * v[b]);
+          q1 = g.qf[b];
         } else {
-          q1 = (float)(sscale[b] * v[2 * b]);
-          q2 = (float)(sscale[b] * v[2 * b + 1]);
+          const float2 qq = reinterpret_cast<const float2*>(g.qf)[b];
+          q1 = qq.x;
+          q2 = qq.y;
         }
       }
       if (far) {
@@ -418,13 +433,19 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
 #pragma unroll
   for (int k = 0; k < kT32; ++k) {
     const int a = a0 + k * kB32;
-    const double dax_k = (double)sx[k] + (double)ex[k], day_k = (double)sy[k] + (double)ey[k];
     if (a < M) {
-      if (KIND == 0)
-        partial[(long long)blockIdx.y * M + a] = g.nx[a] * dax_k + g.ny[a] * day_k;
-      else {
-        partial[((long long)blockIdx.y * M + a) * 2] = dax_k;
-        partial[((long long)blockIdx.y * M + a) * 2 + 1] = day_k;
+      if (KIND == 0) {
+        // n_a . (sx + ex, sy + ey) in float-float: the normal's hi/lo split,
+        // error-free products, one TwoSum (no FP64 pipe per target and block)
+        const float4 n = g.nff[a];
+        float p1, e1, p2, e2, h, l;
+        ff_mul(n.x, n.y, sx[k], ex[k], p1, e1);
+        ff_mul(n.z, n.w, sy[k], ey[k], p2, e2);
+        two_sum(p1, p2, h, l);
+        partial[(long long)blockIdx.y * M + a] = (double)h + (double)(l + (e1 + e2));
+      } else {
+        partial[((long long)blockIdx.y * M + a) * 2] = (double)sx[k] + (double)ex[k];
+        partial[((long long)blockIdx.y * M + a) * 2 + 1] = (double)sy[k] + (double)ey[k];
       }
     }
   }
@@ -814,10 +835,15 @@ void launch_pairs(const Geo& g, int kind, int precision, const PairPlan& p, VecR
       k_pair64<1, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
   } else if (precision == 1) {
     dim3 grid((g.M + kB32 * kT32 - 1) / (kB32 * kT32), p.S);
-    if (kind == 0)
+    const int gs = (int)std::min<long long>(1216, (g.M + 255) / 256);
+    if (kind == 0) {
+      k_src32<0><<<gs, 256, 0, s>>>(g, v, sscale, stop);
       k_pair32<0, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
-    else
+    } else {
+      k_src32<1><<<gs, 256, 0, s>>>(g, v, sscale, stop);
       k_pair32<1, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+    }
+    note_launches(1);
   } else {
     dim3 grid((g.M + kBF * kTF - 1) / (kBF * kTF), p.S);
     if (kind == 0)
