@@ -68,3 +68,17 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     rc = lib.bie_create(ctypes.byref(h), 0, 0)
     assert rc == bie.ERR_CUDA and not h.value
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    # argument checks come before any CUDA call: no context, no count, no server
+    geo = (bie.BieGeometry * 1)()
+    ptrs = (ctypes.c_void_p * 1)()
+    infos = (bie.BieInfo * 1)()
+    status = (ctypes.c_int32 * 1)()
+    for fn in (lib.elastance_solve_batch, lib.mobility_solve_batch):
+        assert fn(None, 1, geo, ptrs, ptrs, None, infos, status, None) == bie.ERR_INVALID
+    S, ms = ctypes.c_int32(), ctypes.c_double()
+    assert lib.bie_tune(None, None, 0, 1, ctypes.byref(S), ctypes.byref(ms), None) == bie.ERR_INVALID
+    lib.bie_tune_clear()  # host-side table only
+    assert lib.bie_server_batching(None, 8, 0, None) == bie.ERR_INVALID
