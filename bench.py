@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--batch-requests", type=int, default=1000,
                     help="batched solves: served-mix requests solved in batches of one kind (0 = skip the section)")
     ap.add_argument("--batch-size", type=int, default=16)
+    ap.add_argument("--mobility-steps", type=int, default=5,
+                    help="timed mobility solves of 400 ellipses x 128 nodes, direct pair sums (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
@@ -473,6 +475,52 @@ def run_large(args, rank, local):
             "info": info}
 
 
+def run_mobility(args, rank, local):
+    """Mobility of 400 ellipses (M = 51,200, direct pair sums): FP32 inner
+    solves with a float-float residual (mixed_ff) and with FP64 residuals
+    (mixed), split counts tuned first (bie_tune) unless --no-tune."""
+    import torch
+
+    from paper_1507_05925_gb300 import bie
+
+    g = synth.ellipse_suspension(seed=2000 + rank)
+    dev = torch.device("cuda", local)
+    gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
+    N = g["body_start"].size - 1
+    FT = torch.from_numpy(np.ascontiguousarray(g["FT"].reshape(-1))).to(dev)
+    UW = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    ctx = bie.Context(local)
+    tuning = None
+    if not args.no_tune:
+        tuning = {}
+        for name, prec in (("stokes_fp32", bie.MIXED), ("stokes_ff", bie.MIXED_FF)):
+            rc, S, tms = bie.tune(ctx, gd, bie.STOKES, prec)
+            assert rc == bie.OK, ctx.last_error()
+            tuning[name] = {"splits": S, "ms_per_application": tms}
+    out = {"workload": "ellipses400_M51200", "M": int(g["x"].size), "pair_sum_tuning": tuning}
+    for name, prec, steps in (("mixed_ff", bie.MIXED_FF, args.mobility_steps), ("mixed", bie.MIXED, 1)):
+        if steps <= 0:
+            continue
+        opts = bie.make_opts(precision=prec)
+        rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)  # warm-up
+        assert rc == bie.OK, (rc, ctx.last_error())
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
+            e1.record()
+            torch.cuda.synchronize()
+            assert rc == bie.OK
+            ms.append(e0.elapsed_time(e1))
+        out[name] = {"solves_per_s": 1e3 / float(np.mean(ms)), "ms_per_solve": float(np.mean(ms)), "steps": steps,
+                     "info": info}
+    ctx.close()
+    return out
+
+
 def run_kernel(args, local):
     """Operator applications only (for kernel timing and ncu captures)."""
     import torch
@@ -727,6 +775,8 @@ def main():
         out["serving"] = run_serving(args, rank, local)
     if args.batch_requests > 0:
         out["batched"] = run_batched(args, rank, local)
+    if args.mobility_steps > 0:
+        out["mobility_ellipses400"] = run_mobility(args, rank, local)
     if args.large_steps > 0:
         out["large_mobility"] = run_large(args, rank, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
