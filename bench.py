@@ -45,7 +45,7 @@ FLOPS_PER_PAIR = {"laplace": 10.0, "stokes": 18.0}
 # capture of the current kernels (profiles/k_pair32_laplace_stars100_M25600.md,
 # profiles/k_pair_ff_laplace_stars100_M25600.md); a kernel changed since its
 # capture must be taken out of this table
-DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 1.291e6, "laplace_ff": 1.462e6}
+DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 0.982e6, "laplace_ff": 1.462e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
