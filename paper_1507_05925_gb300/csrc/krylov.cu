@@ -49,11 +49,36 @@ __device__ __forceinline__ double combine(const double* __restrict__ V, long lon
 // is written only by its owner, after the owner has read it.
 
 // Partial dot products of this CTA's elements of w with V_0..V_{jc-1} into
-// out[0..jc).
-__device__ void arn_block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
-                               long long n, int jc, double* __restrict__ out, double (*sh)[kMaxBasis]) {
+// out[0..jc).  NARROW (a grid of at most two CTAs per SM, few elements a
+// CTA): warp u takes basis vectors u, u + 8, ..., its lanes stride the CTA's
+// elements with two independent sums, one warp reduction per vector.  Wide
+// grids: all threads take four vectors at a time, reduced through shared
+// memory.  Both in a fixed order (deterministic).
+template <bool NARROW>
+__device__ __forceinline__ void arn_block_dots(const double* __restrict__ V, long long ld,
+                                               const double* __restrict__ w, long long n, int jc,
+                                               double* __restrict__ out, double (*sh)[kMaxBasis]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * kBV;
+  if (NARROW) {
+    const long long base = blockIdx.x * (long long)kBV;
+    for (int i = wid; i < jc; i += kBV / 32) {
+      const double* __restrict__ Vi = V + (long long)i * ld;
+      double a0 = 0.0, a1 = 0.0;
+      for (long long c = base; c < n; c += stride) {
+#pragma unroll
+        for (int u = 0; u < kBV / 32; u += 2) {
+          const long long k0 = c + u * 32 + lane, k1 = k0 + 32;
+          if (k0 < n) a0 = fma(Vi[k0], w[k0], a0);
+          if (k1 < n) a1 = fma(Vi[k1], w[k1], a1);
+        }
+      }
+      const double t = warp_sum(a0 + a1);
+      if (lane == 0) out[i] = t;
+    }
+    __syncthreads();
+    return;
+  }
   int i = 0;
   for (; i + 4 <= jc; i += 4) {
     const double* __restrict__ V0 = V + (long long)i * ld;
@@ -112,7 +137,7 @@ __device__ __forceinline__ double warp_gather(const double* part, long long stri
 }
 
 // hs[i] = sum over CTAs b of part[b][i], one warp per i.
-__device__ void arn_grid_sum(const double* part, int jc, double* hs) {
+__device__ __forceinline__ void arn_grid_sum(const double* part, int jc, double* hs) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < jc; i += kBV / 32) {
     const double t = warp_gather(part + i, kMaxBasis);
@@ -128,7 +153,7 @@ __device__ void arn_grid_sum(const double* part, int jc, double* hs) {
 // reports an error).
 constexpr long long kBarrierSpins = 1LL << 24;
 
-__device__ void grid_barrier(KState* st) {
+__device__ __forceinline__ void grid_barrier(KState* st) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = &st->bar_gen;
@@ -211,7 +236,8 @@ __device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long 
   }
 }
 
-__global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
+template <bool NARROW>
+__global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) {
   KState* st = a.st;
   if (st->stop) return;  // read by every CTA before the first barrier: uniform
   __shared__ double sh[kBV / 32][kMaxBasis];
@@ -227,14 +253,14 @@ __global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
   double* part2 = part1 + G * kMaxBasis;
   double* part3 = part2 + G * kMaxBasis;
   // h1 = V^T w
-  arn_block_dots(a.V, ld, w, n, jc, part1 + blockIdx.x * kMaxBasis, sh);
+  arn_block_dots<NARROW>(a.V, ld, w, n, jc, part1 + blockIdx.x * kMaxBasis, sh);
   grid_barrier(st);
   arn_grid_sum(part1, jc, hs1);
   // w -= V h1; h2 = V^T w
   for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride)
     w[k] = w[k] - combine(a.V, ld, k, hs1, jc);
   __syncthreads();
-  arn_block_dots(a.V, ld, w, n, jc, part2 + blockIdx.x * kMaxBasis, sh);
+  arn_block_dots<NARROW>(a.V, ld, w, n, jc, part2 + blockIdx.x * kMaxBasis, sh);
   grid_barrier(st);
   arn_grid_sum(part2, jc, hs2);
   // w -= V h2; ||w||^2
@@ -334,51 +360,27 @@ __global__ void __launch_bounds__(kBV) k_arnoldi(ArnoldiArgs a) {
 // earlier is skipped and its next basis vector set to zero, so that the
 // operator applied to it gives zero.
 
-// Partial dot products of w[e0, e1) with V_0..V_{jc-1} into out[0..jc).
+// Partial dot products of w[e0, e1) with V_0..V_{jc-1} into out[0..jc):
+// warp u takes basis vectors u, u + 8, ..., its lanes stride the range with
+// two independent sums (fixed order: deterministic).
 __device__ __forceinline__ void seg_block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
-                               long long e0, long long e1, int jc, double* __restrict__ out,
-                               double (*sh)[kMaxBasis]) {
+                                               long long e0, long long e1, int jc, double* __restrict__ out,
+                                               double (*sh)[kMaxBasis]) {
+  (void)sh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int i = 0;
-  for (; i + 4 <= jc; i += 4) {
-    const double* __restrict__ V0 = V + (long long)i * ld;
-    const double* __restrict__ V1 = V0 + ld;
-    const double* __restrict__ V2 = V1 + ld;
-    const double* __restrict__ V3 = V2 + ld;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) {
-      const double wk = w[k];
-      a0 = fma(V0[k], wk, a0);
-      a1 = fma(V1[k], wk, a1);
-      a2 = fma(V2[k], wk, a2);
-      a3 = fma(V3[k], wk, a3);
-    }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    a3 = warp_sum(a3);
-    if (lane == 0) {
-      sh[wid][i] = a0;
-      sh[wid][i + 1] = a1;
-      sh[wid][i + 2] = a2;
-      sh[wid][i + 3] = a3;
-    }
-  }
-  for (; i < jc; ++i) {
+  for (int i = wid; i < jc; i += kBV / 32) {
     const double* __restrict__ Vi = V + (long long)i * ld;
-    double acc = 0.0;
-    for (long long k = e0 + threadIdx.x; k < e1; k += kBV) acc = fma(Vi[k], w[k], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) sh[wid][i] = acc;
+    double a0 = 0.0, a1 = 0.0;
+    long long k = e0 + lane;
+    for (; k + 32 < e1; k += 64) {
+      a0 = fma(Vi[k], w[k], a0);
+      a1 = fma(Vi[k + 32], w[k + 32], a1);
+    }
+    if (k < e1) a0 = fma(Vi[k], w[k], a0);
+    const double t = warp_sum(a0 + a1);
+    if (lane == 0) out[i] = t;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < jc; q += kBV) {
-    double t = 0.0;
-#pragma unroll
-    for (int u = 0; u < kBV / 32; ++u) t += sh[u][q];
-    out[q] = t;
-  }
-  __syncthreads();  // sh is reused by the next range
+  __syncthreads();  // out is read after a grid barrier; sh is no longer used
 }
 
 // hs[i] = sum over the ranges [it0, it1) of part[it][i] (written by other CTAs
@@ -740,27 +742,47 @@ int vec_grid(long long n) {
   return (int)b;
 }
 
-int arnoldi_grid(long long n) {
-  static std::atomic<int> coresident[64];
+// The narrow instance for grids of at most two CTAs per SM.
+bool arnoldi_narrow(long long n) {
+  static std::atomic<int> sms[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (coresident[dev].load() == 0) {
+  if (sms[dev].load() == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 152;
+    }
+    sms[dev].store(v);
+  }
+  return vec_grid(n) <= 2 * sms[dev].load();
+}
+
+int arnoldi_grid(long long n) {
+  static std::atomic<int> coresident[64][2];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  const int narrow = arnoldi_narrow(n) ? 1 : 0;
+  if (coresident[dev][narrow].load() == 0) {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, kBV, 0) != cudaSuccess ||
+    const void* fn = narrow ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBV, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm * sms < 1) {
       cudaGetLastError();
       return 1;  // not cached: a launch of one CTA is always co-resident
     }
-    coresident[dev].store(per_sm * sms);
+    coresident[dev][narrow].store(per_sm * sms);
   }
-  return std::min(vec_grid(n), coresident[dev].load());
+  return std::min(vec_grid(n), coresident[dev][narrow].load());
 }
 
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s) {
   ArnoldiArgs args = a;
   void* params[] = {&args};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(grid), dim3(kBV), params, 0, s);
+  const void* fn = arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>;
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBV), params, 0, s);
   note_launches(1);
   return e;
 }
