@@ -612,17 +612,38 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
     const double os = scaled ? g.sw[a] : 1.0;
     const double wk = g.w[a] * g.kappa[a];
     if (KIND == 0) {
-      double k = 0.0;
-      for (int s = 0; s < S; ++s) k += partial[(long long)s * M + a];
+      // four independent sums over the source splits (loads in flight), added in a fixed order
+      double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0;
+      int s = 0;
+      for (; s + 4 <= S; s += 4) {
+        k0 += partial[(long long)s * M + a];
+        k1 += partial[(long long)(s + 1) * M + a];
+        k2 += partial[(long long)(s + 2) * M + a];
+        k3 += partial[(long long)(s + 3) * M + a];
+      }
+      for (; s < S; ++s) k0 += partial[(long long)s * M + a];
+      const double k = (k0 + k1) + (k2 + k3);
       const double mu = v[a] / os;
       const double y = -kInv2Pi * k - kInv4Pi * wk * mu + m0;
       out[a] = sign * (0.5 * v[a] + os * y);
     } else {
-      double k1 = 0.0, k2 = 0.0;
-      for (int s = 0; s < S; ++s) {
-        k1 += partial[((long long)s * M + a) * 2];
-        k2 += partial[((long long)s * M + a) * 2 + 1];
+      double k1 = 0.0, k2 = 0.0, k1b = 0.0, k2b = 0.0;
+      int s = 0;
+      for (; s + 2 <= S; s += 2) {
+        const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
+        const double2 p1 = reinterpret_cast<const double2*>(partial)[(long long)(s + 1) * M + a];
+        k1 += p0.x;
+        k2 += p0.y;
+        k1b += p1.x;
+        k2b += p1.y;
       }
+      if (s < S) {
+        const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
+        k1 += p0.x;
+        k2 += p0.y;
+      }
+      k1 += k1b;
+      k2 += k2b;
       const double mu1 = v[2 * a] / os, mu2 = v[2 * a + 1] / os;
       const double tx = -g.ny[a], ty = g.nx[a];
       const double dd = -0.5 * kInvPi * wk * (tx * mu1 + ty * mu2);
