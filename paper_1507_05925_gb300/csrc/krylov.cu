@@ -39,7 +39,7 @@ __device__ __forceinline__ double combine(const double* __restrict__ V, long lon
 
 // ------------------------------------------------------------ fused Arnoldi
 // One Arnoldi step after w = A z_j (w = V_{j+1}) in a single cooperative
-// cooperative launch with three grid barriers: CGS2 (h1 = V^T w; w -= V h1; h2 = V^T w;
+// launch with three grid barriers: CGS2 (h1 = V^T w; w -= V h1; h2 = V^T w;
 // w -= V h2), ||w||, the Hessenberg column with its Givens rotations and the
 // residual estimate, v_{j+1} = w / ||w|| and, with the block-Jacobi
 // preconditioner, z_{j+1} = P v_{j+1}.  After each barrier every CTA adds the
@@ -364,9 +364,7 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
 // warp u takes basis vectors u, u + 8, ..., its lanes stride the range with
 // two independent sums (fixed order: deterministic).
 __device__ __forceinline__ void seg_block_dots(const double* __restrict__ V, long long ld, const double* __restrict__ w,
-                                               long long e0, long long e1, int jc, double* __restrict__ out,
-                                               double (*sh)[kMaxBasis]) {
-  (void)sh;
+                                               long long e0, long long e1, int jc, double* __restrict__ out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < jc; i += kBV / 32) {
     const double* __restrict__ Vi = V + (long long)i * ld;
@@ -380,7 +378,7 @@ __device__ __forceinline__ void seg_block_dots(const double* __restrict__ V, lon
     const double t = warp_sum(a0 + a1);
     if (lane == 0) out[i] = t;
   }
-  __syncthreads();  // out is read after a grid barrier; sh is no longer used
+  __syncthreads();
 }
 
 // hs[i] = sum over the ranges [it0, it1) of part[it][i] (written by other CTAs
@@ -411,7 +409,6 @@ __device__ __forceinline__ double seg_hn(const double* part3, int it0, int it1, 
 __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) {
   KState* st = a.st;
   if (st->stop) return;  // read by every CTA before the first barrier: uniform
-  __shared__ double sh[kBV / 32][kMaxBasis];
   __shared__ double hs[kMaxBasis], hcol[kMaxBasis + 1];
   __shared__ double red[kBV / 32];
   __shared__ double cell;
@@ -428,7 +425,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
   for (int it = blockIdx.x; it < sg.nitem; it += G) {
     const int p = sg.iprob[it];
     if (sg.ps[p].stop_j <= j) continue;
-    seg_block_dots(a.V, ld, w, sg.ibeg[it], sg.ibeg[it + 1], jc, part1 + (long long)it * kMaxBasis, sh);
+    seg_block_dots(a.V, ld, w, sg.ibeg[it], sg.ibeg[it + 1], jc, part1 + (long long)it * kMaxBasis);
   }
   grid_barrier(st);
   // w -= V h1; h2 = V^T w
@@ -439,7 +436,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
     const long long e0 = sg.ibeg[it], e1 = sg.ibeg[it + 1];
     for (long long k = e0 + threadIdx.x; k < e1; k += kBV) w[k] = w[k] - combine(a.V, ld, k, hs, jc);
     __syncthreads();
-    seg_block_dots(a.V, ld, w, e0, e1, jc, part2 + (long long)it * kMaxBasis, sh);
+    seg_block_dots(a.V, ld, w, e0, e1, jc, part2 + (long long)it * kMaxBasis);
   }
   grid_barrier(st);
   // w -= V h2; ||w||^2 per range
