@@ -498,10 +498,12 @@ int validate_batch(bie_ctx* ctx, const BatchIn& b, std::vector<int>& bs, std::ve
     int* d = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void**>(&d), roff[P] * sizeof(int), s));
     for (size_t i = 0; i < segs.size(); ++i) segs[i].dst = d + roff[on_device[i]];
-    CK(gather_segments(segs, s));
     std::vector<int> tmp(roff[P]);
-    CK(cudaMemcpyAsync(tmp.data(), d, roff[P] * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaFreeAsync(d, s));
+    cudaError_t e = gather_segments(segs, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.data(), d, roff[P] * sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t f = cudaFreeAsync(d, s);  // on every path
+    CK(e);
+    CK(f);
     CK(cudaStreamSynchronize(s));
     for (int p : on_device) std::copy(tmp.begin() + roff[p], tmp.begin() + roff[p + 1], raw.begin() + roff[p]);
   }
@@ -1402,12 +1404,23 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   }
   int smax = 1;
   for (int S : cand) smax = std::max(smax, S);
-  double* partial = nullptr;
-  CK(cudaMallocAsync(reinterpret_cast<void**>(&partial), (size_t)smax * w.n * sizeof(double), s));
+  // the timing scratch is released on every return path
+  struct Scratch {
+    double* partial = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t s;
+    ~Scratch() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (partial) cudaFreeAsync(partial, s);
+    }
+  } sc{nullptr, nullptr, nullptr, s};
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&sc.partial), (size_t)smax * w.n * sizeof(double), s));
+  double* partial = sc.partial;
   CK(fill0(w.io_in, w.n, s));  // the cost of a pair sum does not depend on the values
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&sc.e0));
+  CK(cudaEventCreate(&sc.e1));
+  cudaEvent_t e0 = sc.e0, e1 = sc.e1;
   int best = S0;
   double best_ms = 0.0, s0_ms = 0.0;
   for (int S : cand) {
@@ -1435,9 +1448,6 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
       best = S;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  CK(cudaFreeAsync(partial, s));
   CK(cudaStreamSynchronize(s));
   // keep the occupancy rule unless another count is clearly faster (2%)
   if (best != S0 && best_ms > 0.98 * s0_ms) {
