@@ -205,3 +205,54 @@ def test_batch_mixed_host_and_device_arrays(ctx, kind):
     for out, r in zip(outs, ref):
         o = out.cpu().numpy() if isinstance(out, torch.Tensor) else out
         assert np.array_equal(o, r)  # staging does not change the arithmetic
+
+
+def _with_points(g, shift):
+    # one interior point per body: the mean of its nodes, shifted a little
+    bs = g["body_start"]
+    pts = []
+    for i in range(bs.size - 1):
+        pts += [g["x"][bs[i]:bs[i + 1]].mean() + shift, g["y"][bs[i]:bs[i + 1]].mean() - shift]
+    h = _host(g)
+    h["interior_pt"] = np.array(pts)
+    return h
+
+
+def test_batch_interior_points(ctx):
+    probs = _problems(0, 140, 4)
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    geoms = [_with_points(g, 0.05) for g, _ in probs]
+    loads = [ld for _, ld in probs]
+    outs = [np.empty(ld.size) for ld in loads]
+    rc, _, status = bie.elastance_solve_batch(ctx, geoms, loads, outs, opts=opts)
+    assert rc == bie.OK and status == [bie.OK] * 4
+    for gm, ld, out in zip(geoms, loads, outs):
+        solo = np.empty_like(out)
+        assert bie.elastance_solve(ctx, gm, ld, solo, opts=opts)[0] == bie.OK
+        # (a single body's neutral charge is zero: both results are zero)
+        assert np.linalg.norm(out - solo) <= TOL_SOLVE * np.linalg.norm(solo) + 1e-15
+    # interior points for all problems or for none; a point outside its body
+    mixed = [geoms[0], _host(probs[1][0])]
+    assert bie.elastance_solve_batch(ctx, mixed, loads[:2], outs[:2], opts=opts)[0] == bie.ERR_INVALID
+    bad = dict(geoms[2])
+    bad["interior_pt"] = bad["interior_pt"].copy()
+    bad["interior_pt"][:2] = [1e3, 1e3]
+    assert bie.elastance_solve_batch(ctx, [geoms[0], bad], loads[:2], outs[:2], opts=opts)[0] == bie.ERR_OUTSIDE
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_of_many_small_problems(ctx, kind):
+    # more problems than the batched Arnoldi step has CTAs: ranges per CTA > 1
+    rng = np.random.default_rng(150 + kind)
+    probs = []
+    for i in range(700):
+        g = synth.assemble([synth.disc(0.0, 0.0, rng.uniform(0.5, 1.0), 16),
+                            synth.ellipse(3.0, rng.uniform(-0.3, 0.3), 1.0, rng.uniform(0.4, 1.0), rng.uniform(0, 3), 16)])
+        load = synth.charges(2, rng) if kind == 0 else synth.forces_torques(2, rng).reshape(-1)
+        probs.append((g, np.ascontiguousarray(load)))
+    rc, infos, status, outs = _solve_batch(ctx, kind, probs, bie.make_opts(precision=bie.MIXED_FF), device=True)
+    assert rc == bie.OK and set(status) == {bie.OK}
+    assert max(i["rel_residual"] for i in infos) <= 1e-12
+    for i in range(0, 700, 35):
+        g, load = probs[i]
+        assert rel2(outs[i], _oracle(kind, g, load)) <= TOL_SOLVE
