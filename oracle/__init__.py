@@ -17,8 +17,10 @@ Modules:
   geometry  -- weights, normals, curvature, per-body length/centroid/W (Sec. 3, 4.1)
   laplace   -- elastance: K, L, sigma, RHS, LU solve, potentials (Sec. 3)
   stokes    -- mobility: stresslet traction kernel, L, rho, LU solve, v/omega (Sec. 4)
+  capacitance -- the capacitance problem (potentials -> charges) by a different
+               integral equation, for the paper's round trip (Sec. 6.1)
 
 Every function here is pinned by tests against closed forms, the paper's
 identities and the paper's printed two-disc values (see tests/test_oracle_pins.py).
 """
-from . import geometry, laplace, stokes  # noqa: F401
+from . import capacitance, geometry, laplace, stokes  # noqa: F401

@@ -464,3 +464,25 @@ def _check_full_size(g, geo, kind, res, nu, info, res64):
     assert rel2(res, res64) < TOL_SOLVE
     # (4) constraints of the equivalence lemma
     assert info["constraint_residual"] < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# the paper's round trip (Section 6.1) on the GPU path: charges from the
+# capacitance oracle (a different integral equation) drive the GPU elastance
+# solve, which must return the prescribed potentials minus the potential at
+# infinity of the capacitance solution
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["four_discs", "ragged4", "multitile"])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
+def test_capacitance_round_trip_on_gpu(ctx, name, prec):
+    from oracle import capacitance
+    g = GEOMS[name]()
+    N = g["body_start"].size - 1
+    phi = np.random.default_rng(31).standard_normal(N)
+    cap = capacitance.solve(g, phi)
+    out = np.empty(N)
+    rc, info = bie.elastance_solve(ctx, g, cap["q"], out, opts=bie.make_opts(precision=prec))
+    assert rc == bie.OK, (rc, info)
+    back = out + cap["u_inf"]
+    print(f"round trip {name} prec={prec}: {np.max(np.abs(back - phi)):.2e}")
+    assert np.max(np.abs(back - phi)) <= 1e-10 * np.max(np.abs(phi))

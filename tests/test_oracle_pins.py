@@ -13,7 +13,7 @@ import pytest
 
 import synth
 from conftest import read_golden
-from oracle import geometry, laplace, stokes
+from oracle import capacitance, geometry, laplace, stokes
 
 
 def _geo(curves):
@@ -411,3 +411,86 @@ def test_planted_mistakes_are_caught(monkeypatch):
         with monkeypatch.context() as m:
             m.setattr(stokes, name, fn)
             assert not _stokes_pins_pass(), f"stokes mistake {fn.__name__} not caught"
+
+
+# ---------------------------------------------------------------------------
+# the paper's round trip (Section 6.1): a capacitance solve by a different
+# integral equation (exterior Dirichlet problem, double layer plus one
+# logarithmic source per body) gives charges and the potential at infinity;
+# the elastance oracle driven by these charges returns the prescribed
+# potentials minus that constant.
+# ---------------------------------------------------------------------------
+def _round_trip_geometries():
+    stars = synth.assemble([synth.star(0.0, 0.0, 0.9, 0.25, 5, 0.3, 96), synth.star(3.2, 0.3, 0.8, 0.2, 3, 1.1, 64),
+                            synth.ellipse(0.2, 3.1, 1.0, 0.5, 0.7, 80), synth.star(3.3, 3.3, 1.0, 0.15, 4, 2.0, 128)])
+    return {"four_discs": synth.four_discs(seed=0), "stars": stars, "two_discs": synth.two_discs(0.5, 128)}
+
+
+@pytest.mark.parametrize("name", ["four_discs", "stars", "two_discs"])
+def test_capacitance_elastance_round_trip(name):
+    g = _round_trip_geometries()[name]
+    N = g["body_start"].size - 1
+    phi = np.random.default_rng(21).standard_normal(N)
+    sol = capacitance.solve(g, phi)
+    assert abs(sol["q"].sum()) < 1e-12 * np.abs(sol["q"]).sum()  # bounded field: neutral
+    back = laplace.elastance_matrix(g) @ sol["q"] + sol["u_inf"]
+    assert np.max(np.abs(back - phi)) < 1e-11
+
+
+def test_capacitance_two_discs_exact_and_paper_table():
+    # charges (Q, -Q) for potentials (V1, V2): V1 - V2 = (Q/pi) log((alpha + d/2)/(alpha - d/2)),
+    # alpha = sqrt(d + d^2/4) (Section 6.1.1); the potential at infinity is (V1 + V2)/2
+    kv, rows = read_golden("two_disc_elastance.txt")
+    v1, v2 = kv["phi1"][0], kv["phi2"][0]
+    for d, q1, *_ in rows[:2]:
+        n = 256 if d >= 0.5 else 1024
+        sol = capacitance.solve(synth.two_discs(d, n), np.array([v1, v2]))
+        al = math.sqrt(d + d * d / 4)
+        Q = (v1 - v2) * math.pi / math.log((al + d / 2) / (al - d / 2))
+        assert abs(sol["q"][0] - Q) < 1e-12 * Q and abs(sol["q"][1] + Q) < 1e-12 * Q
+        assert abs(sol["u_inf"] - 0.5 * (v1 + v2)) < 1e-13
+        # the paper's printed q1 (6 digits) is the physical charge / (-2 pi)
+        assert abs(sol["q"][0] - (-2 * math.pi * q1)) < 3e-6 * Q
+
+
+def test_capacitance_planted_mistakes_break_the_round_trip(monkeypatch):
+    g = _round_trip_geometries()["four_discs"]
+    phi = np.random.default_rng(22).standard_normal(4)
+    E = laplace.elastance_matrix(g)
+    good = capacitance.double_layer_matrix
+
+    def err():
+        sol = capacitance.solve(g, phi)
+        return np.max(np.abs(E @ sol["q"] + sol["u_inf"] - phi))
+
+    assert err() < 1e-11
+
+    def flipped_diagonal(geo):
+        D = good(geo)
+        D[np.arange(geo["M"]), np.arange(geo["M"])] *= -1.0
+        return D
+
+    def target_normal(geo):
+        rx = geo["x"][:, None] - geo["x"][None, :]
+        ry = geo["y"][:, None] - geo["y"][None, :]
+        r2 = rx * rx + ry * ry
+        np.fill_diagonal(r2, 1.0)
+        D = -(rx * geo["nx"][:, None] + ry * geo["ny"][:, None]) / (2 * math.pi * r2)
+        D[np.arange(geo["M"]), np.arange(geo["M"])] = geo["kappa"] / (4 * math.pi)
+        return D * geo["w"][None, :]
+
+    for wrong in (flipped_diagonal, target_normal):
+        monkeypatch.setattr(capacitance, "double_layer_matrix", wrong)
+        assert err() > 1e-6, wrong.__name__
+    monkeypatch.setattr(capacitance, "double_layer_matrix", good)
+    # dropping one density constraint leaves the system singular or wrong
+    good_system = capacitance.system_matrix
+
+    def one_constraint_short(geo):
+        S = good_system(geo)
+        S[geo["M"], :] = 0.0
+        S[geo["M"], geo["M"]] = 1.0  # replaced by A_0 = 0
+        return S
+
+    monkeypatch.setattr(capacitance, "system_matrix", one_constraint_short)
+    assert err() > 1e-6
