@@ -19,8 +19,10 @@ Modules:
   stokes    -- mobility: stresslet traction kernel, L, rho, LU solve, v/omega (Sec. 4)
   capacitance -- the capacitance problem (potentials -> charges) by a different
                integral equation, for the paper's round trip (Sec. 6.1)
+  resistance  -- the resistance problem (rigid motions -> forces and torques) by
+               a different integral equation, for the mobility round trip (Sec. 6.2)
 
 Every function here is pinned by tests against closed forms, the paper's
 identities and the paper's printed two-disc values (see tests/test_oracle_pins.py).
 """
-from . import capacitance, geometry, laplace, stokes  # noqa: F401
+from . import capacitance, geometry, laplace, resistance, stokes  # noqa: F401

@@ -486,3 +486,25 @@ def test_capacitance_round_trip_on_gpu(ctx, name, prec):
     back = out + cap["u_inf"]
     print(f"round trip {name} prec={prec}: {np.max(np.abs(back - phi)):.2e}")
     assert np.max(np.abs(back - phi)) <= 1e-10 * np.max(np.abs(phi))
+
+
+@pytest.mark.parametrize("name", ["four_discs", "ragged4"])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
+def test_resistance_round_trip_on_gpu(ctx, name, prec):
+    # Section 6.2: forces and torques from the resistance oracle (a different
+    # integral equation) drive the GPU mobility solve, which must return the
+    # prescribed rigid motions less the velocity at infinity
+    from oracle import resistance
+    g = GEOMS[name]()
+    N = g["body_start"].size - 1
+    UW = np.random.default_rng(32).standard_normal((N, 3))
+    res = resistance.solve(g, UW)
+    out = np.empty(3 * N)
+    rc, info = bie.mobility_solve(ctx, g, np.ascontiguousarray(res["FT"].reshape(-1)), out,
+                                  opts=bie.make_opts(precision=prec))
+    assert rc == bie.OK, (rc, info)
+    target = UW.copy()
+    target[:, :2] -= res["u_inf"]
+    err = np.max(np.abs(out.reshape(N, 3) - target))
+    print(f"mobility round trip {name} prec={prec}: {err:.2e}")
+    assert err <= 1e-10 * np.max(np.abs(UW))

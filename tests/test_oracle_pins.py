@@ -13,7 +13,7 @@ import pytest
 
 import synth
 from conftest import read_golden
-from oracle import capacitance, geometry, laplace, stokes
+from oracle import capacitance, geometry, laplace, resistance, stokes
 
 
 def _geo(curves):
@@ -420,9 +420,12 @@ def test_planted_mistakes_are_caught(monkeypatch):
 # the elastance oracle driven by these charges returns the prescribed
 # potentials minus that constant.
 # ---------------------------------------------------------------------------
-def _round_trip_geometries():
-    stars = synth.assemble([synth.star(0.0, 0.0, 0.9, 0.25, 5, 0.3, 96), synth.star(3.2, 0.3, 0.8, 0.2, 3, 1.1, 64),
-                            synth.ellipse(0.2, 3.1, 1.0, 0.5, 0.7, 80), synth.star(3.3, 3.3, 1.0, 0.15, 4, 2.0, 128)])
+def _round_trip_geometries(f=1):
+    # f multiplies the node counts of the mixed curves (the Stokes problems need 2)
+    stars = synth.assemble([synth.star(0.0, 0.0, 0.9, 0.25, 5, 0.3, 96 * f),
+                            synth.star(3.2, 0.3, 0.8, 0.2, 3, 1.1, 64 * f),
+                            synth.ellipse(0.2, 3.1, 1.0, 0.5, 0.7, 80 * f),
+                            synth.star(3.3, 3.3, 1.0, 0.15, 4, 2.0, 128 * f)])
     return {"four_discs": synth.four_discs(seed=0), "stars": stars, "two_discs": synth.two_discs(0.5, 128)}
 
 
@@ -494,3 +497,83 @@ def test_capacitance_planted_mistakes_break_the_round_trip(monkeypatch):
 
     monkeypatch.setattr(capacitance, "system_matrix", one_constraint_short)
     assert err() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# the paper's mobility round trip (Section 6.2): a resistance solve by a
+# different integral equation (stresslet double layer plus a Stokeslet and a
+# rotlet per body) gives forces, torques and the velocity at infinity; the
+# mobility oracle driven by them returns the prescribed motions less that
+# velocity.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["four_discs", "stars", "two_discs"])
+def test_resistance_mobility_round_trip(name):
+    # (with half the nodes on the mixed curves the round trip closes to 3e-10:
+    # discretisation error, spectrally convergent)
+    g = _round_trip_geometries(2)[name]
+    N = g["body_start"].size - 1
+    UW = np.random.default_rng(23).standard_normal((N, 3))
+    sol = resistance.solve(g, UW)
+    FT = sol["FT"]
+    assert np.max(np.abs(FT[:, :2].sum(axis=0))) < 1e-12 * np.abs(FT).sum()  # bounded flow: no net force
+    target = UW.copy()
+    target[:, :2] -= sol["u_inf"]
+    back = stokes.solve(g, FT)["UW"]
+    assert np.max(np.abs(back - target)) < 1e-11 * np.max(np.abs(UW))
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.2, 0.3)])
+def test_resistance_single_body_closed_forms(a, b):
+    # one rigid ellipse (viscosity 1): a bounded flow carries no net force, so
+    # the body moves with the flow at infinity; rotation rate omega needs the
+    # torque T = 2 pi (a^2 + b^2) omega (4 pi a^2 omega for a disc)
+    g = synth.assemble([synth.ellipse(0.2, -0.1, a, b, 0.7, 256)])
+    v, om = np.array([0.7, -0.4]), 1.1
+    sol = resistance.solve(g, np.array([[v[0], v[1], om]]))
+    assert np.max(np.abs(sol["FT"][0, :2])) < 1e-12
+    assert abs(sol["FT"][0, 2] - 2 * math.pi * (a * a + b * b) * om) < 1e-12
+    assert np.max(np.abs(sol["u_inf"] - v)) < 1e-12
+
+
+def test_resistance_planted_mistakes_break_the_round_trip(monkeypatch):
+    g = _round_trip_geometries()["four_discs"]
+    UW = np.random.default_rng(24).standard_normal((4, 3))
+
+    def err():
+        sol = resistance.solve(g, UW)
+        target = UW.copy()
+        target[:, :2] -= sol["u_inf"]
+        return np.max(np.abs(stokes.solve(g, sol["FT"])["UW"] - target))
+
+    assert err() < 1e-11
+    good_D, good_S = resistance.double_layer_matrix, resistance.system_matrix
+
+    def flipped_diagonal(geo):
+        D = good_D(geo)
+        i = np.arange(2 * geo["M"])
+        D[i, i] *= -1.0
+        D[0::2, 1::2][np.arange(geo["M"]), np.arange(geo["M"])] *= -1.0
+        return D
+
+    def wrong_jump(geo):
+        S = good_S(geo)
+        n = 2 * geo["M"]
+        S[:n, :n] -= np.eye(n)  # D - 1/2 I: the interior limit
+        return S
+
+    def flipped_rotlet(geo):
+        S = good_S(geo)
+        n, N = 2 * geo["M"], geo["N"]
+        S[:n, n + 2 * N:n + 3 * N] *= -1.0
+        return S
+
+    monkeypatch.setattr(resistance, "double_layer_matrix", flipped_diagonal)
+    assert err() > 1e-6
+    monkeypatch.setattr(resistance, "double_layer_matrix", good_D)
+    for wrong in (wrong_jump, flipped_rotlet):
+        monkeypatch.setattr(resistance, "system_matrix", wrong)
+        try:
+            e = err()
+        except (np.linalg.LinAlgError, ValueError):
+            e = np.inf  # a singular system is caught too
+        assert not (e < 1e-6), wrong.__name__
