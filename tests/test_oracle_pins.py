@@ -535,6 +535,21 @@ def test_resistance_single_body_closed_forms(a, b):
     assert np.max(np.abs(sol["u_inf"] - v)) < 1e-12
 
 
+def test_resistance_two_discs_paper_table():
+    # Section 6.2.1: the paper solves the resistance problem for the prescribed
+    # motions (reading A16 of the velocity components) and prints the forces and
+    # torques; its own round-trip errors are 1e-7 to 2e-5, so the printed values
+    # agree with the converged oracle (n = 256 / 1024 unchanged at twice the
+    # nodes) to 1e-5 (forces) and 1e-4 (torques) relative
+    kv, rows = read_golden("two_disc_mobility.txt")
+    UW = np.array([[kv["v1"][0], kv["v2"][0], kv["omega"][0]], [kv["v1"][1], kv["v2"][1], kv["omega"][1]]])
+    for d, F11, F21, T1, T2, *_ in rows[:2]:
+        FT = resistance.solve(synth.two_discs(d, 256 if d >= 0.5 else 1024), UW)["FT"]
+        assert np.max(np.abs(FT[0, :2] - [F11, F21])) < 1e-5 * abs(F11)
+        assert np.max(np.abs(FT[1, :2] + [F11, F21])) < 1e-5 * abs(F11)  # F_2 = -F_1
+        assert np.max(np.abs(FT[:, 2] - [T1, T2])) < 1e-4 * max(abs(T1), abs(T2))
+
+
 def test_resistance_planted_mistakes_break_the_round_trip(monkeypatch):
     g = _round_trip_geometries()["four_discs"]
     UW = np.random.default_rng(24).standard_normal((4, 3))
