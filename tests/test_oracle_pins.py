@@ -550,6 +550,24 @@ def test_resistance_two_discs_paper_table():
         assert np.max(np.abs(FT[:, 2] - [T1, T2])) < 1e-4 * max(abs(T1), abs(T2))
 
 
+def test_resistance_matrix_reciprocity():
+    # Lorentz reciprocity and dissipation: the map from rigid motions to forces
+    # and torques is symmetric positive semidefinite, and a common translation
+    # of all bodies moves the fluid rigidly with no force (its null space)
+    g = _round_trip_geometries(2)["stars"]
+    N = g["body_start"].size - 1
+    R = np.empty((3 * N, 3 * N))
+    for k in range(3 * N):
+        e = np.zeros(3 * N)
+        e[k] = 1.0
+        R[:, k] = resistance.solve(g, e.reshape(N, 3))["FT"].reshape(-1)
+    assert np.max(np.abs(R - R.T)) < 1e-10 * np.max(np.abs(R))
+    ev = np.linalg.eigvalsh(0.5 * (R + R.T))
+    assert ev[0] > -1e-10 * ev[-1] and ev[2] > 1e-3 * ev[-1]  # exactly two zero modes
+    for c in ([1.0, 0.0, 0.0], [0.0, 1.0, 0.0]):
+        assert np.max(np.abs(R @ np.tile(c, N))) < 1e-10 * np.max(np.abs(R))
+
+
 def test_resistance_planted_mistakes_break_the_round_trip(monkeypatch):
     g = _round_trip_geometries()["four_discs"]
     UW = np.random.default_rng(24).standard_normal((4, 3))
