@@ -456,6 +456,19 @@ def test_capacitance_two_discs_exact_and_paper_table():
         assert abs(sol["q"][0] - (-2 * math.pi * q1)) < 3e-6 * Q
 
 
+def test_capacitance_matrix_reciprocity():
+    # Green's reciprocity and energy: the capacitance matrix (potentials ->
+    # charges, bounded field) is symmetric positive semidefinite, and equal
+    # potentials on every conductor induce no charge (its null space)
+    g = _round_trip_geometries()["stars"]
+    N = g["body_start"].size - 1
+    C = np.column_stack([capacitance.solve(g, e)["q"] for e in np.eye(N)])
+    assert np.max(np.abs(C - C.T)) < 1e-10 * np.max(np.abs(C))
+    ev = np.linalg.eigvalsh(0.5 * (C + C.T))
+    assert ev[0] > -1e-10 * ev[-1] and ev[1] > 1e-3 * ev[-1]  # exactly one zero mode
+    assert np.max(np.abs(C @ np.ones(N))) < 1e-10 * np.max(np.abs(C))
+
+
 def test_capacitance_planted_mistakes_break_the_round_trip(monkeypatch):
     g = _round_trip_geometries()["four_discs"]
     phi = np.random.default_rng(22).standard_normal(4)
