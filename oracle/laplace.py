@@ -52,11 +52,22 @@ def kernel_matrix(geo: dict) -> np.ndarray:
     return kernel_rows(geo, np.arange(geo["M"]))
 
 
-def operator_matrix(geo: dict) -> np.ndarray:
-    """Dense 1/2 I + K + L (unscaled unknowns)."""
+def operator_matrix(geo: dict, block: int = 1024) -> np.ndarray:
+    """Dense 1/2 I + K + L (unscaled unknowns).
+
+    Filled row block by row block into one M x M array, so that the
+    temporaries of the entry formulas stay block x M (M = 25,600 needs 5.2 GB
+    for the matrix itself and no more than a few hundred MB besides).
+    """
     M = geo["M"]
-    idx = np.arange(M)
-    return 0.5 * np.eye(M) + kernel_rows(geo, idx) + completion_rows(geo, idx)
+    A = np.empty((M, M))
+    for s in range(0, M, block):
+        rows = np.arange(s, min(M, s + block))
+        blk = kernel_rows(geo, rows)
+        blk[np.arange(rows.size), rows] += 0.5
+        blk += completion_rows(geo, rows)
+        A[rows] = blk
+    return A
 
 
 def apply(geo: dict, v: np.ndarray, with_L: bool = True, block: int = 2048) -> np.ndarray:
@@ -96,7 +107,9 @@ def solve(g: dict, q: np.ndarray) -> dict:
     sigma = incident_density(geo, q)
     A = operator_matrix(geo)
     b = rhs(geo, sigma)
-    mu = sla.lu_solve(sla.lu_factor(A), b)
+    # LU with partial pivoting, factored in place (A is not used again)
+    mu = sla.lu_solve(sla.lu_factor(A, overwrite_a=True, check_finite=False), b, check_finite=False)
+    del A
     pts = geometry.interior_points(geo)
     phi = single_layer_at(geo, mu + sigma, pts["z0x"], pts["z0y"])
     return dict(phi=phi, mu=mu, sigma=sigma, nu=mu + sigma, b=b, geo=geo)

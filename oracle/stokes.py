@@ -79,23 +79,44 @@ def completion_rows(geo: dict, rows: np.ndarray) -> np.ndarray:
     return out
 
 
-def operator_matrix(geo: dict) -> np.ndarray:
+def operator_matrix(geo: dict, block: int = 512) -> np.ndarray:
+    """Dense 1/2 I + K + L, [2M, 2M], filled node-row block by block."""
     M = geo["M"]
-    idx = np.arange(M)
-    return 0.5 * np.eye(2 * M) + kernel_rows(geo, idx) + completion_rows(geo, idx)
+    A = np.empty((2 * M, 2 * M))
+    for s in range(0, M, block):
+        rows = np.arange(s, min(M, s + block))
+        blk = kernel_rows(geo, rows)
+        blk[np.arange(2 * rows.size), 2 * rows[0] + np.arange(2 * rows.size)] += 0.5
+        blk += completion_rows(geo, rows)
+        A[2 * rows[0]:2 * rows[-1] + 2] = blk
+    return A
 
 
-def apply(geo: dict, v: np.ndarray, with_L: bool = True, block: int = 1024) -> np.ndarray:
-    """(1/2 I + K [+ L]) v for an interleaved [2M] vector, row block by row block."""
+def apply(geo: dict, v: np.ndarray, with_L: bool = True, block: int = 1024, workers: int = 1) -> np.ndarray:
+    """(1/2 I + K [+ L]) v for an interleaved [2M] vector, row block by row block.
+
+    workers > 1 computes the row blocks on that many threads (each block is
+    independent; numpy releases the interpreter lock in its array loops).
+    """
     M = geo["M"]
     out = np.empty(2 * M)
-    for s in range(0, M, block):
+
+    def one(s):
         rows = np.arange(s, min(M, s + block))
         A = kernel_rows(geo, rows)
         if with_L:
             A += completion_rows(geo, rows)
         sl = slice(2 * rows[0], 2 * rows[-1] + 2)
         out[sl] = 0.5 * v[sl] + A @ v
+
+    starts = range(0, M, block)
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(one, starts))
+    else:
+        for s in starts:
+            one(s)
     return out
 
 
@@ -150,9 +171,76 @@ def solve(g: dict, FT: np.ndarray) -> dict:
     rho = incident_density(geo, FT)
     A = operator_matrix(geo)
     b = rhs(geo, rho)
-    mu = sla.lu_solve(sla.lu_factor(A), b)
+    mu = sla.lu_solve(sla.lu_factor(A, overwrite_a=True, check_finite=False), b, check_finite=False)
+    del A
     UW = rigid_motion(geo, mu + rho)
     return dict(UW=UW, mu=mu, rho=rho, nu=mu + rho, b=b, geo=geo)
+
+
+def solve_gmres(g: dict, FT: np.ndarray, tol: float = 1e-13, restart: int = 200, workers: int = 1,
+                block: int = 256, precond: bool = True) -> dict:
+    """Mobility solve without the dense matrix, for systems too large to hold.
+
+    The same discrete equation as `solve` (eq. ModRep2Stokes: rho, the right-hand
+    side -(1/2 I + K) rho, the operator 1/2 I + K + L and the rigid-motion read
+    out), with the LU step replaced by restarted GMRES (scipy) on the operator
+    applied row block by row block, from x = 0.  With precond, GMRES runs with
+    the block-Jacobi preconditioner (each body's own diagonal block of the
+    operator, factored by LU); it changes the iteration count, not the
+    solution.  The true residual b - A mu is recomputed after every GMRES run
+    and, while ||b - A mu|| > tol ||b||, GMRES is run again on it and the
+    correction added (FP64 iterative refinement).  The final true relative
+    residual is returned.
+    """
+    from scipy.sparse.linalg import LinearOperator, gmres
+
+    geo = geometry.nodes(g)
+    rho = incident_density(geo, FT)
+    n = 2 * geo["M"]
+    bs = geo["body_start"]
+    b = -apply(geo, rho, with_L=False, block=block, workers=workers)
+    count = [0]
+
+    def mv(v):
+        count[0] += 1
+        return apply(geo, np.asarray(v).reshape(-1), block=block, workers=workers)
+
+    A = LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    Minv = None
+    if precond:
+        lus = []
+        for i in range(geo["N"]):
+            rows = np.arange(bs[i], bs[i + 1])
+            blk = (kernel_rows(geo, rows) + completion_rows(geo, rows))[:, 2 * bs[i]:2 * bs[i + 1]]
+            blk += 0.5 * np.eye(2 * rows.size)
+            lus.append(sla.lu_factor(blk))
+
+        def pv(v):
+            v = np.asarray(v).reshape(-1)
+            z = np.empty_like(v)
+            for i, lu in enumerate(lus):
+                sl = slice(2 * bs[i], 2 * bs[i + 1])
+                z[sl] = sla.lu_solve(lu, v[sl])
+            return z
+
+        Minv = LinearOperator((n, n), matvec=pv, dtype=np.float64)
+    mu = np.zeros(n)
+    r = b.copy()
+    bn = np.linalg.norm(b)
+    rel = 1.0
+    flags = []
+    for _ in range(6):
+        d, flag = gmres(A, r, rtol=0.1 * tol * bn / max(np.linalg.norm(r), 1e-300), atol=0.0, restart=restart,
+                        maxiter=50, M=Minv)
+        flags.append(int(flag))
+        mu = mu + d
+        r = b - apply(geo, mu, block=block, workers=workers)
+        rel = float(np.linalg.norm(r) / bn)
+        if rel <= tol:
+            break
+    UW = rigid_motion(geo, mu + rho)
+    return dict(UW=UW, mu=mu, rho=rho, nu=mu + rho, b=b, geo=geo, rel_residual=rel, matvecs=count[0],
+                flags=flags)
 
 
 def motion_from_density(g: dict, nu: np.ndarray) -> np.ndarray:

@@ -335,6 +335,34 @@ def _stokes_pins_pass():
     return True
 
 
+@pytest.mark.parametrize("precond", [True, False])
+def test_mobility_gmres_oracle_matches_lu(precond):
+    # the iterative mobility oracle (used where the dense matrix does not fit
+    # host memory) solves the same discrete system as the LU oracle, pinned above
+    g = synth.assemble([synth.ellipse(0, 0, 1, 0.5, 0.3, 100), synth.star(3, 0.2, 0.8, 0.2, 4, 0.5, 77),
+                        synth.ellipse(0.5, 3, 1, 0.3, 1.3, 64), synth.disc(3.2, 3.1, 0.6, 40)])
+    FT = synth.forces_torques(4, np.random.default_rng(8))
+    lu = stokes.solve(g, FT)
+    it = stokes.solve_gmres(g, FT, workers=2, block=64, precond=precond)
+    assert it["rel_residual"] <= 1e-13
+    assert np.linalg.norm(it["UW"] - lu["UW"]) / np.linalg.norm(lu["UW"]) < 1e-12
+    assert np.linalg.norm(it["mu"] - lu["mu"]) / np.linalg.norm(lu["mu"]) < 1e-11
+
+
+def test_blocked_assembly_equals_row_formulas():
+    # the dense matrices are filled block by block; every entry must be the
+    # kernel + completion + 1/2 I of the row formulas
+    g = synth.assemble([synth.star(0, 0, 1.0, 0.3, 5, 0.2, 70), synth.ellipse(3, 0, 1, 0.4, 0.5, 50)])
+    geo = geometry.nodes(g)
+    idx = np.arange(geo["M"])
+    A = laplace.operator_matrix(geo, block=16)
+    B = 0.5 * np.eye(geo["M"]) + laplace.kernel_rows(geo, idx) + laplace.completion_rows(geo, idx)
+    assert np.max(np.abs(A - B)) <= 1e-15
+    A = stokes.operator_matrix(geo, block=16)
+    B = 0.5 * np.eye(2 * geo["M"]) + stokes.kernel_rows(geo, idx) + stokes.completion_rows(geo, idx)
+    assert np.max(np.abs(A - B)) <= 1e-15
+
+
 def test_planted_mistakes_are_caught(monkeypatch):
     assert _laplace_pins_pass() and _stokes_pins_pass()
     good_nodes = geometry.nodes
