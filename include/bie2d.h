@@ -61,9 +61,14 @@ extern "C" {
                                     exists (Sections 3.1, 4.1, conservation conditions);
                                     the result is the free-space log-gauge field u = S(mu+sigma) */
 #define BIE_WARN_NOT_CONVERGED 2 /* tolerance not reached within max_iter; info has the residual */
-#define BIE_ERR_INVALID (-1)     /* bad argument: NULL pointer, N < 1, n_i < 8, non-monotone body_start */
+#define BIE_ERR_INVALID (-1)     /* bad argument: NULL pointer, N < 1, n_i < 8, non-monotone body_start,
+                                    an array in device memory of a device other than the context's */
 #define BIE_ERR_OUTSIDE (-2)     /* an interior evaluation point is not inside its body */
 #define BIE_ERR_CUDA (-3)        /* a CUDA call failed (message in bie_last_error) */
+#define BIE_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up (a grid barrier of the
+                                    cooperative Arnoldi step waited about a second for a CTA that
+                                    never arrived); the kernel returned, outputs are untouched and
+                                    the context stays usable for the next call */
 #define BIE_ERR_NOMEM (-5)       /* workspace needed exceeds the context's cap */
 
 #define BIE_KIND_LAPLACE 0       /* elastance operator, scalar density [M] */
@@ -123,10 +128,13 @@ typedef struct {
   int32_t fmm_order;     /* 0: direct pair sums; p in 2..64: the pair sums are evaluated by the
                             quadtree FMM (FP64 expansions) with order p for residuals and FP64
                             GMRES, and order ceil(p/2) for the inner solves of the refinement */
-  int32_t precond;       /* mixed: right preconditioner of the inner solves; 0: block Jacobi
-                            (one block per body, the body's own diagonal block of the inner
-                            operator inverted in FP32; bodies over 640 unknowns keep the
-                            identity), 1: none */
+  int32_t precond;       /* right preconditioner of the GMRES iterations (the FP32 inner solves
+                            of the mixed precisions, or the FP64 GMRES); 0: block Jacobi (one
+                            block per body, the body's own diagonal block of the operator
+                            GMRES iterates on, inverted in FP32; bodies over 640 unknowns, or
+                            whose inversion meets a bad pivot, keep the identity), 1: none.
+                            A right preconditioner leaves the residual GMRES minimises the
+                            true one: it changes iteration counts, not the solution */
 } bie_opts;
 
 typedef struct {
@@ -144,6 +152,10 @@ typedef struct {
   double fp32_error;           /* mixed: ||A32 x - A x|| / ||A x|| at the first refinement step,
                                   A32 the FP32-pair-sum operator of the inner solves and A the
                                   residual operator (FP64 or float-float); 0 for FP64 solves */
+  int32_t precond_fallbacks;   /* block-Jacobi preconditioner: bodies whose diagonal block met a
+                                  pivot that was not finite or tiny against the block's size during
+                                  its inversion and that therefore keep the identity */
+  int32_t pad_;
 } bie_info;
 
 /* Elastance solve (Section 3): charges q [N] -> conductor potentials phi [N].
@@ -220,8 +232,9 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
  *   - Limits: M <= BIE_NOALLOC_MAX_NODES nodes and N <= BIE_NOALLOC_MAX_BODIES
  *     bodies; larger inputs return BIE_ERR_NOMEM and nothing runs.
  *   - Every array (geometry, in, out) must be device memory of the current
- *     device (BIE_ERR_INVALID otherwise); body_start is read back with a copy
- *     that synchronises the stream.
+ *     device, or managed memory (BIE_ERR_INVALID otherwise).
+ *   - Every call reads body_start back to the host and waits for the stream
+ *     to finish that copy before it launches anything.
  *   - The first call on a device looks up the scratch array's device address
  *     (cudaGetSymbolAddress) with that device current: make that first call
  *     before any stream capture.
@@ -233,6 +246,22 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
 #define BIE_NOALLOC_MAX_BODIES 2048
 int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, const double* in,
                            double* out, void* stream);
+
+/* Test hook for the bounded device waits (no counterpart in the paper).  Arms
+ * a fault for the next fused Arnoldi step launched in this process: CTA
+ * skip_cta of that launch leaves before its first grid barrier, and that
+ * launch's barrier waits give up after `spins` polls of about 64 ns (instead of
+ * about a second).  The other CTAs then record the timeout and return, and the
+ * solve that made the launch returns BIE_ERR_TIMEOUT; nothing waits for ever.
+ * A launch with fewer than skip_cta + 1 CTAs skips no CTA.  spins <= 0 disarms
+ * the hook.  The hook is taken by one launch only. */
+void bie_test_arm_barrier_timeout(int skip_cta, long long spins);
+
+/* Test hook of the block-Jacobi safeguard (no counterpart in the paper): pivots
+ * of later block factorisations count as bad when |p| < floor (default 1e-3 for
+ * floor <= 0), so that a test can drive every body onto the identity block and
+ * check bie_info.precond_fallbacks and the result. */
+void bie_test_precond_pivot_floor(double floor);
 
 /* apply_operator with the pair sums evaluated by the quadtree fast multipole
  * method in complex variables (Laplace: Re(nu F) with F the Cauchy sum of

@@ -15,7 +15,7 @@ import re
 from . import build as _build
 
 OK, WARN_NONNEUTRAL, WARN_NOT_CONVERGED = 0, 1, 2
-ERR_INVALID, ERR_OUTSIDE, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -5
+ERR_INVALID, ERR_OUTSIDE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = -1, -2, -3, -4, -5
 LAPLACE, STOKES = 0, 1
 FP64, MIXED, MIXED_FF = 0, 1, 2
 PRECOND_BLOCK_JACOBI, PRECOND_NONE = 0, 1
@@ -41,10 +41,11 @@ class BieInfo(ctypes.Structure):
                 ("matvecs_fp64", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32),
                 ("matvecs_ff", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("constraint_residual", ctypes.c_double),
-                ("net_load", ctypes.c_double), ("fp32_error", ctypes.c_double)]
+                ("net_load", ctypes.c_double), ("fp32_error", ctypes.c_double),
+                ("precond_fallbacks", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 class BieRequest(ctypes.Structure):
@@ -127,6 +128,10 @@ def load():
     lib.bie_tune_clear.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
+    lib.bie_test_arm_barrier_timeout.argtypes = [i32, ctypes.c_longlong]
+    lib.bie_test_arm_barrier_timeout.restype = None
+    lib.bie_test_precond_pivot_floor.argtypes = [dbl]
+    lib.bie_test_precond_pivot_floor.restype = None
     _ = dbl
     _LIB = lib
     return lib
@@ -289,6 +294,21 @@ def tune(ctx: Context, geom, kind: int, precision: int, splits: int = 0, stream=
                           _stream_ptr(stream))
     del keep
     return rc, int(S.value), float(ms.value)
+
+
+def test_arm_barrier_timeout(skip_cta: int, spins: int) -> None:
+    """bie_test_arm_barrier_timeout: the next fused Arnoldi step skips CTA skip_cta
+    and its barrier waits give up after `spins` polls (spins <= 0 disarms)."""
+    load().bie_test_arm_barrier_timeout(skip_cta, spins)
+
+
+def test_precond_pivot_floor(floor: float) -> None:
+    """bie_test_precond_pivot_floor: block-Jacobi pivots below floor count as bad (<= 0: default)."""
+    load().bie_test_precond_pivot_floor(floor)
+
+
+test_arm_barrier_timeout.__test__ = False  # hooks, not tests: pytest must not collect them
+test_precond_pivot_floor.__test__ = False
 
 
 def tune_clear() -> None:

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -103,6 +104,26 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of a device other than dev (managed memory is reachable from
+// every device and passes).  Such an array is rejected before any kernel
+// could dereference it: without peer access that would be an illegal address.
+bool foreign_device_ptr(const void* p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice && at.device != dev;
+}
+
+int check_local(bie_ctx* ctx, std::initializer_list<const void*> ptrs, const char* what) {
+  for (const void* p : ptrs)
+    if (foreign_device_ptr(p, ctx->device))
+      return fail(ctx, BIE_ERR_INVALID, std::string(what) + " is device memory of another device than the context's");
+  return BIE_OK;
+}
+
 // Bump allocator over the context workspace: a sizing pass (base == nullptr)
 // and a carving pass.
 struct Arena {
@@ -132,6 +153,7 @@ struct Work {
   long long* bj_off = nullptr;
   int* bj_pairs = nullptr;
   float* bj_blocks = nullptr;
+  int* bj_fallbacks = nullptr;  // device counter of bodies left with the identity block
   double* zbuf = nullptr;
   double* arn = nullptr;  // per-CTA partials of the fused Arnoldi step
   // batched solves: per-body problem node range, first body and first entry of
@@ -268,6 +290,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
       w.bj_off = A.take<long long>(N + 1);
       w.bj_pairs = A.take<int>(N);
       w.bj_blocks = A.take<float>((size_t)bj_floats);
+      w.bj_fallbacks = A.take<int>(1);
       w.zbuf = A.take<double>(n);
     }
   }
@@ -311,6 +334,9 @@ int validate(bie_ctx* ctx, const bie_geometry* geom, std::vector<int>& bs) {
   if (geom->n_bodies < 1) return fail(ctx, BIE_ERR_INVALID, "n_bodies must be >= 1");
   if (!geom->body_start || !geom->x || !geom->y || !geom->dx || !geom->dy || !geom->ddx || !geom->ddy)
     return fail(ctx, BIE_ERR_INVALID, "a geometry array is NULL");
+  if (int rc = check_local(ctx, {geom->body_start, geom->x, geom->y, geom->dx, geom->dy, geom->ddx, geom->ddy,
+                                 geom->interior_pt}, "a geometry array"))
+    return rc;
   const int N = geom->n_bodies;
   bs.resize(N + 1);
   if (is_device_ptr(geom->body_start)) {
@@ -475,6 +501,9 @@ int validate_batch(bie_ctx* ctx, const BatchIn& b, std::vector<int>& bs, std::ve
     if (!g.body_start || !g.x || !g.y || !g.dx || !g.dy || !g.ddx || !g.ddy)
       return fail(ctx, BIE_ERR_INVALID, who + "a geometry array is NULL");
     if (!b.loads[p] || !b.outs[p]) return fail(ctx, BIE_ERR_INVALID, who + "a load or output is NULL");
+    if (int rc = check_local(ctx, {g.body_start, g.x, g.y, g.dx, g.dy, g.ddx, g.ddy, g.interior_pt, b.loads[p],
+                                   b.outs[p]}, (who + "an array").c_str()))
+      return rc;
     if (p > 0 && (g.interior_pt != nullptr) != has_ipt)
       return fail(ctx, BIE_ERR_INVALID, "batch: interior points for all problems or for none");
     has_ipt = g.interior_pt != nullptr;
@@ -659,8 +688,9 @@ int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   Op it = op;
   it.skip_stopped = true;
   CK(it.apply(op.precond ? vec(w.zbuf) : vj, vj1, &w.st->stop, s, false));
-  const ArnoldiArgs a{w.V,        ld,       n,      w.st,      w.arn, w.H, w.cs, w.sn, w.gv, w.g,
-                      w.kind,     w.bj_off, op.precond ? w.bj_blocks : nullptr, w.zbuf};
+  ArnoldiArgs a{w.V,        ld,       n,      w.st,      w.arn, w.H, w.cs, w.sn, w.gv, w.g,
+                w.kind,     w.bj_off, op.precond ? w.bj_blocks : nullptr, w.zbuf};
+  a.bj64 = op.prec == 0;  // FP64 GMRES: the preconditioner applied in FP64 arithmetic
   if (w.seg.P > 1) {
     CK(arnoldi_seg(a, w.seg, w.seg_grid, s));
   } else {
@@ -677,7 +707,7 @@ bool capturable(cudaStream_t s) {
 // not while pair-sum timing is on, whose events are per launch).  nullptr if
 // the stream cannot be captured.
 bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
-  if (ctx->prof || !capturable(s)) return nullptr;
+  if (ctx->prof || !capturable(s) || barrier_fault_armed()) return nullptr;
   const PairPlan& p = op.prec == 0 ? w.plan64 : (op.prec == 1 ? w.plan32 : w.planff);
   long long alpha_bits;
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
@@ -730,7 +760,8 @@ int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
       }
     }
     if ((rc = read_state(ctx, w, s))) return rc;
-    if (ctx->h_state->error) return fail(ctx, BIE_ERR_CUDA, "a grid barrier of the Arnoldi step timed out");
+    if (ctx->h_state->error)
+      return fail(ctx, BIE_ERR_TIMEOUT, "a grid barrier of the Arnoldi step timed out (a CTA never arrived)");
     const int done = ctx->h_state->iters - iters_before;
     for (size_t k = mark; k < ctx->pending.size(); ++k) ctx->pending[k].valid = (int)(k - mark) < done;
     resolve_timings(ctx, false);
@@ -753,7 +784,7 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
   CK(fill0(x, n, s));
   CK(residual_start(b, nullptr, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
-  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s, op.prec == 0));
   Op rop = verify ? Op{ctx, &w, 0} : op;
   rop.precond = false;  // residuals of x itself (x = P y is kept in original variables)
   int rc;
@@ -766,7 +797,7 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
       if (op.precond) {  // x += P (V y)
         CK(fill0(w.ytmp, n, s));
         CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, w.ytmp, w.grid, s));
-        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s));
+        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s, op.prec == 0));
         CK(axpy(x, w.zbuf, n, s));
       } else {
         CK(gmres_update(w.V, ld, n, w.st, w.H, w.gv, w.yv, x, w.grid, s));
@@ -787,7 +818,7 @@ int gmres(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, doubl
     CK(rop.apply(vec(x), vec(w.ytmp), nullptr, s));
     if (verify) out.matvecs64 += 1; else out.matvecs += 1;
     CK(residual_start(b, w.ytmp, w.rin, w.V, n, w.st, w.part, w.gv, 1, w.grid, s));
-    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s, op.prec == 0));
     if ((rc = read_state(ctx, w, s))) return rc;
     const KState& h2 = *ctx->h_state;
     if (h2.rnorm <= h2.tol_abs || h2.iters >= h2.maxit) {
@@ -815,7 +846,7 @@ int gmres_seg(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, d
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(KState), cudaMemcpyHostToDevice, s));
   CK(fill0(x, n, s));
   CK(residual_start_seg(b, nullptr, w.rin, w.V, w.st, w.seg, w.gv, w.m, s));
-  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+  if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s, op.prec == 0));
   Op rop = verify ? Op{ctx, &w, 0} : op;
   rop.precond = false;
   auto worst = [&](bool converged) -> int {
@@ -846,7 +877,7 @@ int gmres_seg(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, d
       if (op.precond) {  // x += P (V y)
         CK(fill0(w.ytmp, n, s));
         CK(gmres_update_seg(w.V, ld, w.st, w.seg, w.H, w.gv, w.yv, w.ytmp, w.m, w.max_plen, s));
-        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s));
+        CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.ytmp), w.zbuf, nullptr, w.bj_max_nb, s, op.prec == 0));
         CK(axpy(x, w.zbuf, n, s));
       } else {
         CK(gmres_update_seg(w.V, ld, w.st, w.seg, w.H, w.gv, w.yv, x, w.m, w.max_plen, s));
@@ -859,7 +890,7 @@ int gmres_seg(bie_ctx* ctx, Work& w, const Op& op, const double* b, double* x, d
     CK(rop.apply(vec(x), vec(w.ytmp), nullptr, s));
     if (verify) out.matvecs64 += 1; else out.matvecs += 1;
     CK(residual_start_seg(b, w.ytmp, w.rin, w.V, w.st, w.seg, w.gv, w.m, s));
-    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s));
+    if (op.precond) CK(bj_apply(w.g, w.kind, w.bj_off, w.bj_blocks, vec(w.V), w.zbuf, &w.st->stop, w.bj_max_nb, s, op.prec == 0));
     if ((rc = read_state(ctx, w, s))) return rc;
     const KState& h2 = *ctx->h_state;
     if (h2.nactive == 0 || h2.iters >= h2.maxit) return worst(h2.nactive == 0);
@@ -908,6 +939,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   } else {
     if ((rc = validate(ctx, geom, bs))) return rc;
     if (!load || !out) return fail(ctx, BIE_ERR_INVALID, "load or output pointer is NULL");
+    if ((rc = check_local(ctx, {load, out, density}, "a load, output or density array"))) return rc;
     has_ipt = geom->interior_pt != nullptr;
   }
   bie_opts o;
@@ -924,7 +956,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const int P = batch ? batch->P : 1;
   const int nload = kind == 0 ? N : 3 * N;
   Work w;
-  const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
+  const bool use_bj = o.precond == 0;
   const long long bjf = use_bj ? bj_block_floats(bs.data(), N, kind) : 0;
   Arena sz{nullptr};
   carve(sz, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, bs.data(), pb.data());
@@ -947,7 +979,11 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     const int orders[2] = {p_res, std::max(2, p_in)};
     if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err))) return rc;
   }
-  if (bjf > 0) CK(bj_setup(w.g, kind, kInnerCompletionWeight, bs.data(), w.bj_off, w.bj_pairs, w.bj_blocks, s));
+  // the block of the operator GMRES iterates on: the paper's completion (FP64
+  // GMRES) or the weighted one of the inner solves
+  if (bjf > 0)
+    CK(bj_setup(w.g, kind, o.precision == BIE_PREC_FP64 ? 0.0 : kInnerCompletionWeight, bs.data(), w.bj_off,
+                w.bj_pairs, w.bj_blocks, w.bj_fallbacks, s));
 
   const long long n = w.n;
   // right-hand side (scaled by sqrt(w))
@@ -977,7 +1013,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
   const int fres = o.fmm_order > 0 ? p_res : 0, fin = o.fmm_order > 0 ? std::max(2, p_in) : 0;
-  const Op op64{ctx, &w, 0, 0.0, fres}, op32{ctx, &w, 1, kInnerCompletionWeight, fin, bjf > 0};
+  const Op op64{ctx, &w, 0, 0.0, fres, o.precision == BIE_PREC_FP64 && bjf > 0},
+      op32{ctx, &w, 1, kInnerCompletionWeight, fin, bjf > 0};
   // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF (direct sums),
   // or the FMM of the full order
   const Op opres{ctx, &w, o.precision == BIE_PREC_MIXED_FF ? 2 : 0, 0.0, fres};
@@ -1156,6 +1193,9 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const double* nl = w.outpart + (size_t)P_used * targets * (kind + 1) + N;
   CK(cudaMemcpyAsync(ctx->h_small, w.cres, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_small + 1, nl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int* h_fb = reinterpret_cast<int*>(ctx->h_small + 3);
+  *h_fb = 0;
+  if (w.bj_fallbacks) CK(cudaMemcpyAsync(h_fb, w.bj_fallbacks, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (batch) {
     // every problem's own info and status: per-body constraint values and
     // per-problem net loads from the output kernels
@@ -1185,6 +1225,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
         q.constraint_residual = cmax / std::max(mx, 1e-300);
         q.net_load = net;
         q.fp32_error = eps32_report;
+        q.precond_fallbacks = *h_fb;  // of the whole batch
+        q.pad_ = 0;
       }
       if (st == BIE_WARN_NOT_CONVERGED || (st == BIE_WARN_NONNEUTRAL && worst_status == BIE_OK)) worst_status = st;
     }
@@ -1202,6 +1244,8 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     info->constraint_residual = ctx->h_small[0];
     info->net_load = netload;
     info->fp32_error = eps32_report;
+    info->precond_fallbacks = *h_fb;
+    info->pad_ = 0;
   }
   if (!converged) return BIE_WARN_NOT_CONVERGED;
   if (netload > 1e-12 * std::max(maxload, 1e-300) * std::max(1, N)) return BIE_WARN_NONNEUTRAL;
@@ -1255,7 +1299,7 @@ size_t workspace_bytes_batch(int kind, const int* bs, int n_bodies, const int* p
   fill_opts(opts, o);
   Work w;
   Arena sz{nullptr};
-  const bool use_bj = o.precision != BIE_PREC_FP64 && o.precond == 0;
+  const bool use_bj = o.precond == 0;
   carve(sz, w, n_bodies, bs[n_bodies], kind, o.restart, true, true, true, true, false,
         use_bj ? bj_block_floats(bs, n_bodies, kind) : 0, nprob, bs, pb);
   return sz.off;
@@ -1283,6 +1327,7 @@ int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int ord
   if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
   if (order < 2 || order > 64) return fail(ctx, BIE_ERR_INVALID, "order must be in 2..64");
   if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
+  if ((rc = check_local(ctx, {in, out}, "in or out"))) return rc;
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
   Work w;
@@ -1462,6 +1507,10 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
 
 void bie_tune_clear(void) { clear_tuned_splits(); }
 
+void bie_test_arm_barrier_timeout(int skip_cta, long long spins) { arm_barrier_fault(skip_cta, spins); }
+
+void bie_test_precond_pivot_floor(double floor) { set_bj_pivot_floor(floor); }
+
 int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, const double* in,
                    double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
@@ -1472,6 +1521,7 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
   if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED && precision != BIE_PREC_MIXED_FF)
     return fail(ctx, BIE_ERR_INVALID, "bad precision");
   if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
+  if ((rc = check_local(ctx, {in, out}, "in or out"))) return rc;
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
   Work w;

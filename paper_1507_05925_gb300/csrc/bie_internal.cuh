@@ -157,6 +157,9 @@ cudaError_t scale_by(const Geo& g, int kind, const double* in, const double* fac
 cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- pairsum.cu
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sms();
+
 // partial[s][a] (scalar for Laplace, 2-vector for Stokes) = sum over sources b
 // of split s, b != a, of the kernel without its constant, with source strength
 // sscale_b * v_b.  FP64 and FP32 variants.
@@ -231,13 +234,20 @@ cudaError_t seg_zero_below(int nprob, const long long* pnode, const double* norm
 // Largest per-body block (unknowns) that the block-Jacobi preconditioner inverts.
 constexpr int kBjMaxBlock = 640;
 
-// Block-Jacobi (per body) preconditioner of the weighted-completion operator.
+// Block-Jacobi (per body) preconditioner: each body's diagonal block of the
+// operator GMRES iterates on (alpha = 0: the paper's completion; alpha > 0:
+// the completion weighted by alpha/|Gamma_i|, alpha/W_i), inverted in FP32.  A
+// block whose inversion meets a pivot that is not finite or below the floor
+// (|p| < floor; the blocks are 1/2 I + compact) keeps the identity, and
+// *fallbacks (device int, cleared here) counts those bodies.
 long long bj_block_floats(const int* body_start_host, int N, int kind);
 cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
-                     int* pair_dev, float* blocks, cudaStream_t s);
-// z = P v (v scaled, z scaled)
+                     int* pair_dev, float* blocks, int* fallbacks, cudaStream_t s);
+// Test hook: the pivot floor of later factorisations (<= 0: the default).
+void set_bj_pivot_floor(double floor);
+// z = P v (v scaled, z scaled); f64: in FP64 arithmetic on the FP32 blocks
 cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
-                     const int* stop, int max_nb, cudaStream_t s);
+                     const int* stop, int max_nb, cudaStream_t s, bool f64 = false);
 
 // ---------------------------------------------------------------- krylov.cu
 constexpr int kMaxVecGrid = 608;  // largest grid of the vector kernels and the Arnoldi step
@@ -256,7 +266,14 @@ struct ArnoldiArgs {
   const long long* off;
   const float* blocks;
   double* z;
+  int bj64 = 0;            // apply the FP32 blocks in FP64 arithmetic (FP64 GMRES)
+  int fault_skip = -1;     // test hook: this CTA leaves before the first grid barrier
+  long long spins = 0;     // polls before a grid barrier gives up (set by the launcher)
 };
+// Test hook of the bounded barrier waits: the next Arnoldi launch skips CTA
+// skip_cta and gives up waiting after `spins` polls (spins <= 0: disarmed).
+void arm_barrier_fault(int skip_cta, long long spins);
+bool barrier_fault_armed();
 int arnoldi_grid(long long n);  // co-resident CTAs for the cooperative launch
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s);
 // h[i] = <V_i, w> for i <= j (first CGS pass)

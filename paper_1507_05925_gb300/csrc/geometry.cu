@@ -445,7 +445,7 @@ cudaError_t incident_density_scaled(const Geo& g, int kind, const double* load, 
 
 int output_splits(const Geo& g, int kind) {
   const int targets = kind == 0 ? g.N : 3 * g.N;
-  int P = (4 * 152 + targets - 1) / targets;
+  int P = (4 * device_sms() + targets - 1) / targets;
   const int maxP = (g.M + 255) / 256;
   if (P > maxP) P = maxP;
   if (P < 1) P = 1;

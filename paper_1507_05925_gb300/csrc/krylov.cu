@@ -148,34 +148,50 @@ __device__ __forceinline__ void arn_grid_sum(const double* part, int jc, double*
 
 // Grid barrier for a cooperative launch (all CTAs co-resident): arrival
 // counter plus generation number in the solver state.  The wait is bounded:
-// after about a second it records st->error and returns, so a fault can never
-// hang the GPU (the results of that step are then invalid and the host
-// reports an error).
+// after `spins` polls (about a second for the default) it records st->error,
+// sets st->stop (so that every later kernel of the iteration returns at once)
+// and gives up; a CTA that finds the error already recorded neither arrives
+// nor waits.  Returns true when the barrier failed: the caller then returns,
+// so a fault can never hang the GPU, and the host reports BIE_ERR_TIMEOUT.  The
+// counter is left as it was; the next solve starts from a cleared state.
 constexpr long long kBarrierSpins = 1LL << 24;
 
-__device__ __forceinline__ void grid_barrier(KState* st) {
+__device__ __forceinline__ bool grid_barrier(KState* st, long long spins) {
+  __shared__ int failed;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &st->bar_gen;
-    const unsigned g0 = *gen;
-    __threadfence();
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
-      st->bar_count = 0;
+    volatile int* err = &st->error;
+    int f = *err;
+    if (!f) {
+      volatile unsigned* gen = &st->bar_gen;
+      const unsigned g0 = *gen;
       __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
-      long long it = 0;
-      while (*gen == g0) {
-        if (++it > kBarrierSpins) {
-          atomicExch(&st->error, 1);
-          break;
+      if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+        st->bar_count = 0;
+        __threadfence();
+        atomicAdd(&st->bar_gen, 1u);
+      } else {
+        long long it = 0;
+        while (*gen == g0) {
+          if (*err) {
+            f = 1;
+            break;
+          }
+          if (++it > spins) {
+            atomicExch(&st->error, 1);
+            atomicExch(&st->stop, 1);
+            f = 1;
+            break;
+          }
+          __nanosleep(64);
         }
-        __nanosleep(64);
       }
+      __threadfence();
     }
-    __threadfence();
+    failed = f;
   }
   __syncthreads();
+  return failed != 0;
 }
 
 // z = B v for one body's block-Jacobi block B (column-major nb x nb, FP32;
@@ -236,6 +252,25 @@ __device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long 
   }
 }
 
+// z = B v in FP64 arithmetic on the FP32 block (the FP64 GMRES: the
+// preconditioner must be one fixed linear map to FP64 rounding, so that the
+// Arnoldi relation A P V = V H holds to FP64 accuracy and x = P (V y) is the
+// minimiser GMRES computed).
+__device__ __forceinline__ void bj_body_apply64(const float* __restrict__ B, int nb, const double* wd,
+                                                double* __restrict__ z) {
+  for (int r = threadIdx.x; r < nb; r += kBV) {
+    double s0 = 0.0, s1 = 0.0;
+    int col = 0;
+#pragma unroll 4
+    for (; col + 2 <= nb; col += 2) {
+      s0 = fma((double)B[(long long)col * nb + r], wd[col], s0);
+      s1 = fma((double)B[(long long)(col + 1) * nb + r], wd[col + 1], s1);
+    }
+    if (col < nb) s0 = fma((double)B[(long long)col * nb + r], wd[col], s0);
+    z[r] = s0 + s1;
+  }
+}
+
 template <bool NARROW>
 __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) {
   KState* st = a.st;
@@ -244,6 +279,7 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
   __shared__ double hs1[kMaxBasis], hs2[kMaxBasis];
   __shared__ double red[kBV / 32];
   __shared__ float ws[kBjMaxBlock];
+  __shared__ double wsd[kBjMaxBlock];
   const int j = st->j, jc = j + 1;
   const long long n = a.n, ld = a.ld;
   double* __restrict__ w = a.V + (long long)(j + 1) * ld;
@@ -254,14 +290,15 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
   double* part3 = part2 + G * kMaxBasis;
   // h1 = V^T w
   arn_block_dots<NARROW>(a.V, ld, w, n, jc, part1 + blockIdx.x * kMaxBasis, sh);
-  grid_barrier(st);
+  if ((int)blockIdx.x == a.fault_skip) return;  // test hook: this CTA never arrives
+  if (grid_barrier(st, a.spins)) return;
   arn_grid_sum(part1, jc, hs1);
   // w -= V h1; h2 = V^T w
   for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride)
     w[k] = w[k] - combine(a.V, ld, k, hs1, jc);
   __syncthreads();
   arn_block_dots<NARROW>(a.V, ld, w, n, jc, part2 + blockIdx.x * kMaxBasis, sh);
-  grid_barrier(st);
+  if (grid_barrier(st, a.spins)) return;
   arn_grid_sum(part2, jc, hs2);
   // w -= V h2; ||w||^2
   double nrm = 0.0;
@@ -272,7 +309,7 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
   }
   nrm = block_sum<kBV>(nrm, red);
   if (threadIdx.x == 0) part3[blockIdx.x * kMaxBasis] = nrm;
-  grid_barrier(st);
+  if (grid_barrier(st, a.spins)) return;
   __shared__ double hn_s;
   if (threadIdx.x < 32) {
     const double t = warp_gather(part3, kMaxBasis);
@@ -342,10 +379,16 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
     for (int r = threadIdx.x; r < nb; r += kBV) {
       const double v = __ldcg(w + a0 + r) * inv;
       w[a0 + r] = v;
-      ws[r] = (float)v;
+      if (a.bj64)
+        wsd[r] = v;
+      else
+        ws[r] = (float)v;
     }
     __syncthreads();
-    bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
+    if (a.bj64)
+      bj_body_apply64(a.blocks + a.off[i], nb, wsd, a.z + a0);
+    else
+      bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
     __syncthreads();
   }
 }
@@ -413,6 +456,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
   __shared__ double red[kBV / 32];
   __shared__ double cell;
   __shared__ float ws[kBjMaxBlock];
+  __shared__ double wsd[kBjMaxBlock];
   __shared__ float4 red4[kBV];
   const int j = st->j, jc = j + 1;
   const long long ld = a.ld;
@@ -427,7 +471,8 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
     if (sg.ps[p].stop_j <= j) continue;
     seg_block_dots(a.V, ld, w, sg.ibeg[it], sg.ibeg[it + 1], jc, part1 + (long long)it * kMaxBasis);
   }
-  grid_barrier(st);
+  if ((int)blockIdx.x == a.fault_skip) return;  // test hook: this CTA never arrives
+  if (grid_barrier(st, a.spins)) return;
   // w -= V h1; h2 = V^T w
   for (int it = blockIdx.x; it < sg.nitem; it += G) {
     const int p = sg.iprob[it];
@@ -438,7 +483,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
     __syncthreads();
     seg_block_dots(a.V, ld, w, e0, e1, jc, part2 + (long long)it * kMaxBasis);
   }
-  grid_barrier(st);
+  if (grid_barrier(st, a.spins)) return;
   // w -= V h2; ||w||^2 per range
   for (int it = blockIdx.x; it < sg.nitem; it += G) {
     const int p = sg.iprob[it];
@@ -454,7 +499,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
     nrm = block_sum<kBV>(nrm, red);
     if (threadIdx.x == 0) part3[(long long)it * kMaxBasis] = nrm;
   }
-  grid_barrier(st);
+  if (grid_barrier(st, a.spins)) return;
   // Hessenberg column, rotations and stopping test of each problem
   const int m = st->m;
   for (int p = blockIdx.x; p < sg.P; p += G) {
@@ -533,10 +578,16 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
     for (int r = threadIdx.x; r < nb; r += kBV) {
       const double v = __ldcg(w + a0 + r) * inv;
       w[a0 + r] = v;
-      ws[r] = (float)v;
+      if (a.bj64)
+        wsd[r] = v;
+      else
+        ws[r] = (float)v;
     }
     __syncthreads();
-    bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
+    if (a.bj64)
+      bj_body_apply64(a.blocks + a.off[i], nb, wsd, a.z + a0);
+    else
+      bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
   }
 }
 
@@ -740,21 +791,7 @@ int vec_grid(long long n) {
 }
 
 // The narrow instance for grids of at most two CTAs per SM.
-bool arnoldi_narrow(long long n) {
-  static std::atomic<int> sms[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (sms[dev].load() == 0) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
-      cudaGetLastError();
-      v = 152;
-    }
-    sms[dev].store(v);
-  }
-  return vec_grid(n) <= 2 * sms[dev].load();
-}
+bool arnoldi_narrow(long long n) { return vec_grid(n) <= 2 * device_sms(); }
 
 int arnoldi_grid(long long n) {
   static std::atomic<int> coresident[64][2];
@@ -775,8 +812,34 @@ int arnoldi_grid(long long n) {
   return std::min(vec_grid(n), coresident[dev][narrow].load());
 }
 
+namespace {
+// Test hook of the bounded barrier waits (bie_test_arm_barrier_timeout): taken
+// by the next Arnoldi launch only.
+std::atomic<long long> g_fault_spins{0};
+std::atomic<int> g_fault_skip{-1};
+
+void take_fault(ArnoldiArgs& args) {
+  const long long sp = g_fault_spins.exchange(0);
+  if (sp > 0) {
+    args.fault_skip = g_fault_skip.load();
+    args.spins = sp;
+  } else {
+    args.fault_skip = -1;
+    args.spins = kBarrierSpins;
+  }
+}
+}  // namespace
+
+void arm_barrier_fault(int skip_cta, long long spins) {
+  g_fault_skip.store(skip_cta);
+  g_fault_spins.store(spins > 0 ? spins : 0);
+}
+
+bool barrier_fault_armed() { return g_fault_spins.load() > 0; }
+
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s) {
   ArnoldiArgs args = a;
+  take_fault(args);
   void* params[] = {&args};
   const void* fn = arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>;
   const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBV), params, 0, s);
@@ -837,6 +900,7 @@ int arnoldi_seg_grid(long long n) {
 
 cudaError_t arnoldi_seg(const ArnoldiArgs& a, const SegArgs& sg, int grid, cudaStream_t s) {
   ArnoldiArgs args = a;
+  take_fault(args);
   SegArgs sargs = sg;
   void* params[] = {&args, &sargs};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi_seg, dim3(grid), dim3(kBV), params, 0, s);

@@ -45,13 +45,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 char* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-bool device_ptr(const void* p) {
+// Device memory of device `dev`, or managed memory.  Device memory of another
+// GPU is refused: a kernel here would read it as a peer address (an illegal
+// address without peer access).
+bool device_ptr(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 struct Carver {
@@ -80,11 +83,16 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
   const int N = geom->n_bodies;
   if (N < 1) return BIE_ERR_INVALID;
   if (N > kNoallocMaxBodies) return BIE_ERR_NOMEM;
-  // every array must already be on the device: nothing is staged
+  // every array must already be on the current device: nothing is staged
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
   const void* arrays[] = {geom->body_start, geom->x, geom->y, geom->dx, geom->dy, geom->ddx, geom->ddy, in, out};
   for (const void* p : arrays)
-    if (!device_ptr(p)) return BIE_ERR_INVALID;
-  if (geom->interior_pt && !device_ptr(geom->interior_pt)) return BIE_ERR_INVALID;
+    if (!device_ptr(p, cur)) return BIE_ERR_INVALID;
+  if (geom->interior_pt && !device_ptr(geom->interior_pt, cur)) return BIE_ERR_INVALID;
   int bs_host[kNoallocMaxBodies + 1];
   if (cudaMemcpyAsync(bs_host, geom->body_start, (N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||

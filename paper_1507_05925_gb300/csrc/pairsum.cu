@@ -727,7 +727,7 @@ const DeviceShape& device_shape() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][0], k_pair_ff<0, false>, kBF, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t.occ[2][1], k_pair_ff<1, false>, kBF, 0);
     cudaGetLastError();
-    if (t.nsm <= 0) t.nsm = 152;
+    if (t.nsm <= 0) t.nsm = 1;  // a failed query plans for one SM: slower, still correct
     for (auto& row : t.occ)
       for (int& o : row)
         if (o <= 0) o = 4;
@@ -737,6 +737,8 @@ const DeviceShape& device_shape() {
 }
 
 }  // namespace
+
+int device_sms() { return device_shape().nsm; }
 
 // Choose the source split so that one wave fills every SM with as many
 // blocks as can be resident: blocks = target blocks x splits ~ SMs x occupancy.

@@ -1,13 +1,20 @@
-// Block-Jacobi preconditioner for the FP32 inner solves of the refinement.
+// Block-Jacobi preconditioner of the GMRES iterations: the FP32 inner solves
+// of the refinement (operator with the per-body weighted completion) and the
+// FP64 GMRES (the paper's completion).
 //
-// The inner operator is the second-kind operator with the per-body weighted
-// completion (sqrt(w)-scaled).  Its diagonal block for body i,
+// The operator is the second-kind operator, sqrt(w)-scaled.  Its diagonal
+// block for body i,
 //   B_i = 1/2 I + D (K_ii + C_i L_ii) D^{-1}     (Laplace: n_i x n_i; Stokes: 2n_i x 2n_i)
-// is assembled in FP32 (from FP64 coordinate differences) directly in shared
-// memory and inverted in place by blocked Gauss-Jordan elimination without
-// pivoting: the blocks are 1/2 I + compact, their pivots stay near 1/2 and
-// their condition numbers are small, so no pivoting is needed (an FP32 inverse
-// accurate to ~1e-6 is far more than a preconditioner needs).  A block of
+// (C_i = 1 for the paper's L) is assembled in FP32 (from hi/lo coordinate
+// differences) directly in shared memory and inverted in place by blocked
+// Gauss-Jordan elimination without pivoting: the blocks are 1/2 I + compact,
+// their pivots stay near 1/2 on the shapes measured (0.36 - 0.50) and an FP32
+// inverse accurate to ~1e-6 is far more than a preconditioner needs.  Every
+// pivot is checked: one that is not finite or smaller in magnitude than the
+// floor (default 1e-3, 1/500 of the identity part), or a non-finite entry of
+// the finished inverse, makes the body keep the identity block (counted in
+// bie_info.precond_fallbacks), so a nearly singular block can slow GMRES down
+// but never poisons it with NaN or huge entries.  A block of
 // nb <= 128 unknowns is inverted by one CTA; nb <= 448 by a cluster of four
 // CTAs and nb <= 640 by one of eight, each CTA holding a slice of the columns
 // and reading the pivot panels of the others through distributed shared
@@ -19,6 +26,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/bie2d.h"
@@ -52,8 +60,9 @@ __host__ __device__ __forceinline__ size_t gj_smem_floats(int nb, int cs) {
   return (size_t)gj_ld(nb) * h + (size_t)h * kPB + 2 * kPB + 8 * (size_t)h;
 }
 
-// Entry (row r, column c) of the inner operator's diagonal block of body i
-// (sqrt(w)-scaled, weighted completion), in FP32: coordinate differences from
+// Entry (row r, column c) of the operator's diagonal block of body i
+// (sqrt(w)-scaled; alpha > 0: completion weighted by alpha/|Gamma_i| and
+// alpha/W_i, alpha = 0: the paper's completion), in FP32: coordinate differences from
 // the hi/lo split (x = x_hi + x_lo, exact leading differences as in the near
 // tiles of the pair sum), the column's node data staged in shared memory.
 struct BlockRow {
@@ -64,8 +73,8 @@ struct BlockRow {
   int al;
   __device__ BlockRow(const Geo& g, int kind_, int i, int r, double alpha) : kind(kind_) {
     const int a0 = g.body_start[i];
-    cf = (float)(alpha / g.len[i]);
-    ct = kind == 1 ? (float)(alpha / g.W[i]) : 0.f;
+    cf = alpha > 0.0 ? (float)(alpha / g.len[i]) : 1.0f;
+    ct = kind == 1 ? (alpha > 0.0 ? (float)(alpha / g.W[i]) : 1.0f) : 0.f;
     a = a0 + (kind == 1 ? r >> 1 : r);
     al = kind == 1 ? r & 1 : 0;
     pa = g.pf[a];
@@ -138,8 +147,10 @@ template <int CS>
 __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, double alpha,
                                                            const int* __restrict__ list,
                                                            const long long* __restrict__ off,
-                                                           float* __restrict__ blocks) {
+                                                           float* __restrict__ blocks, float floor,
+                                                           int* __restrict__ fallbacks) {
   extern __shared__ float sm[];
+  __shared__ int bad_s;  // this CTA met a bad pivot or a non-finite entry
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int i = list[blockIdx.x / CS];
   const int nb = (g.body_start[i + 1] - g.body_start[i]) * (kind + 1);
@@ -152,6 +163,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
   float4* colw = colp + h;                                       // [h] column node data
   const int r = threadIdx.x;
   const bool live = r < nb;
+  if (threadIdx.x == 0) bad_s = 0;
   {
     const int a0 = g.body_start[i];
     const double xc = g.xc[i], yc = g.yc[i];
@@ -186,7 +198,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
             for (int u = 0; u < kPB; ++u) rb[u] = pr[u];
           }
           __syncthreads();
-          const float ip = 1.0f / rb[t];
+          const float pv = rb[t];
+          if (threadIdx.x == 0 && !(fabsf(pv) >= floor && isfinite(pv))) bad_s = 1;
+          const float ip = 1.0f / pv;
           if (r == k0 + t) {
 #pragma unroll
             for (int u = 0; u < kPB; ++u) pr[u] = (u == t) ? ip : pr[u] * ip;
@@ -226,22 +240,45 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
     }
     __syncthreads();
   }
-  if constexpr (CS > 1) cg::this_cluster().sync();  // no CTA leaves while the last panel is read
+  // an entry that overflowed in the updates also rejects the block
+  if (live) {
+    bool nf = false;
+    for (int j = 0; j < nc; ++j) nf |= !isfinite(A[j * ld + r]);
+    if (nf) bad_s = 1;
+  }
+  // every CTA of the cluster learns whether any of them rejected the block
+  // (the first sync also keeps every CTA alive while the last panel is read)
+  int bad;
+  if constexpr (CS > 1) {
+    cg::this_cluster().sync();
+    bad = 0;
+    for (int q = 0; q < CS; ++q) bad |= *cg::this_cluster().map_shared_rank(&bad_s, q);
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+    bad = bad_s;
+  }
+  if (bad && rank == 0 && threadIdx.x == 0) atomicAdd(fallbacks, 1);
   float* B = blocks + off[i];
   if (live)
-    for (int j = 0; j < nc; ++j) B[(long long)(c0 + j) * nb + r] = A[j * ld + r];
+    for (int j = 0; j < nc; ++j) B[(long long)(c0 + j) * nb + r] = bad ? (c0 + j == r ? 1.f : 0.f) : A[j * ld + r];
 }
 
 // z = P v: z_i = B_i^{-1} v_i per body (identity for bodies left out).  CTA
 // (i, y) computes rows [64 y, 64 y + 64) of body i with four column groups of
 // 64 threads, reduced in shared memory; each warp reads 32 consecutive rows of
 // one column (coalesced).
+// F64: the same product in FP64 arithmetic (v not rounded to FP32), so that
+// P is one fixed linear map to FP64 rounding (FP64 GMRES).
+template <bool F64>
 __global__ void __launch_bounds__(kBA) k_bj_apply(Geo g, int kind, const long long* __restrict__ off,
                                                   const float* __restrict__ blocks, VecRef vr, double* __restrict__ z,
                                                   const int* __restrict__ stop) {
+  using T = typename std::conditional<F64, double, float>::type;
   if (stop && *stop) return;
-  extern __shared__ float vs[];
-  __shared__ float part[kBA];
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  T* vs = reinterpret_cast<T*>(vs_raw);
+  __shared__ T part[kBA];
   const double* v = vr.ptr();
   const int i = blockIdx.x;
   const int c = kind + 1;
@@ -254,20 +291,20 @@ __global__ void __launch_bounds__(kBA) k_bj_apply(Geo g, int kind, const long lo
     if (grp == 0 && r < nb) z[a0 + r] = v[a0 + r];
     return;
   }
-  for (int e = threadIdx.x; e < nb; e += kBA) vs[e] = (float)v[a0 + e];
+  for (int e = threadIdx.x; e < nb; e += kBA) vs[e] = (T)v[a0 + e];
   __syncthreads();
   const float* B = blocks + off[i];
-  float acc = 0.f;
+  T acc = 0;
   if (r < nb) {
     const int per = (nb + kApplyGroups - 1) / kApplyGroups;
     const int cb = grp * per, ce = min(nb, cb + per);
 #pragma unroll 4
-    for (int col = cb; col < ce; ++col) acc = fmaf(B[(long long)col * nb + r], vs[col], acc);
+    for (int col = cb; col < ce; ++col) acc = fma((T)B[(long long)col * nb + r], vs[col], acc);
   }
   part[threadIdx.x] = acc;
   __syncthreads();
   if (grp == 0 && r < nb) {
-    float t = part[lr];
+    T t = part[lr];
 #pragma unroll
     for (int q = 1; q < kApplyGroups; ++q) t += part[q * kApplyRows + lr];
     z[a0 + r] = (double)t;
@@ -288,9 +325,12 @@ long long bj_block_floats(const int* body_start_host, int N, int kind) {
 namespace {
 
 // Launch of k_bj_factor<CS> over count bodies of list, one thread per row.
+float g_pivot_floor = 0.f;  // test hook (0: the default floor)
+constexpr float kPivotFloor = 1e-3f;
+
 template <int CS>
 cudaError_t launch_factor(const Geo& g, int kind, double alpha, const int* list, int count, int threads, size_t smem,
-                          const long long* off, float* blocks, cudaStream_t s) {
+                          const long long* off, float* blocks, int* fallbacks, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_bj_factor<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -305,15 +345,18 @@ cudaError_t launch_factor(const Geo& g, int kind, double alpha, const int* list,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = CS > 1 ? 1 : 0;
-  e = cudaLaunchKernelEx(&cfg, k_bj_factor<CS>, g, kind, alpha, list, off, blocks);
+  const float floor = g_pivot_floor > 0.f ? g_pivot_floor : kPivotFloor;
+  e = cudaLaunchKernelEx(&cfg, k_bj_factor<CS>, g, kind, alpha, list, off, blocks, floor, fallbacks);
   note_launches(1);
   return e;
 }
 
 }  // namespace
 
+void set_bj_pivot_floor(double floor) { g_pivot_floor = floor > 0.0 ? (float)floor : 0.f; }
+
 cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
-                     int* list_dev, float* blocks, cudaStream_t s) {
+                     int* list_dev, float* blocks, int* fallbacks, cudaStream_t s) {
   // bodies by kernel: one CTA (nb <= 128), clusters of four (<= 448) and eight (<= 640) CTAs
   constexpr int kCs[3] = {1, 4, 8};
   std::vector<long long> off(g.N + 1, 0);
@@ -333,6 +376,8 @@ cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start
   for (const auto& l : lists) all.insert(all.end(), l.begin(), l.end());
   cudaError_t e = cudaMemcpyAsync(off_dev, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(fallbacks, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   if (!all.empty()) {
     e = cudaMemcpyAsync(list_dev, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
@@ -343,9 +388,9 @@ cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start
     if (count == 0) continue;
     const int threads = (max_nb[c] + 31) / 32 * 32;
     const int* l = list_dev + at;
-    e = c == 0   ? launch_factor<1>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s)
-        : c == 1 ? launch_factor<4>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s)
-                 : launch_factor<8>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, s);
+    e = c == 0   ? launch_factor<1>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, fallbacks, s)
+        : c == 1 ? launch_factor<4>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, fallbacks, s)
+                 : launch_factor<8>(g, kind, alpha, l, count, threads, smem[c], off_dev, blocks, fallbacks, s);
     if (e != cudaSuccess) return e;
     at += count;
   }
@@ -354,10 +399,13 @@ cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start
 }
 
 cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
-                     const int* stop, int max_nb, cudaStream_t s) {
+                     const int* stop, int max_nb, cudaStream_t s, bool f64) {
   const dim3 grid(g.N, (max_nb + kApplyRows - 1) / kApplyRows);
-  k_bj_apply<<<grid, kBA, (size_t)std::min(max_nb, kMaxBlock) * sizeof(float), s>>>(g, kind, off_dev, blocks, v, z,
-                                                                                     stop);
+  const size_t nv = (size_t)std::min(max_nb, kMaxBlock);
+  if (f64)
+    k_bj_apply<true><<<grid, kBA, nv * sizeof(double), s>>>(g, kind, off_dev, blocks, v, z, stop);
+  else
+    k_bj_apply<false><<<grid, kBA, nv * sizeof(float), s>>>(g, kind, off_dev, blocks, v, z, stop);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -263,8 +263,11 @@ def test_gpu_closed_forms(ctx):
     rc, _ = bie.mobility_solve(ctx, to_dev(g), torch.tensor([0.7, -0.4, 1.1], dtype=torch.float64, device="cuda"), UW)
     assert rc == bie.WARN_NONNEUTRAL
     u = UW.cpu().numpy()
-    assert np.max(np.abs(u[:2] - np.array([0.7, -0.4]) * (0.5 - math.log(1.7)) / (4 * math.pi))) < 1e-14
-    assert abs(u[2] - 1.1 / (4 * math.pi * 1.7**2)) < 1e-14
+    # the solve stops at a relative residual of 1e-12; the single-layer sum that
+    # gives v adds terms about 40 times v itself (|G| ~ 0.04 against v ~ 2e-3),
+    # so the density's 1e-12 shows as up to ~1e-13 in v
+    assert np.max(np.abs(u[:2] - np.array([0.7, -0.4]) * (0.5 - math.log(1.7)) / (4 * math.pi))) < 1e-13
+    assert abs(u[2] - 1.1 / (4 * math.pi * 1.7**2)) < 1e-13
 
 
 def test_two_disc_mobility_table_gpu(ctx):
@@ -381,12 +384,35 @@ def test_full_size_operator_rows(ctx, wl, kind):
         assert err <= tol
 
 
+FULL_SIZE_GOLDEN = {"stars100_M25600": "stars100_M25600_elastance.txt",
+                    "ellipses400_M51200": "ellipses400_M51200_mobility.txt"}
+
+
+def _full_size_oracle(wl, g, load):
+    """The oracle's solution of a full-size workload, stored by
+    tests/golden/make_fullsize.py (dense LU for the 100 stars; GMRES on
+    row-blocked operator applications to a true relative residual of 1e-13 for
+    the 400 ellipses), after checking that the inputs are the ones it solved."""
+    from conftest import read_golden
+    kv, rows = read_golden(FULL_SIZE_GOLDEN[wl])
+    assert int(kv["M"][0]) == g["x"].size and int(kv["N"][0]) == g["body_start"].size - 1
+    for key, val in (("sum_x", np.sum(g["x"])), ("sum_y", np.sum(g["y"])), ("sum_load", np.sum(np.abs(load)))):
+        assert abs(val - kv[key][0]) <= 1e-12 * abs(kv[key][0]), (key, val, kv[key][0])
+    if "rel_residual" in kv:
+        assert kv["rel_residual"][0] <= 1e-13
+    return np.array(rows).reshape(-1)
+
+
 @pytest.mark.parametrize("wl,kind", [("stars100_M25600", 0), ("ellipses400_M51200", 1)])
-def test_full_size_solve_properties(ctx, wl, kind):
+def test_full_size_solves_match_oracle(ctx, wl, kind):
+    # the headline workloads, every precision, element by element against the
+    # oracle's own solution of the same discrete system (eqs. ModRep2,
+    # ModRep2Stokes), plus the sampled-row and constraint checks
     g = synth.WORKLOADS[wl]()
     geo = geometry.nodes(g)
     N, M = geo["N"], geo["M"]
     load = g["q"] if kind == 0 else g["FT"].reshape(-1)
+    ref = _full_size_oracle(wl, g, load)
     gd = to_dev(g)
     outs = {}
     for prec in (bie.MIXED_FF, bie.MIXED, bie.FP64):
@@ -396,8 +422,12 @@ def test_full_size_solve_properties(ctx, wl, kind):
         rc, info = fn(ctx, gd, torch.from_numpy(load).cuda(), out, dens, opts=bie.make_opts(precision=prec))
         torch.cuda.synchronize()
         assert rc == bie.OK, (rc, info)
-        print(f"{wl} prec={prec}: {info}")
-        outs[prec] = (out.cpu().numpy(), dens.cpu().numpy(), info)
+        res = out.cpu().numpy()
+        e2, emax = rel2(res, ref), float(np.max(np.abs(res - ref)) / np.max(np.abs(ref)))
+        print(f"{wl} prec={prec}: vs oracle rel2 {e2:.2e} relmax {emax:.2e} {info}")
+        assert e2 <= TOL_SOLVE
+        assert emax <= TOL_SOLVE
+        outs[prec] = (res, dens.cpu().numpy(), info)
     for prec in (bie.MIXED, bie.MIXED_FF):
         res, nu, info = outs[prec]
         _check_full_size(g, geo, kind, res, nu, info, outs[bie.FP64][0])

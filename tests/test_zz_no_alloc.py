@@ -4,9 +4,10 @@ allocation, or a loop that must not synchronise through cudaMalloc/cudaFree).
 
 Its output must equal apply_operator's within the operator tolerances of the
 parity tests (FP64: 1e-13; FP32 pair sums: the FP32 bound, since a different
-source split regroups the FP32 tile sums), on two calls in a row with
-different sizes, so that what an earlier call left in the shared scratch array
-cannot leak into a later result.
+source split regroups the FP32 tile sums; float-float: 1e-12), on two calls in
+a row with different sizes, so that what an earlier call left in the shared
+scratch array cannot leak into a later result.  It is also compared with the
+FP64 oracle directly, and run once on a caller-made stream.
 This file is collected last on purpose.
 """
 import numpy as np
@@ -15,11 +16,13 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import synth  # noqa: E402
+from oracle import geometry, laplace, stokes  # noqa: E402
 from paper_1507_05925_gb300 import bie  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {bie.FP64: {0: 1e-13, 1: 1e-13}, bie.MIXED: {0: 2e-6, 1: 5e-6}}  # as in test_gpu_parity
+# as in test_gpu_parity: FP64, FP32 pair sums, float-float pair sums
+TOL = {bie.FP64: {0: 1e-13, 1: 1e-13}, bie.MIXED: {0: 2e-6, 1: 5e-6}, bie.MIXED_FF: {0: 1e-12, 1: 1e-12}}
 
 
 def _dev(g):
@@ -29,7 +32,7 @@ def _dev(g):
 
 
 @pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
-@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED])
+@pytest.mark.parametrize("prec", [bie.FP64, bie.MIXED, bie.MIXED_FF])
 def test_noalloc_matches_apply_operator(kind, prec):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -50,6 +53,33 @@ def test_noalloc_matches_apply_operator(kind, prec):
         torch.cuda.synchronize()
         err = (got - ref).abs().max().item() / ref.abs().max().item()
         assert err <= TOL[prec][kind], err
+        # and against the FP64 oracle itself
+        ora = (laplace if kind == 0 else stokes).apply(geometry.nodes(g), v.cpu().numpy())
+        err_o = np.max(np.abs(got.cpu().numpy() - ora)) / np.max(np.abs(ora))
+        assert err_o <= TOL[prec][kind], err_o
+    ctx.close()
+
+
+def test_noalloc_on_a_caller_stream():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_05925_gb300 import build
+    build.build()
+    ctx = bie.Context(0)
+    g = synth.star_grid(seed=5, rows=2, cols=3, n=160)
+    gd = _dev(g)
+    v = torch.from_numpy(np.random.default_rng(4).standard_normal(2 * g["x"].size)).cuda()
+    ref = torch.empty_like(v)
+    got = torch.full_like(v, float("nan"))
+    assert bie.apply_operator(ctx, gd, bie.STOKES, bie.MIXED_FF, v, ref) == bie.OK
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        assert bie.apply_operator_noalloc(gd, bie.STOKES, bie.MIXED_FF, v, got, stream=st) == bie.OK
+    st.synchronize()
+    err = (got - ref).abs().max().item() / ref.abs().max().item()
+    assert err <= TOL[bie.MIXED_FF][1], err
     ctx.close()
 
 
