@@ -60,6 +60,8 @@ def parse():
                     help="headline path: FP32 pair sums in refinement with an FP64 (mixed) or a "
                          "float-float (mixed_ff) residual")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--four-disc-steps", type=int, default=100,
+                    help="solves of the four-disc case (M = 512) per precision, host clock (0 = skip)")
     ap.add_argument("--splits", type=int, default=0,
                     help="--kernel: install this pair-sum split count instead of searching (0 = search)")
     ap.add_argument("--no-tune", action="store_true",
@@ -68,6 +70,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="served stream: mixed elastance/mobility requests (0 = skip)")
     ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--serve-hbm-fraction", type=float, default=0.05,
+                    help="served stream: admission cap as a fraction of the device's HBM")
+    ap.add_argument("--cpu-1core", action="store_true",
+                    help="also time the full oracle solve with one BLAS thread (about 8 minutes)")
     ap.add_argument("--serve-batch", type=int, default=8,
                     help="served stream again with up to this many queued requests solved together (<= 1: skip)")
     ap.add_argument("--fmm-order", type=int, default=36)
@@ -116,35 +122,52 @@ def job_rate(world: int, steps: int, seconds: float) -> float:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
+# CPU oracle baseline: the full solve of the benchmark workload
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(full_M: int, n_sample_bodies: int = 16):
-    """Time the FP64 oracle on a subset of the same workload and scale to full size.
+def oracle_full_solve(n_stars: int = 100):
+    """Time the FP64 oracle, as it stands, on the benchmark workload: one complete
+    oracle.laplace.solve (dense Nystrom assembly, LU with partial pivoting,
+    potentials at the interior points) of the 100-star problem (M = 25,600;
+    n_stars < 100: the first rows of the same grid, used only to warm up)."""
+    from oracle import laplace
 
-    The oracle's cost is dense assembly + output (O(M^2)) plus LU (O(M^3));
-    each part is timed and scaled to the full M separately.
-    """
-    import scipy.linalg as sla
-
-    from oracle import geometry, laplace
-
-    g = synth.star_grid(seed=1000, rows=4, cols=n_sample_bodies // 4)
-    M = g["x"].size
+    g = synth.star_grid(seed=1000) if n_stars >= 100 else synth.star_grid(seed=1000, rows=4, cols=n_stars // 4)
     t0 = time.perf_counter()
-    geo = geometry.nodes(g)
-    sigma = laplace.incident_density(geo, g["q"])
-    A = laplace.operator_matrix(geo)
-    b = laplace.rhs(geo, sigma)
-    t1 = time.perf_counter()
-    lu = sla.lu_factor(A)
-    mu = sla.lu_solve(lu, b)
-    t2 = time.perf_counter()
-    pts = geometry.interior_points(geo)
-    laplace.single_layer_at(geo, mu + sigma, pts["z0x"], pts["z0y"])
-    t3 = time.perf_counter()
-    s = full_M / M
-    t_full = (t1 - t0 + t3 - t2) * s * s + (t2 - t1) * s**3
-    return dict(seconds_sample=t3 - t0, seconds_full_estimate=t_full, M_sample=M)
+    res = laplace.solve(g, g["q"])
+    return dict(seconds=time.perf_counter() - t0, M=int(g["x"].size), phi=res["phi"])
+
+
+def oracle_single_core_seconds():
+    """The same full oracle solve with one BLAS thread, in a child process (the
+    thread count of OpenBLAS is fixed when numpy is first imported)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_full_solve(); print(json.dumps({'seconds': r['seconds']}))" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def stored_oracle(name: str):
+    """The oracle's solution of a full-size workload as stored in tests/golden
+    (written by tests/golden/make_fullsize.py, which calls only the oracle)."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            try:
+                rows.append([float(x) for x in line.split()])
+            except ValueError:
+                pass
+    return np.array(rows).reshape(-1)
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
 
 
 def cpu_cores():
@@ -230,27 +253,33 @@ def measured_peaks():
 
 
 def run_reference(args, rank, world):
-    """The oracle arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    """The oracle arm: the FP64 CPU oracle, as it stands, on the host cores.  Every
+    timed step is one complete oracle solve of the benchmark workload (about 43 s
+    on 16 Grace cores); the warm-up steps solve the first 16 stars only (they
+    load the libraries and start the BLAS threads)."""
     if rank != 0:
         return
-    M = 25600
     for _ in range(args.warmup):
-        oracle_sample_rate(M, 8)
-    per = []
+        oracle_full_solve(16)
+    secs = []
     for _ in range(args.steps):
-        per.append(oracle_sample_rate(M, 8))
-    secs = [p["seconds_full_estimate"] for p in per]
+        r = oracle_full_solve()
+        secs.append(r["seconds"])
     value = len(secs) / sum(secs)
-    sample = (f"oracle (dense assembly + LU + output, FP64, numpy/scipy) on 8 of the 100 stars "
-              f"(M={per[0]['M_sample']}), O(M^2) parts scaled by (25600/M)^2 and LU by (25600/M)^3")
+    ref = stored_oracle("stars100_M25600_elastance.txt")
+    sample = ("the full workload every step: oracle.laplace.solve of the 100 stars (M = 25,600: dense "
+              "Nystrom assembly, LU with partial pivoting, potentials), FP64, numpy/scipy")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(secs) / len(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "M": M, "N": 100, "tol": 1e-12},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "M": 25600, "N": 100, "nodes_per_body": 256,
+                                        "tol": 1e-12, "precision": "f64 dense LU",
+                                        "parallelism": f"replicas x{world}"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_vs_stored_solution": rel_err(r["phi"], ref) if ref is not None else None,
     }))
 
 
@@ -274,7 +303,8 @@ def run_serving(args, rank, local):
         load = np.ascontiguousarray(g["q"] if g["kind"] == 0 else g["FT"].reshape(-1))
         n = g["body_start"].size - 1
         host.append((g["kind"], geom, load, np.empty(n if g["kind"] == 0 else 3 * n)))
-    cap = 8 << 30
+    _, hbm_total = torch.cuda.mem_get_info(local)
+    cap = int(args.serve_hbm_fraction * hbm_total)
     srv = bie.Server(local, workers=args.serve_workers, hbm_cap_bytes=cap)
     opts = bie.make_opts(precision=bie.MIXED_FF)
 
@@ -297,30 +327,39 @@ def run_serving(args, rank, local):
         lat_sat.append(sec)
     sat_s = time.perf_counter() - t0
     sat_rate = len(host) / sat_s
-    rate = 0.8 * sat_rate
-    gaps = np.random.default_rng(4000 + rank).exponential(1.0 / rate, len(host))
-    tickets = [None] * len(host)
 
-    def producer():
-        t_next = time.perf_counter()
+    def poisson(frac, seed):
+        """Arrivals at frac x the saturated rate (exponential gaps); returns latencies."""
+        rate = frac * sat_rate
+        gaps = np.random.default_rng(seed).exponential(1.0 / rate, len(host))
+        tickets = [None] * len(host)
+
+        def producer():
+            t_next = time.perf_counter()
+            for i in range(len(host)):
+                t_next += gaps[i]
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = submit(i)
+
+        th = threading.Thread(target=producer)
+        t0 = time.perf_counter()
+        th.start()
+        lat = []
         for i in range(len(host)):
-            t_next += gaps[i]
-            d = t_next - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tickets[i] = submit(i)
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            rc, _, sec = srv.wait(tickets[i])
+            if rc < 0:
+                raise RuntimeError(f"served solve failed: {rc}")
+            lat.append(sec)
+        th.join()
+        wall = time.perf_counter() - t0
+        return {"arrival_rate_per_s": rate, "solves_per_s": len(host) / wall,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
 
-    th = threading.Thread(target=producer)
-    t0 = time.perf_counter()
-    th.start()
-    lat = []
-    for i in range(len(host)):
-        while tickets[i] is None:
-            time.sleep(0.0002)
-        rc, _, sec = srv.wait(tickets[i])
-        lat.append(sec)
-    th.join()
-    poisson_s = time.perf_counter() - t0
+    sweep = {f"poisson_{int(round(100 * f))}pct": poisson(f, 4000 + rank + int(100 * f)) for f in (0.5, 0.8, 0.95)}
     st = srv.stats()
     srv.close()
     batched = None
@@ -350,12 +389,11 @@ def run_serving(args, rank, local):
         "precision": "mixed_ff", "elastance": int(sum(1 for g in reqs if g["kind"] == 0)),
         "mobility": int(sum(1 for g in reqs if g["kind"] == 1)), "mean_nodes": float(np.mean(M)),
         "max_nodes": int(max(M)),
+        "hbm_cap_fraction": args.serve_hbm_fraction,
         "saturated": {"solves_per_s": sat_rate, "seconds": sat_s,
                       "p50_ms": 1e3 * float(np.percentile(lat_sat, 50)),
                       "p99_ms": 1e3 * float(np.percentile(lat_sat, 99))},
-        "poisson_80pct": {"arrival_rate_per_s": rate, "solves_per_s": len(host) / poisson_s,
-                          "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                          "p99_ms": 1e3 * float(np.percentile(lat, 99))},
+        **sweep,
         "peak_inflight_bytes": st["peak_inflight_bytes"],
         "saturated_batched": batched,
     }
@@ -436,6 +474,40 @@ def run_batched(args, rank, local):
     out["served_mix"] = {"requests": n_all, "batch_size": args.batch_size, "solves_per_s": n_all / t_all,
                          "seconds": t_all, "median_iters": float(np.median(iters)),
                          "note": "same request generator and seed as the serving section; host inputs"}
+    ctx.close()
+    return out
+
+
+def run_four_discs(args, rank, local):
+    """The small elastance case (4 discs x 128 nodes, M = 512, GMRES tol 1e-12):
+    solves/s one at a time with inputs on the device, FP64 GMRES (block-Jacobi
+    preconditioned) and the mixed-precision paths; latency bound."""
+    import torch
+
+    from paper_1507_05925_gb300 import bie
+
+    g = synth.four_discs(seed=0)
+    dev = torch.device("cuda", local)
+    gd = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(dev) for k in ("x", "y", "dx", "dy", "ddx", "ddy")}
+    gd["body_start"] = torch.from_numpy(g["body_start"]).to(dev)
+    q = torch.from_numpy(g["q"]).to(dev)
+    phi = torch.empty(4, dtype=torch.float64, device=dev)
+    ctx = bie.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, prec in (("fp64", bie.FP64), ("mixed", bie.MIXED), ("mixed_ff", bie.MIXED_FF)):
+        opts = bie.make_opts(precision=prec)
+        for _ in range(3):
+            rc, info = bie.elastance_solve(ctx, gd, q, phi, opts=opts, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.four_disc_steps):
+            rc, info = bie.elastance_solve(ctx, gd, q, phi, opts=opts, stream=stream)
+            assert rc == bie.OK
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.four_disc_steps
+        out[name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": 1e3 * dt, "iters": info["iters"],
+                     "rel_residual": info["rel_residual"]}
     ctx.close()
     return out
 
@@ -630,13 +702,16 @@ def main():
     q = torch.from_numpy(g["q"]).to(dev)
     phi = torch.empty(N, dtype=torch.float64, device=dev)
     ctx = bie.Context(local)
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the legacy default stream cannot be captured, so the
+    # library would not replay its GMRES iterations as CUDA graphs there)
+    stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     head_prec = bie.MIXED_FF if args.precision == "mixed_ff" else bie.MIXED
     other_prec = bie.MIXED if head_prec == bie.MIXED_FF else bie.MIXED_FF
     mixed = bie.make_opts(precision=head_prec)
     other = bie.make_opts(precision=other_prec)
     fp64 = bie.make_opts(precision=bie.FP64)
+    fp64_noprec = bie.make_opts(precision=bie.FP64, precond=bie.PRECOND_NONE)
 
     def solve(opts):
         rc, info = bie.elastance_solve(ctx, gd, q, phi, opts=opts, stream=stream)
@@ -644,7 +719,9 @@ def main():
             raise RuntimeError(f"solve failed: {rc} {ctx.last_error()} {info}")
         return info
 
-    # split counts of the headline shape tuned by timing (bie_tune), before the
+    # measured arithmetic peaks of this GPU (the roofline denominators)
+    peaks = bie.measure_alu_peaks(local)
+    # split plans of the headline shape tuned by timing (bie_tune), before the
     # warm-up: the FP32 inner pair sums and the float-float residual
     tuning = None
     if not args.no_tune:
@@ -662,6 +739,8 @@ def main():
     torch.cuda.synchronize()
 
     def timed(opts, steps, profile):
+        """Solves on `stream`, each bracketed by CUDA events recorded on it, the
+        L2 flushed (on the same stream) before each, outside the events."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if dist is not None:
             dist.barrier()
@@ -670,7 +749,8 @@ def main():
             ctx.profile(True)
         infos = []
         for e0, e1 in evs:
-            flush.zero_()
+            with torch.cuda.stream(stream):
+                flush.zero_()
             e0.record(stream)
             infos.append(solve(opts))
             e1.record(stream)
@@ -681,20 +761,36 @@ def main():
         ms = [e0.elapsed_time(e1) for e0, e1 in evs]
         return ms, infos, prof
 
-    ms, infos, prof = timed(mixed, args.steps, True)
-    cs.__exit__(None, None, None)
-    clocks = cs.summary()
-    phi_mixed = phi.clone()
+    # the headline: GMRES iterations replayed as CUDA graphs (no per-launch timing)
+    ms, infos, _ = timed(mixed, args.steps, False)
+    phi_mixed = phi.cpu().numpy()
     total_ms = max_over_ranks(sum(ms), dist, dev)
     value = job_rate(world, args.steps, total_ms / 1000.0)
+    # the same solves again with per-launch pair-sum timing (no graphs): kernel
+    # times for the roofline, launch count, shares of the step
+    ms_p, _, prof = timed(mixed, args.steps, True)
+    cs.__exit__(None, None, None)
+    clocks = cs.summary()
 
-    # the other mixed-precision residual and the plain FP64 GPU path on the same workload
+    # the other mixed-precision residual and the FP64 GPU path on the same workload
     for _ in range(2):
         solve(other)
     ms_o, infos_o, _ = timed(other, args.steps, False)
+    phi_other = phi.cpu().numpy()
     other_rate = len(ms_o) / (sum(ms_o) / 1000.0)
     ms64, infos64, prof64 = timed(fp64, args.fp64_steps, True)
+    phi64 = phi.cpu().numpy()
     fp64_rate = len(ms64) / (sum(ms64) / 1000.0)
+    ms64n, infos64n, _ = timed(fp64_noprec, 1, False)
+    fp64_noprec_rate = len(ms64n) / (sum(ms64n) / 1000.0)
+    ref_phi = stored_oracle("stars100_M25600_elastance.txt")
+    oracle_err = None
+    if ref_phi is not None and ref_phi.size == N and rank == 0:
+        oracle_err = {args.precision: rel_err(phi_mixed, ref_phi),
+                      ("mixed" if other_prec == bie.MIXED else "mixed_ff"): rel_err(phi_other, ref_phi),
+                      "fp64": rel_err(phi64, ref_phi),
+                      "note": "||phi - phi_oracle|| / ||phi_oracle||, oracle = dense LU of the same system "
+                              "(tests/golden/stars100_M25600_elastance.txt)"}
 
     # end to end through the C ABI with host (pinned) buffers (headline precision): the library copies
     # the geometry and charges in and the potentials out inside the timed call
@@ -710,19 +806,19 @@ def main():
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
         rc, _ = bie.elastance_solve(ctx, host, qh, phih, opts=mixed, stream=stream)
         assert rc == bie.OK
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_rate = job_rate(world, args.e2e_steps, e2e_s)
-    assert np.array_equal(phih.numpy(), phi_mixed.cpu().numpy()), "host and device paths disagree"
+    assert np.array_equal(phih.numpy(), phi_mixed), "host and device paths disagree"
 
-    # dominant kernel of the timed mixed-precision solves
-    peaks = measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
-    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 rate
+    # dominant kernel of the timed mixed-precision solves, against the measured
+    # FP32 peak (the better of scalar and packed FMA)
+    fp32_peak = max(peaks["fp32_ffma_tflops"], peaks["fp32_ffma2_tflops"])
+    fp64_peak = peaks["fp64_dfma_tflops"]
     launches = prof.pop("kernel_launches")
     prof64.pop("kernel_launches")
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -733,12 +829,17 @@ def main():
     pairs_per_launch = d["pairs"] / max(d["launches"], 1)
     achieved = FLOPS_PER_PAIR[kind] * pairs_per_launch / (per_launch_ms / 1e3) / 1e12
     peak = fp32_peak if is32 else fp64_peak
+
     def rate(p):
         return p["pairs"] / (p["ms"] / 1e3) if p["ms"] > 0 else None
     pair_rate32 = rate(prof["laplace_fp32"])
     pair_rate64 = rate(prof64["laplace_fp64"])
     pair_rate_ff = rate(prof["laplace_ff"])
-    kernel_share = {k: round(v["ms"] / total_ms * world, 4) for k, v in prof.items() if v["ms"] > 0}
+    kernel_share = {k: round(v["ms"] / sum(ms_p), 4) for k, v in prof.items() if v["ms"] > 0}
+    # the far-pair loop of the FP32 Laplace kernel needs 7 FP32 lane operations
+    # and one MUFU reciprocal a pair: its own ALU bound is the smaller of the two
+    lane_ops = fp32_peak * 1e12 / 2.0
+    pipe_bound_pairs = min(lane_ops / 7.0, peaks["mufu_rcp_tops"] * 1e12)
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -749,28 +850,41 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "M": M, "N": N, "nodes_per_body": 256, "tol": 1e-12,
                    "precision": args.precision, "l2": "flushed (256 MB write) before every step, outside the events",
+                   "graphs": "GMRES iterations replayed as CUDA graphs (a stream of its own)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
-        "fp64_solves_per_s": fp64_rate,
+        "residual_certified_by": ("float-float pair sums (about 48 bits), then FP32 residual updates with "
+                                  "their error bound" if head_prec == bie.MIXED_FF else "FP64 pair sums"),
         ("mixed_fp64_residual_solves_per_s" if other_prec == bie.MIXED else "mixed_ff_residual_solves_per_s"):
             other_rate,
+        "fp64_solves_per_s": fp64_rate,
+        "fp64_unpreconditioned_solves_per_s": fp64_noprec_rate,
         "mixed_over_fp64": value / world / fp64_rate,
+        "oracle_rel_error": oracle_err,
         "pair_interactions_per_s": {"laplace_fp32": pair_rate32, "laplace_ff": pair_rate_ff,
                                     "laplace_fp64": pair_rate64},
-        "solve_info": {args.precision: infos[-1], "other_mixed": infos_o[-1], "fp64": infos64[-1]},
+        "solve_info": {args.precision: infos[-1], "other_mixed": infos_o[-1], "fp64": infos64[-1],
+                       "fp64_unpreconditioned": infos64n[-1]},
         "kernel_share_of_step": kernel_share,
+        "profiled_ms_per_step": sum(ms_p) / len(ms_p),
         "pair_sum_tuning": tuning,
         "gpu_launches": launches,
         "e2e": {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "measured_peaks": peaks,
         "roofline": {"bound": "alu", "kernel": f"pair sum {dname}", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(dname),
                      "traffic_note": "DRAM bytes per launch from ncu (inputs L2-resident)",
-                     "peak_note": (f"FP32: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of measured peaks)"
-                                   + ("; float-float kernel: algorithmic flops of the FP64 formula" if dname.endswith("ff") else "")
-                                   if is32 else "FP64: nominal GB300 1.25 TFLOP/s"),
-                     "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms},
+                     "peak_note": ("FP32: measured on this GPU by bie_measure_alu_peaks (FFMA/FFMA2 chains on "
+                                   "every SM), FMA = 2 flop" if is32 else
+                                   "FP64: measured on this GPU by bie_measure_alu_peaks (DFMA chains)"),
+                     "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms,
+                     "pipe_bound_pairs_per_s": pipe_bound_pairs,
+                     "frac_of_pipe_bound": (pairs_per_launch / (per_launch_ms / 1e3)) / pipe_bound_pairs,
+                     "pipe_bound_note": "far pairs: 7 FP32 lane operations + 1 MUFU rcp each; measured MUFU rate"},
         "clocks": clocks,
     }
+    if args.four_disc_steps > 0:
+        out["four_discs_M512"] = run_four_discs(args, rank, local)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, rank, local)
     if args.batch_requests > 0:
@@ -780,12 +894,13 @@ def main():
     if args.large_steps > 0:
         out["large_mobility"] = run_large(args, rank, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = oracle_sample_rate(M, 16)
-        out["cpu_baseline"] = {"value": 1.0 / smp["seconds_full_estimate"], "unit": "solves/s",
-                               "cores": blas_threads(), "kind": "oracle",
-                               "sample": (f"16 of the 100 stars (M={smp['M_sample']}), dense assembly + LU + "
-                                          f"output in {smp['seconds_sample']:.2f} s; O(M^2) parts scaled by "
-                                          f"(25600/M)^2, LU by (25600/M)^3")}
+        r = oracle_full_solve()
+        out["cpu_baseline"] = {"value": 1.0 / r["seconds"], "unit": "solves/s", "cores": blas_threads(),
+                               "kind": "oracle",
+                               "sample": ("the full workload: one oracle.laplace.solve of the 100 stars (M = 25,600: "
+                                          f"dense assembly, LU, potentials) in {r['seconds']:.1f} s")}
+        if args.cpu_1core:
+            out["cpu_baseline"]["single_core_seconds"] = oracle_single_core_seconds()
     ctx.close()
     if rank == 0:
         print(json.dumps(out))

@@ -174,15 +174,17 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
 /* Autotuning of the pair-sum grid (no counterpart in the paper).  Times one
  * application of the operator (pair sum + epilogue, CUDA events on the stream,
  * the fastest of five after two warm-ups) on this geometry for source-split
- * counts around the occupancy rule's, and keeps the fastest for this device
- * and shape (M, kind, precision): later solves and operator applications of
- * that shape, in any context of the process, use it (the occupancy rule is
- * kept unless another count is faster by 2%).  A different split count changes
- * the summation order, so results of that shape may change in rounding.
- * splits (nullable): on input 0 to search, or a count to install without
- * timing (rounded to the counts the source chunking allows); on output the
- * count kept.  ms (nullable) receives its time (0 when installed untimed).
- * Errors as for apply_operator. */
+ * plans around the occupancy rule's -- uniform split counts, splits of whole
+ * 256-source tiles, and (M >= 8192) two-level plans whose large chunks are
+ * dispatched first and small chunks last -- and keeps the fastest for this
+ * device and shape (M, kind, precision): later solves and operator applications
+ * of that shape, in any context of the process, use it (the occupancy rule is
+ * kept unless another plan is faster by 2%).  A different plan changes the
+ * summation order, so results of that shape may change in rounding.
+ * splits (nullable): on input 0 to search, or a count to install a uniform plan
+ * without timing (rounded to the counts the source chunking allows); on output
+ * the number of splits of the plan kept.  ms (nullable) receives its time (0
+ * when installed untimed).  Errors as for apply_operator. */
 int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
              void* stream);
 /* Forget every tuned split count (back to the occupancy rule). */
@@ -321,6 +323,15 @@ int bie_server_batching(bie_server* srv, int max_batch, int max_request_nodes, i
 int bie_server_stats(bie_server* srv, int64_t* completed, size_t* inflight_bytes, size_t* peak_inflight_bytes);
 /* Finish the queued requests, stop the workers and free everything. */
 void bie_server_destroy(bie_server* srv);
+
+/* Measured arithmetic peaks of a device (no counterpart in the paper: the
+ * denominators of the pair-sum rooflines).  Runs four short throughput kernels
+ * on every SM of `device` (independent FMA / reciprocal chains, CUDA events,
+ * the fastest of five runs) and writes out[4] = {FP32 FFMA TFLOP/s, FP32 packed
+ * FFMA2 TFLOP/s (both counting an FMA as 2 flop), MUFU rcp.approx.f32 T op/s,
+ * FP64 DFMA TFLOP/s}.  Takes about 20 ms; allocates 32 KB of device memory for
+ * the duration.  BIE_ERR_CUDA if the device cannot run them. */
+int bie_measure_alu_peaks(int device, double* out);
 
 /* Kernel timing of the pair sums (the O(M^2) hot loop), for measurement.
  * counters[precision][kind] (precision 0 FP64, 1 FP32, 2 float-float): launches that did work and their summed device

@@ -128,6 +128,8 @@ def load():
     lib.bie_tune_clear.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
+    lib.bie_measure_alu_peaks.argtypes = [i32, ctypes.POINTER(dbl)]
+    lib.bie_measure_alu_peaks.restype = i32
     lib.bie_test_arm_barrier_timeout.argtypes = [i32, ctypes.c_longlong]
     lib.bie_test_arm_barrier_timeout.restype = None
     lib.bie_test_precond_pivot_floor.argtypes = [dbl]
@@ -309,6 +311,16 @@ def test_precond_pivot_floor(floor: float) -> None:
 
 test_arm_barrier_timeout.__test__ = False  # hooks, not tests: pytest must not collect them
 test_precond_pivot_floor.__test__ = False
+
+
+def measure_alu_peaks(device: int = 0) -> dict:
+    """bie_measure_alu_peaks: measured FP32 (FFMA, FFMA2), MUFU and FP64 rates of a device."""
+    out = (ctypes.c_double * 4)()
+    rc = load().bie_measure_alu_peaks(device, out)
+    if rc != OK:
+        raise RuntimeError(f"bie_measure_alu_peaks failed with status {rc}")
+    return {"fp32_ffma_tflops": out[0], "fp32_ffma2_tflops": out[1], "mufu_rcp_tops": out[2],
+            "fp64_dfma_tflops": out[3]}
 
 
 def tune_clear() -> None:

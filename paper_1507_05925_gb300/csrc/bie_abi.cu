@@ -646,10 +646,10 @@ struct Op {
       const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
       cudaError_t e = timed_pair_sum(ctx, g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
       if (e != cudaSuccess) return e;
-      return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
+      return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1);
     }
     if (fmm_p > 0) {
-      const PairPlan one{1, w->g.M};
+      const PairPlan one = uniform_plan(1, w->g.M);
       cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s, prec);
       if (e != cudaSuccess) return e;
       return epilogue(w->g, w->kind, one, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
@@ -657,7 +657,7 @@ struct Op {
     const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
     cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
     if (e != cudaSuccess) return e;
-    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
+    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1);
   }
 };
 
@@ -713,7 +713,8 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
   const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
                              w.kind + 4LL * w.seg.P, w.m, op.prec * 1000 + op.fmm_p + (op.precond ? 500 : 0), alpha_bits,
-                             p.S * 1000003LL + p.chunk, w.grid + 1000003LL * w.seg.nitem};
+                             (p.S * 1000003LL + p.chunk) * 1000003LL + p.S1 * 4099LL + p.chunk2 * 2 + p.sym,
+                             w.grid + 1000003LL * w.seg.nitem};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
   const long long before = thread_launches();
@@ -1342,7 +1343,7 @@ int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int ord
   if ((rc = stage_in(ctx, in, w.io_in, (size_t)w.n, &din, s))) return rc;
   const bool dev_out = is_device_ptr(out);
   double* dout = dev_out ? out : w.io_out;
-  const PairPlan one{1, M};
+  const PairPlan one = uniform_plan(1, M);
   CK(fmm_pair_sum(ctx->fmm, w.g, kind, order, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr, s));
   CK(epilogue(w.g, kind, one, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s));
   if (!dev_out) {
@@ -1427,9 +1428,9 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
   if (splits && *splits > 0) {  // install the given count, no timing
-    const int S = plan_with_splits(M, *splits).S;
-    set_tuned_splits(M, kind, precision, S);
-    *splits = S;
+    const PairPlan p = plan_with_splits(M, *splits);
+    set_tuned_plan(M, kind, precision, p);
+    *splits = p.S;
     if (ms) *ms = 0.0;
     return BIE_OK;
   }
@@ -1440,15 +1441,33 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   Arena ar{ctx->ws};
   carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;
-  // candidates around the occupancy rule's split count
-  const int S0 = occupancy_plan(M, kind, precision).S;
-  std::vector<int> cand;
-  for (int c : {S0, S0 / 2, (2 * S0) / 3, (3 * S0) / 2, 2 * S0, 3 * S0, 4 * S0, 6 * S0, 1}) {
-    const int S = plan_with_splits(M, std::max(1, c)).S;
-    if (std::find(cand.begin(), cand.end(), S) == cand.end()) cand.push_back(S);
+  // candidates: uniform split counts around the occupancy rule's, chunks of
+  // whole source tiles (256 sources), and two-level plans (large chunks first,
+  // small chunks last, so that the last wave drains fast)
+  const PairPlan P0 = occupancy_plan(M, kind, precision);
+  const int S0 = P0.S;
+  std::vector<PairPlan> cand;
+  auto add = [&](const PairPlan& p) {
+    for (const PairPlan& q : cand)
+      if (q.S == p.S && q.chunk == p.chunk && q.S1 == p.S1 && q.chunk2 == p.chunk2 && q.sym == p.sym) return;
+    if (p.S >= 1 && p.chunk >= 1) cand.push_back(p);
+  };
+  add(P0);
+  for (int c : {S0 / 2, (2 * S0) / 3, (3 * S0) / 2, 2 * S0, 3 * S0, 4 * S0, 6 * S0, 1}) add(plan_with_splits(M, std::max(1, c)));
+  for (int t : {1, 2, 3, 4}) add(plan_with_splits(M, (M + 256 * t - 1) / (256 * t)));
+  // the symmetric FP32 Laplace kernel, while its partials (one slot per tile) stay small
+  if (precision == BIE_PREC_MIXED && kind == BIE_KIND_LAPLACE) {
+    const PairPlan ps = plan_symmetric(M);
+    if ((double)ps.S * M * sizeof(double) <= (1 << 30) && ps.S <= 4096) add(ps);
+  }
+  if (M >= 8192) {
+    add(plan_two_level(M, 512, 128, 0.75));
+    add(plan_two_level(M, 512, 256, 0.5));
+    add(plan_two_level(M, 768, 256, 0.6));
+    add(plan_two_level(M, 1024, 256, 0.75));
   }
   int smax = 1;
-  for (int S : cand) smax = std::max(smax, S);
+  for (const PairPlan& p : cand) smax = std::max(smax, p.S);
   // the timing scratch is released on every return path
   struct Scratch {
     double* partial = nullptr;
@@ -1466,14 +1485,14 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   CK(cudaEventCreate(&sc.e0));
   CK(cudaEventCreate(&sc.e1));
   cudaEvent_t e0 = sc.e0, e1 = sc.e1;
-  int best = S0;
+  PairPlan best = P0;
   double best_ms = 0.0, s0_ms = 0.0;
-  for (int S : cand) {
-    const PairPlan p = plan_with_splits(M, S);
+  for (const PairPlan& p : cand) {
     auto apply = [&]() -> cudaError_t {
       cudaError_t e = pair_sum(w.g, kind, precision, p, vec(w.io_in), w.g.w, partial, nullptr, s);
       if (e != cudaSuccess) return e;
-      return epilogue(w.g, kind, p, vec(w.io_in), partial, 0, 1, 1.0, vec(w.io_out), nullptr, s);
+      return epilogue(w.g, kind, p, vec(w.io_in), partial, 0, 1, 1.0, vec(w.io_out), nullptr, s, 0.0,
+                      precision == 1);
     };
     for (int it = 0; it < 2; ++it) CK(apply());
     // the fastest of five single applications
@@ -1487,20 +1506,20 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
       CK(cudaEventElapsedTime(&t, e0, e1));
       t_min = std::min(t_min, (double)t);
     }
-    if (S == S0) s0_ms = t_min;
+    if (&p == &cand[0]) s0_ms = t_min;
     if (best_ms == 0.0 || t_min < best_ms) {
       best_ms = t_min;
-      best = S;
+      best = p;
     }
   }
   CK(cudaStreamSynchronize(s));
-  // keep the occupancy rule unless another count is clearly faster (2%)
-  if (best != S0 && best_ms > 0.98 * s0_ms) {
-    best = S0;
+  // keep the occupancy rule unless another plan is clearly faster (2%)
+  if (best_ms > 0.98 * s0_ms) {
+    best = P0;
     best_ms = s0_ms;
   }
-  set_tuned_splits(M, kind, precision, best);
-  if (splits) *splits = best;
+  set_tuned_plan(M, kind, precision, best);
+  if (splits) *splits = best.S;
   if (ms) *ms = best_ms;
   return BIE_OK;
 }
@@ -1538,7 +1557,8 @@ int apply_operator(bie_ctx* ctx, const bie_geometry* geom, int kind, int precisi
   double* dout = dev_out ? out : w.io_out;
   CK(timed_pair_sum(ctx, w.g, kind, precision, p, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr,
                     true, s));
-  CK(epilogue(w.g, kind, p, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s));
+  CK(epilogue(w.g, kind, p, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s, 0.0,
+              precision == 1));
   if (!dev_out) {
     CK(cudaMemcpyAsync(out, dout, (size_t)w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -163,16 +163,29 @@ int device_sms();
 // partial[s][a] (scalar for Laplace, 2-vector for Stokes) = sum over sources b
 // of split s, b != a, of the kernel without its constant, with source strength
 // sscale_b * v_b.  FP64 and FP32 variants.
+// Source splits of a pair sum: splits s < S1 take `chunk` sources each, the
+// remaining S - S1 splits `chunk2` each (a two-level plan: large chunks are
+// dispatched first and small ones last, so that the last wave drains fast).
+// Uniform plans have S1 = S.  Batched solves use `chunk` only.
 struct PairPlan {
-  int S;      // source splits
-  int chunk;  // sources per split
+  int S;         // source splits
+  int chunk;     // sources per split (the first S1 splits)
+  int S1;        // splits of `chunk` sources
+  int chunk2;    // sources per split after the first S1
+  int sym = 0;   // FP32 Laplace: the symmetric kernel (S = tiles of 256 nodes, one CTA per tile pair)
 };
+inline PairPlan uniform_plan(int S, int chunk) { return PairPlan{S, chunk, S, chunk}; }
 // the tuned split count of this shape (bie_tune) if any, else occupancy_plan:
 // one wave of blocks (target blocks x splits) over every SM
 PairPlan plan_pairs(int M, int kind, int precision);
 PairPlan occupancy_plan(int M, int kind, int precision);
 PairPlan plan_with_splits(int M, int S);
-void set_tuned_splits(int M, int kind, int precision, int S);  // S <= 0: forget
+// two-level plan: a fraction f of the sources in chunks of c1, the rest in chunks of c2
+PairPlan plan_two_level(int M, int c1, int c2, double f);
+// the symmetric FP32 Laplace pair sum (partials: one slot per 256-node tile)
+PairPlan plan_symmetric(int M);
+void set_tuned_plan(int M, int kind, int precision, const PairPlan& p);
+void forget_tuned_plan(int M, int kind, int precision);
 void clear_tuned_splits();
 // batched solves (host arrays: body_start [N+1], first body of each problem [P+1])
 PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P, int kind, int precision);
@@ -184,9 +197,11 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 // scaled = 0: v unscaled, source strength w, output unscaled.
 // alpha = 0: the paper's completion L; alpha > 0: L weighted per body by
 // alpha/|Gamma_i| (force part) and alpha/W_i (torque part).
+// pff: the partials are float-float pairs (written by the FP32 pair sums,
+// precision 1), summed in float-float; otherwise doubles.
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s, double alpha = 0.0);
+                     cudaStream_t s, double alpha = 0.0, bool pff = false);
 // out = in - (I - C) L~(in) for a correction solved with the weighted completion.
 cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* in, double* out,
                            cudaStream_t s);

@@ -160,8 +160,7 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
     const int tile = 256;
     int chunk = (M + kNoallocMaxSplits - 1) / kNoallocMaxSplits;
     chunk = (chunk + tile - 1) / tile * tile;
-    p.chunk = chunk;
-    p.S = (M + chunk - 1) / chunk;
+    p = uniform_plan((M + chunk - 1) / chunk, chunk);
   }
   if (cudaMemcpyAsync(body_start, geom->body_start, (N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
@@ -172,6 +171,8 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
     return BIE_ERR_CUDA;
   VecRef vin = vec(const_cast<double*>(in));
   if (pair_sum(g, kind, precision, p, vin, g.w, partial, nullptr, s) != cudaSuccess) return BIE_ERR_CUDA;
-  if (epilogue(g, kind, p, vin, partial, 0, 1, 1.0, vec(out), nullptr, s) != cudaSuccess) return BIE_ERR_CUDA;
+  if (epilogue(g, kind, p, vin, partial, 0, 1, 1.0, vec(out), nullptr, s, 0.0, precision == BIE_PREC_MIXED) !=
+      cudaSuccess)
+    return BIE_ERR_CUDA;
   return BIE_OK;
 }

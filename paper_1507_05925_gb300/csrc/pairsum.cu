@@ -47,14 +47,16 @@ struct SrcRange {
 };
 
 template <bool BATCH>
-__device__ __forceinline__ SrcRange src_range(const Geo& g, int tbase, int tend, int chunk) {
+__device__ __forceinline__ SrcRange src_range(const Geo& g, int tbase, int tend, const PairPlan& p) {
   SrcRange r;
   if (!BATCH) {
-    r.j0 = blockIdx.y * chunk;
-    r.j1 = min(g.M, r.j0 + chunk);
+    const int s = blockIdx.y;
+    r.j0 = s < p.S1 ? s * p.chunk : p.S1 * p.chunk + (s - p.S1) * p.chunk2;
+    r.j1 = min(g.M, r.j0 + (s < p.S1 ? p.chunk : p.chunk2));
     r.straddle = false;
     return r;
   }
+  const int chunk = p.chunk;
   const int2 p0 = g.prange[g.body_of[tbase]], p1 = g.prange[g.body_of[tend - 1]];
   const int len = p1.y - p0.x;
   const int ch = max(chunk, (len + (int)gridDim.y - 1) / (int)gridDim.y);
@@ -108,7 +110,7 @@ constexpr int kB64 = 128, kT64 = 2, kTile64 = 128;
 
 template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double* __restrict__ sscale,
-                                                 int chunk, double* __restrict__ partial,
+                                                 PairPlan pp, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
   __shared__ double sx[kTile64], sy[kTile64], sq1[kTile64], sq2[kTile64];
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kB64) k_pair64(Geo g, VecRef vr, const double*
     zero_partials<KIND>(tbase, min(M, tbase + kB64 * kT64), M, partial);
     return;
   }
-  const SrcRange sr = src_range<BATCH>(g, tbase, min(M, tbase + kB64 * kT64), chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, min(M, tbase + kB64 * kT64), pp);
   const int j0 = sr.j0, j1 = sr.j1;
   double tx[kT64], ty[kT64], tnx[kT64], tny[kT64], ax[kT64], ay[kT64];
   int ta[kT64];
@@ -309,7 +311,7 @@ __global__ void k_src32(Geo g, VecRef vr, const double* __restrict__ sscale, con
 
 template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, VecRef vr, const double* __restrict__ sscale,
-                                                 int chunk, double* __restrict__ partial,
+                                                 PairPlan pp, double* __restrict__ partial,
                                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
   __shared__ float4 sp[kTile32];  // near: (xh, yh, xl, yl)
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
     zero_partials<KIND>(tbase, tend, M, partial);
     return;
   }
-  const SrcRange sr = src_range<BATCH>(g, tbase, tend, chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, tend, pp);
   const int j0 = sr.j0, j1 = sr.j1;
   // the target block's box, centre and half-diagonal
   const float4 tb = body_range_box(g.bbox, g.body_of[tbase], g.body_of[tend - 1]);
@@ -442,11 +444,190 @@ __global__ void __launch_bounds__(kB32, KIND == 0 ? 12 : 10) k_pair32(Geo g, Vec
         ff_mul(n.x, n.y, sx[k], ex[k], p1, e1);
         ff_mul(n.z, n.w, sy[k], ey[k], p2, e2);
         two_sum(p1, p2, h, l);
-        partial[(long long)blockIdx.y * M + a] = (double)h + (double)(l + (e1 + e2));
+        reinterpret_cast<float2*>(partial)[(long long)blockIdx.y * M + a] = make_float2(h, l + (e1 + e2));
       } else {
-        partial[((long long)blockIdx.y * M + a) * 2] = (double)sx[k] + (double)ex[k];
-        partial[((long long)blockIdx.y * M + a) * 2 + 1] = (double)sy[k] + (double)ey[k];
+        // (sx + ex, sy + ey) as two float-float pairs: no FP64 pipe in the kernel
+        float hx, lx, hy, ly;
+        two_sum(sx[k], ex[k], hx, lx);
+        two_sum(sy[k], ey[k], hy, ly);
+        reinterpret_cast<float4*>(partial)[(long long)blockIdx.y * M + a] = make_float4(hx, lx, hy, ly);
       }
+    }
+  }
+}
+
+// ------------------------------------------------------- symmetric FP32 ----
+// Laplace pair sums with each reciprocal used for both directions of a pair.
+// The M nodes are cut into tiles of kTS = 256 consecutive nodes; one CTA takes
+// one unordered pair of tiles (A = tile i, B = tile j, i <= j) and writes the
+// contribution of B's sources to A's targets into partial[j][A] and that of
+// A's sources to B's targets into partial[i][B]: every (source tile, target
+// tile) slot is written exactly once, and the epilogue adds the S = tiles
+// slots of a target in a fixed order (deterministic).
+//
+// Far tile pairs (boxes at least both half-diagonals apart): with r = x_a - x_b
+// and w = 1/|r|^2, target a gains q_b r w and target b gains -q_a r w, so one
+// MUFU reciprocal and about 10 FP32 lane operations serve two directed pairs
+// (the directed kernel: one reciprocal and 7 operations for one).  Each lane
+// holds four A targets in registers (packed two by two); B's sources sit in
+// shared memory and are visited on a diagonal schedule (lane l takes source
+// (l + k) mod 32 of the current group of 32 at step k), and the accumulator of
+// B's source travels with it from lane to lane by a warp shuffle, so no two
+// lanes ever add into the same place.  Coordinates are relative to A's box
+// centre, as in the directed far tiles.  Near tile pairs (and i = j) run the
+// directed near path in both directions (exact hi/lo differences).
+constexpr int kTS = kB32 * kT32;  // 256 nodes a tile
+
+__device__ __forceinline__ void tri_decode(int t, int& i, int& j) {
+  int jj = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // then corrected exactly
+  while ((long long)(jj + 1) * (jj + 2) / 2 <= t) ++jj;
+  while ((long long)jj * (jj + 1) / 2 > t) --jj;
+  j = jj;
+  i = t - jj * (jj + 1) / 2;
+}
+
+// Is box b far from box a (gap at least both half-diagonals)?
+__device__ __forceinline__ bool boxes_far(float4 a, float4 b) {
+  const float gx = fmaxf(0.f, fmaxf(b.x - a.z, a.x - b.z));
+  const float gy = fmaxf(0.f, fmaxf(b.y - a.w, a.y - b.w));
+  const float ea = 0.5f * sqrtf((a.z - a.x) * (a.z - a.x) + (a.w - a.y) * (a.w - a.y));
+  const float eb = 0.5f * sqrtf((b.z - b.x) * (b.z - b.x) + (b.w - b.y) * (b.w - b.y));
+  const float gap2 = gx * gx + gy * gy;
+  const float need = fmaxf(ea, eb);
+  return gap2 > 0.f && gap2 >= need * need;
+}
+
+// partial[slot][a] = n_a . (ax, ay) in float-float (the normal's hi/lo split),
+// stored as the float pair (h, l): no FP64 pipe in the kernel
+__device__ __forceinline__ void write_projected(const Geo& g, int a, int slot, float ax, float ay,
+                                                double* __restrict__ partial) {
+  const float4 n = g.nff[a];
+  float p1, e1, p2, e2, h, l;
+  ff_mul(n.x, n.y, ax, 0.f, p1, e1);
+  ff_mul(n.z, n.w, ay, 0.f, p2, e2);
+  two_sum(p1, p2, h, l);
+  reinterpret_cast<float2*>(partial)[(long long)slot * g.M + a] = make_float2(h, l + (e1 + e2));
+}
+
+// Directed near pass: targets [t0, t0 + kTS) gain the sources [s0, s1) (one
+// tile, exact hi/lo differences), written to partial[slot].
+template <bool DIAG>
+__device__ __forceinline__ void sym_near_pass(const Geo& g, int t0, int s0, int s1, int slot,
+                                              double* __restrict__ partial, float4* sp, float2* sq) {
+  const int M = g.M, nt = s1 - s0;
+  __syncthreads();  // the tile buffers may still be read
+  for (int l = threadIdx.x; l < nt; l += kB32) {
+    sp[l] = g.pf[s0 + l];
+    sq[l] = make_float2(g.qf[s0 + l], 0.f);
+  }
+  __syncthreads();
+  float ax[kT32], ay[kT32], tnx[kT32], tny[kT32];
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) ax[k] = ay[k] = tnx[k] = tny[k] = 0.f;
+  tile_near<0, DIAG>(g.pf, sp, sq, nt, s0, t0 + threadIdx.x, M, tnx, tny, ax, ay);
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) {
+    const int a = t0 + threadIdx.x + k * kB32;
+    if (a < M) write_projected(g, a, slot, ax[k], ay[k], partial);
+  }
+}
+
+__global__ void __launch_bounds__(kB32, 12) k_pair32s(Geo g, int ntile, double* __restrict__ partial,
+                                                      const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ __align__(16) unsigned char sm_raw[kTS * 32];  // far: sources + 2 accumulator rows; near: sp, sq
+  const int M = g.M;
+  int ti, tj;
+  tri_decode(blockIdx.x, ti, tj);
+  const int A0 = ti * kTS, A1 = min(M, A0 + kTS), B0 = tj * kTS, B1 = min(M, B0 + kTS);
+  const float4 boxA = body_range_box(g.bbox, g.body_of[A0], g.body_of[A1 - 1]);
+  const float4 boxB = body_range_box(g.bbox, g.body_of[B0], g.body_of[B1 - 1]);
+  if (ti == tj || !boxes_far(boxA, boxB)) {
+    float4* sp = reinterpret_cast<float4*>(sm_raw);
+    float2* sq = reinterpret_cast<float2*>(sm_raw + kTS * sizeof(float4));
+    if (ti == tj) {
+      sym_near_pass<true>(g, A0, B0, B1, tj, partial, sp, sq);
+    } else {
+      sym_near_pass<false>(g, A0, B0, B1, tj, partial, sp, sq);
+      sym_near_pass<false>(g, B0, A0, A1, ti, partial, sp, sq);
+    }
+    return;
+  }
+  float4* sB = reinterpret_cast<float4*>(sm_raw);                    // (-x', -y', q, 0) per source
+  float2* accB = reinterpret_cast<float2*>(sm_raw + kTS * sizeof(float4));  // [2 warps][kTS]
+  const float cx = 0.5f * (boxA.x + boxA.z), cy = 0.5f * (boxA.y + boxA.w);
+  constexpr float kAway = 1e15f;  // padding: far from everything, zero strength
+  for (int l = threadIdx.x; l < kTS; l += kB32) {
+    const int b = B0 + l;
+    float4 v = make_float4(-kAway, -kAway, 0.f, 0.f);
+    if (b < M) {
+      const float4 p = g.pf[b];
+      v = make_float4(-((p.x - cx) + p.z), -((p.y - cy) + p.w), g.qf[b], 0.f);
+    }
+    sB[l] = v;
+  }
+  // four A targets per lane, packed two by two: (t0, t1) and (t2, t3)
+  float tx[kT32], ty[kT32], qa[kT32];
+#pragma unroll
+  for (int k = 0; k < kT32; ++k) {
+    const int a = A0 + threadIdx.x + k * kB32;
+    tx[k] = ty[k] = kAway;
+    qa[k] = 0.f;
+    if (a < M) {
+      const float4 p = g.pf[a];
+      tx[k] = (p.x - cx) + p.z;
+      ty[k] = (p.y - cy) + p.w;
+      qa[k] = g.qf[a];
+    }
+  }
+  const float2 TXa = make_float2(tx[0], tx[1]), TXb = make_float2(tx[2], tx[3]);
+  const float2 TYa = make_float2(ty[0], ty[1]), TYb = make_float2(ty[2], ty[3]);
+  const float2 QAa = make_float2(qa[0], qa[1]), QAb = make_float2(qa[2], qa[3]);
+  float2 AXa = make_float2(0.f, 0.f), AXb = AXa, AYa = AXa, AYb = AXa;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < kTS; r0 += 32) {
+    float bx = 0.f, by = 0.f;  // accumulator of the source this lane holds (travels)
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float4 src = sB[r0 + ((lane + k) & 31)];
+      const float2 sx = make_float2(src.x, src.x), sy = make_float2(src.y, src.y);
+      const float2 dxa = __fadd2_rn(TXa, sx), dxb = __fadd2_rn(TXb, sx);
+      const float2 dya = __fadd2_rn(TYa, sy), dyb = __fadd2_rn(TYb, sy);
+      const float2 r2a = __ffma2_rn(dxa, dxa, __fmul2_rn(dya, dya));
+      const float2 r2b = __ffma2_rn(dxb, dxb, __fmul2_rn(dyb, dyb));
+      const float2 ia = make_float2(rcp_approx(r2a.x), rcp_approx(r2a.y));
+      const float2 ib = make_float2(rcp_approx(r2b.x), rcp_approx(r2b.y));
+      const float2 qb = make_float2(src.z, src.z);
+      const float2 sba = __fmul2_rn(qb, ia), sbb = __fmul2_rn(qb, ib);
+      AXa = __ffma2_rn(dxa, sba, AXa);
+      AXb = __ffma2_rn(dxb, sbb, AXb);
+      AYa = __ffma2_rn(dya, sba, AYa);
+      AYb = __ffma2_rn(dyb, sbb, AYb);
+      const float2 saa = __fmul2_rn(QAa, ia), sab = __fmul2_rn(QAb, ib);
+      const float2 ux = __ffma2_rn(dxb, sab, __fmul2_rn(dxa, saa));
+      const float2 uy = __ffma2_rn(dyb, sab, __fmul2_rn(dya, saa));
+      bx -= ux.x + ux.y;  // the source gains -q_a r w
+      by -= uy.x + uy.y;
+      // hand the accumulator to the lane that takes this source next
+      bx = __shfl_sync(0xffffffffu, bx, (lane + 1) & 31);
+      by = __shfl_sync(0xffffffffu, by, (lane + 1) & 31);
+    }
+    accB[warp * kTS + r0 + lane] = make_float2(bx, by);  // back at its own lane: source r0 + lane
+  }
+  {
+    const int a = A0 + threadIdx.x;
+    if (a < M) write_projected(g, a, tj, AXa.x, AYa.x, partial);
+    if (a + kB32 < M) write_projected(g, a + kB32, tj, AXa.y, AYa.y, partial);
+    if (a + 2 * kB32 < M) write_projected(g, a + 2 * kB32, tj, AXb.x, AYb.x, partial);
+    if (a + 3 * kB32 < M) write_projected(g, a + 3 * kB32, tj, AXb.y, AYb.y, partial);
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < kTS; l += kB32) {
+    const int b = B0 + l;
+    if (b < M) {
+      const float2 u = accB[l], v = accB[kTS + l];
+      write_projected(g, b, ti, u.x + v.x, u.y + v.y, partial);
     }
   }
 }
@@ -485,7 +666,7 @@ __device__ __forceinline__ void tile_ff(const float4* __restrict__ sa, const flo
 }
 
 template <int KIND, bool BATCH>
-__global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double* __restrict__ sscale, int chunk,
+__global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double* __restrict__ sscale, PairPlan pp,
                                                  double* __restrict__ partial, const int* __restrict__ stop) {
   if (stop && *stop) return;
   __shared__ float4 sa[kTileF];
@@ -500,7 +681,7 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
     return;
   }
   const int a0 = tbase + threadIdx.x;
-  const SrcRange sr = src_range<BATCH>(g, tbase, tend, chunk);
+  const SrcRange sr = src_range<BATCH>(g, tbase, tend, pp);
   const int j0 = sr.j0, j1 = sr.j1;
   FFTarget t[kTF];
   // float-float sums over the tiles
@@ -571,10 +752,18 @@ constexpr int kBE = 256;
 
 // One block per body: completion moments, then per node
 //   y = Kv (constant applied) + diagonal limit + [L]; out = sign (1/2 v + oscale y).
+// (sh, sl) += (h, l) in float-float
+__device__ __forceinline__ void ffadd(float& sh, float& sl, float h, float l) {
+  float u, e;
+  two_sum(sh, h, u, e);
+  sh = u;
+  sl += e + l;
+}
+
 template <int KIND, int B>
 __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* __restrict__ partial,
                                                   int S, int scaled, int with_L, double alpha, double sign,
-                                                  VecRef outr, const int* __restrict__ stop) {
+                                                  VecRef outr, const int* __restrict__ stop, int pff) {
   if (stop && *stop) return;
   __shared__ double sh[B / 32];
   const double* __restrict__ v = vr.ptr();
@@ -612,38 +801,71 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
     const double os = scaled ? g.sw[a] : 1.0;
     const double wk = g.w[a] * g.kappa[a];
     if (KIND == 0) {
-      // four independent sums over the source splits (loads in flight), added in a fixed order
-      double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0;
-      int s = 0;
-      for (; s + 4 <= S; s += 4) {
-        k0 += partial[(long long)s * M + a];
-        k1 += partial[(long long)(s + 1) * M + a];
-        k2 += partial[(long long)(s + 2) * M + a];
-        k3 += partial[(long long)(s + 3) * M + a];
+      double k;
+      if (pff) {
+        // float-float partials of the FP32 pair sums: two independent float-float
+        // sums (loads in flight), added in a fixed order, converted once
+        const float2* __restrict__ pf2 = reinterpret_cast<const float2*>(partial);
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        int s = 0;
+        for (; s + 2 <= S; s += 2) {
+          const float2 u = pf2[(long long)s * M + a], v = pf2[(long long)(s + 1) * M + a];
+          ffadd(h0, l0, u.x, u.y);
+          ffadd(h1, l1, v.x, v.y);
+        }
+        if (s < S) {
+          const float2 u = pf2[(long long)s * M + a];
+          ffadd(h0, l0, u.x, u.y);
+        }
+        ffadd(h0, l0, h1, l1);
+        k = (double)h0 + (double)l0;
+      } else {
+        // four independent sums over the source splits (loads in flight), added in a fixed order
+        double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0;
+        int s = 0;
+        for (; s + 4 <= S; s += 4) {
+          k0 += partial[(long long)s * M + a];
+          k1 += partial[(long long)(s + 1) * M + a];
+          k2 += partial[(long long)(s + 2) * M + a];
+          k3 += partial[(long long)(s + 3) * M + a];
+        }
+        for (; s < S; ++s) k0 += partial[(long long)s * M + a];
+        k = (k0 + k1) + (k2 + k3);
       }
-      for (; s < S; ++s) k0 += partial[(long long)s * M + a];
-      const double k = (k0 + k1) + (k2 + k3);
       const double mu = v[a] / os;
       const double y = -kInv2Pi * k - kInv4Pi * wk * mu + m0;
       out[a] = sign * (0.5 * v[a] + os * y);
     } else {
-      double k1 = 0.0, k2 = 0.0, k1b = 0.0, k2b = 0.0;
-      int s = 0;
-      for (; s + 2 <= S; s += 2) {
-        const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
-        const double2 p1 = reinterpret_cast<const double2*>(partial)[(long long)(s + 1) * M + a];
-        k1 += p0.x;
-        k2 += p0.y;
-        k1b += p1.x;
-        k2b += p1.y;
+      double k1 = 0.0, k2 = 0.0;
+      if (pff) {
+        const float4* __restrict__ pf4 = reinterpret_cast<const float4*>(partial);
+        float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+        for (int s = 0; s < S; ++s) {
+          const float4 u = pf4[(long long)s * M + a];
+          ffadd(h1, l1, u.x, u.y);
+          ffadd(h2, l2, u.z, u.w);
+        }
+        k1 = (double)h1 + (double)l1;
+        k2 = (double)h2 + (double)l2;
+      } else {
+        double k1b = 0.0, k2b = 0.0;
+        int s = 0;
+        for (; s + 2 <= S; s += 2) {
+          const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
+          const double2 p1 = reinterpret_cast<const double2*>(partial)[(long long)(s + 1) * M + a];
+          k1 += p0.x;
+          k2 += p0.y;
+          k1b += p1.x;
+          k2b += p1.y;
+        }
+        if (s < S) {
+          const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
+          k1 += p0.x;
+          k2 += p0.y;
+        }
+        k1 += k1b;
+        k2 += k2b;
       }
-      if (s < S) {
-        const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
-        k1 += p0.x;
-        k2 += p0.y;
-      }
-      k1 += k1b;
-      k2 += k2b;
       const double mu1 = v[2 * a] / os, mu2 = v[2 * a + 1] / os;
       const double tx = -g.ny[a], ty = g.nx[a];
       const double dd = -0.5 * kInvPi * wk * (tx * mu1 + ty * mu2);
@@ -748,7 +970,7 @@ namespace {
 // Split counts chosen by timing (bie_tune), per device and shape (M, kind,
 // precision); plan_pairs takes them before the occupancy rule.
 std::mutex g_tune_mu;
-std::map<std::array<int, 4>, int> g_tuned;
+std::map<std::array<int, 4>, PairPlan> g_tuned;
 
 std::array<int, 4> tune_key(int M, int kind, int precision) {
   int dev = 0;
@@ -758,12 +980,14 @@ std::array<int, 4> tune_key(int M, int kind, int precision) {
 
 }  // namespace
 
-void set_tuned_splits(int M, int kind, int precision, int S) {
+void set_tuned_plan(int M, int kind, int precision, const PairPlan& p) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (S > 0)
-    g_tuned[tune_key(M, kind, precision)] = S;
-  else
-    g_tuned.erase(tune_key(M, kind, precision));
+  g_tuned[tune_key(M, kind, precision)] = p;
+}
+
+void forget_tuned_plan(int M, int kind, int precision) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.erase(tune_key(M, kind, precision));
 }
 
 void clear_tuned_splits() {
@@ -775,9 +999,21 @@ PairPlan plan_with_splits(int M, int S) {
   const long long cap = std::max(1, (M + 63) / 64);  // chunks of at least 64 sources
   long long s = std::min<long long>(std::max(S, 1), cap);
   const long long chunk = (M + s - 1) / s;
-  PairPlan p;
-  p.chunk = (int)chunk;
-  p.S = (int)((M + chunk - 1) / chunk);
+  return uniform_plan((int)((M + chunk - 1) / chunk), (int)chunk);
+}
+
+PairPlan plan_two_level(int M, int c1, int c2, double f) {
+  c1 = std::max(64, c1);
+  c2 = std::max(64, std::min(c1, c2));
+  const int S1 = std::max(0, std::min((int)(f * M / c1), M / c1));
+  const int rem = M - S1 * c1;
+  if (rem <= 0) return uniform_plan(S1, c1);
+  return PairPlan{S1 + (rem + c2 - 1) / c2, c1, S1, c2};
+}
+
+PairPlan plan_symmetric(int M) {
+  PairPlan p = uniform_plan((M + kTS - 1) / kTS, kTS);
+  p.sym = 1;
   return p;
 }
 
@@ -785,13 +1021,19 @@ PairPlan plan_pairs(int M, int kind, int precision) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(tune_key(M, kind, precision));
-    if (it != g_tuned.end()) return plan_with_splits(M, it->second);
+    if (it != g_tuned.end()) return it->second;
   }
   return occupancy_plan(M, kind, precision);
 }
 
 PairPlan occupancy_plan(int M, int kind, int precision) {
   const DeviceShape& d = device_shape();
+  if (precision == 1 && kind == 0) {
+    // the symmetric FP32 Laplace kernel once its tile pairs fill the GPU a few
+    // times over and its partials (one slot per tile) stay within 256 MB
+    const long long nt = (M + kTS - 1) / kTS;
+    if (nt * (nt + 1) / 2 >= 4LL * d.nsm && nt * (long long)M * 8 <= (256LL << 20)) return plan_symmetric(M);
+  }
   const int per_block = precision == 0 ? kB64 * kT64 : (precision == 1 ? kB32 * kT32 : kBF * kTF);
   const long long bx = (M + per_block - 1) / per_block;
   const long long slots = (long long)d.nsm * d.occ[precision][kind];
@@ -800,10 +1042,7 @@ PairPlan occupancy_plan(int M, int kind, int precision) {
   if (S > (M + min_chunk - 1) / min_chunk) S = (M + min_chunk - 1) / min_chunk;
   if (S < 1) S = 1;
   const long long chunk = (M + S - 1) / S;
-  PairPlan p;
-  p.chunk = (int)chunk;
-  p.S = (int)((M + chunk - 1) / chunk);
-  return p;
+  return uniform_plan((int)((M + chunk - 1) / chunk), (int)chunk);
 }
 
 // Batched solves: target block x sums over the len_x nodes of its problems.
@@ -839,10 +1078,7 @@ PairPlan plan_pairs_batch(const int* body_start, int N, const int* pbody, int P,
     }
     if (busy >= slots) break;
   }
-  PairPlan p;
-  p.S = S;
-  p.chunk = (src_max + S - 1) / S;
-  return p;
+  return uniform_plan(S, (src_max + S - 1) / S);
 }
 
 namespace {
@@ -853,26 +1089,31 @@ void launch_pairs(const Geo& g, int kind, int precision, const PairPlan& p, VecR
   if (precision == 0) {
     dim3 grid((g.M + kB64 * kT64 - 1) / (kB64 * kT64), p.S);
     if (kind == 0)
-      k_pair64<0, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair64<0, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p, partial, stop);
     else
-      k_pair64<1, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair64<1, BATCH><<<grid, kB64, 0, s>>>(g, v, sscale, p, partial, stop);
   } else if (precision == 1) {
     dim3 grid((g.M + kB32 * kT32 - 1) / (kB32 * kT32), p.S);
     const int gs = (int)std::min<long long>(1216, (g.M + 255) / 256);
     if (kind == 0) {
       k_src32<0><<<gs, 256, 0, s>>>(g, v, sscale, stop);
-      k_pair32<0, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      if (!BATCH && p.sym) {
+        const long long nt = (g.M + kTS - 1) / kTS;
+        k_pair32s<<<(unsigned)(nt * (nt + 1) / 2), kB32, 0, s>>>(g, (int)nt, partial, stop);
+      } else {
+        k_pair32<0, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p, partial, stop);
+      }
     } else {
       k_src32<1><<<gs, 256, 0, s>>>(g, v, sscale, stop);
-      k_pair32<1, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair32<1, BATCH><<<grid, kB32, 0, s>>>(g, v, sscale, p, partial, stop);
     }
     note_launches(1);
   } else {
     dim3 grid((g.M + kBF * kTF - 1) / (kBF * kTF), p.S);
     if (kind == 0)
-      k_pair_ff<0, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair_ff<0, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p, partial, stop);
     else
-      k_pair_ff<1, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p.chunk, partial, stop);
+      k_pair_ff<1, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p, partial, stop);
   }
 }
 
@@ -892,19 +1133,19 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s, double alpha) {
+                     cudaStream_t s, double alpha, bool pff) {
   // one block per body, sized to the bodies (many small bodies: small blocks)
   const int avg = g.M / std::max(1, g.N);
   if (avg <= 64) {
     if (kind == 0)
-      k_epilogue<0, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+      k_epilogue<0, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pff ? 1 : 0);
     else
-      k_epilogue<1, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+      k_epilogue<1, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pff ? 1 : 0);
   } else {
     if (kind == 0)
-      k_epilogue<0, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+      k_epilogue<0, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pff ? 1 : 0);
     else
-      k_epilogue<1, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop);
+      k_epilogue<1, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pff ? 1 : 0);
   }
   note_launches(1);
   return cudaGetLastError();

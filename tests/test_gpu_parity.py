@@ -538,3 +538,58 @@ def test_resistance_round_trip_on_gpu(ctx, name, prec):
     err = np.max(np.abs(out.reshape(N, 3) - target))
     print(f"mobility round trip {name} prec={prec}: {err:.2e}")
     assert err <= 1e-10 * np.max(np.abs(UW))
+
+
+# ---------------------------------------------------------------------------
+# the symmetric FP32 Laplace pair sum (the default plan once the 256-node tile
+# pairs fill the GPU): ragged bodies, tiles that span bodies, a last partial
+# tile, near and far tile pairs
+# ---------------------------------------------------------------------------
+def ragged_large(seed=31):
+    rng = np.random.default_rng(seed)
+    curves = []
+    for i in range(8):
+        for j in range(7):
+            n = int(rng.integers(90, 331))
+            if (i + j) % 3:
+                curves.append(synth.ellipse(3.2 * i, 3.2 * j, 1.0, rng.uniform(0.4, 1.0), rng.uniform(0, 3), n))
+            else:
+                curves.append(synth.star(3.2 * i, 3.2 * j, rng.uniform(0.6, 1.0), rng.uniform(0, 0.3),
+                                         int(rng.integers(3, 7)), rng.uniform(0, 6), n))
+    return synth.assemble(curves)
+
+
+def test_symmetric_pair_sum_operator_and_solve(ctx):
+    g = ragged_large()
+    geo = geometry.nodes(g)
+    M = geo["M"]
+    assert M % 256 != 0 and M > 9000
+    gd = to_dev(g)
+    v = np.random.default_rng(5).standard_normal(M)
+    ref = laplace.apply(geo, v)
+    bie.tune_clear()
+    out = torch.empty(M, dtype=torch.float64, device="cuda")
+    assert bie.apply_operator(ctx, gd, bie.LAPLACE, bie.MIXED, torch.from_numpy(v).cuda(), out) == bie.OK
+    torch.cuda.synchronize()
+    sym = out.cpu().numpy()
+    err = rel_max(sym, ref)
+    print(f"symmetric FP32 Laplace operator, M={M}: {err:.2e}")
+    assert err <= TOL32[0]
+    # the directed kernel (a uniform split plan installed untimed) agrees
+    rc, S, _ = bie.tune(ctx, gd, bie.LAPLACE, bie.MIXED, splits=24)
+    assert rc == bie.OK
+    assert bie.apply_operator(ctx, gd, bie.LAPLACE, bie.MIXED, torch.from_numpy(v).cuda(), out) == bie.OK
+    torch.cuda.synchronize()
+    bie.tune_clear()
+    assert rel_max(out.cpu().numpy(), ref) <= TOL32[0]
+    assert rel_max(out.cpu().numpy(), sym) <= 2 * TOL32[0]
+    # a mixed-precision solve on the symmetric kernel, against the oracle's LU
+    N = geo["N"]
+    q = synth.charges(N, np.random.default_rng(12))
+    phi_ref = laplace.solve(g, q)["phi"]
+    for prec in (bie.MIXED, bie.MIXED_FF):
+        phi = torch.empty(N, dtype=torch.float64, device="cuda")
+        rc, info = bie.elastance_solve(ctx, gd, torch.from_numpy(q).cuda(), phi, opts=bie.make_opts(precision=prec))
+        torch.cuda.synchronize()
+        assert rc == bie.OK, (rc, ctx.last_error(), info)
+        assert rel2(phi.cpu().numpy(), phi_ref) <= TOL_SOLVE
