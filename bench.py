@@ -42,10 +42,10 @@ METRIC = "elastance solves/s at 1e-12 relative residual (mixed precision: FP32 p
 # r.n (3), (r.mu)(r.n)/|r|^4 (3), accumulate (4)
 FLOPS_PER_PAIR = {"laplace": 10.0, "stokes": 18.0}
 # DRAM bytes (read + write) per launch of the 100-star pair sums, from one ncu
-# capture of the current kernels (profiles/k_pair32_laplace_stars100_M25600.md,
-# profiles/k_pair_ff_laplace_stars100_M25600.md); a kernel changed since its
-# capture must be taken out of this table
-DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 0.982e6, "laplace_ff": 1.462e6}
+# capture of the current kernels (profiles/k_pair32s_laplace_stars100_M25600.md:
+# the symmetric FP32 kernel); a kernel changed since its capture must be taken
+# out of this table
+DRAM_BYTES_PER_LAUNCH = {"laplace_fp32": 1.002e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--four-disc-steps", type=int, default=100,
                     help="solves of the four-disc case (M = 512) per precision, host clock (0 = skip)")
     ap.add_argument("--splits", type=int, default=0,
-                    help="--kernel: install this pair-sum split count instead of searching (0 = search)")
+                    help="--kernel: install this pair-sum split count instead of searching (0 = search, "
+                         "negative = the symmetric FP32 Laplace plan)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the occupancy rule's pair-sum split counts (no bie_tune before the warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -836,10 +837,13 @@ def main():
     pair_rate64 = rate(prof64["laplace_fp64"])
     pair_rate_ff = rate(prof["laplace_ff"])
     kernel_share = {k: round(v["ms"] / sum(ms_p), 4) for k, v in prof.items() if v["ms"] > 0}
-    # the far-pair loop of the FP32 Laplace kernel needs 7 FP32 lane operations
-    # and one MUFU reciprocal a pair: its own ALU bound is the smaller of the two
+    # the pair kernel's own ALU bound, from its far-pair loop: the directed kernel
+    # needs 7 FP32 lane operations and one MUFU reciprocal a pair, the
+    # symmetric one (tile pairs, one reciprocal for both directions) 5.5 and 0.5
+    sym = bool(tuning and tuning["laplace_fp32"]["splits"] < 0) if tuning else M >= 8960
+    ops_pair, mufu_pair = (5.5, 0.5) if sym else (7.0, 1.0)
     lane_ops = fp32_peak * 1e12 / 2.0
-    pipe_bound_pairs = min(lane_ops / 7.0, peaks["mufu_rcp_tops"] * 1e12)
+    pipe_bound_pairs = min(lane_ops / ops_pair, peaks["mufu_rcp_tops"] * 1e12 / mufu_pair)
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -880,7 +884,9 @@ def main():
                      "flops_per_pair": FLOPS_PER_PAIR[kind], "launch_ms": per_launch_ms,
                      "pipe_bound_pairs_per_s": pipe_bound_pairs,
                      "frac_of_pipe_bound": (pairs_per_launch / (per_launch_ms / 1e3)) / pipe_bound_pairs,
-                     "pipe_bound_note": "far pairs: 7 FP32 lane operations + 1 MUFU rcp each; measured MUFU rate"},
+                     "pair_kernel": "symmetric (k_pair32s)" if sym else "directed (k_pair32)",
+                     "pipe_bound_note": (f"far pairs: {ops_pair} FP32 lane operations + {mufu_pair} MUFU rcp each, "
+                                         "at the measured FFMA and MUFU rates")},
         "clocks": clocks,
     }
     if args.four_disc_steps > 0:

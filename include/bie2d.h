@@ -181,10 +181,17 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
  * of that shape, in any context of the process, use it (the occupancy rule is
  * kept unless another plan is faster by 2%).  A different plan changes the
  * summation order, so results of that shape may change in rounding.
- * splits (nullable): on input 0 to search, or a count to install a uniform plan
- * without timing (rounded to the counts the source chunking allows); on output
- * the number of splits of the plan kept.  ms (nullable) receives its time (0
- * when installed untimed).  Errors as for apply_operator. */
+ * The FP32 and float-float Laplace pair sums have one more candidate, the
+ * symmetric kernels (one CTA per unordered pair of 256-node tiles, each
+ * difference, |r|^2 and reciprocal serving both directions of a pair; one
+ * partial slot per tile), which are also the occupancy rule's plans once the
+ * tile pairs fill the GPU four times over.
+ * splits (nullable): on input 0 to search, a positive count to install a
+ * uniform plan without timing (rounded to the counts the source chunking
+ * allows), or a negative value to install the symmetric plan (Laplace with
+ * BIE_PREC_MIXED or BIE_PREC_MIXED_FF only, else BIE_ERR_INVALID); on output
+ * the number of splits of the plan kept, negated for the symmetric plan.  ms (nullable) receives its time (0 when
+ * installed untimed).  Errors as for apply_operator. */
 int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
              void* stream);
 /* Forget every tuned split count (back to the occupancy rule). */

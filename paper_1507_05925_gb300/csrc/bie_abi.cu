@@ -1427,10 +1427,12 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
     return fail(ctx, BIE_ERR_INVALID, "bad precision");
   DeviceGuard dg(ctx->device);
   const int N = geom->n_bodies, M = bs[N];
-  if (splits && *splits > 0) {  // install the given count, no timing
-    const PairPlan p = plan_with_splits(M, *splits);
+  if (splits && *splits != 0) {  // install a plan, no timing
+    if (*splits < 0 && (precision == BIE_PREC_FP64 || kind != BIE_KIND_LAPLACE))
+      return fail(ctx, BIE_ERR_INVALID, "the symmetric plan exists for the FP32 and float-float Laplace pair sums only");
+    const PairPlan p = *splits > 0 ? plan_with_splits(M, *splits) : plan_symmetric(M);
     set_tuned_plan(M, kind, precision, p);
-    *splits = p.S;
+    *splits = p.sym ? -p.S : p.S;
     if (ms) *ms = 0.0;
     return BIE_OK;
   }
@@ -1456,7 +1458,7 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   for (int c : {S0 / 2, (2 * S0) / 3, (3 * S0) / 2, 2 * S0, 3 * S0, 4 * S0, 6 * S0, 1}) add(plan_with_splits(M, std::max(1, c)));
   for (int t : {1, 2, 3, 4}) add(plan_with_splits(M, (M + 256 * t - 1) / (256 * t)));
   // the symmetric FP32 Laplace kernel, while its partials (one slot per tile) stay small
-  if (precision == BIE_PREC_MIXED && kind == BIE_KIND_LAPLACE) {
+  if (precision != BIE_PREC_FP64 && kind == BIE_KIND_LAPLACE) {
     const PairPlan ps = plan_symmetric(M);
     if ((double)ps.S * M * sizeof(double) <= (1 << 30) && ps.S <= 4096) add(ps);
   }
@@ -1519,7 +1521,7 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
     best_ms = s0_ms;
   }
   set_tuned_plan(M, kind, precision, best);
-  if (splits) *splits = best.S;
+  if (splits) *splits = best.sym ? -best.S : best.S;
   if (ms) *ms = best_ms;
   return BIE_OK;
 }

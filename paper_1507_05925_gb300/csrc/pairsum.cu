@@ -747,6 +747,164 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
   }
 }
 
+// ------------------------------------------------- symmetric float-float ----
+// The float-float Laplace pair sum on unordered pairs of 256-node tiles, each
+// reciprocal (MUFU seed + one float-float Newton step) and each difference and
+// |r|^2 serving both directions: target a gains q_b r w, target b gains
+// -q_a r w.  Float-float positions give exact leading differences for every
+// pair, so every pair of different tiles takes the symmetric loop; a tile
+// with itself (the self pairs) runs the directed float-float pass.  The
+// source's float-float accumulator travels between lanes by warp shuffle on
+// the diagonal schedule of k_pair32s.  Partials: FP64, one slot per (source
+// tile, target tile), projected on the target normal in FP64.
+constexpr int kTFS = 2;                      // targets a lane
+constexpr int kBFS = kTileF / kTFS;          // 128 threads a CTA
+
+__device__ __forceinline__ void ff_write_projected(const Geo& g, int a, int slot, float xh, float xl, float yh,
+                                                   float yl, double* __restrict__ partial) {
+  const double dax = (double)xh + (double)xl, day = (double)yh + (double)yl;
+  partial[(long long)slot * g.M + a] = g.nx[a] * dax + g.ny[a] * day;
+}
+
+__global__ void __launch_bounds__(kBFS, 6) k_pair_ffs(Geo g, int ntile, double* __restrict__ partial,
+                                                     const double* __restrict__ sscale, VecRef vr,
+                                                     const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ float4 sA[kTileF];  // (xh, xm, yh, ym)
+  __shared__ float4 sC[kTileF];  // (xl, yl, qh, ql)
+  __shared__ float4 accB[kBFS / 32][kTileF];  // per warp: the sources' (xh, xl, yh, yl)
+  const double* __restrict__ v = vr.ptr();
+  const int M = g.M;
+  int ti, tj;
+  tri_decode(blockIdx.x, ti, tj);
+  const int A0 = ti * kTileF, B0 = tj * kTileF;
+  if (ti == tj) {
+    // directed float-float pass of the tile with itself (excludes r = 0)
+    const int a1 = min(M, A0 + kTileF), nt = a1 - A0;
+    for (int l = threadIdx.x; l < nt; l += kBFS) {
+      const int b = A0 + l;
+      const float4 xa = g.xff[b];
+      const float2 xl = g.xfl[b];
+      const double q = sscale[b] * v[b];
+      const float qh = (float)q;
+      sA[l] = xa;
+      sC[l] = make_float4(xl.x, xl.y, qh, (float)(q - (double)qh));
+    }
+    __syncthreads();
+    for (int m = 0; m < kTFS; ++m) {
+      const int a = A0 + threadIdx.x + m * kBFS;
+      if (a >= M) continue;
+      FFTarget t;
+      const float4 p = g.xff[a];
+      const float2 pl = g.xfl[a];
+      t.xh = p.x; t.xm = p.y; t.yh = p.z; t.ym = p.w; t.xl = pl.x; t.yl = pl.y;
+      t.n = make_float4(0.f, 0.f, 0.f, 0.f);
+      float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
+      for (int l = 0; l < nt; ++l) {
+        if (A0 + l == a) continue;
+        const float4 c = sC[l];
+        float cxh, cxl, cyh, cyl;
+        ff_pair<0>(t, sA[l], make_float2(c.x, c.y), make_float4(c.z, c.w, 0.f, 0.f), cxh, cxl, cyh, cyl);
+        ff_acc(axh, axl, cxh, cxl);
+        ff_acc(ayh, ayl, cyh, cyl);
+      }
+      ff_write_projected(g, a, ti, axh, axl, ayh, ayl, partial);
+    }
+    return;
+  }
+  // sources of tile B; padding far from everything with zero strength
+  for (int l = threadIdx.x; l < kTileF; l += kBFS) {
+    const int b = B0 + l;
+    float4 xa = make_float4(1e15f, 0.f, 1e15f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b < M) {
+      xa = g.xff[b];
+      const float2 xl = g.xfl[b];
+      const double q = sscale[b] * v[b];
+      const float qh = (float)q;
+      c = make_float4(xl.x, xl.y, qh, (float)(q - (double)qh));
+    }
+    sA[l] = xa;
+    sC[l] = c;
+  }
+  // kTFS targets of tile A a lane (all of tile A is inside [0, M): ti < tj)
+  float txh[kTFS], txm[kTFS], txl[kTFS], tyh[kTFS], tym[kTFS], tyl[kTFS], qah[kTFS], qal[kTFS];
+  float axh[kTFS], axl[kTFS], ayh[kTFS], ayl[kTFS];
+#pragma unroll
+  for (int m = 0; m < kTFS; ++m) {
+    const int a = A0 + threadIdx.x + m * kBFS;
+    const float4 p = g.xff[a];
+    const float2 pl = g.xfl[a];
+    txh[m] = p.x; txm[m] = p.y; tyh[m] = p.z; tym[m] = p.w; txl[m] = pl.x; tyl[m] = pl.y;
+    const double q = sscale[a] * v[a];
+    qah[m] = (float)q;
+    qal[m] = (float)(q - (double)qah[m]);
+    axh[m] = axl[m] = ayh[m] = ayl[m] = 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < kTileF; r0 += 32) {
+    float bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;  // travels with its source
+#pragma unroll 2
+    for (int k = 0; k < 32; ++k) {
+      const int l = r0 + ((lane + k) & 31);
+      const float4 sa = sA[l], sc = sC[l];
+#pragma unroll
+      for (int m = 0; m < kTFS; ++m) {
+        float dxh, dxl, dyh, dyl;
+        ff_diff(txh[m], txm[m], txl[m], sa.x, sa.y, sc.x, dxh, dxl);
+        ff_diff(tyh[m], tym[m], tyl[m], sa.z, sa.w, sc.y, dyh, dyl);
+        // |r|^2 and 1/|r|^2 in float-float, as in the directed pair
+        const float p1 = dxh * dxh, p1e = fmaf(dxh, dxh, -p1);
+        const float p2 = dyh * dyh, p2e = fmaf(dyh, dyh, -p2);
+        const float s2 = p1 + p2;
+        const float se = fminf(p1, p2) - (s2 - fmaxf(p1, p2));
+        const float lo = fmaf(2.0f, fmaf(dxh, dxl, dyh * dyl), (se + p1e) + p2e);
+        const float r2h = s2 + lo;
+        const float r2l = lo - (r2h - s2);
+        const float y0 = rcp_approx(r2h);
+        const float ee = fmaf(-r2l, y0, fmaf(-r2h, y0, 1.0f));
+        const float il = y0 * ee;
+        float ch, cl, ph, pl;
+        // target a gains q_b r w
+        ff_mul(sc.z, sc.w, y0, il, ch, cl);
+        ff_mul(ch, cl, dxh, dxl, ph, pl);
+        ff_acc(axh[m], axl[m], ph, pl);
+        ff_mul(ch, cl, dyh, dyl, ph, pl);
+        ff_acc(ayh[m], ayl[m], ph, pl);
+        // the source gains -q_a r w
+        ff_mul(qah[m], qal[m], y0, il, ch, cl);
+        ff_mul(ch, cl, dxh, dxl, ph, pl);
+        ff_acc(bxh, bxl, -ph, -pl);
+        ff_mul(ch, cl, dyh, dyl, ph, pl);
+        ff_acc(byh, byl, -ph, -pl);
+      }
+      const int nxt = (lane + 1) & 31;
+      bxh = __shfl_sync(0xffffffffu, bxh, nxt);
+      bxl = __shfl_sync(0xffffffffu, bxl, nxt);
+      byh = __shfl_sync(0xffffffffu, byh, nxt);
+      byl = __shfl_sync(0xffffffffu, byl, nxt);
+    }
+    accB[warp][r0 + lane] = make_float4(bxh, bxl, byh, byl);
+  }
+#pragma unroll
+  for (int m = 0; m < kTFS; ++m)
+    ff_write_projected(g, A0 + threadIdx.x + m * kBFS, tj, axh[m], axl[m], ayh[m], ayl[m], partial);
+  __syncthreads();
+  for (int l = threadIdx.x; l < kTileF; l += kBFS) {
+    const int b = B0 + l;
+    if (b >= M) continue;
+    // the warps' sums in a fixed order
+    float4 t = accB[0][l];
+#pragma unroll
+    for (int w = 1; w < kBFS / 32; ++w) {
+      const float4 u = accB[w][l];
+      ff_acc(t.x, t.y, u.x, u.y);
+      ff_acc(t.z, t.w, u.z, u.w);
+    }
+    ff_write_projected(g, b, ti, t.x, t.y, t.z, t.w, partial);
+  }
+}
+
 // --------------------------------------------------------------- epilogue ----
 constexpr int kBE = 256;
 
@@ -875,6 +1033,72 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
       out[2 * a] = sign * (0.5 * v[2 * a] + os * y1);
       out[2 * a + 1] = sign * (0.5 * v[2 * a + 1] + os * y2);
     }
+  }
+}
+
+// Sum of the float-float partial slots of the FP32 pair sums, wide: a CTA
+// takes 32 target entries x 8 slot groups; each thread adds slots g, g + 8, ...
+// in float-float, the 8 group sums are combined in a fixed order
+// (deterministic), and the total overwrites slot 0 as a double (the entry's
+// own 8 bytes, after every thread has read it).  cw = float-float pairs per
+// target entry (1 Laplace, 2 Stokes).
+constexpr int kRT = 32, kRG = 8;
+
+__global__ void __launch_bounds__(kRT * kRG) k_reduce_slots(double* __restrict__ partial, int S, long long n,
+                                                            const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ float sh[kRG][kRT], sl[kRG][kRT];
+  const int tx = threadIdx.x % kRT, grp = threadIdx.x / kRT;
+  const long long e = (long long)blockIdx.x * kRT + tx;  // a float-float entry
+  const float2* __restrict__ pf2 = reinterpret_cast<const float2*>(partial);
+  float h = 0.f, l = 0.f, h2 = 0.f, l2 = 0.f;
+  if (e < n) {
+    int s = grp;
+    for (; s + kRG < S; s += 2 * kRG) {
+      const float2 u = pf2[(long long)s * n + e], v = pf2[(long long)(s + kRG) * n + e];
+      ffadd(h, l, u.x, u.y);
+      ffadd(h2, l2, v.x, v.y);
+    }
+    if (s < S) {
+      const float2 u = pf2[(long long)s * n + e];
+      ffadd(h, l, u.x, u.y);
+    }
+    ffadd(h, l, h2, l2);
+  }
+  sh[grp][tx] = h;
+  sl[grp][tx] = l;
+  __syncthreads();
+  if (grp == 0 && e < n) {
+    float th = sh[0][tx], tl = sl[0][tx];
+#pragma unroll
+    for (int q = 1; q < kRG; ++q) ffadd(th, tl, sh[q][tx], sl[q][tx]);
+    partial[e] = (double)th + (double)tl;
+  }
+}
+
+// The same for FP64 partial slots (FP64 and float-float pair sums).
+__global__ void __launch_bounds__(kRT * kRG) k_reduce_slots64(double* __restrict__ partial, int S, long long n,
+                                                              const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ double sd[kRG][kRT];
+  const int tx = threadIdx.x % kRT, grp = threadIdx.x / kRT;
+  const long long e = (long long)blockIdx.x * kRT + tx;
+  double a = 0.0, b = 0.0;
+  if (e < n) {
+    int s = grp;
+    for (; s + kRG < S; s += 2 * kRG) {
+      a += partial[(long long)s * n + e];
+      b += partial[(long long)(s + kRG) * n + e];
+    }
+    if (s < S) a += partial[(long long)s * n + e];
+  }
+  sd[grp][tx] = a + b;
+  __syncthreads();
+  if (grp == 0 && e < n) {
+    double t = sd[0][tx];
+#pragma unroll
+    for (int q = 1; q < kRG; ++q) t += sd[q][tx];
+    partial[e] = t;
   }
 }
 
@@ -1028,9 +1252,10 @@ PairPlan plan_pairs(int M, int kind, int precision) {
 
 PairPlan occupancy_plan(int M, int kind, int precision) {
   const DeviceShape& d = device_shape();
-  if (precision == 1 && kind == 0) {
-    // the symmetric FP32 Laplace kernel once its tile pairs fill the GPU a few
-    // times over and its partials (one slot per tile) stay within 256 MB
+  if ((precision == 1 || precision == 2) && kind == 0) {
+    // the symmetric FP32 / float-float Laplace kernels once their tile pairs fill
+    // the GPU a few times over and their partials (one slot per tile) stay
+    // within 256 MB
     const long long nt = (M + kTS - 1) / kTS;
     if (nt * (nt + 1) / 2 >= 4LL * d.nsm && nt * (long long)M * 8 <= (256LL << 20)) return plan_symmetric(M);
   }
@@ -1110,7 +1335,10 @@ void launch_pairs(const Geo& g, int kind, int precision, const PairPlan& p, VecR
     note_launches(1);
   } else {
     dim3 grid((g.M + kBF * kTF - 1) / (kBF * kTF), p.S);
-    if (kind == 0)
+    if (kind == 0 && !BATCH && p.sym) {
+      const long long nt = (g.M + kTileF - 1) / kTileF;
+      k_pair_ffs<<<(unsigned)(nt * (nt + 1) / 2), kBFS, 0, s>>>(g, (int)nt, partial, sscale, v, stop);
+    } else if (kind == 0)
       k_pair_ff<0, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p, partial, stop);
     else
       k_pair_ff<1, BATCH><<<grid, kBF, 0, s>>>(g, v, sscale, p, partial, stop);
@@ -1134,6 +1362,17 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
                      cudaStream_t s, double alpha, bool pff) {
+  if (p.S >= kRG) {
+    // add the slots wide first (float-float or FP64), then an epilogue over one FP64 slot
+    const long long n = (long long)g.M * (kind + 1);
+    const unsigned nb = (unsigned)((n + kRT - 1) / kRT);
+    if (pff)
+      k_reduce_slots<<<nb, kRT * kRG, 0, s>>>(const_cast<double*>(partial), p.S, n, stop);
+    else
+      k_reduce_slots64<<<nb, kRT * kRG, 0, s>>>(const_cast<double*>(partial), p.S, n, stop);
+    note_launches(1);
+    return epilogue(g, kind, uniform_plan(1, g.M), v, partial, scaled, with_L, sign, out, stop, s, alpha, false);
+  }
   // one block per body, sized to the bodies (many small bodies: small blocks)
   const int avg = g.M / std::max(1, g.N);
   if (avg <= 64) {

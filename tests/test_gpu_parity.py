@@ -568,6 +568,8 @@ def test_symmetric_pair_sum_operator_and_solve(ctx):
     v = np.random.default_rng(5).standard_normal(M)
     ref = laplace.apply(geo, v)
     bie.tune_clear()
+    rc, S, _ = bie.tune(ctx, gd, bie.LAPLACE, bie.MIXED, splits=-1)  # the symmetric plan, explicitly
+    assert rc == bie.OK and S == -((M + 255) // 256)
     out = torch.empty(M, dtype=torch.float64, device="cuda")
     assert bie.apply_operator(ctx, gd, bie.LAPLACE, bie.MIXED, torch.from_numpy(v).cuda(), out) == bie.OK
     torch.cuda.synchronize()
@@ -577,9 +579,22 @@ def test_symmetric_pair_sum_operator_and_solve(ctx):
     assert err <= TOL32[0]
     # the directed kernel (a uniform split plan installed untimed) agrees
     rc, S, _ = bie.tune(ctx, gd, bie.LAPLACE, bie.MIXED, splits=24)
-    assert rc == bie.OK
+    assert rc == bie.OK and S > 0
     assert bie.apply_operator(ctx, gd, bie.LAPLACE, bie.MIXED, torch.from_numpy(v).cuda(), out) == bie.OK
     torch.cuda.synchronize()
+    bie.tune_clear()
+    # the symmetric plan is the occupancy rule's for this size; Stokes and FP64 have none
+    assert bie.tune(ctx, gd, bie.STOKES, bie.MIXED, splits=-1)[0] == bie.ERR_INVALID
+    assert bie.tune(ctx, gd, bie.LAPLACE, bie.FP64, splits=-1)[0] == bie.ERR_INVALID
+    # the symmetric float-float kernel against the oracle (and the directed one)
+    for S in (-1, 24):
+        rc, SS, _ = bie.tune(ctx, gd, bie.LAPLACE, bie.MIXED_FF, splits=S)
+        assert rc == bie.OK and (SS < 0) == (S < 0)
+        assert bie.apply_operator(ctx, gd, bie.LAPLACE, bie.MIXED_FF, torch.from_numpy(v).cuda(), out) == bie.OK
+        torch.cuda.synchronize()
+        e = rel_max(out.cpu().numpy(), ref)
+        print(f"float-float Laplace operator, plan {SS}: {e:.2e}")
+        assert e <= TOLFF
     bie.tune_clear()
     assert rel_max(out.cpu().numpy(), ref) <= TOL32[0]
     assert rel_max(out.cpu().numpy(), sym) <= 2 * TOL32[0]
