@@ -216,6 +216,19 @@ void bie_tune_clear(void);
  * pair sums only (fmm_order 0), no density output; interior points for all
  * problems or for none; 1 <= count <= 65535.  Errors: BIE_ERR_INVALID for a bad
  * argument in any problem (message names it). */
+/* Batches of small problems -- every problem at most 1,024 nodes and 128
+ * bodies, BIE_PREC_MIXED_FF, direct pair sums (fmm_order 0), restart <= 50 --
+ * are solved by one persistent launch with one CTA per problem that runs the
+ * problem's whole refinement (FP32-pair-sum GMRES on the correction equation
+ * with the per-body weighted completion, no preconditioner; float-float
+ * residuals; all reductions inside the CTA, in a fixed order), with no host
+ * round trip until the end.  Each problem then stops at its own tolerance and
+ * its bie_info counts (iters, refinements, matvecs) are its own.
+ * bie_small_batch_path(0) sends such batches through the multi-launch path
+ * instead (lockstep GMRES over the block-diagonal system); process-wide,
+ * default on. */
+void bie_small_batch_path(int enable);
+
 int elastance_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* q,
                           double* const* phi, const bie_opts* opts, bie_info* info, int* status, void* stream);
 int mobility_solve_batch(bie_ctx* ctx, int count, const bie_geometry* geoms, const double* const* FT,

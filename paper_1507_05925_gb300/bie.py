@@ -128,6 +128,8 @@ def load():
     lib.bie_tune_clear.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
     lib.bie_profile.restype = i32
+    lib.bie_small_batch_path.argtypes = [i32]
+    lib.bie_small_batch_path.restype = None
     lib.bie_measure_alu_peaks.argtypes = [i32, ctypes.POINTER(dbl)]
     lib.bie_measure_alu_peaks.restype = i32
     lib.bie_test_arm_barrier_timeout.argtypes = [i32, ctypes.c_longlong]
@@ -311,6 +313,11 @@ def test_precond_pivot_floor(floor: float) -> None:
 
 test_arm_barrier_timeout.__test__ = False  # hooks, not tests: pytest must not collect them
 test_precond_pivot_floor.__test__ = False
+
+
+def small_batch_path(enable: bool) -> None:
+    """bie_small_batch_path: one-launch solves of batches of small problems on or off."""
+    load().bie_small_batch_path(1 if enable else 0)
 
 
 def measure_alu_peaks(device: int = 0) -> dict:

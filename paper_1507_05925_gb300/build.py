@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbie2d.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["bie_abi.cu", "pairsum.cu", "krylov.cu", "geometry.cu", "noalloc.cu", "server.cu", "fmm.cu", "precond.cu",
-           "peaks.cu"]
+           "peaks.cu", "small.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE]
 

@@ -164,6 +164,7 @@ struct Work {
   double* pscale = nullptr;
   double* pnorm = nullptr;  // per-problem residual norms of the refinement
   double* pnet = nullptr;   // per-problem net load and largest |load|
+  SmallInfo* sinfo = nullptr;  // one-launch small-problem solves: per-problem counts
   // batched GMRES (one Krylov space per problem): element ranges of the fused
   // Arnoldi step and per-problem state; seg.P == 0 for a single system
   SegArgs seg;
@@ -250,6 +251,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     w.pscale = A.take<double>(nprob);
     w.pnorm = A.take<double>(nprob);
     w.pnet = A.take<double>(2 * nprob);
+    w.sinfo = A.take<SmallInfo>(nprob);
   }
   if (nprob > 1) {
     w.prange = A.take<int2>(N);
@@ -957,7 +959,20 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const int P = batch ? batch->P : 1;
   const int nload = kind == 0 ? N : 3 * N;
   Work w;
-  const bool use_bj = o.precond == 0;
+  // batches of small problems: one persistent launch, one CTA per problem
+  // running the whole float-float refinement (no host round trip, no
+  // preconditioner)
+  int small_nodes = 0;
+  bool small = false;
+  if (batch && small_batch_path() && o.precision == BIE_PREC_MIXED_FF && o.fmm_order == 0) {
+    int max_bodies = 0;
+    for (int p = 0; p < P; ++p) {
+      small_nodes = std::max(small_nodes, bs[pb[p + 1]] - bs[pb[p]]);
+      max_bodies = std::max(max_bodies, pb[p + 1] - pb[p]);
+    }
+    small = small_batch_eligible(small_nodes, max_bodies, o.restart);
+  }
+  const bool use_bj = o.precond == 0 && !small;
   const long long bjf = use_bj ? bj_block_floats(bs.data(), N, kind) : 0;
   Arena sz{nullptr};
   carve(sz, w, N, M, kind, o.restart, true, true, has_ipt, true, false, bjf, batch ? P : 0, bs.data(), pb.data());
@@ -1029,7 +1044,31 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     return w.seg.P > 1 ? gmres_seg(ctx, w, op, b, x, tol_rel, maxit, verify, kr, s)
                        : gmres(ctx, w, op, b, x, tol_rel, maxit, verify, kr, s);
   };
-  if (o.precision == BIE_PREC_FP64) {
+  std::vector<SmallInfo> sinfo;
+  {
+    if (small) {
+      CK(small_batch_solve(w.g, kind, P, w.pbody, w.pnode, w.f, w.xs, w.r, w.d, w.rc, w.rin, w.ytmp, w.V, w.ld, w.m,
+                           tol_user, o.inner_tol, o.max_refine, o.max_iter, small_nodes, w.sinfo, s));
+      sinfo.resize(P);
+      CK(cudaMemcpyAsync(sinfo.data(), w.sinfo, P * sizeof(SmallInfo), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      converged = true;
+      for (const SmallInfo& q : sinfo) {
+        iters = std::max(iters, q.iters);
+        refs = std::max(refs, q.refinements);
+        m32 += q.matvecs32;
+        mff += q.matvecsff;
+        eps32_report = std::max(eps32_report, q.fp32_error);
+        prob_rel.push_back(q.rel_residual);
+        relres = std::max(relres, q.rel_residual);
+        converged = converged && q.rel_residual <= tol_user;
+      }
+      relres_per_problem = true;
+    }
+  }
+  if (small) {
+    // solved above
+  } else if (o.precision == BIE_PREC_FP64) {
     KrylovResult kr;
     // batched: every problem to the relative tolerance on its own right-hand side
     if ((rc = krylov(op64, w.f, w.xs, w.seg.P > 1 ? tol_user : o.tol, o.max_iter, true, kr))) return rc;
@@ -1222,6 +1261,12 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
         q.matvecs_fp64 = m64;
         q.matvecs_fp32 = m32;
         q.matvecs_ff = mff;
+        if (small) {  // the one-launch path: each problem's own counts
+          q.iters = sinfo[p].iters;
+          q.refinements = sinfo[p].refinements;
+          q.matvecs_fp32 = sinfo[p].matvecs32;
+          q.matvecs_ff = sinfo[p].matvecsff;
+        }
         q.rel_residual = prob_rel[p];
         q.constraint_residual = cmax / std::max(mx, 1e-300);
         q.net_load = net;
@@ -1529,6 +1574,8 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
 void bie_tune_clear(void) { clear_tuned_splits(); }
 
 void bie_test_arm_barrier_timeout(int skip_cta, long long spins) { arm_barrier_fault(skip_cta, spins); }
+
+void bie_small_batch_path(int enable) { set_small_batch_path(enable != 0); }
 
 void bie_test_precond_pivot_floor(double floor) { set_bj_pivot_floor(floor); }
 

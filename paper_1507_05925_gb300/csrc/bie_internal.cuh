@@ -264,6 +264,29 @@ void set_bj_pivot_floor(double floor);
 cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
                      const int* stop, int max_nb, cudaStream_t s, bool f64 = false);
 
+// ---------------------------------------------------------------- small.cu
+// One-launch solves of batches of small problems (one CTA per problem, the
+// whole float-float refinement inside it).
+constexpr int kSmallMaxNodes = 1024;
+constexpr int kSmallMaxBodies = 128;
+struct SmallInfo {
+  int iters, refinements, matvecs32, matvecsff;
+  double rel_residual, fp32_error;
+};
+bool small_batch_eligible(int max_nodes, int max_bodies, int restart);
+// Every problem p of the batch: solve the sqrt(w)-scaled total-density system
+// with right-hand side f (batch layout, per-problem entries [pnode[p],
+// pnode[p+1]), bodies [pbody[p], pbody[p+1])) into x, to tol relative to its
+// own ||f||; r, d, rc, rin, y are batch-layout scratch vectors and V the basis
+// rows (V + i ld).  info[p] receives the counts.
+cudaError_t small_batch_solve(const Geo& g, int kind, int P, const int* pbody, const long long* pnode,
+                              const double* f, double* x, double* r, double* d, double* rc, double* rin, double* y,
+                              double* V, long long ld, int m, double tol, double inner_tol, int max_refine,
+                              int max_iter, int max_nodes, SmallInfo* info, cudaStream_t s);
+// the one-launch path for batches of small problems: on (default) or off
+void set_small_batch_path(bool on);
+bool small_batch_path();
+
 // ---------------------------------------------------------------- krylov.cu
 constexpr int kMaxVecGrid = 608;  // largest grid of the vector kernels and the Arnoldi step
 int vec_grid(long long n);

@@ -160,6 +160,14 @@ def test_batch_iterations_follow_the_slowest_problem(ctx, kind):
         g = synth.four_discs(seed=i)
         load = synth.charges(4, rng) if kind == 0 else synth.forces_torques(4, rng).reshape(-1)
         probs.append((g, np.ascontiguousarray(load)))
+    bie.small_batch_path(False)  # the lockstep multi-launch path (small batches default to one launch)
+    try:
+        _lockstep_iterations(ctx, kind, probs)
+    finally:
+        bie.small_batch_path(True)
+
+
+def _lockstep_iterations(ctx, kind, probs):
     for prec in (bie.FP64, bie.MIXED_FF):
         opts = bie.make_opts(precision=prec)
         rc, infos, _, outs = _solve_batch(ctx, kind, probs, opts)
@@ -256,3 +264,52 @@ def test_batch_of_many_small_problems(ctx, kind):
     for i in range(0, 700, 35):
         g, load = probs[i]
         assert rel2(outs[i], _oracle(kind, g, load)) <= TOL_SOLVE
+
+
+# ---------------------------------------------------------------------------
+# one persistent launch for batches of small problems (one CTA per problem)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [0, 1])
+def test_one_launch_small_batches(ctx, kind):
+    probs = []
+    rng = np.random.default_rng(130 + kind)
+    for _ in range(24):  # 1-4 bodies of 40-200 nodes: at most 800 nodes a problem
+        g = synth.random_request(rng, max_bodies=4, nodes=(40, 64, 137, 200))
+        N = g["body_start"].size - 1
+        load = synth.charges(N, rng) if kind == 0 else synth.forces_torques(N, rng).reshape(-1)
+        probs.append((g, np.ascontiguousarray(load)))
+    g, load = probs[5]
+    probs[5] = (g, np.zeros_like(load))  # a zero load: exactly zero out
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    rc, infos, status, outs = _solve_batch(ctx, kind, probs, opts, device=True)
+    assert rc == bie.OK, (rc, ctx.last_error())
+    assert np.all(outs[5] == 0.0)
+    for i, ((gg, ld), out) in enumerate(zip(probs, outs)):
+        if not np.any(ld):  # problem 5, and one-body problems (mean-free charges are zero)
+            assert np.all(out == 0.0)
+            continue
+        assert rel2(out, _oracle(kind, gg, ld)) <= TOL_SOLVE
+        assert infos[i]["rel_residual"] <= 1e-12 and infos[i]["refinements"] >= 1
+    # each problem stops on its own: the counts differ between problems
+    assert len({q["iters"] for q in infos}) > 1
+    # the multi-launch path gives the same solutions
+    bie.small_batch_path(False)
+    try:
+        rc2, _, _, outs2 = _solve_batch(ctx, kind, probs, opts, device=True)
+    finally:
+        bie.small_batch_path(True)
+    assert rc2 == bie.OK
+    for (gg, ld), o1, o2 in zip(probs, outs, outs2):
+        if np.any(ld):
+            assert rel2(o1, o2) <= TOL_SOLVE
+
+
+def test_one_launch_is_deterministic_and_handles_a_batch_of_one(ctx):
+    g = synth.four_discs(seed=3)
+    rng = np.random.default_rng(7)
+    probs = [(g, synth.charges(4, rng))]
+    opts = bie.make_opts(precision=bie.MIXED_FF)
+    r1 = _solve_batch(ctx, 0, probs, opts)[3][0]
+    r2 = _solve_batch(ctx, 0, probs, opts)[3][0]
+    assert np.array_equal(r1, r2)
+    assert rel2(r1, _oracle(0, *probs[0])) <= TOL_SOLVE
