@@ -529,23 +529,38 @@ def run_large(args, rank, local):
     UW = torch.empty(3 * N, dtype=torch.float64, device=dev)
     ctx = bie.Context(local)
     opts = bie.make_opts(precision=bie.MIXED_FF, fmm_order=args.fmm_order)
-    rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
-    assert rc == bie.OK, (rc, ctx.last_error())
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(args.large_steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+
+    def timed_solves():
         rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
-        e1.record()
+        assert rc == bie.OK, (rc, ctx.last_error())
         torch.cuda.synchronize()
-        assert rc == bie.OK
-        ms.append(e0.elapsed_time(e1))
+        ms = []
+        for _ in range(args.large_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
+            e1.record()
+            torch.cuda.synchronize()
+            assert rc == bie.OK
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms)), info
+
+    ms_default, info_default = timed_solves()
+    out = {"workload": "ellipses10000_M640000 (hexagonal lattice, area fraction %.2f)" % g["area_fraction"],
+           "M": int(g["x"].size), "fmm_order": args.fmm_order, "precision": "mixed_ff",
+           "default_schedule": {"leaf_nodes": 24, "inner_order": (args.fmm_order + 1) // 2,
+                                "seconds_per_solve": ms_default / 1e3, "info": info_default}}
+    ms, info = ms_default, info_default
+    if not args.no_tune:
+        # the FMM schedule (leaf population, inner order) tuned by timing whole solves
+        rc, leaf, inner, tms = bie.tune_fmm(ctx, gd, 1, FT, opts)
+        assert rc == bie.OK, ctx.last_error()
+        ms, info = timed_solves()
+        out["tuned_schedule"] = {"leaf_nodes": leaf, "inner_order": inner, "seconds_per_solve": ms / 1e3,
+                                 "info": info}
     ctx.close()
-    return {"workload": "ellipses10000_M640000 (hexagonal lattice, area fraction %.2f)" % g["area_fraction"],
-            "M": int(g["x"].size), "fmm_order": args.fmm_order, "precision": "mixed_ff",
-            "seconds_per_solve": float(np.mean(ms)) / 1e3, "solves_per_s": 1e3 / float(np.mean(ms)),
-            "info": info}
+    out.update({"seconds_per_solve": ms / 1e3, "solves_per_s": 1e3 / ms, "info": info})
+    return out
 
 
 def run_mobility(args, rank, local):

@@ -194,7 +194,22 @@ int mobility_solve(bie_ctx* ctx, const bie_geometry* geom, const double* FT, dou
  * installed untimed).  Errors as for apply_operator. */
 int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, int* splits, double* ms,
              void* stream);
-/* Forget every tuned split count (back to the occupancy rule). */
+/* FMM schedule tuning (no counterpart in the paper).  Times whole solves of
+ * this geometry and load (kind 0 elastance, 1 mobility; opts->fmm_order = p in
+ * 2..64 and a mixed precision) for candidate leaf populations (the leaf level
+ * is the finest whose non-empty leaves hold at least 12, 24 or 48 nodes) and
+ * inner-solve FMM orders (ceil(p/2) + {-4, -2, 0, 2, 4} within 2..p: a lower
+ * order makes each inner iteration cheaper but may cost refinement steps), the
+ * faster of two runs after a warm-up, and keeps the fastest candidate whose
+ * solve converged for this device and shape (M, kind, p): later FMM solves and
+ * apply_operator_fmm calls of that shape use it (the defaults 24 and
+ * ceil(p/2) are kept unless another candidate is faster by 2%).  leaf_nodes,
+ * inner_order and ms (nullable) receive the schedule kept and its solve time.
+ * Errors as for the solves. */
+int bie_tune_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, const double* load, const bie_opts* opts,
+                 int* leaf_nodes, int* inner_order, double* ms, void* stream);
+
+/* Forget every tuned split count and FMM schedule (back to the defaults). */
 void bie_tune_clear(void);
 
 /* Batched solves (no counterpart in the paper: a throughput path for many small

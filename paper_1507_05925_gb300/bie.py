@@ -124,6 +124,9 @@ def load():
     lib.bie_tune.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, ctypes.POINTER(i32),
                              ctypes.POINTER(ctypes.c_double), vp]
     lib.bie_tune.restype = i32
+    lib.bie_tune_fmm.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, vp, ctypes.POINTER(BieOpts),
+                                 ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), vp]
+    lib.bie_tune_fmm.restype = i32
     lib.bie_tune_clear.argtypes = []
     lib.bie_tune_clear.restype = None
     lib.bie_profile.argtypes = [vp, i32, ctypes.POINTER(BieProfileCounters)]
@@ -328,6 +331,18 @@ def measure_alu_peaks(device: int = 0) -> dict:
         raise RuntimeError(f"bie_measure_alu_peaks failed with status {rc}")
     return {"fp32_ffma_tflops": out[0], "fp32_ffma2_tflops": out[1], "mufu_rcp_tops": out[2],
             "fp64_dfma_tflops": out[3]}
+
+
+def tune_fmm(ctx: Context, geom, kind: int, load, opts: BieOpts, stream=None):
+    """bie_tune_fmm of include/bie2d.h: time whole FMM solves over leaf populations
+    and inner orders, keep the fastest converged schedule for this shape;
+    returns (status, leaf_nodes, inner_order, ms)."""
+    g, keep = make_geometry(geom)
+    leaf, inner, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    rc = ctx.lib.bie_tune_fmm(ctx.handle, ctypes.byref(g), kind, _ptr(load), ctypes.byref(opts), ctypes.byref(leaf),
+                              ctypes.byref(inner), ctypes.byref(ms), _stream_ptr(stream))
+    del keep
+    return rc, int(leaf.value), int(inner.value), float(ms.value)
 
 
 def tune_clear() -> None:

@@ -9,7 +9,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -22,7 +25,25 @@ using namespace bie;
 namespace {
 // weight alpha of the per-body completion used inside the FP32 inner solves
 constexpr double kInnerCompletionWeight = 1.0;
+
+// FMM schedules chosen by bie_tune_fmm, per device and shape (M, kind, order)
+std::mutex g_fmm_mu;
+std::map<std::array<int, 4>, bie::FmmSchedule> g_fmm_sched;
+std::array<int, 4> fmm_key(int M, int kind, int order) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return {dev, M, kind, order};
+}
 }  // namespace
+
+namespace bie {
+FmmSchedule fmm_schedule(int M, int kind, int order) {
+  std::lock_guard<std::mutex> lk(g_fmm_mu);
+  auto it = g_fmm_sched.find(fmm_key(M, kind, order));
+  if (it != g_fmm_sched.end()) return it->second;
+  return FmmSchedule{kDefaultLeafNodes, std::max(2, (order + 1) / 2)};
+}
+}  // namespace bie
 
 namespace bie {
 static std::atomic<long long> g_launches{0};
@@ -990,10 +1011,11 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const double* dload = w.load;
   if (!batch && (rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
   if ((rc = check_inside(ctx, w, s))) return rc;
-  const int p_res = o.fmm_order, p_in = (o.fmm_order + 1) / 2;
+  const FmmSchedule fsched = o.fmm_order > 0 ? fmm_schedule(M, kind, o.fmm_order) : FmmSchedule{0, 0};
+  const int p_res = o.fmm_order, p_in = fsched.inner_order;
   if (o.fmm_order > 0) {
     const int orders[2] = {p_res, std::max(2, p_in)};
-    if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err))) return rc;
+    if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err, fsched.leaf_nodes))) return rc;
   }
   // the block of the operator GMRES iterates on: the paper's completion (FP64
   // GMRES) or the weighted one of the inner solves
@@ -1383,7 +1405,8 @@ int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int ord
   Arena ar{ctx->ws};
   carve(ar, w, N, M, kind, 1, false, true, geom->interior_pt != nullptr, false, true);
   if ((rc = setup(ctx, geom, bs, w, s))) return rc;
-  if ((rc = fmm_setup(ctx->fmm, w.g, kind, &order, 1, s, ctx->err))) return rc;
+  if ((rc = fmm_setup(ctx->fmm, w.g, kind, &order, 1, s, ctx->err, fmm_schedule(M, kind, order).leaf_nodes)))
+    return rc;
   const double* din;
   if ((rc = stage_in(ctx, in, w.io_in, (size_t)w.n, &din, s))) return rc;
   const bool dev_out = is_device_ptr(out);
@@ -1571,7 +1594,98 @@ int bie_tune(bie_ctx* ctx, const bie_geometry* geom, int kind, int precision, in
   return BIE_OK;
 }
 
-void bie_tune_clear(void) { clear_tuned_splits(); }
+void bie_tune_clear(void) {
+  clear_tuned_splits();
+  std::lock_guard<std::mutex> lk(g_fmm_mu);
+  g_fmm_sched.clear();
+}
+
+int bie_tune_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, const double* load, const bie_opts* opts,
+                 int* leaf_nodes, int* inner_order, double* ms, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx) return BIE_ERR_INVALID;
+  if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
+  bie_opts o;
+  fill_opts(opts, o);
+  if (o.fmm_order < 2 || o.fmm_order > 64 || o.precision == BIE_PREC_FP64)
+    return fail(ctx, BIE_ERR_INVALID, "bie_tune_fmm: a mixed precision and fmm_order in 2..64");
+  std::vector<int> bs;
+  int rc = validate(ctx, geom, bs);
+  if (rc) return rc;
+  if (!load) return fail(ctx, BIE_ERR_INVALID, "load is NULL");
+  DeviceGuard dg(ctx->device);
+  const int N = geom->n_bodies, M = bs[N], p = o.fmm_order;
+  const int nout = kind == 0 ? N : 3 * N;
+  struct Scratch {
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t s;
+    ~Scratch() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (out) cudaFreeAsync(out, s);
+    }
+  } sc{nullptr, nullptr, nullptr, s};
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&sc.out), nout * sizeof(double), s));
+  CK(cudaEventCreate(&sc.e0));
+  CK(cudaEventCreate(&sc.e1));
+  // candidates: leaf populations around the default, and inner orders around
+  // ceil(p/2) (a lower order is cheaper a matvec but may need more refinement
+  // steps, so whole solves are timed); a candidate counts only if it converges
+  const int pin0 = std::max(2, (p + 1) / 2);
+  std::vector<FmmSchedule> cand;
+  for (int leaf : {kDefaultLeafNodes, 12, 48})
+    for (int pin : {pin0, pin0 - 4, pin0 - 2, pin0 + 2, pin0 + 4})
+      if (pin >= 2 && pin <= p) cand.push_back(FmmSchedule{leaf, pin});
+  const std::array<int, 4> key = fmm_key(M, kind, p);
+  FmmSchedule best = cand[0];
+  double best_ms = 0.0, def_ms = 0.0;
+  bool any = false;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    {
+      std::lock_guard<std::mutex> lk(g_fmm_mu);
+      g_fmm_sched[key] = cand[c];
+    }
+    double t_min = 1e300;
+    bool ok = true;
+    for (int it = 0; it < 3 && ok; ++it) {  // one warm-up, the faster of two
+      CK(cudaEventRecord(sc.e0, s));
+      bie_info info;
+      const int st = solve_common(ctx, geom, kind, load, sc.out, nullptr, &o, &info, s);
+      CK(cudaEventRecord(sc.e1, s));
+      CK(cudaEventSynchronize(sc.e1));
+      if (st < 0) {
+        std::lock_guard<std::mutex> lk(g_fmm_mu);
+        g_fmm_sched.erase(key);
+        return st;
+      }
+      if (st == BIE_WARN_NOT_CONVERGED) ok = false;
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, sc.e0, sc.e1));
+      if (it > 0) t_min = std::min(t_min, (double)t);
+    }
+    if (!ok) continue;
+    if (c == 0) def_ms = t_min;
+    if (!any || t_min < best_ms) {
+      any = true;
+      best_ms = t_min;
+      best = cand[c];
+    }
+  }
+  // keep the defaults unless another schedule is clearly faster (2%)
+  if (def_ms > 0.0 && best_ms > 0.98 * def_ms) {
+    best = cand[0];
+    best_ms = def_ms;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_fmm_mu);
+    g_fmm_sched[key] = best;
+  }
+  if (leaf_nodes) *leaf_nodes = best.leaf_nodes;
+  if (inner_order) *inner_order = best.inner_order;
+  if (ms) *ms = best_ms;
+  return BIE_OK;
+}
 
 void bie_test_arm_barrier_timeout(int skip_cta, long long spins) { arm_barrier_fault(skip_cta, spins); }
 

@@ -210,8 +210,19 @@ cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* i
 struct FmmState;
 // Build the quadtree for the staged geometry and the translation operators of
 // every order in `orders` (at most 64).  One host round trip.
+// leaf_nodes: the leaf level is the finest whose non-empty leaves hold at
+// least that many nodes (<= 0: kDefaultLeafNodes).
+constexpr int kDefaultLeafNodes = 24;
 int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norders, cudaStream_t s,
-              std::string& err);
+              std::string& err, int leaf_nodes = 0);
+// FMM schedule of a shape (device, M, kind, residual order): leaf population
+// and the order of the inner solves' FMM, as tuned by bie_tune_fmm (else the
+// defaults: kDefaultLeafNodes and ceil(order / 2)).
+struct FmmSchedule {
+  int leaf_nodes;
+  int inner_order;
+};
+FmmSchedule fmm_schedule(int M, int kind, int order);
 // Pair sums by the FMM of order p into partial (layout of a single source
 // split); the near field in FP64 (near_prec 0), FP32 (1) or float-float (2).
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,

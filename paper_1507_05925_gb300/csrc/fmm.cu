@@ -816,7 +816,8 @@ void fmm_free(FmmState* f, cudaStream_t s) {
 
 // Build the tree for the staged geometry (one host round trip for the box).
 int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norders, cudaStream_t s,
-              std::string& err) {
+              std::string& err, int leaf_nodes) {
+  if (leaf_nodes <= 0) leaf_nodes = kDefaultLeafNodes;
   int pmax = 0;
   for (int k = 0; k < norders; ++k) {
     if (orders[k] < 2 || orders[k] > kMaxP) {
@@ -845,12 +846,13 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   f->x0 = h[0];
   f->y0 = h[1];
   f->D = h[2];
-  // leaf level: the finest level whose non-empty leaves hold at least ~24 nodes;
-  // nodes on curves of total length P occupy about min(4^L, 1.3 P 2^L / D) leaves
+  // leaf level: the finest level whose non-empty leaves hold at least
+  // leaf_nodes nodes (default 24); nodes on curves of total length P occupy
+  // about min(4^L, 1.3 P 2^L / D) leaves
   int L = 2;
   for (int l = 2; l <= 10; ++l) {
     const double boxes = fmin((double)(1LL << (2 * l)), 1.3 * h[3] * (double)(1 << l) / f->D);
-    if ((double)g.M / fmax(boxes, 1.0) >= 24.0) L = l;
+    if ((double)g.M / fmax(boxes, 1.0) >= (double)leaf_nodes) L = l;
   }
   f->L = L;
   f->nb = 1 << L;

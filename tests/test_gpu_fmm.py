@@ -127,3 +127,38 @@ def test_large_mobility_solve_with_fmm(ctx):
     rhs = np.stack([FT[b, 0] + FT[b, 2] * px[rows], FT[b, 1] + FT[b, 2] * py[rows]], 1).reshape(-1)
     assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-10
     assert info["rel_residual"] <= 1e-12
+
+
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+def test_tuned_fmm_schedule_keeps_the_solution(ctx, kind):
+    # bie_tune_fmm times whole solves over leaf populations and inner orders;
+    # whatever it keeps, the solve still matches the oracle
+    g = multitile(rows=4, cols=4) if kind == 0 else multitile(rows=3, cols=3)
+    N = g["body_start"].size - 1
+    if kind == 0:
+        load = synth.charges(N, np.random.default_rng(21))
+        ref = laplace.solve(g, load)["phi"]
+        fn, nout = bie.elastance_solve, N
+    else:
+        FT = synth.forces_torques(N, np.random.default_rng(22))
+        load = FT.reshape(-1)
+        ref = stokes.solve(g, FT)["UW"].reshape(-1)
+        fn, nout = bie.mobility_solve, 3 * N
+    opts = bie.make_opts(precision=bie.MIXED_FF, fmm_order=24)
+    gd = to_dev(g)
+    ld = torch.from_numpy(load).cuda()
+    try:
+        rc, leaf, inner, ms = bie.tune_fmm(ctx, gd, kind, ld, opts)
+        assert rc == bie.OK, ctx.last_error()
+        assert leaf in (12, 24, 48) and 2 <= inner <= 24 and ms > 0
+        out = torch.empty(nout, dtype=torch.float64, device="cuda")
+        rc, info = fn(ctx, gd, ld, out, opts=opts)
+        torch.cuda.synchronize()
+        assert rc == bie.OK, (rc, ctx.last_error(), info)
+        print(f"tuned fmm kind={kind}: leaf {leaf} inner {inner} {ms:.3f} ms {info}")
+        assert rel2(out.cpu().numpy(), ref) <= 1e-10
+    finally:
+        bie.tune_clear()
+    # invalid requests are refused
+    assert bie.tune_fmm(ctx, gd, kind, ld, bie.make_opts(precision=bie.MIXED_FF))[0] == bie.ERR_INVALID
+    assert bie.tune_fmm(ctx, gd, kind, ld, bie.make_opts(precision=bie.FP64, fmm_order=24))[0] == bie.ERR_INVALID
