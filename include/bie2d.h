@@ -308,6 +308,17 @@ void bie_test_precond_pivot_floor(double floor);
 int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, const double* in,
                        double* out, void* stream);
 
+/* apply_operator_fmm in the arithmetic that a solve of the given precision
+ * uses for FMM pair sums (the fast evaluation of the operator of Sections 3.4
+ * and 4.3): BIE_PREC_FP64 as apply_operator_fmm; BIE_PREC_MIXED the inner
+ * solves' operator (FP32 expansions of order p and an FP32 near field);
+ * BIE_PREC_MIXED_FF the float-float refinement's residual operator (FP64
+ * multipoles and local expansions, the multipole-to-local step in float-float
+ * arithmetic, a float-float near field).  Arguments, ownership and errors as
+ * for apply_operator_fmm; BIE_ERR_INVALID for another precision. */
+int apply_operator_fmm_prec(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, int precision,
+                            const double* in, double* out, void* stream);
+
 /* Device workspace (bytes) that elastance_solve (kind 0) or mobility_solve
  * (kind 1) needs for N bodies, M nodes and GMRES restart length `restart`
  * (0 = default): the Krylov basis, the staged geometry, the partial sums and

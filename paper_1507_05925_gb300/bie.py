@@ -104,6 +104,8 @@ def load():
     lib.apply_operator.restype = i32
     lib.apply_operator_fmm.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator_fmm.restype = i32
+    lib.apply_operator_fmm_prec.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, i32, vp, vp, vp]
+    lib.apply_operator_fmm_prec.restype = i32
     lib.apply_operator_noalloc.argtypes = [ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator_noalloc.restype = i32
     lib.bie_workspace_bytes.argtypes = [i32, i32, i32, i32]
@@ -436,5 +438,15 @@ def apply_operator_fmm(ctx: Context, geom, kind: int, order: int, inp, out, stre
     g, keep = make_geometry(geom)
     rc = ctx.lib.apply_operator_fmm(ctx.handle, ctypes.byref(g), kind, order, _ptr(inp), _ptr(out),
                                     _stream_ptr(stream))
+    del keep
+    return rc
+
+
+def apply_operator_fmm_prec(ctx: Context, geom, kind: int, order: int, precision: int, inp, out,
+                            stream=None) -> int:
+    """apply_operator_fmm_prec of include/bie2d.h: the FMM operator in a solve precision's arithmetic."""
+    g, keep = make_geometry(geom)
+    rc = ctx.lib.apply_operator_fmm_prec(ctx.handle, ctypes.byref(g), kind, order, precision, _ptr(inp),
+                                         _ptr(out), _stream_ptr(stream))
     del keep
     return rc

@@ -1388,12 +1388,19 @@ extern "C" {
 
 int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, const double* in, double* out,
                        void* stream) {
+  return apply_operator_fmm_prec(ctx, geom, kind, order, BIE_PREC_FP64, in, out, stream);
+}
+
+int apply_operator_fmm_prec(bie_ctx* ctx, const bie_geometry* geom, int kind, int order, int precision,
+                            const double* in, double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<int> bs;
   int rc = validate(ctx, geom, bs);
   if (rc) return rc;
   if (kind != BIE_KIND_LAPLACE && kind != BIE_KIND_STOKES) return fail(ctx, BIE_ERR_INVALID, "bad kind");
   if (order < 2 || order > 64) return fail(ctx, BIE_ERR_INVALID, "order must be in 2..64");
+  if (precision != BIE_PREC_FP64 && precision != BIE_PREC_MIXED && precision != BIE_PREC_MIXED_FF)
+    return fail(ctx, BIE_ERR_INVALID, "bad precision");
   if (!in || !out) return fail(ctx, BIE_ERR_INVALID, "in or out is NULL");
   if ((rc = check_local(ctx, {in, out}, "in or out"))) return rc;
   DeviceGuard dg(ctx->device);
@@ -1412,7 +1419,8 @@ int apply_operator_fmm(bie_ctx* ctx, const bie_geometry* geom, int kind, int ord
   const bool dev_out = is_device_ptr(out);
   double* dout = dev_out ? out : w.io_out;
   const PairPlan one = uniform_plan(1, M);
-  CK(fmm_pair_sum(ctx->fmm, w.g, kind, order, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr, s));
+  CK(fmm_pair_sum(ctx->fmm, w.g, kind, order, vec(const_cast<double*>(din)), w.g.w, w.partial, nullptr, s,
+                  precision));
   CK(epilogue(w.g, kind, one, vec(const_cast<double*>(din)), w.partial, 0, 1, 1.0, vec(dout), nullptr, s));
   if (!dev_out) {
     CK(cudaMemcpyAsync(out, dout, (size_t)w.n * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -13,9 +13,10 @@
 // Uniform quadtree on the bounding square, leaf level L chosen so that a
 // non-empty leaf holds about 24-50 nodes.  Expansions in scaled form (powers of
 // (z - c)/s), so the translation operators do not depend on the level: 4
-// multipole-to-multipole, 4 local-to-local and 49 multipole-to-local
-// (offsets -3..3 in each direction) p x p complex matrices, built on the host
-// in double precision.  Multipole:  F(z) = sum_k a_k s^k / (z - c)^(k+1),
+// multipole-to-multipole and 4 local-to-local p x p complex matrices, and for
+// the multipole-to-local step (offsets -3..3 in each direction) two diagonal
+// factors per offset around one real Pascal matrix, built on the host in
+// double precision.  Multipole:  F(z) = sum_k a_k s^k / (z - c)^(k+1),
 // a_k = sum_j q_j ((z_j - c)/s)^k; local: F(z) = sum_l b_l ((z - c)/s)^l.
 // Translations (d = target centre - source centre):
 //   M2M  a'_k = sum_{m<=k} C(k,m) 2^-m w^(k-m) a_m,        w = (c_child - c_parent)/S
@@ -38,6 +39,7 @@
 #include <algorithm>
 #include <complex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/bie2d.h"
@@ -52,7 +54,6 @@ namespace {
 constexpr int kMaxP = 64;
 constexpr int kB = 64;       // threads per box block (>= p)
 constexpr int kChunk = 32;   // points per P2M chunk
-constexpr int kNops = 106;   // 4 M2M + 4 L2L + 49 Cauchy M2L + 49 logarithm M2L
 constexpr int kMaxNd = 4;    // channels per box
 
 __host__ __device__ inline long long lev_off(int l) { return ((1LL << (2 * l)) - 1) / 3; }
@@ -325,84 +326,335 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int*
     for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
 }
 
-// M2L for the target boxes of all levels 2..L (one block per box).  Cauchy
-// channels: b = (1/s) T_D a; logarithm channels: b = T^log_D a, plus
-// a_0 log(s) on b_0 (the level's share of log d = log D + log s).  The
-// multipoles of the whole interaction list (at most 27 boxes) are staged in
-// shared memory behind one barrier; thread e < p nd computes coefficient
-// e % p of channel e / p.
-constexpr int kBM = 128;
+// M2L for the target boxes of all levels 2..L (one block per box), through
+// a factorisation of the translation operators (d = D s, D the integer
+// offset of the target centre from the source centre in box sides):
+//   Cauchy:    T_D[l][k] = (-1)^l C(k+l, l) D^-(k+l+1) = beta_l(D) P[l][k] alpha_k(D),
+//              P[l][k] = C(k+l, l),  alpha_k = D^-k,  beta_l = (-1)^l D^-(l+1);
+//   logarithm: T^log_D[l][k] = beta_l(D) P^log[l][k] alpha_k(D) for k >= 1,
+//              P^log[l][k] = C(k+l-1, l),  alpha_k = D^-k / k,  beta_l = -(-1)^l D^-l,
+//              and the a_0 column gamma_l(D) = log D (l = 0), (-1)^(l+1) D^-l / l (l >= 1).
+// P is real and the same for every offset, so a box pair costs 2 p^2 real
+// multiply-adds (the Pascal matrix times a complex vector) and 8 p for the
+// two diagonal scalings, against 4 p^2 for a complex p x p operator.  Cauchy
+// channels carry 1/s; logarithm channels add a_0 log(s) on b_0 (the level's
+// share of log d = log D + log s).
+//
+// One warp finds the interaction list (at most 27 boxes, in row-major order
+// of the parent's 6 x 6 neighbourhood); the sources' multipoles are staged
+// in shared memory already scaled by alpha, U[q][d][k] (q padded with zeros
+// to a multiple of 4); thread e < p nd computes coefficient l = e % p of
+// channel d = e / p over four sources at a time (four independent chains).
+// PM > 0: the thread's Pascal row is held in registers and U is zero-padded
+// to PM coefficients (p <= PM); PM = 0: the Pascal matrices are read from
+// shared memory, transposed, for any p.
 constexpr int kMaxList = 27;
+constexpr int kListPad = 28;  // kMaxList rounded up to the 4-source step
+constexpr int kOffs = 49;     // offsets -3..3 x -3..3 (the 3 x 3 near ones unused)
 
-template <class T2>
-__global__ void __launch_bounds__(kBM) k_fmm_m2l(FmmDevT<T2> f, const int* stop) {
+// Layout of the operator table of order p (complex entries): M2M and L2L
+// matrices [op][in][out], then the M2L factors alpha[2][49][p], beta[2][49][p],
+// gamma[49][p] and the Pascal matrices [2][k][l] (real, in the real parts);
+// type 0 = Cauchy, 1 = logarithm, offset index (Dx + 3) + 7 (Dy + 3).
+__host__ __device__ inline long long tab_alpha(int p) { return 8LL * p * p; }
+__host__ __device__ inline long long tab_beta(int p) { return tab_alpha(p) + 2LL * kOffs * p; }
+__host__ __device__ inline long long tab_gamma(int p) { return tab_beta(p) + 2LL * kOffs * p; }
+__host__ __device__ inline long long tab_pascal(int p) { return tab_gamma(p) + (long long)kOffs * p; }
+__host__ __device__ inline long long tab_size(int p) { return tab_pascal(p) + 2LL * p * p; }
+
+// w += (pp.x u.x, pp.y u.y): a real factor (duplicated in pp) times a complex value
+__device__ __forceinline__ void rfma(float2& w, float2 pp, float2 u) { w = __ffma2_rn(pp, u, w); }
+__device__ __forceinline__ void rfma(double2& w, double2 pp, double2 u) {
+  w.x = fma(pp.x, u.x, w.x);
+  w.y = fma(pp.y, u.y, w.y);
+}
+
+template <class T2, int PM>
+__global__ void __launch_bounds__(256) k_fmm_m2l(FmmDevT<T2> f, const int* stop) {
+  using R = decltype(T2{}.x);
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T2* sm = reinterpret_cast<T2*>(smraw);  // [kMaxList][nd][p]
-  __shared__ int soi[kMaxList];
-  __shared__ int ns;
+  __shared__ int s_src[kListPad];
+  __shared__ int s_off[kListPad];
+  __shared__ T2 s_a0[kListPad][kMaxNd];  // raw a_0 of the logarithm channels
+  __shared__ int s_cnt;
   long long gb = blockIdx.x + lev_off(2);
   int l = 2;
   while (l < f.L && gb >= lev_off(l + 1)) ++l;
   if (f.tcount[gb] == 0) return;
+  const int p = f.p, nd = f.nd, pk = PM > 0 ? PM : p;
   const int n = 1 << l;
   const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
   const int px = bx >> 1, py = by >> 1;
-  const double s = ldexp(f.D, -l), inv_s = ldexp(f.Dinv, l);
-  const int np = f.nd * f.p;
-  if (threadIdx.x == 0) {
-    int c = 0;
-    for (int sy = max(0, 2 * py - 2); sy <= min(n - 1, 2 * py + 3); ++sy)
-      for (int sx = max(0, 2 * px - 2); sx <= min(n - 1, 2 * px + 3); ++sx) {
-        if (abs(sx - bx) <= 1 && abs(sy - by) <= 1) continue;
-        const long long src = lev_off(l) + sy * n + sx;
-        if (f.count[src] == 0) continue;
-        soi[c++] = (int)(src - lev_off(l)) * 64 + (bx - sx + 3) + 7 * (by - sy + 3);
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    int base = 0;
+    for (int r = 0; r < 2; ++r) {
+      const int c = r * 32 + tid;
+      const int sx = 2 * px - 2 + c % 6, sy = 2 * py - 2 + c / 6;
+      bool ok = c < 36 && sx >= 0 && sy >= 0 && sx < n && sy < n && !(abs(sx - bx) <= 1 && abs(sy - by) <= 1);
+      const long long src = lev_off(l) + (long long)sy * n + sx;
+      if (ok) ok = f.count[src] != 0;
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int pos = base + __popc(m & ((1u << tid) - 1u));
+        s_src[pos] = sy * n + sx;
+        s_off[pos] = (bx - sx + 3) + 7 * (by - sy + 3);
       }
-    ns = c;
-  }
-  __syncthreads();
-  const int cnt = ns;
-  for (int e = threadIdx.x; e < cnt * np; e += kBM) {
-    const int q = e / np, r = e % np;
-    const long long src = lev_off(l) + soi[q] / 64;
-    sm[e] = f.mp[src * np + r];
-  }
-  __syncthreads();
-  if (f.cm >= 0) {
-    // source moment density relative to the target centre: rho_S - conj(D) rho_0,
-    // D = (c_T - c_S)/s the integer offset
-    for (int e = threadIdx.x; e < cnt * f.p; e += kBM) {
-      const int q = e / f.p, k = e % f.p;
-      const int oi = soi[q] % 64;
-      const int Dx = oi % 7 - 3, Dy = oi / 7 - 3;
-      T2* a = sm + (long long)q * np;
-      T2 v = a[f.cm * f.p + k];
-      cfma(v, cx<T2>((double)-Dx, (double)Dy), a[k]);
-      a[f.cm * f.p + k] = v;
+      base += __popc(m);
     }
-    __syncthreads();
+    if (tid == 0) s_cnt = base;
   }
-  const double logs = f.nlog ? log(s) : 0.0;  // only the output's logarithm channels use it
-  for (int e = threadIdx.x; e < np; e += kBM) {
-    const int d = e / f.p, t = e % f.p;
-    const bool lg = d < f.nlog;
+  __syncthreads();
+  const int cnt = s_cnt, cnt4 = (cnt + 3) & ~3;
+  T2* U = reinterpret_cast<T2*>(smraw);  // [cnt4][nd][pk]
+  R* Pt = reinterpret_cast<R*>(U + (long long)kListPad * nd * pk);  // PM = 0: [type][k][l]
+  const T2* alpha = f.ops + tab_alpha(p);
+  const T2* beta = f.ops + tab_beta(p);
+  const T2* gamma = f.ops + tab_gamma(p);
+  const T2* pas = f.ops + tab_pascal(p);
+  const int ntype = f.nlog > 0 ? 2 : 1;
+  if (PM == 0)
+    for (int e = tid; e < ntype * p * p; e += blockDim.x) {
+      const int t = e / (p * p), r = e % (p * p);
+      Pt[e] = pas[(long long)(f.nlog > 0 ? t : 0) * p * p + r].x;
+    }
+  const int per = nd * pk;
+  for (int e = tid; e < cnt4 * per; e += blockDim.x) {
+    const int q = e / per, r = e % per, d = r / pk, k = r % pk;
+    T2 u = cx<T2>(0.0, 0.0);
+    if (q < cnt && k < p) {
+      const T2* a = f.mp + ((lev_off(l) + s_src[q]) * nd) * p;
+      const int oi = s_off[q];
+      T2 v = a[d * p + k];
+      if (d == f.cm) {
+        // source moment density relative to the target centre: rho_S - conj(D) rho_0
+        cfma(v, cx<T2>((double)(3 - oi % 7), (double)(oi / 7 - 3)), a[k]);
+      }
+      const int ty = d < f.nlog ? 1 : 0;
+      if (ty == 1 && k == 0) s_a0[q][d] = v;
+      u = cmul(alpha[((long long)ty * kOffs + oi) * p + k], v);
+    }
+    U[e] = u;
+  }
+  __syncthreads();
+  const double s = ldexp(f.D, -l), inv_s = ldexp(f.Dinv, l);
+  const R logs = f.nlog ? (R)log(s) : (R)0;  // only the logarithm channels use it
+  for (int e = tid; e < nd * p; e += blockDim.x) {
+    const int d = e / p, t = e % p;
+    const int ty = d < f.nlog ? 1 : 0;
+    const int tp = f.nlog > 0 ? ty : 0;  // Pascal slot of this channel
+    T2 prow[PM > 0 ? PM : 1];
+    if (PM > 0) {
+#pragma unroll
+      for (int k = 0; k < (PM > 0 ? PM : 1); ++k) {
+        const R v = k < p ? pas[((long long)ty * p + k) * p + t].x : (R)0;
+        prow[k] = cx<T2>((double)v, (double)v);
+      }
+    }
     T2 acc = cx<T2>(0.0, 0.0);
-    for (int q = 0; q < cnt; ++q) {
-      const int oi = soi[q] % 64;
-      const T2* op = f.ops + (long long)((lg ? 57 : 8) + oi) * f.p * f.p + t;
-      const T2* a = sm + (long long)q * np + d * f.p;
-      for (int k = 0; k < f.p; ++k) cfma(acc, op[(long long)k * f.p], a[k]);
-      if (lg && t == 0) {
-        acc.x += logs * a[0].x;
-        acc.y += logs * a[0].y;
+    for (int q0 = 0; q0 < cnt; q0 += 4) {
+      T2 w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = cx<T2>(0.0, 0.0);
+      const T2* u = U + ((long long)q0 * nd + d) * pk;
+      if (PM > 0) {
+#pragma unroll
+        for (int k = 0; k < (PM > 0 ? PM : 1); ++k)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) rfma(w[j], prow[k], u[(long long)j * per + k]);
+      } else {
+        const R* pt = Pt + (long long)tp * p * p + t;
+        for (int k = 0; k < p; ++k) {
+          const R pv = pt[(long long)k * p];
+          const T2 pp = cx<T2>((double)pv, (double)pv);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) rfma(w[j], pp, u[(long long)j * per + k]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (q0 + j < cnt) {
+          const int oi = s_off[q0 + j];
+          cfma(acc, beta[((long long)ty * kOffs + oi) * p + t], w[j]);
+          if (ty == 1) {
+            T2 gm = gamma[(long long)oi * p + t];
+            if (t == 0) gm.x += logs;
+            cfma(acc, gm, s_a0[q0 + j][d]);
+          }
+        }
       }
     }
     // Cauchy channels carry 1/s; in the precision of the expansions
-    const decltype(acc.x) sc = lg ? 1.0 : inv_s;
+    const R sc = ty == 1 ? (R)1 : (R)inv_s;
     acc.x *= sc;
     acc.y *= sc;
-    f.lc[(gb * f.nd + d) * f.p + t] = acc;
+    f.lc[(gb * nd + d) * p + t] = acc;
+  }
+}
+
+// Shared memory of one M2L block: the staged sources and, for PM = 0, the
+// transposed Pascal matrices.
+template <class T2>
+size_t m2l_smem(int p, int nd, int nlog, int pm) {
+  const int pk = pm > 0 ? pm : p;
+  size_t b = (size_t)kListPad * nd * pk * sizeof(T2);
+  if (pm == 0) b += (size_t)(nlog > 0 ? 2 : 1) * p * p * sizeof(decltype(T2{}.x));
+  return b;
+}
+
+// ---- float-float M2L: the residual operator of the float-float refinement ----
+// The multipoles (FP64) are split once into float-float pairs hi + lo
+// (k_fmm_mp_ff); the factorised M2L then runs on the FP32 pipe in pairs of
+// lanes (real, imaginary): a Pascal entry times a source coefficient is an
+// exact FP32 product plus its error term and the cross terms (about 48
+// significant bits), accumulated with an error-free sum and renormalised at
+// every step, and the diagonal factors alpha and beta are float-float splits
+// of the FP64 tables.  Relative rounding about 2^-48 per operation, against
+// 2^-53 in FP64, on a pipe that issues many times more operations; the local
+// expansions are written back in FP64.  Cauchy channels only (the pair sums).
+// Complex float-float values are float4 (re_hi, im_hi, re_lo, im_lo).
+__global__ void k_fmm_mp_ff(const double2* __restrict__ mp, long long n, float4* __restrict__ mpff) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = mp[i];
+    const float rh = (float)a.x, ih = (float)a.y;
+    mpff[i] = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+  }
+}
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// (ph, pl) = (ah + al)(bh + bl) lane-wise: exact leading product, its error
+// and the cross terms
+__device__ __forceinline__ void ff_mul2(float2 ah, float2 al, float2 bh, float2 bl, float2& ph, float2& pl) {
+  ph = __fmul2_rn(ah, bh);
+  pl = __ffma2_rn(ah, bh, neg2(ph));
+  pl = __ffma2_rn(ah, bl, pl);
+  pl = __ffma2_rn(al, bh, pl);
+}
+
+// (sh, sl) += (ph, pl) lane-wise: error-free sum of the leading parts, the
+// low parts added, renormalised
+__device__ __forceinline__ void ff_acc2(float2& sh, float2& sl, float2 ph, float2 pl) {
+  const float2 s = __fadd2_rn(sh, ph);
+  const float2 bb = __fadd2_rn(s, neg2(sh));
+  const float2 e = __fadd2_rn(__fadd2_rn(sh, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(ph, neg2(bb)));
+  const float2 t = __fadd2_rn(e, __fadd2_rn(sl, pl));
+  sh = __fadd2_rn(s, t);
+  sl = __fadd2_rn(t, neg2(__fadd2_rn(sh, neg2(s))));
+}
+
+// (sh, sl) += a b, complex float-float: a = (ah, al), b = (bh, bl) as
+// (re, im) lane pairs
+__device__ __forceinline__ void ff_cfma(float2& sh, float2& sl, float2 ah, float2 al, float2 bh, float2 bl) {
+  float2 xh, xl, yh, yl;
+  // (a_re b_re, a_re b_im) + (-a_im b_im, a_im b_re)
+  ff_mul2(make_float2(ah.x, ah.x), make_float2(al.x, al.x), bh, bl, xh, xl);
+  ff_mul2(make_float2(ah.y, ah.y), make_float2(al.y, al.y), make_float2(-bh.y, bh.x), make_float2(-bl.y, bl.x), yh,
+          yl);
+  ff_acc2(sh, sl, xh, xl);
+  ff_acc2(sh, sl, yh, yl);
+}
+
+// Tables of order p: alpha[49][p], beta[49][p] (float4, Cauchy factors), then
+// the Pascal matrix [k][l] (float2 hi, lo).
+__host__ __device__ inline long long fftab_beta(int p) { return (long long)kOffs * p; }
+__host__ __device__ inline long long fftab_floats(int p) { return 8LL * kOffs * p + 2LL * p * p; }
+
+constexpr int kBFF = 128;
+
+__global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __restrict__ mpff,
+                                                     const float* __restrict__ tab, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_src[kListPad];
+  __shared__ int s_off[kListPad];
+  __shared__ int s_cnt;
+  long long gb = blockIdx.x + lev_off(2);
+  int l = 2;
+  while (l < f.L && gb >= lev_off(l + 1)) ++l;
+  if (f.tcount[gb] == 0) return;
+  const int p = f.p, nd = f.nd;
+  const int n = 1 << l;
+  const int b = (int)(gb - lev_off(l)), bx = b % n, by = b / n;
+  const int px = bx >> 1, py = by >> 1;
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    int base = 0;
+    for (int r = 0; r < 2; ++r) {
+      const int c = r * 32 + tid;
+      const int sx = 2 * px - 2 + c % 6, sy = 2 * py - 2 + c / 6;
+      bool ok = c < 36 && sx >= 0 && sy >= 0 && sx < n && sy < n && !(abs(sx - bx) <= 1 && abs(sy - by) <= 1);
+      const long long src = lev_off(l) + (long long)sy * n + sx;
+      if (ok) ok = f.count[src] != 0;
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int pos = base + __popc(m & ((1u << tid) - 1u));
+        s_src[pos] = sy * n + sx;
+        s_off[pos] = (bx - sx + 3) + 7 * (by - sy + 3);
+      }
+      base += __popc(m);
+    }
+    if (tid == 0) s_cnt = base;
+  }
+  __syncthreads();
+  const int cnt = s_cnt, cnt4 = (cnt + 3) & ~3;
+  float4* U = reinterpret_cast<float4*>(smraw);  // [cnt4][nd][p]
+  const float4* alpha = reinterpret_cast<const float4*>(tab);
+  const float4* beta = alpha + fftab_beta(p);
+  const float2* pas = reinterpret_cast<const float2*>(beta + fftab_beta(p));
+  const int per = nd * p;
+  for (int e = tid; e < cnt4 * per; e += blockDim.x) {
+    const int q = e / per, r = e % per, d = r / p, k = r % p;
+    float2 uh = make_float2(0.f, 0.f), ul = uh;
+    if (q < cnt) {
+      const float4* a = mpff + ((lev_off(l) + s_src[q]) * nd) * p;
+      const int oi = s_off[q];
+      const float4 v = a[d * p + k];
+      float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
+      if (d == f.cm) {
+        // source moment density relative to the target centre: rho_S - conj(D) rho_0
+        const float4 a0 = a[k];
+        ff_cfma(vh, vl, make_float2((float)(3 - oi % 7), (float)(oi / 7 - 3)), make_float2(0.f, 0.f),
+                make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
+      }
+      const float4 al = alpha[(long long)oi * p + k];
+      ff_cfma(uh, ul, make_float2(al.x, al.y), make_float2(al.z, al.w), vh, vl);
+    }
+    U[e] = make_float4(uh.x, uh.y, ul.x, ul.y);
+  }
+  __syncthreads();
+  const double inv_s = ldexp(f.Dinv, l);
+  for (int e = tid; e < per; e += blockDim.x) {
+    const int d = e / p, t = e % p;
+    float2 ah = make_float2(0.f, 0.f), al = ah;
+    for (int q0 = 0; q0 < cnt; q0 += 4) {
+      float2 sh[4], sl[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sh[j] = sl[j] = make_float2(0.f, 0.f);
+      const float4* u = U + (long long)q0 * per + d * p;
+      for (int k = 0; k < p; ++k) {
+        const float2 pv = __ldg(pas + (long long)k * p + t);
+        const float2 PH = make_float2(pv.x, pv.x), PL = make_float2(pv.y, pv.y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 uv = u[(long long)j * per + k];
+          float2 ph, pl;
+          ff_mul2(PH, PL, make_float2(uv.x, uv.y), make_float2(uv.z, uv.w), ph, pl);
+          ff_acc2(sh[j], sl[j], ph, pl);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (q0 + j < cnt) {
+          const float4 be = beta[(long long)s_off[q0 + j] * p + t];
+          ff_cfma(ah, al, make_float2(be.x, be.y), make_float2(be.z, be.w), sh[j], sl[j]);
+        }
+      }
+    }
+    // Cauchy channels carry 1/s
+    f.lc[(gb * nd + d) * p + t] =
+        make_double2(((double)ah.x + (double)al.x) * inv_s, ((double)ah.y + (double)al.y) * inv_s);
   }
 }
 
@@ -745,7 +997,7 @@ inline int grid_for(long long n) {
   return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
-// Translation operators for order p, stored [op][in][out].
+// Translation operators for order p in the layout of tab_alpha..tab_size.
 std::vector<std::complex<double>> build_ops(int p) {
   using C = std::complex<double>;
   std::vector<double> bin((2 * p + 1) * (2 * p + 1), 0.0);
@@ -754,7 +1006,7 @@ std::vector<std::complex<double>> build_ops(int p) {
     B(a, 0) = 1.0;
     for (int b = 1; b <= a; ++b) B(a, b) = B(a - 1, b - 1) + (b <= a - 1 ? B(a - 1, b) : 0.0);
   }
-  std::vector<C> ops((size_t)kNops * p * p, C(0, 0));
+  std::vector<C> ops((size_t)tab_size(p), C(0, 0));
   auto at = [&](int o, int in, int out) -> C& { return ops[((size_t)o * p + in) * p + out]; };
   for (int c = 0; c < 4; ++c) {
     const C w(((c & 1) - 0.5) / 2.0, ((c >> 1) - 0.5) / 2.0);
@@ -763,25 +1015,31 @@ std::vector<std::complex<double>> build_ops(int p) {
     for (int m = 0; m < p; ++m)
       for (int l = m; l < p; ++l) at(4 + c, l, m) = B(l, m) * std::pow(0.5, m) * std::pow(w, l - m);  // L2L
   }
+  // M2L factors.  Cauchy: (d + u)^-(k+1) = sum_l C(k+l, l) (-1)^l u^l d^-(k+l+1).
+  // Logarithm: log(d + u) = log d + sum_l (-1)^(l+1) (u/d)^l / l and
+  // (d + u)^-k = sum_l C(k+l-1, l) (-1)^l u^l d^-(k+l); the log s part of log d
+  // is added by the kernel.
+  const size_t A = tab_alpha(p), Bt = tab_beta(p), G = tab_gamma(p), P = tab_pascal(p);
   for (int dy = -3; dy <= 3; ++dy)
     for (int dx = -3; dx <= 3; ++dx) {
       if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
-      const int o = 8 + (dx + 3) + 7 * (dy + 3);
+      const size_t o = (size_t)(dx + 3) + 7 * (dy + 3);
       const C Dinv = 1.0 / C(dx, dy);
-      for (int l = 0; l < p; ++l)
-        for (int k = 0; k < p; ++k)
-          at(o, k, l) = ((l & 1) ? -1.0 : 1.0) * B(k + l, l) * std::pow(Dinv, k + l + 1);  // M2L
-      // logarithm kernel: log(d + u) = log d + sum_l (-1)^(l+1) (u/d)^l / l and
-      // (d + u)^-k = sum_l C(k+l-1, l) (-1)^l u^l d^-(k+l); the log s part of log d
-      // is added by the kernel
-      const int ol = o + 49;
-      at(ol, 0, 0) = std::log(C(dx, dy));
-      for (int l = 1; l < p; ++l) at(ol, 0, l) = ((l & 1) ? 1.0 : -1.0) * std::pow(Dinv, l) / (double)l;
-      for (int k = 1; k < p; ++k) {
-        at(ol, k, 0) = -std::pow(Dinv, k) / (double)k;
-        for (int l = 1; l < p; ++l)
-          at(ol, k, l) = -((l & 1) ? -1.0 : 1.0) * B(k + l - 1, l) * std::pow(Dinv, k + l) / (double)k;
+      for (int k = 0; k < p; ++k) {
+        ops[A + o * p + k] = std::pow(Dinv, k);
+        ops[A + (kOffs + o) * p + k] = k == 0 ? C(0, 0) : std::pow(Dinv, k) / (double)k;
       }
+      for (int l = 0; l < p; ++l) {
+        const double sg = (l & 1) ? -1.0 : 1.0;
+        ops[Bt + o * p + l] = sg * std::pow(Dinv, l + 1);
+        ops[Bt + (kOffs + o) * p + l] = -sg * std::pow(Dinv, l);
+        ops[G + o * p + l] = l == 0 ? std::log(C(dx, dy)) : -sg * std::pow(Dinv, l) / (double)l;
+      }
+    }
+  for (int k = 0; k < p; ++k)
+    for (int l = 0; l < p; ++l) {
+      ops[P + (size_t)k * p + l] = B(k + l, l);
+      ops[P + ((size_t)p + k) * p + l] = k == 0 ? 0.0 : B(k + l - 1, l);
     }
   return ops;
 }
@@ -804,6 +1062,9 @@ struct FmmState {
   // operators per order (FP64, and their FP32 copies)
   std::vector<std::pair<int, double2*>> ops;
   std::vector<std::pair<int, float2*>> ops32;
+  // float-float M2L: split multipoles and the split factor tables per order
+  float4* mpff = nullptr;
+  std::vector<std::pair<int, float*>> opsff;
 };
 
 void fmm_free(FmmState* f, cudaStream_t s) {
@@ -811,6 +1072,7 @@ void fmm_free(FmmState* f, cudaStream_t s) {
   if (f->buf) cudaFreeAsync(f->buf, s);
   for (auto& o : f->ops) cudaFreeAsync(o.second, s);
   for (auto& o : f->ops32) cudaFreeAsync(o.second, s);
+  for (auto& o : f->opsff) cudaFreeAsync(o.second, s);
   delete f;
 }
 
@@ -866,7 +1128,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   // buffers
   auto pad = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t need = 3 * pad((size_t)g.M * 4) + 2 * pad(((size_t)f->nleaf + 1) * 4) + 2 * pad((size_t)f->nbox * 4) +
-                      pad((size_t)g.M * nd * 16) + 2 * pad((size_t)f->nbox * nd * pmax * 16) +
+                      pad((size_t)g.M * nd * 16) + 3 * pad((size_t)f->nbox * nd * pmax * 16) +
                       pad((size_t)3 * g.N * 4) + 2 * pad((size_t)3 * g.N * 8);
   if (need > f->buf_size) {
     if (f->buf) cudaFreeAsync(f->buf, s);
@@ -894,6 +1156,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   f->Q = (double2*)take((size_t)g.M * nd * 16);
   f->mp = (double2*)take((size_t)f->nbox * nd * pmax * 16);
   f->lc = (double2*)take((size_t)f->nbox * nd * pmax * 16);
+  f->mpff = (float4*)take((size_t)f->nbox * nd * pmax * 16);
   // counting sort of the nodes by leaf, node order inside a leaf
   if (!ck(cudaMemsetAsync(f->cursor, 0, ((size_t)f->nleaf + 1) * 4, s), "fmm memset")) return BIE_ERR_CUDA;
   k_fmm_leaf<<<grid_for(g.M), 256, 0, s>>>(g, L, f->x0, f->y0, f->D, f->leaf, f->cursor);
@@ -926,11 +1189,56 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
       return BIE_ERR_CUDA;
     f->ops.push_back({p, ops});
     f->ops32.push_back({p, ops32});
+    // float-float splits of the Cauchy M2L factors and of the Pascal matrix
+    std::vector<float> hff((size_t)fftab_floats(p));
+    auto split = [](double x, float& h, float& l) {
+      h = (float)x;
+      l = (float)(x - (double)h);
+    };
+    for (int o = 0; o < kOffs; ++o)
+      for (int k = 0; k < p; ++k)
+        for (int t = 0; t < 2; ++t) {
+          const auto v = host[(size_t)(t == 0 ? tab_alpha(p) : tab_beta(p)) + (size_t)o * p + k];
+          float* q = hff.data() + ((size_t)t * kOffs * p + (size_t)o * p + k) * 4;
+          split(v.real(), q[0], q[2]);
+          split(v.imag(), q[1], q[3]);
+        }
+    for (int e = 0; e < p * p; ++e) {
+      float* q = hff.data() + (size_t)8 * kOffs * p + 2 * (size_t)e;
+      split(host[(size_t)tab_pascal(p) + e].real(), q[0], q[1]);
+    }
+    float* opsff = nullptr;
+    if (!ck(cudaMallocAsync(reinterpret_cast<void**>(&opsff), hff.size() * sizeof(float), s), "fmm ops") ||
+        !ck(cudaMemcpyAsync(opsff, hff.data(), hff.size() * sizeof(float), cudaMemcpyHostToDevice, s), "fmm ops") ||
+        !ck(cudaStreamSynchronize(s), "fmm ops"))
+      return BIE_ERR_CUDA;
+    f->opsff.push_back({p, opsff});
   }
   return BIE_OK;
 }
 
 namespace {
+
+template <class T2, int PM>
+void m2l_launch_pm(const FmmDevT<T2>& d, int L, const int* stop, cudaStream_t s) {
+  const size_t sm = m2l_smem<T2>(d.p, d.nd, d.nlog, PM);
+  const int threads = std::max(64, std::min(256, (d.nd * d.p + 31) / 32 * 32));
+  cudaFuncSetAttribute(k_fmm_m2l<T2, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_fmm_m2l<T2, PM><<<(int)(lev_off(L + 1) - lev_off(2)), threads, sm, s>>>(d, stop);
+}
+
+// FP32 expansions of order <= 32 hold their Pascal rows in registers.
+template <class T2>
+void launch_m2l(const FmmDevT<T2>& d, int L, const int* stop, cudaStream_t s) {
+  if constexpr (std::is_same<T2, float2>::value) {
+    if (d.p <= 12) return m2l_launch_pm<T2, 12>(d, L, stop, s);
+    if (d.p <= 16) return m2l_launch_pm<T2, 16>(d, L, stop, s);
+    if (d.p <= 20) return m2l_launch_pm<T2, 20>(d, L, stop, s);
+    if (d.p <= 24) return m2l_launch_pm<T2, 24>(d, L, stop, s);
+    if (d.p <= 32) return m2l_launch_pm<T2, 32>(d, L, stop, s);
+  }
+  m2l_launch_pm<T2, 0>(d, L, stop, s);
+}
 
 // The upward pass, M2L, downward pass and evaluation with expansions of type T2.
 template <class T2, int NEARP>
@@ -940,9 +1248,22 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(T2);
   k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<T2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
-  const size_t sm_m2l = (size_t)kMaxList * nd * p * sizeof(T2);
-  cudaFuncSetAttribute(k_fmm_m2l<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2l);
-  k_fmm_m2l<T2><<<(int)(lev_off(f->L + 1) - lev_off(2)), kBM, sm_m2l, s>>>(d, stop);
+  bool done = false;
+  if constexpr (std::is_same<T2, double2>::value && NEARP == 2) {
+    // the float-float residual operator: float-float M2L
+    const float* tab = nullptr;
+    for (auto& o : f->opsff)
+      if (o.first == p) tab = o.second;
+    if (tab) {
+      const long long nmp = (lev_off(f->L + 1) - lev_off(2)) * nd * p;
+      k_fmm_mp_ff<<<grid_for(nmp), 256, 0, s>>>(d.mp + lev_off(2) * nd * p, nmp, f->mpff + lev_off(2) * nd * p);
+      const size_t sm = (size_t)kListPad * nd * p * sizeof(float4);
+      cudaFuncSetAttribute(k_fmm_m2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_fmm_m2l_ff<<<(int)(lev_off(f->L + 1) - lev_off(2)), kBFF, sm, s>>>(d, f->mpff, tab, stop);
+      done = true;
+    }
+  }
+  if (!done) launch_m2l(d, f->L, stop, s);
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<T2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
   k_fmm_eval<T2, NEARP><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
 }
@@ -977,7 +1298,7 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
     else
       fmm_passes<double2, 0>(d, f, g, partial, stop, s);
   }
-  note_launches(4 + 2 * std::max(0, f->L - 2));
+  note_launches(4 + 2 * std::max(0, f->L - 2) + (near_prec == 2 ? 1 : 0));
   return cudaGetLastError();
 }
 
@@ -1008,9 +1329,7 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
   k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
-  const size_t sm_m2l = (size_t)kMaxList * nd * p * sizeof(double2);
-  cudaFuncSetAttribute(k_fmm_m2l<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2l);
-  k_fmm_m2l<double2><<<(int)(lev_off(f->L + 1) - lev_off(2)), kBM, sm_m2l, s>>>(d, nullptr);
+  launch_m2l(d, f->L, nullptr, s);
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
   k_fmm_eval_targets<<<grid_for(T), 256, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y, part);
   note_launches(7 + f->L + 2 * std::max(0, f->L - 2));

@@ -53,6 +53,37 @@ def test_fmm_operator_matches_direct(ctx, kind, order):
     assert np.array_equal(got, _apply(ctx, g, kind, v, order=order))  # deterministic
 
 
+def _apply_prec(ctx, g, kind, v, order, prec):
+    out = torch.empty(v.size, dtype=torch.float64, device="cuda")
+    rc = bie.apply_operator_fmm_prec(ctx, to_dev(g), kind, order, prec, torch.from_numpy(v).cuda(), out)
+    torch.cuda.synchronize()
+    assert rc == bie.OK, ctx.last_error()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+def test_fmm_operator_in_solve_precisions(ctx, kind):
+    """The FMM operator as the solves use it: the inner solves' FP32 expansions
+    (order 18) and the float-float refinement's residual operator (order 36,
+    float-float multipole-to-local step), against the direct FP64 sums; the
+    float-float one also against the FP64-expansion FMM, which isolates its
+    rounding (about 2^-48 a step) from the truncation of the expansions."""
+    g = multitile(rows=5, cols=5)
+    v = np.random.default_rng(13).standard_normal(g["x"].size * (kind + 1))
+    ref = _apply(ctx, g, kind, v)
+    got32 = _apply_prec(ctx, g, kind, v, 18, bie.MIXED)
+    gotff = _apply_prec(ctx, g, kind, v, 36, bie.MIXED_FF)
+    fmm64 = _apply(ctx, g, kind, v, order=36)
+    e32, eff, eff64 = rel_max(got32, ref), rel_max(gotff, ref), rel_max(gotff, fmm64)
+    print(f"kind={kind}: fp32 expansions {e32:.2e}, float-float M2L {eff:.2e} (vs FP64 FMM {eff64:.2e})")
+    assert e32 <= 2e-5
+    assert eff <= TOL_FMM[36]
+    assert eff64 <= 1e-13
+    assert np.array_equal(gotff, _apply_prec(ctx, g, kind, v, 36, bie.MIXED_FF))  # deterministic
+    assert bie.apply_operator_fmm_prec(ctx, to_dev(g), kind, 36, 7, torch.from_numpy(v).cuda(),
+                                       torch.empty(v.size, dtype=torch.float64, device="cuda")) == bie.ERR_INVALID
+
+
 @pytest.mark.parametrize("wl,kind,nrows", [("stars100_M25600", 0, 48), ("ellipses400_M51200", 1, 24),
                                            ("ellipses10000_M640000", 1, 8)])
 def test_fmm_full_size_rows(ctx, wl, kind, nrows):
