@@ -155,7 +155,9 @@ typedef struct {
   int32_t precond_fallbacks;   /* block-Jacobi preconditioner: bodies whose diagonal block met a
                                   pivot that was not finite or tiny against the block's size during
                                   its inversion and that therefore keep the identity */
-  int32_t pad_;
+  int32_t graph_replay;        /* 1 when the GMRES iterations were replayed from a captured CUDA
+                                  graph (a stream that can be captured), 0 when launched kernel by
+                                  kernel (the legacy default stream, or pair-sum timing on) */
 } bie_info;
 
 /* Elastance solve (Section 3): charges q [N] -> conductor potentials phi [N].

@@ -42,10 +42,10 @@ class BieInfo(ctypes.Structure):
                 ("matvecs_ff", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("constraint_residual", ctypes.c_double),
                 ("net_load", ctypes.c_double), ("fp32_error", ctypes.c_double),
-                ("precond_fallbacks", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("precond_fallbacks", ctypes.c_int32), ("graph_replay", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BieRequest(ctypes.Structure):

@@ -82,9 +82,11 @@ struct bie_ctx {
   struct IterGraph {
     long long key[10];
     cudaGraphExec_t exec;
-    long long kernels;
+    long long kernels;  // per iteration
+    int last_cycle;     // iterations of the last cycle replayed from it (0: none yet)
   };
   std::vector<IterGraph> graphs;
+  int graph_replay = 0;  // launch mode of the last GMRES cycle (bie_info.graph_replay)
   bie::FmmState* fmm = nullptr;  // quadtree of the last FMM call
 };
 
@@ -740,6 +742,19 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
                              w.grid + 1000003LL * w.seg.nitem};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
+  auto keep = [&](cudaGraphExec_t exec, long long kernels) {
+    if (ctx->graphs.size() >= 4) {
+      cudaGraphExecDestroy(ctx->graphs.front().exec);
+      ctx->graphs.erase(ctx->graphs.begin());
+    }
+    bie_ctx::IterGraph gi;
+    memcpy(gi.key, key, sizeof(key));
+    gi.exec = exec;
+    gi.kernels = kernels;
+    gi.last_cycle = 0;
+    ctx->graphs.push_back(gi);
+    return &ctx->graphs.back();
+  };
   const long long before = thread_launches();
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -757,22 +772,22 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
     return nullptr;
   }
   cudaGraphDestroy(graph);
-  if (ctx->graphs.size() >= 4) {
-    cudaGraphExecDestroy(ctx->graphs.front().exec);
-    ctx->graphs.erase(ctx->graphs.begin());
-  }
-  bie_ctx::IterGraph gi;
-  memcpy(gi.key, key, sizeof(key));
-  gi.exec = exec;
-  gi.kernels = kernels;
-  ctx->graphs.push_back(gi);
-  return &ctx->graphs.back();
+  return keep(exec, kernels);
 }
 
+// One GMRES cycle: iterations launched in chunks (graph replays where the
+// stream can be captured) with a state read after each chunk.  Iterations
+// launched after the one that stops the cycle return at once; to launch few
+// of them without reading the state more often, the first chunk is as long as
+// the last cycle replayed from the same graph (the cycles of a refinement, and
+// the solves of one shape, take similar counts), the later ones 2, 4, 8, 16.
 int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
-  int chunk = 4, rc;
-  int iters_before = ctx->h_state->iters;
+  int rc;
+  const int start = ctx->h_state->iters;
+  int iters_before = start;
   bie_ctx::IterGraph* graph = iteration_graph(ctx, w, op, s);
+  ctx->graph_replay = graph ? 1 : 0;
+  int chunk = graph && graph->last_cycle > 0 ? graph->last_cycle : 4, next = graph && graph->last_cycle > 0 ? 2 : 8;
   for (;;) {
     const size_t mark = ctx->pending.size();
     for (int it = 0; it < chunk; ++it) {
@@ -790,8 +805,12 @@ int run_cycle(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
     for (size_t k = mark; k < ctx->pending.size(); ++k) ctx->pending[k].valid = (int)(k - mark) < done;
     resolve_timings(ctx, false);
     iters_before = ctx->h_state->iters;
-    if (ctx->h_state->stop) return BIE_OK;
-    chunk = std::min(chunk * 2, 16);
+    if (ctx->h_state->stop) {
+      if (graph) graph->last_cycle = std::max(1, std::min(ctx->h_state->iters - start, w.m));
+      return BIE_OK;
+    }
+    chunk = next;
+    next = std::min(next * 2, 16);
   }
 }
 
@@ -1217,7 +1236,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(axpy(w.xs, w.rin, n, s));
   }
   if (o.fmm_order > 0) {
-    CK(fmm_output(ctx->fmm, w.g, kind, p_res, v, w.outpart, s));
+    CK(fmm_output(ctx->fmm, w.g, kind, p_res, v, w.outpart, s, o.precision == BIE_PREC_MIXED_FF));
     CK(finalize_output(w.g, kind, v, dload, w.outpart, 1, w.outv, w.cres, s));
   } else {
     CK(evaluate_output(w.g, kind, v, dload, w.outpart, w.P, w.outv, w.cres, s));
@@ -1294,7 +1313,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
         q.net_load = net;
         q.fp32_error = eps32_report;
         q.precond_fallbacks = *h_fb;  // of the whole batch
-        q.pad_ = 0;
+        q.graph_replay = ctx->graph_replay;
       }
       if (st == BIE_WARN_NOT_CONVERGED || (st == BIE_WARN_NONNEUTRAL && worst_status == BIE_OK)) worst_status = st;
     }
@@ -1313,7 +1332,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     info->net_load = netload;
     info->fp32_error = eps32_report;
     info->precond_fallbacks = *h_fb;
-    info->pad_ = 0;
+    info->graph_replay = ctx->graph_replay;
   }
   if (!converged) return BIE_WARN_NOT_CONVERGED;
   if (netload > 1e-12 * std::max(maxload, 1e-300) * std::max(1, N)) return BIE_WARN_NONNEUTRAL;

@@ -230,7 +230,8 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
 void fmm_free(FmmState* f, cudaStream_t s);
 // Output single layers at the interior targets by the FMM (one split, the
 // layout of evaluate_output's direct sums).
-cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s);
+cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s,
+                       bool ff = false);
 
 // workspace of a solve with the given host body_start (bie_workspace_bytes assumes equal bodies)
 size_t workspace_bytes_for(int kind, const int* body_start_host, int n_bodies, int restart);

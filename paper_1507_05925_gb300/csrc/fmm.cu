@@ -438,12 +438,13 @@ __global__ void __launch_bounds__(256) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
     U[e] = u;
   }
   __syncthreads();
-  const double s = ldexp(f.D, -l), inv_s = ldexp(f.Dinv, l);
-  const R logs = f.nlog ? (R)log(s) : (R)0;  // only the logarithm channels use it
+  const double inv_s = ldexp(f.Dinv, l);
   for (int e = tid; e < nd * p; e += blockDim.x) {
     const int d = e / p, t = e % p;
     const int ty = d < f.nlog ? 1 : 0;
     const int tp = f.nlog > 0 ? ty : 0;  // Pascal slot of this channel
+    // log s (s = D 2^-l), on b_0 of the logarithm channels only
+    const R logs = (ty == 1 && t == 0) ? (R)(log(f.D) - l * 0.69314718055994530942) : (R)0;
     T2 prow[PM > 0 ? PM : 1];
     if (PM > 0) {
 #pragma unroll
@@ -556,10 +557,13 @@ __device__ __forceinline__ void ff_cfma(float2& sh, float2& sl, float2 ah, float
   ff_acc2(sh, sl, yh, yl);
 }
 
-// Tables of order p: alpha[49][p], beta[49][p] (float4, Cauchy factors), then
-// the Pascal matrix [k][l] (float2 hi, lo).
-__host__ __device__ inline long long fftab_beta(int p) { return (long long)kOffs * p; }
-__host__ __device__ inline long long fftab_floats(int p) { return 8LL * kOffs * p + 2LL * p * p; }
+// Tables of order p: alpha[2][49][p], beta[2][49][p], gamma[49][p] (float4;
+// type 0 Cauchy, 1 logarithm, as tab_alpha..tab_gamma), then the Pascal
+// matrices [2][k][l] (float2 hi, lo).
+__host__ __device__ inline long long fftab_beta(int p) { return 2LL * kOffs * p; }
+__host__ __device__ inline long long fftab_gamma(int p) { return 4LL * kOffs * p; }
+__host__ __device__ inline long long fftab_pascal(int p) { return 5LL * kOffs * p; }  // in float4 units
+__host__ __device__ inline long long fftab_floats(int p) { return 20LL * kOffs * p + 4LL * p * p; }
 
 constexpr int kBFF = 128;
 
@@ -569,6 +573,7 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_src[kListPad];
   __shared__ int s_off[kListPad];
+  __shared__ float4 s_a0[kListPad][kMaxNd];  // a_0 of the logarithm channels
   __shared__ int s_cnt;
   long long gb = blockIdx.x + lev_off(2);
   int l = 2;
@@ -602,7 +607,8 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
   float4* U = reinterpret_cast<float4*>(smraw);  // [cnt4][nd][p]
   const float4* alpha = reinterpret_cast<const float4*>(tab);
   const float4* beta = alpha + fftab_beta(p);
-  const float2* pas = reinterpret_cast<const float2*>(beta + fftab_beta(p));
+  const float4* gamma = alpha + fftab_gamma(p);
+  const float2* pas = reinterpret_cast<const float2*>(alpha + fftab_pascal(p));
   const int per = nd * p;
   for (int e = tid; e < cnt4 * per; e += blockDim.x) {
     const int q = e / per, r = e % per, d = r / p, k = r % p;
@@ -618,7 +624,9 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
         ff_cfma(vh, vl, make_float2((float)(3 - oi % 7), (float)(oi / 7 - 3)), make_float2(0.f, 0.f),
                 make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
       }
-      const float4 al = alpha[(long long)oi * p + k];
+      const int ty = d < f.nlog ? 1 : 0;
+      if (ty == 1 && k == 0) s_a0[q][d] = make_float4(vh.x, vh.y, vl.x, vl.y);
+      const float4 al = alpha[((long long)ty * kOffs + oi) * p + k];
       ff_cfma(uh, ul, make_float2(al.x, al.y), make_float2(al.z, al.w), vh, vl);
     }
     U[e] = make_float4(uh.x, uh.y, ul.x, ul.y);
@@ -627,6 +635,15 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
   const double inv_s = ldexp(f.Dinv, l);
   for (int e = tid; e < per; e += blockDim.x) {
     const int d = e / p, t = e % p;
+    const int ty = d < f.nlog ? 1 : 0;
+    // log s (s = D 2^-l) on b_0 of the logarithm channels, split hi + lo
+    float lsh = 0.f, lsl = 0.f;
+    if (ty == 1 && t == 0) {
+      const double ls = log(f.D) - l * 0.69314718055994530942;
+      lsh = (float)ls;
+      lsl = (float)(ls - (double)lsh);
+    }
+    const float2* pcol = pas + (long long)ty * p * p + t;
     float2 ah = make_float2(0.f, 0.f), al = ah;
     for (int q0 = 0; q0 < cnt; q0 += 4) {
       float2 sh[4], sl[4];
@@ -634,7 +651,7 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
       for (int j = 0; j < 4; ++j) sh[j] = sl[j] = make_float2(0.f, 0.f);
       const float4* u = U + (long long)q0 * per + d * p;
       for (int k = 0; k < p; ++k) {
-        const float2 pv = __ldg(pas + (long long)k * p + t);
+        const float2 pv = __ldg(pcol + (long long)k * p);
         const float2 PH = make_float2(pv.x, pv.x), PL = make_float2(pv.y, pv.y);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -647,14 +664,24 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (q0 + j < cnt) {
-          const float4 be = beta[(long long)s_off[q0 + j] * p + t];
+          const int oi = s_off[q0 + j];
+          const float4 be = beta[((long long)ty * kOffs + oi) * p + t];
           ff_cfma(ah, al, make_float2(be.x, be.y), make_float2(be.z, be.w), sh[j], sl[j]);
+          if (ty == 1) {
+            // the a_0 column: gamma_l(D) a_0, and log s on b_0
+            float4 gm = gamma[(long long)oi * p + t];
+            float2 gh = make_float2(gm.x, gm.y), gl = make_float2(gm.z, gm.w);
+            ff_acc2(gh, gl, make_float2(lsh, 0.f), make_float2(lsl, 0.f));
+            const float4 a0 = s_a0[q0 + j][d];
+            ff_cfma(ah, al, gh, gl, make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
+          }
         }
       }
     }
     // Cauchy channels carry 1/s
+    const double sc = ty == 1 ? 1.0 : inv_s;
     f.lc[(gb * nd + d) * p + t] =
-        make_double2(((double)ah.x + (double)al.x) * inv_s, ((double)ah.y + (double)al.y) * inv_s);
+        make_double2(((double)ah.x + (double)al.x) * sc, ((double)ah.y + (double)al.y) * sc);
   }
 }
 
@@ -1189,22 +1216,22 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
       return BIE_ERR_CUDA;
     f->ops.push_back({p, ops});
     f->ops32.push_back({p, ops32});
-    // float-float splits of the Cauchy M2L factors and of the Pascal matrix
+    // float-float splits of the M2L factors and of the Pascal matrices
     std::vector<float> hff((size_t)fftab_floats(p));
     auto split = [](double x, float& h, float& l) {
       h = (float)x;
       l = (float)(x - (double)h);
     };
-    for (int o = 0; o < kOffs; ++o)
-      for (int k = 0; k < p; ++k)
-        for (int t = 0; t < 2; ++t) {
-          const auto v = host[(size_t)(t == 0 ? tab_alpha(p) : tab_beta(p)) + (size_t)o * p + k];
-          float* q = hff.data() + ((size_t)t * kOffs * p + (size_t)o * p + k) * 4;
-          split(v.real(), q[0], q[2]);
-          split(v.imag(), q[1], q[3]);
-        }
-    for (int e = 0; e < p * p; ++e) {
-      float* q = hff.data() + (size_t)8 * kOffs * p + 2 * (size_t)e;
+    const size_t tabs[3] = {(size_t)tab_alpha(p), (size_t)tab_beta(p), (size_t)tab_gamma(p)};
+    for (int t = 0; t < 5; ++t)  // alpha (2 types), beta (2 types), gamma
+      for (int e = 0; e < kOffs * p; ++e) {
+        const auto v = host[tabs[t / 2] + (size_t)(t % 2) * kOffs * p + e];
+        float* q = hff.data() + ((size_t)t * kOffs * p + e) * 4;
+        split(v.real(), q[0], q[2]);
+        split(v.imag(), q[1], q[3]);
+      }
+    for (int e = 0; e < 2 * p * p; ++e) {
+      float* q = hff.data() + (size_t)20 * kOffs * p + 2 * (size_t)e;
       split(host[(size_t)tab_pascal(p) + e].real(), q[0], q[1]);
     }
     float* opsff = nullptr;
@@ -1308,7 +1335,8 @@ namespace bie {
 
 // The output single layers at the interior targets by the FMM of order p
 // (logarithm and Cauchy channels on the source tree of fmm_setup).
-cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s) {
+cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s,
+                       bool ff) {
   if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;
   double2* ops = nullptr;
   for (auto& o : f->ops)
@@ -1329,7 +1357,20 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
   k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
-  launch_m2l(d, f->L, nullptr, s);
+  const float* tab = nullptr;
+  for (auto& o : f->opsff)
+    if (o.first == p) tab = o.second;
+  if (ff && tab) {
+    // float-float multipole-to-local step (the float-float refinement's solves)
+    const long long nmp = (lev_off(f->L + 1) - lev_off(2)) * nd * p;
+    k_fmm_mp_ff<<<grid_for(nmp), 256, 0, s>>>(f->mp + lev_off(2) * nd * p, nmp, f->mpff + lev_off(2) * nd * p);
+    const size_t sm = (size_t)kListPad * nd * p * sizeof(float4);
+    cudaFuncSetAttribute(k_fmm_m2l_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fmm_m2l_ff<<<(int)(lev_off(f->L + 1) - lev_off(2)), kBFF, sm, s>>>(d, f->mpff, tab, nullptr);
+    note_launches(1);
+  } else {
+    launch_m2l(d, f->L, nullptr, s);
+  }
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
   k_fmm_eval_targets<<<grid_for(T), 256, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y, part);
   note_launches(7 + f->L + 2 * std::max(0, f->L - 2));
