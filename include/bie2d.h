@@ -296,6 +296,13 @@ int apply_operator_noalloc(const bie_geometry* geom, int kind, int precision, co
  * the hook.  The hook is taken by one launch only. */
 void bie_test_arm_barrier_timeout(int skip_cta, long long spins);
 
+/* Test hook of the output sums' logarithm (no counterpart in the paper): for
+ * device arrays x [n] and out [2n], out[i] = the table-driven FP64 logarithm
+ * of x[i] that the output kernels use and out[n + i] = the CUDA library's
+ * log(x[i]), so that a test can bound their difference.  Asynchronous on
+ * `stream`; BIE_ERR_INVALID for NULL arrays or n < 0. */
+int bie_test_log(const double* x, double* out, long long n, void* stream);
+
 /* Test hook of the block-Jacobi safeguard (no counterpart in the paper): pivots
  * of later block factorisations count as bad when |p| < floor (default 1e-3 for
  * floor <= 0), so that a test can drive every body onto the identity block and

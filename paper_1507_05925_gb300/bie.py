@@ -104,6 +104,8 @@ def load():
     lib.apply_operator.restype = i32
     lib.apply_operator_fmm.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
     lib.apply_operator_fmm.restype = i32
+    lib.bie_test_log.argtypes = [vp, vp, ctypes.c_int64, vp]
+    lib.bie_test_log.restype = i32
     lib.apply_operator_fmm_prec.argtypes = [vp, ctypes.POINTER(BieGeometry), i32, i32, i32, vp, vp, vp]
     lib.apply_operator_fmm_prec.restype = i32
     lib.apply_operator_noalloc.argtypes = [ctypes.POINTER(BieGeometry), i32, i32, vp, vp, vp]
@@ -440,6 +442,14 @@ def apply_operator_fmm(ctx: Context, geom, kind: int, order: int, inp, out, stre
                                     _stream_ptr(stream))
     del keep
     return rc
+
+
+def test_log(x, out, stream=None) -> int:
+    """bie_test_log: out[:n] = the output sums' table-driven log of x, out[n:] = CUDA's log."""
+    return load().bie_test_log(_ptr(x), _ptr(out), int(x.numel()), _stream_ptr(stream))
+
+
+test_log.__test__ = False
 
 
 def apply_operator_fmm_prec(ctx: Context, geom, kind: int, order: int, precision: int, inp, out,

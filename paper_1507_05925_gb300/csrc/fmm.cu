@@ -44,6 +44,7 @@
 
 #include "../../include/bie2d.h"
 #include "bie_internal.cuh"
+#include "logtab.cuh"
 #include "pair_math.cuh"
 #include "reduce.cuh"
 
@@ -973,37 +974,56 @@ __global__ void k_fmm_targets(Geo g, int per, int L, double x0, double y0, doubl
 // Single layers at the output targets: local expansion plus the 3 x 3 near
 // leaves, in the layout of the direct output sums (Laplace: sum w nu log r^2;
 // Stokes: sum [-log|r| f + r (r . f)/|r|^2] as a 2-vector).
-__global__ void k_fmm_eval_targets(FmmDev f, Geo g, int kind, int T, const double* __restrict__ tx,
-                                   const double* __restrict__ ty, const int* __restrict__ tleaf, double c0x,
-                                   double c0y, double* __restrict__ part) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kTW = 8;  // targets (one warp each) per block of k_fmm_eval_targets
+
+// One warp per target: the lanes split the near-field sources of the 3 x 3
+// leaves (one reciprocal and one table-driven logarithm a pair), their sums
+// are reduced across the warp in a fixed order, and lane 0 adds the local
+// expansions of the target's leaf (Horner) and writes the output.
+__global__ void __launch_bounds__(32 * kTW) k_fmm_eval_targets(FmmDev f, Geo g, int kind, int T,
+                                                            const double* __restrict__ tx,
+                                                            const double* __restrict__ ty,
+                                                            const int* __restrict__ tleaf, double c0x, double c0y,
+                                                            double* __restrict__ part) {
+  __shared__ double2 ltab[kLogTab];
+  log_table_fill(ltab);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kTW + (threadIdx.x >> 5);
   if (t >= T) return;
   const int b = tleaf[t], bx = b % f.nb, by = b / f.nb;
   const long long box = lev_off(f.L) + b;
+  const double x = tx[t], y = ty[t];
+  double2 val[kMaxNd];
+  for (int d = 0; d < kMaxNd; ++d) val[d] = make_double2(0.0, 0.0);
+  for (int ny = max(0, by - 1); ny <= min(f.nb - 1, by + 1); ++ny)
+    for (int nx = max(0, bx - 1); nx <= min(f.nb - 1, bx + 1); ++nx) {
+      const int nl = ny * f.nb + nx;
+      for (int k = f.start[nl] + lane; k < f.start[nl + 1]; k += 32) {
+        const int j = f.perm[k];
+        const double rx = x - g.x[j], ry = y - g.y[j];
+        const double r2 = rx * rx + ry * ry;
+        const double lg = 0.5 * log_tab(r2, ltab);
+        for (int d = 0; d < f.nlog; ++d) val[d].x += f.Q[(long long)j * f.nd + d].x * lg;
+        const double ir2 = 1.0 / r2;
+        const double2 inv = make_double2(rx * ir2, -ry * ir2);
+        for (int d = f.nlog; d < f.nd; ++d) cfma(val[d], f.Q[(long long)j * f.nd + d], inv);
+      }
+    }
+  for (int d = 0; d < f.nd; ++d) {
+    val[d].x = warp_sum(val[d].x);
+    val[d].y = warp_sum(val[d].y);
+  }
+  if (lane != 0) return;
   double s;
   const double2 c = box_center(f, f.L, bx, by, s);
-  const double x = tx[t], y = ty[t];
   const double2 u = make_double2((x - c.x) / s, (y - c.y) / s);
-  double2 val[kMaxNd];
   for (int d = 0; d < f.nd; ++d) {
     const double2* lc = f.lc + (box * f.nd + d) * f.p;
     double2 h = lc[f.p - 1];
     for (int l = f.p - 2; l >= 0; --l) h = cadd(cmul(h, u), lc[l]);
-    val[d] = h;
+    val[d] = cadd(h, val[d]);
   }
-  for (int ny = max(0, by - 1); ny <= min(f.nb - 1, by + 1); ++ny)
-    for (int nx = max(0, bx - 1); nx <= min(f.nb - 1, bx + 1); ++nx) {
-      const int nl = ny * f.nb + nx;
-      for (int k = f.start[nl]; k < f.start[nl + 1]; ++k) {
-        const int j = f.perm[k];
-        const double rx = x - g.x[j], ry = y - g.y[j];
-        const double r2 = rx * rx + ry * ry;
-        const double lg = 0.5 * log(r2);
-        for (int d = 0; d < f.nlog; ++d) val[d].x += f.Q[(long long)j * f.nd + d].x * lg;
-        const double2 inv = make_double2(rx / r2, -ry / r2);
-        for (int d = f.nlog; d < f.nd; ++d) cfma(val[d], f.Q[(long long)j * f.nd + d], inv);
-      }
-    }
   if (kind == 0) {
     part[t] = 2.0 * val[0].x;
   } else {
@@ -1372,7 +1392,8 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
     launch_m2l(d, f->L, nullptr, s);
   }
   for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
-  k_fmm_eval_targets<<<grid_for(T), 256, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y, part);
+  k_fmm_eval_targets<<<(T + kTW - 1) / kTW, 32 * kTW, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y,
+                                                               part);
   note_launches(7 + f->L + 2 * std::max(0, f->L - 2));
   return cudaGetLastError();
 }

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "bie_internal.cuh"
+#include "logtab.cuh"
 #include "reduce.cuh"
 
 namespace bie {
@@ -303,6 +304,9 @@ __global__ void __launch_bounds__(kB) k_seg_zero_below(double* __restrict__ x, c
 __global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict__ v,
                                                 double* __restrict__ part, int P) {
   __shared__ double sh[kB / 32];
+  __shared__ double2 ltab[kLogTab];
+  log_table_fill(ltab);
+  __syncthreads();
   const int i = blockIdx.x, p = blockIdx.y;
   const double zx = g.zx[i], zy = g.zy[i];
   // sources: all nodes, or the nodes of body i's problem (batched solves)
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict_
   double acc = 0.0;
   for (int b = b0 + threadIdx.x; b < b1; b += kB) {
     const double rx = zx - g.x[b], ry = zy - g.y[b];
-    acc += g.sw[b] * v[b] * log(rx * rx + ry * ry);
+    acc += g.sw[b] * v[b] * log_tab(rx * rx + ry * ry, ltab);
   }
   acc = block_sum<kB>(acc, sh);
   if (threadIdx.x == 0) part[(long long)p * g.N + i] = acc;
@@ -324,6 +328,9 @@ __global__ void __launch_bounds__(kB) k_out_lap(Geo g, const double* __restrict_
 __global__ void __launch_bounds__(kB) k_out_stk(Geo g, const double* __restrict__ v,
                                                 double* __restrict__ part, int P) {
   __shared__ double sh[kB / 32];
+  __shared__ double2 ltab[kLogTab];
+  log_table_fill(ltab);
+  __syncthreads();
   const int t = blockIdx.x, p = blockIdx.y;
   const int i = t / 3, s = t % 3;
   const double d = g.delta[i];
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(kB) k_out_stk(Geo g, const double* __restrict_
     const double rx = zx - g.x[b], ry = zy - g.y[b];
     const double r2 = rx * rx + ry * ry;
     const double f1 = g.sw[b] * v[2 * b], f2 = g.sw[b] * v[2 * b + 1];
-    const double lg = -0.5 * log(r2);
+    const double lg = -0.5 * log_tab(r2, ltab);
     const double c = (rx * f1 + ry * f2) / r2;
     u1 += lg * f1 + c * rx;
     u2 += lg * f2 + c * ry;
@@ -546,3 +553,26 @@ cudaError_t net_load(int N, int kind, const double* load, double* out, cudaStrea
 }
 
 }  // namespace bie
+
+namespace bie {
+namespace {
+__global__ void __launch_bounds__(256) k_test_log(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  __shared__ double2 ltab[kLogTab];
+  log_table_fill(ltab);
+  __syncthreads();
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    out[i] = log_tab(x[i], ltab);
+    out[n + i] = log(x[i]);
+  }
+}
+}  // namespace
+}  // namespace bie
+
+extern "C" int bie_test_log(const double* x, double* out, long long n, void* stream) {
+  if (!x || !out || n < 0) return BIE_ERR_INVALID;
+  if (n == 0) return BIE_OK;
+  const long long b = (n + 255) / 256;
+  bie::k_test_log<<<(unsigned)(b > 4096 ? 4096 : b), 256, 0, (cudaStream_t)stream>>>(x, n, out);
+  bie::note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? BIE_OK : BIE_ERR_CUDA;
+}

@@ -608,3 +608,27 @@ def test_symmetric_pair_sum_operator_and_solve(ctx):
         torch.cuda.synchronize()
         assert rc == bie.OK, (rc, ctx.last_error(), info)
         assert rel2(phi.cpu().numpy(), phi_ref) <= TOL_SOLVE
+
+
+def test_output_logarithm_against_library(ctx):
+    """The table-driven FP64 logarithm of the output sums (Tang 1990) against
+    the CUDA library's log over 24 decades, near 1, at powers of two and at
+    the special values: within 2 ulp of the result plus 4 * 2^-53 absolute
+    (the cancellation of e log 2 against log c for x just below 1 costs
+    relative, not absolute, accuracy; the sums need absolute accuracy)."""
+    rng = np.random.default_rng(77)
+    x = np.concatenate([10.0 ** rng.uniform(-12, 12, 200000), 1.0 + rng.uniform(-1e-3, 1e-3, 20000),
+                        2.0 ** np.arange(-60, 61), 1.0 + (np.arange(128) + 0.5) / 128,
+                        [1e-300, 1e300, 3.0, 0.0, 1e-310, np.inf]])
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty(2 * x.size, dtype=torch.float64, device="cuda")
+    assert bie.test_log(xt, out) == bie.OK
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    a, b = o[:x.size], o[x.size:]
+    fin = np.isfinite(b)
+    assert np.array_equal(a[~fin], b[~fin])  # log 0 = -inf, log inf = inf: the library's values
+    err = np.abs(a[fin] - b[fin])
+    bound = 2 * np.spacing(np.abs(b[fin])) + 4 * 2.0 ** -53
+    print(f"table log: max |diff| {err.max():.2e}, max diff / ulp {np.max(err / np.spacing(np.abs(b[fin]))):.2f}")
+    assert np.all(err <= bound)
