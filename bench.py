@@ -87,6 +87,11 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=16)
     ap.add_argument("--mobility-steps", type=int, default=5,
                     help="timed mobility solves of 400 ellipses x 128 nodes, direct pair sums (0 = skip)")
+    ap.add_argument("--mobility-fmm-order", type=int, default=36,
+                    help="the 400-ellipse solves again with FMM pair sums of this order (0 = skip)")
+    ap.add_argument("--headline-fmm-order", type=int, default=30,
+                    help="the 100-star solves again with FMM pair sums of this order, reported beside "
+                         "the headline (0 = skip)")
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mobility solves of 10,000 ellipses x 64 nodes with FMM pair sums (0 = skip)")
     ap.add_argument("--kernel", default=None,
@@ -169,6 +174,44 @@ def stored_oracle(name: str):
 
 def rel_err(a, b):
     return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+
+
+def fmm_solves(bie, ctx, gd, kind, load, out, order, steps, tune, stream=None):
+    """Float-float-refined solves with FMM pair sums of the given order: the
+    default schedule (leaf population 24, inner order ceil(p/2)) and, with
+    tune, the schedule bie_tune_fmm keeps; mean ms of `steps` solves each."""
+    import torch
+
+    fn = bie.elastance_solve if kind == 0 else bie.mobility_solve
+    opts = bie.make_opts(precision=bie.MIXED_FF, fmm_order=order)
+
+    def timed():
+        rc, info = fn(ctx, gd, load, out, opts=opts, stream=stream)
+        assert rc == bie.OK, (rc, ctx.last_error())
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, info = fn(ctx, gd, load, out, opts=opts, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert rc == bie.OK
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms)), info, out.cpu().numpy()
+
+    res = {"order": order}
+    ms, info, x = timed()
+    res["default_schedule"] = {"leaf_nodes": 24, "inner_order": (order + 1) // 2, "ms_per_solve": ms,
+                               "iters": info["iters"]}
+    if tune:
+        rc, leaf, inner, _ = bie.tune_fmm(ctx, gd, kind, load, opts, stream=stream)
+        assert rc == bie.OK, ctx.last_error()
+        ms, info, x = timed()
+        res["tuned_schedule"] = {"leaf_nodes": leaf, "inner_order": inner, "ms_per_solve": ms,
+                                 "iters": info["iters"]}
+    res["solves_per_s"] = 1e3 / ms
+    return res, x
 
 
 def cpu_cores():
@@ -587,6 +630,8 @@ def run_mobility(args, rank, local):
             assert rc == bie.OK, ctx.last_error()
             tuning[name] = {"splits": S, "ms_per_application": tms}
     out = {"workload": "ellipses400_M51200", "M": int(g["x"].size), "pair_sum_tuning": tuning}
+    # the oracle's solution of this workload (seed 2000 only: rank 0)
+    ref = stored_oracle("ellipses400_M51200_mobility.txt") if rank == 0 else None
     for name, prec, steps in (("mixed_ff", bie.MIXED_FF, args.mobility_steps), ("mixed", bie.MIXED, 1)):
         if steps <= 0:
             continue
@@ -605,6 +650,14 @@ def run_mobility(args, rank, local):
             ms.append(e0.elapsed_time(e1))
         out[name] = {"solves_per_s": 1e3 / float(np.mean(ms)), "ms_per_solve": float(np.mean(ms)), "steps": steps,
                      "info": info}
+        if ref is not None:
+            out[name]["oracle_rel_error"] = rel_err(UW.cpu().numpy(), ref)
+    if args.mobility_fmm_order > 0:
+        # the same workload with FMM pair sums (the quadtree's O(M) work wins at this size)
+        res, x = fmm_solves(bie, ctx, gd, 1, FT, UW, args.mobility_fmm_order, args.mobility_steps, not args.no_tune)
+        if ref is not None:
+            res["oracle_rel_error"] = rel_err(x, ref)
+        out["mixed_ff_fmm"] = res
     ctx.close()
     return out
 
@@ -808,6 +861,14 @@ def main():
                       "note": "||phi - phi_oracle|| / ||phi_oracle||, oracle = dense LU of the same system "
                               "(tests/golden/stars100_M25600_elastance.txt)"}
 
+    # the same workload with FMM pair sums (tuned schedule), beside the headline's direct pair sums
+    fmm_alt = None
+    if args.headline_fmm_order > 0:
+        fmm_alt, x = fmm_solves(bie, ctx, gd, 0, q, phi, args.headline_fmm_order, max(3, min(args.steps, 10)),
+                                not args.no_tune, stream)
+        if ref_phi is not None and ref_phi.size == N and rank == 0:
+            fmm_alt["oracle_rel_error"] = rel_err(x, ref_phi)
+
     # end to end through the C ABI with host (pinned) buffers (headline precision): the library copies
     # the geometry and charges in and the potentials out inside the timed call
     host = {k: torch.from_numpy(np.ascontiguousarray(g[k])).pin_memory() for k in
@@ -880,6 +941,7 @@ def main():
         "fp64_unpreconditioned_solves_per_s": fp64_noprec_rate,
         "mixed_over_fp64": value / world / fp64_rate,
         "oracle_rel_error": oracle_err,
+        "fmm_alternative": fmm_alt,
         "pair_interactions_per_s": {"laplace_fp32": pair_rate32, "laplace_ff": pair_rate_ff,
                                     "laplace_fp64": pair_rate64},
         "solve_info": {args.precision: infos[-1], "other_mixed": infos_o[-1], "fp64": infos64[-1],

@@ -80,7 +80,7 @@ struct bie_ctx {
   std::vector<Timing> pending;
   // CUDA graphs of one GMRES iteration, keyed by everything their kernels read
   struct IterGraph {
-    long long key[10];
+    long long key[12];
     cudaGraphExec_t exec;
     long long kernels;  // per iteration
     int last_cycle;     // iterations of the last cycle replayed from it (0: none yet)
@@ -736,10 +736,14 @@ bie_ctx::IterGraph* iteration_graph(bie_ctx* ctx, Work& w, const Op& op, cudaStr
   const PairPlan& p = op.prec == 0 ? w.plan64 : (op.prec == 1 ? w.plan32 : w.planff);
   long long alpha_bits;
   memcpy(&alpha_bits, &op.alpha, sizeof(alpha_bits));
-  const long long key[10] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
+  // an FMM application's captured launches depend on the tree (buffers, level
+  // count, bounding square), which a later setup may rebuild or reallocate
+  long long fsig[2] = {0, 0};
+  if (op.fmm_p > 0) fmm_signature(ctx->fmm, fsig);
+  const long long key[12] = {(long long)(uintptr_t)ctx->ws, (long long)ctx->ws_size, w.g.N, w.g.M,
                              w.kind + 4LL * w.seg.P, w.m, op.prec * 1000 + op.fmm_p + (op.precond ? 500 : 0), alpha_bits,
                              (p.S * 1000003LL + p.chunk) * 1000003LL + p.S1 * 4099LL + p.chunk2 * 2 + p.sym,
-                             w.grid + 1000003LL * w.seg.nitem};
+                             w.grid + 1000003LL * w.seg.nitem, fsig[0], fsig[1]};
   for (auto& gi : ctx->graphs)
     if (memcmp(gi.key, key, sizeof(key)) == 0) return &gi;
   auto keep = [&](cudaGraphExec_t exec, long long kernels) {

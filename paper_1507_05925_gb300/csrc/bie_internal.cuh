@@ -230,6 +230,10 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
 void fmm_free(FmmState* f, cudaStream_t s);
 // Output single layers at the interior targets by the FMM (one split, the
 // layout of evaluate_output's direct sums).
+// What a captured FMM application depends on besides its arguments: the
+// tree's buffers, level count and bounding square (baked into the captured
+// launches); two values that change whenever any of them does.
+void fmm_signature(const FmmState* f, long long sig[2]);
 cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double* v, double* part, cudaStream_t s,
                        bool ff = false);
 

@@ -1317,6 +1317,32 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
 
 }  // namespace
 
+void fmm_signature(const FmmState* f, long long sig[2]) {
+  if (!f) {
+    sig[0] = sig[1] = 0;
+    return;
+  }
+  unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the fields
+  auto mix = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xff;
+      h *= 1099511628211ULL;
+    }
+  };
+  unsigned long long u;
+  memcpy(&u, &f->x0, 8);
+  mix(u);
+  memcpy(&u, &f->y0, 8);
+  mix(u);
+  memcpy(&u, &f->D, 8);
+  mix(u);
+  mix((unsigned long long)f->L);
+  mix((unsigned long long)f->buf_size);
+  mix((unsigned long long)f->M);
+  sig[0] = (long long)(uintptr_t)f->buf;
+  sig[1] = (long long)h;
+}
+
 cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, const double* sscale,
                          double* partial, const int* stop, cudaStream_t s, int near_prec) {
   if (!f || p > f->pmax || kind != f->kind) return cudaErrorInvalidValue;

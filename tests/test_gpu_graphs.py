@@ -104,3 +104,38 @@ def test_batched_graph_replay_matches(ctx):
     for a, b, g, q in zip(res[0], res[1], geoms, loads):
         assert np.array_equal(a, b)
         assert rel2(b, laplace.solve(g, q)["phi"]) <= TOL_SOLVE
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_fmm_graphs_follow_the_tree(ctx, kind):
+    """FMM solves replayed from captured graphs in one context while the tree
+    changes: the same bodies translated (same sizes, another bounding square:
+    the captured launches hold the square), then the tuned leaf population
+    (another tree, reallocated buffers), then the first geometry again.  The
+    solution is translation invariant, so every solve matches the oracle's
+    solution of the first geometry, and each matches its kernel-by-kernel
+    twin bitwise."""
+    g, load, ref = _problem(kind, 43 + kind)
+    h = dict(g)
+    h["x"] = g["x"] + 7.3
+    h["y"] = g["y"] - 2.1
+    opts = dict(precision=bie.MIXED_FF, fmm_order=24)
+    st = torch.cuda.Stream()
+    for geo in (g, h, g):
+        info1, out1 = _solve(ctx, geo, kind, load, st, **opts)
+        info0, out0 = _solve(ctx, geo, kind, load, None, **opts)
+        assert info1["graph_replay"] == 1
+        assert np.array_equal(out0, out1)
+        assert rel2(out1, ref) <= TOL_SOLVE
+    gd = to_dev(h)
+    try:
+        rc, leaf, inner, ms = bie.tune_fmm(ctx, gd, kind, torch.from_numpy(np.ascontiguousarray(load)).cuda(),
+                                           bie.make_opts(**opts), stream=st)
+        assert rc == bie.OK, ctx.last_error()
+        for geo in (h, g):
+            info1, out1 = _solve(ctx, geo, kind, load, st, **opts)
+            info0, out0 = _solve(ctx, geo, kind, load, None, **opts)
+            assert np.array_equal(out0, out1)
+            assert rel2(out1, ref) <= TOL_SOLVE
+    finally:
+        bie.tune_clear()
