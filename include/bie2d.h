@@ -127,7 +127,11 @@ typedef struct {
   double inner_tol;      /* mixed: relative tolerance of each FP32 inner solve; default 1e-6 */
   int32_t fmm_order;     /* 0: direct pair sums; p in 2..64: the pair sums are evaluated by the
                             quadtree FMM (FP64 expansions) with order p for residuals and FP64
-                            GMRES, and order ceil(p/2) for the inner solves of the refinement */
+                            GMRES, and order ceil(p/2) for the inner solves of the refinement;
+                            -p (p in 2..64, mixed precisions only): direct FP32 pair sums for the
+                            inner solves and the FMM of order p for the refinement's residuals and
+                            the output sums (the reported residual is the FMM operator's, whose
+                            relative error is about 1e-13 at p = 36) */
   int32_t precond;       /* right preconditioner of the GMRES iterations (the FP32 inner solves
                             of the mixed precisions, or the FP64 GMRES); 0: block Jacobi (one
                             block per body, the body's own diagonal block of the operator

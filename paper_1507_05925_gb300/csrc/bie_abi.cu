@@ -995,8 +995,10 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     return fail(ctx, BIE_ERR_INVALID, "precision must be BIE_PREC_FP64, BIE_PREC_MIXED or BIE_PREC_MIXED_FF");
   if (o.formulation != 0 && o.formulation != 1) return fail(ctx, BIE_ERR_INVALID, "formulation must be 0 or 1");
   if (o.precond != 0 && o.precond != 1) return fail(ctx, BIE_ERR_INVALID, "precond must be 0 or 1");
-  if (o.fmm_order != 0 && (o.fmm_order < 2 || o.fmm_order > 64))
-    return fail(ctx, BIE_ERR_INVALID, "fmm_order must be 0 or in 2..64");
+  if (o.fmm_order != 0 && (std::abs(o.fmm_order) < 2 || std::abs(o.fmm_order) > 64))
+    return fail(ctx, BIE_ERR_INVALID, "fmm_order must be 0, in 2..64 or in -64..-2");
+  if (o.fmm_order < 0 && o.precision == BIE_PREC_FP64)
+    return fail(ctx, BIE_ERR_INVALID, "fmm_order < 0 (FMM residuals only) needs a mixed precision");
   if (batch && o.fmm_order != 0) return fail(ctx, BIE_ERR_INVALID, "batch: direct pair sums only (fmm_order 0)");
   DeviceGuard dg(ctx->device);
   const int N = (int)bs.size() - 1, M = bs[N];
@@ -1034,11 +1036,14 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   const double* dload = w.load;
   if (!batch && (rc = stage_in(ctx, load, w.load, nload, &dload, s))) return rc;
   if ((rc = check_inside(ctx, w, s))) return rc;
-  const FmmSchedule fsched = o.fmm_order > 0 ? fmm_schedule(M, kind, o.fmm_order) : FmmSchedule{0, 0};
-  const int p_res = o.fmm_order, p_in = fsched.inner_order;
-  if (o.fmm_order > 0) {
+  // fmm_order > 0: FMM pair sums everywhere; < 0: for the residuals and outputs only
+  const int p_res = std::abs(o.fmm_order);
+  const FmmSchedule fsched = p_res > 0 ? fmm_schedule(M, kind, p_res) : FmmSchedule{0, 0};
+  const int p_in = o.fmm_order > 0 ? fsched.inner_order : 0;
+  if (p_res > 0) {
     const int orders[2] = {p_res, std::max(2, p_in)};
-    if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, 2, s, ctx->err, fsched.leaf_nodes))) return rc;
+    if ((rc = fmm_setup(ctx->fmm, w.g, kind, orders, o.fmm_order > 0 ? 2 : 1, s, ctx->err, fsched.leaf_nodes)))
+      return rc;
   }
   // the block of the operator GMRES iterates on: the paper's completion (FP64
   // GMRES) or the weighted one of the inner solves
@@ -1073,7 +1078,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   }
   // inner FP32 solves use the completion weighted per body (weight 1/|Gamma_i|):
   // same solution, no outlier eigenvalue per body in the Krylov spectrum
-  const int fres = o.fmm_order > 0 ? p_res : 0, fin = o.fmm_order > 0 ? std::max(2, p_in) : 0;
+  const int fres = p_res, fin = o.fmm_order > 0 ? std::max(2, p_in) : 0;
   const Op op64{ctx, &w, 0, 0.0, fres, o.precision == BIE_PREC_FP64 && bjf > 0},
       op32{ctx, &w, 1, kInnerCompletionWeight, fin, bjf > 0};
   // refinement residual: FP64, or float-float for BIE_PREC_MIXED_FF (direct sums),
@@ -1153,7 +1158,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     // r -= A32 d, with the FP32 operator's relative error eps32 measured on this
     // geometry (A32 x against A_ff x at the first step) and the accumulated
     // bound 3 eps32 sum ||A32 d|| added to ||r|| before comparing with tol.
-    const bool recursive = o.precision == BIE_PREC_MIXED_FF && o.fmm_order == 0;
+    const bool recursive = o.precision == BIE_PREC_MIXED_FF && o.fmm_order <= 0;
     const Op op32p{ctx, &w, 1, 0.0, fin};  // FP32 pair sums (or FP32 FMM), the paper's completion
     double eps32 = -1.0, bound = 0.0;
     bool true_residual = true;
@@ -1239,7 +1244,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
     CK(incident_density_scaled(w.g, kind, dload, w.rin, s));
     CK(axpy(w.xs, w.rin, n, s));
   }
-  if (o.fmm_order > 0) {
+  if (o.fmm_order != 0) {
     CK(fmm_output(ctx->fmm, w.g, kind, p_res, v, w.outpart, s, o.precision == BIE_PREC_MIXED_FF));
     CK(finalize_output(w.g, kind, v, dload, w.outpart, 1, w.outv, w.cres, s));
   } else {
@@ -1274,7 +1279,7 @@ int solve_common(bie_ctx* ctx, const bie_geometry* geom, int kind, const double*
   }
   // constraint residual and net load
   const int targets = kind == 0 ? N : 3 * N;
-  const int P_used = o.fmm_order > 0 ? 1 : w.P;  // splits of the output sums
+  const int P_used = o.fmm_order != 0 ? 1 : w.P;  // splits of the output sums
   const double* nl = w.outpart + (size_t)P_used * targets * (kind + 1) + N;
   CK(cudaMemcpyAsync(ctx->h_small, w.cres, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_small + 1, nl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -117,19 +117,37 @@ struct BlockRow {
 
 // A_:j += F G_j for the local columns [j0, j1) of row r (F = this row of the
 // panel minus E_K, G_j = rows K of column j).
-__device__ __forceinline__ void rank_update(float* __restrict__ A, const float* __restrict__ G, int ld, int r,
+__device__ __forceinline__ void rank_update(float* __restrict__ A, const float* __restrict__ G, int h, int ld, int r,
                                             const float (&fr)[kPB], int j0, int j1) {
-  for (int j = j0; j < j1; ++j) {
-    const float4* gj = reinterpret_cast<const float4*>(G + j * kPB);
+  // G is [kPB][h] (panel row t of the local columns): one 16-byte load gives
+  // four columns of one row, added with packed FP32x2 multiply-adds; each
+  // column's terms in the order t = 0, 1, ..., as one column at a time
+  int j = j0;
+  for (; j < j1 && (j & 3); ++j) {
     float acc = A[j * ld + r];
 #pragma unroll
-    for (int q = 0; q < kPB / 4; ++q) {
-      const float4 v = gj[q];
-      acc = fmaf(fr[4 * q], v.x, acc);
-      acc = fmaf(fr[4 * q + 1], v.y, acc);
-      acc = fmaf(fr[4 * q + 2], v.z, acc);
-      acc = fmaf(fr[4 * q + 3], v.w, acc);
+    for (int t = 0; t < kPB; ++t) acc = fmaf(fr[t], G[t * h + j], acc);
+    A[j * ld + r] = acc;
+  }
+  for (; j + 4 <= j1; j += 4) {
+    float2 a01 = make_float2(A[j * ld + r], A[(j + 1) * ld + r]);
+    float2 a23 = make_float2(A[(j + 2) * ld + r], A[(j + 3) * ld + r]);
+#pragma unroll
+    for (int t = 0; t < kPB; ++t) {
+      const float4 g = *reinterpret_cast<const float4*>(G + t * h + j);
+      const float2 f = make_float2(fr[t], fr[t]);
+      a01 = __ffma2_rn(f, make_float2(g.x, g.y), a01);
+      a23 = __ffma2_rn(f, make_float2(g.z, g.w), a23);
     }
+    A[j * ld + r] = a01.x;
+    A[(j + 1) * ld + r] = a01.y;
+    A[(j + 2) * ld + r] = a23.x;
+    A[(j + 3) * ld + r] = a23.y;
+  }
+  for (; j < j1; ++j) {
+    float acc = A[j * ld + r];
+#pragma unroll
+    for (int t = 0; t < kPB; ++t) acc = fmaf(fr[t], G[t * h + j], acc);
     A[j * ld + r] = acc;
   }
 }
@@ -143,8 +161,12 @@ __device__ __forceinline__ void rank_update(float* __restrict__ A, const float* 
 // columns, reading the panel from the owner's shared memory.  The panel stays
 // unchanged until the owner's next update, which follows the next panel's
 // cluster barrier, which no CTA reaches before it is done reading.
+// Launch bounds per cluster size: one thread per row of the largest block the
+// instance takes; the clusters of four keep at least two CTAs of 448 threads
+// (three of 256) on an SM.
 template <int CS>
-__global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, double alpha,
+__global__ void __launch_bounds__(CS == 1 ? kMaxSingle : CS == 4 ? kMaxBlock4 : kMaxThreads, CS == 4 ? 2 : 1)
+    k_bj_factor(Geo g, int kind, double alpha,
                                                            const int* __restrict__ list,
                                                            const long long* __restrict__ off,
                                                            float* __restrict__ blocks, float floor,
@@ -157,7 +179,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
   const int ld = gj_ld(nb), h = gj_cols(nb, CS);
   const int c0 = min(nb, rank * h), nc = min(nb, c0 + h) - c0;
   float* A = sm;                 // ld x h, column-major
-  float* G = A + (size_t)ld * h; // h x kPB: rows K of the local columns
+  float* G = A + (size_t)ld * h; // kPB x h: rows K of the local columns
   float* rowbuf = G + (size_t)h * kPB;  // [2][kPB] pivot rows of the panel steps
   float4* colp = reinterpret_cast<float4*>(rowbuf + 2 * kPB);  // [h] column node positions
   float4* colw = colp + h;                                       // [h] column node data
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
     // rows K of the local columns, before any of them changes
     for (int e = threadIdx.x; e < nc * bsz; e += blockDim.x) {
       const int j = e / bsz, t = e % bsz;
-      G[j * kPB + t] = A[j * ld + k0 + t];
+      G[t * h + j] = A[j * ld + k0 + t];
     }
     if constexpr (CS > 1) {
       cg::this_cluster().sync();
@@ -235,8 +257,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_bj_factor(Geo g, int kind, doub
       for (int t = 0; t < kPB; ++t) fr[t] = t < bsz ? P[t * ld + r] - (r == k0 + t ? 1.f : 0.f) : 0.f;
       // all local columns but the panel's own (owner: [k0 - c0, k0 - c0 + bsz))
       const int s0 = rank == owner ? k0 - c0 : nc, s1 = rank == owner ? k0 - c0 + bsz : nc;
-      rank_update(A, G, ld, r, fr, 0, s0);
-      rank_update(A, G, ld, r, fr, s1, nc);
+      rank_update(A, G, h, ld, r, fr, 0, s0);
+      rank_update(A, G, h, ld, r, fr, s1, nc);
     }
     __syncthreads();
   }

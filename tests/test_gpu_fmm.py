@@ -193,3 +193,35 @@ def test_tuned_fmm_schedule_keeps_the_solution(ctx, kind):
     # invalid requests are refused
     assert bie.tune_fmm(ctx, gd, kind, ld, bie.make_opts(precision=bie.MIXED_FF))[0] == bie.ERR_INVALID
     assert bie.tune_fmm(ctx, gd, kind, ld, bie.make_opts(precision=bie.FP64, fmm_order=24))[0] == bie.ERR_INVALID
+
+
+@pytest.mark.parametrize("kind", [bie.LAPLACE, bie.STOKES])
+@pytest.mark.parametrize("prec", [bie.MIXED, bie.MIXED_FF])
+def test_fmm_residuals_only(ctx, kind, prec):
+    """fmm_order = -p: direct FP32 pair sums in the inner solves, the FMM of
+    order p for the refinement's residuals and the output sums; against the
+    oracle, and refused for FP64 GMRES."""
+    g = multitile(rows=4, cols=4) if kind == 0 else multitile(rows=3, cols=3)
+    N = g["body_start"].size - 1
+    if kind == 0:
+        load = synth.charges(N, np.random.default_rng(21))
+        ref = laplace.solve(g, load)["phi"]
+        fn, nout = bie.elastance_solve, N
+    else:
+        FT = synth.forces_torques(N, np.random.default_rng(22))
+        load = FT.reshape(-1)
+        ref = stokes.solve(g, FT)["UW"].reshape(-1)
+        fn, nout = bie.mobility_solve, 3 * N
+    out = torch.empty(nout, dtype=torch.float64, device="cuda")
+    rc, info = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out,
+                  opts=bie.make_opts(precision=prec, fmm_order=-36))
+    torch.cuda.synchronize()
+    assert rc == bie.OK, (rc, ctx.last_error(), info)
+    err = rel2(out.cpu().numpy(), ref)
+    print(f"fmm residuals only kind={kind} prec={prec}: {err:.2e} {info}")
+    assert err <= 1e-10
+    assert info["rel_residual"] <= 1e-12 and info["matvecs_fp32"] > 0
+    rc, _ = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out, opts=bie.make_opts(precision=bie.FP64, fmm_order=-36))
+    assert rc == bie.ERR_INVALID
+    rc, _ = fn(ctx, to_dev(g), torch.from_numpy(load).cuda(), out, opts=bie.make_opts(precision=prec, fmm_order=-70))
+    assert rc == bie.ERR_INVALID
