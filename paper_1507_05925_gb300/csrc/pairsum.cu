@@ -760,6 +760,22 @@ __global__ void __launch_bounds__(kBF) k_pair_ff(Geo g, VecRef vr, const double*
 constexpr int kTFS = 2;                      // targets a lane
 constexpr int kBFS = kTileF / kTFS;          // 128 threads a CTA
 
+// Packed forms of the float-float helpers: the two halves of a float2 are two
+// independent values, each rounded exactly as the scalar form rounds it.
+__device__ __forceinline__ float2 neg2f(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void ff_mul2(float2 ah, float2 al, float2 bh, float2 bl, float2& p, float2& e) {
+  p = __fmul2_rn(ah, bh);
+  e = __ffma2_rn(ah, bh, neg2f(p));
+  e = __ffma2_rn(ah, bl, __ffma2_rn(al, bh, e));
+}
+__device__ __forceinline__ void ff_acc2(float2& sh, float2& sl, float2 th, float2 tl) {
+  const float2 u = __fadd2_rn(sh, th);
+  const float2 bb = __fadd2_rn(u, neg2f(sh));
+  const float2 e = __fadd2_rn(__fadd2_rn(sh, neg2f(__fadd2_rn(u, neg2f(bb)))), __fadd2_rn(th, neg2f(bb)));
+  sh = u;
+  sl = __fadd2_rn(sl, __fadd2_rn(e, tl));
+}
+
 __device__ __forceinline__ void ff_write_projected(const Geo& g, int a, int slot, float xh, float xl, float yh,
                                                    float yl, double* __restrict__ partial) {
   const double dax = (double)xh + (double)xl, day = (double)yh + (double)yl;
@@ -812,34 +828,43 @@ __global__ void __launch_bounds__(kBFS, 6) k_pair_ffs(Geo g, int ntile, double* 
     }
     return;
   }
-  // sources of tile B; padding far from everything with zero strength
+  // sources of tile B, negated (so that a difference is a packed add);
+  // padding far from everything with zero strength
   for (int l = threadIdx.x; l < kTileF; l += kBFS) {
     const int b = B0 + l;
-    float4 xa = make_float4(1e15f, 0.f, 1e15f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xa = make_float4(-1e15f, 0.f, -1e15f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
     if (b < M) {
-      xa = g.xff[b];
+      const float4 x = g.xff[b];
       const float2 xl = g.xfl[b];
       const double q = sscale[b] * v[b];
       const float qh = (float)q;
-      c = make_float4(xl.x, xl.y, qh, (float)(q - (double)qh));
+      xa = make_float4(-x.x, -x.y, -x.z, -x.w);
+      c = make_float4(-xl.x, -xl.y, qh, (float)(q - (double)qh));
     }
     sA[l] = xa;
     sC[l] = c;
   }
-  // kTFS targets of tile A a lane (all of tile A is inside [0, M): ti < tj)
-  float txh[kTFS], txm[kTFS], txl[kTFS], tyh[kTFS], tym[kTFS], tyl[kTFS], qah[kTFS], qal[kTFS];
-  float axh[kTFS], axl[kTFS], ayh[kTFS], ayl[kTFS];
-#pragma unroll
-  for (int m = 0; m < kTFS; ++m) {
-    const int a = A0 + threadIdx.x + m * kBFS;
-    const float4 p = g.xff[a];
-    const float2 pl = g.xfl[a];
-    txh[m] = p.x; txm[m] = p.y; tyh[m] = p.z; tym[m] = p.w; txl[m] = pl.x; tyl[m] = pl.y;
-    const double q = sscale[a] * v[a];
-    qah[m] = (float)q;
-    qal[m] = (float)(q - (double)qah[m]);
-    axh[m] = axl[m] = ayh[m] = ayl[m] = 0.f;
+  // the kTFS = 2 targets of tile A a lane, packed as the two halves of
+  // FP32x2 operands (all of tile A is inside [0, M): ti < tj)
+  static_assert(kTFS == 2, "two targets a lane, one packed pair");
+  float2 TXH, TXM, TXL, TYH, TYM, TYL, QAH, QAL;
+  {
+    const int a0 = A0 + threadIdx.x, a1 = a0 + kBFS;
+    const float4 p0 = g.xff[a0], p1 = g.xff[a1];
+    const float2 l0 = g.xfl[a0], l1 = g.xfl[a1];
+    TXH = make_float2(p0.x, p1.x);
+    TXM = make_float2(p0.y, p1.y);
+    TYH = make_float2(p0.z, p1.z);
+    TYM = make_float2(p0.w, p1.w);
+    TXL = make_float2(l0.x, l1.x);
+    TYL = make_float2(l0.y, l1.y);
+    const double q0 = sscale[a0] * v[a0], q1 = sscale[a1] * v[a1];
+    const float h0 = (float)q0, h1 = (float)q1;
+    QAH = make_float2(h0, h1);
+    QAL = make_float2((float)(q0 - (double)h0), (float)(q1 - (double)h1));
   }
+  float2 AXH = make_float2(0.f, 0.f), AXL = AXH, AYH = AXH, AYL = AXH;
+  const float2 ONE = make_float2(1.f, 1.f), TWO = make_float2(2.f, 2.f);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r0 = 0; r0 < kTileF; r0 += 32) {
@@ -848,36 +873,45 @@ __global__ void __launch_bounds__(kBFS, 6) k_pair_ffs(Geo g, int ntile, double* 
     for (int k = 0; k < 32; ++k) {
       const int l = r0 + ((lane + k) & 31);
       const float4 sa = sA[l], sc = sC[l];
-#pragma unroll
-      for (int m = 0; m < kTFS; ++m) {
-        float dxh, dxl, dyh, dyl;
-        ff_diff(txh[m], txm[m], txl[m], sa.x, sa.y, sc.x, dxh, dxl);
-        ff_diff(tyh[m], tym[m], tyl[m], sa.z, sa.w, sc.y, dyh, dyl);
-        // |r|^2 and 1/|r|^2 in float-float, as in the directed pair
-        const float p1 = dxh * dxh, p1e = fmaf(dxh, dxh, -p1);
-        const float p2 = dyh * dyh, p2e = fmaf(dyh, dyh, -p2);
-        const float s2 = p1 + p2;
-        const float se = fminf(p1, p2) - (s2 - fmaxf(p1, p2));
-        const float lo = fmaf(2.0f, fmaf(dxh, dxl, dyh * dyl), (se + p1e) + p2e);
-        const float r2h = s2 + lo;
-        const float r2l = lo - (r2h - s2);
-        const float y0 = rcp_approx(r2h);
-        const float ee = fmaf(-r2l, y0, fmaf(-r2h, y0, 1.0f));
-        const float il = y0 * ee;
-        float ch, cl, ph, pl;
-        // target a gains q_b r w
-        ff_mul(sc.z, sc.w, y0, il, ch, cl);
-        ff_mul(ch, cl, dxh, dxl, ph, pl);
-        ff_acc(axh[m], axl[m], ph, pl);
-        ff_mul(ch, cl, dyh, dyl, ph, pl);
-        ff_acc(ayh[m], ayl[m], ph, pl);
-        // the source gains -q_a r w
-        ff_mul(qah[m], qal[m], y0, il, ch, cl);
-        ff_mul(ch, cl, dxh, dxl, ph, pl);
-        ff_acc(bxh, bxl, -ph, -pl);
-        ff_mul(ch, cl, dyh, dyl, ph, pl);
-        ff_acc(byh, byl, -ph, -pl);
-      }
+      // float-float differences r = x_a - x_b from the exact splits (as ff_diff)
+      const float2 d1x = __fadd2_rn(TXH, make_float2(sa.x, sa.x)), d2x = __fadd2_rn(TXM, make_float2(sa.y, sa.y));
+      const float2 d1y = __fadd2_rn(TYH, make_float2(sa.z, sa.z)), d2y = __fadd2_rn(TYM, make_float2(sa.w, sa.w));
+      const float2 DXH = __fadd2_rn(d1x, d2x), DYH = __fadd2_rn(d1y, d2y);
+      const float2 DXL = __fadd2_rn(__fadd2_rn(d2x, neg2f(__fadd2_rn(DXH, neg2f(d1x)))),
+                                    __fadd2_rn(TXL, make_float2(sc.x, sc.x)));
+      const float2 DYL = __fadd2_rn(__fadd2_rn(d2y, neg2f(__fadd2_rn(DYH, neg2f(d1y)))),
+                                    __fadd2_rn(TYL, make_float2(sc.y, sc.y)));
+      // |r|^2 in float-float: error-free squares, an error-free sum of the two,
+      // the cross terms, renormalised (as the directed pair)
+      const float2 P1 = __fmul2_rn(DXH, DXH), P1E = __ffma2_rn(DXH, DXH, neg2f(P1));
+      const float2 P2 = __fmul2_rn(DYH, DYH), P2E = __ffma2_rn(DYH, DYH, neg2f(P2));
+      const float2 S = __fadd2_rn(P1, P2);
+      const float2 BB = __fadd2_rn(S, neg2f(P1));
+      const float2 SE = __fadd2_rn(__fadd2_rn(P1, neg2f(__fadd2_rn(S, neg2f(BB)))), __fadd2_rn(P2, neg2f(BB)));
+      const float2 LO = __ffma2_rn(TWO, __ffma2_rn(DXH, DXL, __fmul2_rn(DYH, DYL)),
+                                   __fadd2_rn(__fadd2_rn(SE, P1E), P2E));
+      const float2 R2H = __fadd2_rn(S, LO);
+      const float2 R2L = __fadd2_rn(LO, neg2f(__fadd2_rn(R2H, neg2f(S))));
+      // 1/|r|^2: MUFU seed and one float-float Newton step
+      const float2 Y0 = make_float2(rcp_approx(R2H.x), rcp_approx(R2H.y));
+      const float2 EE = __ffma2_rn(neg2f(R2L), Y0, __ffma2_rn(neg2f(R2H), Y0, ONE));
+      const float2 IL = __fmul2_rn(Y0, EE);
+      // target a gains q_b r w
+      float2 CH, CL, PH, PL;
+      ff_mul2(make_float2(sc.z, sc.z), make_float2(sc.w, sc.w), Y0, IL, CH, CL);
+      ff_mul2(CH, CL, DXH, DXL, PH, PL);
+      ff_acc2(AXH, AXL, PH, PL);
+      ff_mul2(CH, CL, DYH, DYL, PH, PL);
+      ff_acc2(AYH, AYL, PH, PL);
+      // the source gains -q_a r w (both targets' terms, in the order of the
+      // scalar pass: target 0, then target 1)
+      ff_mul2(QAH, QAL, Y0, IL, CH, CL);
+      ff_mul2(CH, CL, DXH, DXL, PH, PL);
+      ff_acc(bxh, bxl, -PH.x, -PL.x);
+      ff_acc(bxh, bxl, -PH.y, -PL.y);
+      ff_mul2(CH, CL, DYH, DYL, PH, PL);
+      ff_acc(byh, byl, -PH.x, -PL.x);
+      ff_acc(byh, byl, -PH.y, -PL.y);
       const int nxt = (lane + 1) & 31;
       bxh = __shfl_sync(0xffffffffu, bxh, nxt);
       bxl = __shfl_sync(0xffffffffu, bxl, nxt);
@@ -886,9 +920,8 @@ __global__ void __launch_bounds__(kBFS, 6) k_pair_ffs(Geo g, int ntile, double* 
     }
     accB[warp][r0 + lane] = make_float4(bxh, bxl, byh, byl);
   }
-#pragma unroll
-  for (int m = 0; m < kTFS; ++m)
-    ff_write_projected(g, A0 + threadIdx.x + m * kBFS, tj, axh[m], axl[m], ayh[m], ayl[m], partial);
+  ff_write_projected(g, A0 + threadIdx.x, tj, AXH.x, AXL.x, AYH.x, AYL.x, partial);
+  ff_write_projected(g, A0 + threadIdx.x + kBFS, tj, AXH.y, AXL.y, AYH.y, AYL.y, partial);
   __syncthreads();
   for (int l = threadIdx.x; l < kTileF; l += kBFS) {
     const int b = B0 + l;
