@@ -284,29 +284,36 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int*
     for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
 }
 
-// M2M into level l (parents) from level l + 1.
+// M2M into level l (parents) from level l + 1.  Per child, its multipoles and
+// the translation matrix are staged in shared memory (coalesced, one round
+// trip each); thread e < nd p computes coefficient e % p of channel e / p
+// (its terms in the order m = 0..k), summed over the children in order.
+constexpr int kAccPer = (kMaxNd * kMaxP + kB - 1) / kB;  // outputs a thread keeps
+
 template <class T2>
 __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
+  T2* so = sm + f.nd * f.p;               // [p][p] the child's M2M matrix, [in][out]
   const int n = 1 << l;
   const int b = blockIdx.x, bx = b % n, by = b / n;
   const long long box = lev_off(l) + b;
   if (f.count[box] == 0) return;
-  const int t = threadIdx.x;
-  T2 acc[kMaxNd];
-  for (int d = 0; d < kMaxNd; ++d) acc[d] = cx<T2>(0.0, 0.0);
+  const int t = threadIdx.x, np = f.nd * f.p, pp = f.p * f.p;
+  T2 acc[kAccPer];
+#pragma unroll
+  for (int u = 0; u < kAccPer; ++u) acc[u] = cx<T2>(0.0, 0.0);
   for (int c = 0; c < 4; ++c) {
     const long long child = lev_off(l + 1) + (2 * by + (c >> 1)) * (2 * n) + 2 * bx + (c & 1);
     if (f.count[child] == 0) continue;  // uniform over the block
     __syncthreads();
-    for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.mp[child * f.nd * f.p + e];
+    for (int e = t; e < np; e += kB) sm[e] = f.mp[child * np + e];
+    for (int e = t; e < pp; e += kB) so[e] = f.ops[(long long)c * pp + e];
     __syncthreads();
     if (f.cm >= 0) {
       // child moment density relative to the parent centre: 1/2 rho_C + gamma rho_0,
       // gamma = conj(c_C - c_P)/(2 s_C)
-      __syncthreads();
       const T2 gam = cx<T2>(0.5 * ((c & 1) - 0.5), -0.5 * ((c >> 1) - 0.5));
       for (int m = t; m < f.p; m += kB) {
         T2 v = cx<T2>(0.5 * (double)sm[f.cm * f.p + m].x, 0.5 * (double)sm[f.cm * f.p + m].y);
@@ -315,16 +322,20 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int*
       }
       __syncthreads();
     }
-    if (t < f.p) {
-      const T2* op = f.ops + (long long)c * f.p * f.p;  // [in][out]
-      for (int m = 0; m <= t; ++m) {
-        const T2 o = op[m * f.p + t];
-        for (int d = 0; d < f.nd; ++d) cfma(acc[d], o, sm[d * f.p + m]);
+#pragma unroll
+    for (int u = 0; u < kAccPer; ++u) {
+      const int e = t + u * kB;
+      if (e < np) {
+        const int d = e / f.p, k = e % f.p;
+        for (int m = 0; m <= k; ++m) cfma(acc[u], so[m * f.p + k], sm[d * f.p + m]);
       }
     }
   }
-  if (t < f.p)
-    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
+#pragma unroll
+  for (int u = 0; u < kAccPer; ++u) {
+    const int e = t + u * kB;
+    if (e < np) f.mp[box * np + e] = acc[u];
+  }
 }
 
 // M2L for the target boxes of all levels 2..L (one block per box), through
@@ -349,8 +360,7 @@ __global__ void __launch_bounds__(kB) k_fmm_m2m(FmmDevT<T2> f, int l, const int*
 // PM > 0: the thread's Pascal row is held in registers and U is zero-padded
 // to PM coefficients (p <= PM); PM = 0: the Pascal matrices are read from
 // shared memory, transposed, for any p.
-constexpr int kMaxList = 27;
-constexpr int kListPad = 28;  // kMaxList rounded up to the 4-source step
+constexpr int kListPad = 28;  // the 27 interaction-list boxes rounded up to the 4-source step
 constexpr int kOffs = 49;     // offsets -3..3 x -3..3 (the 3 x 3 near ones unused)
 
 // Layout of the operator table of order p (complex entries): M2M and L2L
@@ -686,20 +696,25 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
   }
 }
 
-// L2L from level l to the children at level l + 1 (added to their M2L part).
+// L2L from level l to the children at level l + 1 (added to their M2L part):
+// the parent's local expansion and the child's L2L matrix staged in shared
+// memory; thread e < nd p updates coefficient e % p of channel e / p (terms
+// in the order m = k..p-1).
 template <class T2>
 __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDevT<T2> f, int l, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);  // [nd][p]
+  T2* so = sm + f.nd * f.p;               // [p][p] the L2L matrix, [in][out]
   const int nc = 2 << l;
   const int b = blockIdx.x, bx = b % nc, by = b / nc;
   const long long child = lev_off(l + 1) + b;
   if (f.tcount[child] == 0) return;
   const long long parent = lev_off(l) + (by >> 1) * (nc >> 1) + (bx >> 1);
   const int c = (bx & 1) + 2 * (by & 1);
-  const int t = threadIdx.x;
-  for (int e = t; e < f.nd * f.p; e += kB) sm[e] = f.lc[parent * f.nd * f.p + e];
+  const int t = threadIdx.x, np = f.nd * f.p, pp = f.p * f.p;
+  for (int e = t; e < np; e += kB) sm[e] = f.lc[parent * np + e];
+  for (int e = t; e < pp; e += kB) so[e] = f.ops[(long long)(4 + c) * pp + e];
   __syncthreads();
   if (f.cm >= 0) {
     // moment density relative to the child centre: 2 rho_P + delta rho_0,
@@ -712,13 +727,11 @@ __global__ void __launch_bounds__(kB) k_fmm_l2l(FmmDevT<T2> f, int l, const int*
     }
     __syncthreads();
   }
-  if (t < f.p) {
-    const T2* op = f.ops + (long long)(4 + c) * f.p * f.p;
-    for (int d = 0; d < f.nd; ++d) {
-      T2 acc = f.lc[(child * f.nd + d) * f.p + t];
-      for (int m = t; m < f.p; ++m) cfma(acc, op[m * f.p + t], sm[d * f.p + m]);
-      f.lc[(child * f.nd + d) * f.p + t] = acc;
-    }
+  for (int e = t; e < np; e += kB) {
+    const int d = e / f.p, k = e % f.p;
+    T2 acc = f.lc[child * np + e];
+    for (int m = k; m < f.p; ++m) cfma(acc, so[m * f.p + k], sm[d * f.p + m]);
+    f.lc[child * np + e] = acc;
   }
 }
 
@@ -1287,6 +1300,18 @@ void launch_m2l(const FmmDevT<T2>& d, int L, const int* stop, cudaStream_t s) {
   m2l_launch_pm<T2, 0>(d, L, stop, s);
 }
 
+// Shared memory of the M2M and L2L blocks: one box's expansions and one
+// p x p translation matrix (above the default 48 KB for FP64 at high order).
+template <class T2>
+size_t tree_smem(int nd, int p) {
+  const size_t sm = ((size_t)nd * p + (size_t)p * p) * sizeof(T2);
+  if (sm > 48 * 1024) {
+    cudaFuncSetAttribute(k_fmm_m2m<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_fmm_l2l<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  }
+  return sm;
+}
+
 // The upward pass, M2L, downward pass and evaluation with expansions of type T2.
 template <class T2, int NEARP>
 void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial, const int* stop, cudaStream_t s) {
@@ -1294,7 +1319,8 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
   const size_t sm_exp = (size_t)nd * p * sizeof(T2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(T2);
   k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
-  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<T2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, stop);
+  const size_t sm_tree = tree_smem<T2>(nd, p);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<T2><<<1 << (2 * l), kB, sm_tree, s>>>(d, l, stop);
   bool done = false;
   if constexpr (std::is_same<T2, double2>::value && NEARP == 2) {
     // the float-float residual operator: float-float M2L
@@ -1311,7 +1337,7 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
     }
   }
   if (!done) launch_m2l(d, f->L, stop, s);
-  for (int l = 2; l < f->L; ++l) k_fmm_l2l<T2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, stop);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<T2><<<1 << (2 * (l + 1)), kB, sm_tree, s>>>(d, l, stop);
   k_fmm_eval<T2, NEARP><<<f->nleaf, kB, sm_exp, s>>>(d, g, partial, stop);
 }
 
@@ -1399,10 +1425,10 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
   k_fmm_out_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, c0x, c0y, v, f->Q);
   FmmDev d{f->L, f->nb, p, nd, g.M, nlog, -1, f->x0, f->y0, f->D, 1.0 / f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
            f->Q, f->mp, f->lc, ops};
-  const size_t sm_exp = (size_t)nd * p * sizeof(double2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
   k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
-  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_exp, s>>>(d, l, nullptr);
+  const size_t sm_tree = tree_smem<double2>(nd, p);
+  for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_tree, s>>>(d, l, nullptr);
   const float* tab = nullptr;
   for (auto& o : f->opsff)
     if (o.first == p) tab = o.second;
@@ -1417,7 +1443,7 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
   } else {
     launch_m2l(d, f->L, nullptr, s);
   }
-  for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_exp, s>>>(d, l, nullptr);
+  for (int l = 2; l < f->L; ++l) k_fmm_l2l<double2><<<1 << (2 * (l + 1)), kB, sm_tree, s>>>(d, l, nullptr);
   k_fmm_eval_targets<<<(T + kTW - 1) / kTW, 32 * kTW, 0, s>>>(d, g, kind, T, f->tx, f->ty, f->tleaf, c0x, c0y,
                                                                part);
   note_launches(7 + f->L + 2 * std::max(0, f->L - 2));

@@ -1023,9 +1023,9 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
         for (; s < S; ++s) k0 += partial[(long long)s * M + a];
         k = (k0 + k1) + (k2 + k3);
       }
-      const double mu = v[a] / os;
-      const double y = -kInv2Pi * k - kInv4Pi * wk * mu + m0;
-      out[a] = sign * (0.5 * v[a] + os * y);
+      // os y with y = -k/2pi - wk mu/4pi + m0 and mu = v/os: the diagonal term
+      // os wk mu/4pi = wk v/4pi needs no division
+      out[a] = sign * (0.5 * v[a] + os * (m0 - kInv2Pi * k) - kInv4Pi * wk * v[a]);
     } else {
       double k1 = 0.0, k2 = 0.0;
       if (pff) {
@@ -1057,14 +1057,14 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
         k1 += k1b;
         k2 += k2b;
       }
-      const double mu1 = v[2 * a] / os, mu2 = v[2 * a + 1] / os;
+      // os y with the diagonal term os dd t, dd = -wk (t . mu)/2pi and mu = v/os:
+      // os dd = -wk (t . v)/2pi needs no division
       const double tx = -g.ny[a], ty = g.nx[a];
-      const double dd = -0.5 * kInvPi * wk * (tx * mu1 + ty * mu2);
+      const double v1 = v[2 * a], v2 = v[2 * a + 1];
+      const double odd = -0.5 * kInvPi * wk * (tx * v1 + ty * v2);
       const double px = -(g.y[a] - yc), py = g.x[a] - xc;
-      const double y1 = -kInvPi * k1 + dd * tx + m0 + px * m2;
-      const double y2 = -kInvPi * k2 + dd * ty + m1 + py * m2;
-      out[2 * a] = sign * (0.5 * v[2 * a] + os * y1);
-      out[2 * a + 1] = sign * (0.5 * v[2 * a + 1] + os * y2);
+      out[2 * a] = sign * (0.5 * v1 + os * (m0 + px * m2 - kInvPi * k1) + odd * tx);
+      out[2 * a + 1] = sign * (0.5 * v2 + os * (m1 + py * m2 - kInvPi * k2) + odd * ty);
     }
   }
 }
