@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
   __shared__ float4 spa[kNearChunk];  // FP32: (x_hi, y_hi, x_lo, y_lo); float-float: (xh, xm, yh, ym)
   __shared__ float2 spb[NEARP == 2 ? kNearChunk : 1];  // float-float: (xl, yl)
   __shared__ float4 sq[kNearChunk];   // FP32: (q1, q2, -, -); float-float: (q1h, q1l, q2h, q2l)
-  __shared__ int sid[kNearChunk];
+  __shared__ __align__(16) int sid[kNearChunk];
   __shared__ int lst[10], lbeg[9];
   const int b = blockIdx.x, bx = b % f.nb, by = b / f.nb;
   const int s0 = f.start[b], n = f.start[b + 1] - s0;
@@ -875,6 +875,77 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
         }
       }
       float ax = 0.f, ay = 0.f, axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
+      if constexpr (NEARP == 1) {
+        // FP32: two sources a packed FP32x2 operation, staged in pairs
+        // (positions hi and lo, strengths, node ids); an odd count is padded
+        // with a zero-strength source far from everything
+        float4* sp2 = spa;                  // [kNearChunk / 2] (xh0, xh1, yh0, yh1)
+        float4* sl2 = spa + kNearChunk / 2;  // [kNearChunk / 2] (xl0, xl1, yl0, yl1)
+        float4* sq2 = sq;                   // [kNearChunk / 2] (q1_0, q1_1, q2_0, q2_1)
+        int2* sid2 = reinterpret_cast<int2*>(sid);
+        const float2 TXH = make_float2(tp.x, tp.x), TYH = make_float2(tp.y, tp.y);
+        const float2 TXL = make_float2(tp.z, tp.z), TYL = make_float2(tp.w, tp.w);
+        const float2 NX = make_float2(tn.x, tn.x), NY = make_float2(tn.y, tn.y);
+        float2 AX = make_float2(0.f, 0.f), AY = AX;
+        for (int v0 = 0; v0 < total; v0 += kNearChunk) {
+          const int m = min(kNearChunk, total - v0), m2 = (m + 1) >> 1;
+          __syncthreads();
+          for (int e2 = threadIdx.x; e2 < m2; e2 += kB) {
+            float4 P[2];
+            float2 q[2];
+            int id[2];
+            for (int h = 0; h < 2; ++h) {
+              const int e = 2 * e2 + h;
+              P[h] = make_float4(1e15f, 1e15f, 0.f, 0.f);
+              q[h] = make_float2(0.f, 0.f);
+              id[h] = -1;
+              if (e < m) {
+                const int vv = v0 + e;
+                int lf = 0;
+                while (vv >= lst[lf + 1]) ++lf;
+                const int i2 = f.perm[lbeg[lf] + (vv - lst[lf])];
+                const double2 qd = f.Q[(long long)i2 * f.nd];
+                P[h] = g.pf[i2];
+                q[h] = make_float2((float)qd.x, (float)qd.y);
+                id[h] = i2;
+              }
+            }
+            sp2[e2] = make_float4(P[0].x, P[1].x, P[0].y, P[1].y);
+            sl2[e2] = make_float4(P[0].z, P[1].z, P[0].w, P[1].w);
+            sq2[e2] = make_float4(q[0].x, q[1].x, q[0].y, q[1].y);
+            sid2[e2] = make_int2(id[0], id[1]);
+          }
+          __syncthreads();
+          if (act) {
+            for (int e2 = 0; e2 < m2; ++e2) {
+              const float4 P = sp2[e2], PL = sl2[e2], Q = sq2[e2];
+              const int2 S = sid2[e2];
+              // exact leading differences, as the scalar pair
+              const float2 dx = __fadd2_rn(__fadd2_rn(TXH, make_float2(-P.x, -P.y)),
+                                           __fadd2_rn(TXL, make_float2(-PL.x, -PL.y)));
+              const float2 dy = __fadd2_rn(__fadd2_rn(TYH, make_float2(-P.z, -P.w)),
+                                           __fadd2_rn(TYL, make_float2(-PL.z, -PL.w)));
+              const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+              const float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+              float2 cc;
+              if (f.nd == 1) {
+                cc = __fmul2_rn(make_float2(Q.x, Q.y), inv);
+              } else {
+                const float2 rq = __ffma2_rn(dx, make_float2(Q.x, Q.y), __fmul2_rn(dy, make_float2(Q.z, Q.w)));
+                const float2 rn = __ffma2_rn(dx, NX, __fmul2_rn(dy, NY));
+                cc = __fmul2_rn(__fmul2_rn(rq, rn), __fmul2_rn(inv, inv));
+              }
+              float2 cx2 = __fmul2_rn(cc, dx), cy2 = __fmul2_rn(cc, dy);
+              if (S.x == i) cx2.x = cy2.x = 0.f;  // the self pair (r = 0)
+              if (S.y == i) cx2.y = cy2.y = 0.f;
+              AX = __fadd2_rn(AX, cx2);
+              AY = __fadd2_rn(AY, cy2);
+            }
+          }
+        }
+        ax = AX.x + AX.y;
+        ay = AY.x + AY.y;
+      } else
       for (int v0 = 0; v0 < total; v0 += kNearChunk) {
         const int m = min(kNearChunk, total - v0);
         __syncthreads();
