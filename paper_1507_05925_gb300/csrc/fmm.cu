@@ -431,22 +431,27 @@ __global__ void __launch_bounds__(256) k_fmm_m2l(FmmDevT<T2> f, const int* stop)
       Pt[e] = pas[(long long)(f.nlog > 0 ? t : 0) * p * p + r].x;
     }
   const int per = nd * pk;
-  for (int e = tid; e < cnt4 * per; e += blockDim.x) {
-    const int q = e / per, r = e % per, d = r / pk, k = r % pk;
-    T2 u = cx<T2>(0.0, 0.0);
-    if (q < cnt && k < p) {
-      const T2* a = f.mp + ((lev_off(l) + s_src[q]) * nd) * p;
-      const int oi = s_off[q];
-      T2 v = a[d * p + k];
-      if (d == f.cm) {
-        // source moment density relative to the target centre: rho_S - conj(D) rho_0
-        cfma(v, cx<T2>((double)(3 - oi % 7), (double)(oi / 7 - 3)), a[k]);
+  // a thread keeps its (channel, coefficient) and walks the sources
+  for (int dk = tid; dk < per; dk += blockDim.x) {
+    const int d = dk / pk, k = dk % pk;
+    const int ty = d < f.nlog ? 1 : 0;
+    const T2* al = alpha + (long long)ty * kOffs * p + k;
+#pragma unroll 4
+    for (int q = 0; q < cnt4; ++q) {
+      T2 u = cx<T2>(0.0, 0.0);
+      if (q < cnt && k < p) {
+        const T2* a = f.mp + ((lev_off(l) + s_src[q]) * nd) * p;
+        const int oi = s_off[q];
+        T2 v = a[d * p + k];
+        if (d == f.cm) {
+          // source moment density relative to the target centre: rho_S - conj(D) rho_0
+          cfma(v, cx<T2>((double)(3 - oi % 7), (double)(oi / 7 - 3)), a[k]);
+        }
+        if (ty == 1 && k == 0) s_a0[q][d] = v;
+        u = cmul(al[(long long)oi * p], v);
       }
-      const int ty = d < f.nlog ? 1 : 0;
-      if (ty == 1 && k == 0) s_a0[q][d] = v;
-      u = cmul(alpha[((long long)ty * kOffs + oi) * p + k], v);
+      U[q * per + dk] = u;
     }
-    U[e] = u;
   }
   __syncthreads();
   const double inv_s = ldexp(f.Dinv, l);
@@ -621,26 +626,31 @@ __global__ void __launch_bounds__(kBFF) k_fmm_m2l_ff(FmmDev f, const float4* __r
   const float4* gamma = alpha + fftab_gamma(p);
   const float2* pas = reinterpret_cast<const float2*>(alpha + fftab_pascal(p));
   const int per = nd * p;
-  for (int e = tid; e < cnt4 * per; e += blockDim.x) {
-    const int q = e / per, r = e % per, d = r / p, k = r % p;
-    float2 uh = make_float2(0.f, 0.f), ul = uh;
-    if (q < cnt) {
-      const float4* a = mpff + ((lev_off(l) + s_src[q]) * nd) * p;
-      const int oi = s_off[q];
-      const float4 v = a[d * p + k];
-      float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
-      if (d == f.cm) {
-        // source moment density relative to the target centre: rho_S - conj(D) rho_0
-        const float4 a0 = a[k];
-        ff_cfma(vh, vl, make_float2((float)(3 - oi % 7), (float)(oi / 7 - 3)), make_float2(0.f, 0.f),
-                make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
+  // a thread keeps its (channel, coefficient) and walks the sources
+  for (int dk = tid; dk < per; dk += blockDim.x) {
+    const int d = dk / p, k = dk % p;
+    const int ty = d < f.nlog ? 1 : 0;
+    const float4* alk = alpha + (long long)ty * kOffs * p + k;
+#pragma unroll 2
+    for (int q = 0; q < cnt4; ++q) {
+      float2 uh = make_float2(0.f, 0.f), ul = uh;
+      if (q < cnt) {
+        const float4* a = mpff + ((lev_off(l) + s_src[q]) * nd) * p;
+        const int oi = s_off[q];
+        const float4 v = a[d * p + k];
+        float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
+        if (d == f.cm) {
+          // source moment density relative to the target centre: rho_S - conj(D) rho_0
+          const float4 a0 = a[k];
+          ff_cfma(vh, vl, make_float2((float)(3 - oi % 7), (float)(oi / 7 - 3)), make_float2(0.f, 0.f),
+                  make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
+        }
+        if (ty == 1 && k == 0) s_a0[q][d] = make_float4(vh.x, vh.y, vl.x, vl.y);
+        const float4 al = alk[(long long)oi * p];
+        ff_cfma(uh, ul, make_float2(al.x, al.y), make_float2(al.z, al.w), vh, vl);
       }
-      const int ty = d < f.nlog ? 1 : 0;
-      if (ty == 1 && k == 0) s_a0[q][d] = make_float4(vh.x, vh.y, vl.x, vl.y);
-      const float4 al = alpha[((long long)ty * kOffs + oi) * p + k];
-      ff_cfma(uh, ul, make_float2(al.x, al.y), make_float2(al.z, al.w), vh, vl);
+      U[q * per + dk] = make_float4(uh.x, uh.y, ul.x, ul.y);
     }
-    U[e] = make_float4(uh.x, uh.y, ul.x, ul.y);
   }
   __syncthreads();
   const double inv_s = ldexp(f.Dinv, l);
