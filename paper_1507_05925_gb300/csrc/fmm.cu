@@ -573,6 +573,36 @@ __device__ __forceinline__ void ff_cfma(float2& sh, float2& sl, float2 ah, float
   ff_acc2(sh, sl, yh, yl);
 }
 
+// Complex float-float values as (re, im) lane pairs: h the leading parts, l
+// the trailing ones.
+struct cff {
+  float2 h, l;
+};
+__device__ __forceinline__ cff cff_zero() { return cff{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ cff cff_load(float4 v) { return cff{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ cff cff_split(double re, double im) {
+  const float rh = (float)re, ih = (float)im;
+  return cff{make_float2(rh, ih), make_float2((float)(re - (double)rh), (float)(im - (double)ih))};
+}
+__device__ __forceinline__ double2 cff_to(cff a) {
+  return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
+}
+__device__ __forceinline__ cff cff_conj(cff a) {
+  return cff{make_float2(a.h.x, -a.h.y), make_float2(a.l.x, -a.l.y)};
+}
+__device__ __forceinline__ cff cff_neg(cff a) { return cff{neg2(a.h), neg2(a.l)}; }
+// acc + a b
+__device__ __forceinline__ cff cff_fma(cff acc, cff a, cff b) {
+  ff_cfma(acc.h, acc.l, a.h, a.l, b.h, b.l);
+  return acc;
+}
+// a (sh + sl), a real float-float factor
+__device__ __forceinline__ cff cff_scale(cff a, float sh, float sl) {
+  cff r;
+  ff_mul2(make_float2(sh, sh), make_float2(sl, sl), a.h, a.l, r.h, r.l);
+  return r;
+}
+
 // Tables of order p: alpha[2][49][p], beta[2][49][p], gamma[49][p] (float4;
 // type 0 Cauchy, 1 logarithm, as tab_alpha..tab_gamma), then the Pascal
 // matrices [2][k][l] (float2 hi, lo).
@@ -770,7 +800,17 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
   const int s0 = f.start[b], n = f.start[b + 1] - s0;
   if (n == 0) return;
   const long long box = lev_off(f.L) + b;
-  for (int e = threadIdx.x; e < f.nd * f.p; e += kB) sm[e] = f.lc[box * f.nd * f.p + e];
+  if constexpr (NEARP == 2) {
+    // float-float residuals: the local expansion split into hi + lo pairs
+    float4* smf = reinterpret_cast<float4*>(smraw);
+    for (int e = threadIdx.x; e < f.nd * f.p; e += kB) {
+      const double2 a = f.lc[box * f.nd * f.p + e];
+      const float rh = (float)a.x, ih = (float)a.y;
+      smf[e] = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
+    }
+  } else {
+    for (int e = threadIdx.x; e < f.nd * f.p; e += kB) sm[e] = f.lc[box * f.nd * f.p + e];
+  }
   const int y0 = max(0, by - 1), y1 = min(f.nb - 1, by + 1);
   const int x0 = max(0, bx - 1), x1 = min(f.nb - 1, bx + 1);
   if (threadIdx.x == 0) {
@@ -796,7 +836,48 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
     const int i = act ? f.perm[s0 + j] : 0;
     double ox = 0.0, oy = 0.0;
     const double nx1 = act ? g.nx[i] : 0.0, ny1 = act ? g.ny[i] : 0.0;
-    if (act) {
+    if (NEARP == 2 && act) {
+      // the far field in float-float on the FP32 pipe (Horner for F and F',
+      // then the kernel's combination), about the leaf centre
+      const float4* smf = reinterpret_cast<const float4*>(smraw);
+      const double ux = (g.x[i] - c.x) * inv_s, uy = (g.y[i] - c.y) * inv_s;
+      const cff U = cff_split(ux, uy);
+      const float ish = (float)inv_s, isl = (float)(inv_s - (double)ish);
+      cff F[3], dF[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (d < f.nd) {
+          cff h = cff_load(smf[d * f.p + f.p - 1]), dh = cff_zero();
+          for (int l = f.p - 2; l >= 0; --l) {
+            dh = cff_fma(h, dh, U);                         // h + dh u (the old h)
+            h = cff_fma(cff_load(smf[d * f.p + l]), h, U);  // a_l + h u
+          }
+          F[d] = h;
+          dF[d] = cff_scale(dh, ish, isl);
+        }
+      }
+      if (f.nd == 1) {
+        const double2 f0 = cff_to(F[0]);
+        ox = nx1 * f0.x - ny1 * f0.y;
+      } else {
+        const cff nu = cff_split(nx1, ny1), nub = cff_conj(nu);
+        const float slh = (float)s, sll = (float)(s - (double)slh);
+        // S3 = -F'_{q conj(z_j - c)} with c the leaf centre (channel cm holds that density / s)
+        const cff S2 = cff_neg(dF[0]), S3 = cff_neg(cff_scale(dF[2], slh, sll));
+        const cff S1 = F[0], S6 = F[1];
+        const cff zb = cff_split(g.x[i] - c.x, -(g.y[i] - c.y));
+        const cff w = cff_fma(cff_neg(S3), zb, S2);  // conj(z - c) S2 - S3
+        cff tt = cff_zero();
+        tt = cff_fma(tt, nub, cff_conj(w));
+        tt = cff_fma(tt, nu, cff_conj(S1));
+        tt = cff_fma(tt, nub, cff_conj(S6));
+        tt = cff_fma(tt, nu, S1);
+        const double2 t2 = cff_to(tt);
+        ox = 0.25 * t2.x;
+        oy = 0.25 * t2.y;
+      }
+    }
+    if (NEARP != 2 && act) {
       const double2 zi = make_double2(g.x[i], g.y[i]);
       const T2 u = cx<T2>((zi.x - c.x) * inv_s, (zi.y - c.y) * inv_s);
       using R = decltype(u.x);
@@ -955,40 +1036,27 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
         }
         ax = AX.x + AX.y;
         ay = AY.x + AY.y;
-      } else
-      for (int v0 = 0; v0 < total; v0 += kNearChunk) {
-        const int m = min(kNearChunk, total - v0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < m; e += kB) {
-          const int vv = v0 + e;
-          int lf = 0;
-          while (vv >= lst[lf + 1]) ++lf;
-          const int i2 = f.perm[lbeg[lf] + (vv - lst[lf])];
-          sid[e] = i2;
-          const double2 q = f.Q[(long long)i2 * f.nd];
-          if (NEARP == 1) {
-            spa[e] = g.pf[i2];
-            sq[e] = make_float4((float)q.x, (float)q.y, 0.f, 0.f);
-          } else {
+      } else {
+        // float-float: one source at a time, float-float sums
+        for (int v0 = 0; v0 < total; v0 += kNearChunk) {
+          const int m = min(kNearChunk, total - v0);
+          __syncthreads();
+          for (int e = threadIdx.x; e < m; e += kB) {
+            const int vv = v0 + e;
+            int lf = 0;
+            while (vv >= lst[lf + 1]) ++lf;
+            const int i2 = f.perm[lbeg[lf] + (vv - lst[lf])];
+            sid[e] = i2;
+            const double2 q = f.Q[(long long)i2 * f.nd];
             spa[e] = g.xff[i2];
             spb[e] = g.xfl[i2];
             const float q1h = (float)q.x, q2h = (float)q.y;
             sq[e] = make_float4(q1h, (float)(q.x - (double)q1h), q2h, (float)(q.y - (double)q2h));
           }
-        }
-        __syncthreads();
-        if (act) {
-          for (int e = 0; e < m; ++e) {
-            if (sid[e] == i) continue;
-            if (NEARP == 1) {
-              float cxv, cyv;
-              if (f.nd == 1)
-                f32_pair<0>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, spa[e], sq[e].x, 0.f, cxv, cyv);
-              else
-                f32_pair<1>(tp.x, tp.y, tp.z, tp.w, tn.x, tn.y, spa[e], sq[e].x, sq[e].y, cxv, cyv);
-              ax += cxv;
-              ay += cyv;
-            } else {
+          __syncthreads();
+          if (act) {
+            for (int e = 0; e < m; ++e) {
+              if (sid[e] == i) continue;
               float cxh, cxl, cyh, cyl;
               if (f.nd == 1)
                 ff_pair<0>(t, spa[e], spb[e], sq[e], cxh, cxl, cyh, cyl);
