@@ -572,17 +572,18 @@ def run_large(args, rank, local):
     UW = torch.empty(3 * N, dtype=torch.float64, device=dev)
     ctx = bie.Context(local)
     opts = bie.make_opts(precision=bie.MIXED_FF, fmm_order=args.fmm_order)
+    stream = torch.cuda.Stream(device=dev)  # capturable: the GMRES iterations replay as CUDA graphs
 
     def timed_solves():
-        rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
+        rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts, stream=stream)
         assert rc == bie.OK, (rc, ctx.last_error())
         torch.cuda.synchronize()
         ms = []
         for _ in range(args.large_steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts)
-            e1.record()
+            e0.record(stream)
+            rc, info = bie.mobility_solve(ctx, gd, FT, UW, opts=opts, stream=stream)
+            e1.record(stream)
             torch.cuda.synchronize()
             assert rc == bie.OK
             ms.append(e0.elapsed_time(e1))
@@ -596,7 +597,7 @@ def run_large(args, rank, local):
     ms, info = ms_default, info_default
     if not args.no_tune:
         # the FMM schedule (leaf population, inner order) tuned by timing whole solves
-        rc, leaf, inner, tms = bie.tune_fmm(ctx, gd, 1, FT, opts)
+        rc, leaf, inner, tms = bie.tune_fmm(ctx, gd, 1, FT, opts, stream=stream)
         assert rc == bie.OK, ctx.last_error()
         ms, info = timed_solves()
         out["tuned_schedule"] = {"leaf_nodes": leaf, "inner_order": inner, "seconds_per_solve": ms / 1e3,

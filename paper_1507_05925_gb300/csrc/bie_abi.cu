@@ -170,6 +170,7 @@ struct Work {
   double *x = nullptr, *y = nullptr, *dx = nullptr, *dy = nullptr, *ddx = nullptr, *ddy = nullptr;
   double *ipt = nullptr, *load = nullptr, *io_in = nullptr, *io_out = nullptr;
   // solver
+  float* VF = nullptr;  // FP32 copy of the basis for the FP32 inner solves (single systems)
   double *V = nullptr, *f = nullptr, *xs = nullptr, *r = nullptr, *d = nullptr, *rin = nullptr, *ytmp = nullptr;
   double* rc = nullptr;
   // block-Jacobi preconditioner of the inner solves
@@ -294,6 +295,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   w.st = A.take<KState>(1);
   if (solve) {
     w.V = A.take<double>((size_t)(m + 1) * w.ld);
+    if (nprob <= 1) w.VF = A.take<float>((size_t)(m + 1) * w.ld);
     w.f = A.take<double>(n);
     w.xs = A.take<double>(n);
     w.r = A.take<double>(n);
@@ -719,7 +721,9 @@ int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   if (w.seg.P > 1) {
     CK(arnoldi_seg(a, w.seg, w.seg_grid, s));
   } else {
-    CK(arnoldi(a, arnoldi_grid(n), s));
+    // the FP32 inner solves on wide grids: CGS2 in FP32 against the FP32 basis
+    if (op.prec == 1 && w.VF && !arnoldi_narrow(n)) a.vf = w.VF;
+    CK(arnoldi(a, arnoldi_grid(n, a.vf != nullptr), s));
   }
   return BIE_OK;
 }

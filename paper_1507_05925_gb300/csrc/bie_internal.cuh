@@ -321,6 +321,7 @@ struct ArnoldiArgs {
   const float* blocks;
   double* z;
   int bj64 = 0;            // apply the FP32 blocks in FP64 arithmetic (FP64 GMRES)
+  float* vf = nullptr;     // FP32 copy of the basis ((m + 1) x ld): CGS2 in FP32 (FP32 inner solves, wide grids)
   int fault_skip = -1;     // test hook: this CTA leaves before the first grid barrier
   long long spins = 0;     // polls before a grid barrier gives up (set by the launcher)
 };
@@ -328,7 +329,9 @@ struct ArnoldiArgs {
 // skip_cta and gives up waiting after `spins` polls (spins <= 0: disarmed).
 void arm_barrier_fault(int skip_cta, long long spins);
 bool barrier_fault_armed();
-int arnoldi_grid(long long n);  // co-resident CTAs for the cooperative launch
+// co-resident CTAs for the cooperative launch (fp32: the FP32 step of wide grids)
+int arnoldi_grid(long long n, bool fp32 = false);
+bool arnoldi_narrow(long long n);
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s);
 // h[i] = <V_i, w> for i <= j (first CGS pass)
 

@@ -198,16 +198,22 @@ __device__ __forceinline__ bool grid_barrier(KState* st, long long spins) {
 // off = its offset in the block array) and v = ws in shared memory.
 __device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long long off, int nb, const float* ws,
                               double* __restrict__ z, float4* red4) {
-  if ((nb & 3) == 0 && (off & 3) == 0) {
-    // 16-byte loads of four consecutive rows: 64 row quads x 4 column groups
-    const int nq = nb >> 2, qd = threadIdx.x & 63, grp = threadIdx.x >> 6;
-    const int per = (nb + 3) >> 2, cb = grp * per, ce = min(nb, cb + per);
-    for (int q0 = 0; q0 < nq; q0 += 64) {
+  if ((nb & 3) == 0 && (off & 3) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+    // 16-byte loads of four consecutive rows: R row-quad slots (the smallest
+    // power of two >= nb/4, from 8 to 64) x kBV/R column groups, so that
+    // every thread streams part of the block (a body of 64 Stokes nodes: 32
+    // row quads x 8 groups of 16 columns, 16 loads in flight a thread)
+    const int nq = nb >> 2;
+    int R = 64;
+    while (R > 8 && (R >> 1) >= nq) R >>= 1;
+    const int ng = kBV / R, qd = threadIdx.x & (R - 1), grp = threadIdx.x / R;
+    const int per = (nb + ng - 1) / ng, cb = grp * per, ce = min(nb, cb + per);
+    for (int q0 = 0; q0 < nq; q0 += R) {
       const int q = q0 + qd;
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       if (q < nq) {
         const float4* __restrict__ Bq = reinterpret_cast<const float4*>(B) + q;
-#pragma unroll 8
+#pragma unroll 16
         for (int col = cb; col < ce; ++col) {
           const float4 b = Bq[(long long)col * nq];
           const float x = ws[col];
@@ -221,19 +227,16 @@ __device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long 
       __syncthreads();
       if (grp == 0 && q < nq) {
         float4 t = red4[qd];
-#pragma unroll
-        for (int u = 1; u < 4; ++u) {
-          const float4 o = red4[u * 64 + qd];
+        for (int u = 1; u < ng; ++u) {
+          const float4 o = red4[u * R + qd];
           t.x += o.x;
           t.y += o.y;
           t.z += o.z;
           t.w += o.w;
         }
-        double* zr = z + 4 * q;
-        zr[0] = t.x;
-        zr[1] = t.y;
-        zr[2] = t.z;
-        zr[3] = t.w;
+        double2* zr = reinterpret_cast<double2*>(z + 4 * q);
+        zr[0] = make_double2(t.x, t.y);
+        zr[1] = make_double2(t.z, t.w);
       }
       __syncthreads();
     }
@@ -269,6 +272,51 @@ __device__ __forceinline__ void bj_body_apply64(const float* __restrict__ B, int
     if (col < nb) s0 = fma((double)B[(long long)col * nb + r], wd[col], s0);
     z[r] = s0 + s1;
   }
+}
+
+// CTA 0, all threads: Hessenberg column j (hs1 + hs2, then ||w||), the
+// previous rotations and the new one, the residual estimate and the stopping
+// test.  The column and rotations are kept in shared memory (one thread
+// applies the rotations; no global round trips in the chain).
+__device__ __noinline__ void arn_hessenberg(const ArnoldiArgs& a, KState* st, int j, const double* hs1,
+                                            const double* hs2, double hn) {
+  // Hessenberg column j and the previous rotations in shared memory (one
+  // thread applies the rotations; no global round trips in the chain)
+  __shared__ double hcol[kMaxBasis + 1], css[kMaxBasis], sns[kMaxBasis];
+  const int m = st->m;
+  double* Hc = a.H + (long long)j * (m + 1);
+  for (int i = threadIdx.x; i <= j; i += kBV) hcol[i] = hs1[i] + hs2[i];
+  for (int i = threadIdx.x; i < j; i += kBV) {
+    css[i] = a.cs[i];
+    sns[i] = a.sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    hcol[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = css[i] * hcol[i] + sns[i] * hcol[i + 1];
+      hcol[i + 1] = -sns[i] * hcol[i] + css[i] * hcol[i + 1];
+      hcol[i] = t;
+    }
+    const double x = hcol[j], y = hcol[j + 1];
+    const double r = hypot(x, y);
+    const double c = r > 0.0 ? x / r : 1.0, sg = r > 0.0 ? y / r : 0.0;
+    a.cs[j] = c;
+    a.sn[j] = sg;
+    hcol[j] = r;
+    hcol[j + 1] = 0.0;
+    const double g = a.gv[j];
+    a.gv[j + 1] = -sg * g;
+    a.gv[j] = c * g;
+    st->res = fabs(sg * g);
+    st->hnext = hn;
+    st->j = j + 1;
+    st->iters += 1;
+    if (st->res <= st->tol_abs || !(hn > 1e-300 * st->beta) || st->j >= m || st->iters >= st->maxit)
+      st->stop = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += kBV) Hc[i] = hcol[i];
 }
 
 template <bool NARROW>
@@ -317,45 +365,7 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
   }
   __syncthreads();
   const double hn = hn_s;
-  if (blockIdx.x == 0) {
-    // Hessenberg column j and the previous rotations in shared memory (one
-    // thread applies the rotations; no global round trips in the chain)
-    __shared__ double hcol[kMaxBasis + 1], css[kMaxBasis], sns[kMaxBasis];
-    const int m = st->m;
-    double* Hc = a.H + (long long)j * (m + 1);
-    for (int i = threadIdx.x; i <= j; i += kBV) hcol[i] = hs1[i] + hs2[i];
-    for (int i = threadIdx.x; i < j; i += kBV) {
-      css[i] = a.cs[i];
-      sns[i] = a.sn[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      hcol[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double t = css[i] * hcol[i] + sns[i] * hcol[i + 1];
-        hcol[i + 1] = -sns[i] * hcol[i] + css[i] * hcol[i + 1];
-        hcol[i] = t;
-      }
-      const double x = hcol[j], y = hcol[j + 1];
-      const double r = hypot(x, y);
-      const double c = r > 0.0 ? x / r : 1.0, sg = r > 0.0 ? y / r : 0.0;
-      a.cs[j] = c;
-      a.sn[j] = sg;
-      hcol[j] = r;
-      hcol[j + 1] = 0.0;
-      const double g = a.gv[j];
-      a.gv[j + 1] = -sg * g;
-      a.gv[j] = c * g;
-      st->res = fabs(sg * g);
-      st->hnext = hn;
-      st->j = j + 1;
-      st->iters += 1;
-      if (st->res <= st->tol_abs || !(hn > 1e-300 * st->beta) || st->j >= m || st->iters >= st->maxit)
-        st->stop = 1;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j + 1; i += kBV) Hc[i] = hcol[i];
-  }
+  if (blockIdx.x == 0) arn_hessenberg(a, st, j, hs1, hs2, hn);
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   if (!a.blocks) {
     // v_{j+1} = w / ||w|| over this CTA's own elements
@@ -389,6 +399,167 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
       bj_body_apply64(a.blocks + a.off[i], nb, wsd, a.z + a0);
     else
       bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------- Arnoldi step of the FP32 solves
+// The inner solves of the refinement apply the operator in FP32 and stop at a
+// relative residual of about 1e-6, so their Krylov basis needs FP32
+// orthogonality only.  This step runs CGS2 in FP32 arithmetic against an
+// FP32 copy VF of the basis (v_i as the floats the preconditioner and the
+// operator already see): rounding w = A z_j to FP32 and the FP32 projections
+// perturb the Arnoldi relation A P V = V H by O(eps32 ||w||), the size of the
+// FP32 operator's own error, and the second pass restores orthogonality to
+// O(eps32) (classical Gram-Schmidt twice).  The FP64 path above spends 4(j+1)
+// FP64 multiply-adds an element on GB300's narrow FP64 pipe; this one
+// 4(j+1) FP32 ones, and reads half the bytes.  The sums run in a fixed order
+// (deterministic); the grid sums, the Hessenberg column and the rotations
+// stay in FP64.  V_{j+1} (FP64, read by the solution update) receives the
+// FP32 basis vector exactly.
+
+// Partial dot products of this CTA's elements of x (FP32) with VF_0..VF_{jc-1}
+// into out[0..jc): eight basis vectors a pass, FP32 sums per thread, a fixed
+// shuffle tree per warp, the warps added in FP64 in order.
+__device__ __forceinline__ void arn_block_dots32(const float* __restrict__ VF, long long ld,
+                                                 const float* __restrict__ x, long long n, int jc,
+                                                 double* __restrict__ out, float (*sh)[kMaxBasis]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long stride = (long long)gridDim.x * kBV;
+  for (int i = 0; i < jc; i += 8) {
+    const int cnt = min(8, jc - i);
+    float acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+      const float xk = x[k];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < cnt) acc[u] = fmaf(VF[(long long)(i + u) * ld + k], xk, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < cnt) {
+        const float t = warp_sumf(acc[u]);
+        if (lane == 0) sh[wid][i + u] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < jc; q += kBV) {
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < kBV / 32; ++u) t += (double)sh[u][q];
+    out[q] = t;
+  }
+}
+
+// x[k] -= sum_i h[i] VF_i[k] over this CTA's elements (two FP32 chains, fixed
+// order); returns this thread's FP32 sum of the new x[k]^2 when NORM.
+template <bool NORM>
+__device__ __forceinline__ float arn_project32(const float* __restrict__ VF, long long ld, float* __restrict__ x,
+                                               long long n, int jc, const float* h) {
+  const long long stride = (long long)gridDim.x * kBV;
+  float nrm = 0.f;
+  for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+    float t0 = x[k], t1 = 0.f;
+    int i = 0;
+    for (; i + 2 <= jc; i += 2) {
+      t0 = fmaf(-h[i], VF[(long long)i * ld + k], t0);
+      t1 = fmaf(-h[i + 1], VF[(long long)(i + 1) * ld + k], t1);
+    }
+    if (i < jc) t0 = fmaf(-h[i], VF[(long long)i * ld + k], t0);
+    const float t = t0 + t1;
+    x[k] = t;
+    if (NORM) nrm = fmaf(t, t, nrm);
+  }
+  return nrm;
+}
+
+__global__ void __launch_bounds__(kBV, 4) k_arnoldi32(ArnoldiArgs a) {
+  KState* st = a.st;
+  if (st->stop) return;  // read by every CTA before the first barrier: uniform
+  __shared__ float shf[kBV / 32][kMaxBasis];
+  __shared__ double hs1[kMaxBasis], hs2[kMaxBasis];
+  __shared__ float hf[kMaxBasis];
+  __shared__ double red[kBV / 32];
+  __shared__ float ws[kBjMaxBlock];
+  __shared__ float4 red4[kBV];
+  const int j = st->j, jc = j + 1;
+  const long long n = a.n, ld = a.ld;
+  float* __restrict__ VF = a.vf;
+  double* __restrict__ w = a.V + (long long)(j + 1) * ld;  // A z_j (FP64, from the operator)
+  float* __restrict__ wf = VF + (long long)(j + 1) * ld;    // w in FP32, then v_{j+1}
+  const long long stride = (long long)gridDim.x * kBV;
+  const long long G = gridDim.x;
+  double* part1 = a.part;
+  double* part2 = part1 + G * kMaxBasis;
+  double* part3 = part2 + G * kMaxBasis;
+  // VF_j = V_j in FP32 (exact for j > 0: V_j came from VF_j), w in FP32
+  {
+    const double* __restrict__ vj = a.V + (long long)j * ld;
+    float* __restrict__ vfj = VF + (long long)j * ld;
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+      vfj[k] = (float)vj[k];
+      wf[k] = (float)w[k];
+    }
+  }
+  // h1 = VF^T w
+  arn_block_dots32(VF, ld, wf, n, jc, part1 + blockIdx.x * kMaxBasis, shf);
+  if ((int)blockIdx.x == a.fault_skip) return;  // test hook: this CTA never arrives
+  if (grid_barrier(st, a.spins)) return;
+  arn_grid_sum(part1, jc, hs1);
+  for (int i = threadIdx.x; i < jc; i += kBV) hf[i] = (float)hs1[i];
+  __syncthreads();
+  // w -= VF h1; h2 = VF^T w
+  arn_project32<false>(VF, ld, wf, n, jc, hf);
+  __syncthreads();  // hf and shf are reused below
+  arn_block_dots32(VF, ld, wf, n, jc, part2 + blockIdx.x * kMaxBasis, shf);
+  if (grid_barrier(st, a.spins)) return;
+  arn_grid_sum(part2, jc, hs2);
+  for (int i = threadIdx.x; i < jc; i += kBV) hf[i] = (float)hs2[i];
+  __syncthreads();
+  // w -= VF h2; ||w||^2
+  double nrm = (double)arn_project32<true>(VF, ld, wf, n, jc, hf);
+  nrm = block_sum<kBV>(nrm, red);
+  if (threadIdx.x == 0) part3[blockIdx.x * kMaxBasis] = nrm;
+  if (grid_barrier(st, a.spins)) return;
+  __shared__ double hn_s;
+  if (threadIdx.x < 32) {
+    const double t = warp_gather(part3, kMaxBasis);
+    if (threadIdx.x == 0) hn_s = sqrt(t);
+  }
+  __syncthreads();
+  const double hn = hn_s;
+  if (blockIdx.x == 0) arn_hessenberg(a, st, j, hs1, hs2, hn);
+  const float inv = hn > 0.0 ? (float)(1.0 / hn) : 0.f;
+  if (!a.blocks) {
+    // v_{j+1} = w / ||w|| over this CTA's own elements
+    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
+      const float v = wf[k] * inv;
+      wf[k] = v;
+      w[k] = (double)v;
+    }
+    return;
+  }
+  // per body: v = w inv (w read through L2: other CTAs wrote it), z = P v
+  const int c = a.kind + 1;
+  for (int i = blockIdx.x; i < a.g.N; i += (int)G) {
+    const long long a0 = (long long)a.g.body_start[i] * c;
+    const int nb = (a.g.body_start[i + 1] - a.g.body_start[i]) * c;
+    const bool apply = nb <= kBjMaxBlock;
+    for (int r = threadIdx.x; r < nb; r += kBV) {
+      const float v = __ldcg(wf + a0 + r) * inv;
+      wf[a0 + r] = v;
+      w[a0 + r] = (double)v;
+      if (apply)
+        ws[r] = v;
+      else
+        a.z[a0 + r] = (double)v;
+    }
+    if (!apply) continue;
+    __syncthreads();
+    bj_body_apply(a.blocks + a.off[i], a.off[i], nb, ws, a.z + a0, red4);
     __syncthreads();
   }
 }
@@ -793,23 +964,24 @@ int vec_grid(long long n) {
 // The narrow instance for grids of at most two CTAs per SM.
 bool arnoldi_narrow(long long n) { return vec_grid(n) <= 2 * device_sms(); }
 
-int arnoldi_grid(long long n) {
-  static std::atomic<int> coresident[64][2];
+int arnoldi_grid(long long n, bool fp32) {
+  static std::atomic<int> coresident[64][3];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   const int narrow = arnoldi_narrow(n) ? 1 : 0;
-  if (coresident[dev][narrow].load() == 0) {
+  const int v = narrow ? 1 : (fp32 ? 2 : 0);
+  if (coresident[dev][v].load() == 0) {
     int per_sm = 0, sms = 0;
-    const void* fn = narrow ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>;
+    const void* fn = v == 1 ? (const void*)k_arnoldi<true> : (v == 2 ? (const void*)k_arnoldi32 : (const void*)k_arnoldi<false>);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBV, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm * sms < 1) {
       cudaGetLastError();
       return 1;  // not cached: a launch of one CTA is always co-resident
     }
-    coresident[dev][narrow].store(per_sm * sms);
+    coresident[dev][v].store(per_sm * sms);
   }
-  return std::min(vec_grid(n), coresident[dev][narrow].load());
+  return std::min(vec_grid(n), coresident[dev][v].load());
 }
 
 namespace {
@@ -841,7 +1013,8 @@ cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s) {
   ArnoldiArgs args = a;
   take_fault(args);
   void* params[] = {&args};
-  const void* fn = arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>;
+  const void* fn = arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true>
+                   : (a.vf ? (const void*)k_arnoldi32 : (const void*)k_arnoldi<false>);
   const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBV), params, 0, s);
   note_launches(1);
   return e;
