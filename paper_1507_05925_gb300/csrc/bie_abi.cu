@@ -228,6 +228,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   g.kappa = A.take<double>(M);
   g.pf = A.take<float4>(M);
   g.nf = A.take<float2>(M);
+  g.wkf = A.take<float2>(M);
   g.xff = A.take<float4>(M);
   g.xfl = A.take<float2>(M);
   g.nff = A.take<float4>(M);
@@ -673,18 +674,18 @@ struct Op {
       const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
       cudaError_t e = timed_pair_sum(ctx, g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
       if (e != cudaSuccess) return e;
-      return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1);
+      return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1, prec == 1);
     }
     if (fmm_p > 0) {
       const PairPlan one = uniform_plan(1, w->g.M);
       cudaError_t e = fmm_pair_sum(ctx->fmm, w->g, w->kind, fmm_p, in, w->g.sw, w->partial, stop, s, prec);
       if (e != cudaSuccess) return e;
-      return epilogue(w->g, w->kind, one, in, w->partial, 1, 1, 1.0, out, stop, s, alpha);
+      return epilogue(w->g, w->kind, one, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, false, prec == 1);
     }
     const PairPlan& p = prec == 0 ? w->plan64 : (prec == 1 ? w->plan32 : w->planff);
     cudaError_t e = timed_pair_sum(ctx, w->g, w->kind, prec, p, in, w->g.sw, w->partial, stop, valid, s);
     if (e != cudaSuccess) return e;
-    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1);
+    return epilogue(w->g, w->kind, p, in, w->partial, 1, 1, 1.0, out, stop, s, alpha, prec == 1, prec == 1);
   }
 };
 

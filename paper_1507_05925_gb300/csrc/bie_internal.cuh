@@ -3,7 +3,8 @@
 // Data layout in device memory (one staged geometry per call):
 //   per node  [M]: x, y, nx, ny, w, sw = sqrt(w), kappa (float64),
 //                  pf = (x_hi, y_hi, x_lo, y_lo) float4 with x = x_hi + x_lo exactly
-//                  to ~2^-48 relative, nf = (nx, ny) float2, body_of (int32)
+//                  to ~2^-48 relative, nf = (nx, ny) float2, wkf = (sqrt(w), w kappa)
+//                  float2, body_of (int32)
 //   per body  [N]: len = |Gamma_i|, xc, yc (arc-length centroid), W_i, interior
 //                  point z0 and stencil step delta, FP32 bounding box
 //   densities: scaled by sqrt(w) (the L2 rescaling of Section 6.1.1); Stokes
@@ -46,6 +47,7 @@ struct Geo {
   double *w = nullptr, *sw = nullptr, *kappa = nullptr;
   float4* pf = nullptr;
   float2* nf = nullptr;
+  float2* wkf = nullptr;  // [M] (sqrt(w), w kappa) in FP32, for the FP32 operator's epilogue
   double *len = nullptr, *xc = nullptr, *yc = nullptr, *W = nullptr;
   double *zx = nullptr, *zy = nullptr, *delta = nullptr, *wind = nullptr;
   float4* bbox = nullptr;  // [N] (xmin, ymin, xmax, ymax) of the body's nodes, FP32
@@ -201,7 +203,7 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 // precision 1), summed in float-float; otherwise doubles.
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s, double alpha = 0.0, bool pff = false);
+                     cudaStream_t s, double alpha = 0.0, bool pff = false, bool fp32 = false);
 // out = in - (I - C) L~(in) for a correction solved with the weighted completion.
 cudaError_t consistent_rhs(const Geo& g, int kind, double alpha, const double* in, double* out,
                            cudaStream_t s);

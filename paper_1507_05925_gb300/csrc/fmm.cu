@@ -104,6 +104,7 @@ struct FmmDevT {
   T2* mp;
   T2* lc;
   const T2* ops;
+  const float2* Qf = nullptr;  // FP32 expansions: q per source in FP32 (channel 0), from k_fmm_density32
 };
 using FmmDev = FmmDevT<double2>;
 
@@ -234,6 +235,86 @@ __global__ void k_fmm_density(Geo g, int nd, double cx0, double cy0, VecRef vr, 
       Q[3 * i + 2] = cmul(q, make_double2(g.x[i] - cx0, -(g.y[i] - cy0)));
     }
   }
+}
+
+// The FP32 operator's strengths: q = sqrt(w) v per source in FP32 (Laplace:
+// (q, 0); Stokes: the complex density).  The other channels (conj(q) and the
+// leaf-relative moment density) are formed where they are used, so the FP32
+// passes read 8 bytes a source and convert nothing from FP64.
+__global__ void k_fmm_density32(Geo g, int nd, VecRef vr, const double* __restrict__ sscale, float2* Qf,
+                                const int* stop) {
+  if (stop && *stop) return;
+  const double* v = vr.ptr();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.M; i += gridDim.x * blockDim.x) {
+    if (nd == 1)
+      Qf[i] = make_float2((float)(sscale[i] * v[i]), 0.f);
+    else
+      Qf[i] = make_float2((float)(sscale[i] * v[2 * i]), (float)(sscale[i] * v[2 * i + 1]));
+  }
+}
+
+// Leaf centre c of block b split as float hi + lo, and 1/s in FP32: computed
+// once per block (FP64 arithmetic on one thread) for the FP32 passes, which
+// then form u = (z - c)/s from the hi/lo split of z in FP32 (z_hi - c_hi is
+// exact for a node inside the leaf unless |z| is of the order of s).
+__device__ __forceinline__ void leaf_center32(const FmmDevT<float2>& f, int b, float* cen) {
+  if (threadIdx.x == 0) {
+    double s;
+    const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
+    const float hx = (float)c.x, hy = (float)c.y;
+    cen[0] = hx;
+    cen[1] = hy;
+    cen[2] = (float)(c.x - (double)hx);
+    cen[3] = (float)(c.y - (double)hy);
+    cen[4] = (float)ldexp(f.Dinv, f.L);
+    cen[5] = (float)s;
+  }
+}
+
+// P2M of the FP32 expansions (inner solves) with no FP64 instruction per
+// source: positions from the hi/lo split, strengths from k_fmm_density32.
+__global__ void __launch_bounds__(kB) k_fmm_p2m32(FmmDevT<float2> f, Geo g, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* pw = reinterpret_cast<float2*>(smraw);  // [p][kChunk + 1]
+  float2* qs = pw + f.p * (kChunk + 1);            // [kChunk][nd]
+  __shared__ float cen[6];
+  const int b = blockIdx.x;
+  const long long box = lev_off(f.L) + b;
+  const int s0 = f.start[b], n = f.start[b + 1] - s0;
+  if (n == 0) return;
+  leaf_center32(f, b, cen);
+  __syncthreads();
+  const int t = threadIdx.x;
+  float2 acc[kMaxNd];
+  for (int d = 0; d < kMaxNd; ++d) acc[d] = make_float2(0.f, 0.f);
+  for (int ch = 0; ch < n; ch += kChunk) {
+    const int m = min(kChunk, n - ch);
+    if (t < m) {
+      const int i = f.perm[s0 + ch + t];
+      const float4 P = g.pf[i];
+      const float2 u = make_float2(((P.x - cen[0]) + (P.z - cen[2])) * cen[4], ((P.y - cen[1]) + (P.w - cen[3])) * cen[4]);
+      float2 w = make_float2(1.f, 0.f);
+      for (int k = 0; k < f.p; ++k) {
+        pw[k * (kChunk + 1) + t] = w;
+        w = cmul(w, u);
+      }
+      const float2 q = f.Qf[i];
+      qs[t * f.nd] = q;
+      if (f.nd == 3) {
+        qs[t * 3 + 1] = make_float2(q.x, -q.y);
+        // channel cm = 2: q conj(u), the leaf-relative moment density
+        qs[t * 3 + 2] = make_float2(q.x * u.x + q.y * u.y, q.y * u.x - q.x * u.y);
+      }
+    }
+    __syncthreads();
+    if (t < f.p)
+      for (int j = 0; j < m; ++j)
+        for (int d = 0; d < f.nd; ++d) cfma(acc[d], pw[t * (kChunk + 1) + j], qs[j * f.nd + d]);
+    __syncthreads();
+  }
+  if (t < f.p)
+    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
 }
 
 // P2M on the leaves: a_k = sum_j q_j u_j^k, u = (z - c)/s.
@@ -796,6 +877,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
   __shared__ float4 sq[kNearChunk];   // FP32: (q1, q2, -, -); float-float: (q1h, q1l, q2h, q2l)
   __shared__ __align__(16) int sid[kNearChunk];
   __shared__ int lst[10], lbeg[9];
+  __shared__ float cen[6];  // FP32 instance: split leaf centre, 1/s, s
   const int b = blockIdx.x, bx = b % f.nb, by = b / f.nb;
   const int s0 = f.start[b], n = f.start[b + 1] - s0;
   if (n == 0) return;
@@ -813,6 +895,7 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
   }
   const int y0 = max(0, by - 1), y1 = min(f.nb - 1, by + 1);
   const int x0 = max(0, bx - 1), x1 = min(f.nb - 1, bx + 1);
+  if constexpr (NEARP == 1) leaf_center32(f, b, cen);
   if (threadIdx.x == 0) {
     int c = 0, tot = 0;
     for (int ny = y0; ny <= y1; ++ny)
@@ -835,7 +918,8 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
     const bool act = j < n;
     const int i = act ? f.perm[s0 + j] : 0;
     double ox = 0.0, oy = 0.0;
-    const double nx1 = act ? g.nx[i] : 0.0, ny1 = act ? g.ny[i] : 0.0;
+    float oxf = 0.f, oyf = 0.f;  // FP32 instance
+    const double nx1 = (NEARP != 1 && act) ? g.nx[i] : 0.0, ny1 = (NEARP != 1 && act) ? g.ny[i] : 0.0;
     if (NEARP == 2 && act) {
       // the far field in float-float on the FP32 pipe (Horner for F and F',
       // then the kernel's combination), about the leaf centre
@@ -877,7 +961,48 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
         oy = 0.25 * t2.y;
       }
     }
-    if (NEARP != 2 && act) {
+    if constexpr (NEARP == 1) {
+      if (act) {
+        // FP32 throughout: u from the hi/lo split of z and the block's split
+        // centre (no FP64 instruction per target)
+        const float4 P = g.pf[i];
+        const float2 nn = g.nf[i];
+        const float dxc = (P.x - cen[0]) + (P.z - cen[2]), dyc = (P.y - cen[1]) + (P.w - cen[3]);
+        const float2 u = make_float2(dxc * cen[4], dyc * cen[4]);
+        float2 F[3], dF[3];  // nd = 1 or 3 (operator channels), unrolled: registers
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (d < f.nd) {
+            float2 h = sm[d * f.p + f.p - 1], dh = make_float2(0.f, 0.f);
+            for (int l = f.p - 2; l >= 0; --l) {
+              dh = cadd(cmul(dh, u), h);
+              h = cadd(cmul(h, u), sm[d * f.p + l]);
+            }
+            F[d] = h;
+            dF[d] = make_float2(dh.x * cen[4], dh.y * cen[4]);
+          }
+        }
+        if (f.nd == 1) {
+          oxf = nn.x * F[0].x - nn.y * F[0].y;
+        } else {
+          // the kernel's combination about the leaf centre, as in the FP64 instance
+          const float2 nu = nn, nub = make_float2(nn.x, -nn.y);
+          const float2 S2 = make_float2(-dF[0].x, -dF[0].y);
+          const float2 S3 = make_float2(-cen[5] * dF[2].x, -cen[5] * dF[2].y);
+          const float2 S1 = F[0], S6 = F[1];
+          float2 w = cmul(make_float2(dxc, -dyc), S2);
+          w.x -= S3.x;
+          w.y -= S3.y;
+          float2 tt = cmul(nub, cconj(w));
+          tt = cadd(tt, cmul(nu, cconj(S1)));
+          tt = cadd(tt, cmul(nub, cconj(S6)));
+          tt = cadd(tt, cmul(nu, S1));
+          oxf = 0.25f * tt.x;
+          oyf = 0.25f * tt.y;
+        }
+      }
+    }
+    if (NEARP == 0 && act) {
       const double2 zi = make_double2(g.x[i], g.y[i]);
       const T2 u = cx<T2>((zi.x - c.x) * inv_s, (zi.y - c.y) * inv_s);
       using R = decltype(u.x);
@@ -995,9 +1120,8 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
                 int lf = 0;
                 while (vv >= lst[lf + 1]) ++lf;
                 const int i2 = f.perm[lbeg[lf] + (vv - lst[lf])];
-                const double2 qd = f.Q[(long long)i2 * f.nd];
                 P[h] = g.pf[i2];
-                q[h] = make_float2((float)qd.x, (float)qd.y);
+                q[h] = f.Qf[i2];
                 id[h] = i2;
               }
             }
@@ -1078,12 +1202,14 @@ __global__ void __launch_bounds__(kB) k_fmm_eval(FmmDevT<T2> f, Geo g, double* _
           oy += day;
         }
       } else {
-        if (f.nd == 1)
-          ox += nx1 * (double)ax + ny1 * (double)ay;
-        else {
-          ox += (double)ax;
-          oy += (double)ay;
+        if (f.nd == 1) {
+          oxf += tn.x * ax + tn.y * ay;
+        } else {
+          oxf += ax;
+          oyf += ay;
         }
+        ox = (double)oxf;
+        oy = (double)oyf;
       }
     }
     if (act) {
@@ -1467,7 +1593,10 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
   const int p = d.p, nd = d.nd;
   const size_t sm_exp = (size_t)nd * p * sizeof(T2);
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(T2);
-  k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
+  if constexpr (std::is_same<T2, float2>::value)
+    k_fmm_p2m32<<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
+  else
+    k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
   const size_t sm_tree = tree_smem<T2>(nd, p);
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<T2><<<1 << (2 * l), kB, sm_tree, s>>>(d, l, stop);
   bool done = false;
@@ -1529,16 +1658,20 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
     if (o.first == p) ops32 = o.second;
   if (!ops || !ops32) return cudaErrorInvalidValue;  // fmm_setup prepares every order
   const int nd = kind == 0 ? 1 : 3;
-  k_fmm_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, f->x0 + 0.5 * f->D, f->y0 + 0.5 * f->D, v, sscale, f->Q,
-                                               stop);
   if (near_prec == 1) {
-    // the inner solves' operator: FP32 expansions (in the FP64 buffers) and FP32 near field
-    const FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,       kind == 1 ? 2 : -1,
-                            f->x0,    f->y0,     f->D,     1.0 / f->D, f->leaf,  f->perm, f->start,
-                            f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
-                            reinterpret_cast<float2*>(f->lc), ops32};
+    // the inner solves' operator: FP32 strengths, expansions (in the FP64
+    // buffers) and near field
+    float2* Qf = reinterpret_cast<float2*>(f->Q);
+    k_fmm_density32<<<grid_for(g.M), 256, 0, s>>>(g, nd, v, sscale, Qf, stop);
+    FmmDevT<float2> d{f->L,     f->nb,     p,        nd,       g.M,     0,       kind == 1 ? 2 : -1,
+                      f->x0,    f->y0,     f->D,     1.0 / f->D, f->leaf,  f->perm, f->start,
+                      f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
+                      reinterpret_cast<float2*>(f->lc), ops32};
+    d.Qf = Qf;
     fmm_passes<float2, 1>(d, f, g, partial, stop, s);
   } else {
+    k_fmm_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, f->x0 + 0.5 * f->D, f->y0 + 0.5 * f->D, v, sscale, f->Q,
+                                                 stop);
     const FmmDev d{f->L,    f->nb,    p,     nd,    g.M,   0,   kind == 1 ? 2 : -1, f->x0, f->y0, f->D, 1.0 / f->D, f->leaf,
                    f->perm, f->start, f->count, f->count, f->Q, f->mp, f->lc,  ops};
     if (near_prec == 2)

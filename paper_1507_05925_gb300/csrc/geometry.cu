@@ -41,11 +41,13 @@ __global__ void __launch_bounds__(kB) k_stage(Geo g, const double* __restrict__ 
     g.nx[a] = ty;
     g.ny[a] = -tx;
     g.w[a] = w;
-    g.sw[a] = sqrt(w);
+    const double sw = sqrt(w);
+    g.sw[a] = sw;
     g.kappa[a] = kap;
     const float xh = (float)x, yh = (float)y;
     g.pf[a] = make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
     g.nf[a] = make_float2((float)ty, (float)(-tx));
+    g.wkf[a] = make_float2((float)sw, (float)(w * kap));
     g.body_of[a] = i;
     sl += w;
     sx += w * x;

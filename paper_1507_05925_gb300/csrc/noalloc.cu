@@ -26,14 +26,14 @@ constexpr int kNoallocMaxBodies = BIE_NOALLOC_MAX_BODIES;
 constexpr int kNoallocMaxSplits = 16;
 constexpr int kMaxDevices = 64;
 
-// Bytes for: staged geometry (per node 7 doubles + 3 float4 + 2 float2 + 2 floats + int, per
+// Bytes for: staged geometry (per node 7 doubles + 3 float4 + 3 float2 + 2 floats + int, per
 // body 8 doubles + float4 + body_start) and the partials [splits][2 * nodes] doubles,
 // each section padded to 256 bytes.
 constexpr size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kScratchBytes =
     pad256((kNoallocMaxBodies + 1) * sizeof(int)) + pad256(kNoallocMaxNodes * sizeof(int)) +
     7 * pad256(kNoallocMaxNodes * sizeof(double)) + 3 * pad256(kNoallocMaxNodes * sizeof(float4)) +
-    2 * pad256(kNoallocMaxNodes * sizeof(float2)) + pad256(2 * kNoallocMaxNodes * sizeof(float)) +
+    3 * pad256(kNoallocMaxNodes * sizeof(float2)) + pad256(2 * kNoallocMaxNodes * sizeof(float)) +
     8 * pad256(kNoallocMaxBodies * sizeof(double)) +
     pad256(kNoallocMaxBodies * sizeof(float4)) + pad256(2 * sizeof(double)) +
     pad256((size_t)kNoallocMaxSplits * 2 * kNoallocMaxNodes * sizeof(double));
@@ -137,6 +137,7 @@ extern "C" int apply_operator_noalloc(const bie_geometry* geom, int kind, int pr
   g.kappa = c.take<double>(kNoallocMaxNodes);
   g.pf = c.take<float4>(kNoallocMaxNodes);
   g.nf = c.take<float2>(kNoallocMaxNodes);
+  g.wkf = c.take<float2>(kNoallocMaxNodes);
   g.xff = c.take<float4>(kNoallocMaxNodes);
   g.xfl = c.take<float2>(kNoallocMaxNodes);
   g.nff = c.take<float4>(kNoallocMaxNodes);

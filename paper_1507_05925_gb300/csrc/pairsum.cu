@@ -964,6 +964,11 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
   const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
   const double xc = g.xc[i], yc = g.yc[i];
   double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  __shared__ double cfs[2];  // completion weights alpha/|Gamma_i|, alpha/W_i: one FP64 division each per block
+  if (with_L && alpha > 0.0 && threadIdx.x == 0) {
+    cfs[0] = alpha / g.len[i];
+    cfs[1] = KIND == 1 ? alpha / g.W[i] : 1.0;
+  }
   if (with_L) {
     for (int a = a0 + threadIdx.x; a < a1; a += B) {
       const double s = scaled ? g.sw[a] : g.w[a];
@@ -982,10 +987,10 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
       m2 = block_sum<B>(m2, sh);
     }
     if (alpha > 0.0) {  // completion weighted per body: force part alpha/|Gamma_i|, torque part alpha/W_i
-      const double cf = alpha / g.len[i];
+      const double cf = cfs[0];  // written before block_sum's barriers
       m0 *= cf;
       m1 *= cf;
-      if (KIND == 1) m2 *= alpha / g.W[i];
+      if (KIND == 1) m2 *= cfs[1];
     }
   }
   for (int a = a0 + threadIdx.x; a < a1; a += B) {
@@ -1059,6 +1064,156 @@ __global__ void __launch_bounds__(B) k_epilogue(Geo g, VecRef vr, const double* 
       }
       // os y with the diagonal term os dd t, dd = -wk (t . mu)/2pi and mu = v/os:
       // os dd = -wk (t . v)/2pi needs no division
+      const double tx = -g.ny[a], ty = g.nx[a];
+      const double v1 = v[2 * a], v2 = v[2 * a + 1];
+      const double odd = -0.5 * kInvPi * wk * (tx * v1 + ty * v2);
+      const double px = -(g.y[a] - yc), py = g.x[a] - xc;
+      out[2 * a] = sign * (0.5 * v1 + os * (m0 + px * m2 - kInvPi * k1) + odd * tx);
+      out[2 * a + 1] = sign * (0.5 * v2 + os * (m1 + py * m2 - kInvPi * k2) + odd * ty);
+    }
+  }
+}
+
+// The epilogue of the FP32 operator (the inner solves).  On GB300 most of
+// k_epilogue's FP64-pipe time goes to the per-body completion moments and
+// their block sums; here they run on the FP32 pipe in float-float (FP32
+// products s v with their exact rounding errors, error-free sums), which
+// keeps them accurate well beyond FP32 (the per-term roundings of s and v
+// average out; no total is ever rounded to FP32), and the per-node output
+// is k_epilogue's FP64 expression.  Fixed order throughout (deterministic).
+// (h, l) += (bh, bl) in float-float
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+// (h, l) += a b with the product's rounding error
+__device__ __forceinline__ void ff_add_prod(float& h, float& l, float a, float b) {
+  const float p = a * b;
+  ff_add(h, l, p, fmaf(a, b, -p));
+}
+
+// Block sum of a float-float value; the result, as a double, in *out (shared)
+// after the call.  sh needs B/32 float2.
+template <int B>
+__device__ __forceinline__ void block_sum_ff(float h, float l, float2* sh, double* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, h, o), ol = __shfl_down_sync(0xffffffffu, l, o);
+    ff_add(h, l, oh, ol);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(h, l);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float th = sh[0].x, tl = sh[0].y;
+#pragma unroll
+    for (int k = 1; k < B / 32; ++k) ff_add(th, tl, sh[k].x, sh[k].y);
+    *out = (double)th + (double)tl;
+  }
+}
+
+template <int KIND, int B>
+__global__ void __launch_bounds__(B) k_epilogue32(Geo g, VecRef vr, const double* __restrict__ partial, int S,
+                                                    int scaled, int with_L, double alpha, double sign, VecRef outr,
+                                                    const int* __restrict__ stop, int pff) {
+  if (stop && *stop) return;
+  __shared__ float2 sh[B / 32];
+  __shared__ float cst[4];   // body centre split hi + lo
+  __shared__ double mom[3];  // completion moments, weighted
+  const double* __restrict__ v = vr.ptr();
+  double* __restrict__ out = outr.ptr();
+  const int M = g.M;
+  const int i = blockIdx.x;
+  const int a0 = g.body_start[i], a1 = g.body_start[i + 1];
+  const double xc = g.xc[i], yc = g.yc[i];
+  if (threadIdx.x == 0) {
+    const float hx = (float)xc, hy = (float)yc;
+    cst[0] = hx;
+    cst[1] = hy;
+    cst[2] = (float)(xc - (double)hx);
+    cst[3] = (float)(yc - (double)hy);
+    mom[0] = mom[1] = mom[2] = 0.0;
+  }
+  __syncthreads();
+  if (with_L) {
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    for (int a = a0 + threadIdx.x; a < a1; a += B) {
+      const float2 wk = g.wkf[a];
+      const float sc = scaled ? wk.x : wk.x * wk.x;
+      if (KIND == 0) {
+        ff_add_prod(h0, l0, sc, (float)v[a]);
+      } else {
+        const float4 P = g.pf[a];
+        const float dx = (P.x - cst[0]) + (P.z - cst[2]), dy = (P.y - cst[1]) + (P.w - cst[3]);
+        const float f1 = (float)v[2 * a] * sc, f2 = (float)v[2 * a + 1] * sc;
+        ff_add_prod(h0, l0, sc, (float)v[2 * a]);
+        ff_add_prod(h1, l1, sc, (float)v[2 * a + 1]);
+        ff_add_prod(h2, l2, -dy, f1);
+        ff_add_prod(h2, l2, dx, f2);
+      }
+    }
+    block_sum_ff<B>(h0, l0, sh, &mom[0]);
+    if (KIND == 1) {
+      block_sum_ff<B>(h1, l1, sh, &mom[1]);
+      block_sum_ff<B>(h2, l2, sh, &mom[2]);
+    }
+    if (threadIdx.x == 0 && alpha > 0.0) {  // completion weighted per body
+      const double cf = alpha / g.len[i];
+      mom[0] *= cf;
+      mom[1] *= cf;
+      if (KIND == 1) mom[2] *= alpha / g.W[i];
+    }
+    __syncthreads();
+  }
+  const double m0 = mom[0], m1 = mom[1], m2 = mom[2];
+  for (int a = a0 + threadIdx.x; a < a1; a += B) {
+    const double os = scaled ? g.sw[a] : 1.0;
+    const double wk = g.w[a] * g.kappa[a];
+    if (KIND == 0) {
+      double k;
+      if (pff) {
+        const float2* __restrict__ pf2 = reinterpret_cast<const float2*>(partial);
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        int s = 0;
+        for (; s + 2 <= S; s += 2) {
+          const float2 u = pf2[(long long)s * M + a], w2 = pf2[(long long)(s + 1) * M + a];
+          ffadd(h0, l0, u.x, u.y);
+          ffadd(h1, l1, w2.x, w2.y);
+        }
+        if (s < S) {
+          const float2 u = pf2[(long long)s * M + a];
+          ffadd(h0, l0, u.x, u.y);
+        }
+        ffadd(h0, l0, h1, l1);
+        k = (double)h0 + (double)l0;
+      } else {
+        k = 0.0;
+        for (int s = 0; s < S; ++s) k += partial[(long long)s * M + a];
+      }
+      out[a] = sign * (0.5 * v[a] + os * (m0 - kInv2Pi * k) - kInv4Pi * wk * v[a]);
+    } else {
+      double k1 = 0.0, k2 = 0.0;
+      if (pff) {
+        const float4* __restrict__ pf4 = reinterpret_cast<const float4*>(partial);
+        float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+        for (int s = 0; s < S; ++s) {
+          const float4 u = pf4[(long long)s * M + a];
+          ffadd(h1, l1, u.x, u.y);
+          ffadd(h2, l2, u.z, u.w);
+        }
+        k1 = (double)h1 + (double)l1;
+        k2 = (double)h2 + (double)l2;
+      } else {
+        for (int s = 0; s < S; ++s) {
+          const double2 p0 = reinterpret_cast<const double2*>(partial)[(long long)s * M + a];
+          k1 += p0.x;
+          k2 += p0.y;
+        }
+      }
       const double tx = -g.ny[a], ty = g.nx[a];
       const double v1 = v[2 * a], v2 = v[2 * a + 1];
       const double odd = -0.5 * kInvPi * wk * (tx * v1 + ty * v2);
@@ -1394,7 +1549,7 @@ cudaError_t pair_sum(const Geo& g, int kind, int precision, const PairPlan& p, V
 
 cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const double* partial,
                      int scaled, int with_L, double sign, VecRef out, const int* stop,
-                     cudaStream_t s, double alpha, bool pff) {
+                     cudaStream_t s, double alpha, bool pff, bool fp32) {
   if (p.S >= kRG) {
     // add the slots wide first (float-float or FP64), then an epilogue over one FP64 slot
     const long long n = (long long)g.M * (kind + 1);
@@ -1404,10 +1559,27 @@ cudaError_t epilogue(const Geo& g, int kind, const PairPlan& p, VecRef v, const 
     else
       k_reduce_slots64<<<nb, kRT * kRG, 0, s>>>(const_cast<double*>(partial), p.S, n, stop);
     note_launches(1);
-    return epilogue(g, kind, uniform_plan(1, g.M), v, partial, scaled, with_L, sign, out, stop, s, alpha, false);
+    return epilogue(g, kind, uniform_plan(1, g.M), v, partial, scaled, with_L, sign, out, stop, s, alpha, false,
+                    fp32);
   }
   // one block per body, sized to the bodies (many small bodies: small blocks)
   const int avg = g.M / std::max(1, g.N);
+  const int pf = pff ? 1 : 0;
+  if (fp32) {  // the FP32 operator: the epilogue in FP32 arithmetic
+    if (avg <= 64) {
+      if (kind == 0)
+        k_epilogue32<0, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pf);
+      else
+        k_epilogue32<1, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pf);
+    } else {
+      if (kind == 0)
+        k_epilogue32<0, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pf);
+      else
+        k_epilogue32<1, kBE><<<g.N, kBE, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pf);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+  }
   if (avg <= 64) {
     if (kind == 0)
       k_epilogue<0, 64><<<g.N, 64, 0, s>>>(g, v, partial, p.S, scaled, with_L, alpha, sign, out, stop, pff ? 1 : 0);
