@@ -412,33 +412,45 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
 // perturb the Arnoldi relation A P V = V H by O(eps32 ||w||), the size of the
 // FP32 operator's own error, and the second pass restores orthogonality to
 // O(eps32) (classical Gram-Schmidt twice).  The FP64 path above spends 4(j+1)
-// FP64 multiply-adds an element on GB300's narrow FP64 pipe; this one
-// 4(j+1) FP32 ones, and reads half the bytes.  The sums run in a fixed order
-// (deterministic); the grid sums, the Hessenberg column and the rotations
-// stay in FP64.  V_{j+1} (FP64, read by the solution update) receives the
-// FP32 basis vector exactly.
+// FP64 multiply-adds an element on GB300's narrow FP64 pipe (two lanes a
+// clock per SM); this one 4(j+1) FP32 ones, and reads half the bytes.
+// Threads own chunks of four consecutive elements (16-byte loads; VF rows
+// are 16-byte aligned and padded to ld, the padding of the chunk at the end
+// holds zeros).  The per-CTA partials and the grid sums are FP32 too (sums of
+// FP32 dot products, in a fixed order: deterministic); the Hessenberg column
+// and the rotations stay in FP64.  V_{j+1} (FP64, read by the solution
+// update) receives the FP32 basis vector exactly.
 
-// Partial dot products of this CTA's elements of x (FP32) with VF_0..VF_{jc-1}
-// into out[0..jc): eight basis vectors a pass, FP32 sums per thread, a fixed
-// shuffle tree per warp, the warps added in FP64 in order.
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
+}
+
+constexpr int kDot32 = 4;  // basis vectors a pass of the FP32 inner products
+
+// Partial dot products of this CTA's chunks of x with VF_0..VF_{jc-1} into
+// out[0..jc): kDot32 basis vectors a pass, FP32 sums per thread, a fixed
+// shuffle tree per warp, the warps added in order.
 __device__ __forceinline__ void arn_block_dots32(const float* __restrict__ VF, long long ld,
-                                                 const float* __restrict__ x, long long n, int jc,
-                                                 double* __restrict__ out, float (*sh)[kMaxBasis]) {
+                                                 const float* __restrict__ x, long long n4, int jc,
+                                                 float* __restrict__ out, float (*sh)[kMaxBasis]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * kBV;
-  for (int i = 0; i < jc; i += 8) {
-    const int cnt = min(8, jc - i);
-    float acc[8];
+  const long long ld4 = ld >> 2;
+  const float4* __restrict__ V4 = reinterpret_cast<const float4*>(VF);
+  const float4* __restrict__ x4 = reinterpret_cast<const float4*>(x);
+  for (int i = 0; i < jc; i += kDot32) {
+    const int cnt = min(kDot32, jc - i);
+    float acc[kDot32];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0.f;
-    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-      const float xk = x[k];
+    for (int u = 0; u < kDot32; ++u) acc[u] = 0.f;
+    for (long long c = blockIdx.x * (long long)kBV + threadIdx.x; c < n4; c += stride) {
+      const float4 xc = x4[c];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (u < cnt) acc[u] = fmaf(VF[(long long)(i + u) * ld + k], xk, acc[u]);
+      for (int u = 0; u < kDot32; ++u)
+        if (u < cnt) acc[u] = dot4(V4[(long long)(i + u) * ld4 + c], xc, acc[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kDot32; ++u) {
       if (u < cnt) {
         const float t = warp_sumf(acc[u]);
         if (lane == 0) sh[wid][i + u] = t;
@@ -447,31 +459,63 @@ __device__ __forceinline__ void arn_block_dots32(const float* __restrict__ VF, l
   }
   __syncthreads();
   for (int q = threadIdx.x; q < jc; q += kBV) {
-    double t = 0.0;
+    float t = 0.f;
 #pragma unroll
-    for (int u = 0; u < kBV / 32; ++u) t += (double)sh[u][q];
+    for (int u = 0; u < kBV / 32; ++u) t += sh[u][q];
     out[q] = t;
   }
 }
 
-// x[k] -= sum_i h[i] VF_i[k] over this CTA's elements (two FP32 chains, fixed
-// order); returns this thread's FP32 sum of the new x[k]^2 when NORM.
+// hs[i] = sum over CTAs b of part[b * kMaxBasis + i] (FP32 partials written
+// by other CTAs before a grid barrier; read through L2), i < jc: warp u takes
+// i = u, u + 8, ...; its lanes take b = lane, lane + 32, ... with four
+// independent sums (loads in flight), then a fixed shuffle tree.
+__device__ __forceinline__ void arn_grid_sum32(const float* part, int jc, double* hs) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = (int)gridDim.x;
+  for (int i = wid; i < jc; i += kBV / 32) {
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      t0 += __ldcg(part + (long long)b * kMaxBasis + i);
+      t1 += __ldcg(part + (long long)(b + 32) * kMaxBasis + i);
+      t2 += __ldcg(part + (long long)(b + 64) * kMaxBasis + i);
+      t3 += __ldcg(part + (long long)(b + 96) * kMaxBasis + i);
+    }
+    for (; b < G; b += 32) t0 += __ldcg(part + (long long)b * kMaxBasis + i);
+    const float t = warp_sumf((t0 + t1) + (t2 + t3));
+    if (lane == 0) hs[i] = (double)t;
+  }
+  __syncthreads();
+}
+
+// x -= VF h over this CTA's chunks (two FP32 chains, fixed order); returns
+// this thread's FP32 sum of the new x^2 when NORM.
 template <bool NORM>
 __device__ __forceinline__ float arn_project32(const float* __restrict__ VF, long long ld, float* __restrict__ x,
-                                               long long n, int jc, const float* h) {
+                                               long long n4, int jc, const float* h) {
   const long long stride = (long long)gridDim.x * kBV;
+  const long long ld4 = ld >> 2;
+  const float4* __restrict__ V4 = reinterpret_cast<const float4*>(VF);
+  float4* __restrict__ x4 = reinterpret_cast<float4*>(x);
   float nrm = 0.f;
-  for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-    float t0 = x[k], t1 = 0.f;
+  for (long long c = blockIdx.x * (long long)kBV + threadIdx.x; c < n4; c += stride) {
+    float4 t0 = x4[c], t1 = make_float4(0.f, 0.f, 0.f, 0.f);
     int i = 0;
     for (; i + 2 <= jc; i += 2) {
-      t0 = fmaf(-h[i], VF[(long long)i * ld + k], t0);
-      t1 = fmaf(-h[i + 1], VF[(long long)(i + 1) * ld + k], t1);
+      const float4 a = V4[(long long)i * ld4 + c], b = V4[(long long)(i + 1) * ld4 + c];
+      const float ha = -h[i], hb = -h[i + 1];
+      t0 = make_float4(fmaf(ha, a.x, t0.x), fmaf(ha, a.y, t0.y), fmaf(ha, a.z, t0.z), fmaf(ha, a.w, t0.w));
+      t1 = make_float4(fmaf(hb, b.x, t1.x), fmaf(hb, b.y, t1.y), fmaf(hb, b.z, t1.z), fmaf(hb, b.w, t1.w));
     }
-    if (i < jc) t0 = fmaf(-h[i], VF[(long long)i * ld + k], t0);
-    const float t = t0 + t1;
-    x[k] = t;
-    if (NORM) nrm = fmaf(t, t, nrm);
+    if (i < jc) {
+      const float4 a = V4[(long long)i * ld4 + c];
+      const float ha = -h[i];
+      t0 = make_float4(fmaf(ha, a.x, t0.x), fmaf(ha, a.y, t0.y), fmaf(ha, a.z, t0.z), fmaf(ha, a.w, t0.w));
+    }
+    const float4 t = make_float4(t0.x + t1.x, t0.y + t1.y, t0.z + t1.z, t0.w + t1.w);
+    x4[c] = t;
+    if (NORM) nrm = dot4(t, t, nrm);
   }
   return nrm;
 }
@@ -482,69 +526,101 @@ __global__ void __launch_bounds__(kBV, 4) k_arnoldi32(ArnoldiArgs a) {
   __shared__ float shf[kBV / 32][kMaxBasis];
   __shared__ double hs1[kMaxBasis], hs2[kMaxBasis];
   __shared__ float hf[kMaxBasis];
-  __shared__ double red[kBV / 32];
+  __shared__ float redf[kBV / 32];
   __shared__ float ws[kBjMaxBlock];
   __shared__ float4 red4[kBV];
   const int j = st->j, jc = j + 1;
-  const long long n = a.n, ld = a.ld;
+  const long long n = a.n, ld = a.ld, n4 = (n + 3) >> 2;
   float* __restrict__ VF = a.vf;
   double* __restrict__ w = a.V + (long long)(j + 1) * ld;  // A z_j (FP64, from the operator)
   float* __restrict__ wf = VF + (long long)(j + 1) * ld;    // w in FP32, then v_{j+1}
   const long long stride = (long long)gridDim.x * kBV;
   const long long G = gridDim.x;
-  double* part1 = a.part;
-  double* part2 = part1 + G * kMaxBasis;
-  double* part3 = part2 + G * kMaxBasis;
-  // VF_j = V_j in FP32 (exact for j > 0: V_j came from VF_j), w in FP32
+  // FP32 partials in the partial arrays: [G][kMaxBasis] floats each
+  float* part1 = reinterpret_cast<float*>(a.part);
+  float* part2 = part1 + G * kMaxBasis;
+  float* part3 = part2 + G * kMaxBasis;
+  // VF_j = V_j in FP32 (exact for j > 0: V_j came from VF_j), w in FP32; the
+  // padding after element n of the last chunk set to zero
   {
     const double* __restrict__ vj = a.V + (long long)j * ld;
-    float* __restrict__ vfj = VF + (long long)j * ld;
-    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-      vfj[k] = (float)vj[k];
-      wf[k] = (float)w[k];
+    float4* __restrict__ vfj4 = reinterpret_cast<float4*>(VF + (long long)j * ld);
+    float4* __restrict__ wf4 = reinterpret_cast<float4*>(wf);
+    for (long long c = blockIdx.x * (long long)kBV + threadIdx.x; c < n4; c += stride) {
+      const long long k = 4 * c;
+      float4 vv, ww;
+      if (k + 4 <= n) {
+        const double2 v0 = *reinterpret_cast<const double2*>(vj + k), v1 = *reinterpret_cast<const double2*>(vj + k + 2);
+        const double2 w0 = *reinterpret_cast<const double2*>(w + k), w1 = *reinterpret_cast<const double2*>(w + k + 2);
+        vv = make_float4((float)v0.x, (float)v0.y, (float)v1.x, (float)v1.y);
+        ww = make_float4((float)w0.x, (float)w0.y, (float)w1.x, (float)w1.y);
+      } else {
+        float vt[4], wt[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          vt[e] = k + e < n ? (float)vj[k + e] : 0.f;
+          wt[e] = k + e < n ? (float)w[k + e] : 0.f;
+        }
+        vv = make_float4(vt[0], vt[1], vt[2], vt[3]);
+        ww = make_float4(wt[0], wt[1], wt[2], wt[3]);
+      }
+      vfj4[c] = vv;
+      wf4[c] = ww;
     }
   }
   // h1 = VF^T w
-  arn_block_dots32(VF, ld, wf, n, jc, part1 + blockIdx.x * kMaxBasis, shf);
+  arn_block_dots32(VF, ld, wf, n4, jc, part1 + blockIdx.x * kMaxBasis, shf);
   if ((int)blockIdx.x == a.fault_skip) return;  // test hook: this CTA never arrives
   if (grid_barrier(st, a.spins)) return;
-  arn_grid_sum(part1, jc, hs1);
+  arn_grid_sum32(part1, jc, hs1);
   for (int i = threadIdx.x; i < jc; i += kBV) hf[i] = (float)hs1[i];
   __syncthreads();
   // w -= VF h1; h2 = VF^T w
-  arn_project32<false>(VF, ld, wf, n, jc, hf);
+  arn_project32<false>(VF, ld, wf, n4, jc, hf);
   __syncthreads();  // hf and shf are reused below
-  arn_block_dots32(VF, ld, wf, n, jc, part2 + blockIdx.x * kMaxBasis, shf);
+  arn_block_dots32(VF, ld, wf, n4, jc, part2 + blockIdx.x * kMaxBasis, shf);
   if (grid_barrier(st, a.spins)) return;
-  arn_grid_sum(part2, jc, hs2);
+  arn_grid_sum32(part2, jc, hs2);
   for (int i = threadIdx.x; i < jc; i += kBV) hf[i] = (float)hs2[i];
   __syncthreads();
   // w -= VF h2; ||w||^2
-  double nrm = (double)arn_project32<true>(VF, ld, wf, n, jc, hf);
-  nrm = block_sum<kBV>(nrm, red);
-  if (threadIdx.x == 0) part3[blockIdx.x * kMaxBasis] = nrm;
-  if (grid_barrier(st, a.spins)) return;
-  __shared__ double hn_s;
-  if (threadIdx.x < 32) {
-    const double t = warp_gather(part3, kMaxBasis);
-    if (threadIdx.x == 0) hn_s = sqrt(t);
-  }
+  float nrm = arn_project32<true>(VF, ld, wf, n4, jc, hf);
+  nrm = warp_sumf(nrm);
+  if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = nrm;
   __syncthreads();
-  const double hn = hn_s;
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int u = 0; u < kBV / 32; ++u) t += redf[u];
+    part3[blockIdx.x * kMaxBasis] = t;
+  }
+  if (grid_barrier(st, a.spins)) return;
+  __shared__ double hn2[1];
+  arn_grid_sum32(part3, 1, hn2);
+  const double hn = sqrt(hn2[0]);
   if (blockIdx.x == 0) arn_hessenberg(a, st, j, hs1, hs2, hn);
   const float inv = hn > 0.0 ? (float)(1.0 / hn) : 0.f;
   if (!a.blocks) {
     // v_{j+1} = w / ||w|| over this CTA's own elements
-    for (long long k = blockIdx.x * (long long)kBV + threadIdx.x; k < n; k += stride) {
-      const float v = wf[k] * inv;
-      wf[k] = v;
-      w[k] = (double)v;
+    for (long long c = blockIdx.x * (long long)kBV + threadIdx.x; c < n4; c += stride) {
+      for (int e = 0; e < 4; ++e) {
+        const long long k = 4 * c + e;
+        if (k < n) {
+          const float v = wf[k] * inv;
+          wf[k] = v;
+          w[k] = (double)v;
+        }
+      }
     }
     return;
   }
-  // per body: v = w inv (w read through L2: other CTAs wrote it), z = P v
+  // per body: v = w inv (w read through L2: other CTAs wrote it), z = P v.
+  // CTA 0 computes the Hessenberg column and rotations above, so the bodies
+  // go to CTAs 1..G-1 (with one CTA, to CTA 0).
   const int c = a.kind + 1;
-  for (int i = blockIdx.x; i < a.g.N; i += (int)G) {
+  const int first = G > 1 ? (int)blockIdx.x - 1 : 0, nworkers = G > 1 ? (int)G - 1 : 1;
+  if (first < 0) return;
+  for (int i = first; i < a.g.N; i += nworkers) {
     const long long a0 = (long long)a.g.body_start[i] * c;
     const int nb = (a.g.body_start[i + 1] - a.g.body_start[i]) * c;
     const bool apply = nb <= kBjMaxBlock;
