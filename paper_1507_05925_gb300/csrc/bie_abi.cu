@@ -176,7 +176,7 @@ struct Work {
   // block-Jacobi preconditioner of the inner solves
   long long* bj_off = nullptr;
   int* bj_pairs = nullptr;
-  float* bj_blocks = nullptr;
+  bj_t* bj_blocks = nullptr;
   int* bj_fallbacks = nullptr;  // device counter of bodies left with the identity block
   double* zbuf = nullptr;
   double* arn = nullptr;  // per-CTA partials of the fused Arnoldi step
@@ -317,7 +317,7 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
     if (bj_floats > 0) {
       w.bj_off = A.take<long long>(N + 1);
       w.bj_pairs = A.take<int>(N);
-      w.bj_blocks = A.take<float>((size_t)bj_floats);
+      w.bj_blocks = A.take<bj_t>((size_t)bj_floats);
       w.bj_fallbacks = A.take<int>(1);
       w.zbuf = A.take<double>(n);
     }

@@ -11,6 +11,7 @@
 //              vectors node-interleaved (2a + c).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -273,13 +274,18 @@ constexpr int kBjMaxBlock = 640;
 // block whose inversion meets a pivot that is not finite or below the floor
 // (|p| < floor; the blocks are 1/2 I + compact) keeps the identity, and
 // *fallbacks (device int, cleared here) counts those bodies.
+// Storage: per body W = B^{-1} - 2I (B^{-1} = 2I + O(compact)) in FP16,
+// column-major; P v = 2 v + W v.  An inverse with an entry of W outside
+// FP16's range also keeps the identity (W = -I).
+using bj_t = __half;
+constexpr float kBjShift = 2.0f;
 long long bj_block_floats(const int* body_start_host, int N, int kind);
 cudaError_t bj_setup(const Geo& g, int kind, double alpha, const int* body_start_host, long long* off_dev,
-                     int* pair_dev, float* blocks, int* fallbacks, cudaStream_t s);
+                     int* pair_dev, bj_t* blocks, int* fallbacks, cudaStream_t s);
 // Test hook: the pivot floor of later factorisations (<= 0: the default).
 void set_bj_pivot_floor(double floor);
-// z = P v (v scaled, z scaled); f64: in FP64 arithmetic on the FP32 blocks
-cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const float* blocks, VecRef v, double* z,
+// z = P v (v scaled, z scaled); f64: in FP64 arithmetic on the FP16 blocks
+cudaError_t bj_apply(const Geo& g, int kind, const long long* off_dev, const bj_t* blocks, VecRef v, double* z,
                      const int* stop, int max_nb, cudaStream_t s, bool f64 = false);
 
 // ---------------------------------------------------------------- small.cu
@@ -320,7 +326,7 @@ struct ArnoldiArgs {
   Geo g;
   int kind;
   const long long* off;
-  const float* blocks;
+  const bj_t* blocks;
   double* z;
   int bj64 = 0;            // apply the FP32 blocks in FP64 arithmetic (FP64 GMRES)
   float* vf = nullptr;     // FP32 copy of the basis ((m + 1) x ld): CGS2 in FP32 (FP32 inner solves, wide grids)

@@ -194,49 +194,58 @@ __device__ __forceinline__ bool grid_barrier(KState* st, long long spins) {
   return failed != 0;
 }
 
-// z = B v for one body's block-Jacobi block B (column-major nb x nb, FP32;
-// off = its offset in the block array) and v = ws in shared memory.
-__device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long long off, int nb, const float* ws,
-                              double* __restrict__ z, float4* red4) {
-  if ((nb & 3) == 0 && (off & 3) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
-    // 16-byte loads of four consecutive rows: R row-quad slots (the smallest
-    // power of two >= nb/4, from 8 to 64) x kBV/R column groups, so that
-    // every thread streams part of the block (a body of 64 Stokes nodes: 32
-    // row quads x 8 groups of 16 columns, 16 loads in flight a thread)
-    const int nq = nb >> 2;
+// z = P v = 2 v + W v for one body's block-Jacobi block W (column-major
+// nb x nb, FP16; off = its offset in the block array) and v = ws in shared
+// memory, in FP32 arithmetic.  red8 holds 2 kBV float4.
+__device__ __forceinline__ void bj_body_apply(const bj_t* __restrict__ B, long long off, int nb, const float* ws,
+                                              double* __restrict__ z, float4* red8) {
+  if ((nb & 7) == 0 && (off & 7) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+    // 16-byte loads of eight consecutive rows: R row-octet slots (the
+    // smallest power of two >= nb/8, from 8 to 64) x kBV/R column groups, so
+    // that every thread streams part of the block (a body of 64 Stokes
+    // nodes: 16 row octets x 16 groups of 8 columns, 8 loads in flight a
+    // thread)
+    const int no = nb >> 3;
     int R = 64;
-    while (R > 8 && (R >> 1) >= nq) R >>= 1;
+    while (R > 8 && (R >> 1) >= no) R >>= 1;
     const int ng = kBV / R, qd = threadIdx.x & (R - 1), grp = threadIdx.x / R;
     const int per = (nb + ng - 1) / ng, cb = grp * per, ce = min(nb, cb + per);
-    for (int q0 = 0; q0 < nq; q0 += R) {
+    for (int q0 = 0; q0 < no; q0 += R) {
       const int q = q0 + qd;
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (q < nq) {
-        const float4* __restrict__ Bq = reinterpret_cast<const float4*>(B) + q;
-#pragma unroll 16
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+      if (q < no) {
+        const uint4* __restrict__ Bq = reinterpret_cast<const uint4*>(B) + q;
+#pragma unroll 4
         for (int col = cb; col < ce; ++col) {
-          const float4 b = Bq[(long long)col * nq];
+          const uint4 b = Bq[(long long)col * no];
           const float x = ws[col];
-          acc.x = fmaf(b.x, x, acc.x);
-          acc.y = fmaf(b.y, x, acc.y);
-          acc.z = fmaf(b.z, x, acc.z);
-          acc.w = fmaf(b.w, x, acc.w);
+          const __half2* h = reinterpret_cast<const __half2*>(&b);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 f = __half22float2(h[u]);
+            acc[2 * u] = fmaf(f.x, x, acc[2 * u]);
+            acc[2 * u + 1] = fmaf(f.y, x, acc[2 * u + 1]);
+          }
         }
       }
-      red4[threadIdx.x] = acc;
+      red8[2 * threadIdx.x] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      red8[2 * threadIdx.x + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
       __syncthreads();
-      if (grp == 0 && q < nq) {
-        float4 t = red4[qd];
+      if (grp == 0 && q < no) {
+        float4 t0 = red8[2 * qd], t1 = red8[2 * qd + 1];
         for (int u = 1; u < ng; ++u) {
-          const float4 o = red4[u * R + qd];
-          t.x += o.x;
-          t.y += o.y;
-          t.z += o.z;
-          t.w += o.w;
+          const float4 o0 = red8[2 * (u * R + qd)], o1 = red8[2 * (u * R + qd) + 1];
+          t0 = make_float4(t0.x + o0.x, t0.y + o0.y, t0.z + o0.z, t0.w + o0.w);
+          t1 = make_float4(t1.x + o1.x, t1.y + o1.y, t1.z + o1.z, t1.w + o1.w);
         }
-        double2* zr = reinterpret_cast<double2*>(z + 4 * q);
-        zr[0] = make_double2(t.x, t.y);
-        zr[1] = make_double2(t.z, t.w);
+        const float* v8 = ws + 8 * q;
+        double2* zr = reinterpret_cast<double2*>(z + 8 * q);
+        zr[0] = make_double2(fmaf(kBjShift, v8[0], t0.x), fmaf(kBjShift, v8[1], t0.y));
+        zr[1] = make_double2(fmaf(kBjShift, v8[2], t0.z), fmaf(kBjShift, v8[3], t0.w));
+        zr[2] = make_double2(fmaf(kBjShift, v8[4], t1.x), fmaf(kBjShift, v8[5], t1.y));
+        zr[3] = make_double2(fmaf(kBjShift, v8[6], t1.z), fmaf(kBjShift, v8[7], t1.w));
       }
       __syncthreads();
     }
@@ -246,31 +255,31 @@ __device__ __forceinline__ void bj_body_apply(const float* __restrict__ B, long 
       int col = 0;
 #pragma unroll 4
       for (; col + 2 <= nb; col += 2) {
-        s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
-        s1 = fmaf(B[(long long)(col + 1) * nb + r], ws[col + 1], s1);
+        s0 = fmaf(__half2float(B[(long long)col * nb + r]), ws[col], s0);
+        s1 = fmaf(__half2float(B[(long long)(col + 1) * nb + r]), ws[col + 1], s1);
       }
-      if (col < nb) s0 = fmaf(B[(long long)col * nb + r], ws[col], s0);
-      z[r] = (double)(s0 + s1);
+      if (col < nb) s0 = fmaf(__half2float(B[(long long)col * nb + r]), ws[col], s0);
+      z[r] = (double)fmaf(kBjShift, ws[r], s0 + s1);
     }
   }
 }
 
-// z = B v in FP64 arithmetic on the FP32 block (the FP64 GMRES: the
+// z = P v in FP64 arithmetic on the FP16 block (the FP64 GMRES: the
 // preconditioner must be one fixed linear map to FP64 rounding, so that the
 // Arnoldi relation A P V = V H holds to FP64 accuracy and x = P (V y) is the
 // minimiser GMRES computed).
-__device__ __forceinline__ void bj_body_apply64(const float* __restrict__ B, int nb, const double* wd,
+__device__ __forceinline__ void bj_body_apply64(const bj_t* __restrict__ B, int nb, const double* wd,
                                                 double* __restrict__ z) {
   for (int r = threadIdx.x; r < nb; r += kBV) {
     double s0 = 0.0, s1 = 0.0;
     int col = 0;
 #pragma unroll 4
     for (; col + 2 <= nb; col += 2) {
-      s0 = fma((double)B[(long long)col * nb + r], wd[col], s0);
-      s1 = fma((double)B[(long long)(col + 1) * nb + r], wd[col + 1], s1);
+      s0 = fma((double)__half2float(B[(long long)col * nb + r]), wd[col], s0);
+      s1 = fma((double)__half2float(B[(long long)(col + 1) * nb + r]), wd[col + 1], s1);
     }
-    if (col < nb) s0 = fma((double)B[(long long)col * nb + r], wd[col], s0);
-    z[r] = s0 + s1;
+    if (col < nb) s0 = fma((double)__half2float(B[(long long)col * nb + r]), wd[col], s0);
+    z[r] = fma((double)kBjShift, wd[r], s0 + s1);
   }
 }
 
@@ -373,7 +382,7 @@ __global__ void __launch_bounds__(kBV, NARROW ? 1 : 4) k_arnoldi(ArnoldiArgs a) 
     return;
   }
   // per body: v = w inv (w read through L2: other CTAs wrote it), z = P v
-  __shared__ float4 red4[kBV];
+  __shared__ float4 red4[2 * kBV];
   const int c = a.kind + 1;
   for (int i = blockIdx.x; i < a.g.N; i += (int)G) {
     const long long a0 = (long long)a.g.body_start[i] * c;
@@ -528,7 +537,7 @@ __global__ void __launch_bounds__(kBV, 4) k_arnoldi32(ArnoldiArgs a) {
   __shared__ float hf[kMaxBasis];
   __shared__ float redf[kBV / 32];
   __shared__ float ws[kBjMaxBlock];
-  __shared__ float4 red4[kBV];
+  __shared__ float4 red4[2 * kBV];
   const int j = st->j, jc = j + 1;
   const long long n = a.n, ld = a.ld, n4 = (n + 3) >> 2;
   float* __restrict__ VF = a.vf;
@@ -704,7 +713,7 @@ __global__ void __launch_bounds__(kBV) k_arnoldi_seg(ArnoldiArgs a, SegArgs sg) 
   __shared__ double cell;
   __shared__ float ws[kBjMaxBlock];
   __shared__ double wsd[kBjMaxBlock];
-  __shared__ float4 red4[kBV];
+  __shared__ float4 red4[2 * kBV];
   const int j = st->j, jc = j + 1;
   const long long ld = a.ld;
   double* __restrict__ w = a.V + (long long)(j + 1) * ld;
