@@ -237,6 +237,27 @@ __global__ void k_fmm_density(Geo g, int nd, double cx0, double cy0, VecRef vr, 
   }
 }
 
+// The P2M terms of one chunk of m sources: output e = d p + k (channel d,
+// coefficient k) is owned by thread e mod kB, which adds its terms in source
+// order (fixed: deterministic).  All p nd outputs run in parallel (p = 18,
+// nd = 3: 54 of 64 threads), each a chain of m complex multiply-adds.
+constexpr int kP2MAcc = (kMaxNd * kMaxP + kB - 1) / kB;  // outputs a thread keeps
+template <class T2>
+__device__ __forceinline__ void p2m_chunk(T2* acc, const T2* pw, const T2* qs, int p, int nd, int m) {
+  const int np = p * nd;
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u) {
+    const int e = threadIdx.x + u * kB;
+    if (e < np) {
+      const int d = e / p, k = e - d * p;
+      const T2* pk = pw + k * (kChunk + 1);
+      T2 a = acc[u];
+      for (int j = 0; j < m; ++j) cfma(a, pk[j], qs[j * nd + d]);
+      acc[u] = a;
+    }
+  }
+}
+
 // The FP32 operator's strengths: q = sqrt(w) v per source in FP32 (Laplace:
 // (q, 0); Stokes: the complex density).  The other channels (conj(q) and the
 // leaf-relative moment density) are formed where they are used, so the FP32
@@ -286,8 +307,9 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m32(FmmDevT<float2> f, Geo g, cons
   leaf_center32(f, b, cen);
   __syncthreads();
   const int t = threadIdx.x;
-  float2 acc[kMaxNd];
-  for (int d = 0; d < kMaxNd; ++d) acc[d] = make_float2(0.f, 0.f);
+  float2 acc[kP2MAcc];
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u) acc[u] = make_float2(0.f, 0.f);
   for (int ch = 0; ch < n; ch += kChunk) {
     const int m = min(kChunk, n - ch);
     if (t < m) {
@@ -308,13 +330,12 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m32(FmmDevT<float2> f, Geo g, cons
       }
     }
     __syncthreads();
-    if (t < f.p)
-      for (int j = 0; j < m; ++j)
-        for (int d = 0; d < f.nd; ++d) cfma(acc[d], pw[t * (kChunk + 1) + j], qs[j * f.nd + d]);
+    p2m_chunk(acc, pw, qs, f.p, f.nd, m);
     __syncthreads();
   }
-  if (t < f.p)
-    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u)
+    if (t + u * kB < f.nd * f.p) f.mp[box * f.nd * f.p + t + u * kB] = acc[u];
 }
 
 // P2M on the leaves: a_k = sum_j q_j u_j^k, u = (z - c)/s.
@@ -332,8 +353,9 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int*
   double s;
   const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
   const int t = threadIdx.x;
-  T2 acc[kMaxNd];
-  for (int d = 0; d < kMaxNd; ++d) acc[d] = cx<T2>(0.0, 0.0);
+  T2 acc[kP2MAcc];
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u) acc[u] = cx<T2>(0.0, 0.0);
   for (int ch = 0; ch < n; ch += kChunk) {
     const int m = min(kChunk, n - ch);
     if (t < kChunk) {
@@ -356,13 +378,12 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m(FmmDevT<T2> f, Geo g, const int*
       }
     }
     __syncthreads();
-    if (t < f.p)
-      for (int j = 0; j < m; ++j)
-        for (int d = 0; d < f.nd; ++d) cfma(acc[d], pw[t * (kChunk + 1) + j], qs[j * f.nd + d]);
+    p2m_chunk(acc, pw, qs, f.p, f.nd, m);
     __syncthreads();
   }
-  if (t < f.p)
-    for (int d = 0; d < f.nd; ++d) f.mp[(box * f.nd + d) * f.p + t] = acc[d];
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u)
+    if (t + u * kB < f.nd * f.p) f.mp[box * f.nd * f.p + t + u * kB] = acc[u];
 }
 
 // M2M into level l (parents) from level l + 1.  Per child, its multipoles and
