@@ -105,6 +105,8 @@ struct FmmDevT {
   T2* lc;
   const T2* ops;
   const float2* Qf = nullptr;  // FP32 expansions: q per source in FP32 (channel 0), from k_fmm_density32
+  const float4* cen32 = nullptr;  // FP32 expansions: leaf centres split hi + lo
+  float is32 = 0.f, s32 = 0.f;    // FP32 expansions: 1/s and s of a leaf
 };
 using FmmDev = FmmDevT<double2>;
 
@@ -274,21 +276,28 @@ __global__ void k_fmm_density32(Geo g, int nd, VecRef vr, const double* __restri
   }
 }
 
-// Leaf centre c of block b split as float hi + lo, and 1/s in FP32: computed
-// once per block (FP64 arithmetic on one thread) for the FP32 passes, which
-// then form u = (z - c)/s from the hi/lo split of z in FP32 (z_hi - c_hi is
-// exact for a node inside the leaf unless |z| is of the order of s).
+// Leaf centres split as float hi + lo, once per tree (FP64 arithmetic here,
+// so that the FP32 passes form u = (z - c)/s from the hi/lo split of z in
+// FP32 with no FP64 instruction: z_hi - c_hi is exact for a node inside the
+// leaf unless |z| is of the order of s).
+__global__ void k_fmm_leaf_centers(int nb, double x0, double y0, double s, float4* cen) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb * nb; b += gridDim.x * blockDim.x) {
+    const double cx = x0 + (b % nb + 0.5) * s, cy = y0 + (b / nb + 0.5) * s;
+    const float hx = (float)cx, hy = (float)cy;
+    cen[b] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
+  }
+}
+
+// The block's leaf centre split (x_h, y_h, x_l, y_l), 1/s and s in shared memory.
 __device__ __forceinline__ void leaf_center32(const FmmDevT<float2>& f, int b, float* cen) {
   if (threadIdx.x == 0) {
-    double s;
-    const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
-    const float hx = (float)c.x, hy = (float)c.y;
-    cen[0] = hx;
-    cen[1] = hy;
-    cen[2] = (float)(c.x - (double)hx);
-    cen[3] = (float)(c.y - (double)hy);
-    cen[4] = (float)ldexp(f.Dinv, f.L);
-    cen[5] = (float)s;
+    const float4 c = f.cen32[b];
+    cen[0] = c.x;
+    cen[1] = c.y;
+    cen[2] = c.z;
+    cen[3] = c.w;
+    cen[4] = f.is32;
+    cen[5] = f.s32;
   }
 }
 
@@ -1413,6 +1422,7 @@ struct FmmState {
   int *tcount = nullptr, *tleaf = nullptr;
   double *tx = nullptr, *ty = nullptr;
   double2 *Q = nullptr, *mp = nullptr, *lc = nullptr;
+  float4* cen32 = nullptr;  // per leaf: centre split as float hi + lo (x_h, y_h, x_l, y_l)
   double* scal = nullptr;
   int pmax = 0;
   // operators per order (FP64, and their FP32 copies)
@@ -1485,7 +1495,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   auto pad = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t need = 3 * pad((size_t)g.M * 4) + 2 * pad(((size_t)f->nleaf + 1) * 4) + 2 * pad((size_t)f->nbox * 4) +
                       pad((size_t)g.M * nd * 16) + 3 * pad((size_t)f->nbox * nd * pmax * 16) +
-                      pad((size_t)3 * g.N * 4) + 2 * pad((size_t)3 * g.N * 8);
+                      pad((size_t)3 * g.N * 4) + 2 * pad((size_t)3 * g.N * 8) + pad((size_t)f->nleaf * 16);
   if (need > f->buf_size) {
     if (f->buf) cudaFreeAsync(f->buf, s);
     f->buf = nullptr;
@@ -1513,6 +1523,7 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   f->mp = (double2*)take((size_t)f->nbox * nd * pmax * 16);
   f->lc = (double2*)take((size_t)f->nbox * nd * pmax * 16);
   f->mpff = (float4*)take((size_t)f->nbox * nd * pmax * 16);
+  f->cen32 = (float4*)take((size_t)f->nleaf * 16);
   // counting sort of the nodes by leaf, node order inside a leaf
   if (!ck(cudaMemsetAsync(f->cursor, 0, ((size_t)f->nleaf + 1) * 4, s), "fmm memset")) return BIE_ERR_CUDA;
   k_fmm_leaf<<<grid_for(g.M), 256, 0, s>>>(g, L, f->x0, f->y0, f->D, f->leaf, f->cursor);
@@ -1522,7 +1533,8 @@ int fmm_setup(FmmState*& f, const Geo& g, int kind, const int* orders, int norde
   k_fmm_order<<<f->nleaf, 128, 0, s>>>(f->start, f->tmp, f->perm);
   k_fmm_leaf_counts<<<grid_for(f->nleaf), 256, 0, s>>>(f->start, f->nleaf, f->count + lev_off(L));
   for (int l = L - 1; l >= 0; --l) k_fmm_parent_counts<<<grid_for(1LL << (2 * l)), 256, 0, s>>>(l, f->count);
-  note_launches(6 + L);
+  k_fmm_leaf_centers<<<grid_for(f->nleaf), 256, 0, s>>>(f->nb, f->x0, f->y0, ldexp(f->D, -L), f->cen32);
+  note_launches(7 + L);
   if (!ck(cudaGetLastError(), "fmm setup")) return BIE_ERR_CUDA;
   // translation operators, built before any capture of the apply
   for (int k = 0; k < norders; ++k) {
@@ -1689,6 +1701,9 @@ cudaError_t fmm_pair_sum(FmmState* f, const Geo& g, int kind, int p, VecRef v, c
                       f->count, f->count,  f->Q,     reinterpret_cast<float2*>(f->mp),
                       reinterpret_cast<float2*>(f->lc), ops32};
     d.Qf = Qf;
+    d.cen32 = f->cen32;
+    d.is32 = (float)ldexp(1.0 / f->D, f->L);
+    d.s32 = (float)ldexp(f->D, -f->L);
     fmm_passes<float2, 1>(d, f, g, partial, stop, s);
   } else {
     k_fmm_density<<<grid_for(g.M), 256, 0, s>>>(g, nd, f->x0 + 0.5 * f->D, f->y0 + 0.5 * f->D, v, sscale, f->Q,
