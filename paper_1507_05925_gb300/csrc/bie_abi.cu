@@ -292,7 +292,9 @@ void carve(Arena& A, Work& w, int N, int M, int kind, int m, bool solve, bool st
   w.partial = A.take<double>((size_t)S * n);
   w.grid = vec_grid(n);
   w.part = A.take<double>((size_t)w.grid * 201 + 64);
-  w.arn = A.take<double>((size_t)3 * std::max<long long>(w.grid, arn_units) * 201 + 64);
+  // per-CTA partials of the Arnoldi step: its grid is at most max(vec_grid, N + 1) CTAs
+  const long long arn_grid = std::max<long long>(w.grid, std::min<long long>((long long)N + 1, kMaxVecGrid));
+  w.arn = A.take<double>((size_t)3 * std::max<long long>(arn_grid, arn_units) * 201 + 64);
   w.st = A.take<KState>(1);
   if (solve) {
     w.V = A.take<double>((size_t)(m + 1) * w.ld);
@@ -722,9 +724,9 @@ int launch_iteration(bie_ctx* ctx, Work& w, const Op& op, cudaStream_t s) {
   if (w.seg.P > 1) {
     CK(arnoldi_seg(a, w.seg, w.seg_grid, s));
   } else {
-    // the FP32 inner solves on wide grids: CGS2 in FP32 against the FP32 basis
-    if (op.prec == 1 && w.VF && !arnoldi_narrow(n)) a.vf = w.VF;
-    CK(arnoldi(a, arnoldi_grid(n, a.vf != nullptr), s));
+    // the FP32 inner solves: CGS2 in FP32 against the FP32 basis
+    if (op.prec == 1 && w.VF) a.vf = w.VF;
+    CK(arnoldi(a, arnoldi_grid(n, a.vf != nullptr, w.g.N), s));
   }
   return BIE_OK;
 }

@@ -338,7 +338,7 @@ struct ArnoldiArgs {
 void arm_barrier_fault(int skip_cta, long long spins);
 bool barrier_fault_armed();
 // co-resident CTAs for the cooperative launch (fp32: the FP32 step of wide grids)
-int arnoldi_grid(long long n, bool fp32 = false);
+int arnoldi_grid(long long n, bool fp32 = false, int nbodies = 0);
 bool arnoldi_narrow(long long n);
 cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s);
 // h[i] = <V_i, w> for i <= j (first CGS pass)

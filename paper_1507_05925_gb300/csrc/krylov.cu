@@ -1049,13 +1049,13 @@ int vec_grid(long long n) {
 // The narrow instance for grids of at most two CTAs per SM.
 bool arnoldi_narrow(long long n) { return vec_grid(n) <= 2 * device_sms(); }
 
-int arnoldi_grid(long long n, bool fp32) {
+int arnoldi_grid(long long n, bool fp32, int nbodies) {
   static std::atomic<int> coresident[64][3];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   const int narrow = arnoldi_narrow(n) ? 1 : 0;
-  const int v = narrow ? 1 : (fp32 ? 2 : 0);
+  const int v = fp32 ? 2 : (narrow ? 1 : 0);
   if (coresident[dev][v].load() == 0) {
     int per_sm = 0, sms = 0;
     const void* fn = v == 1 ? (const void*)k_arnoldi<true> : (v == 2 ? (const void*)k_arnoldi32 : (const void*)k_arnoldi<false>);
@@ -1066,7 +1066,10 @@ int arnoldi_grid(long long n, bool fp32) {
     }
     coresident[dev][v].store(per_sm * sms);
   }
-  return std::min(vec_grid(n), coresident[dev][v].load());
+  // the FP32 step gives CTA 0 the rotations and CTAs 1.. the bodies: at least
+  // one CTA a body where the grid allows
+  const int want = fp32 ? std::max(vec_grid(n), std::min(nbodies + 1, kMaxVecGrid)) : vec_grid(n);
+  return std::min(want, coresident[dev][v].load());
 }
 
 namespace {
@@ -1098,8 +1101,8 @@ cudaError_t arnoldi(const ArnoldiArgs& a, int grid, cudaStream_t s) {
   ArnoldiArgs args = a;
   take_fault(args);
   void* params[] = {&args};
-  const void* fn = arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true>
-                   : (a.vf ? (const void*)k_arnoldi32 : (const void*)k_arnoldi<false>);
+  const void* fn = a.vf ? (const void*)k_arnoldi32
+                        : (arnoldi_narrow(a.n) ? (const void*)k_arnoldi<true> : (const void*)k_arnoldi<false>);
   const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBV), params, 0, s);
   note_launches(1);
   return e;
