@@ -714,6 +714,66 @@ __device__ __forceinline__ cff cff_scale(cff a, float sh, float sl) {
   return r;
 }
 
+__device__ __forceinline__ float4 cff_store(cff a) { return make_float4(a.h.x, a.h.y, a.l.x, a.l.y); }
+
+// P2M of the float-float residual's FMM (FP64 expansions): the powers of u
+// and the sums in float-float on the FP32 pipe (about 48 bits, what the
+// float-float residual certifies; GB300 runs FP64 multiply-adds at two lanes
+// a clock per SM).  Layout and term order as k_fmm_p2m: output e = d p + k
+// on thread e mod kB, sources in order.
+__global__ void __launch_bounds__(kB) k_fmm_p2m_ff(FmmDevT<double2> f, Geo g, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* pw = reinterpret_cast<float4*>(smraw);  // [p][kChunk + 1] u^k as (re_h, im_h, re_l, im_l)
+  float4* qs = pw + f.p * (kChunk + 1);            // [kChunk][nd]
+  const int b = blockIdx.x;
+  const long long box = lev_off(f.L) + b;
+  const int s0 = f.start[b], n = f.start[b + 1] - s0;
+  if (n == 0) return;
+  const int t = threadIdx.x, np = f.p * f.nd;
+  cff acc[kP2MAcc];
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u) acc[u] = cff_zero();
+  for (int ch = 0; ch < n; ch += kChunk) {
+    const int m = min(kChunk, n - ch);
+    if (t < m) {
+      double s;
+      const double2 c = box_center(f, f.L, b % f.nb, b / f.nb, s);
+      const int i = f.perm[s0 + ch + t];
+      const double is = ldexp(f.Dinv, f.L);
+      const cff U = cff_split((g.x[i] - c.x) * is, (g.y[i] - c.y) * is);
+      cff w = cff_split(1.0, 0.0);
+      for (int k = 0; k < f.p; ++k) {
+        pw[k * (kChunk + 1) + t] = cff_store(w);
+        w = cff_fma(cff_zero(), w, U);
+      }
+      const double2 q = f.Q[(long long)i * f.nd];
+      const cff Qc = cff_split(q.x, q.y);
+      qs[t * f.nd] = cff_store(Qc);
+      if (f.nd == 3) {
+        qs[t * 3 + 1] = cff_store(cff_conj(Qc));                         // conj(q)
+        qs[t * 3 + 2] = cff_store(cff_fma(cff_zero(), Qc, cff_conj(U)));  // channel cm: q conj(u)
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kP2MAcc; ++u) {
+      const int e = t + u * kB;
+      if (e < np) {
+        const int d = e / f.p, k = e - d * f.p;
+        const float4* pk = pw + k * (kChunk + 1);
+        cff a = acc[u];
+        for (int j = 0; j < m; ++j) a = cff_fma(a, cff_load(pk[j]), cff_load(qs[j * f.nd + d]));
+        acc[u] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kP2MAcc; ++u)
+    if (t + u * kB < np) f.mp[box * np + t + u * kB] = cff_to(acc[u]);
+}
+
 // Tables of order p: alpha[2][49][p], beta[2][49][p], gamma[49][p] (float4;
 // type 0 Cauchy, 1 logarithm, as tab_alpha..tab_gamma), then the Pascal
 // matrices [2][k][l] (float2 hi, lo).
@@ -1628,6 +1688,8 @@ void fmm_passes(const FmmDevT<T2>& d, FmmState* f, const Geo& g, double* partial
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(T2);
   if constexpr (std::is_same<T2, float2>::value)
     k_fmm_p2m32<<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
+  else if constexpr (NEARP == 2)
+    k_fmm_p2m_ff<<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);  // float4 = double2 in size
   else
     k_fmm_p2m<T2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, stop);
   const size_t sm_tree = tree_smem<T2>(nd, p);
