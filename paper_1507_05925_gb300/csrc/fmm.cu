@@ -716,8 +716,9 @@ __device__ __forceinline__ cff cff_scale(cff a, float sh, float sl) {
 
 __device__ __forceinline__ float4 cff_store(cff a) { return make_float4(a.h.x, a.h.y, a.l.x, a.l.y); }
 
-// P2M of the float-float residual's FMM (FP64 expansions): the powers of u
-// and the sums in float-float on the FP32 pipe (about 48 bits, what the
+// P2M of the float-float residual's FMM and of the float-float solves'
+// output FMM (FP64 expansions): the powers of u and the sums in float-float
+// on the FP32 pipe (about 48 bits, what the
 // float-float residual certifies; GB300 runs FP64 multiply-adds at two lanes
 // a clock per SM).  Layout and term order as k_fmm_p2m: output e = d p + k
 // on thread e mod kB, sources in order.
@@ -747,12 +748,11 @@ __global__ void __launch_bounds__(kB) k_fmm_p2m_ff(FmmDevT<double2> f, Geo g, co
         pw[k * (kChunk + 1) + t] = cff_store(w);
         w = cff_fma(cff_zero(), w, U);
       }
-      const double2 q = f.Q[(long long)i * f.nd];
-      const cff Qc = cff_split(q.x, q.y);
-      qs[t * f.nd] = cff_store(Qc);
-      if (f.nd == 3) {
-        qs[t * 3 + 1] = cff_store(cff_conj(Qc));                         // conj(q)
-        qs[t * 3 + 2] = cff_store(cff_fma(cff_zero(), Qc, cff_conj(U)));  // channel cm: q conj(u)
+      for (int d = 0; d < f.nd; ++d) {
+        // channel cm: q_0 conj(u), the leaf-relative moment density
+        const double2 q = f.Q[(long long)i * f.nd + (d == f.cm ? 0 : d)];
+        const cff qd = cff_split(q.x, q.y);
+        qs[t * f.nd + d] = cff_store(d == f.cm ? cff_fma(cff_zero(), qd, cff_conj(U)) : qd);
       }
     }
     __syncthreads();
@@ -1806,7 +1806,10 @@ cudaError_t fmm_output(FmmState* f, const Geo& g, int kind, int p, const double*
   FmmDev d{f->L, f->nb, p, nd, g.M, nlog, -1, f->x0, f->y0, f->D, 1.0 / f->D, f->leaf, f->perm, f->start, f->count, f->tcount,
            f->Q, f->mp, f->lc, ops};
   const size_t sm_p2m = ((size_t)p * (kChunk + 1) + (size_t)kChunk * nd) * sizeof(double2);
-  k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
+  if (ff)
+    k_fmm_p2m_ff<<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);  // float4 = double2 in size
+  else
+    k_fmm_p2m<double2><<<f->nleaf, kB, sm_p2m, s>>>(d, g, nullptr);
   const size_t sm_tree = tree_smem<double2>(nd, p);
   for (int l = f->L - 1; l >= 2; --l) k_fmm_m2m<double2><<<1 << (2 * l), kB, sm_tree, s>>>(d, l, nullptr);
   const float* tab = nullptr;
